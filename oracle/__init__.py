@@ -1,0 +1,187 @@
+"""CPU oracle for differentiable Monte Carlo ray tracing through edge sampling.
+
+TEST INFRASTRUCTURE ONLY: tests, the package smoke check and the benchmark's
+CPU-baseline leg may use this module; the product path never does.
+
+A thin ctypes wrapper over ``oracle.cpp`` (see its header for the method and
+the precision rules).  Scenes are any object with the attributes of
+``paper_1904_12228_gb300.scenegen.Scene`` (numpy arrays), so this module
+imports nothing from the CUDA package.
+
+Parameter layout of gradients (length ``3V + 3T + 16``):
+  [0, 3V)            vertex positions, [V,3] row-major
+  [3V, 3V+3T)        per-triangle albedo, [T,3]
+  [3V+3T, +3)        light radiance (RGB)
+  [.., +12)          camera-to-world rows 0..2 (4 entries each)
+  [.., +1)           camera scale (tan(fov_y/2) or ortho half height)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import build
+
+TERM_INTERIOR = 1
+TERM_PRIMARY = 2
+TERM_SECONDARY = 4
+TERMS_ALL = 7
+
+EPS_REL = 2.0 ** -16
+
+_LIB = None
+
+
+class _Scene(ctypes.Structure):
+    _fields_ = [("n_verts", ctypes.c_int32), ("n_tris", ctypes.c_int32), ("n_light_tris", ctypes.c_int32),
+                ("cam_type", ctypes.c_int32), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("verts", ctypes.c_void_p), ("tris", ctypes.c_void_p), ("albedo", ctypes.c_void_p),
+                ("light_tris", ctypes.c_void_p), ("radiance", ctypes.c_void_p), ("cam_to_world", ctypes.c_void_p),
+                ("cam_scale", ctypes.c_float)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("spp", ctypes.c_int32), ("edge_spp", ctypes.c_int32), ("max_depth", ctypes.c_int32),
+                ("primary_only", ctypes.c_int32), ("seed", ctypes.c_uint64), ("eps_rel", ctypes.c_float),
+                ("terms", ctypes.c_int32), ("pix_begin", ctypes.c_int32), ("pix_end", ctypes.c_int32),
+                ("edge_begin", ctypes.c_int64), ("edge_end", ctypes.c_int64), ("n_threads", ctypes.c_int32),
+                ("scene_id", ctypes.c_int32)]
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        _LIB = ctypes.CDLL(build())
+    return _LIB
+
+
+def n_threads_default() -> int:
+    return max(1, len(os.sched_getaffinity(0)))
+
+
+class _Pinned:
+    """Keeps the numpy arrays alive while the C structure points at them."""
+
+    def __init__(self, scene):
+        self.arrays = [np.ascontiguousarray(a, dtype=t) for a, t in (
+            (scene.verts, np.float32), (scene.tris, np.int32), (scene.albedo, np.float32),
+            (scene.light_tris, np.int32), (scene.radiance, np.float32), (scene.cam_to_world, np.float32))]
+        v, t, a, lt, r, c = self.arrays
+        self.s = _Scene(len(v), len(t), len(lt), int(scene.cam_type), int(scene.width), int(scene.height),
+                        v.ctypes.data, t.ctypes.data, a.ctypes.data, lt.ctypes.data, r.ctypes.data, c.ctypes.data,
+                        float(scene.cam_scale))
+
+
+def _opts(spp, edge_spp, max_depth, primary_only, seed, eps_rel, terms, pixels, edges, n_threads, scene_id):
+    pb, pe = pixels if pixels is not None else (0, 0)
+    eb, ee = edges if edges is not None else (0, 0)
+    return _Opts(int(spp), int(edge_spp), int(max_depth), int(bool(primary_only)), int(seed) & (2 ** 64 - 1),
+                 float(eps_rel), int(terms), int(pb), int(pe), int(eb), int(ee),
+                 int(n_threads or n_threads_default()), int(scene_id))
+
+
+def num_params(scene) -> int:
+    return 3 * len(scene.verts) + 3 * len(scene.tris) + 3 + 13
+
+
+def split_params(scene, g: np.ndarray) -> dict:
+    """Split a flat gradient into named parts."""
+    V, T = len(scene.verts), len(scene.tris)
+    o = 0
+    out = {}
+    for name, n, shape in (("verts", 3 * V, (V, 3)), ("albedo", 3 * T, (T, 3)), ("radiance", 3, (3,)),
+                           ("cam_to_world", 12, (3, 4)), ("cam_scale", 1, (1,))):
+        out[name] = g[o:o + n].reshape(shape)
+        o += n
+    return out
+
+
+def render(scene, *, spp: int, seed: int, max_depth: int = 1, primary_only: bool = False,
+           pixels=None, n_threads=None, scene_id: int = 0) -> np.ndarray:
+    """Image [H,W,3] (FP64).  ``pixels=(begin,end)`` restricts to a linear
+    pixel range; other pixels are NaN."""
+    P = _Pinned(scene)
+    o = _opts(spp, spp, max_depth, primary_only, seed, EPS_REL, 0, pixels, None, n_threads, scene_id)
+    img = np.full((scene.height, scene.width, 3), np.nan, np.float64)
+    rc = lib().or_render(ctypes.byref(P.s), ctypes.byref(o), img.ctypes.data_as(ctypes.c_void_p))
+    if rc != 0:
+        raise RuntimeError("oracle render failed (%d)" % rc)
+    return img
+
+
+def backward(scene, d_image: np.ndarray, *, spp: int, edge_spp: int, seed: int, max_depth: int = 1,
+             primary_only: bool = False, terms: int = TERMS_ALL, eps_rel: float = EPS_REL, pixels=None,
+             edges=None, n_threads=None, scene_id: int = 0):
+    """Gradient of sum(d_image * image) as a flat FP64 vector, and the sum of
+    |contribution| per entry (the tolerance scale of each entry)."""
+    P = _Pinned(scene)
+    w = np.ascontiguousarray(d_image, dtype=np.float32).reshape(scene.height, scene.width, 3)
+    o = _opts(spp, edge_spp, max_depth, primary_only, seed, eps_rel, terms, pixels, edges, n_threads, scene_id)
+    n = num_params(scene)
+    g = np.zeros(n, np.float64)
+    a = np.zeros(n, np.float64)
+    rc = lib().or_backward(ctypes.byref(P.s), ctypes.byref(o), w.ctypes.data_as(ctypes.c_void_p),
+                           g.ctypes.data_as(ctypes.c_void_p), a.ctypes.data_as(ctypes.c_void_p))
+    if rc != 0:
+        raise RuntimeError("oracle backward failed (%d)" % rc)
+    return g, a
+
+
+def philox(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, np.uint32)
+    k = np.ascontiguousarray(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().or_philox(c.ctypes.data_as(ctypes.c_void_p), k.ctypes.data_as(ctypes.c_void_p),
+                    out.ctypes.data_as(ctypes.c_void_p))
+    return out
+
+
+def closest(scene, o: np.ndarray, d: np.ndarray, n_threads=None):
+    """Brute-force closest hits for rays [N,3]: (tri [N], (t,b1,b2) [N,3])."""
+    P = _Pinned(scene)
+    o = np.ascontiguousarray(o, np.float32).reshape(-1, 3)
+    d = np.ascontiguousarray(d, np.float32).reshape(-1, 3)
+    n = len(o)
+    tri = np.zeros(n, np.int32)
+    tb = np.zeros((n, 3), np.float32)
+    lib().or_closest_batch(ctypes.byref(P.s), ctypes.c_int(n), o.ctypes.data_as(ctypes.c_void_p),
+                           d.ctypes.data_as(ctypes.c_void_p), ctypes.c_int(n_threads or n_threads_default()),
+                           tri.ctypes.data_as(ctypes.c_void_p), tb.ctypes.data_as(ctypes.c_void_p))
+    return tri, tb
+
+
+def edges(scene) -> np.ndarray:
+    P = _Pinned(scene)
+    cap = 3 * len(scene.tris)
+    out = np.zeros((cap, 2), np.int32)
+    n = lib().or_edges(ctypes.byref(P.s), out.ctypes.data_as(ctypes.c_void_p), ctypes.c_int(cap))
+    return out[:n]
+
+
+def primary_edges(scene) -> np.ndarray:
+    """[E,7] = (ax, ay, bx, by, t0, t1, clipped screen length)."""
+    P = _Pinned(scene)
+    cap = 3 * len(scene.tris)
+    out = np.zeros((cap, 7), np.float64)
+    n = lib().or_primary_edges(ctypes.byref(P.s), out.ctypes.data_as(ctypes.c_void_p), ctypes.c_int(cap))
+    return out[:n]
+
+
+def sincos_2pi(r: float):
+    c = ctypes.c_float()
+    s = ctypes.c_float()
+    lib().or_sincos_2pi(ctypes.c_float(r), ctypes.byref(c), ctypes.byref(s))
+    return c.value, s.value
+
+
+def sec_edge_forms(p, v0, v1, t, nm, plane_d) -> np.ndarray:
+    """Area-form and solid-angle-form secondary edge weights (see oracle.cpp)."""
+    arr = [np.ascontiguousarray(x, np.float64) for x in (p, v0, v1, nm)]
+    out = np.zeros(12, np.float64)
+    lib().or_sec_edge_forms(arr[0].ctypes.data_as(ctypes.c_void_p), arr[1].ctypes.data_as(ctypes.c_void_p),
+                            arr[2].ctypes.data_as(ctypes.c_void_p), ctypes.c_double(t),
+                            arr[3].ctypes.data_as(ctypes.c_void_p), ctypes.c_double(plane_d),
+                            out.ctypes.data_as(ctypes.c_void_p))
+    return out

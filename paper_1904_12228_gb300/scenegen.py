@@ -1,0 +1,156 @@
+"""Seeded synthetic scene generators.
+
+These build the inputs that both the CUDA path and the CPU oracle consume:
+triangle meshes, per-triangle albedo, area lights, cameras and loss adjoints.
+They hold none of the rendering method's arithmetic (no projection, edge
+extraction, shading or sampling); they only place geometry, the way the
+thesis's scenes are built from lists of tensors (Sec. 5.4).
+
+Every generator is deterministic in its ``seed``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+CAM_ORTHO = 0
+CAM_PINHOLE = 1
+
+
+@dataclasses.dataclass
+class Scene:
+    """A triangle-mesh scene in host memory (float32 / int32, C order).
+
+    verts [V,3]; tris [T,3] (counter-clockwise seen from the front);
+    albedo [T,3]; light_tris [L] indices of emitting triangles (front face
+    only); radiance [3]; cam_to_world [4,4] row-major (camera looks down -z,
+    y up); cam_scale = tan(fov_y/2) for a pinhole camera or the half height
+    of the view for an orthographic one; image width x height.
+    """
+
+    verts: np.ndarray
+    tris: np.ndarray
+    albedo: np.ndarray
+    light_tris: np.ndarray
+    radiance: np.ndarray
+    cam_to_world: np.ndarray
+    cam_scale: float
+    cam_type: int
+    width: int
+    height: int
+
+    def __post_init__(self):
+        self.verts = np.ascontiguousarray(self.verts, dtype=np.float32).reshape(-1, 3)
+        self.tris = np.ascontiguousarray(self.tris, dtype=np.int32).reshape(-1, 3)
+        self.albedo = np.ascontiguousarray(self.albedo, dtype=np.float32).reshape(-1, 3)
+        self.light_tris = np.ascontiguousarray(self.light_tris, dtype=np.int32).reshape(-1)
+        self.radiance = np.ascontiguousarray(self.radiance, dtype=np.float32).reshape(3)
+        self.cam_to_world = np.ascontiguousarray(self.cam_to_world, dtype=np.float32).reshape(4, 4)
+        self.cam_scale = float(np.float32(self.cam_scale))
+
+    @property
+    def n_params(self) -> int:
+        return 3 * len(self.verts) + 3 * len(self.tris) + 3 + 13
+
+    def copy(self) -> "Scene":
+        return dataclasses.replace(self, verts=self.verts.copy(), tris=self.tris.copy(),
+                                   albedo=self.albedo.copy(), light_tris=self.light_tris.copy(),
+                                   radiance=self.radiance.copy(), cam_to_world=self.cam_to_world.copy())
+
+
+def look_at(eye, target, up=(0.0, 1.0, 0.0)) -> np.ndarray:
+    """Camera-to-world matrix whose -z axis points from eye to target."""
+    eye = np.asarray(eye, np.float64)
+    f = np.asarray(target, np.float64) - eye
+    f /= np.linalg.norm(f)
+    x = np.cross(f, np.asarray(up, np.float64))
+    x /= np.linalg.norm(x)
+    y = np.cross(x, f)
+    m = np.eye(4)
+    m[:3, 0], m[:3, 1], m[:3, 2], m[:3, 3] = x, y, -f, eye
+    return m.astype(np.float32)
+
+
+def icosphere(subdiv: int) -> tuple[np.ndarray, np.ndarray]:
+    """Unit icosphere by midpoint subdivision (20 * 4**subdiv faces)."""
+    t = (1.0 + math.sqrt(5.0)) / 2.0
+    v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
+         (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    verts = [np.array(p, np.float64) / np.linalg.norm(p) for p in v]
+    faces = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2),
+             (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5),
+             (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(subdiv):
+        cache: dict[tuple[int, int], int] = {}
+
+        def mid(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in cache:
+                m = verts[a] + verts[b]
+                verts.append(m / np.linalg.norm(m))
+                cache[key] = len(verts) - 1
+            return cache[key]
+
+        nf = []
+        for a, b, c in faces:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = nf
+    return np.array(verts), np.array(faces, np.int64)
+
+
+def quad(center, ex, ey) -> tuple[np.ndarray, np.ndarray]:
+    """Two triangles spanning center +- ex +- ey; front normal = ex x ey."""
+    c, ex, ey = (np.asarray(a, np.float64) for a in (center, ex, ey))
+    v = np.array([c - ex - ey, c + ex - ey, c + ex + ey, c - ex + ey])
+    return v, np.array([[0, 1, 2], [0, 2, 3]], np.int64)
+
+
+def _merge(parts):
+    verts, tris, off = [], [], 0
+    for v, f in parts:
+        verts.append(v)
+        tris.append(f + off)
+        off += len(v)
+    return np.concatenate(verts), np.concatenate(tris)
+
+
+def single_triangle(seed: int, width: int = 64, height: int = 64, color: float = 0.7) -> Scene:
+    """One triangle with vertices uniform in [-1,1]^2 (z=0) under an
+    orthographic camera at z=1 spanning [-1,1]^2; constant color over black."""
+    rng = np.random.default_rng(seed)
+    xy = rng.uniform(-1.0, 1.0, size=(3, 2))
+    verts = np.concatenate([xy, np.zeros((3, 1))], axis=1)
+    cam = np.eye(4, dtype=np.float32)
+    cam[2, 3] = 1.0
+    return Scene(verts=verts, tris=[[0, 1, 2]], albedo=[[color] * 3], light_tris=np.zeros(0, np.int32),
+                 radiance=[0, 0, 0], cam_to_world=cam, cam_scale=1.0, cam_type=CAM_ORTHO, width=width,
+                 height=height)
+
+
+def direct_lighting(seed: int, width: int = 256, height: int = 256, subdiv: int = 4,
+                    jitter: float = 0.01) -> Scene:
+    """Jittered icosphere (radius 1) on a 2-triangle ground at y=-1 spanning
+    [-4,4]^2, lit by a 1x1 two-triangle area light at y=3 facing down with
+    radiance 10; per-triangle albedo uniform in [0.2,0.8]^3; pinhole camera
+    at (0,1,5) looking at the origin, 45 degree vertical field of view."""
+    rng = np.random.default_rng(seed)
+    sv, sf = icosphere(subdiv)
+    sv = sv + rng.normal(0.0, jitter, size=sv.shape)
+    gv, gf = quad((0, -1, 0), (0, 0, 4), (4, 0, 0))
+    lv, lf = quad((0, 3, 0), (0.5, 0, 0), (0, 0, 0.5))
+    verts, tris = _merge([(sv, sf), (gv, gf), (lv, lf)])
+    n = len(tris)
+    albedo = rng.uniform(0.2, 0.8, size=(n, 3))
+    light_tris = np.array([n - 2, n - 1], np.int32)
+    return Scene(verts=verts, tris=tris, albedo=albedo, light_tris=light_tris, radiance=[10.0, 10.0, 10.0],
+                 cam_to_world=look_at((0, 1, 5), (0, 0, 0)), cam_scale=math.tan(math.radians(22.5)),
+                 cam_type=CAM_PINHOLE, width=width, height=height)
+
+
+def loss_adjoint(seed: int, width: int, height: int) -> np.ndarray:
+    """d loss / d image, uniform in [-1,1] per pixel and channel, [H,W,3]."""
+    rng = np.random.default_rng(seed + 7919)
+    return rng.uniform(-1.0, 1.0, size=(height, width, 3)).astype(np.float32)
