@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Benchmark: forward + backward samples/s of differentiable Monte Carlo ray
+tracing with edge sampling on the direct-lighting workload.
+
+Workload (one step): 256x256 image of a jittered icosphere (5120 triangles)
+on a 2-triangle ground, lit by a 2-triangle area light; 64 samples per pixel
+with one shadow ray each, 64 primary edge samples per pixel, one secondary
+edge sample per interior sample.  A step is the whole hot path: vertex
+update (LBVH rebuild, edge CDFs), render with a checkpoint tape, and the
+backward pass (interior adjoint, secondary and primary edge terms, gradient
+scatter).  Inputs are synthetic and seeded.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  For N > 1 (torchrun) every rank renders its
+own replica and the value is the aggregate over ranks ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd samples/sec and gradient variance x time vs plain edge sampler, 1 GB300"
+UNIT = "samples/s"
+W_IMG, H_IMG, SPP, EDGE_SPP = 256, 256, 64, 64
+SCENE_SEED = 1236
+WORKLOAD = ("direct lighting 256x256: jittered icosphere (5120 tris) + 2-tri ground + 2-tri area light; "
+            "64 spp with 1 shadow ray, 64 primary edge spp, 1 secondary edge sample per path vertex; "
+            "step = vertex update (LBVH + edge CDFs) + render + backward (all gradient terms)")
+# FP32 lane-operations of one BVH node visit (two slab tests) and one
+# watertight triangle test, counted from the kernels' arithmetic.
+OPS_PER_NODE = 46
+OPS_PER_TRI = 45
+SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def peak_alu_tops():
+    return SMS * LANES * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in ("paper_1904_12228_gb300/csrc/render.cu", "paper_1904_12228_gb300/csrc/drt_device.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            t = json.load(f)
+        ent = t.get(kernel)
+        if ent and ent.get("source_hash") == kernel_source_hash():
+            return ent.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device, self.proc = device, None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), max=float(f[2]), reasons=f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        seen = sorted({names[i] for r in rows for i, v in enumerate(r["reasons"]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["max"] for r in rows),
+                "reasons": seen, "samples": len(rows)}
+
+
+def cpu_workload_sample(seconds_target, n_threads):
+    """Time the CPU oracle on a bounded sample of the same workload: a block
+    of pixels (all spp, interior + secondary edges) and a proportional range
+    of primary edge samples.  Returns (samples/s, description, cores)."""
+    import oracle
+    from paper_1904_12228_gb300 import scenegen as sg
+    scene = sg.direct_lighting(SCENE_SEED)
+    w = sg.loss_adjoint(1, W_IMG, H_IMG)
+    p0 = (H_IMG // 2) * W_IMG + W_IMG // 4
+
+    def run(npix):
+        t = time.perf_counter()
+        oracle.render(scene, spp=SPP, seed=1, pixels=(p0, p0 + npix), n_threads=n_threads)
+        oracle.backward(scene, w, spp=SPP, edge_spp=EDGE_SPP, seed=1, pixels=(p0, p0 + npix),
+                        edges=(0, npix * EDGE_SPP), n_threads=n_threads)
+        return time.perf_counter() - t
+
+    n = 4
+    dt = run(n)
+    while dt < 0.15 * seconds_target and n < 4096:
+        n *= 4
+        dt = run(n)
+    if dt < seconds_target and n < 4096:
+        n2 = int(min(4096, n * seconds_target / max(dt, 1e-3)))
+        if n2 > n:
+            n, dt = n2, run(n2)
+    samples = n * SPP
+    desc = ("oracle, %d pixels x %d spp (render + backward with all terms) + %d primary edge samples of the "
+            "256x256 workload, brute-force intersection over 5124 triangles" % (n, SPP, n * EDGE_SPP))
+    return samples / dt, desc, n_threads, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cores = oracle.n_threads_default()
+    per_step = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    vals = []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        v, desc, cores, dt = cpu_workload_sample(per_step, cores)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    from paper_1904_12228_gb300 import drt
+    from paper_1904_12228_gb300 import scenegen as sg
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    ctx = drt.Context(local)
+    scene = sg.direct_lighting(SCENE_SEED + rank)
+    S = drt.Scene.from_arrays(ctx, scene)
+    V, T = len(scene.verts), len(scene.tris)
+    verts = torch.from_numpy(scene.verts).to(dev)
+    d_image = torch.from_numpy(sg.loss_adjoint(1 + rank, W_IMG, H_IMG)).to(dev)
+    image = torch.zeros((H_IMG, W_IMG, 3), device=dev)
+    g = dict(d_verts=torch.zeros((V, 3), device=dev), d_albedo=torch.zeros((T, 3), device=dev),
+             d_radiance=torch.zeros(3, device=dev), d_cam_to_world=torch.zeros((3, 4), device=dev),
+             d_cam_scale=torch.zeros(1, device=dev))
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    tape = S.render(image, drt.make_opts(SPP, EDGE_SPP, seed=0), want_tape=True)
+    n_samples = W_IMG * H_IMG * SPP
+
+    def step(k):
+        opts = drt.make_opts(SPP, EDGE_SPP, seed=1000 + k)
+        S.update_vertices(verts)
+        S.render(image, opts, reuse=tape)
+        S.backward(d_image, opts, tape=tape, **g)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    code, info = ctx.check_device()
+    if code != 0:
+        raise RuntimeError("device error flag %d (%d) during warm-up" % (code, info))
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ctx.profile(True)
+    ctx.profile_read()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            flush.zero_()                      # L2 flush between timed steps (not timed)
+            starts[k].record()
+            step(args.warmup + k)
+            ends[k].record()
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * n_samples / (ms_per_step / 1e3)
+
+    # work counters of one extra (untimed) step
+    ctx.counters(True)
+    ctx.counters_read()
+    step(0)
+    cnt = ctx.counters_read()
+    ctx.counters(False)
+    rays = sum(c["closest_rays"] + c["shadow_rays"] for c in cnt.values())
+
+    # dominant kernel and its roofline
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_launches) = dom
+    avg_ms = dom_ms / dom_launches
+    c = cnt.get(dom_name)
+    roof = None
+    if c:
+        ops = OPS_PER_NODE * c["nodes"] + OPS_PER_TRI * c["tris"]
+        achieved = ops / (avg_ms / 1e3) / 1e12
+        peak = peak_alu_tops()
+        traffic = ncu_traffic(dom_name)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": dom_name, "avg_launch_ms": avg_ms,
+                "algorithmic_ops_per_launch": ops,
+                "l1l2_bytes_per_launch": 64 * c["nodes"] + 48 * c["tris"],
+                "peak_note": "152 SMs x 128 FP32 lanes x 2070 MHz (recipe unit counts and max clock)"}
+    gpu_launches = sum(v[1] for v in prof.values())
+
+    # end to end through the API with host buffers
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    h_verts = pin(scene.verts)
+    h_dimg = pin(d_image.cpu().numpy())
+    h_img = torch.zeros((H_IMG, W_IMG, 3)).pin_memory()
+    hg = dict(d_verts=torch.zeros((V, 3)).pin_memory(), d_albedo=torch.zeros((T, 3)).pin_memory(),
+              d_radiance=torch.zeros(3).pin_memory(), d_cam_to_world=torch.zeros((3, 4)).pin_memory(),
+              d_cam_scale=torch.zeros(1).pin_memory())
+
+    def e2e_step(k):
+        opts = drt.make_opts(SPP, EDGE_SPP, seed=2000 + k)
+        S.update_vertices(h_verts)
+        S.render(h_img, opts, reuse=tape)
+        S.backward(h_dimg, opts, tape=tape, **hg)
+
+    for k in range(2):
+        e2e_step(k)
+    torch.cuda.synchronize()
+    ke = max(3, args.steps // 4)
+    t0 = time.perf_counter()
+    for k in range(ke):
+        e2e_step(k)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / ke
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    grad_bytes = 4 * (3 * V + 3 * T + 3 + 12 + 1)
+    h2d = 12 * V + 12 * W_IMG * H_IMG + grad_bytes
+    d2h = 12 * W_IMG * H_IMG + grad_bytes
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        v, desc, cores, dt = cpu_workload_sample(args.cpu_seconds, oracle.n_threads_default())
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc, "seconds": dt}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "width": W_IMG, "height": H_IMG, "spp": SPP, "edge_spp": EDGE_SPP,
+                           "triangles": T, "l2": "flushed between timed steps (256 MiB write)",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "rays_per_s": world * rays / (ms_per_step / 1e3),
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": world * n_samples / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": gpu_launches,
+                "kernels": {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items()},
+                "counters": cnt, "clocks": clocks.summary(),
+                "peaks": {k: measured_peaks().get(k) for k in ("hbm_gbs", "bf16_tflops")}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * drt.h -- C ABI of the GB300 differentiable Monte Carlo ray tracer with edge
+ * sampling (T.-M. Li, "Differentiable Visual Computing", Chapter 5).
+ *
+ * The library renders a triangle-mesh scene by Monte Carlo ray tracing and
+ * returns the gradient of a scalar loss of the image with respect to vertex
+ * positions, per-triangle albedo, light radiance and camera (the problem
+ * statement of Sec. 5.2).  The gradient is the sum of
+ *   - the interior term: reverse-mode derivative of the per-sample integrand
+ *     (second integral of Eq. redner_product_rule), and
+ *   - the edge terms: explicitly sampled points on triangle edges, the
+ *     radiance difference across each edge (Eq. dirac_rewrite, Eq. mc for
+ *     primary visibility; Eq. dirac_3d, Eq. dirac_3d_edge, Eq. alpha_3d for
+ *     shadows and indirect light).
+ *
+ * Conventions shared by every call
+ *   - Pointers to arrays may be device memory or host memory; the library
+ *     checks each with cudaPointerGetAttributes.  Host inputs are copied to the
+ *     device on `stream`; when an OUTPUT pointer is host memory the call
+ *     synchronises `stream` before returning so the data is there.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All device
+ *     work of a call is enqueued on it, in order.
+ *   - Arrays are C-order float32 / int32 unless stated.  Images are [H,W,3],
+ *     row 0 at the top of the view.
+ *   - Every call returns a drt_status; none throws.  drt_last_error() gives a
+ *     message for the last failing call on this thread.
+ *   - Objects (context, scene, tape) are owned by the library and freed with
+ *     the matching *_free / drt_destroy call.  Caller arrays are borrowed for
+ *     the duration of the call only; the library keeps its own copies.
+ */
+#ifndef DRT_H
+#define DRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DRT_OK = 0,
+  DRT_ERR_INVALID_ARG = 1, /* bad size, index, NaN/Inf input, NULL where not allowed */
+  DRT_ERR_CUDA = 2,        /* a CUDA runtime call failed (message has the CUDA error) */
+  DRT_ERR_OOM = 3,         /* device allocation failed */
+  DRT_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
+  DRT_ERR_DEVICE_FLAG = 5, /* a kernel raised the device error flag (see drt_check_device) */
+  DRT_ERR_STATE = 6        /* call out of order (e.g. backward with a tape of another scene) */
+} drt_status;
+
+/* Device error-flag codes, read back by drt_check_device. */
+enum {
+  DRT_DEV_OK = 0,
+  DRT_DEV_STACK_OVERFLOW = 1,  /* traversal stack full: a subtree was skipped (info = node) */
+  DRT_DEV_NONFINITE_INPUT = 2, /* NaN/Inf vertex coordinate (info = flat index) */
+  DRT_DEV_BAD_INDEX = 3,       /* out-of-range index met on the device */
+  DRT_DEV_TRAVERSAL_CAP = 4,   /* traversal visited more nodes than the tree has (malformed BVH) */
+  DRT_DEV_REFIT_CAP = 5        /* BVH refit climbed more levels than there are nodes */
+};
+
+typedef struct drt_context drt_context;
+typedef struct drt_scene drt_scene;
+typedef struct drt_tape drt_tape;
+
+enum { DRT_CAMERA_ORTHO = 0, DRT_CAMERA_PINHOLE = 1 };
+
+/* A scene given as flat arrays, the way Sec. 5.4 builds scenes from tensors
+ * (float vertices, integer indices, material, light and camera).  All triangles are both occluders and reflectors
+ * (two-sided Lambertian, flat face normal); triangles listed in light_tris
+ * also emit `radiance` from their front face (counter-clockwise winding). */
+typedef struct {
+  const float* verts;          /* [n_verts,3] world positions */
+  int32_t n_verts;
+  const int32_t* tris;         /* [n_tris,3] vertex indices */
+  int32_t n_tris;
+  const float* albedo;         /* [n_tris,3] Lambertian albedo (or constant colour, see primary_only) */
+  const int32_t* light_tris;   /* [n_light_tris] indices into tris; may be NULL if n_light_tris == 0 */
+  int32_t n_light_tris;
+  const float* radiance;       /* [3] emitted radiance of every light triangle */
+  const float* cam_to_world;   /* [4,4] row-major affine camera matrix; camera looks down -z, y up */
+  float cam_scale;             /* pinhole: tan(fov_y/2); ortho: half height of the view */
+  int32_t cam_type;            /* DRT_CAMERA_ORTHO or DRT_CAMERA_PINHOLE */
+  int32_t width, height;       /* image size in pixels */
+} drt_scene_desc;
+
+/* Sampling options of one render/backward pair. */
+typedef struct {
+  int32_t spp;          /* interior samples per pixel (Eq. gradient_monte_carlo) */
+  int32_t edge_spp;     /* primary edge samples = edge_spp * width * height, spread over the
+                           screen by the edge-length CDF (Sec. 5.2.1) */
+  int32_t max_depth;    /* scattering vertices per path: 1 = direct lighting; >1 path tracing */
+  int32_t primary_only; /* 1: radiance = albedo of the first hit (no lighting), 0: lit */
+  uint64_t seed;        /* Philox key */
+  float eps_rel;        /* edge side offset: eps_rel*max(W,H) pixels for primary edges and
+                           eps_rel*|omega| for secondary edges (the two-sided evaluation of
+                           Sec. 5.2.1 needs a small offset); <= 0 selects 2^-16 */
+  int32_t terms;        /* gradient terms: bit0 interior, bit1 primary edges, bit2 secondary
+                           edges; 0 selects all */
+} drt_render_opts;
+
+/* Gradient outputs: device or host arrays, each may be NULL (not wanted).
+ * Values are ADDED to what the arrays hold. */
+typedef struct {
+  float* d_verts;        /* [n_verts,3] */
+  float* d_albedo;       /* [n_tris,3] */
+  float* d_radiance;     /* [3] */
+  float* d_cam_to_world; /* [3,4] rows 0..2 of the camera matrix */
+  float* d_cam_scale;    /* [1] */
+} drt_grads;
+
+/* Create a context on CUDA device `device` (owns the device error flag and
+ * scratch pools).  out receives the handle. */
+drt_status drt_create(int device, drt_context** out);
+drt_status drt_destroy(drt_context* ctx);
+
+/* Upload a scene and build everything derived from it: the LBVH over the
+ * triangles (Morton codes, radix sort, Karras hierarchy, bottom-up refit), the
+ * unique edge list, the light-area CDF, the CDF of projected and clipped
+ * screen-space edge lengths used to pick primary edges (Sec. 5.2.1) and the
+ * 3D edge-length CDF for secondary visibility.  Enqueued on stream.
+ * Errors: DRT_ERR_INVALID_ARG for out-of-range indices or sizes (checked on
+ * the host); non-finite vertices raise the device flag. */
+drt_status drt_scene_upload(drt_context* ctx, const drt_scene_desc* desc, void* stream, drt_scene** out);
+
+/* Replace the vertex positions (same topology) and rebuild the LBVH and the
+ * edge CDFs -- one step of an optimisation loop.  verts: [n_verts,3]. */
+drt_status drt_scene_update_vertices(drt_context* ctx, drt_scene* scene, const float* verts, void* stream);
+
+/* Replace per-triangle albedo [n_tris,3] / radiance [3] / camera [4,4] and scale. */
+drt_status drt_scene_update_params(drt_context* ctx, drt_scene* scene, const float* albedo, const float* radiance,
+                                   const float* cam_to_world, const float* cam_scale, void* stream);
+drt_status drt_scene_free(drt_context* ctx, drt_scene* scene);
+
+/* Forward pass (Eq. first estimated by Eq. gradient_monte_carlo): image
+ * [H,W,3] = per-pixel mean of spp path samples with next-event estimation at
+ * every vertex.  If tape != NULL every path vertex is checkpointed (the
+ * per-vertex checkpointing of Sec. 5.4) in a library-owned tape that the
+ * backward pass reads (12 bytes per sample and vertex); free it with
+ * drt_tape_free.  If *tape already holds a tape of this scene large enough
+ * for these options it is overwritten in place (no allocation); any other
+ * non-NULL *tape is freed and replaced. */
+drt_status drt_render(drt_context* ctx, drt_scene* scene, const drt_render_opts* opts, float* image,
+                      drt_tape** tape, void* stream);
+
+/* Backward pass: given d_image = d loss / d image [H,W,3], ADD d loss / d
+ * parameter to grads.  Interior term: hand-written reverse sweep over the
+ * checkpointed path, from the last vertex back to the camera (Sec. 5.4).
+ * Primary edges: Eq. mc with the edge-equation derivatives of
+ * Eq. redner_dirac_jacobian, chained through the projection.  Secondary
+ * edges: Eq. dirac_3d_edge at every path vertex.  tape must come from
+ * drt_render on this scene with the same opts (else DRT_ERR_STATE); tape may
+ * be NULL, in which case the camera paths are traced again. */
+drt_status drt_render_backward(drt_context* ctx, drt_scene* scene, const drt_tape* tape,
+                               const drt_render_opts* opts, const float* d_image, const drt_grads* grads,
+                               void* stream);
+drt_status drt_tape_free(drt_context* ctx, drt_tape* tape);
+
+/* Closest-hit query through the scene's LBVH for n rays (test and debug
+ * entry point; the render kernels use the same traversal).  o, d: [n,3]
+ * origins and directions; tri: [n] hit triangle or -1; tb1b2: [n,3] =
+ * (t, b1, b2).  Hits have t > 0, ties on t go to the lowest triangle id
+ * (Sec. 5.2.1 relies on exact visibility; see the watertight test of Woop et
+ * al. 2013 used for every ray). */
+drt_status drt_debug_closest(drt_context* ctx, drt_scene* scene, int64_t n, const float* o, const float* d,
+                             int32_t* tri, float* tb1b2, void* stream);
+
+/* Profiling (off by default).  When enabled, every kernel launch of the
+ * library is bracketed by CUDA events recorded on its stream; drt_profile_read
+ * synchronises on them and returns, per kernel name (first-launch order), the
+ * summed device time in ms and the launch count, then clears the record.
+ * names: [max][64] chars (may be NULL); ms, launches: [max]; *n: entries. */
+drt_status drt_profile_enable(drt_context* ctx, int enable);
+drt_status drt_profile_read(drt_context* ctx, int max, char* names, double* ms, int64_t* launches, int* n);
+
+/* Work counters (off by default): per kernel slot (0 render, 1 backward
+ * interior, 2 backward primary edges, 3 debug) four int64 counts -- rays
+ * traced to the closest hit, shadow rays, BVH nodes visited, triangle tests.
+ * drt_counters_read synchronises the device, copies [4][4] counts to out and
+ * resets them. */
+drt_status drt_counters_enable(drt_context* ctx, int enable);
+drt_status drt_counters_read(drt_context* ctx, int64_t* out);
+
+/* Synchronise stream and read the device error flag: DRT_OK, or
+ * DRT_ERR_DEVICE_FLAG with *code / *info (may be NULL) set and the flag
+ * cleared. */
+drt_status drt_check_device(drt_context* ctx, void* stream, int32_t* code, int32_t* info);
+
+/* Message of the last failing call on this thread (static storage). */
+const char* drt_last_error(void);
+
+/* Library version string. */
+const char* drt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DRT_H */

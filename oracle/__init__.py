@@ -114,8 +114,9 @@ def render(scene, *, spp: int, seed: int, max_depth: int = 1, primary_only: bool
 def backward(scene, d_image: np.ndarray, *, spp: int, edge_spp: int, seed: int, max_depth: int = 1,
              primary_only: bool = False, terms: int = TERMS_ALL, eps_rel: float = EPS_REL, pixels=None,
              edges=None, n_threads=None, scene_id: int = 0):
-    """Gradient of sum(d_image * image) as a flat FP64 vector, and the sum of
-    |contribution| per entry (the tolerance scale of each entry)."""
+    """Gradient of sum(d_image * image) as a flat FP64 vector, and per entry
+    the magnitude of the terms summed into it (absolute-value chain rule),
+    which scales the rounding error an FP32 implementation may make."""
     P = _Pinned(scene)
     w = np.ascontiguousarray(d_image, dtype=np.float32).reshape(scene.height, scene.width, 3)
     o = _opts(spp, edge_spp, max_depth, primary_only, seed, eps_rel, terms, pixels, edges, n_threads, scene_id)

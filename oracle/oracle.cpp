@@ -81,6 +81,14 @@ double u01d(uint32_t x0, uint32_t x1) {
 
 /* ------------------------------------------------------------------------ */
 /* Sparse forward-mode dual numbers, FP64 (Sec. 2.2.1).                      */
+/*                                                                           */
+/* Beside each derivative d the dual carries ad, the same chain rule taken  */
+/* with absolute values of every partial (|c_a| ad_a + |c_b| ad_b).  ad is  */
+/* the magnitude of the terms that sum to d; where d is small by            */
+/* cancellation (in-plane motion of a plane, an edge of the light seen from */
+/* the light, an occluded edge whose two sides agree) an FP32              */
+/* implementation of the same chain rule errs by about u * ad, not u * |d|, */
+/* so parity tolerances are scaled by the sum of ad, not of |d|.            */
 /* ------------------------------------------------------------------------ */
 constexpr int MAXD = 192;
 bool g_dual_overflow = false;
@@ -90,21 +98,24 @@ struct Dual {
   int n = 0;
   int32_t idx[MAXD];
   double d[MAXD];
+  double ad[MAXD];
   Dual() {}
   Dual(double x) : v(x), n(0) {}
   Dual(const Dual& o) : v(o.v), n(o.n) {
     std::memcpy(idx, o.idx, sizeof(int32_t) * n);
     std::memcpy(d, o.d, sizeof(double) * n);
+    std::memcpy(ad, o.ad, sizeof(double) * n);
   }
   Dual& operator=(const Dual& o) {
     v = o.v; n = o.n;
     std::memcpy(idx, o.idx, sizeof(int32_t) * n);
     std::memcpy(d, o.d, sizeof(double) * n);
+    std::memcpy(ad, o.ad, sizeof(double) * n);
     return *this;
   }
   static Dual param(double x, int i, bool track) {
     Dual r(x);
-    if (track) { r.n = 1; r.idx[0] = i; r.d[0] = 1.0; }
+    if (track) { r.n = 1; r.idx[0] = i; r.d[0] = 1.0; r.ad[0] = 1.0; }
     return r;
   }
 };
@@ -113,15 +124,16 @@ struct Dual {
 Dual lin(double v, double ca, const Dual& a, double cb, const Dual& b) {
   Dual r(v);
   int i = 0, j = 0, n = 0;
+  double aa = std::fabs(ca), ab = std::fabs(cb);
   while (i < a.n || j < b.n) {
     int ia = i < a.n ? a.idx[i] : INT32_MAX;
     int ib = j < b.n ? b.idx[j] : INT32_MAX;
-    double dv; int id;
-    if (ia == ib) { id = ia; dv = ca * a.d[i++] + cb * b.d[j++]; }
-    else if (ia < ib) { id = ia; dv = ca * a.d[i++]; }
-    else { id = ib; dv = cb * b.d[j++]; }
+    double dv, av; int id;
+    if (ia == ib) { id = ia; dv = ca * a.d[i] + cb * b.d[j]; av = aa * a.ad[i++] + ab * b.ad[j++]; }
+    else if (ia < ib) { id = ia; dv = ca * a.d[i]; av = aa * a.ad[i++]; }
+    else { id = ib; dv = cb * b.d[j]; av = ab * b.ad[j++]; }
     if (n >= MAXD) { g_dual_overflow = true; break; }
-    r.idx[n] = id; r.d[n] = dv; ++n;
+    r.idx[n] = id; r.d[n] = dv; r.ad[n] = av; ++n;
   }
   r.n = n;
   return r;
@@ -129,7 +141,8 @@ Dual lin(double v, double ca, const Dual& a, double cb, const Dual& b) {
 Dual scaled(double v, double c, const Dual& a) {
   Dual r(v);
   r.n = a.n;
-  for (int i = 0; i < a.n; ++i) { r.idx[i] = a.idx[i]; r.d[i] = c * a.d[i]; }
+  double ac = std::fabs(c);
+  for (int i = 0; i < a.n; ++i) { r.idx[i] = a.idx[i]; r.d[i] = c * a.d[i]; r.ad[i] = ac * a.ad[i]; }
   return r;
 }
 Dual operator+(const Dual& a, const Dual& b) { return lin(a.v + b.v, 1.0, a, 1.0, b); }
@@ -213,8 +226,9 @@ constexpr double INV_PI = 0.31830988618379067;
 
 struct R32 { float o[3], d[3]; };
 
-/* Camera ray through screen point (sx, sy) in pixel units, y down (Sec. 5.2.1
- * "linear projective cameras"; pinhole looks down -z, y up; ortho spans
+/* Camera ray through screen point (sx, sy) in pixel units, y down.  Sec. 5.2.1
+ * restricts primary edges to cameras whose projection maps lines to lines:
+ * pinhole (looks down -z, y up) and orthographic (spans
  * [-aspect*s, aspect*s] x [-s, s] in camera xy). */
 R32 camera_ray32(const or_scene_t& sc, float sx, float sy) {
   const float* M = sc.cam_to_world;
@@ -609,11 +623,11 @@ struct Ctx {
   double* ga;            /* sum of |contribution| per parameter [P] */
 };
 
-void accumulate(Ctx& C, double coef, const Dual& x) {
+/* grad += coef * x';  tolerance scale += coef_abs * |x|' (see Dual). */
+void accumulate(Ctx& C, double coef, double coef_abs, const Dual& x) {
   for (int i = 0; i < x.n; ++i) {
-    double c = coef * x.d[i];
-    C.g[x.idx[i]] += c;
-    C.ga[x.idx[i]] += std::fabs(c);
+    C.g[x.idx[i]] += coef * x.d[i];
+    C.ga[x.idx[i]] += coef_abs * x.ad[i];
   }
 }
 
@@ -728,8 +742,11 @@ void secondary_edge(Ctx& C, int b, uint32_t c0, uint32_t c1, uint32_t pass, cons
       double cos_m = -vdot(nm, wh);
       if (cos_m > 0.0) {
         double G = cos_p * cos_m / r2;
-        double hs = 0.0;
-        for (int c = 0; c < 3; ++c) hs += wscale[c] * beta[c] * albedo_k[c] * INV_PI * Le[c] * G;
+        double hs = 0.0, hs_abs = 0.0;
+        for (int c = 0; c < 3; ++c) {
+          hs += wscale[c] * beta[c] * albedo_k[c] * INV_PI * Le[c] * G;
+          hs_abs += std::fabs(wscale[c]) * beta[c] * albedo_k[c] * INV_PI * Le[c] * G;
+        }
         double wn = vdot(w, nm);
         double tau = vdot(dm, nm) / wn;
         V3 J = tau * (E - (vdot(E, nm) / wn) * w);
@@ -740,7 +757,7 @@ void secondary_edge(Ctx& C, int b, uint32_t c0, uint32_t c1, uint32_t pass, cons
           D3 Md = w0 * vert_dual(P, M.i0, C.track) + w1 * vert_dual(P, M.i1, C.track) +
                   w2 * vert_dual(P, M.i2, C.track);
           Dual alpha = dot(Md - Pd, Nd);
-          accumulate(C, sgn * hs * W * inv_pe, alpha);
+          accumulate(C, sgn * hs * W * inv_pe, hs_abs * W * inv_pe, alpha);
         }
       }
     }
@@ -754,11 +771,14 @@ void secondary_edge(Ctx& C, int b, uint32_t c0, uint32_t c1, uint32_t pass, cons
       path_radiance(C, b + 1, max_depth, p32, ds, Oc, Dc, k, false, c0, c1, PASS_SECONDARY_BASE + (uint32_t)b,
                     zero, one, false, &Lr);
       C.track = saved;
-      double hs = 0.0;
-      for (int c = 0; c < 3; ++c) hs += wscale[c] * beta[c] * albedo_k[c] * INV_PI * cos_p * Lr.c[c].v;
+      double hs = 0.0, hs_abs = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        hs += wscale[c] * beta[c] * albedo_k[c] * INV_PI * cos_p * Lr.c[c].v;
+        hs_abs += std::fabs(wscale[c] * beta[c] * albedo_k[c] * INV_PI * cos_p * Lr.c[c].v);
+      }
       if (hs != 0.0) {
         Dual alpha = dot(d3(what.x, what.y, what.z), Nd);
-        accumulate(C, sgn * hs / wl2 * inv_pe, alpha);
+        accumulate(C, sgn * hs / wl2 * inv_pe, hs_abs / wl2 * inv_pe, alpha);
       }
     }
   }
@@ -913,8 +933,11 @@ void primary_edge_sample(Ctx& C, int64_t jj) {
   camera_path(C, xu, yu, j, 0, PASS_PRIMARY_EDGE, zero, false, &Lu);
   camera_path(C, xl, yl, j, 0, PASS_PRIMARY_EDGE, zero, false, &Ll);
   C.track = saved;
-  double diff = 0.0;
-  for (int c = 0; c < 3; ++c) diff += (double)w[c] * (Lu.c[c].v - Ll.c[c].v);
+  double diff = 0.0, diff_abs = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    diff += (double)w[c] * (Lu.c[c].v - Ll.c[c].v);
+    diff_abs += std::fabs((double)w[c]) * (std::fabs(Lu.c[c].v) + std::fabs(Ll.c[c].v));
+  }
   if (diff == 0.0) return;
   Dual Ax, Ay, Bx, By;
   project_dual(P, vert_dual(P, P.e0[e], C.track), C.track, &Ax, &Ay);
@@ -923,7 +946,8 @@ void primary_edge_sample(Ctx& C, int64_t jj) {
   Dual alpha = (Ay - By) * X + (Bx - Ax) * Y + (Ax * By - Bx * Ay);
   double gl = std::sqrt((Ax.v - Bx.v) * (Ax.v - Bx.v) + (Ay.v - By.v) * (Ay.v - By.v));
   int64_t N_edge = (int64_t)op.edge_spp * sc.width * sc.height;
-  accumulate(C, diff * P.ptotal / (gl * (double)N_edge), alpha);
+  double k = P.ptotal / (gl * (double)N_edge);
+  accumulate(C, diff * k, diff_abs * k, alpha);
 }
 
 template <class F>
@@ -1018,8 +1042,10 @@ int or_render(const or_scene_t* sc, const or_opts_t* op, double* image) {
   return g_dual_overflow ? 2 : 0;
 }
 
-/* Gradient of sum_p w_p . I_p into grad[P] (FP64), with sum |contribution|
- * per parameter in abs_grad[P].  Both are overwritten. */
+/* Gradient of sum_p w_p . I_p into grad[P] (FP64), and into abs_grad[P] the
+ * magnitude of the terms that were summed (absolute-value chain rule, see
+ * Dual) -- the scale of the rounding error an FP32 evaluation may make.
+ * Both are overwritten. */
 int or_backward(const or_scene_t* sc, const or_opts_t* op, const float* d_image, double* grad, double* abs_grad) {
   Prep P;
   prepare(sc, P);
@@ -1045,7 +1071,7 @@ int or_backward(const or_scene_t* sc, const or_opts_t* op, const float* d_image,
           camera_path(C, sx, sy, (uint32_t)pix, (uint32_t)s, PASS_INTERIOR, ws, true, &L);
           if (op->terms & 1) {
             Dual sc_ = ws[0] * L.c[0] + ws[1] * L.c[1] + ws[2] * L.c[2];
-            accumulate(C, 1.0, sc_);
+            accumulate(C, 1.0, 1.0, sc_);
           }
         }
       }

@@ -1,0 +1,465 @@
+// api.cu -- the C ABI declared in include/drt.h: contexts, scene upload and
+// update, render / backward orchestration, tapes and error reporting.
+//
+// Host-side rules: every call validates its arguments on the host and returns
+// a status (nothing throws across the ABI); device work is enqueued on the
+// caller's stream; caller arrays may be host or device memory.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <climits>
+
+#include "drt_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+drt_status fail(drt_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CUDA_TRY(x)                                                                  \
+  do {                                                                               \
+    cudaError_t e_ = (x);                                                            \
+    if (e_ != cudaSuccess) return fail(DRT_ERR_CUDA, "%s: %s", #x, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define DRT_TRY(x)                    \
+  do {                                \
+    drt_status s_ = (x);              \
+    if (s_ != DRT_OK) return s_;      \
+  } while (0)
+
+// Allocation with host-side fault injection: DRT_FAULT_ALLOC_AT=n makes the
+// n-th library allocation of the process fail with DRT_ERR_OOM.
+long g_alloc_count = 0;
+drt_status dalloc(void** p, size_t bytes) {
+  *p = nullptr;
+  ++g_alloc_count;
+  const char* f = std::getenv("DRT_FAULT_ALLOC_AT");
+  if (f && std::atol(f) == g_alloc_count) return fail(DRT_ERR_OOM, "injected allocation failure #%ld", g_alloc_count);
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? DRT_ERR_OOM : DRT_ERR_CUDA, "cudaMalloc(%zu): %s", bytes,
+                cudaGetErrorString(e));
+  }
+  return DRT_OK;
+}
+template <class T>
+drt_status dalloc_n(T** p, size_t n) {
+  return dalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+}
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// A device view of a caller array: the array itself if it is device memory,
+// else a temporary device copy (inputs) or staging buffer (outputs).
+struct Staged {
+  void* dev = nullptr;
+  void* user = nullptr;
+  size_t bytes = 0;
+  bool temp = false;
+  bool is_output = false;
+};
+drt_status stage(Staged& s, const void* user, size_t bytes, bool input, bool output, cudaStream_t st) {
+  s.user = const_cast<void*>(user);
+  s.bytes = bytes;
+  s.is_output = output;
+  if (!user) return DRT_OK;
+  if (is_device_ptr(user)) {
+    s.dev = s.user;
+    return DRT_OK;
+  }
+  DRT_TRY(dalloc(&s.dev, bytes));
+  s.temp = true;
+  if (input) CUDA_TRY(cudaMemcpyAsync(s.dev, user, bytes, cudaMemcpyHostToDevice, st));
+  return DRT_OK;
+}
+// Copy staged outputs back, synchronise, release temporaries.
+drt_status unstage(Staged* arr, int n, cudaStream_t st) {
+  bool any = false;
+  for (int i = 0; i < n; ++i)
+    if (arr[i].temp && arr[i].is_output) {
+      CUDA_TRY(cudaMemcpyAsync(arr[i].user, arr[i].dev, arr[i].bytes, cudaMemcpyDeviceToHost, st));
+      any = true;
+    }
+  bool anytemp = false;
+  for (int i = 0; i < n; ++i) anytemp |= arr[i].temp;
+  if (any || anytemp) CUDA_TRY(cudaStreamSynchronize(st));
+  for (int i = 0; i < n; ++i)
+    if (arr[i].temp) {
+      dfree(arr[i].dev);
+      arr[i].dev = nullptr;
+      arr[i].temp = false;
+    }
+  return DRT_OK;
+}
+
+void free_scene_buffers(drt_scene* s) {
+  void* bufs[] = {s->verts, s->albedo, s->radiance, s->cam, s->cam_scale, s->tris, s->light_tris, s->light_of_tri,
+                  s->w2c, s->light_cdf, s->light_area, s->nodes, s->soup, s->edges, s->pedge, s->plen, s->pcdf,
+                  s->slen, s->scdf, s->scan_tmp, s->keys, s->keys2, s->vals, s->vals2, s->parent, s->leaf_parent,
+                  s->flags, s->hist, s->bounds, s->partials};
+  for (void* b : bufs) dfree(b);
+}
+
+drt_status make_opts(const drt_render_opts* o, drt::Opts* op) {
+  if (!o) return fail(DRT_ERR_INVALID_ARG, "opts is NULL");
+  if (o->spp < 1) return fail(DRT_ERR_INVALID_ARG, "spp must be >= 1 (got %d)", o->spp);
+  if (o->edge_spp < 0) return fail(DRT_ERR_INVALID_ARG, "edge_spp must be >= 0");
+  if (o->max_depth < 1 || o->max_depth > 8) return fail(DRT_ERR_INVALID_ARG, "max_depth must be in [1,8]");
+  if (o->terms < 0 || o->terms > 7) return fail(DRT_ERR_INVALID_ARG, "terms must be a 3-bit mask");
+  op->spp = o->spp;
+  op->edge_spp = o->edge_spp;
+  op->max_depth = o->max_depth;
+  op->primary_only = o->primary_only ? 1 : 0;
+  op->terms = o->terms == 0 ? 7 : o->terms;
+  op->key = make_uint2((uint32_t)o->seed, (uint32_t)(o->seed >> 32));
+  op->eps_rel = o->eps_rel > 0.0f ? o->eps_rel : 1.52587890625e-05f;
+  // DRT_DEBUG_RANGES="pix_begin,pix_end,edge_begin,edge_end" restricts which
+  // samples the backward pass evaluates (for bisecting against the oracle)
+  op->pix_begin = 0;
+  op->pix_end = INT32_MAX;
+  op->edge_begin = 0;
+  op->edge_end = INT64_MAX;
+  if (const char* r = std::getenv("DRT_DEBUG_RANGES")) {
+    long long a = 0, b = 0, c = 0, d = 0;
+    if (std::sscanf(r, "%lld,%lld,%lld,%lld", &a, &b, &c, &d) == 4) {
+      op->pix_begin = (int)a; op->pix_end = (int)b; op->edge_begin = c; op->edge_end = d;
+    }
+  }
+  return DRT_OK;
+}
+
+}  // namespace
+
+drt::SceneView drt_scene::view() const {
+  drt::SceneView v;
+  v.verts = verts; v.tris = tris; v.albedo = albedo; v.radiance = radiance; v.cam = cam; v.cam_scale = cam_scale;
+  v.w2c = w2c; v.light_tris = light_tris; v.light_of_tri = light_of_tri; v.light_cdf = light_cdf;
+  v.light_area = light_area; v.nodes = nodes; v.soup = soup; v.edges = edges; v.pedge = pedge; v.pcdf = pcdf;
+  v.scdf = scdf; v.err = ctx->err; v.counters = nullptr;
+  v.V = V; v.T = T; v.L = L; v.E = E; v.W = W; v.H = H; v.cam_type = cam_type;
+  v.root = T > 1 ? 0 : ~0;
+  return v;
+}
+
+extern "C" {
+
+const char* drt_last_error(void) { return g_err.c_str(); }
+const char* drt_version(void) { return "drt 0.1 (sm_103a)"; }
+
+drt_status drt_create(int device, drt_context** out) {
+  if (!out) return fail(DRT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  CUDA_TRY(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return fail(DRT_ERR_INVALID_ARG, "device %d out of range (%d devices)", device, n);
+  CUDA_TRY(cudaSetDevice(device));
+  drt_context* c = new drt_context();
+  c->device = device;
+  CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
+  drt_status s = dalloc_n(&c->err, 2);
+  if (s != DRT_OK) {
+    delete c;
+    return s;
+  }
+  CUDA_TRY(cudaMemset(c->err, 0, 2 * sizeof(int)));
+  *out = c;
+  return DRT_OK;
+}
+
+drt_status drt_destroy(drt_context* ctx) {
+  if (!ctx) return DRT_OK;
+  dfree(ctx->err);
+  delete ctx;
+  return DRT_OK;
+}
+
+drt_status drt_scene_upload(drt_context* ctx, const drt_scene_desc* d, void* stream, drt_scene** out) {
+  if (!ctx || !d || !out) return fail(DRT_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (d->n_verts < 3 || d->n_tris < 1) return fail(DRT_ERR_INVALID_ARG, "need >= 3 vertices and >= 1 triangle");
+  if (d->width < 1 || d->height < 1) return fail(DRT_ERR_INVALID_ARG, "bad image size %dx%d", d->width, d->height);
+  if (d->cam_type != DRT_CAMERA_ORTHO && d->cam_type != DRT_CAMERA_PINHOLE)
+    return fail(DRT_ERR_INVALID_ARG, "bad cam_type %d", d->cam_type);
+  if (!d->verts || !d->tris || !d->albedo || !d->radiance || !d->cam_to_world)
+    return fail(DRT_ERR_INVALID_ARG, "NULL scene array");
+  if (d->n_light_tris < 0 || (d->n_light_tris > 0 && !d->light_tris))
+    return fail(DRT_ERR_INVALID_ARG, "bad light list");
+  if (!(d->cam_scale > 0.0f)) return fail(DRT_ERR_INVALID_ARG, "cam_scale must be > 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  // topology on the host: index validation and the unique edge list
+  std::vector<int32_t> tris(3 * (size_t)d->n_tris);
+  std::vector<int32_t> lts(d->n_light_tris);
+  if (is_device_ptr(d->tris) || (d->n_light_tris > 0 && is_device_ptr(d->light_tris))) CUDA_TRY(cudaStreamSynchronize(st));
+  CUDA_TRY(cudaMemcpy(tris.data(), d->tris, tris.size() * 4, cudaMemcpyDefault));
+  if (d->n_light_tris > 0) CUDA_TRY(cudaMemcpy(lts.data(), d->light_tris, lts.size() * 4, cudaMemcpyDefault));
+  for (size_t i = 0; i < tris.size(); ++i)
+    if (tris[i] < 0 || tris[i] >= d->n_verts) return fail(DRT_ERR_INVALID_ARG, "triangle index %d out of range", tris[i]);
+  std::vector<int32_t> light_of(d->n_tris, -1);
+  for (int j = 0; j < d->n_light_tris; ++j) {
+    if (lts[j] < 0 || lts[j] >= d->n_tris) return fail(DRT_ERR_INVALID_ARG, "light triangle %d out of range", lts[j]);
+    light_of[lts[j]] = j;
+  }
+  std::vector<uint64_t> keys(tris.size());
+  for (int t = 0; t < d->n_tris; ++t)
+    for (int k = 0; k < 3; ++k) {
+      uint32_t a = (uint32_t)tris[3 * t + k], b = (uint32_t)tris[3 * t + (k + 1) % 3];
+      keys[3 * t + k] = ((uint64_t)std::min(a, b) << 32) | std::max(a, b);
+    }
+  std::sort(keys.begin(), keys.end());
+  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+  std::vector<int2> edges(keys.size());
+  for (size_t e = 0; e < keys.size(); ++e) edges[e] = make_int2((int)(keys[e] >> 32), (int)(keys[e] & 0xffffffffu));
+
+  drt_scene* s = new drt_scene();
+  s->ctx = ctx;
+  s->V = d->n_verts; s->T = d->n_tris; s->L = d->n_light_tris; s->E = (int)edges.size();
+  s->W = d->width; s->H = d->height; s->cam_type = d->cam_type;
+  int T = s->T, E = s->E;
+  int nb = (T + 2047) / 2048;
+  s->sort_blocks = nb;
+  drt_status stt = DRT_OK;
+#define ALLOC(ptr, n)                                        \
+  if (stt == DRT_OK) stt = dalloc_n(&s->ptr, (size_t)(n));
+  ALLOC(verts, 3 * (size_t)s->V) ALLOC(albedo, 3 * (size_t)T) ALLOC(radiance, 3) ALLOC(cam, 16)
+  ALLOC(cam_scale, 1) ALLOC(tris, 3 * (size_t)T) ALLOC(light_tris, std::max(1, s->L)) ALLOC(light_of_tri, T)
+  ALLOC(w2c, 12) ALLOC(light_cdf, std::max(1, s->L)) ALLOC(light_area, std::max(1, s->L))
+  ALLOC(nodes, 4 * (size_t)std::max(1, T - 1)) ALLOC(soup, 3 * (size_t)T) ALLOC(edges, std::max(1, E))
+  ALLOC(pedge, 8 * (size_t)std::max(1, E)) ALLOC(plen, std::max(1, E)) ALLOC(pcdf, std::max(1, E))
+  ALLOC(slen, std::max(1, E)) ALLOC(scdf, std::max(1, E)) ALLOC(scan_tmp, std::max(1, E / 1024 + 2))
+  ALLOC(keys, T) ALLOC(keys2, T) ALLOC(vals, T) ALLOC(vals2, T) ALLOC(parent, std::max(1, T))
+  ALLOC(leaf_parent, T) ALLOC(flags, std::max(1, T)) ALLOC(hist, 256 * (size_t)nb) ALLOC(bounds, 8)
+#undef ALLOC
+  if (stt != DRT_OK) {
+    free_scene_buffers(s);
+    delete s;
+    return stt;
+  }
+  cudaError_t e = cudaSuccess;
+  auto cp = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st);
+  };
+  cp(s->verts, d->verts, 12 * (size_t)s->V);
+  cp(s->albedo, d->albedo, 12 * (size_t)T);
+  cp(s->radiance, d->radiance, 12);
+  cp(s->cam, d->cam_to_world, 64);
+  cp(s->cam_scale, &d->cam_scale, 4);
+  cp(s->tris, tris.data(), 12 * (size_t)T);
+  if (s->L > 0) cp(s->light_tris, lts.data(), 4 * (size_t)s->L);
+  cp(s->light_of_tri, light_of.data(), 4 * (size_t)T);
+  if (E > 0) cp(s->edges, edges.data(), sizeof(int2) * (size_t)E);
+  // host vectors above are read by the copies; wait before they go away
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = drt::check_finite(s, st);
+  if (e == cudaSuccess) e = drt::build_scene_derived(s, st);
+  if (e != cudaSuccess) {
+    free_scene_buffers(s);
+    delete s;
+    return fail(DRT_ERR_CUDA, "scene upload: %s", cudaGetErrorString(e));
+  }
+  *out = s;
+  return DRT_OK;
+}
+
+drt_status drt_scene_update_vertices(drt_context* ctx, drt_scene* s, const float* verts, void* stream) {
+  if (!ctx || !s || !verts) return fail(DRT_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemcpyAsync(s->verts, verts, 12 * (size_t)s->V, cudaMemcpyDefault, st));
+  CUDA_TRY(drt::check_finite(s, st));
+  CUDA_TRY(drt::build_scene_derived(s, st));
+  ++s->generation;
+  return DRT_OK;
+}
+
+drt_status drt_scene_update_params(drt_context* ctx, drt_scene* s, const float* albedo, const float* radiance,
+                                   const float* cam_to_world, const float* cam_scale, void* stream) {
+  if (!ctx || !s) return fail(DRT_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (albedo) CUDA_TRY(cudaMemcpyAsync(s->albedo, albedo, 12 * (size_t)s->T, cudaMemcpyDefault, st));
+  if (radiance) CUDA_TRY(cudaMemcpyAsync(s->radiance, radiance, 12, cudaMemcpyDefault, st));
+  if (cam_to_world) CUDA_TRY(cudaMemcpyAsync(s->cam, cam_to_world, 64, cudaMemcpyDefault, st));
+  if (cam_scale) CUDA_TRY(cudaMemcpyAsync(s->cam_scale, cam_scale, 4, cudaMemcpyDefault, st));
+  if (cam_to_world || cam_scale) CUDA_TRY(drt::build_scene_derived(s, st));
+  ++s->generation;
+  return DRT_OK;
+}
+
+drt_status drt_scene_free(drt_context* ctx, drt_scene* s) {
+  (void)ctx;
+  if (!s) return DRT_OK;
+  cudaDeviceSynchronize();
+  free_scene_buffers(s);
+  delete s;
+  return DRT_OK;
+}
+
+drt_status drt_tape_free(drt_context* ctx, drt_tape* t) {
+  (void)ctx;
+  if (!t) return DRT_OK;
+  dfree(t->tri);  // cudaFree waits for work that may still use the buffers
+  dfree(t->bary);
+  delete t;
+  return DRT_OK;
+}
+
+drt_status drt_render(drt_context* ctx, drt_scene* s, const drt_render_opts* opts, float* image, drt_tape** tape,
+                      void* stream) {
+  if (!ctx || !s || !image) return fail(DRT_ERR_INVALID_ARG, "NULL argument");
+  drt::Opts op;
+  DRT_TRY(make_opts(opts, &op));
+  cudaStream_t st = (cudaStream_t)stream;
+  drt_tape* tp = nullptr;
+  if (tape) {
+    int64_t n = (int64_t)s->W * s->H * op.spp;
+    int depth = op.primary_only ? 1 : op.max_depth;
+    if (*tape && (*tape)->scene == s && (*tape)->n * (*tape)->depth >= n * depth) {
+      tp = *tape;  // reuse the caller's tape storage (no allocation, no sync)
+    } else {
+      if (*tape) drt_tape_free(ctx, *tape);
+      *tape = nullptr;
+      tp = new drt_tape();
+      tp->scene = s;
+      drt_status a = dalloc_n(&tp->tri, (size_t)(n * depth));
+      if (a == DRT_OK) a = dalloc_n(&tp->bary, (size_t)(n * depth));
+      if (a != DRT_OK) {
+        dfree(tp->tri);
+        delete tp;
+        return a;
+      }
+    }
+    tp->generation = s->generation;
+    tp->opts = *opts;
+    tp->n = n;
+    tp->depth = depth;
+  }
+  Staged img;
+  drt_status r = stage(img, image, 12 * (size_t)s->W * s->H, false, true, st);
+  if (r != DRT_OK) {
+    drt_tape_free(ctx, tp);
+    return r;
+  }
+  cudaError_t e = drt::launch_render(s, op, (float*)img.dev, tp, st);
+  if (e != cudaSuccess) {
+    unstage(&img, 1, st);
+    drt_tape_free(ctx, tp);
+    return fail(DRT_ERR_CUDA, "render launch: %s", cudaGetErrorString(e));
+  }
+  r = unstage(&img, 1, st);
+  if (r != DRT_OK) {
+    drt_tape_free(ctx, tp);
+    return r;
+  }
+  if (tape) *tape = tp;
+  return DRT_OK;
+}
+
+drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* tape, const drt_render_opts* opts,
+                               const float* d_image, const drt_grads* grads, void* stream) {
+  if (!ctx || !s || !d_image || !grads) return fail(DRT_ERR_INVALID_ARG, "NULL argument");
+  drt::Opts op;
+  DRT_TRY(make_opts(opts, &op));
+  if (!op.primary_only && op.max_depth > 1)
+    return fail(DRT_ERR_INVALID_ARG, "backward supports max_depth == 1 in this build");
+  if (tape) {
+    const drt_render_opts& t = tape->opts;
+    if (tape->scene != s || tape->generation != s->generation)
+      return fail(DRT_ERR_STATE, "tape belongs to another scene or an older version of this scene");
+    if (t.spp != opts->spp || t.seed != opts->seed || t.max_depth != opts->max_depth ||
+        (t.primary_only != 0) != (opts->primary_only != 0))
+      return fail(DRT_ERR_STATE, "tape was recorded with different sampling options");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  Staged sg[6];
+  size_t npix = (size_t)s->W * s->H;
+  drt_status r = stage(sg[0], d_image, 12 * npix, true, false, st);
+  if (r == DRT_OK) r = stage(sg[1], grads->d_verts, 12 * (size_t)s->V, true, true, st);
+  if (r == DRT_OK) r = stage(sg[2], grads->d_albedo, 12 * (size_t)s->T, true, true, st);
+  if (r == DRT_OK) r = stage(sg[3], grads->d_radiance, 12, true, true, st);
+  if (r == DRT_OK) r = stage(sg[4], grads->d_cam_to_world, 48, true, true, st);
+  if (r == DRT_OK) r = stage(sg[5], grads->d_cam_scale, 4, true, true, st);
+  // per-block partial sums of the global parameters: scene-owned scratch,
+  // grown on demand (the stream is drained before the old buffer is freed)
+  int64_t rows = drt::backward_partial_rows(s, op);
+  size_t need = (size_t)rows * 16 + 16;
+  if (r == DRT_OK && need > s->partials_cap) {
+    cudaStreamSynchronize(st);
+    dfree(s->partials);
+    s->partials = nullptr;
+    s->partials_cap = 0;
+    r = dalloc_n(&s->partials, need);
+    if (r == DRT_OK) s->partials_cap = need;
+  }
+  if (r != DRT_OK) {
+    unstage(sg, 6, st);
+    return r;
+  }
+  cudaError_t e = drt::launch_backward(s, op, tape, (const float*)sg[0].dev, (float*)sg[1].dev, (float*)sg[2].dev,
+                                       (float*)sg[3].dev, (float*)sg[4].dev, (float*)sg[5].dev, s->partials, st);
+  r = unstage(sg, 6, st);
+  if (e != cudaSuccess) return fail(DRT_ERR_CUDA, "backward launch: %s", cudaGetErrorString(e));
+  return r;
+}
+
+drt_status drt_debug_closest(drt_context* ctx, drt_scene* s, int64_t n, const float* o, const float* d,
+                             int32_t* tri, float* tb1b2, void* stream) {
+  if (!ctx || !s || n < 0 || (n > 0 && (!o || !d || !tri || !tb1b2))) return fail(DRT_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  Staged sg[4];
+  drt_status r = stage(sg[0], o, 12 * (size_t)n, true, false, st);
+  if (r == DRT_OK) r = stage(sg[1], d, 12 * (size_t)n, true, false, st);
+  if (r == DRT_OK) r = stage(sg[2], tri, 4 * (size_t)n, false, true, st);
+  if (r == DRT_OK) r = stage(sg[3], tb1b2, 12 * (size_t)n, false, true, st);
+  cudaError_t e = cudaSuccess;
+  if (r == DRT_OK)
+    e = drt::launch_debug_closest(s, n, (const float*)sg[0].dev, (const float*)sg[1].dev, (int32_t*)sg[2].dev,
+                                  (float*)sg[3].dev, st);
+  drt_status r2 = unstage(sg, 4, st);
+  if (r != DRT_OK) return r;
+  if (e != cudaSuccess) return fail(DRT_ERR_CUDA, "debug_closest: %s", cudaGetErrorString(e));
+  return r2;
+}
+
+drt_status drt_check_device(drt_context* ctx, void* stream, int32_t* code, int32_t* info) {
+  if (!ctx) return fail(DRT_ERR_INVALID_ARG, "NULL context");
+  cudaStream_t st = (cudaStream_t)stream;
+  int h[2] = {0, 0};
+  CUDA_TRY(cudaStreamSynchronize(st));
+  CUDA_TRY(cudaMemcpy(h, ctx->err, sizeof(h), cudaMemcpyDeviceToHost));
+  if (code) *code = h[0];
+  if (info) *info = h[1];
+  if (h[0] != 0) {
+    CUDA_TRY(cudaMemset(ctx->err, 0, sizeof(h)));
+    return fail(DRT_ERR_DEVICE_FLAG, "device flag %d (info %d)", h[0], h[1]);
+  }
+  return DRT_OK;
+}
+
+}  // extern "C"

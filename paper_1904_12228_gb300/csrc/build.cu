@@ -1,0 +1,477 @@
+// build.cu -- everything derived from the scene parameters, rebuilt whenever
+// vertices change: the camera inverse, the light-area CDF, the LBVH over the
+// triangles (Morton codes, LSD radix sort, Karras hierarchy, bottom-up refit)
+// and the edge CDFs for primary (projected, clipped screen length) and
+// secondary (3D length) edge sampling.
+//
+// Sec. 5.3.1 builds its edge hierarchies with this construction (a radix tree
+// over sorted Morton codes of box centroids); here it serves the ray-casting
+// BVH, which the thesis took from Embree / OptiX Prime.
+#include <climits>
+#include <cstdio>
+
+#include "drt_internal.h"
+
+namespace drt {
+namespace {
+
+constexpr int kBlock = 256;
+
+// ---------------------------------------------------------------------------
+// Validation and small FP64 prep (one thread: exact operation order)
+// ---------------------------------------------------------------------------
+__global__ void k_check_finite(const float* v, int n, int* err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && !isfinite(v[i])) raise_flag(err, DRT_DEV_NONFINITE_INPUT, i);
+}
+
+// World-to-camera rows: adjugate / determinant of the camera's 3x3 in FP64,
+// translation -inv*t, each entry rounded once to FP32.
+__global__ void k_world_to_cam(const float* M, float* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double R[3][3], t[3];
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) R[i][j] = M[4 * i + j];
+    t[i] = M[4 * i + 3];
+  }
+  double c00 = ds(dm(R[1][1], R[2][2]), dm(R[1][2], R[2][1]));
+  double c01 = ds(dm(R[1][2], R[2][0]), dm(R[1][0], R[2][2]));
+  double c02 = ds(dm(R[1][0], R[2][1]), dm(R[1][1], R[2][0]));
+  double det = da(da(dm(R[0][0], c00), dm(R[0][1], c01)), dm(R[0][2], c02));
+  double inv[3][3];
+  inv[0][0] = ddv(c00, det);
+  inv[0][1] = ddv(ds(dm(R[0][2], R[2][1]), dm(R[0][1], R[2][2])), det);
+  inv[0][2] = ddv(ds(dm(R[0][1], R[1][2]), dm(R[0][2], R[1][1])), det);
+  inv[1][0] = ddv(c01, det);
+  inv[1][1] = ddv(ds(dm(R[0][0], R[2][2]), dm(R[0][2], R[2][0])), det);
+  inv[1][2] = ddv(ds(dm(R[0][2], R[1][0]), dm(R[0][0], R[1][2])), det);
+  inv[2][0] = ddv(c02, det);
+  inv[2][1] = ddv(ds(dm(R[0][1], R[2][0]), dm(R[0][0], R[2][1])), det);
+  inv[2][2] = ddv(ds(dm(R[0][0], R[1][1]), dm(R[0][1], R[1][0])), det);
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) out[4 * i + j] = __double2float_rn(inv[i][j]);
+    double tt = da(da(dm(inv[i][0], t[0]), dm(inv[i][1], t[1])), dm(inv[i][2], t[2]));
+    out[4 * i + 3] = __double2float_rn(-tt);
+  }
+}
+
+// Light-triangle areas (FP64 from FP32 edge vectors) and their inclusive
+// prefix in list order.
+__global__ void k_light_cdf(const float* verts, const int32_t* tris, const int32_t* light_tris, int L, double* area,
+                            double* cdf) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double acc = 0.0;
+  for (int j = 0; j < L; ++j) {
+    int t = light_tris[j];
+    const float *a = verts + 3 * tris[3 * t], *b = verts + 3 * tris[3 * t + 1], *c = verts + 3 * tris[3 * t + 2];
+    double e1x = fs(b[0], a[0]), e1y = fs(b[1], a[1]), e1z = fs(b[2], a[2]);
+    double e2x = fs(c[0], a[0]), e2y = fs(c[1], a[1]), e2z = fs(c[2], a[2]);
+    double cx = ds(dm(e1y, e2z), dm(e1z, e2y));
+    double cy = ds(dm(e1z, e2x), dm(e1x, e2z));
+    double cz = ds(dm(e1x, e2y), dm(e1y, e2x));
+    double ar = dm(0.5, __dsqrt_rn(da(da(dm(cx, cx), dm(cy, cy)), dm(cz, cz))));
+    area[j] = ar;
+    acc = da(acc, ar);
+    cdf[j] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Edge tables (Sec. 5.2.1 primary, Sec. 5.2.2 secondary)
+// ---------------------------------------------------------------------------
+__global__ void k_edge_tables(SceneView s, float* pedge, double* plen, double* slen) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= s.E) return;
+  int2 ev = s.edges[e];
+  const float *a = vtx(s, ev.x), *b = vtx(s, ev.y);
+  float ax, ay, bx, by, t0, t1;
+  double len = 0.0;
+  float row[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (project(s, a, &ax, &ay) && project(s, b, &bx, &by) &&
+      clip_screen(ax, ay, bx, by, (float)s.W, (float)s.H, &t0, &t1)) {
+    row[0] = ax; row[1] = ay; row[2] = bx; row[3] = by; row[4] = t0; row[5] = t1;
+    double dx = fs(bx, ax), dy = fs(by, ay);
+    len = dm(ds((double)t1, (double)t0), __dsqrt_rn(da(dm(dx, dx), dm(dy, dy))));
+  }
+  float4* pr = reinterpret_cast<float4*>(pedge + 8 * e);
+  pr[0] = make_float4(row[0], row[1], row[2], row[3]);
+  pr[1] = make_float4(row[4], row[5], 0.0f, 0.0f);
+  plen[e] = len;
+  double ex = fs(b[0], a[0]), ey = fs(b[1], a[1]), ez = fs(b[2], a[2]);
+  slen[e] = __dsqrt_rn(da(da(dm(ex, ex), dm(ey, ey)), dm(ez, ez)));
+}
+
+// ---------------------------------------------------------------------------
+// Inclusive FP64 scan: per-block scan, scan of block totals, add.
+// ---------------------------------------------------------------------------
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kBlock * kScanItems;
+
+__device__ double block_excl_scan(double x, double* total) {
+  __shared__ double warp_sums[kBlock / 32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double v = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    double y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  if (lane == 31) warp_sums[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    double w = lane < kBlock / 32 ? warp_sums[lane] : 0.0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      double y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kBlock / 32) warp_sums[lane] = w;
+  }
+  __syncthreads();
+  double before = (wid > 0 ? warp_sums[wid - 1] : 0.0) + v - x;
+  *total = warp_sums[kBlock / 32 - 1];
+  __syncthreads();
+  return before;
+}
+
+__global__ void k_scan_tiles(const double* in, double* out, double* tile_sums, int n) {
+  int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  double v[kScanItems];
+  double acc = 0.0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = base + i < n ? in[base + i] : 0.0;
+    acc += v[i];
+    v[i] = acc;
+  }
+  double total;
+  double before = block_excl_scan(acc, &total);
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i)
+    if (base + i < n) out[base + i] = before + v[i];
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_sums(double* sums, int nt) {
+  __shared__ double carry;
+  if (threadIdx.x == 0) carry = 0.0;
+  __syncthreads();
+  for (int base = 0; base < nt; base += kBlock) {
+    int i = base + threadIdx.x;
+    double x = i < nt ? sums[i] : 0.0;
+    double total;
+    double before = block_excl_scan(x, &total);
+    if (i < nt) sums[i] = carry + before + x;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += total;
+    __syncthreads();
+  }
+}
+
+__global__ void k_scan_add(double* out, const double* sums, int n) {
+  if (blockIdx.x == 0) return;
+  double add = sums[blockIdx.x - 1];
+  int base = blockIdx.x * kScanTile;
+  for (int i = threadIdx.x; i < kScanTile; i += kBlock)
+    if (base + i < n) out[base + i] += add;
+}
+
+cudaError_t scan_inclusive(const double* in, double* out, double* tmp, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int nt = (n + kScanTile - 1) / kScanTile;
+  DRT_PROF_LAUNCH("scan_tiles", st, k_scan_tiles<<<nt, kBlock, 0, st>>>(in, out, tmp, n));
+  if (nt > 1) {
+    DRT_PROF_LAUNCH("scan_sums", st, k_scan_sums<<<1, kBlock, 0, st>>>(tmp, nt));
+    DRT_PROF_LAUNCH("scan_add", st, k_scan_add<<<nt, kBlock, 0, st>>>(out, tmp, n));
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// LBVH: bounds, Morton codes, radix sort, Karras hierarchy, refit
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ord(float f) {
+  int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float unord(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+__global__ void k_bounds_init(int* b) {
+  if (threadIdx.x < 3) b[threadIdx.x] = INT_MAX;
+  else if (threadIdx.x < 6) b[threadIdx.x] = INT_MIN;
+}
+__global__ void k_bounds(const float* v, int n, int* b) {
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = fminf(lo[k], v[3 * i + k]);
+      hi[k] = fmaxf(hi[k], v[3 * i + k]);
+    }
+  for (int k = 0; k < 3; ++k) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    }
+  }
+  if ((threadIdx.x & 31) == 0)
+    for (int k = 0; k < 3; ++k) {
+      atomicMin(b + k, ord(lo[k]));
+      atomicMax(b + 3 + k, ord(hi[k]));
+    }
+}
+
+__device__ __forceinline__ uint32_t expand10(uint32_t x) {
+  x &= 0x3ffu;
+  x = (x | (x << 16)) & 0x030000FFu;
+  x = (x | (x << 8)) & 0x0300F00Fu;
+  x = (x | (x << 4)) & 0x030C30C3u;
+  x = (x | (x << 2)) & 0x09249249u;
+  return x;
+}
+
+__global__ void k_morton(SceneView s, const int* b, uint32_t* keys, int32_t* vals) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= s.T) return;
+  const int32_t* id = s.tris + 3 * t;
+  float q[3];
+  for (int k = 0; k < 3; ++k) {
+    float lo = unord(b[k]), hi = unord(b[3 + k]);
+    float c = (s.verts[3 * id[0] + k] + s.verts[3 * id[1] + k] + s.verts[3 * id[2] + k]) * (1.0f / 3.0f);
+    float ext = hi - lo;
+    float u = ext > 0.0f ? (c - lo) / ext : 0.5f;
+    q[k] = fminf(fmaxf(u * 1024.0f, 0.0f), 1023.0f);
+  }
+  keys[t] = (expand10((uint32_t)q[0]) << 2) | (expand10((uint32_t)q[1]) << 1) | expand10((uint32_t)q[2]);
+  vals[t] = t;
+}
+
+// One 8-bit LSD pass.  Tiles of kSortTile keys; per-tile digit histograms
+// (digit-major), a global exclusive scan, then a stable scatter in which each
+// warp ranks its 32 keys with __match_any_sync.
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kBlock * kSortItems;
+
+__global__ void k_sort_hist(const uint32_t* keys, int n, int shift, uint32_t* hist, int nblocks) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  int base = blockIdx.x * kSortTile;
+  for (int i = threadIdx.x; i < kSortTile; i += kBlock)
+    if (base + i < n) atomicAdd(&h[(keys[base + i] >> shift) & 0xffu], 1u);
+  __syncthreads();
+  hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void k_sort_scan(uint32_t* hist, int m) {
+  __shared__ uint32_t warp_sums[kBlock / 32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int base = 0; base < m; base += kBlock) {
+    int i = base + threadIdx.x;
+    uint32_t x = i < m ? hist[i] : 0u, v = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    if (lane == 31) warp_sums[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t w = lane < kBlock / 32 ? warp_sums[lane] : 0u;
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      if (lane < kBlock / 32) warp_sums[lane] = w;
+    }
+    __syncthreads();
+    uint32_t excl = carry + (wid > 0 ? warp_sums[wid - 1] : 0u) + v - x;
+    if (i < m) hist[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += warp_sums[kBlock / 32 - 1];
+    __syncthreads();
+  }
+}
+
+__global__ void k_sort_scatter(const uint32_t* keys, const int32_t* vals, uint32_t* okeys, int32_t* ovals, int n,
+                               int shift, const uint32_t* hist, int nblocks) {
+  __shared__ uint32_t run[256];
+  __shared__ uint32_t wcnt[kBlock / 32][256];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  run[threadIdx.x] = hist[threadIdx.x * nblocks + blockIdx.x];
+  int base = blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortItems; ++r) {
+    for (int k = 0; k < kBlock / 32; ++k) wcnt[k][threadIdx.x] = 0;
+    __syncthreads();
+    int i = base + r * kBlock + threadIdx.x;
+    bool valid = i < n;
+    uint32_t key = valid ? keys[i] : 0u;
+    int32_t val = valid ? vals[i] : 0;
+    uint32_t dig = valid ? (key >> shift) & 0xffu : 256u + lane;  // invalid lanes never match valid ones
+    uint32_t peers = __match_any_sync(0xffffffffu, dig);
+    uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+    if (valid && rank == 0) wcnt[wid][dig] = __popc(peers);
+    __syncthreads();
+    // exclusive prefix over warps per digit; thread == digit
+    uint32_t acc = 0;
+    for (int k = 0; k < kBlock / 32; ++k) {
+      uint32_t c = wcnt[k][threadIdx.x];
+      wcnt[k][threadIdx.x] = acc;
+      acc += c;
+    }
+    __syncthreads();
+    if (valid) {
+      uint32_t pos = run[dig] + wcnt[wid][dig] + rank;
+      okeys[pos] = key;
+      ovals[pos] = val;
+    }
+    __syncthreads();
+    run[threadIdx.x] += acc;
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int delta(const uint32_t* k, int n, int i, int j) {
+  if (j < 0 || j >= n) return -1;
+  uint32_t a = k[i], b = k[j];
+  if (a == b) return 32 + __clz((uint32_t)(i ^ j));
+  return __clz(a ^ b);
+}
+
+// Karras (HPG 2012): internal node i covers a key range; its split is the
+// highest differing bit; children are leaves when the range has one key.
+__global__ void k_karras(const uint32_t* keys, int n, float4* nodes, int32_t* parent, int32_t* leaf_parent) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  int d = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+  int dmin = delta(keys, n, i, i - d);
+  int lmax = 2;
+  while (delta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  int l = 0;
+  for (int t = lmax >> 1; t >= 1; t >>= 1)
+    if (delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+  int j = i + l * d;
+  int dnode = delta(keys, n, i, j);
+  int s = 0;
+  int len = l;
+  for (int t = (len + 1) >> 1;; t = (t + 1) >> 1) {
+    if (s + t < len + 1 && delta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+    if (t == 1) break;
+  }
+  int gamma = i + s * d + min(d, 0);
+  int lo = min(i, j), hi = max(i, j);
+  int left = (lo == gamma) ? ~gamma : gamma;
+  int right = (hi == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+  reinterpret_cast<int4*>(nodes)[4 * i + 3] = make_int4(left, right, 0, 0);
+  if (left < 0) leaf_parent[~left] = i; else parent[left] = i;
+  if (right < 0) leaf_parent[~right] = i; else parent[right] = i;
+  if (i == 0) parent[0] = -1;
+}
+
+// Triangle soup in leaf order and bottom-up refit with arrival counters.
+__global__ void k_refit(SceneView s, const int32_t* vals, float4* nodes, float4* soup, const int32_t* parent,
+                        const int32_t* leaf_parent, int32_t* flags) {
+  int pos = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= s.T) return;
+  int t = vals[pos];
+  const int32_t* id = s.tris + 3 * t;
+  float3 v[3];
+  for (int k = 0; k < 3; ++k) v[k] = ld3(s.verts + 3 * id[k]);
+  soup[3 * pos + 0] = make_float4(v[0].x, v[0].y, v[0].z, __int_as_float(t));
+  soup[3 * pos + 1] = make_float4(v[1].x, v[1].y, v[1].z, 0.0f);
+  soup[3 * pos + 2] = make_float4(v[2].x, v[2].y, v[2].z, 0.0f);
+  float lo[3], hi[3];
+  float mag = 0.0f;
+  for (int k = 0; k < 3; ++k) {
+    float a = comp(v[0], k), b = comp(v[1], k), c = comp(v[2], k);
+    lo[k] = fminf(a, fminf(b, c));
+    hi[k] = fmaxf(a, fmaxf(b, c));
+    mag = fmaxf(mag, fmaxf(fabsf(lo[k]), fabsf(hi[k])));
+  }
+  // enlarge so the FP32 slab test is conservative w.r.t. the watertight test
+  float pad = mag * 3.0517578125e-05f + 1e-30f;
+  for (int k = 0; k < 3; ++k) { lo[k] -= pad; hi[k] += pad; }
+  if (s.T == 1) return;
+  int child = ~pos;
+  int node = leaf_parent[pos];
+  int climb = 0;
+  while (node >= 0) {
+    if (++climb > s.T) {  // deeper than the tree can be: parent links are broken
+      raise_flag(s.err, DRT_DEV_REFIT_CAP, pos);
+      return;
+    }
+    float4* n4 = nodes + 4 * node;
+    int4 ch = reinterpret_cast<int4*>(n4)[3];
+    bool is_left = ch.x == child;
+    // write this child's box into its slot of the parent
+    float* f = reinterpret_cast<float*>(n4);
+    if (is_left) {
+      f[0] = lo[0]; f[1] = lo[1]; f[2] = lo[2]; f[3] = hi[0]; f[4] = hi[1]; f[5] = hi[2];
+    } else {
+      f[6] = lo[0]; f[7] = lo[1]; f[8] = lo[2]; f[9] = hi[0]; f[10] = hi[1]; f[11] = hi[2];
+    }
+    __threadfence();
+    if (atomicAdd(flags + node, 1) == 0) return;  // the sibling finishes this node
+    __threadfence();
+    const float* o = reinterpret_cast<const float*>(n4) + (is_left ? 6 : 0);
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = fminf(lo[k], __ldcg(o + k));
+      hi[k] = fmaxf(hi[k], __ldcg(o + 3 + k));
+    }
+    child = node;
+    node = parent[node];
+  }
+}
+
+}  // namespace
+
+cudaError_t check_finite(drt_scene* s, cudaStream_t st) {
+  int n = 3 * s->V;
+  if (n > 0) DRT_PROF_LAUNCH("check_finite", st, k_check_finite<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(s->verts, n, s->ctx->err));
+  return cudaGetLastError();
+}
+
+cudaError_t build_bvh(drt_scene* s, cudaStream_t st) {
+  SceneView v = s->view();
+  int T = s->T;
+  DRT_PROF_LAUNCH("bounds_init", st, k_bounds_init<<<1, 32, 0, st>>>(s->bounds));
+  DRT_PROF_LAUNCH("bounds", st, k_bounds<<<std::min(1024, (s->V + kBlock - 1) / kBlock), kBlock, 0, st>>>(s->verts, s->V, s->bounds));
+  DRT_PROF_LAUNCH("morton", st, k_morton<<<(T + kBlock - 1) / kBlock, kBlock, 0, st>>>(v, s->bounds, s->keys, s->vals));
+  uint32_t *ka = s->keys, *kb = s->keys2;
+  int32_t *va = s->vals, *vb = s->vals2;
+  int nb = (T + kSortTile - 1) / kSortTile;
+  for (int shift = 0; shift < 30; shift += 8) {
+    DRT_PROF_LAUNCH("sort_hist", st, k_sort_hist<<<nb, kBlock, 0, st>>>(ka, T, shift, s->hist, nb));
+    DRT_PROF_LAUNCH("sort_scan", st, k_sort_scan<<<1, kBlock, 0, st>>>(s->hist, 256 * nb));
+    DRT_PROF_LAUNCH("sort_scatter", st, k_sort_scatter<<<nb, kBlock, 0, st>>>(ka, va, kb, vb, T, shift, s->hist, nb));
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  // 4 passes: sorted data is back in keys/vals
+  if (T > 1) {
+    cudaMemsetAsync(s->flags, 0, sizeof(int32_t) * (T - 1), st);
+    DRT_PROF_LAUNCH("karras", st, k_karras<<<(T - 1 + kBlock - 1) / kBlock, kBlock, 0, st>>>(ka, T, s->nodes, s->parent, s->leaf_parent));
+  }
+  DRT_PROF_LAUNCH("refit", st, k_refit<<<(T + kBlock - 1) / kBlock, kBlock, 0, st>>>(v, va, s->nodes, s->soup, s->parent, s->leaf_parent, s->flags));
+  return cudaGetLastError();
+}
+
+cudaError_t build_edge_cdfs(drt_scene* s, cudaStream_t st) {
+  if (s->E <= 0) return cudaSuccess;
+  DRT_PROF_LAUNCH("edge_tables", st, k_edge_tables<<<(s->E + kBlock - 1) / kBlock, kBlock, 0, st>>>(s->view(), s->pedge, s->plen, s->slen));
+  cudaError_t e = scan_inclusive(s->plen, s->pcdf, s->scan_tmp, s->E, st);
+  if (e != cudaSuccess) return e;
+  return scan_inclusive(s->slen, s->scdf, s->scan_tmp, s->E, st);
+}
+
+cudaError_t build_scene_derived(drt_scene* s, cudaStream_t st) {
+  DRT_PROF_LAUNCH("world_to_cam", st, k_world_to_cam<<<1, 1, 0, st>>>(s->cam, s->w2c));
+  if (s->L > 0) DRT_PROF_LAUNCH("light_cdf", st, k_light_cdf<<<1, 1, 0, st>>>(s->verts, s->tris, s->light_tris, s->L, s->light_area, s->light_cdf));
+  cudaError_t e = build_bvh(s, st);
+  if (e != cudaSuccess) return e;
+  e = build_edge_cdfs(s, st);
+  return e;
+}
+
+}  // namespace drt

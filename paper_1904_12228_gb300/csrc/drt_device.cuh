@@ -1,0 +1,509 @@
+// drt_device.cuh -- device-side building blocks of the GB300 edge-sampling
+// differentiable ray tracer: counter RNG, the FP32 decision path, and the
+// BVH traversal.
+//
+// Decision path.  Every value that decides a discrete outcome (which triangle
+// a ray hits, whether a shadow ray is blocked, which edge or light triangle is
+// picked, where a sample point lies) is computed with explicit
+// round-to-nearest intrinsics (__fadd_rn, __fmul_rn, ...), which the compiler
+// never contracts into FMAs, in a fixed operation order.  Two runs of the same
+// estimator therefore take identical decisions on any IEEE machine that
+// evaluates the same order, which is what makes per-sample comparison against
+// an independent CPU implementation possible.  Smooth values (shading,
+// derivatives) use ordinary FP32 arithmetic.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/drt.h"
+
+namespace drt {
+
+// ---------------------------------------------------------------------------
+// Exact-order scalar arithmetic
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fdv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fsq(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double da(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double ds(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dm(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double ddv(double a, double b) { return __ddiv_rn(a, b); }
+
+__device__ __forceinline__ float dot3x(const float* a, const float* b) {
+  return fa(fa(fm(a[0], b[0]), fm(a[1], b[1])), fm(a[2], b[2]));
+}
+
+// ---------------------------------------------------------------------------
+// Constants of the estimator
+// ---------------------------------------------------------------------------
+constexpr float kNearZ = 1e-4f;        // camera depth below which a vertex is behind
+constexpr float kShadowTmax = 0.9999f; // shadow rays stop short of the light point
+constexpr float kInvPi = 0.318309886f;
+constexpr int kStackSize = 64;
+// device error-flag codes (mirrors the public enum in drt.h)
+
+
+enum { kCamera = 0, kLight = 1, kBsdf = 2, kEdgePrimary = 3, kEdgeSecondary = 4 };
+enum { kPassInterior = 0, kPassPrimaryEdge = 1, kPassSecondaryBase = 2 };
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+// Counter layout: (c0, c1, kind<<24 | bounce<<16 | pass, scene).
+__device__ __forceinline__ uint4 rng4(uint2 key, uint32_t c0, uint32_t c1, uint32_t kind, uint32_t bounce,
+                                      uint32_t pass, uint32_t scene) {
+  return philox(make_uint4(c0, c1, (kind << 24) | ((bounce & 0xffu) << 16) | (pass & 0xffffu), scene), key);
+}
+__device__ __forceinline__ float u01f(uint32_t x) { return fm((float)(x >> 8), 5.9604644775390625e-08f); }
+__device__ __forceinline__ double u01d(uint32_t x0, uint32_t x1) {
+  return dm(da(dm((double)(x0 >> 5), 67108864.0), (double)(x1 >> 6)), 1.1102230246251565e-16);
+}
+
+// ---------------------------------------------------------------------------
+// Device view of an uploaded scene (plain pointers into library buffers)
+// ---------------------------------------------------------------------------
+struct SceneView {
+  const float* verts;        // [V,3]
+  const int32_t* tris;       // [T,3]
+  const float* albedo;       // [T,3]
+  const float* radiance;     // [3]
+  const float* cam;          // [16]
+  const float* cam_scale;    // [1]
+  const float* w2c;          // [12]  FP64 inverse of cam rows, rounded once
+  const int32_t* light_tris; // [L]
+  const int32_t* light_of_tri; // [T] index into light_tris or -1
+  const double* light_cdf;   // [L] inclusive prefix of light areas
+  const double* light_area;  // [L]
+  const float4* nodes;       // [4*(T-1)] BVH2 nodes, 64 B each
+  const float4* soup;        // [3*T] triangles in BVH leaf order, w = original id bits
+  const int2* edges;         // [E] unique edges (v0 < v1), sorted
+  const float* pedge;        // [E,8] primary edge table: ax ay bx by t0 t1 (2 pad)
+  const double* pcdf;        // [E] inclusive prefix of clipped screen lengths
+  const double* scdf;        // [E] inclusive prefix of 3D edge lengths
+  int* err;                  // [2] device error flag (code, info)
+  unsigned long long* counters;  // optional work counters [4] for this launch (or null)
+  int V, T, L, E, W, H, cam_type, root;
+};
+
+// Work counters (enabled per launch): rays traced by trace_closest, rays
+// traced by trace_any, BVH nodes visited (two boxes each), triangle tests.
+enum { kCntClosest = 0, kCntAny = 1, kCntNodes = 2, kCntTris = 3 };
+__device__ __forceinline__ void count_trace(const SceneView& s, int kind, int nodes, int tris) {
+  if (s.counters == nullptr) return;
+  unsigned m = __activemask();
+  int lead = __ffs(m) - 1;
+  int nr = __popc(m);
+  unsigned tn = __reduce_add_sync(m, (unsigned)nodes), tt = __reduce_add_sync(m, (unsigned)tris);
+  if ((int)(threadIdx.x & 31) == lead) {
+    atomicAdd(s.counters + kind, (unsigned long long)nr);
+    atomicAdd(s.counters + kCntNodes, (unsigned long long)tn);
+    atomicAdd(s.counters + kCntTris, (unsigned long long)tt);
+  }
+}
+
+struct Opts {
+  int spp, edge_spp, max_depth, primary_only, terms;
+  uint2 key;
+  float eps_rel;
+  // debug restriction of the backward pass to sample ranges (full range by default)
+  int pix_begin, pix_end;
+  int64_t edge_begin, edge_end;
+};
+
+__device__ __forceinline__ void raise_flag(int* err, int code, int info) {
+  if (atomicCAS(err, 0, code) == 0) err[1] = info;
+}
+
+__device__ __forceinline__ const float* vtx(const SceneView& s, int i) { return s.verts + 3 * i; }
+
+// ---------------------------------------------------------------------------
+// FP32 decision path
+// ---------------------------------------------------------------------------
+// Camera ray through screen point (sx, sy), pixel units, y down.
+__device__ __forceinline__ void camera_ray(const SceneView& s, float sx, float sy, float o[3], float d[3]) {
+  const float* M = s.cam;
+  float S = s.cam_scale[0];
+  float fw = (float)s.W, fh = (float)s.H;
+  float xn = fdv(fs(fm(2.0f, sx), fw), fw);
+  float yn = fdv(fs(fh, fm(2.0f, sy)), fh);
+  float aspect = fdv(fw, fh);
+  float sxs = fm(aspect, S);
+  float lx = fm(xn, sxs), ly = fm(yn, S);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float m0 = M[4 * i], m1 = M[4 * i + 1], m2 = M[4 * i + 2], m3 = M[4 * i + 3];
+    if (s.cam_type == 1) {
+      o[i] = m3;
+      d[i] = fs(fa(fm(m0, lx), fm(m1, ly)), m2);
+    } else {
+      o[i] = fa(fa(fm(m0, lx), fm(m1, ly)), m3);
+      d[i] = -m2;
+    }
+  }
+}
+
+// Screen projection with the FP32 world-to-camera rows; false if behind.
+__device__ __forceinline__ bool project(const SceneView& s, const float v[3], float* sx, float* sy) {
+  const float* Wm = s.w2c;
+  float vc[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    vc[i] = fa(fa(fa(fm(Wm[4 * i], v[0]), fm(Wm[4 * i + 1], v[1])), fm(Wm[4 * i + 2], v[2])), Wm[4 * i + 3]);
+  if (!(vc[2] < -kNearZ)) return false;
+  float S = s.cam_scale[0];
+  float fw = (float)s.W, fh = (float)s.H;
+  float aspect = fdv(fw, fh);
+  float px = vc[0], py = vc[1];
+  if (s.cam_type == 1) {
+    float iz = -vc[2];
+    px = fdv(vc[0], iz);
+    py = fdv(vc[1], iz);
+  }
+  float xn = fdv(px, fm(aspect, S));
+  float yn = fdv(py, S);
+  *sx = fm(fa(xn, 1.0f), fm(0.5f, fw));
+  *sy = fm(fs(1.0f, yn), fm(0.5f, fh));
+  return true;
+}
+
+// Liang-Barsky clip to [0,W]x[0,H]; planes x>=0, x<=W, y>=0, y<=H.
+__device__ __forceinline__ bool clip_screen(float ax, float ay, float bx, float by, float W, float H, float* t0o,
+                                            float* t1o) {
+  float dx = fs(bx, ax), dy = fs(by, ay);
+  float t0 = 0.0f, t1 = 1.0f;
+  float p[4] = {-dx, dx, -dy, dy};
+  float q[4] = {ax, fs(W, ax), ay, fs(H, ay)};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (p[k] == 0.0f) {
+      if (q[k] < 0.0f) return false;
+      continue;
+    }
+    float r = fdv(q[k], p[k]);
+    if (p[k] < 0.0f) {
+      if (r > t0) t0 = r;
+    } else {
+      if (r < t1) t1 = r;
+    }
+  }
+  if (!(t0 < t1)) return false;
+  *t0o = t0;
+  *t1o = t1;
+  return true;
+}
+
+// Upper bound in an inclusive CDF; falls back to the last entry with mass.
+__device__ __forceinline__ int cdf_pick(const double* cdf, int n, double target) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (cdf[mid] > target) hi = mid; else lo = mid + 1;
+  }
+  if (lo >= n) {
+    lo = n - 1;
+    while (lo > 0 && cdf[lo] == cdf[lo - 1]) --lo;
+  }
+  return lo;
+}
+
+// Watertight ray/triangle test (Woop, Benthin, Wald 2013), FP32.
+struct Shear {
+  int kx, ky, kz;
+  float Sx, Sy, Sz;
+};
+__device__ __forceinline__ Shear make_shear(const float d[3]) {
+  int kz = 0;
+  if (fabsf(d[1]) > fabsf(d[kz])) kz = 1;
+  if (fabsf(d[2]) > fabsf(d[kz])) kz = 2;
+  int kx = kz + 1;
+  if (kx == 3) kx = 0;
+  int ky = kx + 1;
+  if (ky == 3) ky = 0;
+  if (d[kz] < 0.0f) {
+    int t = kx; kx = ky; ky = t;
+  }
+  Shear sh;
+  sh.kx = kx; sh.ky = ky; sh.kz = kz;
+  sh.Sx = fdv(d[kx], d[kz]);
+  sh.Sy = fdv(d[ky], d[kz]);
+  sh.Sz = fdv(1.0f, d[kz]);
+  return sh;
+}
+__device__ __forceinline__ float comp(const float3& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+
+__device__ __forceinline__ bool watertight(const Shear& sh, const float o[3], float3 v0, float3 v1, float3 v2,
+                                           float tmax, float* t_out, float* b1_out, float* b2_out) {
+  float3 A = make_float3(fs(v0.x, o[0]), fs(v0.y, o[1]), fs(v0.z, o[2]));
+  float3 B = make_float3(fs(v1.x, o[0]), fs(v1.y, o[1]), fs(v1.z, o[2]));
+  float3 C = make_float3(fs(v2.x, o[0]), fs(v2.y, o[1]), fs(v2.z, o[2]));
+  float Akz = comp(A, sh.kz), Bkz = comp(B, sh.kz), Ckz = comp(C, sh.kz);
+  float Ax = fs(comp(A, sh.kx), fm(sh.Sx, Akz)), Ay = fs(comp(A, sh.ky), fm(sh.Sy, Akz));
+  float Bx = fs(comp(B, sh.kx), fm(sh.Sx, Bkz)), By = fs(comp(B, sh.ky), fm(sh.Sy, Bkz));
+  float Cx = fs(comp(C, sh.kx), fm(sh.Sx, Ckz)), Cy = fs(comp(C, sh.ky), fm(sh.Sy, Ckz));
+  float U = fs(fm(Cx, By), fm(Cy, Bx));
+  float V = fs(fm(Ax, Cy), fm(Ay, Cx));
+  float Wv = fs(fm(Bx, Ay), fm(By, Ax));
+  if ((U < 0.0f || V < 0.0f || Wv < 0.0f) && (U > 0.0f || V > 0.0f || Wv > 0.0f)) return false;
+  float det = fa(fa(U, V), Wv);
+  if (det == 0.0f) return false;
+  float Az = fm(sh.Sz, Akz), Bz = fm(sh.Sz, Bkz), Cz = fm(sh.Sz, Ckz);
+  float T = fa(fa(fm(U, Az), fm(V, Bz)), fm(Wv, Cz));
+  float t = fdv(T, det);
+  if (!(t > 0.0f && t < tmax)) return false;
+  *t_out = t;
+  *b1_out = fdv(V, det);
+  *b2_out = fdv(Wv, det);
+  return true;
+}
+
+__device__ __forceinline__ void bary_point(float3 v0, float3 v1, float3 v2, float b1, float b2, float p[3]) {
+  float b0 = fs(fs(1.0f, b1), b2);
+  p[0] = fa(fa(fm(b0, v0.x), fm(b1, v1.x)), fm(b2, v2.x));
+  p[1] = fa(fa(fm(b0, v0.y), fm(b1, v1.y)), fm(b2, v2.y));
+  p[2] = fa(fa(fm(b0, v0.z), fm(b1, v1.z)), fm(b2, v2.z));
+}
+__device__ __forceinline__ void face_normal(float3 v0, float3 v1, float3 v2, float n[3]) {
+  float e1x = fs(v1.x, v0.x), e1y = fs(v1.y, v0.y), e1z = fs(v1.z, v0.z);
+  float e2x = fs(v2.x, v0.x), e2y = fs(v2.y, v0.y), e2z = fs(v2.z, v0.z);
+  n[0] = fs(fm(e1y, e2z), fm(e1z, e2y));
+  n[1] = fs(fm(e1z, e2x), fm(e1x, e2z));
+  n[2] = fs(fm(e1x, e2y), fm(e1y, e2x));
+}
+
+// Own sin/cos of 2*pi*r: quadrant from 4r, Taylor series of sin and cos on
+// [0, pi/2) by Horner's rule (coefficients 1/n!).
+__device__ __forceinline__ void sincos_2pi(float r, float* c_out, float* s_out) {
+  float q4 = fm(r, 4.0f);
+  int q = (int)q4;
+  if (q > 3) q = 3;
+  float f = fs(q4, (float)q);
+  float a = fm(f, 1.57079637f);
+  float a2 = fm(a, a);
+  float s = fm(a2, 1.60590444e-10f);
+  s = fm(a2, fs(s, 2.50521084e-08f));
+  s = fm(a2, fa(s, 2.75573192e-06f));
+  s = fm(a2, fs(s, 1.98412698e-04f));
+  s = fm(a2, fa(s, 8.33333377e-03f));
+  s = fm(a2, fs(s, 1.66666672e-01f));
+  s = fa(a, fm(a, s));
+  float c = fm(a2, -1.14707454e-11f);
+  c = fm(a2, fa(c, 2.08767570e-09f));
+  c = fm(a2, fs(c, 2.75573192e-07f));
+  c = fm(a2, fa(c, 2.48015876e-05f));
+  c = fm(a2, fs(c, 1.38888892e-03f));
+  c = fm(a2, fa(c, 4.16666679e-02f));
+  c = fm(a2, fs(c, 0.5f));
+  c = fa(1.0f, c);
+  if (q == 0) { *c_out = c; *s_out = s; }
+  else if (q == 1) { *c_out = -s; *s_out = c; }
+  else if (q == 2) { *c_out = -c; *s_out = -s; }
+  else { *c_out = s; *s_out = -c; }
+}
+
+// Cosine-weighted direction around unit normal n; basis of Duff et al.,
+// "Building an Orthonormal Basis, Revisited" (JCGT 2017).
+__device__ __forceinline__ void cosine_dir(const float n[3], float r1, float r2, float out[3]) {
+  float rr = fsq(r1);
+  float c, s;
+  sincos_2pi(r2, &c, &s);
+  float lx = fm(rr, c), ly = fm(rr, s);
+  float lz = fsq(fmaxf(0.0f, fs(1.0f, r1)));
+  float sgn = copysignf(1.0f, n[2]);
+  float a = fdv(-1.0f, fa(sgn, n[2]));
+  float bb = fm(fm(n[0], n[1]), a);
+  float t[3] = {fa(1.0f, fm(fm(fm(sgn, n[0]), n[0]), a)), fm(sgn, bb), -fm(sgn, n[0])};
+  float bt[3] = {bb, fa(sgn, fm(fm(n[1], n[1]), a)), -n[1]};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) out[i] = fa(fa(fm(lx, t[i]), fm(ly, bt[i])), fm(lz, n[i]));
+}
+
+// ---------------------------------------------------------------------------
+// BVH traversal (BVH2, 64-byte nodes, stack in registers/local memory)
+// ---------------------------------------------------------------------------
+// Node n: f4[4n+0] = (loL.xyz, hiL.x), f4[4n+1] = (hiL.yz, loR.xy),
+//         f4[4n+2] = (loR.z, hiR.xyz), f4[4n+3] = (childL, childR, -, -) as int.
+// child >= 0: internal node; child < 0: leaf at sorted position ~child.
+// Boxes are enlarged when built so the slab test below never rejects a ray
+// that the watertight test would accept.
+struct Hit {
+  int tri;
+  float t, b1, b2;
+};
+
+struct RayPre {
+  float o[3], d[3], inv[3];
+  Shear sh;
+};
+__device__ __forceinline__ void ray_pre(RayPre& r, const float o[3], const float d[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    r.o[i] = o[i];
+    r.d[i] = d[i];
+    float di = fabsf(d[i]) < 1e-20f ? copysignf(1e-20f, d[i]) : d[i];
+    r.inv[i] = 1.0f / di;
+  }
+  r.sh = make_shear(d);
+}
+
+__device__ __forceinline__ void slab2(const RayPre& r, const float4& a, const float4& b, const float4& c, float tmax,
+                                      float* tl, bool* hl, float* tr, bool* hr) {
+  // left box: lo=(a.x,a.y,a.z) hi=(a.w,b.x,b.y); right: lo=(b.z,b.w,c.x) hi=(c.y,c.z,c.w)
+  float lx0 = (a.x - r.o[0]) * r.inv[0], lx1 = (a.w - r.o[0]) * r.inv[0];
+  float ly0 = (a.y - r.o[1]) * r.inv[1], ly1 = (b.x - r.o[1]) * r.inv[1];
+  float lz0 = (a.z - r.o[2]) * r.inv[2], lz1 = (b.y - r.o[2]) * r.inv[2];
+  float tin = fmaxf(fmaxf(fminf(lx0, lx1), fminf(ly0, ly1)), fmaxf(fminf(lz0, lz1), 0.0f));
+  float tout = fminf(fminf(fmaxf(lx0, lx1), fmaxf(ly0, ly1)), fminf(fmaxf(lz0, lz1), tmax));
+  *tl = tin;
+  *hl = tin <= tout * 1.00000024f;
+  float rx0 = (b.z - r.o[0]) * r.inv[0], rx1 = (c.y - r.o[0]) * r.inv[0];
+  float ry0 = (b.w - r.o[1]) * r.inv[1], ry1 = (c.z - r.o[1]) * r.inv[1];
+  float rz0 = (c.x - r.o[2]) * r.inv[2], rz1 = (c.w - r.o[2]) * r.inv[2];
+  float tin2 = fmaxf(fmaxf(fminf(rx0, rx1), fminf(ry0, ry1)), fmaxf(fminf(rz0, rz1), 0.0f));
+  float tout2 = fminf(fminf(fmaxf(rx0, rx1), fmaxf(ry0, ry1)), fminf(fmaxf(rz0, rz1), tmax));
+  *tr = tin2;
+  *hr = tin2 <= tout2 * 1.00000024f;
+}
+
+// Closest hit with t in (0, tmax); ties on t go to the lowest triangle id;
+// triangle `exclude` is skipped.  Returns tri = -1 on a miss.
+__device__ __forceinline__ Hit trace_closest(const SceneView& s, const float o[3], const float d[3], float tmax,
+                                             int exclude) {
+  RayPre r;
+  ray_pre(r, o, d);
+  Hit h;
+  h.tri = -1;
+  h.t = tmax;
+  h.b1 = h.b2 = 0.0f;
+  int stack[kStackSize];
+  int sp = 0;
+  int node = s.root;
+  // a tree has 2T-1 nodes and leaves, each visited at most once
+  int budget = 2 * s.T + 8;
+  int n_nodes = 0, n_tris = 0;
+  while (true) {
+    if (--budget < 0) {
+      raise_flag(s.err, DRT_DEV_TRAVERSAL_CAP, s.T);
+      break;
+    }
+    if (node >= 0) {
+      ++n_nodes;
+      const float4* n4 = s.nodes + 4 * node;
+      float4 a = __ldg(n4), b = __ldg(n4 + 1), c = __ldg(n4 + 2);
+      int4 ch = __ldg(reinterpret_cast<const int4*>(n4 + 3));
+      float tl, tr;
+      bool hl, hr;
+      slab2(r, a, b, c, h.t, &tl, &hl, &tr, &hr);
+      if (hl && hr) {
+        int nearc = tl <= tr ? ch.x : ch.y, farc = tl <= tr ? ch.y : ch.x;
+        if (sp < kStackSize) {
+          stack[sp++] = farc;
+        } else {
+          raise_flag(s.err, DRT_DEV_STACK_OVERFLOW, node);
+        }
+        node = nearc;
+        continue;
+      } else if (hl) {
+        node = ch.x;
+        continue;
+      } else if (hr) {
+        node = ch.y;
+        continue;
+      }
+    } else {
+      int pos = ~node;
+      const float4* t4 = s.soup + 3 * pos;
+      float4 p0 = __ldg(t4), p1 = __ldg(t4 + 1), p2 = __ldg(t4 + 2);
+      int id = __float_as_int(p0.w);
+      ++n_tris;
+      if (id != exclude) {
+        float t, b1, b2;
+        // t must beat the best so far; a lower id also wins a tie on t
+        float lim = (h.tri >= 0 && id < h.tri) ? __uint_as_float(__float_as_uint(h.t) + 1u) : h.t;
+        if (watertight(r.sh, r.o, make_float3(p0.x, p0.y, p0.z), make_float3(p1.x, p1.y, p1.z),
+                       make_float3(p2.x, p2.y, p2.z), lim, &t, &b1, &b2)) {
+          h.tri = id; h.t = t; h.b1 = b1; h.b2 = b2;
+        }
+      }
+    }
+    if (sp == 0) break;
+    node = stack[--sp];
+  }
+  count_trace(s, kCntClosest, n_nodes, n_tris);
+  return h;
+}
+
+// Any hit with t in (0, tmax), skipping two triangle ids.
+__device__ __forceinline__ bool trace_any(const SceneView& s, const float o[3], const float d[3], float tmax, int ex0,
+                                          int ex1) {
+  RayPre r;
+  ray_pre(r, o, d);
+  int stack[kStackSize];
+  int sp = 0;
+  int node = s.root;
+  int budget = 2 * s.T + 8;
+  int n_nodes = 0, n_tris = 0;
+  bool found = false;
+  while (true) {
+    if (--budget < 0) {
+      raise_flag(s.err, DRT_DEV_TRAVERSAL_CAP, s.T);
+      break;
+    }
+    if (node >= 0) {
+      ++n_nodes;
+      const float4* n4 = s.nodes + 4 * node;
+      float4 a = __ldg(n4), b = __ldg(n4 + 1), c = __ldg(n4 + 2);
+      int4 ch = __ldg(reinterpret_cast<const int4*>(n4 + 3));
+      float tl, tr;
+      bool hl, hr;
+      slab2(r, a, b, c, tmax, &tl, &hl, &tr, &hr);
+      if (hl && hr) {
+        if (sp < kStackSize) stack[sp++] = ch.y; else raise_flag(s.err, DRT_DEV_STACK_OVERFLOW, node);
+        node = ch.x;
+        continue;
+      } else if (hl) {
+        node = ch.x;
+        continue;
+      } else if (hr) {
+        node = ch.y;
+        continue;
+      }
+    } else {
+      int pos = ~node;
+      const float4* t4 = s.soup + 3 * pos;
+      float4 p0 = __ldg(t4), p1 = __ldg(t4 + 1), p2 = __ldg(t4 + 2);
+      int id = __float_as_int(p0.w);
+      ++n_tris;
+      if (id != ex0 && id != ex1) {
+        float t, b1, b2;
+        if (watertight(r.sh, r.o, make_float3(p0.x, p0.y, p0.z), make_float3(p1.x, p1.y, p1.z),
+                       make_float3(p2.x, p2.y, p2.z), tmax, &t, &b1, &b2)) {
+          found = true;
+          break;
+        }
+      }
+    }
+    if (sp == 0) break;
+    node = stack[--sp];
+  }
+  count_trace(s, kCntAny, n_nodes, n_tris);
+  return found;
+}
+
+__device__ __forceinline__ float3 ld3(const float* p) { return make_float3(p[0], p[1], p[2]); }
+
+}  // namespace drt

@@ -1,0 +1,83 @@
+// drt_internal.h -- host-side structures and kernel launchers shared by the
+// translation units of the library (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "../../include/drt.h"
+#include "drt_device.cuh"
+
+struct drt_context {
+  int device = 0;
+  int* err = nullptr;        // device error flag [2]
+  int num_sms = 0;
+};
+
+struct drt_scene {
+  drt_context* ctx = nullptr;
+  int V = 0, T = 0, L = 0, E = 0, W = 0, H = 0, cam_type = 0;
+  uint64_t generation = 0;   // bumped on every update; tapes remember it
+  // parameters (library copies)
+  float *verts = nullptr, *albedo = nullptr, *radiance = nullptr, *cam = nullptr, *cam_scale = nullptr;
+  int32_t *tris = nullptr, *light_tris = nullptr, *light_of_tri = nullptr;
+  // derived
+  float* w2c = nullptr;
+  double *light_cdf = nullptr, *light_area = nullptr;
+  float4 *nodes = nullptr, *soup = nullptr;
+  int2* edges = nullptr;
+  float* pedge = nullptr;
+  double *plen = nullptr, *pcdf = nullptr, *slen = nullptr, *scdf = nullptr, *scan_tmp = nullptr;
+  // LBVH build scratch
+  uint32_t *keys = nullptr, *keys2 = nullptr;
+  int32_t *vals = nullptr, *vals2 = nullptr, *parent = nullptr, *leaf_parent = nullptr, *flags = nullptr;
+  uint32_t* hist = nullptr;
+  int* bounds = nullptr;     // ordered-int AABB [6]
+  float* partials = nullptr; // backward: per-block partial sums of global parameters
+  size_t partials_cap = 0;
+  int sort_blocks = 0;
+  drt::SceneView view() const;
+};
+
+struct drt_tape {
+  const drt_scene* scene = nullptr;
+  uint64_t generation = 0;
+  drt_render_opts opts{};
+  int64_t n = 0;             // samples = W*H*spp
+  int depth = 0;
+  int32_t* tri = nullptr;    // [depth, n]  tri id | (nee visible << 31), -1 = none
+  float2* bary = nullptr;    // [depth, n]
+};
+
+namespace drt {
+// prof.cu: event timing of launches (when enabled) and work-counter slots
+struct ProfToken {
+  const char* name;
+  cudaEvent_t a, b;
+};
+ProfToken prof_begin(const char* name, cudaStream_t st);
+void prof_end(const ProfToken& t, cudaStream_t st);
+enum { kSlotRender = 0, kSlotBwdInterior = 1, kSlotBwdPrimary = 2, kSlotDebug = 3, kKernelSlots = 4 };
+unsigned long long* counter_slot(int kernel);  // null unless counters are enabled
+#define DRT_PROF_LAUNCH(name, st, ...)                      \
+  do {                                                      \
+    ::drt::ProfToken t_ = ::drt::prof_begin(name, st);      \
+    __VA_ARGS__;                                            \
+    ::drt::prof_end(t_, st);                                \
+  } while (0)
+// build.cu
+cudaError_t build_scene_derived(drt_scene* s, cudaStream_t st);   // w2c, lights, BVH, edge CDFs
+cudaError_t build_bvh(drt_scene* s, cudaStream_t st);
+cudaError_t build_edge_cdfs(drt_scene* s, cudaStream_t st);
+cudaError_t check_finite(drt_scene* s, cudaStream_t st);
+// render.cu
+cudaError_t launch_render(const drt_scene* s, const Opts& op, float* image, drt_tape* tape, cudaStream_t st);
+cudaError_t launch_backward(const drt_scene* s, const Opts& op, const drt_tape* tape, const float* d_image,
+                            float* d_verts, float* d_albedo, float* d_radiance, float* d_cam, float* d_cam_scale,
+                            float* scratch_global, cudaStream_t st);
+int64_t backward_partial_rows(const drt_scene* s, const Opts& op);
+cudaError_t launch_debug_closest(const drt_scene* s, int64_t n, const float* o, const float* d, int32_t* tri,
+                                 float* tb, cudaStream_t st);
+}  // namespace drt

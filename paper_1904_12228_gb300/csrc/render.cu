@@ -1,0 +1,735 @@
+// render.cu -- forward path tracing with next-event estimation (Eq. first via
+// Eq. gradient_monte_carlo), and the backward pass: the reverse sweep over
+// the checkpointed path (interior term of Eq. redner_product_rule), secondary
+// edge samples at each shading vertex (Eq. dirac_3d_edge, Appendix 5.A,
+// Eq. alpha_3d) and primary edge samples (Eq. mc, Eq. redner_dirac_jacobian).
+//
+// Thread mapping.  A warp owns 32/G pixels, G = min(32, spp rounded up to a
+// power of two); lane l works on pixel l/G and samples l%G, l%G+G, ...  The
+// 32 rays of a warp start in the same pixel, so traversal is coherent, and
+// the per-pixel sum is a fixed-order butterfly (images are bit-reproducible).
+#include <cstdio>
+
+#include "drt_internal.h"
+
+namespace drt {
+namespace {
+
+constexpr int kBlock = 256;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kGlobals = 16;  // d_radiance[3], d_cam[12], d_cam_scale[1]
+
+// ---- smooth float3 helpers (contraction allowed) ---------------------------
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator-(float3 a) { return make_float3(-a.x, -a.y, -a.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float3 b) { return make_float3(a.x * b.x, a.y * b.y, a.z * b.z); }
+__device__ __forceinline__ void operator+=(float3& a, float3 b) { a.x += b.x; a.y += b.y; a.z += b.z; }
+__device__ __forceinline__ void operator-=(float3& a, float3 b) { a.x -= b.x; a.y -= b.y; a.z -= b.z; }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float len(float3 a) { return sqrtf(dot(a, a)); }
+__device__ __forceinline__ float3 f3(const float p[3]) { return make_float3(p[0], p[1], p[2]); }
+__device__ __forceinline__ float3 zero3() { return make_float3(0.f, 0.f, 0.f); }
+
+// ---- warp-aggregated scatter (Sec. 5.4.6: reductions over pixels that hit
+// the same object are the backward bottleneck).  All 32 lanes must call. ----
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  return x;
+}
+__device__ __forceinline__ void scatter3(float* arr, int id, float3 v, bool active) {
+  if (arr == nullptr) return;
+  int lane = threadIdx.x & 31;
+  unsigned pending = __ballot_sync(kFull, active);
+  while (pending) {
+    int leader = __ffs(pending) - 1;
+    int key = __shfl_sync(kFull, id, leader);
+    bool mine = active && id == key;
+    unsigned peers = __ballot_sync(kFull, mine);
+    float3 x = mine ? v : zero3();
+    if (__popc(peers) > 1) {
+      x.x = warp_sum(x.x);
+      x.y = warp_sum(x.y);
+      x.z = warp_sum(x.z);
+    } else {
+      x.x = __shfl_sync(kFull, x.x, leader);
+      x.y = __shfl_sync(kFull, x.y, leader);
+      x.z = __shfl_sync(kFull, x.z, leader);
+    }
+    if (lane == leader) {
+      atomicAdd(arr + 3 * key, x.x);
+      atomicAdd(arr + 3 * key + 1, x.y);
+      atomicAdd(arr + 3 * key + 2, x.z);
+    }
+    pending &= ~peers;
+  }
+}
+
+// Block reduction of the global parameters into one row of partials; the
+// rows are summed in a fixed order by k_reduce_globals (deterministic).
+__device__ __forceinline__ void block_globals(float g[kGlobals], float* partials) {
+  __shared__ float sm[kBlock / 32][kGlobals];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < kGlobals; ++i) {
+    float x = warp_sum(g[i]);
+    if (lane == 0) sm[wid][i] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < kGlobals) {
+    float acc = 0.f;
+    for (int w = 0; w < kBlock / 32; ++w) acc += sm[w][threadIdx.x];
+    partials[(size_t)blockIdx.x * kGlobals + threadIdx.x] = acc;
+  }
+}
+
+__global__ void k_reduce_globals(const float* partials, int rows, float* d_radiance, float* d_cam, float* d_scale) {
+  int i = threadIdx.x;
+  if (i >= kGlobals) return;
+  double acc = 0.0;
+  for (int r = 0; r < rows; ++r) acc += partials[(size_t)r * kGlobals + i];
+  float v = (float)acc;
+  if (i < 3) { if (d_radiance) d_radiance[i] += v; }
+  else if (i < 15) { if (d_cam) d_cam[i - 3] += v; }
+  else if (d_scale) d_scale[0] += v;
+}
+
+// ---- shading data of a hit -------------------------------------------------
+struct Vertex {
+  int k;
+  float p[3];       // FP32 hit point (decision path)
+  float nu[3];      // unnormalised face normal (decision path)
+  float side;       // nu . d
+  float3 v0, v1, v2;
+};
+__device__ __forceinline__ void load_vertex(const SceneView& s, int k, float b1, float b2, const float d[3], Vertex& x) {
+  x.k = k;
+  const int32_t* id = s.tris + 3 * k;
+  x.v0 = ld3(s.verts + 3 * id[0]);
+  x.v1 = ld3(s.verts + 3 * id[1]);
+  x.v2 = ld3(s.verts + 3 * id[2]);
+  bary_point(x.v0, x.v1, x.v2, b1, b2, x.p);
+  face_normal(x.v0, x.v1, x.v2, x.nu);
+  x.side = dot3x(x.nu, d);
+}
+// Flipped unit normal on the viewer side (decision-path FP32).
+__device__ __forceinline__ void shading_normal32(const Vertex& x, float n[3]) {
+  float nl = fsq(dot3x(x.nu, x.nu));
+  float fl = x.side > 0.0f ? -1.0f : 1.0f;
+  n[0] = fm(fl, fdv(x.nu[0], nl));
+  n[1] = fm(fl, fdv(x.nu[1], nl));
+  n[2] = fm(fl, fdv(x.nu[2], nl));
+}
+
+struct LightSample {
+  int j, lt;
+  float y[3];
+  float w[3];  // barycentric weights
+  float3 l0, l1, l2;
+};
+__device__ __forceinline__ void sample_light(const SceneView& s, uint4 r, LightSample& ls) {
+  double total = s.light_cdf[s.L - 1];
+  ls.j = cdf_pick(s.light_cdf, s.L, dm(u01d(r.x, r.y), total));
+  ls.lt = s.light_tris[ls.j];
+  const int32_t* id = s.tris + 3 * ls.lt;
+  ls.l0 = ld3(s.verts + 3 * id[0]);
+  ls.l1 = ld3(s.verts + 3 * id[1]);
+  ls.l2 = ld3(s.verts + 3 * id[2]);
+  float r1 = u01f(r.z), r2 = u01f(r.w);
+  float su = fsq(r1);
+  float b0 = fs(1.0f, su), b1 = fm(su, r2), b2 = fs(su, b1);
+  ls.w[0] = b0; ls.w[1] = b1; ls.w[2] = b2;
+  ls.y[0] = fa(fa(fm(b0, ls.l0.x), fm(b1, ls.l1.x)), fm(b2, ls.l2.x));
+  ls.y[1] = fa(fa(fm(b0, ls.l0.y), fm(b1, ls.l1.y)), fm(b2, ls.l2.y));
+  ls.y[2] = fa(fa(fm(b0, ls.l0.z), fm(b1, ls.l1.z)), fm(b2, ls.l2.z));
+}
+
+// NEE value at a vertex (factor multiplying rho/pi * Le): G * A_j / P(j).
+__device__ __forceinline__ float nee_geometry(const SceneView& s, float3 p, float3 n, const LightSample& ls) {
+  float3 W = f3(ls.y) - p;
+  float r2 = dot(W, W);
+  float r = sqrtf(r2);
+  float3 w = (1.0f / r) * W;
+  float cp = dot(n, w);
+  float3 Nl = cross(ls.l1 - ls.l0, ls.l2 - ls.l0);
+  float nll = len(Nl);
+  float cy = -dot(Nl, w) / nll;
+  if (!(cp > 0.f && cy > 0.f)) return 0.f;
+  double total = s.light_cdf[s.L - 1];
+  float invP = (float)(total / s.light_area[ls.j]);
+  return cp * cy / r2 * (0.5f * nll) * invP;
+}
+
+// Radiance along a path (value only).  Vertices depth0..max_depth-1 are
+// shaded; emission is counted only at the first camera hit.  If tape_tri is
+// given, vertex b is stored at tape_tri[b*n_stride + n_idx].
+__device__ float3 path_value(const SceneView& s, const Opts& op, float o_in[3], float d_in[3], int exclude,
+                             bool emission_first, int depth0, uint32_t c0, uint32_t c1, uint32_t pass,
+                             int32_t* tape_tri, float2* tape_bary, int64_t n_idx, int64_t n_stride) {
+  float o[3] = {o_in[0], o_in[1], o_in[2]}, d[3] = {d_in[0], d_in[1], d_in[2]};
+  float3 L = zero3(), beta = make_float3(1.f, 1.f, 1.f);
+  int md = op.primary_only ? 1 : op.max_depth;
+  const float3 Le = ld3(s.radiance);
+  int b = depth0;
+  for (; b < md; ++b) {
+    Hit h = trace_closest(s, o, d, INFINITY, exclude);
+    if (h.tri < 0) break;
+    Vertex x;
+    load_vertex(s, h.tri, h.b1, h.b2, d, x);
+    float3 alb = ld3(s.albedo + 3 * x.k);
+    if (op.primary_only) {
+      L += beta * alb;
+      if (tape_tri) {
+        tape_tri[b * n_stride + n_idx] = x.k;
+        tape_bary[b * n_stride + n_idx] = make_float2(h.b1, h.b2);
+      }
+      ++b;
+      break;
+    }
+    if (b == depth0 && emission_first && s.light_of_tri[x.k] >= 0 && x.side < 0.0f) L += beta * Le;
+    float n32[3];
+    shading_normal32(x, n32);
+    int vis = 0;
+    if (s.L > 0) {
+      uint4 r = rng4(op.key, c0, c1, kLight, (uint32_t)b, pass, 0u);
+      LightSample ls;
+      sample_light(s, r, ls);
+      float sd[3] = {fs(ls.y[0], x.p[0]), fs(ls.y[1], x.p[1]), fs(ls.y[2], x.p[2])};
+      if (!trace_any(s, x.p, sd, kShadowTmax, x.k, ls.lt)) {
+        vis = 1;
+        float g = nee_geometry(s, f3(x.p), f3(n32), ls);
+        L += (kInvPi * g) * (beta * alb * Le);
+      }
+    }
+    if (tape_tri) {
+      tape_tri[b * n_stride + n_idx] = x.k | (vis << 31);
+      tape_bary[b * n_stride + n_idx] = make_float2(h.b1, h.b2);
+    }
+    if (b + 1 >= md) { ++b; break; }
+    uint4 r = rng4(op.key, c0, c1, kBsdf, (uint32_t)b, pass, 0u);
+    float nd[3];
+    cosine_dir(n32, u01f(r.x), u01f(r.y), nd);
+    if (!(dot(f3(n32), f3(nd)) > 0.f)) { ++b; break; }
+    beta = beta * alb;
+    for (int i = 0; i < 3; ++i) { o[i] = x.p[i]; d[i] = nd[i]; }
+    exclude = x.k;
+  }
+  if (tape_tri)
+    for (; b < md; ++b) tape_tri[b * n_stride + n_idx] = -1;
+  return L;
+}
+
+__device__ __forceinline__ void jitter(const Opts& op, int pix, int sidx, int W, float* sx, float* sy) {
+  uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kCamera, 0u, kPassInterior, 0u);
+  *sx = fa((float)(pix % W), u01f(r.x));
+  *sy = fa((float)(pix / W), u01f(r.y));
+}
+
+// ---------------------------------------------------------------------------
+// Forward
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_render(SceneView s, Opts op, float* image, int32_t* tape_tri,
+                                                   float2* tape_bary, int G) {
+  int lane = threadIdx.x & 31;
+  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int ppw = 32 / G;
+  int64_t pix = gw * ppw + lane / G;
+  int npix = s.W * s.H;
+  bool active = pix < npix;
+  int64_t n = (int64_t)npix * op.spp;
+  float3 acc = zero3();
+  if (active) {
+    for (int sidx = lane % G; sidx < op.spp; sidx += G) {
+      float sx, sy, o[3], d[3];
+      jitter(op, (int)pix, sidx, s.W, &sx, &sy);
+      camera_ray(s, sx, sy, o, d);
+      acc += path_value(s, op, o, d, -1, true, 0, (uint32_t)pix, (uint32_t)sidx, kPassInterior, tape_tri, tape_bary,
+                        pix * op.spp + sidx, n);
+    }
+  }
+  for (int o = G >> 1; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(kFull, acc.x, o);
+    acc.y += __shfl_xor_sync(kFull, acc.y, o);
+    acc.z += __shfl_xor_sync(kFull, acc.z, o);
+  }
+  if (active && lane % G == 0) {
+    float inv = 1.0f / (float)op.spp;
+    image[3 * pix] = acc.x * inv;
+    image[3 * pix + 1] = acc.y * inv;
+    image[3 * pix + 2] = acc.z * inv;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Backward helpers: camera adjoints
+// ---------------------------------------------------------------------------
+// Camera ray o, d as functions of the camera (same formulas as camera_ray):
+// accumulate d loss/d(camera) given the adjoints do_, dd_.
+__device__ __forceinline__ void camera_ray_adjoint(const SceneView& s, float sx, float sy, float3 do_, float3 dd_,
+                                                   float g[kGlobals]) {
+  const float* M = s.cam;
+  float S = s.cam_scale[0];
+  float fw = (float)s.W, fh = (float)s.H;
+  float xn = (2.0f * sx - fw) / fw, yn = (fh - 2.0f * sy) / fh;
+  float aspect = fw / fh;
+  float lx = xn * aspect * S, ly = yn * S;
+  float dov[3] = {do_.x, do_.y, do_.z}, ddv[3] = {dd_.x, dd_.y, dd_.z};
+  float dlx = 0.f, dly = 0.f;
+  for (int r = 0; r < 3; ++r) {
+    float* gm = g + 3 + 4 * r;
+    if (s.cam_type == 1) {
+      gm[3] += dov[r];
+      gm[0] += ddv[r] * lx;
+      gm[1] += ddv[r] * ly;
+      gm[2] -= ddv[r];
+      dlx += ddv[r] * M[4 * r];
+      dly += ddv[r] * M[4 * r + 1];
+    } else {
+      gm[0] += dov[r] * lx;
+      gm[1] += dov[r] * ly;
+      gm[3] += dov[r];
+      gm[2] -= ddv[r];
+      dlx += dov[r] * M[4 * r];
+      dly += dov[r] * M[4 * r + 1];
+    }
+  }
+  g[15] += dlx * xn * aspect + dly * yn;
+}
+
+// Projection of world point v to the screen: given d loss/d(sx, sy), return
+// d loss/dv and accumulate the camera adjoints (vc = R^-1 (v - t)).
+__device__ __forceinline__ float3 project_adjoint(const SceneView& s, float3 v, float dsx, float dsy,
+                                                  float g[kGlobals]) {
+  const float* Wm = s.w2c;
+  float vc[3];
+  for (int i = 0; i < 3; ++i) vc[i] = Wm[4 * i] * v.x + Wm[4 * i + 1] * v.y + Wm[4 * i + 2] * v.z + Wm[4 * i + 3];
+  float S = s.cam_scale[0];
+  float fw = (float)s.W, fh = (float)s.H;
+  float aspect = fw / fh;
+  float px = vc[0], py = vc[1], iz = 1.f;
+  if (s.cam_type == 1) {
+    iz = -vc[2];
+    px = vc[0] / iz;
+    py = vc[1] / iz;
+  }
+  float xn = px / (aspect * S), yn = py / S;
+  float dxn = dsx * (0.5f * fw), dyn = -dsy * (0.5f * fh);
+  float dpx = dxn / (aspect * S), dpy = dyn / S;
+  g[15] += -(dxn * xn + dyn * yn) / S;
+  float dvc[3];
+  if (s.cam_type == 1) {
+    dvc[0] = dpx / iz;
+    dvc[1] = dpy / iz;
+    dvc[2] = (dpx * px + dpy * py) / iz;
+  } else {
+    dvc[0] = dpx; dvc[1] = dpy; dvc[2] = 0.f;
+  }
+  float3 dv;
+  dv.x = Wm[0] * dvc[0] + Wm[4] * dvc[1] + Wm[8] * dvc[2];
+  dv.y = Wm[1] * dvc[0] + Wm[5] * dvc[1] + Wm[9] * dvc[2];
+  dv.z = Wm[2] * dvc[0] + Wm[6] * dvc[1] + Wm[10] * dvc[2];
+  float dva[3] = {dv.x, dv.y, dv.z};
+  for (int i = 0; i < 3; ++i) {
+    float* gm = g + 3 + 4 * i;
+    gm[3] -= dva[i];
+    for (int j = 0; j < 3; ++j) gm[j] -= dva[i] * vc[j];
+  }
+  return dv;
+}
+
+// ---------------------------------------------------------------------------
+// Backward: interior term + secondary edges (depth-1 paths)
+// ---------------------------------------------------------------------------
+struct Grads {
+  float* verts;
+  float* albedo;
+  float* partials;
+};
+
+__global__ void __launch_bounds__(kBlock) k_backward_interior(SceneView s, Opts op, const int32_t* tape_tri,
+                                                              const float2* tape_bary, const float* d_image, Grads gr,
+                                                              int G) {
+  int lane = threadIdx.x & 31;
+  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int ppw = 32 / G;
+  int64_t pix = gw * ppw + lane / G;
+  int npix = s.W * s.H;
+  bool pix_ok = pix < npix && pix >= op.pix_begin && pix < op.pix_end;
+  int64_t n = (int64_t)npix * op.spp;
+  float g[kGlobals];
+  for (int i = 0; i < kGlobals; ++i) g[i] = 0.f;
+  float3 wpix = pix_ok ? ld3(d_image + 3 * pix) : zero3();
+  float inv_spp = 1.0f / (float)op.spp;
+  float3 a = inv_spp * wpix;  // adjoint of the sample radiance
+  const float3 Le = ld3(s.radiance);
+  int iters = (op.spp + G - 1) / G;
+  bool do_int = (op.terms & 1) != 0, do_sec = (op.terms & 4) != 0;
+  for (int it = 0; it < iters; ++it) {
+    int sidx = lane % G + it * G;
+    bool active = pix_ok && sidx < op.spp;
+    int k = -1;
+    bool vis = false;
+    float b1 = 0.f, b2 = 0.f;
+    float sx = 0.f, sy = 0.f, o[3] = {0, 0, 0}, d[3] = {0, 0, 1};
+    if (active) {
+      jitter(op, (int)pix, sidx, s.W, &sx, &sy);
+      camera_ray(s, sx, sy, o, d);
+      int64_t ti = pix * op.spp + sidx;
+      if (tape_tri) {
+        int32_t tt = tape_tri[ti];
+        if (tt != -1) {
+          k = tt & 0x7fffffff;
+          vis = (tt >> 31) & 1;
+          float2 bb = tape_bary[ti];
+          b1 = bb.x; b2 = bb.y;
+        }
+      } else {
+        Hit h = trace_closest(s, o, d, INFINITY, -1);
+        if (h.tri >= 0) { k = h.tri; b1 = h.b1; b2 = h.b2; vis = true; /* refined below */ }
+      }
+    }
+    bool hit = active && k >= 0;
+    // per-sample adjoints to scatter
+    float3 dv0 = zero3(), dv1 = zero3(), dv2 = zero3(), dl0 = zero3(), dl1 = zero3(), dl2 = zero3();
+    float3 dalb = zero3();
+    int vid0 = 0, vid1 = 0, vid2 = 0, lid0 = 0, lid1 = 0, lid2 = 0;
+    bool have_light = false;
+    // secondary edge scatter targets
+    float3 de0 = zero3(), de1 = zero3();
+    float3 dmv[2][3] = {{zero3(), zero3(), zero3()}, {zero3(), zero3(), zero3()}};
+    int eid0 = 0, eid1 = 0, mids[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    bool have_edge = false, have_m[2] = {false, false};
+    if (hit) {
+      Vertex x;
+      load_vertex(s, k, b1, b2, d, x);
+      const int32_t* vid = s.tris + 3 * k;
+      vid0 = vid[0]; vid1 = vid[1]; vid2 = vid[2];
+      float3 alb = ld3(s.albedo + 3 * k);
+      float3 ov = f3(o), dvv = f3(d);
+      float3 e1 = x.v1 - x.v0, e2 = x.v2 - x.v0;
+      float3 Nk = cross(e1, e2);
+      float nkl = len(Nk);
+      float flip = x.side > 0.0f ? -1.f : 1.f;
+      float3 nhat = (1.f / nkl) * Nk;
+      float3 n = flip * nhat;
+      float num = dot(x.v0 - ov, Nk), den = dot(dvv, Nk);
+      float tau = num / den;
+      float3 p = f3(x.p);
+      float3 dp = zero3(), dn = zero3();
+      if (op.primary_only) {
+        if (do_int) dalb = a;
+      } else {
+        if (do_int && s.light_of_tri[k] >= 0 && x.side < 0.0f) {
+          g[0] += a.x; g[1] += a.y; g[2] += a.z;
+        }
+        if (s.L > 0 && do_int) {
+          uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kLight, 0u, kPassInterior, 0u);
+          LightSample ls;
+          sample_light(s, r, ls);
+          if (!tape_tri) {
+            float sd[3] = {fs(ls.y[0], x.p[0]), fs(ls.y[1], x.p[1]), fs(ls.y[2], x.p[2])};
+            vis = !trace_any(s, x.p, sd, kShadowTmax, x.k, ls.lt);
+          }
+          if (vis) {
+            float3 W = f3(ls.y) - p;
+            float r2 = dot(W, W);
+            float rr = sqrtf(r2);
+            float3 w = (1.f / rr) * W;
+            float cp = dot(n, w);
+            float3 el1 = ls.l1 - ls.l0, el2 = ls.l2 - ls.l0;
+            float3 Nl = cross(el1, el2);
+            float nll = len(Nl);
+            float3 nl = (1.f / nll) * Nl;
+            float cy = -dot(nl, w);
+            if (cp > 0.f && cy > 0.f) {
+              double total = s.light_cdf[s.L - 1];
+              float invP = (float)(total / s.light_area[ls.j]);
+              float Aj = 0.5f * nll;
+              float Gf = cp * cy / r2;
+              float common = kInvPi * Gf * Aj * invP;
+              g[0] += a.x * alb.x * common;
+              g[1] += a.y * alb.y * common;
+              g[2] += a.z * alb.z * common;
+              dalb = make_float3(a.x * Le.x * common, a.y * Le.y * common, a.z * Le.z * common);
+              float Q = (a.x * alb.x * Le.x + a.y * alb.y * Le.y + a.z * alb.z * Le.z) * kInvPi * invP;
+              float dG = Q * Aj, dA = Q * Gf;
+              float dcp = dG * cy / r2, dcy = dG * cp / r2, dr2 = -dG * Gf / r2;
+              dn += dcp * w;
+              float3 dw = dcp * n - dcy * nl;
+              float3 dnl = -dcy * w;
+              float3 dW = (1.f / rr) * (dw - dot(dw, w) * w) + (2.f * dr2) * W;
+              dp -= dW;
+              float3 dy = dW;
+              float3 dNl = (1.f / nll) * (dnl - dot(dnl, nl) * nl) + (0.5f * dA) * nl;
+              float3 de1l = cross(el2, dNl), de2l = cross(dNl, el1);
+              dl0 = ls.w[0] * dy - de1l - de2l;
+              dl1 = ls.w[1] * dy + de1l;
+              dl2 = ls.w[2] * dy + de2l;
+              const int32_t* lid = s.tris + 3 * ls.lt;
+              lid0 = lid[0]; lid1 = lid[1]; lid2 = lid[2];
+              have_light = true;
+            }
+          }
+        }
+        // secondary edge sample at p (area form, direct lighting part)
+        if (do_sec && s.E > 0 && s.L > 0) {
+          uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kEdgeSecondary, 0u, kPassInterior, 0u);
+          double stotal = s.scdf[s.E - 1];
+          int e = cdf_pick(s.scdf, s.E, dm(u01d(r.x, r.y), stotal));
+          double le = s.scdf[e] - (e > 0 ? s.scdf[e - 1] : 0.0);
+          float t = u01f(r.z);
+          int2 ev = s.edges[e];
+          float3 ve0 = ld3(s.verts + 3 * ev.x), ve1 = ld3(s.verts + 3 * ev.y);
+          float om[3], a0[3], a1[3];
+          om[0] = fs(fa(ve0.x, fm(t, fs(ve1.x, ve0.x))), x.p[0]);
+          om[1] = fs(fa(ve0.y, fm(t, fs(ve1.y, ve0.y))), x.p[1]);
+          om[2] = fs(fa(ve0.z, fm(t, fs(ve1.z, ve0.z))), x.p[2]);
+          a0[0] = fs(ve0.x, x.p[0]); a0[1] = fs(ve0.y, x.p[1]); a0[2] = fs(ve0.z, x.p[2]);
+          a1[0] = fs(ve1.x, x.p[0]); a1[1] = fs(ve1.y, x.p[1]); a1[2] = fs(ve1.z, x.p[2]);
+          float N32[3] = {fs(fm(a0[1], a1[2]), fm(a0[2], a1[1])), fs(fm(a0[2], a1[0]), fm(a0[0], a1[2])),
+                          fs(fm(a0[0], a1[1]), fm(a0[1], a1[0]))};
+          float nlen32 = fsq(dot3x(N32, N32));
+          if (le > 0.0 && nlen32 > 0.0f) {
+            float invPE = (float)(stotal / le);
+            float nh32[3] = {fdv(N32[0], nlen32), fdv(N32[1], nlen32), fdv(N32[2], nlen32)};
+            float wl = fsq(dot3x(om, om));
+            float sh = fm(op.eps_rel, wl);
+            float3 E = ve1 - ve0, w = f3(om), Nv = f3(N32), nh = f3(nh32);
+            float Nlen = len(Nv);
+            float3 a0v = ve0 - p, a1v = ve1 - p;
+            float3 Ne = cross(a0v, a1v);
+            for (int side = 0; side < 2; ++side) {
+              float sg = side == 0 ? 1.f : -1.f;
+              float dsd[3];
+              for (int i = 0; i < 3; ++i) dsd[i] = side == 0 ? fa(om[i], fm(sh, nh32[i])) : fs(om[i], fm(sh, nh32[i]));
+              Hit hm = trace_closest(s, x.p, dsd, INFINITY, k);
+              if (hm.tri < 0) continue;
+              int lj = s.light_of_tri[hm.tri];
+              if (lj < 0) continue;
+              Vertex mv;
+              load_vertex(s, hm.tri, hm.b1, hm.b2, dsd, mv);
+              float3 m = f3(mv.p);
+              float3 dmp = m - p;
+              float mr2 = dot(dmp, dmp);
+              float3 wh = (1.f / sqrtf(mr2)) * dmp;
+              float cpm = dot(n, wh);
+              if (!(cpm > 0.f)) continue;
+              float3 nmu = f3(mv.nu);
+              float3 nm = (1.f / len(nmu)) * nmu;
+              float cm = -dot(nm, wh);
+              if (!(cm > 0.f)) continue;
+              float Gm = cpm * cm / mr2;
+              float hs = kInvPi * Gm * (a.x * alb.x * Le.x + a.y * alb.y * Le.y + a.z * alb.z * Le.z);
+              float wn = dot(w, nm);
+              float tm = dot(dmp, nm) / wn;
+              float3 J = tm * (E - (dot(E, nm) / wn) * w);
+              float cr = len(cross(nm, nh));
+              if (!(cr > 0.f)) continue;
+              float c = sg * hs * (len(J) / (Nlen * cr)) * invPE;
+              float3 mp = m - p;
+              float3 gv0 = cross(a1v, mp), gv1 = cross(mp, a0v);
+              de0 += c * gv0;
+              de1 += c * gv1;
+              dp -= c * (Ne + gv0 + gv1);
+              // m is attached to the light triangle it lies on (weights summing to one)
+              float bw1 = hm.b1, bw2 = hm.b2, bw0 = 1.f - bw1 - bw2;
+              const int32_t* mid = s.tris + 3 * hm.tri;
+              mids[side][0] = mid[0]; mids[side][1] = mid[1]; mids[side][2] = mid[2];
+              dmv[side][0] = (c * bw0) * Ne;
+              dmv[side][1] = (c * bw1) * Ne;
+              dmv[side][2] = (c * bw2) * Ne;
+              have_m[side] = true;
+            }
+            eid0 = ev.x; eid1 = ev.y;
+            have_edge = true;
+          }
+        }
+      }
+      // back-propagate dp and dn to the hit triangle and the camera
+      {
+        float3 dNk = zero3();
+        float3 dnh = flip * dn;
+        dNk += (1.f / nkl) * (dnh - dot(dnh, nhat) * nhat);
+        float dtau = dot(dp, dvv);
+        float3 do_ = dp, dd_ = tau * dp;
+        float dnum = dtau / den, dden = -dtau * tau / den;
+        dv0 += dnum * Nk;
+        do_ -= dnum * Nk;
+        dNk += dnum * (x.v0 - ov);
+        dd_ += dden * Nk;
+        dNk += dden * dvv;
+        float3 de1k = cross(e2, dNk), de2k = cross(dNk, e1);
+        dv1 += de1k;
+        dv2 += de2k;
+        dv0 -= de1k + de2k;
+        camera_ray_adjoint(s, sx, sy, do_, dd_, g);
+      }
+    }
+    // scatter (all lanes participate)
+    scatter3(gr.verts, vid0, dv0, hit);
+    scatter3(gr.verts, vid1, dv1, hit);
+    scatter3(gr.verts, vid2, dv2, hit);
+    scatter3(gr.albedo, k, dalb, hit);
+    scatter3(gr.verts, lid0, dl0, have_light);
+    scatter3(gr.verts, lid1, dl1, have_light);
+    scatter3(gr.verts, lid2, dl2, have_light);
+    scatter3(gr.verts, eid0, de0, have_edge);
+    scatter3(gr.verts, eid1, de1, have_edge);
+    for (int sd = 0; sd < 2; ++sd)
+      for (int q = 0; q < 3; ++q) scatter3(gr.verts, mids[sd][q], dmv[sd][q], have_m[sd]);
+  }
+  block_globals(g, gr.partials);
+}
+
+// ---------------------------------------------------------------------------
+// Backward: primary edge samples (Eq. mc)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_backward_primary(SceneView s, Opts op, const float* d_image, Grads gr,
+                                                             int64_t n_edge, int64_t per_thread) {
+  float g[kGlobals];
+  for (int i = 0; i < kGlobals; ++i) g[i] = 0.f;
+  int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  double ptotal = s.pcdf[s.E - 1];
+  float W = (float)s.W, H = (float)s.H;
+  float eps = fm(op.eps_rel, fmaxf(W, H));
+  for (int64_t it = 0; it < per_thread; ++it) {
+    int64_t j = it * nthreads + tid;
+    bool active = j < n_edge && ptotal > 0.0 && j >= op.edge_begin && j < op.edge_end;
+    float3 da3 = zero3(), db3 = zero3();
+    int ia = 0, ib = 0;
+    if (active) {
+      uint4 r = rng4(op.key, (uint32_t)j, 0u, kEdgePrimary, 0u, kPassPrimaryEdge, 0u);
+      int e = cdf_pick(s.pcdf, s.E, dm(u01d(r.x, r.y), ptotal));
+      const float4* row = reinterpret_cast<const float4*>(s.pedge + 8 * e);
+      float4 r0 = row[0], r1 = row[1];
+      float ax = r0.x, ay = r0.y, bx = r0.z, by = r0.w, t0 = r1.x, t1 = r1.y;
+      float dx = fs(bx, ax), dy = fs(by, ay);
+      float t = fa(t0, fm(u01f(r.z), fs(t1, t0)));
+      float x = fa(ax, fm(t, dx)), y = fa(ay, fm(t, dy));
+      float nlen = fsq(fa(fm(dx, dx), fm(dy, dy)));
+      float nx = fdv(-dy, nlen), ny = fdv(dx, nlen);
+      float xu = fa(x, fm(eps, nx)), yu = fa(y, fm(eps, ny));
+      float xl = fs(x, fm(eps, nx)), yl = fs(y, fm(eps, ny));
+      int px = min(max((int)floorf(x), 0), s.W - 1), py = min(max((int)floorf(y), 0), s.H - 1);
+      float3 w = ld3(d_image + 3 * ((int64_t)py * s.W + px));
+      float o[3], d[3];
+      camera_ray(s, xu, yu, o, d);
+      float3 Lu = path_value(s, op, o, d, -1, true, 0, (uint32_t)j, 0u, kPassPrimaryEdge, nullptr, nullptr, 0, 0);
+      camera_ray(s, xl, yl, o, d);
+      float3 Ll = path_value(s, op, o, d, -1, true, 0, (uint32_t)j, 0u, kPassPrimaryEdge, nullptr, nullptr, 0, 0);
+      float diff = dot(w, Lu - Ll);
+      if (diff != 0.f) {
+        float gl = sqrtf((ax - bx) * (ax - bx) + (ay - by) * (ay - by));
+        float c = (float)((double)diff * ptotal / ((double)gl * (double)n_edge));
+        float dax = c * (by - y), day = c * (x - bx), dbx = c * (y - ay), dby = c * (ax - x);
+        int2 ev = s.edges[e];
+        ia = ev.x; ib = ev.y;
+        da3 = project_adjoint(s, ld3(s.verts + 3 * ia), dax, day, g);
+        db3 = project_adjoint(s, ld3(s.verts + 3 * ib), dbx, dby, g);
+      } else {
+        active = false;
+      }
+    }
+    scatter3(gr.verts, ia, da3, active);
+    scatter3(gr.verts, ib, db3, active);
+  }
+  block_globals(g, gr.partials);
+}
+
+__global__ void k_debug_closest(SceneView s, int64_t n, const float* o, const float* d, int32_t* tri, float* tb) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float oo[3] = {o[3 * i], o[3 * i + 1], o[3 * i + 2]}, dd[3] = {d[3 * i], d[3 * i + 1], d[3 * i + 2]};
+  Hit h = trace_closest(s, oo, dd, INFINITY, -1);
+  tri[i] = h.tri;
+  tb[3 * i] = h.tri >= 0 ? h.t : 0.f;
+  tb[3 * i + 1] = h.b1;
+  tb[3 * i + 2] = h.b2;
+}
+
+int group_size(int spp) {
+  int G = 1;
+  while (G < spp && G < 32) G <<= 1;
+  return G;
+}
+
+}  // namespace
+
+cudaError_t launch_render(const drt_scene* sc, const Opts& op, float* image, drt_tape* tape, cudaStream_t st) {
+  SceneView s = sc->view();
+  s.counters = counter_slot(kSlotRender);
+  int npix = s.W * s.H;
+  int G = group_size(op.spp);
+  int64_t warps = ((int64_t)npix + (32 / G) - 1) / (32 / G);
+  int64_t blocks = (warps * 32 + kBlock - 1) / kBlock;
+  ProfToken pt = prof_begin("render", st);
+  k_render<<<(unsigned)blocks, kBlock, 0, st>>>(s, op, image, tape ? tape->tri : nullptr, tape ? tape->bary : nullptr,
+                                                G);
+  prof_end(pt, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape* tape, const float* d_image,
+                            float* d_verts, float* d_albedo, float* d_radiance, float* d_cam, float* d_cam_scale,
+                            float* partials, cudaStream_t st) {
+  SceneView s = sc->view();
+  int npix = s.W * s.H;
+  int G = group_size(op.spp);
+  int64_t warps = ((int64_t)npix + (32 / G) - 1) / (32 / G);
+  int64_t blocks_i = (warps * 32 + kBlock - 1) / kBlock;
+  int64_t n_edge = (int64_t)op.edge_spp * npix;
+  int64_t blocks_e = 0, per_thread = 0;
+  if ((op.terms & 2) && s.E > 0 && n_edge > 0) {
+    blocks_e = std::min<int64_t>((n_edge + kBlock - 1) / kBlock, 152 * 16);
+    per_thread = (n_edge + blocks_e * kBlock - 1) / (blocks_e * kBlock);
+  }
+  Grads gr{d_verts, d_albedo, partials};
+  bool need_i = (op.terms & 5) != 0;
+  if (need_i) {
+    s.counters = counter_slot(kSlotBwdInterior);
+    ProfToken pt = prof_begin("backward_interior", st);
+    k_backward_interior<<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tape ? tape->tri : nullptr,
+                                                               tape ? tape->bary : nullptr, d_image, gr, G);
+    prof_end(pt, st);
+  }
+  Grads ge{d_verts, d_albedo, partials + (need_i ? blocks_i : 0) * kGlobals};
+  if (blocks_e > 0) {
+    s.counters = counter_slot(kSlotBwdPrimary);
+    ProfToken pt = prof_begin("backward_primary_edges", st);
+    k_backward_primary<<<(unsigned)blocks_e, kBlock, 0, st>>>(s, op, d_image, ge, n_edge, per_thread);
+    prof_end(pt, st);
+  }
+  int rows = (int)((need_i ? blocks_i : 0) + blocks_e);
+  if (rows > 0) {
+    ProfToken pt = prof_begin("reduce_globals", st);
+    k_reduce_globals<<<1, 32, 0, st>>>(partials, rows, d_radiance, d_cam, d_cam_scale);
+    prof_end(pt, st);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_debug_closest(const drt_scene* sc, int64_t n, const float* o, const float* d, int32_t* tri,
+                                 float* tb, cudaStream_t st) {
+  SceneView v = sc->view();
+  v.counters = counter_slot(kSlotDebug);
+  if (n > 0) k_debug_closest<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, st>>>(v, n, o, d, tri, tb);
+  return cudaGetLastError();
+}
+
+int64_t backward_partial_rows(const drt_scene* sc, const Opts& op) {
+  int npix = sc->W * sc->H;
+  int G = group_size(op.spp);
+  int64_t warps = ((int64_t)npix + (32 / G) - 1) / (32 / G);
+  int64_t blocks_i = (warps * 32 + kBlock - 1) / kBlock;
+  int64_t n_edge = (int64_t)op.edge_spp * npix;
+  int64_t blocks_e = std::min<int64_t>((n_edge + kBlock - 1) / kBlock, 152 * 16);
+  return blocks_i + blocks_e;
+}
+
+}  // namespace drt

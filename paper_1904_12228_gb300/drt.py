@@ -1,0 +1,283 @@
+"""Python binding of the C ABI in include/drt.h (argument marshalling only).
+
+Every step of rendering and differentiation runs in the CUDA library
+``_lib/libdrt.so``; this module passes pointers, sizes and the current CUDA
+stream.  There is no fallback: if the library cannot be loaded, every call
+raises.
+
+Arrays may be torch CUDA tensors, torch CPU tensors or numpy arrays (host
+memory is copied by the library on the stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DRT_OK = 0
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "DEVICE_FLAG", 6: "STATE"}
+TERM_INTERIOR, TERM_PRIMARY, TERM_SECONDARY = 1, 2, 4
+
+EXPORTED = ("drt_create", "drt_destroy", "drt_scene_upload", "drt_scene_update_vertices", "drt_scene_update_params",
+            "drt_scene_free", "drt_render", "drt_render_backward", "drt_tape_free", "drt_check_device",
+            "drt_last_error", "drt_version", "drt_debug_closest", "drt_profile_enable", "drt_profile_read",
+            "drt_counters_enable", "drt_counters_read")
+
+
+class DrtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("drt status %s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class SceneDesc(ctypes.Structure):
+    _fields_ = [("verts", ctypes.c_void_p), ("n_verts", ctypes.c_int32), ("tris", ctypes.c_void_p),
+                ("n_tris", ctypes.c_int32), ("albedo", ctypes.c_void_p), ("light_tris", ctypes.c_void_p),
+                ("n_light_tris", ctypes.c_int32), ("radiance", ctypes.c_void_p), ("cam_to_world", ctypes.c_void_p),
+                ("cam_scale", ctypes.c_float), ("cam_type", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32)]
+
+
+class RenderOpts(ctypes.Structure):
+    _fields_ = [("spp", ctypes.c_int32), ("edge_spp", ctypes.c_int32), ("max_depth", ctypes.c_int32),
+                ("primary_only", ctypes.c_int32), ("seed", ctypes.c_uint64), ("eps_rel", ctypes.c_float),
+                ("terms", ctypes.c_int32)]
+
+
+class Grads(ctypes.Structure):
+    _fields_ = [("d_verts", ctypes.c_void_p), ("d_albedo", ctypes.c_void_p), ("d_radiance", ctypes.c_void_p),
+                ("d_cam_to_world", ctypes.c_void_p), ("d_cam_scale", ctypes.c_void_p)]
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libdrt.so (building it first if needed); raises if unavailable."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path) or not _build.up_to_date():
+        if not build_if_missing:
+            raise RuntimeError("CUDA library %s is missing; run __graft_entry__.build()" % path)
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, i32, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "drt_create": ([ctypes.c_int, pp], i32),
+        "drt_destroy": ([vp], i32),
+        "drt_scene_upload": ([vp, ctypes.POINTER(SceneDesc), vp, pp], i32),
+        "drt_scene_update_vertices": ([vp, vp, vp, vp], i32),
+        "drt_scene_update_params": ([vp, vp, vp, vp, vp, vp, vp], i32),
+        "drt_scene_free": ([vp, vp], i32),
+        "drt_render": ([vp, vp, ctypes.POINTER(RenderOpts), vp, pp, vp], i32),
+        "drt_render_backward": ([vp, vp, vp, ctypes.POINTER(RenderOpts), vp, ctypes.POINTER(Grads), vp], i32),
+        "drt_tape_free": ([vp, vp], i32),
+        "drt_check_device": ([vp, vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], i32),
+        "drt_debug_closest": ([vp, vp, ctypes.c_int64, vp, vp, vp, vp, vp], i32),
+        "drt_profile_enable": ([vp, ctypes.c_int], i32),
+        "drt_profile_read": ([vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(ctypes.c_int)], i32),
+        "drt_counters_enable": ([vp, ctypes.c_int], i32),
+        "drt_counters_read": ([vp, vp], i32),
+        "drt_last_error": ([], ctypes.c_char_p),
+        "drt_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _LIB = lib
+    return lib
+
+
+def _check(status):
+    if status != DRT_OK:
+        raise DrtError(status, load().drt_last_error().decode(errors="replace"))
+
+
+def _ptr(a):
+    """Pointer of a torch tensor or numpy array (must stay alive during the call)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("array must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError("unsupported array type %r" % type(a))
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return 0
+
+
+def make_opts(spp, edge_spp=None, max_depth=1, primary_only=False, seed=0, eps_rel=0.0, terms=0) -> RenderOpts:
+    return RenderOpts(int(spp), int(spp if edge_spp is None else edge_spp), int(max_depth), int(bool(primary_only)),
+                      int(seed) & (2 ** 64 - 1), float(eps_rel), int(terms))
+
+
+class Context:
+    """A library context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        _check(self.lib.drt_create(int(device), ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            self.lib.drt_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check_device(self, stream=None):
+        """Synchronise and read the device error flag; returns (code, info)."""
+        code, info = ctypes.c_int32(), ctypes.c_int32()
+        st = self.lib.drt_check_device(self.handle, _stream(stream), ctypes.byref(code), ctypes.byref(info))
+        if st not in (DRT_OK, 5):
+            _check(st)
+        return code.value, info.value
+
+
+    def profile(self, enable: bool):
+        """Bracket every library kernel launch with CUDA events on its stream."""
+        _check(self.lib.drt_profile_enable(self.handle, int(bool(enable))))
+
+    def profile_read(self):
+        """{kernel name: (total ms, launches)} since the last read (synchronises)."""
+        mx = 128
+        names = ctypes.create_string_buffer(64 * mx)
+        ms = np.zeros(mx, np.float64)
+        ln = np.zeros(mx, np.int64)
+        n = ctypes.c_int()
+        _check(self.lib.drt_profile_read(self.handle, mx, names, ms.ctypes.data, ln.ctypes.data, ctypes.byref(n)))
+        out = {}
+        for i in range(n.value):
+            nm = names.raw[64 * i:64 * (i + 1)].split(b"\0")[0].decode()
+            out[nm] = (float(ms[i]), int(ln[i]))
+        return out
+
+    def counters(self, enable: bool):
+        _check(self.lib.drt_counters_enable(self.handle, int(bool(enable))))
+
+    COUNTER_SLOTS = ("render", "backward_interior", "backward_primary_edges", "debug")
+
+    def counters_read(self):
+        """{slot: dict(closest_rays, shadow_rays, nodes, tris)} (synchronises, resets)."""
+        a = np.zeros((4, 4), np.int64)
+        _check(self.lib.drt_counters_read(self.handle, a.ctypes.data))
+        return {nm: dict(closest_rays=int(a[i, 0]), shadow_rays=int(a[i, 1]), nodes=int(a[i, 2]), tris=int(a[i, 3]))
+                for i, nm in enumerate(self.COUNTER_SLOTS)}
+
+
+class Tape:
+    def __init__(self, ctx, handle):
+        self.ctx, self.handle = ctx, handle
+
+    def free(self):
+        if self.handle:
+            self.ctx.lib.drt_tape_free(self.ctx.handle, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Scene:
+    """An uploaded scene.  ``arrays`` are kept alive until the upload returns."""
+
+    def __init__(self, ctx: Context, verts, tris, albedo, light_tris, radiance, cam_to_world, cam_scale, cam_type,
+                 width, height, stream=None):
+        self.ctx = ctx
+        self.n_verts, self.n_tris = int(verts.shape[0]), int(tris.shape[0])
+        self.width, self.height = int(width), int(height)
+        nl = int(light_tris.shape[0]) if light_tris is not None else 0
+        desc = SceneDesc(_ptr(verts), self.n_verts, _ptr(tris), self.n_tris, _ptr(albedo),
+                         _ptr(light_tris) if nl else None, nl, _ptr(radiance), _ptr(cam_to_world),
+                         float(cam_scale), int(cam_type), self.width, self.height)
+        h = ctypes.c_void_p()
+        _check(ctx.lib.drt_scene_upload(ctx.handle, ctypes.byref(desc), _stream(stream), ctypes.byref(h)))
+        self.handle = h
+
+    @classmethod
+    def from_arrays(cls, ctx, sc, stream=None):
+        """Upload a ``scenegen.Scene`` (host numpy arrays)."""
+        return cls(ctx, sc.verts, sc.tris, sc.albedo, sc.light_tris, sc.radiance, sc.cam_to_world, sc.cam_scale,
+                   sc.cam_type, sc.width, sc.height, stream)
+
+    def update_vertices(self, verts, stream=None):
+        _check(self.ctx.lib.drt_scene_update_vertices(self.ctx.handle, self.handle, _ptr(verts), _stream(stream)))
+
+    def update_params(self, albedo=None, radiance=None, cam_to_world=None, cam_scale=None, stream=None):
+        cs = None
+        if cam_scale is not None:
+            cs = np.array([cam_scale], np.float32) if np.isscalar(cam_scale) else cam_scale
+        _check(self.ctx.lib.drt_scene_update_params(self.ctx.handle, self.handle, _ptr(albedo), _ptr(radiance),
+                                                    _ptr(cam_to_world), _ptr(cs), _stream(stream)))
+
+    def free(self):
+        if self.handle:
+            self.ctx.lib.drt_scene_free(self.ctx.handle, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def closest(self, o, d, tri, tb, stream=None):
+        """Closest hits of rays o, d [n,3] into tri [n] (int32) and tb [n,3]."""
+        _check(self.ctx.lib.drt_debug_closest(self.ctx.handle, self.handle, int(o.shape[0]), _ptr(o), _ptr(d),
+                                              _ptr(tri), _ptr(tb), _stream(stream)))
+
+    def render(self, image, opts: RenderOpts, want_tape=False, stream=None, reuse=None):
+        """Render into ``image`` [H,W,3] float32; returns a Tape if asked.
+        ``reuse``: a Tape of this scene whose storage is overwritten."""
+        if reuse is not None:
+            th = reuse.handle
+            _check(self.ctx.lib.drt_render(self.ctx.handle, self.handle, ctypes.byref(opts), _ptr(image),
+                                           ctypes.byref(th), _stream(stream)))
+            reuse.handle = th
+            return reuse
+        th = ctypes.c_void_p()
+        _check(self.ctx.lib.drt_render(self.ctx.handle, self.handle, ctypes.byref(opts), _ptr(image),
+                                       ctypes.byref(th) if want_tape else None, _stream(stream)))
+        return Tape(self.ctx, th) if want_tape else None
+
+    def backward(self, d_image, opts: RenderOpts, tape=None, d_verts=None, d_albedo=None, d_radiance=None,
+                 d_cam_to_world=None, d_cam_scale=None, stream=None):
+        """Add d loss / d parameters into the given gradient arrays."""
+        g = Grads(_ptr(d_verts), _ptr(d_albedo), _ptr(d_radiance), _ptr(d_cam_to_world), _ptr(d_cam_scale))
+        _check(self.ctx.lib.drt_render_backward(self.ctx.handle, self.handle, tape.handle if tape else None,
+                                                ctypes.byref(opts), _ptr(d_image), ctypes.byref(g),
+                                                _stream(stream)))

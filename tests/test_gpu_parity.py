@@ -1,0 +1,255 @@
+"""CUDA path against the CPU oracle, element by element, on the same seeded
+inputs (run on the GB300 machine: ``pytest -m gpu``).
+
+Tolerances (floating point, FP32 kernels vs the oracle's FP64 smooth values
+and FP64 sums, identical discrete decisions):
+  pixels     |I_gpu - I_or| <= 1e-4 |I_or| + 1e-7
+  gradients  |g_gpu - g_or| <= 1e-4 |g_or| + 1e-6 A,  A = the oracle's
+             magnitude of the terms summed into that entry (the chain rule
+             taken with absolute values, and |f_u|+|f_l| for an edge sample's
+             radiance difference); the second term bounds FP32 rounding of
+             contributions that are small by cancellation and of the
+             unordered atomic sums.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1904_12228_gb300 import scenegen as sg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NT = oracle.n_threads_default()
+
+
+@pytest.fixture(scope="module")
+def drt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1904_12228_gb300 import drt as d
+    d.load()
+    return d
+
+
+@pytest.fixture(scope="module")
+def ctx(drt):
+    return drt.Context(0)
+
+
+def gpu_render(drt, ctx, scene, spp, seed, primary_only=False, edge_spp=None, want_tape=False, max_depth=1):
+    s = drt.Scene.from_arrays(ctx, scene)
+    img = torch.zeros((scene.height, scene.width, 3), dtype=torch.float32, device="cuda")
+    opts = drt.make_opts(spp, edge_spp, max_depth=max_depth, primary_only=primary_only, seed=seed)
+    tape = s.render(img, opts, want_tape=want_tape)
+    torch.cuda.synchronize()
+    return s, img, tape, opts
+
+
+def gpu_grads(drt, ctx, scene, d_image, spp, edge_spp, seed, primary_only=False, terms=7, use_tape=True):
+    s, img, tape, _ = gpu_render(drt, ctx, scene, spp, seed, primary_only, edge_spp, want_tape=use_tape)
+    opts = drt.make_opts(spp, edge_spp, primary_only=primary_only, seed=seed, terms=terms)
+    dv = torch.zeros((len(scene.verts), 3), dtype=torch.float32, device="cuda")
+    da = torch.zeros((len(scene.tris), 3), dtype=torch.float32, device="cuda")
+    dr = torch.zeros(3, dtype=torch.float32, device="cuda")
+    dc = torch.zeros((3, 4), dtype=torch.float32, device="cuda")
+    ds = torch.zeros(1, dtype=torch.float32, device="cuda")
+    w = torch.from_numpy(d_image).cuda()
+    s.backward(w, opts, tape=tape if use_tape else None, d_verts=dv, d_albedo=da, d_radiance=dr, d_cam_to_world=dc,
+               d_cam_scale=ds)
+    torch.cuda.synchronize()
+    code, info = ctx.check_device()
+    assert code == 0, (code, info)
+    flat = np.concatenate([x.cpu().numpy().ravel().astype(np.float64) for x in (dv, da, dr, dc, ds)])
+    return flat, img.cpu().numpy()
+
+
+def assert_pixels(got, want):
+    err = np.abs(got - want)
+    bound = 1e-4 * np.abs(want) + 1e-7
+    bad = err > bound
+    assert not bad.any(), "%d/%d pixels off; worst err %g at %s (want %g)" % (
+        bad.sum(), bad.size, err.max(), np.unravel_index(err.argmax(), err.shape), want.flat[err.argmax()])
+
+
+def assert_grads(got, want, absum, label=""):
+    err = np.abs(got - want)
+    bound = 1e-4 * np.abs(want) + 1e-6 * absum + 1e-12
+    bad = err > bound
+    i = int(np.argmax(err / bound))
+    assert not bad.any(), "%s: %d/%d entries off; worst entry %d got %g want %g (A=%g)" % (
+        label, bad.sum(), bad.size, i, got[i], want[i], absum[i])
+
+
+# ---------------------------------------------------------------------------
+def test_library_exports_and_context(drt, ctx):
+    lib = drt.load()
+    for name in drt.EXPORTED:
+        assert hasattr(lib, name)
+    assert b"sm_103a" in lib.drt_version()
+
+
+def test_traversal_matches_brute_force(drt, ctx):
+    scene = sg.direct_lighting(1236, width=8, height=8, subdiv=3)
+    s = drt.Scene.from_arrays(ctx, scene)
+    rng = np.random.default_rng(1)
+    n = 20000
+    o = (np.array([0.0, 1.0, 5.0]) + rng.normal(0, 0.2, (n, 3))).astype(np.float32)
+    d = (rng.normal(0, 0.35, (n, 3)) + np.array([0, -0.2, -1.0])).astype(np.float32)
+    # rays aimed exactly at vertices and edge midpoints stress the watertight test
+    tgt = np.concatenate([scene.verts[:2000], 0.5 * (scene.verts[scene.tris[:2000, 0]] + scene.verts[scene.tris[:2000, 1]])])
+    o2 = np.tile(np.array([0.3, 0.9, 4.0], np.float32), (len(tgt), 1))
+    o = np.concatenate([o, o2]).astype(np.float32)
+    d = np.concatenate([d, (tgt - o2)]).astype(np.float32)
+    tri = torch.zeros(len(o), dtype=torch.int32, device="cuda")
+    tb = torch.zeros((len(o), 3), dtype=torch.float32, device="cuda")
+    s.closest(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda(), tri, tb)
+    torch.cuda.synchronize()
+    want_tri, want_tb = oracle.closest(scene, o, d, n_threads=NT)
+    got_tri = tri.cpu().numpy()
+    assert (got_tri == want_tri).all(), np.nonzero(got_tri != want_tri)[0][:10]
+    hit = want_tri >= 0
+    assert np.array_equal(tb.cpu().numpy()[hit], want_tb[hit])
+
+
+@pytest.mark.parametrize("seed", [1235, 7])
+def test_single_triangle_image(drt, ctx, seed):
+    scene = sg.single_triangle(seed)
+    _, img, _, _ = gpu_render(drt, ctx, scene, 16, seed, primary_only=True)
+    want = oracle.render(scene, spp=16, seed=seed, primary_only=True, n_threads=NT)
+    assert_pixels(img.cpu().numpy().astype(np.float64), want)
+
+
+@pytest.mark.parametrize("seed", [1235, 7])
+def test_single_triangle_gradient(drt, ctx, seed):
+    scene = sg.single_triangle(seed)
+    w = sg.loss_adjoint(seed, scene.width, scene.height)
+    got, _ = gpu_grads(drt, ctx, scene, w, 16, 16, seed, primary_only=True)
+    want, absum = oracle.backward(scene, w, spp=16, edge_spp=16, seed=seed, primary_only=True, n_threads=NT)
+    assert_grads(got, want, absum, "single triangle")
+    assert np.abs(want[:9]).max() > 0
+
+
+def _small_lit(seed=1236, W=40, H=28, subdiv=2):
+    return sg.direct_lighting(seed, width=W, height=H, subdiv=subdiv)
+
+
+def test_direct_lighting_image(drt, ctx):
+    scene = _small_lit()
+    _, img, _, _ = gpu_render(drt, ctx, scene, 8, 11)
+    want = oracle.render(scene, spp=8, seed=11, n_threads=NT)
+    assert_pixels(img.cpu().numpy().astype(np.float64), want)
+
+
+@pytest.mark.parametrize("terms", [1, 2, 4, 7])
+def test_direct_lighting_gradient_terms(drt, ctx, terms):
+    scene = _small_lit()
+    w = sg.loss_adjoint(3, scene.width, scene.height)
+    got, _ = gpu_grads(drt, ctx, scene, w, 8, 8, 11, terms=terms)
+    want, absum = oracle.backward(scene, w, spp=8, edge_spp=8, seed=11, terms=terms, n_threads=NT)
+    assert_grads(got, want, absum, "terms=%d" % terms)
+
+
+def test_backward_without_tape_matches_with_tape(drt, ctx):
+    scene = _small_lit(W=24, H=16)
+    w = sg.loss_adjoint(5, scene.width, scene.height)
+    a, _ = gpu_grads(drt, ctx, scene, w, 4, 4, 3, use_tape=True)
+    b, _ = gpu_grads(drt, ctx, scene, w, 4, 4, 3, use_tape=False)
+    want, absum = oracle.backward(scene, w, spp=4, edge_spp=4, seed=3, n_threads=NT)
+    assert_grads(a, want, absum, "tape")
+    assert_grads(b, want, absum, "no tape")
+
+
+def test_ragged_sizes_and_spp(drt, ctx):
+    """Odd image sizes, spp not a power of two, a single pixel, spp=1."""
+    for (W, H, spp) in ((13, 7, 3), (1, 1, 5), (17, 9, 1), (5, 3, 33)):
+        scene = _small_lit(W=W, H=H, subdiv=1)
+        _, img, _, _ = gpu_render(drt, ctx, scene, spp, 5)
+        want = oracle.render(scene, spp=spp, seed=5, n_threads=NT)
+        assert_pixels(img.cpu().numpy().astype(np.float64), want)
+        w = sg.loss_adjoint(W, W, H)
+        got, _ = gpu_grads(drt, ctx, scene, w, spp, spp, 5)
+        g, a = oracle.backward(scene, w, spp=spp, edge_spp=spp, seed=5, n_threads=NT)
+        assert_grads(got, g, a, "%dx%d spp=%d" % (W, H, spp))
+
+
+def test_render_is_deterministic(drt, ctx):
+    scene = _small_lit(W=32, H=32)
+    _, a, _, _ = gpu_render(drt, ctx, scene, 16, 9)
+    _, b, _, _ = gpu_render(drt, ctx, scene, 16, 9)
+    assert torch.equal(a, b)
+
+
+def test_host_buffers_match_device_buffers(drt, ctx):
+    scene = _small_lit(W=16, H=12, subdiv=1)
+    s = drt.Scene.from_arrays(ctx, scene)
+    opts = drt.make_opts(4, 4, seed=2)
+    dev = torch.zeros((12, 16, 3), dtype=torch.float32, device="cuda")
+    host = np.zeros((12, 16, 3), np.float32)
+    s.render(dev, opts)
+    s.render(host, opts)
+    torch.cuda.synchronize()
+    assert np.array_equal(dev.cpu().numpy(), host)
+
+
+def test_invalid_arguments_are_rejected(drt, ctx):
+    scene = _small_lit(W=8, H=8, subdiv=1)
+    bad = scene.copy()
+    bad.tris = bad.tris.copy()
+    bad.tris[0, 0] = len(bad.verts) + 5
+    with pytest.raises(drt.DrtError) as e:
+        drt.Scene.from_arrays(ctx, bad)
+    assert e.value.status == 1
+    s = drt.Scene.from_arrays(ctx, scene)
+    img = torch.zeros((8, 8, 3), dtype=torch.float32, device="cuda")
+    with pytest.raises(drt.DrtError):
+        s.render(img, drt.make_opts(0))
+    # a tape from another scene is refused
+    s2 = drt.Scene.from_arrays(ctx, scene)
+    tape = s2.render(img, drt.make_opts(2, seed=1), want_tape=True)
+    with pytest.raises(drt.DrtError) as e:
+        s.backward(torch.zeros_like(img), drt.make_opts(2, seed=1), tape=tape,
+                   d_verts=torch.zeros((len(scene.verts), 3), device="cuda"))
+    assert e.value.status == 6
+
+
+def test_nonfinite_vertices_raise_the_device_flag(drt, ctx):
+    scene = _small_lit(W=8, H=8, subdiv=1)
+    bad = scene.copy()
+    bad.verts[3, 1] = np.nan
+    s = drt.Scene.from_arrays(ctx, bad)
+    code, info = ctx.check_device()
+    assert code == 2 and info == 3 * 3 + 1
+    assert ctx.check_device() == (0, 0)
+    del s
+
+
+# ---------------------------------------------------------------------------
+# Full-size direct-lighting workload (256x256, 5124 triangles, 64 spp)
+# ---------------------------------------------------------------------------
+def test_full_size_image_on_sampled_pixels(drt, ctx):
+    scene = sg.direct_lighting(1236)
+    _, img, _, _ = gpu_render(drt, ctx, scene, 64, 1)
+    got = img.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(0)
+    for p in rng.choice(scene.width * scene.height, size=24, replace=False):
+        want = oracle.render(scene, spp=64, seed=1, pixels=(int(p), int(p) + 1), n_threads=NT)
+        y, x = divmod(int(p), scene.width)
+        assert_pixels(got[y, x], want[y, x])
+
+
+def test_full_size_gradient_invariants(drt, ctx):
+    """Properties that hold at any size: the image is invariant under a joint
+    translation of the scene and camera, and linear in the light radiance."""
+    scene = sg.direct_lighting(1236)
+    w = sg.loss_adjoint(1, scene.width, scene.height)
+    got, img = gpu_grads(drt, ctx, scene, w, 64, 64, 1)
+    V, T = len(scene.verts), len(scene.tris)
+    dv = got[:3 * V].reshape(V, 3)
+    dcam = got[3 * V + 3 * T + 3:3 * V + 3 * T + 15].reshape(3, 4)
+    total = dv.sum(0) + dcam[:, 3]
+    assert np.all(np.abs(total) <= 2e-3 * np.abs(dv).sum(0) + 1e-3), total
+    dLe = got[3 * V + 3 * T:3 * V + 3 * T + 3]
+    lhs = float((scene.radiance * dLe).sum())
+    rhs = float((w.astype(np.float64) * img).sum())
+    assert abs(lhs - rhs) <= 1e-4 * abs(rhs) + 1e-3
