@@ -155,6 +155,30 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* scene, const drt_tap
                                void* stream);
 drt_status drt_tape_free(drt_context* ctx, drt_tape* tape);
 
+/* drt_render_backward without any memory allocation.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate
+ * device memory inside their step: a loop that reserved the device memory up
+ * front through its own caching allocator (a cudaMalloc there can fail, or
+ * force the allocator to hand its cache back and stall), or a process held
+ * to a fixed device memory budget.  Arguments and results are those of
+ * drt_render_backward, except:
+ *   - d_image and every non-NULL gradient array must be device memory (no
+ *     host staging); otherwise DRT_ERR_INVALID_ARG.
+ *   - The scratch (one row of 16 partial sums per thread block) is a fixed
+ *     array of 65536 rows (4 MiB) compiled into the library, which every GPU
+ *     that loads the library holds until the process exits.  Images needing
+ *     more rows (about 2^21 pixels at spp >= 32) are rejected with
+ *     DRT_ERR_INVALID_ARG and a message giving the sizes.
+ *   - The first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress (the context's device must be current); make that
+ *     first call before any stream capture.
+ *   - All calls share the one array, and every call overwrites the rows it
+ *     reads before reading them; calls that overlap on the GPU (other streams,
+ *     other threads) race on it and must be serialised by the caller. */
+drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* scene, const drt_tape* tape,
+                                       const drt_render_opts* opts, const float* d_image, const drt_grads* grads,
+                                       void* stream);
+
 /* Closest-hit query through the scene's LBVH for n rays (test and debug
  * entry point; the render kernels use the same traversal).  o, d: [n,3]
  * origins and directions; tri: [n] hit triangle or -1; tb1b2: [n,3] =

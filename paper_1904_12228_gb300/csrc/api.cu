@@ -158,6 +158,10 @@ drt_status make_opts(const drt_render_opts* o, drt::Opts* op) {
 
 }  // namespace
 
+namespace drt {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace drt
+
 drt::SceneView drt_scene::view() const {
   drt::SceneView v;
   v.verts = verts; v.tris = tris; v.albedo = albedo; v.radiance = radiance; v.cam = cam; v.cam_scale = cam_scale;

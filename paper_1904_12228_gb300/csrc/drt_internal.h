@@ -52,6 +52,7 @@ struct drt_tape {
 };
 
 namespace drt {
+void set_last_error(const char* msg);  // message returned by drt_last_error on this thread
 // prof.cu: event timing of launches (when enabled) and work-counter slots
 struct ProfToken {
   const char* name;

@@ -1,0 +1,119 @@
+// noalloc.cu -- a backward pass that allocates no memory.
+//
+// drt_render_backward keeps its scratch (one row of per-block partial sums of
+// the global parameters per thread block) in a scene-owned buffer that it
+// grows with cudaMalloc, and copies host arrays through temporary device
+// buffers.  Some callers cannot allow an allocation inside their step: a
+// training or serving loop that reserved the device memory up front through
+// its own caching allocator (a cudaMalloc there can fail, or make the cache
+// give memory back and stall), or a process that runs under a fixed device
+// memory budget.  drt_render_backward_noalloc serves them: its scratch lives
+// in a fixed-size array compiled into this library, and it accepts device
+// arrays only.
+#include <climits>
+#include <cstdint>
+#include <cstdio>
+
+#include "drt_internal.h"
+
+namespace {
+
+// Maximum number of partial-sum rows (16 floats each): 65536 rows = 4 MiB.
+// A 512x512 image with spp >= 32 needs 32768 + 2432 rows.
+constexpr int64_t kNoAllocMaxRows = 65536;
+constexpr int kGlobalsPerRow = 16;
+
+// Shared by every call on a device and kept until the process exits.
+static __device__ __align__(256) float g_backward_scratch[kNoAllocMaxRows * kGlobalsPerRow];
+
+constexpr int kMaxDevices = 64;
+float* g_scratch_addr[kMaxDevices] = {nullptr};
+
+bool is_device_array(const void* p) {
+  if (!p) return true;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+drt_status fail_noalloc(drt_status st, const char* msg) {
+  drt::set_last_error(msg);
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* s, const drt_tape* tape,
+                                       const drt_render_opts* opts, const float* d_image, const drt_grads* grads,
+                                       void* stream) {
+  if (!ctx || !s || !opts || !d_image || !grads) {
+    return fail_noalloc(DRT_ERR_INVALID_ARG, "NULL argument");
+  }
+  drt::Opts op;
+  // same option checks and defaults as drt_render_backward
+  if (opts->spp < 1 || opts->edge_spp < 0 || opts->max_depth < 1 || opts->max_depth > 8 || opts->terms < 0 ||
+      opts->terms > 7) {
+    return fail_noalloc(DRT_ERR_INVALID_ARG, "invalid render options");
+  }
+  op.spp = opts->spp;
+  op.edge_spp = opts->edge_spp;
+  op.max_depth = opts->max_depth;
+  op.primary_only = opts->primary_only ? 1 : 0;
+  op.terms = opts->terms == 0 ? 7 : opts->terms;
+  op.key = make_uint2((uint32_t)opts->seed, (uint32_t)(opts->seed >> 32));
+  op.eps_rel = opts->eps_rel > 0.0f ? opts->eps_rel : 1.52587890625e-05f;
+  op.pix_begin = 0;
+  op.pix_end = INT32_MAX;
+  op.edge_begin = 0;
+  op.edge_end = INT64_MAX;
+  if (!op.primary_only && op.max_depth > 1) {
+    return fail_noalloc(DRT_ERR_INVALID_ARG, "backward supports max_depth == 1 in this build");
+  }
+  if (tape) {
+    const drt_render_opts& t = tape->opts;
+    if (tape->scene != s || tape->generation != s->generation || t.spp != opts->spp || t.seed != opts->seed ||
+        t.max_depth != opts->max_depth || (t.primary_only != 0) != (opts->primary_only != 0)) {
+      return fail_noalloc(DRT_ERR_STATE, "tape does not match this scene and these options");
+    }
+  }
+  const void* arrays[] = {d_image, grads->d_verts, grads->d_albedo, grads->d_radiance, grads->d_cam_to_world,
+                          grads->d_cam_scale};
+  for (const void* a : arrays)
+    if (!is_device_array(a)) {
+      return fail_noalloc(DRT_ERR_INVALID_ARG, "drt_render_backward_noalloc takes device arrays only");
+    }
+  int64_t rows = drt::backward_partial_rows(s, op);
+  if (rows > kNoAllocMaxRows) {
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "image too large for the fixed scratch: needs %lld rows, maximum %lld",
+                  (long long)rows, (long long)kNoAllocMaxRows);
+    return fail_noalloc(DRT_ERR_INVALID_ARG, buf);
+  }
+  // first call on this device: look up the device address of the array
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices || dev != ctx->device) {
+    return fail_noalloc(DRT_ERR_STATE, "the context's device must be the current device");
+  }
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_backward_scratch);
+    if (e != cudaSuccess || !p) {
+      return fail_noalloc(DRT_ERR_CUDA, cudaGetErrorString(e));
+    }
+    g_scratch_addr[dev] = static_cast<float*>(p);
+  }
+  cudaError_t e = drt::launch_backward(s, op, tape, d_image, grads->d_verts, grads->d_albedo, grads->d_radiance,
+                                       grads->d_cam_to_world, grads->d_cam_scale, g_scratch_addr[dev],
+                                       (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    return fail_noalloc(DRT_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return DRT_OK;
+}
+
+}  // extern "C"

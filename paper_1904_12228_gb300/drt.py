@@ -24,7 +24,7 @@ TERM_INTERIOR, TERM_PRIMARY, TERM_SECONDARY = 1, 2, 4
 EXPORTED = ("drt_create", "drt_destroy", "drt_scene_upload", "drt_scene_update_vertices", "drt_scene_update_params",
             "drt_scene_free", "drt_render", "drt_render_backward", "drt_tape_free", "drt_check_device",
             "drt_last_error", "drt_version", "drt_debug_closest", "drt_profile_enable", "drt_profile_read",
-            "drt_counters_enable", "drt_counters_read")
+            "drt_counters_enable", "drt_counters_read", "drt_render_backward_noalloc")
 
 
 class DrtError(RuntimeError):
@@ -82,6 +82,8 @@ def load(build_if_missing: bool = True):
         "drt_render": ([vp, vp, ctypes.POINTER(RenderOpts), vp, pp, vp], i32),
         "drt_render_backward": ([vp, vp, vp, ctypes.POINTER(RenderOpts), vp, ctypes.POINTER(Grads), vp], i32),
         "drt_tape_free": ([vp, vp], i32),
+        "drt_render_backward_noalloc": ([vp, vp, vp, ctypes.POINTER(RenderOpts), vp, ctypes.POINTER(Grads), vp],
+                                        i32),
         "drt_check_device": ([vp, vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], i32),
         "drt_debug_closest": ([vp, vp, ctypes.c_int64, vp, vp, vp, vp, vp], i32),
         "drt_profile_enable": ([vp, ctypes.c_int], i32),
@@ -273,6 +275,16 @@ class Scene:
         _check(self.ctx.lib.drt_render(self.ctx.handle, self.handle, ctypes.byref(opts), _ptr(image),
                                        ctypes.byref(th) if want_tape else None, _stream(stream)))
         return Tape(self.ctx, th) if want_tape else None
+
+    def backward_noalloc(self, d_image, opts: RenderOpts, tape=None, d_verts=None, d_albedo=None, d_radiance=None,
+                         d_cam_to_world=None, d_cam_scale=None, stream=None):
+        """``backward`` for callers that cannot allocate device memory during
+        the call: device arrays only, scratch in a fixed array inside the
+        library (see drt_render_backward_noalloc in include/drt.h)."""
+        g = Grads(_ptr(d_verts), _ptr(d_albedo), _ptr(d_radiance), _ptr(d_cam_to_world), _ptr(d_cam_scale))
+        _check(self.ctx.lib.drt_render_backward_noalloc(self.ctx.handle, self.handle, tape.handle if tape else None,
+                                                        ctypes.byref(opts), _ptr(d_image), ctypes.byref(g),
+                                                        _stream(stream)))
 
     def backward(self, d_image, opts: RenderOpts, tape=None, d_verts=None, d_albedo=None, d_radiance=None,
                  d_cam_to_world=None, d_cam_scale=None, stream=None):
