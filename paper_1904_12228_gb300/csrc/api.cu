@@ -124,7 +124,8 @@ void free_scene_buffers(drt_scene* s) {
   void* bufs[] = {s->verts, s->albedo, s->radiance, s->cam, s->cam_scale, s->tris, s->light_tris, s->light_of_tri,
                   s->w2c, s->light_cdf, s->light_area, s->nodes, s->soup, s->edges, s->pedge, s->plen, s->pcdf,
                   s->slen, s->scdf, s->scan_tmp, s->keys, s->keys2, s->vals, s->vals2, s->parent, s->leaf_parent,
-                  s->flags, s->hist, s->bounds, s->partials};
+                  s->flags, s->hist, s->hist_tmp, s->bounds, s->partials, s->esort.keys, s->esort.keys2,
+                  s->esort.hist, s->esort.hist_tmp, s->esort.vals, s->esort.vals2};
   for (void* b : bufs) dfree(b);
 }
 
@@ -260,7 +261,8 @@ drt_status drt_scene_upload(drt_context* ctx, const drt_scene_desc* d, void* str
   ALLOC(pedge, 8 * (size_t)std::max(1, E)) ALLOC(plen, std::max(1, E)) ALLOC(pcdf, std::max(1, E))
   ALLOC(slen, std::max(1, E)) ALLOC(scdf, std::max(1, E)) ALLOC(scan_tmp, std::max(1, E / 1024 + 2))
   ALLOC(keys, T) ALLOC(keys2, T) ALLOC(vals, T) ALLOC(vals2, T) ALLOC(parent, std::max(1, T))
-  ALLOC(leaf_parent, T) ALLOC(flags, std::max(1, T)) ALLOC(hist, 256 * (size_t)nb) ALLOC(bounds, 8)
+  ALLOC(leaf_parent, T) ALLOC(flags, std::max(1, T)) ALLOC(hist, drt::radix_hist_entries(T))
+  ALLOC(hist_tmp, drt::radix_hist_tmp_entries(T)) ALLOC(bounds, 8)
 #undef ALLOC
   if (stt != DRT_OK) {
     free_scene_buffers(s);
@@ -425,8 +427,34 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
     unstage(sg, 6, st);
     return r;
   }
+  // primary edge samples are evaluated in screen order: grow the sort scratch
+  int64_t n_edge = (op.terms & 2) ? (int64_t)op.edge_spp * s->W * s->H : 0;
+  const drt::SortBuffers* sort = nullptr;
+  if (n_edge > 0 && n_edge < INT32_MAX) {
+    if (n_edge > s->esort.cap) {
+      cudaStreamSynchronize(st);
+      drt::SortBuffers& b = s->esort;
+      void* old[] = {b.keys, b.keys2, b.hist, b.hist_tmp, b.vals, b.vals2};
+      for (void* p : old) dfree(p);
+      b = drt::SortBuffers();
+      int n = (int)n_edge;
+      drt_status a = dalloc_n(&b.keys, n);
+      if (a == DRT_OK) a = dalloc_n(&b.keys2, n);
+      if (a == DRT_OK) a = dalloc_n(&b.vals, n);
+      if (a == DRT_OK) a = dalloc_n(&b.vals2, n);
+      if (a == DRT_OK) a = dalloc_n(&b.hist, drt::radix_hist_entries(n));
+      if (a == DRT_OK) a = dalloc_n(&b.hist_tmp, drt::radix_hist_tmp_entries(n));
+      if (a != DRT_OK) {
+        unstage(sg, 6, st);
+        return a;
+      }
+      b.cap = n_edge;
+    }
+    sort = &s->esort;
+  }
   cudaError_t e = drt::launch_backward(s, op, tape, (const float*)sg[0].dev, (float*)sg[1].dev, (float*)sg[2].dev,
-                                       (float*)sg[3].dev, (float*)sg[4].dev, (float*)sg[5].dev, s->partials, st);
+                                       (float*)sg[3].dev, (float*)sg[4].dev, (float*)sg[5].dev, s->partials, sort,
+                                       st);
   r = unstage(sg, 6, st);
   if (e != cudaSuccess) return fail(DRT_ERR_CUDA, "backward launch: %s", cudaGetErrorString(e));
   return r;

@@ -262,36 +262,75 @@ __global__ void k_sort_hist(const uint32_t* keys, int n, int shift, uint32_t* hi
   hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-__global__ void k_sort_scan(uint32_t* hist, int m) {
+// Exclusive scan of the digit histograms (digit-major, tile-minor): tiles of
+// kScanTile entries, a scan of the tile totals, then the carry-in.
+__device__ uint32_t block_excl_scan_u32(uint32_t x, uint32_t* total) {
   __shared__ uint32_t warp_sums[kBlock / 32];
-  __shared__ uint32_t carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int base = 0; base < m; base += kBlock) {
-    int i = base + threadIdx.x;
-    uint32_t x = i < m ? hist[i] : 0u, v = x;
+  uint32_t v = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  if (lane == 31) warp_sums[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = lane < kBlock / 32 ? warp_sums[lane] : 0u;
+#pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += y;
+      uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
     }
-    if (lane == 31) warp_sums[wid] = v;
+    if (lane < kBlock / 32) warp_sums[lane] = w;
+  }
+  __syncthreads();
+  uint32_t before = (wid > 0 ? warp_sums[wid - 1] : 0u) + v - x;
+  *total = warp_sums[kBlock / 32 - 1];
+  __syncthreads();
+  return before;
+}
+
+__global__ void k_hist_scan_tiles(uint32_t* h, uint32_t* tile_sums, int m) {
+  int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    uint32_t x = base + i < m ? h[base + i] : 0u;
+    v[i] = acc;  // exclusive within the thread
+    acc += x;
+  }
+  uint32_t total;
+  uint32_t before = block_excl_scan_u32(acc, &total);
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i)
+    if (base + i < m) h[base + i] = before + v[i];
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void k_hist_scan_sums(uint32_t* sums, int nt) {
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0u;
+  __syncthreads();
+  for (int base = 0; base < nt; base += kBlock) {
+    int i = base + threadIdx.x;
+    uint32_t x = i < nt ? sums[i] : 0u;
+    uint32_t total;
+    uint32_t before = block_excl_scan_u32(x, &total);
+    if (i < nt) sums[i] = carry + before;  // exclusive
     __syncthreads();
-    if (wid == 0) {
-      uint32_t w = lane < kBlock / 32 ? warp_sums[lane] : 0u;
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += y;
-      }
-      if (lane < kBlock / 32) warp_sums[lane] = w;
-    }
-    __syncthreads();
-    uint32_t excl = carry + (wid > 0 ? warp_sums[wid - 1] : 0u) + v - x;
-    if (i < m) hist[i] = excl;
-    __syncthreads();
-    if (threadIdx.x == 0) carry += warp_sums[kBlock / 32 - 1];
+    if (threadIdx.x == 0) carry += total;
     __syncthreads();
   }
+}
+
+__global__ void k_hist_scan_add(uint32_t* h, const uint32_t* sums, int m) {
+  uint32_t add = sums[blockIdx.x];
+  if (add == 0u) return;
+  int base = blockIdx.x * kScanTile;
+  for (int i = threadIdx.x; i < kScanTile; i += kBlock)
+    if (base + i < m) h[base + i] += add;
 }
 
 __global__ void k_sort_scatter(const uint32_t* keys, const int32_t* vals, uint32_t* okeys, int32_t* ovals, int n,
@@ -426,6 +465,30 @@ __global__ void k_refit(SceneView s, const int32_t* vals, float4* nodes, float4*
 
 }  // namespace
 
+size_t radix_hist_entries(int n) { return 256 * (size_t)((n + kSortTile - 1) / kSortTile); }
+size_t radix_hist_tmp_entries(int n) { return (radix_hist_entries(n) + kScanTile - 1) / kScanTile + 1; }
+
+bool radix_sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys2, int32_t* vals2, uint32_t* hist,
+                      uint32_t* hist_tmp, int n, int bits, cudaStream_t st) {
+  uint32_t *ka = keys, *kb = keys2;
+  int32_t *va = vals, *vb = vals2;
+  int nb = (n + kSortTile - 1) / kSortTile;
+  int m = 256 * nb;
+  int nt = (m + kScanTile - 1) / kScanTile;
+  bool alt = false;
+  for (int shift = 0; shift < bits; shift += 8) {
+    DRT_PROF_LAUNCH("sort_hist", st, k_sort_hist<<<nb, kBlock, 0, st>>>(ka, n, shift, hist, nb));
+    DRT_PROF_LAUNCH("sort_scan_tiles", st, k_hist_scan_tiles<<<nt, kBlock, 0, st>>>(hist, hist_tmp, m));
+    DRT_PROF_LAUNCH("sort_scan_sums", st, k_hist_scan_sums<<<1, kBlock, 0, st>>>(hist_tmp, nt));
+    DRT_PROF_LAUNCH("sort_scan_add", st, k_hist_scan_add<<<nt, kBlock, 0, st>>>(hist, hist_tmp, m));
+    DRT_PROF_LAUNCH("sort_scatter", st, k_sort_scatter<<<nb, kBlock, 0, st>>>(ka, va, kb, vb, n, shift, hist, nb));
+    std::swap(ka, kb);
+    std::swap(va, vb);
+    alt = !alt;
+  }
+  return alt;
+}
+
 cudaError_t check_finite(drt_scene* s, cudaStream_t st) {
   int n = 3 * s->V;
   if (n > 0) DRT_PROF_LAUNCH("check_finite", st, k_check_finite<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(s->verts, n, s->ctx->err));
@@ -438,17 +501,9 @@ cudaError_t build_bvh(drt_scene* s, cudaStream_t st) {
   DRT_PROF_LAUNCH("bounds_init", st, k_bounds_init<<<1, 32, 0, st>>>(s->bounds));
   DRT_PROF_LAUNCH("bounds", st, k_bounds<<<std::min(1024, (s->V + kBlock - 1) / kBlock), kBlock, 0, st>>>(s->verts, s->V, s->bounds));
   DRT_PROF_LAUNCH("morton", st, k_morton<<<(T + kBlock - 1) / kBlock, kBlock, 0, st>>>(v, s->bounds, s->keys, s->vals));
-  uint32_t *ka = s->keys, *kb = s->keys2;
-  int32_t *va = s->vals, *vb = s->vals2;
-  int nb = (T + kSortTile - 1) / kSortTile;
-  for (int shift = 0; shift < 30; shift += 8) {
-    DRT_PROF_LAUNCH("sort_hist", st, k_sort_hist<<<nb, kBlock, 0, st>>>(ka, T, shift, s->hist, nb));
-    DRT_PROF_LAUNCH("sort_scan", st, k_sort_scan<<<1, kBlock, 0, st>>>(s->hist, 256 * nb));
-    DRT_PROF_LAUNCH("sort_scatter", st, k_sort_scatter<<<nb, kBlock, 0, st>>>(ka, va, kb, vb, T, shift, s->hist, nb));
-    std::swap(ka, kb);
-    std::swap(va, vb);
-  }
-  // 4 passes: sorted data is back in keys/vals
+  bool alt = radix_sort_pairs(s->keys, s->vals, s->keys2, s->vals2, s->hist, s->hist_tmp, T, 30, st);
+  uint32_t* ka = alt ? s->keys2 : s->keys;
+  int32_t* va = alt ? s->vals2 : s->vals;
   if (T > 1) {
     cudaMemsetAsync(s->flags, 0, sizeof(int32_t) * (T - 1), st);
     DRT_PROF_LAUNCH("karras", st, k_karras<<<(T - 1 + kBlock - 1) / kBlock, kBlock, 0, st>>>(ka, T, s->nodes, s->parent, s->leaf_parent));

@@ -16,6 +16,15 @@ struct drt_context {
   int num_sms = 0;
 };
 
+namespace drt {
+// Scratch for sorting primary edge samples by screen position (key, index).
+struct SortBuffers {
+  uint32_t *keys = nullptr, *keys2 = nullptr, *hist = nullptr, *hist_tmp = nullptr;
+  int32_t *vals = nullptr, *vals2 = nullptr;
+  int64_t cap = 0;  // samples the buffers hold
+};
+}  // namespace drt
+
 struct drt_scene {
   drt_context* ctx = nullptr;
   int V = 0, T = 0, L = 0, E = 0, W = 0, H = 0, cam_type = 0;
@@ -34,9 +43,11 @@ struct drt_scene {
   uint32_t *keys = nullptr, *keys2 = nullptr;
   int32_t *vals = nullptr, *vals2 = nullptr, *parent = nullptr, *leaf_parent = nullptr, *flags = nullptr;
   uint32_t* hist = nullptr;
+  uint32_t* hist_tmp = nullptr;
   int* bounds = nullptr;     // ordered-int AABB [6]
   float* partials = nullptr; // backward: per-block partial sums of global parameters
   size_t partials_cap = 0;
+  drt::SortBuffers esort;    // backward: primary edge samples sorted by screen position
   int sort_blocks = 0;
   drt::SceneView view() const;
 };
@@ -70,6 +81,12 @@ unsigned long long* counter_slot(int kernel);  // null unless counters are enabl
   } while (0)
 // build.cu
 cudaError_t build_scene_derived(drt_scene* s, cudaStream_t st);   // w2c, lights, BVH, edge CDFs
+// LSD radix sort of (key, value) pairs on the low `bits` bits; the result is
+// in (keys2, vals2) when the return value is true, else in (keys, vals).
+bool radix_sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys2, int32_t* vals2, uint32_t* hist,
+                      uint32_t* hist_tmp, int n, int bits, cudaStream_t st);
+size_t radix_hist_entries(int n);
+size_t radix_hist_tmp_entries(int n);
 cudaError_t build_bvh(drt_scene* s, cudaStream_t st);
 cudaError_t build_edge_cdfs(drt_scene* s, cudaStream_t st);
 cudaError_t check_finite(drt_scene* s, cudaStream_t st);
@@ -77,7 +94,7 @@ cudaError_t check_finite(drt_scene* s, cudaStream_t st);
 cudaError_t launch_render(const drt_scene* s, const Opts& op, float* image, drt_tape* tape, cudaStream_t st);
 cudaError_t launch_backward(const drt_scene* s, const Opts& op, const drt_tape* tape, const float* d_image,
                             float* d_verts, float* d_albedo, float* d_radiance, float* d_cam, float* d_cam_scale,
-                            float* scratch_global, cudaStream_t st);
+                            float* scratch_global, const SortBuffers* sort, cudaStream_t st);
 int64_t backward_partial_rows(const drt_scene* s, const Opts& op);
 cudaError_t launch_debug_closest(const drt_scene* s, int64_t n, const float* o, const float* d, int32_t* tri,
                                  float* tb, cudaStream_t st);

@@ -88,11 +88,16 @@ __device__ __forceinline__ void block_globals(float g[kGlobals], float* partials
   }
 }
 
+// One warp per column; each lane sums a fixed stride of rows, then a fixed
+// butterfly, so the result does not depend on scheduling.
 __global__ void k_reduce_globals(const float* partials, int rows, float* d_radiance, float* d_cam, float* d_scale) {
-  int i = threadIdx.x;
+  int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (i >= kGlobals) return;
   double acc = 0.0;
-  for (int r = 0; r < rows; ++r) acc += partials[(size_t)r * kGlobals + i];
+  for (int r = lane; r < rows; r += 32) acc += partials[(size_t)r * kGlobals + i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+  if (lane != 0) return;
   float v = (float)acc;
   if (i < 3) { if (d_radiance) d_radiance[i] += v; }
   else if (i < 15) { if (d_cam) d_cam[i - 3] += v; }
@@ -589,29 +594,72 @@ __global__ void __launch_bounds__(kBlock) k_backward_interior(SceneView s, Opts 
 // ---------------------------------------------------------------------------
 // Backward: primary edge samples (Eq. mc)
 // ---------------------------------------------------------------------------
+// Sample j: edge by the clipped-length CDF, uniform point on the clipped
+// segment (exact decision-path arithmetic).
+struct EdgeSample {
+  int e;
+  float ax, ay, bx, by, dx, dy, x, y;
+};
+__device__ __forceinline__ EdgeSample primary_sample(const SceneView& s, const Opts& op, int64_t j, double ptotal) {
+  uint4 r = rng4(op.key, (uint32_t)j, 0u, kEdgePrimary, 0u, kPassPrimaryEdge, 0u);
+  EdgeSample es;
+  es.e = cdf_pick(s.pcdf, s.E, dm(u01d(r.x, r.y), ptotal));
+  const float4* row = reinterpret_cast<const float4*>(s.pedge + 8 * es.e);
+  float4 r0 = row[0], r1 = row[1];
+  es.ax = r0.x; es.ay = r0.y; es.bx = r0.z; es.by = r0.w;
+  float t0 = r1.x, t1 = r1.y;
+  es.dx = fs(es.bx, es.ax);
+  es.dy = fs(es.by, es.ay);
+  float t = fa(t0, fm(u01f(r.z), fs(t1, t0)));
+  es.x = fa(es.ax, fm(t, es.dx));
+  es.y = fa(es.ay, fm(t, es.dy));
+  return es;
+}
+
+__device__ __forceinline__ uint32_t spread_bits16(uint32_t x) {
+  x &= 0xffffu;
+  x = (x | (x << 8)) & 0x00FF00FFu;
+  x = (x | (x << 4)) & 0x0F0F0F0Fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  return x;
+}
+
+// Screen-space Morton key of every primary edge sample, so the samples can be
+// evaluated in screen order (coherent rays, aggregated scatter).  Only the
+// evaluation order changes; each sample's arithmetic is the same.
+__global__ void k_primary_keys(SceneView s, Opts op, int64_t n_edge, uint32_t* keys, int32_t* vals) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_edge) return;
+  double ptotal = s.pcdf[s.E - 1];
+  uint32_t key = 0;
+  if (ptotal > 0.0) {
+    EdgeSample es = primary_sample(s, op, j, ptotal);
+    int px = min(max((int)floorf(es.x), 0), s.W - 1), py = min(max((int)floorf(es.y), 0), s.H - 1);
+    key = spread_bits16((uint32_t)px) | (spread_bits16((uint32_t)py) << 1);
+  }
+  keys[j] = key;
+  vals[j] = (int32_t)j;
+}
 __global__ void __launch_bounds__(kBlock) k_backward_primary(SceneView s, Opts op, const float* d_image, Grads gr,
-                                                             int64_t n_edge, int64_t per_thread) {
+                                                             int64_t n_edge, int64_t per_thread,
+                                                             const int32_t* order) {
   float g[kGlobals];
   for (int i = 0; i < kGlobals; ++i) g[i] = 0.f;
-  int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   double ptotal = s.pcdf[s.E - 1];
   float W = (float)s.W, H = (float)s.H;
   float eps = fm(op.eps_rel, fmaxf(W, H));
   for (int64_t it = 0; it < per_thread; ++it) {
-    int64_t j = it * nthreads + tid;
+    // consecutive threads take consecutive entries of the screen-ordered list
+    int64_t i = (int64_t)blockIdx.x * blockDim.x * per_thread + it * blockDim.x + threadIdx.x;
+    int64_t j = i < n_edge ? (order ? (int64_t)order[i] : i) : n_edge;
     bool active = j < n_edge && ptotal > 0.0 && j >= op.edge_begin && j < op.edge_end;
     float3 da3 = zero3(), db3 = zero3();
     int ia = 0, ib = 0;
     if (active) {
-      uint4 r = rng4(op.key, (uint32_t)j, 0u, kEdgePrimary, 0u, kPassPrimaryEdge, 0u);
-      int e = cdf_pick(s.pcdf, s.E, dm(u01d(r.x, r.y), ptotal));
-      const float4* row = reinterpret_cast<const float4*>(s.pedge + 8 * e);
-      float4 r0 = row[0], r1 = row[1];
-      float ax = r0.x, ay = r0.y, bx = r0.z, by = r0.w, t0 = r1.x, t1 = r1.y;
-      float dx = fs(bx, ax), dy = fs(by, ay);
-      float t = fa(t0, fm(u01f(r.z), fs(t1, t0)));
-      float x = fa(ax, fm(t, dx)), y = fa(ay, fm(t, dy));
+      EdgeSample es = primary_sample(s, op, j, ptotal);
+      int e = es.e;
+      float ax = es.ax, ay = es.ay, bx = es.bx, by = es.by, dx = es.dx, dy = es.dy, x = es.x, y = es.y;
       float nlen = fsq(fa(fm(dx, dx), fm(dy, dy)));
       float nx = fdv(-dy, nlen), ny = fdv(dx, nlen);
       float xu = fa(x, fm(eps, nx)), yu = fa(y, fm(eps, ny));
@@ -677,7 +725,7 @@ cudaError_t launch_render(const drt_scene* sc, const Opts& op, float* image, drt
 
 cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape* tape, const float* d_image,
                             float* d_verts, float* d_albedo, float* d_radiance, float* d_cam, float* d_cam_scale,
-                            float* partials, cudaStream_t st) {
+                            float* partials, const SortBuffers* sort, cudaStream_t st) {
   SceneView s = sc->view();
   int npix = s.W * s.H;
   int G = group_size(op.spp);
@@ -700,15 +748,26 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
   }
   Grads ge{d_verts, d_albedo, partials + (need_i ? blocks_i : 0) * kGlobals};
   if (blocks_e > 0) {
+    const int32_t* order = nullptr;
+    if (sort && sort->cap >= n_edge) {
+      int bits = 2;
+      while ((1 << (bits / 2)) < std::max(s.W, s.H)) bits += 2;
+      DRT_PROF_LAUNCH("primary_keys", st,
+                      k_primary_keys<<<(unsigned)((n_edge + kBlock - 1) / kBlock), kBlock, 0, st>>>(
+                          s, op, n_edge, sort->keys, sort->vals));
+      bool alt = radix_sort_pairs(sort->keys, sort->vals, sort->keys2, sort->vals2, sort->hist, sort->hist_tmp,
+                                  (int)n_edge, bits, st);
+      order = alt ? sort->vals2 : sort->vals;
+    }
     s.counters = counter_slot(kSlotBwdPrimary);
     ProfToken pt = prof_begin("backward_primary_edges", st);
-    k_backward_primary<<<(unsigned)blocks_e, kBlock, 0, st>>>(s, op, d_image, ge, n_edge, per_thread);
+    k_backward_primary<<<(unsigned)blocks_e, kBlock, 0, st>>>(s, op, d_image, ge, n_edge, per_thread, order);
     prof_end(pt, st);
   }
   int rows = (int)((need_i ? blocks_i : 0) + blocks_e);
   if (rows > 0) {
     ProfToken pt = prof_begin("reduce_globals", st);
-    k_reduce_globals<<<1, 32, 0, st>>>(partials, rows, d_radiance, d_cam, d_cam_scale);
+    k_reduce_globals<<<1, 32 * kGlobals, 0, st>>>(partials, rows, d_radiance, d_cam, d_cam_scale);
     prof_end(pt, st);
   }
   return cudaGetLastError();
