@@ -122,7 +122,7 @@ drt_status unstage(Staged* arr, int n, cudaStream_t st) {
 
 void free_scene_buffers(drt_scene* s) {
   void* bufs[] = {s->verts, s->albedo, s->radiance, s->cam, s->cam_scale, s->tris, s->light_tris, s->light_of_tri,
-                  s->w2c, s->light_cdf, s->light_area, s->nodes, s->soup, s->edges, s->pedge, s->plen, s->pcdf,
+                  s->w2c, s->light_cdf, s->light_area, s->light_box, s->nodes, s->soup, s->edges, s->pedge, s->plen, s->pcdf,
                   s->slen, s->scdf, s->scan_tmp, s->keys, s->keys2, s->vals, s->vals2, s->parent, s->leaf_parent,
                   s->flags, s->hist, s->hist_tmp, s->bounds, s->partials, s->esort.keys, s->esort.keys2,
                   s->esort.hist, s->esort.hist_tmp, s->esort.vals, s->esort.vals2};
@@ -167,7 +167,7 @@ drt::SceneView drt_scene::view() const {
   drt::SceneView v;
   v.verts = verts; v.tris = tris; v.albedo = albedo; v.radiance = radiance; v.cam = cam; v.cam_scale = cam_scale;
   v.w2c = w2c; v.light_tris = light_tris; v.light_of_tri = light_of_tri; v.light_cdf = light_cdf;
-  v.light_area = light_area; v.nodes = nodes; v.soup = soup; v.edges = edges; v.pedge = pedge; v.pcdf = pcdf;
+  v.light_area = light_area; v.light_box = light_box; v.nodes = nodes; v.soup = soup; v.edges = edges; v.pedge = pedge; v.pcdf = pcdf;
   v.scdf = scdf; v.err = ctx->err; v.counters = nullptr;
   v.V = V; v.T = T; v.L = L; v.E = E; v.W = W; v.H = H; v.cam_type = cam_type;
   v.root = T > 1 ? 0 : ~0;
@@ -256,7 +256,7 @@ drt_status drt_scene_upload(drt_context* ctx, const drt_scene_desc* d, void* str
   if (stt == DRT_OK) stt = dalloc_n(&s->ptr, (size_t)(n));
   ALLOC(verts, 3 * (size_t)s->V) ALLOC(albedo, 3 * (size_t)T) ALLOC(radiance, 3) ALLOC(cam, 16)
   ALLOC(cam_scale, 1) ALLOC(tris, 3 * (size_t)T) ALLOC(light_tris, std::max(1, s->L)) ALLOC(light_of_tri, T)
-  ALLOC(w2c, 12) ALLOC(light_cdf, std::max(1, s->L)) ALLOC(light_area, std::max(1, s->L))
+  ALLOC(w2c, 12) ALLOC(light_cdf, std::max(1, s->L)) ALLOC(light_area, std::max(1, s->L)) ALLOC(light_box, 8)
   ALLOC(nodes, 4 * (size_t)std::max(1, T - 1)) ALLOC(soup, 3 * (size_t)T) ALLOC(edges, std::max(1, E))
   ALLOC(pedge, 8 * (size_t)std::max(1, E)) ALLOC(plen, std::max(1, E)) ALLOC(pcdf, std::max(1, E))
   ALLOC(slen, std::max(1, E)) ALLOC(scdf, std::max(1, E)) ALLOC(scan_tmp, std::max(1, E / 1024 + 2))

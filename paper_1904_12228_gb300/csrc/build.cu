@@ -58,12 +58,17 @@ __global__ void k_world_to_cam(const float* M, float* out) {
 // Light-triangle areas (FP64 from FP32 edge vectors) and their inclusive
 // prefix in list order.
 __global__ void k_light_cdf(const float* verts, const int32_t* tris, const int32_t* light_tris, int L, double* area,
-                            double* cdf) {
+                            double* cdf, float* box) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double acc = 0.0;
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int j = 0; j < L; ++j) {
     int t = light_tris[j];
     const float *a = verts + 3 * tris[3 * t], *b = verts + 3 * tris[3 * t + 1], *c = verts + 3 * tris[3 * t + 2];
+    for (int i = 0; i < 3; ++i) {
+      lo[i] = fminf(lo[i], fminf(a[i], fminf(b[i], c[i])));
+      hi[i] = fmaxf(hi[i], fmaxf(a[i], fmaxf(b[i], c[i])));
+    }
     double e1x = fs(b[0], a[0]), e1y = fs(b[1], a[1]), e1z = fs(b[2], a[2]);
     double e2x = fs(c[0], a[0]), e2y = fs(c[1], a[1]), e2z = fs(c[2], a[2]);
     double cx = ds(dm(e1y, e2z), dm(e1z, e2y));
@@ -73,6 +78,14 @@ __global__ void k_light_cdf(const float* verts, const int32_t* tris, const int32
     area[j] = ar;
     acc = da(acc, ar);
     cdf[j] = acc;
+  }
+  // padded so the slab test stays conservative w.r.t. the watertight test
+  float ext = 0.f;
+  for (int i = 0; i < 3; ++i) ext = fmaxf(ext, fmaxf(hi[i] - lo[i], fmaxf(fabsf(lo[i]), fabsf(hi[i]))));
+  float pad = 1e-3f * ext + 1e-6f;
+  for (int i = 0; i < 3; ++i) {
+    box[i] = lo[i] - pad;
+    box[3 + i] = hi[i] + pad;
   }
 }
 
@@ -522,7 +535,7 @@ cudaError_t build_edge_cdfs(drt_scene* s, cudaStream_t st) {
 
 cudaError_t build_scene_derived(drt_scene* s, cudaStream_t st) {
   DRT_PROF_LAUNCH("world_to_cam", st, k_world_to_cam<<<1, 1, 0, st>>>(s->cam, s->w2c));
-  if (s->L > 0) DRT_PROF_LAUNCH("light_cdf", st, k_light_cdf<<<1, 1, 0, st>>>(s->verts, s->tris, s->light_tris, s->L, s->light_area, s->light_cdf));
+  if (s->L > 0) DRT_PROF_LAUNCH("light_cdf", st, k_light_cdf<<<1, 1, 0, st>>>(s->verts, s->tris, s->light_tris, s->L, s->light_area, s->light_cdf, s->light_box));
   cudaError_t e = build_bvh(s, st);
   if (e != cudaSuccess) return e;
   e = build_edge_cdfs(s, st);

@@ -89,6 +89,7 @@ struct SceneView {
   const int32_t* light_of_tri; // [T] index into light_tris or -1
   const double* light_cdf;   // [L] inclusive prefix of light areas
   const double* light_area;  // [L]
+  const float* light_box;    // [6] padded bounding box of all light triangles (lo.xyz, hi.xyz)
   const float4* nodes;       // [4*(T-1)] BVH2 nodes, 64 B each
   const float4* soup;        // [3*T] triangles in BVH leaf order, w = original id bits
   const int2* edges;         // [E] unique edges (v0 < v1), sorted

@@ -35,6 +35,7 @@ struct drt_scene {
   // derived
   float* w2c = nullptr;
   double *light_cdf = nullptr, *light_area = nullptr;
+  float* light_box = nullptr;
   float4 *nodes = nullptr, *soup = nullptr;
   int2* edges = nullptr;
   float* pedge = nullptr;
@@ -71,7 +72,8 @@ struct ProfToken {
 };
 ProfToken prof_begin(const char* name, cudaStream_t st);
 void prof_end(const ProfToken& t, cudaStream_t st);
-enum { kSlotRender = 0, kSlotBwdInterior = 1, kSlotBwdPrimary = 2, kSlotDebug = 3, kKernelSlots = 4 };
+enum { kSlotRender = 0, kSlotBwdInterior = 1, kSlotBwdPrimary = 2, kSlotDebug = 3, kSlotBwdSecondary = 4,
+       kKernelSlots = 5 };
 unsigned long long* counter_slot(int kernel);  // null unless counters are enabled
 #define DRT_PROF_LAUNCH(name, st, ...)                      \
   do {                                                      \

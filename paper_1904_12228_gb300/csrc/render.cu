@@ -72,7 +72,7 @@ __device__ __forceinline__ void scatter3(float* arr, int id, float3 v, bool acti
 
 // Block reduction of the global parameters into one row of partials; the
 // rows are summed in a fixed order by k_reduce_globals (deterministic).
-__device__ __forceinline__ void block_globals(float g[kGlobals], float* partials) {
+__device__ __forceinline__ void block_globals(float g[kGlobals], float* partials, bool add) {
   __shared__ float sm[kBlock / 32][kGlobals];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -84,7 +84,8 @@ __device__ __forceinline__ void block_globals(float g[kGlobals], float* partials
   if (threadIdx.x < kGlobals) {
     float acc = 0.f;
     for (int w = 0; w < kBlock / 32; ++w) acc += sm[w][threadIdx.x];
-    partials[(size_t)blockIdx.x * kGlobals + threadIdx.x] = acc;
+    float* dst = partials + (size_t)blockIdx.x * kGlobals + threadIdx.x;
+    *dst = add ? *dst + acc : acc;
   }
 }
 
@@ -348,7 +349,7 @@ __device__ __forceinline__ float3 project_adjoint(const SceneView& s, float3 v, 
 }
 
 // ---------------------------------------------------------------------------
-// Backward: interior term + secondary edges (depth-1 paths)
+// Backward: interior term (depth-1 paths) and secondary edge samples
 // ---------------------------------------------------------------------------
 struct Grads {
   float* verts;
@@ -356,6 +357,82 @@ struct Grads {
   float* partials;
 };
 
+// The camera-path vertex of interior sample (pix, sidx): the tape gives the
+// hit (and NEE visibility); without a tape the camera ray is traced again.
+struct CamHit {
+  float sx, sy, o[3], d[3];
+  int k;
+  bool vis;  // valid with a tape only
+  float b1, b2;
+};
+__device__ __forceinline__ void camera_hit(const SceneView& s, const Opts& op, const int32_t* tape_tri,
+                                           const float2* tape_bary, int64_t pix, int sidx, CamHit& c) {
+  jitter(op, (int)pix, sidx, s.W, &c.sx, &c.sy);
+  camera_ray(s, c.sx, c.sy, c.o, c.d);
+  c.k = -1;
+  c.vis = false;
+  c.b1 = c.b2 = 0.f;
+  if (tape_tri) {
+    int64_t ti = pix * op.spp + sidx;
+    int32_t tt = tape_tri[ti];
+    if (tt != -1) {
+      c.k = tt & 0x7fffffff;
+      c.vis = (tt >> 31) & 1;
+      float2 bb = tape_bary[ti];
+      c.b1 = bb.x;
+      c.b2 = bb.y;
+    }
+  } else {
+    Hit h = trace_closest(s, c.o, c.d, INFINITY, -1);
+    if (h.tri >= 0) {
+      c.k = h.tri;
+      c.b1 = h.b1;
+      c.b2 = h.b2;
+    }
+  }
+}
+
+// Reverse sweep through the ray/plane hit point p = o + tau d of triangle k
+// (and its flipped unit normal n): given d loss/dp and d loss/dn, add the
+// triangle-vertex adjoints and the camera adjoints.
+__device__ __forceinline__ void hit_point_adjoint(const SceneView& s, const CamHit& c, const Vertex& x, float3 dp,
+                                                  float3 dn, float3& dv0, float3& dv1, float3& dv2,
+                                                  float g[kGlobals]) {
+  float3 ov = f3(c.o), dvv = f3(c.d);
+  float3 e1 = x.v1 - x.v0, e2 = x.v2 - x.v0;
+  float3 Nk = cross(e1, e2);
+  float nkl = len(Nk);
+  float flip = x.side > 0.0f ? -1.f : 1.f;
+  float3 nhat = (1.f / nkl) * Nk;
+  float num = dot(x.v0 - ov, Nk), den = dot(dvv, Nk);
+  float tau = num / den;
+  float3 dNk = zero3();
+  float3 dnh = flip * dn;
+  dNk += (1.f / nkl) * (dnh - dot(dnh, nhat) * nhat);
+  float dtau = dot(dp, dvv);
+  float3 do_ = dp, dd_ = tau * dp;
+  float dnum = dtau / den, dden = -dtau * tau / den;
+  dv0 += dnum * Nk;
+  do_ -= dnum * Nk;
+  dNk += dnum * (x.v0 - ov);
+  dd_ += dden * Nk;
+  dNk += dden * dvv;
+  float3 de1k = cross(e2, dNk), de2k = cross(dNk, e1);
+  dv1 += de1k;
+  dv2 += de2k;
+  dv0 -= de1k + de2k;
+  camera_ray_adjoint(s, c.sx, c.sy, do_, dd_, g);
+}
+
+__device__ __forceinline__ float3 shading_normal(const Vertex& x) {
+  float3 Nk = cross(x.v1 - x.v0, x.v2 - x.v0);
+  float flip = x.side > 0.0f ? -1.f : 1.f;
+  return (flip / len(Nk)) * Nk;
+}
+
+// Interior term (second integral of Eq. redner_product_rule): emission and
+// the NEE estimator F * A_j / P(j) at the camera hit, differentiated in
+// reverse with the random numbers and the pick probability held fixed.
 __global__ void __launch_bounds__(kBlock) k_backward_interior(SceneView s, Opts op, const int32_t* tape_tri,
                                                               const float2* tape_bary, const float* d_image, Grads gr,
                                                               int G) {
@@ -365,81 +442,47 @@ __global__ void __launch_bounds__(kBlock) k_backward_interior(SceneView s, Opts 
   int64_t pix = gw * ppw + lane / G;
   int npix = s.W * s.H;
   bool pix_ok = pix < npix && pix >= op.pix_begin && pix < op.pix_end;
-  int64_t n = (int64_t)npix * op.spp;
   float g[kGlobals];
   for (int i = 0; i < kGlobals; ++i) g[i] = 0.f;
   float3 wpix = pix_ok ? ld3(d_image + 3 * pix) : zero3();
-  float inv_spp = 1.0f / (float)op.spp;
-  float3 a = inv_spp * wpix;  // adjoint of the sample radiance
+  float3 a = (1.0f / (float)op.spp) * wpix;  // adjoint of the sample radiance
   const float3 Le = ld3(s.radiance);
   int iters = (op.spp + G - 1) / G;
-  bool do_int = (op.terms & 1) != 0, do_sec = (op.terms & 4) != 0;
   for (int it = 0; it < iters; ++it) {
     int sidx = lane % G + it * G;
     bool active = pix_ok && sidx < op.spp;
-    int k = -1;
-    bool vis = false;
-    float b1 = 0.f, b2 = 0.f;
-    float sx = 0.f, sy = 0.f, o[3] = {0, 0, 0}, d[3] = {0, 0, 1};
-    if (active) {
-      jitter(op, (int)pix, sidx, s.W, &sx, &sy);
-      camera_ray(s, sx, sy, o, d);
-      int64_t ti = pix * op.spp + sidx;
-      if (tape_tri) {
-        int32_t tt = tape_tri[ti];
-        if (tt != -1) {
-          k = tt & 0x7fffffff;
-          vis = (tt >> 31) & 1;
-          float2 bb = tape_bary[ti];
-          b1 = bb.x; b2 = bb.y;
-        }
-      } else {
-        Hit h = trace_closest(s, o, d, INFINITY, -1);
-        if (h.tri >= 0) { k = h.tri; b1 = h.b1; b2 = h.b2; vis = true; /* refined below */ }
-      }
-    }
-    bool hit = active && k >= 0;
-    // per-sample adjoints to scatter
+    CamHit c;
+    c.k = -1;
+    if (active) camera_hit(s, op, tape_tri, tape_bary, pix, sidx, c);
+    bool hit = active && c.k >= 0;
     float3 dv0 = zero3(), dv1 = zero3(), dv2 = zero3(), dl0 = zero3(), dl1 = zero3(), dl2 = zero3();
     float3 dalb = zero3();
     int vid0 = 0, vid1 = 0, vid2 = 0, lid0 = 0, lid1 = 0, lid2 = 0;
     bool have_light = false;
-    // secondary edge scatter targets
-    float3 de0 = zero3(), de1 = zero3();
-    float3 dmv[2][3] = {{zero3(), zero3(), zero3()}, {zero3(), zero3(), zero3()}};
-    int eid0 = 0, eid1 = 0, mids[2][3] = {{0, 0, 0}, {0, 0, 0}};
-    bool have_edge = false, have_m[2] = {false, false};
     if (hit) {
       Vertex x;
-      load_vertex(s, k, b1, b2, d, x);
-      const int32_t* vid = s.tris + 3 * k;
+      load_vertex(s, c.k, c.b1, c.b2, c.d, x);
+      const int32_t* vid = s.tris + 3 * c.k;
       vid0 = vid[0]; vid1 = vid[1]; vid2 = vid[2];
-      float3 alb = ld3(s.albedo + 3 * k);
-      float3 ov = f3(o), dvv = f3(d);
-      float3 e1 = x.v1 - x.v0, e2 = x.v2 - x.v0;
-      float3 Nk = cross(e1, e2);
-      float nkl = len(Nk);
-      float flip = x.side > 0.0f ? -1.f : 1.f;
-      float3 nhat = (1.f / nkl) * Nk;
-      float3 n = flip * nhat;
-      float num = dot(x.v0 - ov, Nk), den = dot(dvv, Nk);
-      float tau = num / den;
-      float3 p = f3(x.p);
-      float3 dp = zero3(), dn = zero3();
+      float3 alb = ld3(s.albedo + 3 * c.k);
       if (op.primary_only) {
-        if (do_int) dalb = a;
+        dalb = a;
       } else {
-        if (do_int && s.light_of_tri[k] >= 0 && x.side < 0.0f) {
+        if (s.light_of_tri[c.k] >= 0 && x.side < 0.0f) {
           g[0] += a.x; g[1] += a.y; g[2] += a.z;
         }
-        if (s.L > 0 && do_int) {
+        float3 dp = zero3(), dn = zero3();
+        if (s.L > 0) {
           uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kLight, 0u, kPassInterior, 0u);
           LightSample ls;
           sample_light(s, r, ls);
+          bool vis = c.vis;
           if (!tape_tri) {
             float sd[3] = {fs(ls.y[0], x.p[0]), fs(ls.y[1], x.p[1]), fs(ls.y[2], x.p[2])};
             vis = !trace_any(s, x.p, sd, kShadowTmax, x.k, ls.lt);
           }
+          float3 n = shading_normal(x);
+          float3 p = f3(x.p);
           if (vis) {
             float3 W = f3(ls.y) - p;
             float r2 = dot(W, W);
@@ -481,114 +524,163 @@ __global__ void __launch_bounds__(kBlock) k_backward_interior(SceneView s, Opts 
             }
           }
         }
-        // secondary edge sample at p (area form, direct lighting part)
-        if (do_sec && s.E > 0 && s.L > 0) {
-          uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kEdgeSecondary, 0u, kPassInterior, 0u);
-          double stotal = s.scdf[s.E - 1];
-          int e = cdf_pick(s.scdf, s.E, dm(u01d(r.x, r.y), stotal));
-          double le = s.scdf[e] - (e > 0 ? s.scdf[e - 1] : 0.0);
-          float t = u01f(r.z);
-          int2 ev = s.edges[e];
-          float3 ve0 = ld3(s.verts + 3 * ev.x), ve1 = ld3(s.verts + 3 * ev.y);
-          float om[3], a0[3], a1[3];
-          om[0] = fs(fa(ve0.x, fm(t, fs(ve1.x, ve0.x))), x.p[0]);
-          om[1] = fs(fa(ve0.y, fm(t, fs(ve1.y, ve0.y))), x.p[1]);
-          om[2] = fs(fa(ve0.z, fm(t, fs(ve1.z, ve0.z))), x.p[2]);
-          a0[0] = fs(ve0.x, x.p[0]); a0[1] = fs(ve0.y, x.p[1]); a0[2] = fs(ve0.z, x.p[2]);
-          a1[0] = fs(ve1.x, x.p[0]); a1[1] = fs(ve1.y, x.p[1]); a1[2] = fs(ve1.z, x.p[2]);
-          float N32[3] = {fs(fm(a0[1], a1[2]), fm(a0[2], a1[1])), fs(fm(a0[2], a1[0]), fm(a0[0], a1[2])),
-                          fs(fm(a0[0], a1[1]), fm(a0[1], a1[0]))};
-          float nlen32 = fsq(dot3x(N32, N32));
-          if (le > 0.0 && nlen32 > 0.0f) {
-            float invPE = (float)(stotal / le);
-            float nh32[3] = {fdv(N32[0], nlen32), fdv(N32[1], nlen32), fdv(N32[2], nlen32)};
-            float wl = fsq(dot3x(om, om));
-            float sh = fm(op.eps_rel, wl);
-            float3 E = ve1 - ve0, w = f3(om), Nv = f3(N32), nh = f3(nh32);
-            float Nlen = len(Nv);
-            float3 a0v = ve0 - p, a1v = ve1 - p;
-            float3 Ne = cross(a0v, a1v);
-            for (int side = 0; side < 2; ++side) {
-              float sg = side == 0 ? 1.f : -1.f;
-              float dsd[3];
-              for (int i = 0; i < 3; ++i) dsd[i] = side == 0 ? fa(om[i], fm(sh, nh32[i])) : fs(om[i], fm(sh, nh32[i]));
-              Hit hm = trace_closest(s, x.p, dsd, INFINITY, k);
-              if (hm.tri < 0) continue;
-              int lj = s.light_of_tri[hm.tri];
-              if (lj < 0) continue;
-              Vertex mv;
-              load_vertex(s, hm.tri, hm.b1, hm.b2, dsd, mv);
-              float3 m = f3(mv.p);
-              float3 dmp = m - p;
-              float mr2 = dot(dmp, dmp);
-              float3 wh = (1.f / sqrtf(mr2)) * dmp;
-              float cpm = dot(n, wh);
-              if (!(cpm > 0.f)) continue;
-              float3 nmu = f3(mv.nu);
-              float3 nm = (1.f / len(nmu)) * nmu;
-              float cm = -dot(nm, wh);
-              if (!(cm > 0.f)) continue;
-              float Gm = cpm * cm / mr2;
-              float hs = kInvPi * Gm * (a.x * alb.x * Le.x + a.y * alb.y * Le.y + a.z * alb.z * Le.z);
-              float wn = dot(w, nm);
-              float tm = dot(dmp, nm) / wn;
-              float3 J = tm * (E - (dot(E, nm) / wn) * w);
-              float cr = len(cross(nm, nh));
-              if (!(cr > 0.f)) continue;
-              float c = sg * hs * (len(J) / (Nlen * cr)) * invPE;
-              float3 mp = m - p;
-              float3 gv0 = cross(a1v, mp), gv1 = cross(mp, a0v);
-              de0 += c * gv0;
-              de1 += c * gv1;
-              dp -= c * (Ne + gv0 + gv1);
-              // m is attached to the light triangle it lies on (weights summing to one)
-              float bw1 = hm.b1, bw2 = hm.b2, bw0 = 1.f - bw1 - bw2;
-              const int32_t* mid = s.tris + 3 * hm.tri;
-              mids[side][0] = mid[0]; mids[side][1] = mid[1]; mids[side][2] = mid[2];
-              dmv[side][0] = (c * bw0) * Ne;
-              dmv[side][1] = (c * bw1) * Ne;
-              dmv[side][2] = (c * bw2) * Ne;
-              have_m[side] = true;
-            }
-            eid0 = ev.x; eid1 = ev.y;
-            have_edge = true;
-          }
-        }
-      }
-      // back-propagate dp and dn to the hit triangle and the camera
-      {
-        float3 dNk = zero3();
-        float3 dnh = flip * dn;
-        dNk += (1.f / nkl) * (dnh - dot(dnh, nhat) * nhat);
-        float dtau = dot(dp, dvv);
-        float3 do_ = dp, dd_ = tau * dp;
-        float dnum = dtau / den, dden = -dtau * tau / den;
-        dv0 += dnum * Nk;
-        do_ -= dnum * Nk;
-        dNk += dnum * (x.v0 - ov);
-        dd_ += dden * Nk;
-        dNk += dden * dvv;
-        float3 de1k = cross(e2, dNk), de2k = cross(dNk, e1);
-        dv1 += de1k;
-        dv2 += de2k;
-        dv0 -= de1k + de2k;
-        camera_ray_adjoint(s, sx, sy, do_, dd_, g);
+        hit_point_adjoint(s, c, x, dp, dn, dv0, dv1, dv2, g);
       }
     }
-    // scatter (all lanes participate)
     scatter3(gr.verts, vid0, dv0, hit);
     scatter3(gr.verts, vid1, dv1, hit);
     scatter3(gr.verts, vid2, dv2, hit);
-    scatter3(gr.albedo, k, dalb, hit);
+    scatter3(gr.albedo, c.k, dalb, hit);
     scatter3(gr.verts, lid0, dl0, have_light);
     scatter3(gr.verts, lid1, dl1, have_light);
     scatter3(gr.verts, lid2, dl2, have_light);
+  }
+  block_globals(g, gr.partials, false);
+}
+
+// Could a ray from o along d reach a light triangle?  Conservative slab test
+// against the lights' padded bounding box.
+__device__ __forceinline__ bool may_reach_light(const SceneView& s, const float o[3], const float d[3]) {
+  float t0 = 0.f, t1 = INFINITY;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float lo = s.light_box[i], hi = s.light_box[3 + i];
+    if (d[i] == 0.f) {
+      if (o[i] < lo || o[i] > hi) return false;
+      continue;
+    }
+    float inv = 1.f / d[i];
+    float ta = (lo - o[i]) * inv, tb = (hi - o[i]) * inv;
+    t0 = fmaxf(t0, fminf(ta, tb));
+    t1 = fminf(t1, fmaxf(ta, tb));
+  }
+  return t0 <= t1 * 1.0001f;
+}
+
+// Secondary edge sample at the camera hit (Sec. 5.2.2): edge by the 3D length
+// CDF, point t, side rays omega +- eps|omega| n_h.  With one scattering vertex
+// only radiance arriving from a light matters (area form, reading of the
+// measure), so a side ray that cannot reach a light, or that leaves below the
+// shading horizon by more than the side offset, contributes exactly nothing
+// and is not traced.
+__global__ void __launch_bounds__(kBlock) k_backward_secondary(SceneView s, Opts op, const int32_t* tape_tri,
+                                                               const float2* tape_bary, const float* d_image, Grads gr,
+                                                               int G, int rows_written) {
+  int lane = threadIdx.x & 31;
+  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int ppw = 32 / G;
+  int64_t pix = gw * ppw + lane / G;
+  int npix = s.W * s.H;
+  bool pix_ok = pix < npix && pix >= op.pix_begin && pix < op.pix_end;
+  float g[kGlobals];
+  for (int i = 0; i < kGlobals; ++i) g[i] = 0.f;
+  float3 wpix = pix_ok ? ld3(d_image + 3 * pix) : zero3();
+  float3 a = (1.0f / (float)op.spp) * wpix;
+  const float3 Le = ld3(s.radiance);
+  int iters = (op.spp + G - 1) / G;
+  double stotal = s.scdf[s.E - 1];
+  for (int it = 0; it < iters; ++it) {
+    int sidx = lane % G + it * G;
+    bool active = pix_ok && sidx < op.spp && !op.primary_only;
+    CamHit c;
+    c.k = -1;
+    if (active) camera_hit(s, op, tape_tri, tape_bary, pix, sidx, c);
+    float3 dv0 = zero3(), dv1 = zero3(), dv2 = zero3(), de0 = zero3(), de1 = zero3();
+    float3 dmv[2][3] = {{zero3(), zero3(), zero3()}, {zero3(), zero3(), zero3()}};
+    int vid0 = 0, vid1 = 0, vid2 = 0, eid0 = 0, eid1 = 0, mids[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    bool have_edge = false, have_m[2] = {false, false};
+    if (active && c.k >= 0) {
+      Vertex x;
+      load_vertex(s, c.k, c.b1, c.b2, c.d, x);
+      uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kEdgeSecondary, 0u, kPassInterior, 0u);
+      int e = cdf_pick(s.scdf, s.E, dm(u01d(r.x, r.y), stotal));
+      double le = s.scdf[e] - (e > 0 ? s.scdf[e - 1] : 0.0);
+      float t = u01f(r.z);
+      int2 ev = s.edges[e];
+      float3 ve0 = ld3(s.verts + 3 * ev.x), ve1 = ld3(s.verts + 3 * ev.y);
+      float om[3], a0[3], a1[3];
+      om[0] = fs(fa(ve0.x, fm(t, fs(ve1.x, ve0.x))), x.p[0]);
+      om[1] = fs(fa(ve0.y, fm(t, fs(ve1.y, ve0.y))), x.p[1]);
+      om[2] = fs(fa(ve0.z, fm(t, fs(ve1.z, ve0.z))), x.p[2]);
+      a0[0] = fs(ve0.x, x.p[0]); a0[1] = fs(ve0.y, x.p[1]); a0[2] = fs(ve0.z, x.p[2]);
+      a1[0] = fs(ve1.x, x.p[0]); a1[1] = fs(ve1.y, x.p[1]); a1[2] = fs(ve1.z, x.p[2]);
+      float N32[3] = {fs(fm(a0[1], a1[2]), fm(a0[2], a1[1])), fs(fm(a0[2], a1[0]), fm(a0[0], a1[2])),
+                      fs(fm(a0[0], a1[1]), fm(a0[1], a1[0]))};
+      float nlen32 = fsq(dot3x(N32, N32));
+      float3 n = shading_normal(x);
+      if (le > 0.0 && nlen32 > 0.0f) {
+        float invPE = (float)(stotal / le);
+        float nh32[3] = {fdv(N32[0], nlen32), fdv(N32[1], nlen32), fdv(N32[2], nlen32)};
+        float wl = fsq(dot3x(om, om));
+        float sh = fm(op.eps_rel, wl);
+        float3 E = ve1 - ve0, w = f3(om), nh = f3(nh32);
+        float Nlen = len(f3(N32));
+        float3 p = f3(x.p);
+        float3 a0v = ve0 - p, a1v = ve1 - p;
+        float3 Ne = cross(a0v, a1v);
+        float3 alb = ld3(s.albedo + 3 * c.k);
+        float3 dp = zero3();
+        for (int side = 0; side < 2; ++side) {
+          float sg = side == 0 ? 1.f : -1.f;
+          float dsd[3];
+          for (int i = 0; i < 3; ++i) dsd[i] = side == 0 ? fa(om[i], fm(sh, nh32[i])) : fs(om[i], fm(sh, nh32[i]));
+          if (dot(n, f3(dsd)) < -1e-5f * wl) continue;  // below the horizon: cos_p < 0 at the hit
+          if (!may_reach_light(s, x.p, dsd)) continue;  // cannot hit a light
+          Hit hm = trace_closest(s, x.p, dsd, INFINITY, c.k);
+          if (hm.tri < 0 || s.light_of_tri[hm.tri] < 0) continue;
+          Vertex mv;
+          load_vertex(s, hm.tri, hm.b1, hm.b2, dsd, mv);
+          float3 m = f3(mv.p);
+          float3 dmp = m - p;
+          float mr2 = dot(dmp, dmp);
+          float3 wh = (1.f / sqrtf(mr2)) * dmp;
+          float cpm = dot(n, wh);
+          if (!(cpm > 0.f)) continue;
+          float3 nmu = f3(mv.nu);
+          float3 nm = (1.f / len(nmu)) * nmu;
+          float cm = -dot(nm, wh);
+          if (!(cm > 0.f)) continue;
+          float Gm = cpm * cm / mr2;
+          float hs = kInvPi * Gm * (a.x * alb.x * Le.x + a.y * alb.y * Le.y + a.z * alb.z * Le.z);
+          float wn = dot(w, nm);
+          float tm = dot(dmp, nm) / wn;
+          float3 J = tm * (E - (dot(E, nm) / wn) * w);
+          float cr = len(cross(nm, nh));
+          if (!(cr > 0.f)) continue;
+          float cc = sg * hs * (len(J) / (Nlen * cr)) * invPE;
+          // alpha = (m-p).(v0-p)x(v1-p): d/dv0 = v1' x m', d/dv1 = m' x v0',
+          // d/dm = v0' x v1', d/dp = -(sum of the three)
+          float3 gv0 = cross(a1v, dmp), gv1 = cross(dmp, a0v);
+          de0 += cc * gv0;
+          de1 += cc * gv1;
+          dp -= cc * (Ne + gv0 + gv1);
+          float bw1 = hm.b1, bw2 = hm.b2, bw0 = 1.f - bw1 - bw2;  // m attached to its light triangle
+          const int32_t* mid = s.tris + 3 * hm.tri;
+          mids[side][0] = mid[0]; mids[side][1] = mid[1]; mids[side][2] = mid[2];
+          dmv[side][0] = (cc * bw0) * Ne;
+          dmv[side][1] = (cc * bw1) * Ne;
+          dmv[side][2] = (cc * bw2) * Ne;
+          have_m[side] = true;
+        }
+        if (have_m[0] || have_m[1]) {
+          eid0 = ev.x;
+          eid1 = ev.y;
+          have_edge = true;
+          const int32_t* vid = s.tris + 3 * c.k;
+          vid0 = vid[0]; vid1 = vid[1]; vid2 = vid[2];
+          hit_point_adjoint(s, c, x, dp, zero3(), dv0, dv1, dv2, g);
+        }
+      }
+    }
     scatter3(gr.verts, eid0, de0, have_edge);
     scatter3(gr.verts, eid1, de1, have_edge);
+    scatter3(gr.verts, vid0, dv0, have_edge);
+    scatter3(gr.verts, vid1, dv1, have_edge);
+    scatter3(gr.verts, vid2, dv2, have_edge);
     for (int sd = 0; sd < 2; ++sd)
       for (int q = 0; q < 3; ++q) scatter3(gr.verts, mids[sd][q], dmv[sd][q], have_m[sd]);
   }
-  block_globals(g, gr.partials);
+  block_globals(g, gr.partials, rows_written != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -687,7 +779,7 @@ __global__ void __launch_bounds__(kBlock) k_backward_primary(SceneView s, Opts o
     scatter3(gr.verts, ia, da3, active);
     scatter3(gr.verts, ib, db3, active);
   }
-  block_globals(g, gr.partials);
+  block_globals(g, gr.partials, false);
 }
 
 __global__ void k_debug_closest(SceneView s, int64_t n, const float* o, const float* d, int32_t* tri, float* tb) {
@@ -739,12 +831,22 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
   }
   Grads gr{d_verts, d_albedo, partials};
   bool need_i = (op.terms & 5) != 0;
-  if (need_i) {
+  const int32_t* tt = tape ? tape->tri : nullptr;
+  const float2* tb = tape ? tape->bary : nullptr;
+  if (op.terms & 1) {
     s.counters = counter_slot(kSlotBwdInterior);
     ProfToken pt = prof_begin("backward_interior", st);
-    k_backward_interior<<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tape ? tape->tri : nullptr,
-                                                               tape ? tape->bary : nullptr, d_image, gr, G);
+    k_backward_interior<<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tt, tb, d_image, gr, G);
     prof_end(pt, st);
+  }
+  if ((op.terms & 4) && s.E > 0 && s.L > 0) {
+    s.counters = counter_slot(kSlotBwdSecondary);
+    ProfToken pt = prof_begin("backward_secondary_edges", st);
+    k_backward_secondary<<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tt, tb, d_image, gr, G, op.terms & 1);
+    prof_end(pt, st);
+  } else if (need_i && !(op.terms & 1)) {
+    // secondary requested but nothing to sample: rows still need zeros
+    cudaMemsetAsync(partials, 0, sizeof(float) * kGlobals * blocks_i, st);
   }
   Grads ge{d_verts, d_albedo, partials + (need_i ? blocks_i : 0) * kGlobals};
   if (blocks_e > 0) {

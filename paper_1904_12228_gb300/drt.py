@@ -188,11 +188,11 @@ class Context:
     def counters(self, enable: bool):
         _check(self.lib.drt_counters_enable(self.handle, int(bool(enable))))
 
-    COUNTER_SLOTS = ("render", "backward_interior", "backward_primary_edges", "debug")
+    COUNTER_SLOTS = ("render", "backward_interior", "backward_primary_edges", "debug", "backward_secondary_edges")
 
     def counters_read(self):
         """{slot: dict(closest_rays, shadow_rays, nodes, tris)} (synchronises, resets)."""
-        a = np.zeros((4, 4), np.int64)
+        a = np.zeros((len(self.COUNTER_SLOTS), 4), np.int64)
         _check(self.lib.drt_counters_read(self.handle, a.ctypes.data))
         return {nm: dict(closest_rays=int(a[i, 0]), shadow_rays=int(a[i, 1]), nodes=int(a[i, 2]), tris=int(a[i, 3]))
                 for i, nm in enumerate(self.COUNTER_SLOTS)}
