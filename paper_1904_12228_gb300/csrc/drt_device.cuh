@@ -224,7 +224,7 @@ __device__ __forceinline__ int cdf_pick(const double* cdf, int n, double target)
 
 // Watertight ray/triangle test (Woop, Benthin, Wald 2013), FP32.
 struct Shear {
-  int kx, ky, kz;
+  unsigned char kx, ky, kz;
   float Sx, Sy, Sz;
 };
 __device__ __forceinline__ Shear make_shear(const float d[3]) {
@@ -347,14 +347,13 @@ struct Hit {
 };
 
 struct RayPre {
-  float o[3], d[3], inv[3];
+  float o[3], inv[3];
   Shear sh;
 };
 __device__ __forceinline__ void ray_pre(RayPre& r, const float o[3], const float d[3]) {
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     r.o[i] = o[i];
-    r.d[i] = d[i];
     float di = fabsf(d[i]) < 1e-20f ? copysignf(1e-20f, d[i]) : d[i];
     r.inv[i] = 1.0f / di;
   }
@@ -503,6 +502,142 @@ __device__ __forceinline__ bool trace_any(const SceneView& s, const float o[3], 
   }
   count_trace(s, kCntAny, n_nodes, n_tris);
   return found;
+}
+
+// Two rays through one traversal: a node is visited when either active ray
+// (with its own current closest t) enters one of its boxes, and every leaf
+// triangle is tested against each active ray with that ray's own limits, so
+// each result equals the ray's single traversal.  Used for the two side paths
+// of an edge sample, which are a tiny offset apart and visit the same nodes.
+__device__ __forceinline__ void trace_closest2(const SceneView& s, const float o0[3], const float d0[3],
+                                               const float o1[3], const float d1[3], bool act0, bool act1, int ex0,
+                                               int ex1, Hit& h0, Hit& h1) {
+  RayPre r0, r1;
+  ray_pre(r0, o0, d0);
+  ray_pre(r1, o1, d1);
+  h0.tri = -1; h0.t = INFINITY; h0.b1 = h0.b2 = 0.f;
+  h1.tri = -1; h1.t = INFINITY; h1.b1 = h1.b2 = 0.f;
+  if (!act0 && !act1) return;
+  int stack[kStackSize];
+  int sp = 0;
+  int node = s.root;
+  int budget = 2 * s.T + 8;
+  int n_nodes = 0, n_tris = 0;
+  while (true) {
+    if (--budget < 0) {
+      raise_flag(s.err, DRT_DEV_TRAVERSAL_CAP, s.T);
+      break;
+    }
+    if (node >= 0) {
+      ++n_nodes;
+      const float4* n4 = s.nodes + 4 * node;
+      float4 a = __ldg(n4), b = __ldg(n4 + 1), c = __ldg(n4 + 2);
+      int4 ch = __ldg(reinterpret_cast<const int4*>(n4 + 3));
+      float tl0, tr0, tl1, tr1;
+      bool hl0, hr0, hl1, hr1;
+      slab2(r0, a, b, c, h0.t, &tl0, &hl0, &tr0, &hr0);
+      slab2(r1, a, b, c, h1.t, &tl1, &hl1, &tr1, &hr1);
+      bool hl = (act0 && hl0) || (act1 && hl1), hr = (act0 && hr0) || (act1 && hr1);
+      float tl = fminf(act0 && hl0 ? tl0 : INFINITY, act1 && hl1 ? tl1 : INFINITY);
+      float tr = fminf(act0 && hr0 ? tr0 : INFINITY, act1 && hr1 ? tr1 : INFINITY);
+      if (hl && hr) {
+        int nearc = tl <= tr ? ch.x : ch.y, farc = tl <= tr ? ch.y : ch.x;
+        if (sp < kStackSize) stack[sp++] = farc; else raise_flag(s.err, DRT_DEV_STACK_OVERFLOW, node);
+        node = nearc;
+        continue;
+      } else if (hl) {
+        node = ch.x;
+        continue;
+      } else if (hr) {
+        node = ch.y;
+        continue;
+      }
+    } else {
+      int pos = ~node;
+      const float4* t4 = s.soup + 3 * pos;
+      float4 p0 = __ldg(t4), p1 = __ldg(t4 + 1), p2 = __ldg(t4 + 2);
+      int id = __float_as_int(p0.w);
+      ++n_tris;
+      float3 v0 = make_float3(p0.x, p0.y, p0.z), v1 = make_float3(p1.x, p1.y, p1.z), v2 = make_float3(p2.x, p2.y, p2.z);
+      float t, b1, b2;
+      if (act0 && id != ex0) {
+        float lim = (h0.tri >= 0 && id < h0.tri) ? __uint_as_float(__float_as_uint(h0.t) + 1u) : h0.t;
+        if (watertight(r0.sh, r0.o, v0, v1, v2, lim, &t, &b1, &b2)) { h0.tri = id; h0.t = t; h0.b1 = b1; h0.b2 = b2; }
+      }
+      if (act1 && id != ex1) {
+        float lim = (h1.tri >= 0 && id < h1.tri) ? __uint_as_float(__float_as_uint(h1.t) + 1u) : h1.t;
+        if (watertight(r1.sh, r1.o, v0, v1, v2, lim, &t, &b1, &b2)) { h1.tri = id; h1.t = t; h1.b1 = b1; h1.b2 = b2; }
+      }
+    }
+    if (sp == 0) break;
+    node = stack[--sp];
+  }
+  count_trace(s, kCntClosest, n_nodes, n_tris);
+}
+
+// Two any-hit queries through one traversal; occ0/occ1 report a hit with t in
+// (0, tmax) that is not one of the ray's two skipped triangles.
+__device__ __forceinline__ void trace_any2(const SceneView& s, const float o0[3], const float d0[3], int a0x, int a0y,
+                                           const float o1[3], const float d1[3], int a1x, int a1y, bool act0,
+                                           bool act1, float tmax, bool& occ0, bool& occ1) {
+  occ0 = occ1 = false;
+  if (!act0 && !act1) return;
+  RayPre r0, r1;
+  ray_pre(r0, o0, d0);
+  ray_pre(r1, o1, d1);
+  bool live0 = act0, live1 = act1;
+  int stack[kStackSize];
+  int sp = 0;
+  int node = s.root;
+  int budget = 2 * s.T + 8;
+  int n_nodes = 0, n_tris = 0;
+  while (live0 || live1) {
+    if (--budget < 0) {
+      raise_flag(s.err, DRT_DEV_TRAVERSAL_CAP, s.T);
+      break;
+    }
+    if (node >= 0) {
+      ++n_nodes;
+      const float4* n4 = s.nodes + 4 * node;
+      float4 a = __ldg(n4), b = __ldg(n4 + 1), c = __ldg(n4 + 2);
+      int4 ch = __ldg(reinterpret_cast<const int4*>(n4 + 3));
+      float tl, tr;
+      bool hl0 = false, hr0 = false, hl1 = false, hr1 = false;
+      if (live0) slab2(r0, a, b, c, tmax, &tl, &hl0, &tr, &hr0);
+      if (live1) slab2(r1, a, b, c, tmax, &tl, &hl1, &tr, &hr1);
+      bool hl = hl0 || hl1, hr = hr0 || hr1;
+      if (hl && hr) {
+        if (sp < kStackSize) stack[sp++] = ch.y; else raise_flag(s.err, DRT_DEV_STACK_OVERFLOW, node);
+        node = ch.x;
+        continue;
+      } else if (hl) {
+        node = ch.x;
+        continue;
+      } else if (hr) {
+        node = ch.y;
+        continue;
+      }
+    } else {
+      int pos = ~node;
+      const float4* t4 = s.soup + 3 * pos;
+      float4 p0 = __ldg(t4), p1 = __ldg(t4 + 1), p2 = __ldg(t4 + 2);
+      int id = __float_as_int(p0.w);
+      ++n_tris;
+      float3 v0 = make_float3(p0.x, p0.y, p0.z), v1 = make_float3(p1.x, p1.y, p1.z), v2 = make_float3(p2.x, p2.y, p2.z);
+      float t, b1, b2;
+      if (live0 && id != a0x && id != a0y && watertight(r0.sh, r0.o, v0, v1, v2, tmax, &t, &b1, &b2)) {
+        occ0 = true;
+        live0 = false;
+      }
+      if (live1 && id != a1x && id != a1y && watertight(r1.sh, r1.o, v0, v1, v2, tmax, &t, &b1, &b2)) {
+        occ1 = true;
+        live1 = false;
+      }
+    }
+    if (sp == 0) break;
+    node = stack[--sp];
+  }
+  count_trace(s, kCntAny, n_nodes, n_tris);
 }
 
 __device__ __forceinline__ float3 ld3(const float* p) { return make_float3(p[0], p[1], p[2]); }

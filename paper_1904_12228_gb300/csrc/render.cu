@@ -230,6 +230,69 @@ __device__ float3 path_value(const SceneView& s, const Opts& op, float o_in[3], 
   return L;
 }
 
+// Radiance along the two side paths of an edge sample (same counters, so the
+// same light and BSDF random numbers on both sides), traced pairwise.
+__device__ void path_value2(const SceneView& s, const Opts& op, float o[2][3], float d[2][3], uint32_t c0,
+                            uint32_t c1, uint32_t pass, float3 L[2]) {
+  int md = op.primary_only ? 1 : op.max_depth;
+  const float3 Le = ld3(s.radiance);
+  bool alive[2] = {true, true};
+  int exclude[2] = {-1, -1};
+  float3 beta[2] = {make_float3(1.f, 1.f, 1.f), make_float3(1.f, 1.f, 1.f)};
+  L[0] = L[1] = zero3();
+  for (int b = 0; b < md; ++b) {
+    Hit h[2];
+    trace_closest2(s, o[0], d[0], o[1], d[1], alive[0], alive[1], exclude[0], exclude[1], h[0], h[1]);
+    Vertex x[2];
+    float3 alb[2];
+    for (int q = 0; q < 2; ++q) {
+      if (!alive[q]) continue;
+      if (h[q].tri < 0) { alive[q] = false; continue; }
+      load_vertex(s, h[q].tri, h[q].b1, h[q].b2, d[q], x[q]);
+      alb[q] = ld3(s.albedo + 3 * x[q].k);
+      if (op.primary_only) {
+        L[q] += beta[q] * alb[q];
+        alive[q] = false;
+        continue;
+      }
+      if (b == 0 && s.light_of_tri[x[q].k] >= 0 && x[q].side < 0.0f) L[q] += beta[q] * Le;
+    }
+    if (!alive[0] && !alive[1]) break;
+    float n32[2][3];
+    for (int q = 0; q < 2; ++q)
+      if (alive[q]) shading_normal32(x[q], n32[q]);
+    if (s.L > 0) {
+      uint4 r = rng4(op.key, c0, c1, kLight, (uint32_t)b, pass, 0u);
+      LightSample ls;
+      sample_light(s, r, ls);
+      float sd[2][3];
+      for (int q = 0; q < 2; ++q)
+        if (alive[q])
+          for (int i = 0; i < 3; ++i) sd[q][i] = fs(ls.y[i], x[q].p[i]);
+      bool occ[2];
+      trace_any2(s, x[0].p, sd[0], x[0].k, ls.lt, x[1].p, sd[1], x[1].k, ls.lt, alive[0], alive[1], kShadowTmax,
+                 occ[0], occ[1]);
+      for (int q = 0; q < 2; ++q)
+        if (alive[q] && !occ[q]) {
+          float g = nee_geometry(s, f3(x[q].p), f3(n32[q]), ls);
+          L[q] += (kInvPi * g) * (beta[q] * alb[q] * Le);
+        }
+    }
+    if (b + 1 >= md) break;
+    uint4 r = rng4(op.key, c0, c1, kBsdf, (uint32_t)b, pass, 0u);
+    for (int q = 0; q < 2; ++q) {
+      if (!alive[q]) continue;
+      float nd[3];
+      cosine_dir(n32[q], u01f(r.x), u01f(r.y), nd);
+      if (!(dot(f3(n32[q]), f3(nd)) > 0.f)) { alive[q] = false; continue; }
+      beta[q] = beta[q] * alb[q];
+      for (int i = 0; i < 3; ++i) { o[q][i] = x[q].p[i]; d[q][i] = nd[i]; }
+      exclude[q] = x[q].k;
+    }
+    if (!alive[0] && !alive[1]) break;
+  }
+}
+
 __device__ __forceinline__ void jitter(const Opts& op, int pix, int sidx, int W, float* sx, float* sy) {
   uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kCamera, 0u, kPassInterior, 0u);
   *sx = fa((float)(pix % W), u01f(r.x));
@@ -733,7 +796,7 @@ __global__ void k_primary_keys(SceneView s, Opts op, int64_t n_edge, uint32_t* k
   keys[j] = key;
   vals[j] = (int32_t)j;
 }
-__global__ void __launch_bounds__(kBlock) k_backward_primary(SceneView s, Opts op, const float* d_image, Grads gr,
+__global__ void __launch_bounds__(kBlock, 2) k_backward_primary(SceneView s, Opts op, const float* d_image, Grads gr,
                                                              int64_t n_edge, int64_t per_thread,
                                                              const int32_t* order) {
   float g[kGlobals];
@@ -758,12 +821,12 @@ __global__ void __launch_bounds__(kBlock) k_backward_primary(SceneView s, Opts o
       float xl = fs(x, fm(eps, nx)), yl = fs(y, fm(eps, ny));
       int px = min(max((int)floorf(x), 0), s.W - 1), py = min(max((int)floorf(y), 0), s.H - 1);
       float3 w = ld3(d_image + 3 * ((int64_t)py * s.W + px));
-      float o[3], d[3];
-      camera_ray(s, xu, yu, o, d);
-      float3 Lu = path_value(s, op, o, d, -1, true, 0, (uint32_t)j, 0u, kPassPrimaryEdge, nullptr, nullptr, 0, 0);
-      camera_ray(s, xl, yl, o, d);
-      float3 Ll = path_value(s, op, o, d, -1, true, 0, (uint32_t)j, 0u, kPassPrimaryEdge, nullptr, nullptr, 0, 0);
-      float diff = dot(w, Lu - Ll);
+      float o2[2][3], d2[2][3];
+      camera_ray(s, xu, yu, o2[0], d2[0]);
+      camera_ray(s, xl, yl, o2[1], d2[1]);
+      float3 L2[2];
+      path_value2(s, op, o2, d2, (uint32_t)j, 0u, kPassPrimaryEdge, L2);
+      float diff = dot(w, L2[0] - L2[1]);
       if (diff != 0.f) {
         float gl = sqrtf((ax - bx) * (ax - bx) + (ay - by) * (ay - by));
         float c = (float)((double)diff * ptotal / ((double)gl * (double)n_edge));
