@@ -124,7 +124,7 @@ void free_scene_buffers(drt_scene* s) {
   void* bufs[] = {s->verts, s->albedo, s->radiance, s->cam, s->cam_scale, s->tris, s->light_tris, s->light_of_tri,
                   s->w2c, s->light_cdf, s->light_area, s->light_box, s->nodes, s->soup, s->edges, s->pedge, s->plen, s->pcdf,
                   s->slen, s->scdf, s->scan_tmp, s->keys, s->keys2, s->vals, s->vals2, s->parent, s->leaf_parent,
-                  s->flags, s->hist, s->hist_tmp, s->bounds, s->partials, s->esort.keys, s->esort.keys2,
+                  s->flags, s->child_orig, s->hist, s->hist_tmp, s->bounds, s->partials, s->esort.keys, s->esort.keys2,
                   s->esort.hist, s->esort.hist_tmp, s->esort.vals, s->esort.vals2};
   for (void* b : bufs) dfree(b);
 }
@@ -170,7 +170,7 @@ drt::SceneView drt_scene::view() const {
   v.light_area = light_area; v.light_box = light_box; v.nodes = nodes; v.soup = soup; v.edges = edges; v.pedge = pedge; v.pcdf = pcdf;
   v.scdf = scdf; v.err = ctx->err; v.counters = nullptr;
   v.V = V; v.T = T; v.L = L; v.E = E; v.W = W; v.H = H; v.cam_type = cam_type;
-  v.root = T > 1 ? 0 : ~0;
+  v.root = T > drt::kLeafMax ? 0 : drt::leaf_enc(0, T);
   return v;
 }
 
@@ -261,7 +261,7 @@ drt_status drt_scene_upload(drt_context* ctx, const drt_scene_desc* d, void* str
   ALLOC(pedge, 8 * (size_t)std::max(1, E)) ALLOC(plen, std::max(1, E)) ALLOC(pcdf, std::max(1, E))
   ALLOC(slen, std::max(1, E)) ALLOC(scdf, std::max(1, E)) ALLOC(scan_tmp, std::max(1, E / 1024 + 2))
   ALLOC(keys, T) ALLOC(keys2, T) ALLOC(vals, T) ALLOC(vals2, T) ALLOC(parent, std::max(1, T))
-  ALLOC(leaf_parent, T) ALLOC(flags, std::max(1, T)) ALLOC(hist, drt::radix_hist_entries(T))
+  ALLOC(leaf_parent, T) ALLOC(flags, std::max(1, T)) ALLOC(child_orig, std::max(1, T)) ALLOC(hist, drt::radix_hist_entries(T))
   ALLOC(hist_tmp, drt::radix_hist_tmp_entries(T)) ALLOC(bounds, 8)
 #undef ALLOC
   if (stt != DRT_OK) {

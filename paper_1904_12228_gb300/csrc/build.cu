@@ -393,7 +393,8 @@ __device__ __forceinline__ int delta(const uint32_t* k, int n, int i, int j) {
 
 // Karras (HPG 2012): internal node i covers a key range; its split is the
 // highest differing bit; children are leaves when the range has one key.
-__global__ void k_karras(const uint32_t* keys, int n, float4* nodes, int32_t* parent, int32_t* leaf_parent) {
+__global__ void k_karras(const uint32_t* keys, int n, float4* nodes, int2* child_orig, int32_t* parent,
+                         int32_t* leaf_parent) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n - 1) return;
   int d = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
@@ -415,15 +416,20 @@ __global__ void k_karras(const uint32_t* keys, int n, float4* nodes, int32_t* pa
   int lo = min(i, j), hi = max(i, j);
   int left = (lo == gamma) ? ~gamma : gamma;
   int right = (hi == gamma + 1) ? ~(gamma + 1) : gamma + 1;
-  reinterpret_cast<int4*>(nodes)[4 * i + 3] = make_int4(left, right, 0, 0);
+  // traversal sees a subtree of at most kLeafMax triangles as one leaf range
+  int lcount = gamma - lo + 1, rcount = hi - gamma;
+  int left_enc = lcount <= kLeafMax ? leaf_enc(lo, lcount) : left;
+  int right_enc = rcount <= kLeafMax ? leaf_enc(gamma + 1, rcount) : right;
+  reinterpret_cast<int4*>(nodes)[4 * i + 3] = make_int4(left_enc, right_enc, 0, 0);
+  child_orig[i] = make_int2(left, right);
   if (left < 0) leaf_parent[~left] = i; else parent[left] = i;
   if (right < 0) leaf_parent[~right] = i; else parent[right] = i;
   if (i == 0) parent[0] = -1;
 }
 
 // Triangle soup in leaf order and bottom-up refit with arrival counters.
-__global__ void k_refit(SceneView s, const int32_t* vals, float4* nodes, float4* soup, const int32_t* parent,
-                        const int32_t* leaf_parent, int32_t* flags) {
+__global__ void k_refit(SceneView s, const int32_t* vals, float4* nodes, float4* soup, const int2* child_orig,
+                        const int32_t* parent, const int32_t* leaf_parent, int32_t* flags) {
   int pos = blockIdx.x * blockDim.x + threadIdx.x;
   if (pos >= s.T) return;
   int t = vals[pos];
@@ -454,8 +460,7 @@ __global__ void k_refit(SceneView s, const int32_t* vals, float4* nodes, float4*
       return;
     }
     float4* n4 = nodes + 4 * node;
-    int4 ch = reinterpret_cast<int4*>(n4)[3];
-    bool is_left = ch.x == child;
+    bool is_left = child_orig[node].x == child;
     // write this child's box into its slot of the parent
     float* f = reinterpret_cast<float*>(n4);
     if (is_left) {
@@ -519,9 +524,9 @@ cudaError_t build_bvh(drt_scene* s, cudaStream_t st) {
   int32_t* va = alt ? s->vals2 : s->vals;
   if (T > 1) {
     cudaMemsetAsync(s->flags, 0, sizeof(int32_t) * (T - 1), st);
-    DRT_PROF_LAUNCH("karras", st, k_karras<<<(T - 1 + kBlock - 1) / kBlock, kBlock, 0, st>>>(ka, T, s->nodes, s->parent, s->leaf_parent));
+    DRT_PROF_LAUNCH("karras", st, k_karras<<<(T - 1 + kBlock - 1) / kBlock, kBlock, 0, st>>>(ka, T, s->nodes, s->child_orig, s->parent, s->leaf_parent));
   }
-  DRT_PROF_LAUNCH("refit", st, k_refit<<<(T + kBlock - 1) / kBlock, kBlock, 0, st>>>(v, va, s->nodes, s->soup, s->parent, s->leaf_parent, s->flags));
+  DRT_PROF_LAUNCH("refit", st, k_refit<<<(T + kBlock - 1) / kBlock, kBlock, 0, st>>>(v, va, s->nodes, s->soup, s->child_orig, s->parent, s->leaf_parent, s->flags));
   return cudaGetLastError();
 }
 

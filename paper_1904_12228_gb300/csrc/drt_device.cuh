@@ -44,6 +44,10 @@ constexpr float kNearZ = 1e-4f;        // camera depth below which a vertex is b
 constexpr float kShadowTmax = 0.9999f; // shadow rays stop short of the light point
 constexpr float kInvPi = 0.318309886f;
 constexpr int kStackSize = 64;
+// BVH leaves hold up to kLeafMax consecutive triangles of the leaf-order soup;
+// a leaf child is encoded as ~(first | (count-1) << 28).
+constexpr int kLeafMax = 1;  // measured: 4 costs more triangle tests than it saves in node visits on LBVH leaves
+__host__ __device__ __forceinline__ int leaf_enc(int first, int count) { return ~(first | ((count - 1) << 28)); }
 // device error-flag codes (mirrors the public enum in drt.h)
 
 
@@ -338,7 +342,7 @@ __device__ __forceinline__ void cosine_dir(const float n[3], float r1, float r2,
 // ---------------------------------------------------------------------------
 // Node n: f4[4n+0] = (loL.xyz, hiL.x), f4[4n+1] = (hiL.yz, loR.xy),
 //         f4[4n+2] = (loR.z, hiR.xyz), f4[4n+3] = (childL, childR, -, -) as int.
-// child >= 0: internal node; child < 0: leaf at sorted position ~child.
+// child >= 0: internal node; child < 0: leaf range (see leaf_enc).
 // Boxes are enlarged when built so the slab test below never rejects a ray
 // that the watertight test would accept.
 struct Hit {
@@ -425,18 +429,20 @@ __device__ __forceinline__ Hit trace_closest(const SceneView& s, const float o[3
         continue;
       }
     } else {
-      int pos = ~node;
-      const float4* t4 = s.soup + 3 * pos;
-      float4 p0 = __ldg(t4), p1 = __ldg(t4 + 1), p2 = __ldg(t4 + 2);
-      int id = __float_as_int(p0.w);
-      ++n_tris;
-      if (id != exclude) {
-        float t, b1, b2;
-        // t must beat the best so far; a lower id also wins a tie on t
-        float lim = (h.tri >= 0 && id < h.tri) ? __uint_as_float(__float_as_uint(h.t) + 1u) : h.t;
-        if (watertight(r.sh, r.o, make_float3(p0.x, p0.y, p0.z), make_float3(p1.x, p1.y, p1.z),
-                       make_float3(p2.x, p2.y, p2.z), lim, &t, &b1, &b2)) {
-          h.tri = id; h.t = t; h.b1 = b1; h.b2 = b2;
+      int enc = ~node, first = enc & 0x0fffffff, count = (enc >> 28) + 1;
+      for (int q = 0; q < count; ++q) {
+        const float4* t4 = s.soup + 3 * (first + q);
+        float4 p0 = __ldg(t4), p1 = __ldg(t4 + 1), p2 = __ldg(t4 + 2);
+        int id = __float_as_int(p0.w);
+        ++n_tris;
+        if (id != exclude) {
+          float t, b1, b2;
+          // t must beat the best so far; a lower id also wins a tie on t
+          float lim = (h.tri >= 0 && id < h.tri) ? __uint_as_float(__float_as_uint(h.t) + 1u) : h.t;
+          if (watertight(r.sh, r.o, make_float3(p0.x, p0.y, p0.z), make_float3(p1.x, p1.y, p1.z),
+                         make_float3(p2.x, p2.y, p2.z), lim, &t, &b1, &b2)) {
+            h.tri = id; h.t = t; h.b1 = b1; h.b2 = b2;
+          }
         }
       }
     }
@@ -483,19 +489,20 @@ __device__ __forceinline__ bool trace_any(const SceneView& s, const float o[3], 
         continue;
       }
     } else {
-      int pos = ~node;
-      const float4* t4 = s.soup + 3 * pos;
-      float4 p0 = __ldg(t4), p1 = __ldg(t4 + 1), p2 = __ldg(t4 + 2);
-      int id = __float_as_int(p0.w);
-      ++n_tris;
-      if (id != ex0 && id != ex1) {
-        float t, b1, b2;
-        if (watertight(r.sh, r.o, make_float3(p0.x, p0.y, p0.z), make_float3(p1.x, p1.y, p1.z),
-                       make_float3(p2.x, p2.y, p2.z), tmax, &t, &b1, &b2)) {
-          found = true;
-          break;
+      int enc = ~node, first = enc & 0x0fffffff, count = (enc >> 28) + 1;
+      for (int q = 0; q < count && !found; ++q) {
+        const float4* t4 = s.soup + 3 * (first + q);
+        float4 p0 = __ldg(t4), p1 = __ldg(t4 + 1), p2 = __ldg(t4 + 2);
+        int id = __float_as_int(p0.w);
+        ++n_tris;
+        if (id != ex0 && id != ex1) {
+          float t, b1, b2;
+          if (watertight(r.sh, r.o, make_float3(p0.x, p0.y, p0.z), make_float3(p1.x, p1.y, p1.z),
+                         make_float3(p2.x, p2.y, p2.z), tmax, &t, &b1, &b2))
+            found = true;
         }
       }
+      if (found) break;
     }
     if (sp == 0) break;
     node = stack[--sp];
@@ -553,8 +560,9 @@ __device__ __forceinline__ void trace_closest2(const SceneView& s, const float o
         continue;
       }
     } else {
-      int pos = ~node;
-      const float4* t4 = s.soup + 3 * pos;
+      int enc = ~node, first = enc & 0x0fffffff, count = (enc >> 28) + 1;
+      for (int q = 0; q < count; ++q) {
+      const float4* t4 = s.soup + 3 * (first + q);
       float4 p0 = __ldg(t4), p1 = __ldg(t4 + 1), p2 = __ldg(t4 + 2);
       int id = __float_as_int(p0.w);
       ++n_tris;
@@ -567,6 +575,7 @@ __device__ __forceinline__ void trace_closest2(const SceneView& s, const float o
       if (act1 && id != ex1) {
         float lim = (h1.tri >= 0 && id < h1.tri) ? __uint_as_float(__float_as_uint(h1.t) + 1u) : h1.t;
         if (watertight(r1.sh, r1.o, v0, v1, v2, lim, &t, &b1, &b2)) { h1.tri = id; h1.t = t; h1.b1 = b1; h1.b2 = b2; }
+      }
       }
     }
     if (sp == 0) break;
@@ -618,20 +627,23 @@ __device__ __forceinline__ void trace_any2(const SceneView& s, const float o0[3]
         continue;
       }
     } else {
-      int pos = ~node;
-      const float4* t4 = s.soup + 3 * pos;
-      float4 p0 = __ldg(t4), p1 = __ldg(t4 + 1), p2 = __ldg(t4 + 2);
-      int id = __float_as_int(p0.w);
-      ++n_tris;
-      float3 v0 = make_float3(p0.x, p0.y, p0.z), v1 = make_float3(p1.x, p1.y, p1.z), v2 = make_float3(p2.x, p2.y, p2.z);
-      float t, b1, b2;
-      if (live0 && id != a0x && id != a0y && watertight(r0.sh, r0.o, v0, v1, v2, tmax, &t, &b1, &b2)) {
-        occ0 = true;
-        live0 = false;
-      }
-      if (live1 && id != a1x && id != a1y && watertight(r1.sh, r1.o, v0, v1, v2, tmax, &t, &b1, &b2)) {
-        occ1 = true;
-        live1 = false;
+      int enc = ~node, first = enc & 0x0fffffff, count = (enc >> 28) + 1;
+      for (int q = 0; q < count && (live0 || live1); ++q) {
+        const float4* t4 = s.soup + 3 * (first + q);
+        float4 p0 = __ldg(t4), p1 = __ldg(t4 + 1), p2 = __ldg(t4 + 2);
+        int id = __float_as_int(p0.w);
+        ++n_tris;
+        float3 v0 = make_float3(p0.x, p0.y, p0.z), v1 = make_float3(p1.x, p1.y, p1.z),
+               v2 = make_float3(p2.x, p2.y, p2.z);
+        float t, b1, b2;
+        if (live0 && id != a0x && id != a0y && watertight(r0.sh, r0.o, v0, v1, v2, tmax, &t, &b1, &b2)) {
+          occ0 = true;
+          live0 = false;
+        }
+        if (live1 && id != a1x && id != a1y && watertight(r1.sh, r1.o, v0, v1, v2, tmax, &t, &b1, &b2)) {
+          occ1 = true;
+          live1 = false;
+        }
       }
     }
     if (sp == 0) break;

@@ -43,6 +43,7 @@ struct drt_scene {
   // LBVH build scratch
   uint32_t *keys = nullptr, *keys2 = nullptr;
   int32_t *vals = nullptr, *vals2 = nullptr, *parent = nullptr, *leaf_parent = nullptr, *flags = nullptr;
+  int2* child_orig = nullptr;  // Karras children before leaf collapsing (refit)
   uint32_t* hist = nullptr;
   uint32_t* hist_tmp = nullptr;
   int* bounds = nullptr;     // ordered-int AABB [6]

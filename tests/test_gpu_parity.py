@@ -112,6 +112,30 @@ def test_traversal_matches_brute_force(drt, ctx):
     assert np.array_equal(tb.cpu().numpy()[hit], want_tb[hit])
 
 
+@pytest.mark.parametrize("n_tris", [2, 3, 4, 5, 9, 300])
+def test_traversal_small_and_random_soups(drt, ctx, n_tris):
+    """Tiny meshes (the root itself may be a leaf range) and random triangle
+    soups with overlaps: traversal returns exactly the brute-force hit."""
+    rng = np.random.default_rng(n_tris)
+    verts = rng.uniform(-1, 1, size=(3 * n_tris, 3))
+    tris = np.arange(3 * n_tris).reshape(n_tris, 3)
+    scene = sg.Scene(verts=verts, tris=tris, albedo=np.full((n_tris, 3), 0.5), light_tris=np.zeros(0, np.int32),
+                     radiance=[0, 0, 0], cam_to_world=np.eye(4), cam_scale=1.0, cam_type=1, width=4, height=4)
+    s = drt.Scene.from_arrays(ctx, scene)
+    n = 5000
+    o = rng.uniform(-2, 2, size=(n, 3)).astype(np.float32)
+    d = (rng.uniform(-1, 1, size=(n, 3)) - 0.5 * o).astype(np.float32)
+    tri = torch.zeros(n, dtype=torch.int32, device="cuda")
+    tb = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    s.closest(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda(), tri, tb)
+    torch.cuda.synchronize()
+    want_tri, want_tb = oracle.closest(scene, o, d, n_threads=NT)
+    assert (tri.cpu().numpy() == want_tri).all()
+    hit = want_tri >= 0
+    assert hit.any()
+    assert np.array_equal(tb.cpu().numpy()[hit], want_tb[hit])
+
+
 @pytest.mark.parametrize("seed", [1235, 7])
 def test_single_triangle_image(drt, ctx, seed):
     scene = sg.single_triangle(seed)
