@@ -392,8 +392,8 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
   if (!ctx || !s || !d_image || !grads) return fail(DRT_ERR_INVALID_ARG, "NULL argument");
   drt::Opts op;
   DRT_TRY(make_opts(opts, &op));
-  if (!op.primary_only && op.max_depth > 1)
-    return fail(DRT_ERR_INVALID_ARG, "backward supports max_depth == 1 in this build");
+  if (!op.primary_only && op.max_depth > 1 && !tape)
+    return fail(DRT_ERR_INVALID_ARG, "backward with max_depth > 1 needs the tape of the forward pass");
   if (tape) {
     const drt_render_opts& t = tape->opts;
     if (tape->scene != s || tape->generation != s->generation)

@@ -458,6 +458,38 @@ __device__ __forceinline__ void camera_hit(const SceneView& s, const Opts& op, c
 // Reverse sweep through the ray/plane hit point p = o + tau d of triangle k
 // (and its flipped unit normal n): given d loss/dp and d loss/dn, add the
 // triangle-vertex adjoints and the camera adjoints.
+// Ray/plane hit p = o + tau d with the triangle of x moving: given d loss/dp
+// and d loss/dn (flipped unit normal), add the vertex adjoints and return
+// the adjoints of the ray origin and direction.
+__device__ __forceinline__ void plane_hit_adjoint(const float o[3], const float d[3], const Vertex& x, float3 dp,
+                                                  float3 dn, float3& dv0, float3& dv1, float3& dv2, float3& do_,
+                                                  float3& dd_) {
+  float3 ov = f3(o), dvv = f3(d);
+  float3 e1 = x.v1 - x.v0, e2 = x.v2 - x.v0;
+  float3 Nk = cross(e1, e2);
+  float nkl = len(Nk);
+  float flip = x.side > 0.0f ? -1.f : 1.f;
+  float3 nhat = (1.f / nkl) * Nk;
+  float num = dot(x.v0 - ov, Nk), den = dot(dvv, Nk);
+  float tau = num / den;
+  float3 dNk = zero3();
+  float3 dnh = flip * dn;
+  dNk += (1.f / nkl) * (dnh - dot(dnh, nhat) * nhat);
+  float dtau = dot(dp, dvv);
+  do_ = dp;
+  dd_ = tau * dp;
+  float dnum = dtau / den, dden = -dtau * tau / den;
+  dv0 += dnum * Nk;
+  do_ -= dnum * Nk;
+  dNk += dnum * (x.v0 - ov);
+  dd_ += dden * Nk;
+  dNk += dden * dvv;
+  float3 de1k = cross(e2, dNk), de2k = cross(dNk, e1);
+  dv1 += de1k;
+  dv2 += de2k;
+  dv0 -= de1k + de2k;
+}
+
 __device__ __forceinline__ void hit_point_adjoint(const SceneView& s, const CamHit& c, const Vertex& x, float3 dp,
                                                   float3 dn, float3& dv0, float3& dv1, float3& dv2,
                                                   float g[kGlobals]) {
@@ -747,6 +779,297 @@ __global__ void __launch_bounds__(kBlock) k_backward_secondary(SceneView s, Opts
 }
 
 // ---------------------------------------------------------------------------
+// Backward for paths with several scattering vertices (path tracing)
+// ---------------------------------------------------------------------------
+constexpr int kMaxDepth = 8;
+
+// NEE at vertex x with throughput-weighted adjoint ab = a * beta: returns the
+// NEE radiance value (per colour) and adds its reverse-mode adjoints.
+__device__ __forceinline__ float3 nee_adjoint(const SceneView& s, const Opts& op, uint32_t c0, uint32_t c1, int b,
+                                              const Vertex& x, float3 n, float3 alb, float3 ab, float3 Le,
+                                              float g[kGlobals], float3& dalb, float3& dp, float3& dn, float3 dl[3],
+                                              int lid[3], bool& have_light) {
+  uint4 r = rng4(op.key, c0, c1, kLight, (uint32_t)b, kPassInterior, 0u);
+  LightSample ls;
+  sample_light(s, r, ls);
+  float3 p = f3(x.p);
+  float3 W = f3(ls.y) - p;
+  float r2 = dot(W, W);
+  float rr = sqrtf(r2);
+  float3 w = (1.f / rr) * W;
+  float cp = dot(n, w);
+  float3 el1 = ls.l1 - ls.l0, el2 = ls.l2 - ls.l0;
+  float3 Nl = cross(el1, el2);
+  float nll = len(Nl);
+  float3 nl = (1.f / nll) * Nl;
+  float cy = -dot(nl, w);
+  if (!(cp > 0.f && cy > 0.f)) return zero3();
+  double total = s.light_cdf[s.L - 1];
+  float invP = (float)(total / s.light_area[ls.j]);
+  float Aj = 0.5f * nll;
+  float Gf = cp * cy / r2;
+  float common = kInvPi * Gf * Aj * invP;
+  g[0] += ab.x * alb.x * common;
+  g[1] += ab.y * alb.y * common;
+  g[2] += ab.z * alb.z * common;
+  dalb += make_float3(ab.x * Le.x * common, ab.y * Le.y * common, ab.z * Le.z * common);
+  float Q = (ab.x * alb.x * Le.x + ab.y * alb.y * Le.y + ab.z * alb.z * Le.z) * kInvPi * invP;
+  float dG = Q * Aj, dA = Q * Gf;
+  float dcp = dG * cy / r2, dcy = dG * cp / r2, dr2 = -dG * Gf / r2;
+  dn += dcp * w;
+  float3 dw = dcp * n - dcy * nl;
+  float3 dnl = -dcy * w;
+  float3 dW = (1.f / rr) * (dw - dot(dw, w) * w) + (2.f * dr2) * W;
+  dp -= dW;
+  float3 dNl = (1.f / nll) * (dnl - dot(dnl, nl) * nl) + (0.5f * dA) * nl;
+  float3 de1l = cross(el2, dNl), de2l = cross(dNl, el1);
+  dl[0] = ls.w[0] * dW - de1l - de2l;
+  dl[1] = ls.w[1] * dW + de1l;
+  dl[2] = ls.w[2] * dW + de2l;
+  const int32_t* li = s.tris + 3 * ls.lt;
+  lid[0] = li[0]; lid[1] = li[1]; lid[2] = li[2];
+  have_light = true;
+  return common * (alb * Le);
+}
+
+// Secondary edge sample at vertex b (Sec. 5.2.2) with both parts: the area
+// form for radiance arriving from lights, and for b+1 < max_depth the
+// solid-angle form for reflected radiance (a traced sub-path from the side
+// hit with the remaining depth, the same counters on both sides).
+struct SecOut {
+  float3 de0, de1, dm[2][3];
+  int eid0, eid1, mid[2][3];
+  bool have_edge, have_m[2];
+};
+__device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Opts& op, uint32_t c0, uint32_t c1,
+                                                    int b, int md, const Vertex& x, float3 n, float3 alb, float3 ab,
+                                                    float3 Le, float3& dp, SecOut& so) {
+  so.de0 = so.de1 = zero3();
+  so.eid0 = so.eid1 = 0;
+  so.have_edge = false;
+  for (int q = 0; q < 2; ++q) {
+    so.have_m[q] = false;
+    for (int i = 0; i < 3; ++i) { so.dm[q][i] = zero3(); so.mid[q][i] = 0; }
+  }
+  double stotal = s.scdf[s.E - 1];
+  uint4 r = rng4(op.key, c0, c1, kEdgeSecondary, (uint32_t)b, kPassInterior, 0u);
+  int e = cdf_pick(s.scdf, s.E, dm(u01d(r.x, r.y), stotal));
+  double le = s.scdf[e] - (e > 0 ? s.scdf[e - 1] : 0.0);
+  float t = u01f(r.z);
+  int2 ev = s.edges[e];
+  float3 ve0 = ld3(s.verts + 3 * ev.x), ve1 = ld3(s.verts + 3 * ev.y);
+  float om[3], a0[3], a1[3];
+  om[0] = fs(fa(ve0.x, fm(t, fs(ve1.x, ve0.x))), x.p[0]);
+  om[1] = fs(fa(ve0.y, fm(t, fs(ve1.y, ve0.y))), x.p[1]);
+  om[2] = fs(fa(ve0.z, fm(t, fs(ve1.z, ve0.z))), x.p[2]);
+  a0[0] = fs(ve0.x, x.p[0]); a0[1] = fs(ve0.y, x.p[1]); a0[2] = fs(ve0.z, x.p[2]);
+  a1[0] = fs(ve1.x, x.p[0]); a1[1] = fs(ve1.y, x.p[1]); a1[2] = fs(ve1.z, x.p[2]);
+  float N32[3] = {fs(fm(a0[1], a1[2]), fm(a0[2], a1[1])), fs(fm(a0[2], a1[0]), fm(a0[0], a1[2])),
+                  fs(fm(a0[0], a1[1]), fm(a0[1], a1[0]))};
+  float nlen32 = fsq(dot3x(N32, N32));
+  if (!(le > 0.0 && nlen32 > 0.0f)) return;
+  float invPE = (float)(stotal / le);
+  float nh32[3] = {fdv(N32[0], nlen32), fdv(N32[1], nlen32), fdv(N32[2], nlen32)};
+  float wl = fsq(dot3x(om, om));
+  float sh = fm(op.eps_rel, wl);
+  float3 E = ve1 - ve0, w = f3(om), nh = f3(nh32);
+  float Nlen = len(f3(N32));
+  float3 p = f3(x.p);
+  float3 a0v = ve0 - p, a1v = ve1 - p;
+  float3 Ne = cross(a0v, a1v);
+  float wl2 = dot(w, w);
+  float3 what = (1.f / sqrtf(wl2)) * w;
+  bool last = b + 1 >= md;
+  for (int side = 0; side < 2; ++side) {
+    float sg = side == 0 ? 1.f : -1.f;
+    float dsd[3];
+    for (int i = 0; i < 3; ++i) dsd[i] = side == 0 ? fa(om[i], fm(sh, nh32[i])) : fs(om[i], fm(sh, nh32[i]));
+    if (dot(n, f3(dsd)) < -1e-5f * wl) continue;
+    if (last && !may_reach_light(s, x.p, dsd)) continue;
+    Hit hm = trace_closest(s, x.p, dsd, INFINITY, x.k);
+    if (hm.tri < 0) continue;
+    Vertex mv;
+    load_vertex(s, hm.tri, hm.b1, hm.b2, dsd, mv);
+    float3 m = f3(mv.p);
+    float3 dmp = m - p;
+    float mr2 = dot(dmp, dmp);
+    float3 wh = (1.f / sqrtf(mr2)) * dmp;
+    float cpm = dot(n, wh);
+    if (!(cpm > 0.f)) continue;
+    if (s.light_of_tri[hm.tri] >= 0) {
+      float3 nmu = f3(mv.nu);
+      float3 nm = (1.f / len(nmu)) * nmu;
+      float cm = -dot(nm, wh);
+      float wn = dot(w, nm);
+      float cr = len(cross(nm, nh));
+      if (cm > 0.f && cr > 0.f) {
+        float Gm = cpm * cm / mr2;
+        float hs = kInvPi * Gm * (ab.x * alb.x * Le.x + ab.y * alb.y * Le.y + ab.z * alb.z * Le.z);
+        float tm = dot(dmp, nm) / wn;
+        float3 J = tm * (E - (dot(E, nm) / wn) * w);
+        float cc = sg * hs * (len(J) / (Nlen * cr)) * invPE;
+        float3 gv0 = cross(a1v, dmp), gv1 = cross(dmp, a0v);
+        so.de0 += cc * gv0;
+        so.de1 += cc * gv1;
+        dp -= cc * (Ne + gv0 + gv1);
+        float bw1 = hm.b1, bw2 = hm.b2, bw0 = 1.f - bw1 - bw2;
+        const int32_t* mid = s.tris + 3 * hm.tri;
+        for (int i = 0; i < 3; ++i) so.mid[side][i] = mid[i];
+        so.dm[side][0] = (cc * bw0) * Ne;
+        so.dm[side][1] = (cc * bw1) * Ne;
+        so.dm[side][2] = (cc * bw2) * Ne;
+        so.have_m[side] = true;
+        so.have_edge = true;
+      }
+    }
+    if (!last) {
+      float o2[3] = {x.p[0], x.p[1], x.p[2]}, d2[3] = {dsd[0], dsd[1], dsd[2]};
+      float3 Lr = path_value(s, op, o2, d2, x.k, false, b + 1, c0, c1, kPassSecondaryBase + (uint32_t)b, nullptr,
+                             nullptr, 0, 0);
+      float hs = kInvPi * cpm * (ab.x * alb.x * Lr.x + ab.y * alb.y * Lr.y + ab.z * alb.z * Lr.z);
+      if (hs != 0.f) {
+        float cc = sg * hs / wl2 * invPE;
+        float3 gv0 = cross(a1v, what), gv1 = cross(what, a0v);
+        so.de0 += cc * gv0;
+        so.de1 += cc * gv1;
+        dp -= cc * (gv0 + gv1);
+        so.have_edge = true;
+      }
+    }
+  }
+  so.eid0 = ev.x;
+  so.eid1 = ev.y;
+}
+
+__global__ void __launch_bounds__(kBlock) k_backward_path(SceneView s, Opts op, const int32_t* tape_tri,
+                                                          const float2* tape_bary, const float* d_image, Grads gr,
+                                                          int G) {
+  int lane = threadIdx.x & 31;
+  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int ppw = 32 / G;
+  int64_t pix = gw * ppw + lane / G;
+  int npix = s.W * s.H;
+  bool pix_ok = pix < npix && pix >= op.pix_begin && pix < op.pix_end;
+  int64_t n = (int64_t)npix * op.spp;
+  int md = min(op.max_depth, kMaxDepth);
+  float g[kGlobals];
+  for (int i = 0; i < kGlobals; ++i) g[i] = 0.f;
+  float3 wpix = pix_ok ? ld3(d_image + 3 * pix) : zero3();
+  float3 a = (1.0f / (float)op.spp) * wpix;
+  const float3 Le = ld3(s.radiance);
+  bool do_int = (op.terms & 1) != 0, do_sec = (op.terms & 4) != 0 && s.E > 0 && s.L > 0;
+  int iters = (op.spp + G - 1) / G;
+  for (int it = 0; it < iters; ++it) {
+    int sidx = lane % G + it * G;
+    bool active = pix_ok && sidx < op.spp;
+    int64_t ti = pix * op.spp + sidx;
+    // forward re-evaluation from the tape
+    int kk[kMaxDepth];
+    float bb1[kMaxDepth], bb2[kMaxDepth], din[kMaxDepth][3], orig[kMaxDepth][3];
+    bool vis[kMaxDepth];
+    float3 beta[kMaxDepth];
+    int nv = 0;
+    CamHit c;
+    c.sx = c.sy = 0.f;
+    if (active) {
+      jitter(op, (int)pix, sidx, s.W, &c.sx, &c.sy);
+      camera_ray(s, c.sx, c.sy, c.o, c.d);
+      float d[3] = {c.d[0], c.d[1], c.d[2]}, o[3] = {c.o[0], c.o[1], c.o[2]};
+      float3 bt = make_float3(1.f, 1.f, 1.f);
+      for (int b = 0; b < md; ++b) {
+        int32_t tt = tape_tri[b * n + ti];
+        if (tt == -1) break;
+        kk[b] = tt & 0x7fffffff;
+        vis[b] = (tt >> 31) & 1;
+        float2 bb = tape_bary[b * n + ti];
+        bb1[b] = bb.x;
+        bb2[b] = bb.y;
+        for (int i = 0; i < 3; ++i) { din[b][i] = d[i]; orig[b][i] = o[i]; }
+        beta[b] = bt;
+        nv = b + 1;
+        if (b + 1 >= md) break;
+        Vertex x;
+        load_vertex(s, kk[b], bb1[b], bb2[b], d, x);
+        float n32[3];
+        shading_normal32(x, n32);
+        uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kBsdf, (uint32_t)b, kPassInterior, 0u);
+        float nd[3];
+        cosine_dir(n32, u01f(r.x), u01f(r.y), nd);
+        if (!(dot(f3(n32), f3(nd)) > 0.f)) break;
+        bt = bt * ld3(s.albedo + 3 * kk[b]);
+        for (int i = 0; i < 3; ++i) { o[i] = x.p[i]; d[i] = nd[i]; }
+      }
+    }
+    // reverse sweep (warp-uniform trip count for the scatter)
+    float3 D_next = zero3(), pbar = zero3();
+    for (int b = md - 1; b >= 0; --b) {
+      bool av = active && b < nv;
+      float3 dv0 = zero3(), dv1 = zero3(), dv2 = zero3(), dalb = zero3(), dl[3] = {zero3(), zero3(), zero3()};
+      int vid[3] = {0, 0, 0}, lid[3] = {0, 0, 0};
+      bool have_light = false;
+      SecOut so;
+      so.have_edge = false;
+      so.have_m[0] = so.have_m[1] = false;
+      so.eid0 = so.eid1 = 0;
+      so.de0 = so.de1 = zero3();
+      for (int q = 0; q < 2; ++q)
+        for (int i = 0; i < 3; ++i) { so.dm[q][i] = zero3(); so.mid[q][i] = 0; }
+      if (av) {
+        Vertex x;
+        load_vertex(s, kk[b], bb1[b], bb2[b], din[b], x);
+        const int32_t* vi = s.tris + 3 * kk[b];
+        vid[0] = vi[0]; vid[1] = vi[1]; vid[2] = vi[2];
+        float3 alb = ld3(s.albedo + 3 * kk[b]);
+        float3 n = shading_normal(x);
+        float3 ab = a * beta[b];
+        float3 Dv = zero3();
+        float3 dp = pbar, dn = zero3();
+        float gl[kGlobals];
+        for (int i = 0; i < kGlobals; ++i) gl[i] = 0.f;
+        if (do_int) {
+          if (b == 0 && s.light_of_tri[kk[b]] >= 0 && x.side < 0.0f) {
+            Dv += Le;
+            gl[0] += ab.x; gl[1] += ab.y; gl[2] += ab.z;
+          }
+          if (s.L > 0 && vis[b]) {
+            float3 dlt[3] = {zero3(), zero3(), zero3()};
+            Dv += nee_adjoint(s, op, (uint32_t)pix, (uint32_t)sidx, b, x, n, alb, ab, Le, gl, dalb, dp, dn, dlt, lid,
+                              have_light);
+            for (int i = 0; i < 3; ++i) dl[i] = dlt[i];
+          }
+          if (b + 1 < nv) {
+            // beta_{b+1} = beta_b * rho_b * cos(n_b, omega_b) / cos_value (pdf held fixed)
+            float3 om = f3(din[b + 1]);
+            float cbar = dot(n, om);
+            dalb += ab * D_next;
+            float cadj = (ab.x * alb.x * D_next.x + ab.y * alb.y * D_next.y + ab.z * alb.z * D_next.z) / cbar;
+            dn += cadj * om;
+            Dv += alb * D_next;
+          }
+        }
+        if (do_sec) secondary_at_vertex(s, op, (uint32_t)pix, (uint32_t)sidx, b, md, x, n, alb, ab, Le, dp, so);
+        for (int i = 0; i < kGlobals; ++i) g[i] += gl[i];
+        float3 do_, dd_;
+        plane_hit_adjoint(orig[b], din[b], x, dp, dn, dv0, dv1, dv2, do_, dd_);
+        if (b == 0) camera_ray_adjoint(s, c.sx, c.sy, do_, dd_, g);
+        pbar = do_;  // the origin of ray b is vertex b-1 (its direction is held fixed)
+        D_next = Dv;
+      }
+      scatter3(gr.verts, vid[0], dv0, av);
+      scatter3(gr.verts, vid[1], dv1, av);
+      scatter3(gr.verts, vid[2], dv2, av);
+      scatter3(gr.albedo, av ? kk[b] : 0, dalb, av && do_int);
+      for (int i = 0; i < 3; ++i) scatter3(gr.verts, lid[i], dl[i], have_light);
+      scatter3(gr.verts, so.eid0, so.de0, so.have_edge);
+      scatter3(gr.verts, so.eid1, so.de1, so.have_edge);
+      for (int q = 0; q < 2; ++q)
+        for (int i = 0; i < 3; ++i) scatter3(gr.verts, so.mid[q][i], so.dm[q][i], so.have_m[q]);
+    }
+  }
+  block_globals(g, gr.partials, false);
+}
+
+// ---------------------------------------------------------------------------
 // Backward: primary edge samples (Eq. mc)
 // ---------------------------------------------------------------------------
 // Sample j: edge by the clipped-length CDF, uniform point on the clipped
@@ -896,13 +1219,21 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
   bool need_i = (op.terms & 5) != 0;
   const int32_t* tt = tape ? tape->tri : nullptr;
   const float2* tb = tape ? tape->bary : nullptr;
-  if (op.terms & 1) {
+  bool path = !op.primary_only && op.max_depth > 1;
+  if (path && need_i) {
+    s.counters = counter_slot(kSlotBwdInterior);
+    ProfToken pt = prof_begin("backward_path", st);
+    k_backward_path<<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tt, tb, d_image, gr, G);
+    prof_end(pt, st);
+  } else if (op.terms & 1) {
     s.counters = counter_slot(kSlotBwdInterior);
     ProfToken pt = prof_begin("backward_interior", st);
     k_backward_interior<<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tt, tb, d_image, gr, G);
     prof_end(pt, st);
   }
-  if ((op.terms & 4) && s.E > 0 && s.L > 0) {
+  if (path) {
+    // the path kernel covers the interior and secondary terms
+  } else if ((op.terms & 4) && s.E > 0 && s.L > 0) {
     s.counters = counter_slot(kSlotBwdSecondary);
     ProfToken pt = prof_begin("backward_secondary_edges", st);
     k_backward_secondary<<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tt, tb, d_image, gr, G, op.terms & 1);

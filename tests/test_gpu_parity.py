@@ -174,6 +174,40 @@ def test_direct_lighting_gradient_terms(drt, ctx, terms):
     assert_grads(got, want, absum, "terms=%d" % terms)
 
 
+def gpu_grads_depth(drt, ctx, scene, d_image, spp, seed, depth, terms=7):
+    s = drt.Scene.from_arrays(ctx, scene)
+    img = torch.zeros((scene.height, scene.width, 3), dtype=torch.float32, device="cuda")
+    opts = drt.make_opts(spp, spp, max_depth=depth, seed=seed, terms=terms)
+    tape = s.render(img, opts, want_tape=True)
+    z = lambda *sh: torch.zeros(sh, dtype=torch.float32, device="cuda")  # noqa: E731
+    dv, da, dr, dc, ds = z(len(scene.verts), 3), z(len(scene.tris), 3), z(3), z(3, 4), z(1)
+    s.backward(torch.from_numpy(d_image).cuda(), opts, tape=tape, d_verts=dv, d_albedo=da, d_radiance=dr,
+               d_cam_to_world=dc, d_cam_scale=ds)
+    torch.cuda.synchronize()
+    assert ctx.check_device() == (0, 0)
+    flat = np.concatenate([x.cpu().numpy().ravel().astype(np.float64) for x in (dv, da, dr, dc, ds)])
+    return flat, img.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("depth", [2, 3])
+def test_path_tracing_image(drt, ctx, depth):
+    scene = _small_lit(W=24, H=18, subdiv=1)
+    _, img = gpu_grads_depth(drt, ctx, scene, np.zeros((18, 24, 3), np.float32), 6, 4, depth)
+    want = oracle.render(scene, spp=6, seed=4, max_depth=depth, n_threads=NT)
+    assert_pixels(img, want)
+    assert not np.allclose(want, oracle.render(scene, spp=6, seed=4, max_depth=1, n_threads=NT))
+
+
+@pytest.mark.parametrize("depth,terms", [(2, 1), (2, 2), (2, 4), (3, 1), (3, 4), (3, 7)])
+def test_path_tracing_gradient_terms(drt, ctx, depth, terms):
+    scene = _small_lit(W=24, H=18, subdiv=1)
+    w = sg.loss_adjoint(9, 24, 18)
+    got, _ = gpu_grads_depth(drt, ctx, scene, w, 6, 4, depth, terms)
+    want, absum = oracle.backward(scene, w, spp=6, edge_spp=6, seed=4, max_depth=depth, terms=terms, n_threads=NT)
+    assert_grads(got, want, absum, "depth %d terms %d" % (depth, terms))
+    assert np.abs(want).max() > 0
+
+
 def test_backward_without_tape_matches_with_tape(drt, ctx):
     scene = _small_lit(W=24, H=16)
     w = sg.loss_adjoint(5, scene.width, scene.height)
