@@ -154,3 +154,107 @@ def loss_adjoint(seed: int, width: int, height: int) -> np.ndarray:
     """d loss / d image, uniform in [-1,1] per pixel and channel, [H,W,3]."""
     rng = np.random.default_rng(seed + 7919)
     return rng.uniform(-1.0, 1.0, size=(height, width, 3)).astype(np.float32)
+
+
+def displaced_icosphere(rng, subdiv: int = 3, amp: float = 0.1, waves: int = 6):
+    """Unit icosphere with a smooth seeded radial displacement of amplitude
+    ``amp``: a sum of random cosine waves over the sphere, scaled to amp."""
+    v, f = icosphere(subdiv)
+    dirs = rng.normal(size=(waves, 3))
+    freq = rng.uniform(1.0, 4.0, size=waves)
+    phase = rng.uniform(0, 2 * np.pi, size=waves)
+    d = np.cos((v @ dirs.T) * freq + phase).sum(axis=1)
+    d = amp * d / max(1e-9, np.abs(d).max())
+    return v * (1.0 + d)[:, None], f
+
+
+def subdivided_box(n: int = 4):
+    """Axis-aligned cube [-1,1]^3 with each face split into n x n quads
+    (12 n^2 triangles; 192 for n = 4), faces wound outward."""
+    verts, tris = [], []
+    g = np.linspace(-1.0, 1.0, n + 1)
+    for axis in range(3):
+        for sign in (-1.0, 1.0):
+            u, w = [a for a in range(3) if a != axis]
+            base = len(verts)
+            for i in range(n + 1):
+                for j in range(n + 1):
+                    p = np.zeros(3)
+                    p[axis], p[u], p[w] = sign, g[i], g[j]
+                    verts.append(p)
+            for i in range(n):
+                for j in range(n):
+                    a, b = base + i * (n + 1) + j, base + (i + 1) * (n + 1) + j
+                    c, d = b + 1, a + 1
+                    tri = [[a, b, c], [a, c, d]]
+                    if (sign > 0) != ((u, w) in ((1, 2), (2, 0), (0, 1))):
+                        tri = [[a, c, b], [a, d, c]]
+                    tris += tri
+    return np.array(verts), np.array(tris, np.int64)
+
+
+def procedural(seed: int, n_target: int = 200_000, width: int = 512, height: int = 512) -> Scene:
+    """Displaced icospheres (1280 triangles each, radial noise amplitude 0.1)
+    and subdivided boxes (192 triangles each), placed in [-5,5]^3 without
+    overlap (rejection on bounding spheres) until the triangle count reaches
+    n_target; a ground quad below and two area lights above (radiance 30);
+    per-triangle albedo uniform in [0.2,0.8]^3; pinhole camera at (0,2,16)
+    looking at (0,-0.5,0), 45 degree field of view."""
+    rng = np.random.default_rng(seed)
+    parts, centers, radii = [], [], []
+    count = 6
+    tries = 0
+    while count < n_target and tries < 200000:
+        tries += 1
+        is_sphere = rng.uniform() < 0.5
+        if is_sphere:
+            r = rng.uniform(0.3, 0.6)
+            bound = r * 1.1
+        else:
+            r = rng.uniform(0.25, 0.5)
+            bound = r * np.sqrt(3.0)
+        c = rng.uniform(-5.0 + bound, 5.0 - bound, size=3)
+        if centers and np.any(np.linalg.norm(np.array(centers) - c, axis=1) < np.array(radii) + bound + 0.02):
+            continue
+        if is_sphere:
+            v, f = displaced_icosphere(rng)
+        else:
+            v, f = subdivided_box()
+        parts.append((v * r + c, f))
+        centers.append(c)
+        radii.append(bound)
+        count += len(f)
+    parts.append(quad((0, -5.5, 0), (0, 0, 8), (8, 0, 0)))
+    l1 = quad((-2, 6, -2), (0.75, 0, 0), (0, 0, 0.75))
+    l2 = quad((2, 6, 2), (0.75, 0, 0), (0, 0, 0.75))
+    parts += [l1, l2]
+    verts, tris = _merge(parts)
+    n = len(tris)
+    albedo = rng.uniform(0.2, 0.8, size=(n, 3))
+    return Scene(verts=verts, tris=tris, albedo=albedo, light_tris=np.arange(n - 4, n, dtype=np.int32),
+                 radiance=[30.0, 30.0, 30.0], cam_to_world=look_at((0, 2, 16), (0, -0.5, 0)),
+                 cam_scale=math.tan(math.radians(22.5)), cam_type=CAM_PINHOLE, width=width, height=height)
+
+
+def perturb_vertices(scene: Scene, seed: int, sigma: float = 0.02) -> np.ndarray:
+    """Vertex positions + N(0, sigma) (the inverse-rendering start point)."""
+    rng = np.random.default_rng(seed + 104729)
+    return (scene.verts + rng.normal(0.0, sigma, size=scene.verts.shape)).astype(np.float32)
+
+
+def gi_panel(width: int = 16, height: int = 16) -> Scene:
+    """A scene lit mostly indirectly: a floor (albedo 0.85) lit by a small
+    area light, a panel above the floor whose underside the camera sees (it
+    receives light only by reflection from the floor), and a small dark
+    blocker between floor and panel that casts an indirect shadow on the
+    panel and a direct shadow on the floor."""
+    floor = quad((0, 0, 0), (2, 0, 0), (0, 0, -2))
+    panel = quad((0, 1.0, 0), (0.6, 0, 0), (0, 0, 0.6))
+    light = quad((0, 2.0, 0), (0.3, 0, 0), (0, 0, 0.3))
+    blocker = (np.array([[-0.3, 0.5, -0.2], [0.35, 0.5, 0.1], [-0.1, 0.5, 0.4]]), np.array([[0, 1, 2]]))
+    verts, tris = _merge([floor, panel, light, blocker])
+    alb = np.full((len(tris), 3), 0.85)
+    alb[-1] = 0.3
+    return Scene(verts=verts, tris=tris, albedo=alb, light_tris=[4, 5], radiance=[20, 20, 20],
+                 cam_to_world=look_at((0.2, 0.25, 2.6), (0, 1.0, 0)), cam_scale=math.tan(math.radians(25)),
+                 cam_type=CAM_PINHOLE, width=width, height=height)
