@@ -96,6 +96,12 @@ typedef struct {
                            Sec. 5.2.1 needs a small offset); <= 0 selects 2^-16 */
   int32_t terms;        /* gradient terms: bit0 interior, bit1 primary edges, bit2 secondary
                            edges; 0 selects all */
+  int32_t proposal;     /* primary edge proposal: 0 edge by clipped screen length (Sec. 5.2.1);
+                           1 tile segment by q = 1/2 len/L + 1/2 w/W with the segment weights
+                           below (every segment keeps q >= 1/2 len/L, so the estimator stays
+                           unbiased; see drt_scene_segments for the segment list) */
+  const float* seg_weights;  /* [n_seg_weights] device array of nonnegative weights (proposal 1) */
+  int64_t n_seg_weights;
 } drt_render_opts;
 
 /* Gradient outputs: device or host arrays, each may be NULL (not wanted).
@@ -178,6 +184,17 @@ drt_status drt_tape_free(drt_context* ctx, drt_tape* tape);
 drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* scene, const drt_tape* tape,
                                        const drt_render_opts* opts, const float* d_image, const drt_grads* grads,
                                        void* stream);
+
+/* Screen-tile segments of the clipped primary edges: every clipped edge is
+ * cut where it crosses the 16-pixel tile grid (FP32 crossing parameters in
+ * increasing order).  Builds them for the scene's current state (this call
+ * synchronises `stream`), stores *n, and if the arrays are non-NULL writes
+ * up to cap entries: edge_tile [cap,2] int32 (edge index in the sorted unique
+ * edge list, tile index row-major), s01 [cap,2] float32 (edge parameters),
+ * lens [cap] float64 (screen lengths).  Arrays may be host or device memory.
+ * The learned proposal scores these segments (proposal 1 of drt_render_opts). */
+drt_status drt_scene_segments(drt_context* ctx, drt_scene* scene, int64_t* n, int32_t* edge_tile, float* s01,
+                              double* lens, int64_t cap, void* stream);
 
 /* Closest-hit query through the scene's LBVH for n rays (test and debug
  * entry point; the render kernels use the same traversal).  o, d: [n,3]

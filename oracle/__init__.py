@@ -47,7 +47,8 @@ class _Opts(ctypes.Structure):
                 ("primary_only", ctypes.c_int32), ("seed", ctypes.c_uint64), ("eps_rel", ctypes.c_float),
                 ("terms", ctypes.c_int32), ("pix_begin", ctypes.c_int32), ("pix_end", ctypes.c_int32),
                 ("edge_begin", ctypes.c_int64), ("edge_end", ctypes.c_int64), ("n_threads", ctypes.c_int32),
-                ("scene_id", ctypes.c_int32)]
+                ("scene_id", ctypes.c_int32), ("proposal", ctypes.c_int32), ("seg_weights", ctypes.c_void_p),
+                ("n_seg_weights", ctypes.c_int64)]
 
 
 def lib():
@@ -74,12 +75,14 @@ class _Pinned:
                         float(scene.cam_scale))
 
 
-def _opts(spp, edge_spp, max_depth, primary_only, seed, eps_rel, terms, pixels, edges, n_threads, scene_id):
+def _opts(spp, edge_spp, max_depth, primary_only, seed, eps_rel, terms, pixels, edges, n_threads, scene_id,
+          weights=None):
     pb, pe = pixels if pixels is not None else (0, 0)
     eb, ee = edges if edges is not None else (0, 0)
+    wp, wn = (weights.ctypes.data, len(weights)) if weights is not None else (None, 0)
     return _Opts(int(spp), int(edge_spp), int(max_depth), int(bool(primary_only)), int(seed) & (2 ** 64 - 1),
                  float(eps_rel), int(terms), int(pb), int(pe), int(eb), int(ee),
-                 int(n_threads or n_threads_default()), int(scene_id))
+                 int(n_threads or n_threads_default()), int(scene_id), 1 if weights is not None else 0, wp, wn)
 
 
 def num_params(scene) -> int:
@@ -113,13 +116,17 @@ def render(scene, *, spp: int, seed: int, max_depth: int = 1, primary_only: bool
 
 def backward(scene, d_image: np.ndarray, *, spp: int, edge_spp: int, seed: int, max_depth: int = 1,
              primary_only: bool = False, terms: int = TERMS_ALL, eps_rel: float = EPS_REL, pixels=None,
-             edges=None, n_threads=None, scene_id: int = 0):
+             edges=None, n_threads=None, scene_id: int = 0, proposal_weights=None):
     """Gradient of sum(d_image * image) as a flat FP64 vector, and per entry
     the magnitude of the terms summed into it (absolute-value chain rule),
-    which scales the rounding error an FP32 implementation may make."""
+    which scales the rounding error an FP32 implementation may make.
+    proposal_weights: per tile segment (see segments()), selects the mixture
+    proposal for primary edges."""
     P = _Pinned(scene)
     w = np.ascontiguousarray(d_image, dtype=np.float32).reshape(scene.height, scene.width, 3)
-    o = _opts(spp, edge_spp, max_depth, primary_only, seed, eps_rel, terms, pixels, edges, n_threads, scene_id)
+    pw = None if proposal_weights is None else np.ascontiguousarray(proposal_weights, np.float32)
+    o = _opts(spp, edge_spp, max_depth, primary_only, seed, eps_rel, terms, pixels, edges, n_threads, scene_id,
+              pw)
     n = num_params(scene)
     g = np.zeros(n, np.float64)
     a = np.zeros(n, np.float64)
@@ -168,6 +175,20 @@ def primary_edges(scene) -> np.ndarray:
     out = np.zeros((cap, 7), np.float64)
     n = lib().or_primary_edges(ctypes.byref(P.s), out.ctypes.data_as(ctypes.c_void_p), ctypes.c_int(cap))
     return out[:n]
+
+
+def segments(scene):
+    """Tile segments of the clipped primary edges: (edge, tile) int arrays,
+    (s0, s1) float32 parameters along the edge, FP64 screen lengths."""
+    P = _Pinned(scene)
+    cap = 3 * len(scene.tris) * (2 + (scene.width + scene.height) // 16)
+    out = np.zeros((cap, 4), np.float64)
+    lens = np.zeros(cap, np.float64)
+    lib().or_segments.restype = ctypes.c_int64
+    n = lib().or_segments(ctypes.byref(P.s), out.ctypes.data_as(ctypes.c_void_p),
+                          lens.ctypes.data_as(ctypes.c_void_p), ctypes.c_int64(cap))
+    out = out[:n]
+    return out[:, 0].astype(np.int32), out[:, 1].astype(np.int32), out[:, 2:].astype(np.float32), lens[:n]
 
 
 def sincos_2pi(r: float):

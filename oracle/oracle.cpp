@@ -213,6 +213,9 @@ typedef struct {
   int64_t edge_begin, edge_end;  /* primary edge sample subset; end<=0: all */
   int32_t n_threads;
   int32_t scene_id;          /* counter word c3 */
+  int32_t proposal;          /* 0: edge by clipped length; 1: tile segments by the mixture of length and seg_weights */
+  const float* seg_weights;  /* [n_seg_weights] nonnegative weight per segment (proposal 1) */
+  int64_t n_seg_weights;
 } or_opts_t;
 }
 
@@ -370,7 +373,14 @@ struct Prep {
   std::vector<double> pcdf; double ptotal = 0.0;
   /* secondary edges: 3D length CDF */
   std::vector<double> scdf; double stotal = 0.0;
+  /* screen-tile segments of the clipped primary edges (learned proposal) */
+  std::vector<int32_t> seg_edge, seg_tile;
+  std::vector<float> seg_s0, seg_s1;
+  std::vector<double> seg_len;
+  std::vector<double> seg_cdf; double seg_total = 0.0;
 };
+
+constexpr float TILE = 16.0f;  /* screen tile size of the segment split, pixels */
 
 const float* vtx(const Prep& P, int i) { return P.sc->verts + 3 * i; }
 
@@ -511,6 +521,70 @@ void prepare(const or_scene_t* sc, Prep& P) {
     P.scdf[e] = acc;
   }
   P.stotal = acc;
+  /* tile segments: split each clipped edge where it crosses the 16-pixel
+   * tile grid (FP32 crossing parameters, merged in increasing t) */
+  int tiles_x = (int)std::ceil(sc->width / TILE), tiles_y = (int)std::ceil(sc->height / TILE);
+  for (int e = 0; e < E; ++e) {
+    double le = P.pcdf[e] - (e > 0 ? P.pcdf[e - 1] : 0.0);
+    if (!(le > 0.0)) continue;
+    float ax = P.pax[e], ay = P.pay[e], t0 = P.pt0[e], t1 = P.pt1[e];
+    float dx = P.pbx[e] - ax, dy = P.pby[e] - ay;
+    std::vector<float> ts[2];
+    for (int axis = 0; axis < 2; ++axis) {
+      float a = axis == 0 ? ax : ay, d = axis == 0 ? dx : dy;
+      if (d == 0.0f) continue;
+      float c0 = a + t0 * d, c1 = a + t1 * d;
+      float lo = std::min(c0, c1), hi = std::max(c0, c1);
+      int m0 = (int)std::floor(lo / TILE) + 1, m1 = (int)std::floor(hi / TILE);
+      for (int m = m0; m <= m1; ++m) {
+        float t = ((float)m * TILE - a) / d;
+        if (t > t0 && t < t1) ts[axis].push_back(t);
+      }
+      if (d < 0.0f) std::reverse(ts[axis].begin(), ts[axis].end());
+    }
+    std::vector<float> cuts;
+    cuts.push_back(t0);
+    size_t i = 0, j = 0;
+    while (i < ts[0].size() || j < ts[1].size()) {
+      float v;
+      if (j >= ts[1].size() || (i < ts[0].size() && ts[0][i] <= ts[1][j])) v = ts[0][i++]; else v = ts[1][j++];
+      if (v > cuts.back()) cuts.push_back(v);
+    }
+    if (t1 > cuts.back()) cuts.push_back(t1);
+    double dl = std::sqrt((double)dx * (double)dx + (double)dy * (double)dy);
+    for (size_t k = 0; k + 1 < cuts.size(); ++k) {
+      float s0 = cuts[k], s1 = cuts[k + 1];
+      float mid = s0 + 0.5f * (s1 - s0);
+      float xm = ax + mid * dx, ym = ay + mid * dy;
+      int tx = std::min(std::max((int)std::floor(xm / TILE), 0), tiles_x - 1);
+      int ty = std::min(std::max((int)std::floor(ym / TILE), 0), tiles_y - 1);
+      P.seg_edge.push_back(e);
+      P.seg_tile.push_back(ty * tiles_x + tx);
+      P.seg_s0.push_back(s0);
+      P.seg_s1.push_back(s1);
+      P.seg_len.push_back(((double)s1 - (double)s0) * dl);
+    }
+  }
+}
+
+/* Mixture proposal over segments: q = 1/2 len/L + 1/2 m/M (q = len/L when
+ * every weight is zero); inclusive FP64 prefix of q in P.seg_cdf. */
+void build_proposal(Prep& P, const float* m, int64_t n) {
+  size_t ns = P.seg_len.size();
+  double L = 0.0, M = 0.0;
+  for (size_t k = 0; k < ns; ++k) {
+    L += P.seg_len[k];
+    if ((int64_t)k < n) M += std::max(0.0f, m[k]);
+  }
+  P.seg_cdf.assign(ns, 0.0);
+  double acc = 0.0;
+  for (size_t k = 0; k < ns; ++k) {
+    double q = P.seg_len[k] / L;
+    if (M > 0.0) q = 0.5 * q + 0.5 * (double)std::max(0.0f, (int64_t)k < n ? m[k] : 0.0f) / M;
+    acc += q;
+    P.seg_cdf[k] = acc;
+  }
+  P.seg_total = acc;
 }
 
 /* ---- brute-force visibility queries (all triangles, index order) -------- */
@@ -911,9 +985,25 @@ void primary_edge_sample(Ctx& C, int64_t jj) {
   uint32_t j = (uint32_t)jj;
   uint32_t r[4];
   rng(op.seed, j, 0, K_EDGE_PRIMARY, 0, PASS_PRIMARY_EDGE, (uint32_t)op.scene_id, r);
-  int e = cdf_pick(P.pcdf, u01d(r[0], r[1]) * P.ptotal);
+  int e;
+  float t0, t1;
+  double inv_pdf_len;  /* 1 / (pdf of the point per unit length) = len_seg / q_seg, or L for the plain sampler */
+  if (op.proposal == 1) {
+    if (P.seg_cdf.empty() || !(P.seg_total > 0.0)) return;
+    int k = cdf_pick(P.seg_cdf, u01d(r[0], r[1]) * P.seg_total);
+    double q = P.seg_cdf[k] - (k > 0 ? P.seg_cdf[k - 1] : 0.0);
+    if (!(q > 0.0)) return;
+    e = P.seg_edge[k];
+    t0 = P.seg_s0[k];
+    t1 = P.seg_s1[k];
+    inv_pdf_len = P.seg_len[k] / (q / P.seg_total);
+  } else {
+    e = cdf_pick(P.pcdf, u01d(r[0], r[1]) * P.ptotal);
+    t0 = P.pt0[e];
+    t1 = P.pt1[e];
+    inv_pdf_len = P.ptotal;
+  }
   float ax = P.pax[e], ay = P.pay[e], bx = P.pbx[e], by = P.pby[e];
-  float t0 = P.pt0[e], t1 = P.pt1[e];
   float dx = bx - ax, dy = by - ay;
   float t = t0 + u01f(r[2]) * (t1 - t0);
   float x = ax + t * dx, y = ay + t * dy;
@@ -946,7 +1036,7 @@ void primary_edge_sample(Ctx& C, int64_t jj) {
   Dual alpha = (Ay - By) * X + (Bx - Ax) * Y + (Ax * By - Bx * Ay);
   double gl = std::sqrt((Ax.v - Bx.v) * (Ax.v - Bx.v) + (Ay.v - By.v) * (Ay.v - By.v));
   int64_t N_edge = (int64_t)op.edge_spp * sc.width * sc.height;
-  double k = P.ptotal / (gl * (double)N_edge);
+  double k = inv_pdf_len / (gl * (double)N_edge);
   accumulate(C, diff * k, diff_abs * k, alpha);
 }
 
@@ -1017,6 +1107,22 @@ int or_primary_edges(const or_scene_t* sc, double* out, int cap) {
   return E;
 }
 
+/* Tile segments [n,4] = (edge, tile, s0, s1) as doubles plus [n] lengths;
+ * returns n (writes at most cap). */
+int64_t or_segments(const or_scene_t* sc, double* out, double* lens, int64_t cap) {
+  Prep P;
+  prepare(sc, P);
+  int64_t n = (int64_t)P.seg_len.size();
+  for (int64_t k = 0; k < n && k < cap; ++k) {
+    out[4 * k] = P.seg_edge[k];
+    out[4 * k + 1] = P.seg_tile[k];
+    out[4 * k + 2] = P.seg_s0[k];
+    out[4 * k + 3] = P.seg_s1[k];
+    lens[k] = P.seg_len[k];
+  }
+  return n;
+}
+
 /* Image [H,W,3] in FP64 for pixels in [pix_begin, pix_end) (others untouched). */
 int or_render(const or_scene_t* sc, const or_opts_t* op, double* image) {
   Prep P;
@@ -1077,6 +1183,7 @@ int or_backward(const or_scene_t* sc, const or_opts_t* op, const float* d_image,
       }
     });
   }
+  if (op->proposal == 1) build_proposal(P, op->seg_weights, op->n_seg_weights);
   if (op->terms & 2) {
     int64_t N = (int64_t)op->edge_spp * npix;
     int64_t eb = op->edge_begin, ee = op->edge_end > 0 ? op->edge_end : N;

@@ -125,7 +125,8 @@ void free_scene_buffers(drt_scene* s) {
                   s->w2c, s->light_cdf, s->light_area, s->light_box, s->nodes, s->soup, s->edges, s->pedge, s->plen, s->pcdf,
                   s->slen, s->scdf, s->scan_tmp, s->keys, s->keys2, s->vals, s->vals2, s->parent, s->leaf_parent,
                   s->flags, s->child_orig, s->hist, s->hist_tmp, s->bounds, s->partials, s->esort.keys, s->esort.keys2,
-                  s->esort.hist, s->esort.hist_tmp, s->esort.vals, s->esort.vals2};
+                  s->esort.hist, s->esort.hist_tmp, s->esort.vals, s->esort.vals2, s->seg_edge, s->seg_tile,
+                  s->seg_count, s->seg_scan_tmp, s->seg_s, s->seg_len, s->seg_a, s->seg_b, s->seg_cdf, s->seg_tmp};
   for (void* b : bufs) dfree(b);
 }
 
@@ -140,6 +141,8 @@ drt_status make_opts(const drt_render_opts* o, drt::Opts* op) {
   op->max_depth = o->max_depth;
   op->primary_only = o->primary_only ? 1 : 0;
   op->terms = o->terms == 0 ? 7 : o->terms;
+  if (o->proposal < 0 || o->proposal > 1) return fail(DRT_ERR_INVALID_ARG, "proposal must be 0 or 1");
+  op->proposal = o->proposal;
   op->key = make_uint2((uint32_t)o->seed, (uint32_t)(o->seed >> 32));
   op->eps_rel = o->eps_rel > 0.0f ? o->eps_rel : 1.52587890625e-05f;
   // DRT_DEBUG_RANGES="pix_begin,pix_end,edge_begin,edge_end" restricts which
@@ -157,6 +160,44 @@ drt_status make_opts(const drt_render_opts* o, drt::Opts* op) {
   return DRT_OK;
 }
 
+// Tile segments for the scene's current state (synchronises to learn the count).
+drt_status build_segments(drt_scene* s, cudaStream_t st) {
+  if (s->seg_generation == s->generation && s->seg_n >= 0) return DRT_OK;
+  int E = s->E;
+  if (!s->seg_count) {
+    DRT_TRY(dalloc_n(&s->seg_count, (size_t)E + 1));
+    DRT_TRY(dalloc_n(&s->seg_scan_tmp, drt::scan_tmp_entries(E + 1)));
+  }
+  CUDA_TRY(cudaMemsetAsync(s->seg_count, 0, sizeof(uint32_t) * ((size_t)E + 1), st));
+  CUDA_TRY(drt::launch_segment_count(s, s->seg_count, st));
+  CUDA_TRY(drt::scan_exclusive_u32(s->seg_count, s->seg_scan_tmp, E + 1, st));
+  uint32_t total = 0;
+  CUDA_TRY(cudaMemcpyAsync(&total, s->seg_count + E, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if ((int64_t)total > s->seg_cap) {
+    void* old[] = {s->seg_edge, s->seg_tile, s->seg_s, s->seg_len, s->seg_a, s->seg_b, s->seg_cdf, s->seg_tmp};
+    for (void* p : old) dfree(p);
+    s->seg_edge = s->seg_tile = nullptr;
+    s->seg_s = nullptr;
+    s->seg_len = s->seg_a = s->seg_b = s->seg_cdf = s->seg_tmp = nullptr;
+    s->seg_cap = 0;
+    size_t n = std::max<size_t>(1, total);
+    DRT_TRY(dalloc_n(&s->seg_edge, n));
+    DRT_TRY(dalloc_n(&s->seg_tile, n));
+    DRT_TRY(dalloc_n(&s->seg_s, n));
+    DRT_TRY(dalloc_n(&s->seg_len, n));
+    DRT_TRY(dalloc_n(&s->seg_a, n));
+    DRT_TRY(dalloc_n(&s->seg_b, n));
+    DRT_TRY(dalloc_n(&s->seg_cdf, n));
+    DRT_TRY(dalloc_n(&s->seg_tmp, n / 1024 + 2));
+    s->seg_cap = (int64_t)n;
+  }
+  CUDA_TRY(drt::launch_segment_fill(s, s->seg_count, st));
+  s->seg_n = total;
+  s->seg_generation = s->generation;
+  return DRT_OK;
+}
+
 }  // namespace
 
 namespace drt {
@@ -169,6 +210,8 @@ drt::SceneView drt_scene::view() const {
   v.w2c = w2c; v.light_tris = light_tris; v.light_of_tri = light_of_tri; v.light_cdf = light_cdf;
   v.light_area = light_area; v.light_box = light_box; v.nodes = nodes; v.soup = soup; v.edges = edges; v.pedge = pedge; v.pcdf = pcdf;
   v.scdf = scdf; v.err = ctx->err; v.counters = nullptr;
+  v.seg_cdf = seg_n > 0 ? seg_cdf : nullptr; v.seg_edge = seg_edge; v.seg_s = seg_s; v.seg_len = seg_len;
+  v.n_seg = (int)std::max<int64_t>(0, seg_n);
   v.V = V; v.T = T; v.L = L; v.E = E; v.W = W; v.H = H; v.cam_type = cam_type;
   v.root = T > drt::kLeafMax ? 0 : drt::leaf_enc(0, T);
   return v;
@@ -403,6 +446,14 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
       return fail(DRT_ERR_STATE, "tape was recorded with different sampling options");
   }
   cudaStream_t st = (cudaStream_t)stream;
+  if (op.proposal == 1) {
+    DRT_TRY(build_segments(s, st));
+    if (!opts->seg_weights || opts->n_seg_weights != s->seg_n)
+      return fail(DRT_ERR_INVALID_ARG, "proposal 1 needs %lld segment weights (got %lld)", (long long)s->seg_n,
+                  (long long)opts->n_seg_weights);
+    if (!is_device_ptr(opts->seg_weights)) return fail(DRT_ERR_INVALID_ARG, "segment weights must be device memory");
+    CUDA_TRY(drt::launch_proposal_cdf(s, opts->seg_weights, st));
+  }
   Staged sg[6];
   size_t npix = (size_t)s->W * s->H;
   drt_status r = stage(sg[0], d_image, 12 * npix, true, false, st);
@@ -458,6 +509,29 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
   r = unstage(sg, 6, st);
   if (e != cudaSuccess) return fail(DRT_ERR_CUDA, "backward launch: %s", cudaGetErrorString(e));
   return r;
+}
+
+drt_status drt_scene_segments(drt_context* ctx, drt_scene* s, int64_t* n, int32_t* edge_tile, float* s01,
+                              double* lens, int64_t cap, void* stream) {
+  if (!ctx || !s || !n || cap < 0) return fail(DRT_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  DRT_TRY(build_segments(s, st));
+  *n = s->seg_n;
+  int64_t k = std::min<int64_t>(cap, s->seg_n);
+  if (k <= 0) return DRT_OK;
+  // edge_tile interleaves (edge, tile); s01 is the float2 array; lens the lengths
+  if (edge_tile) {
+    std::vector<int32_t> e(k), t(k), et(2 * k);
+    CUDA_TRY(cudaMemcpyAsync(e.data(), s->seg_edge, 4 * k, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(t.data(), s->seg_tile, 4 * k, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < k; ++i) { et[2 * i] = e[i]; et[2 * i + 1] = t[i]; }
+    CUDA_TRY(cudaMemcpy(edge_tile, et.data(), 8 * k, cudaMemcpyDefault));
+  }
+  if (s01) CUDA_TRY(cudaMemcpyAsync(s01, s->seg_s, 8 * k, cudaMemcpyDefault, st));
+  if (lens) CUDA_TRY(cudaMemcpyAsync(lens, s->seg_len, 8 * k, cudaMemcpyDefault, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return DRT_OK;
 }
 
 drt_status drt_debug_closest(drt_context* ctx, drt_scene* s, int64_t n, const float* o, const float* d,

@@ -481,7 +481,151 @@ __global__ void k_refit(SceneView s, const int32_t* vals, float4* nodes, float4*
   }
 }
 
+// Tile segments of primary edge e (same crossing arithmetic as the oracle):
+// calls emit(s0, s1) for each piece in increasing t.
+template <class F>
+__device__ __forceinline__ int for_each_segment(const SceneView& s, int e, F emit) {
+  const float4* row = reinterpret_cast<const float4*>(s.pedge + 8 * e);
+  float4 r0 = row[0], r1 = row[1];
+  float ax = r0.x, ay = r0.y, t0 = r1.x, t1 = r1.y;
+  float dx = fs(r0.z, ax), dy = fs(r0.w, ay);
+  // crossing sequences along x and y, each monotone in t
+  int mlo[2], mhi[2], dir[2];
+  float av[2] = {ax, ay}, dv[2] = {dx, dy};
+  for (int a = 0; a < 2; ++a) {
+    mlo[a] = 1;
+    mhi[a] = 0;
+    dir[a] = 1;
+    if (dv[a] == 0.0f) continue;
+    float c0 = fa(av[a], fm(t0, dv[a])), c1 = fa(av[a], fm(t1, dv[a]));
+    float lo = fminf(c0, c1), hi = fmaxf(c0, c1);
+    mlo[a] = (int)floorf(fdv(lo, kTile)) + 1;
+    mhi[a] = (int)floorf(fdv(hi, kTile));
+    dir[a] = dv[a] > 0.0f ? 1 : -1;
+  }
+  int i[2] = {0, 0};
+  int cnt[2] = {mhi[0] - mlo[0] + 1, mhi[1] - mlo[1] + 1};
+  auto cross = [&](int a, int k) {
+    int m = dir[a] > 0 ? mlo[a] + k : mhi[a] - k;
+    return fdv(fs(fm((float)m, kTile), av[a]), dv[a]);
+  };
+  float last = t0;
+  int nseg = 0;
+  while (true) {
+    // next valid crossing of each sequence
+    float v[2];
+    for (int a = 0; a < 2; ++a) {
+      v[a] = INFINITY;
+      while (i[a] < cnt[a]) {
+        float t = cross(a, i[a]);
+        if (t > t0 && t < t1) { v[a] = t; break; }
+        ++i[a];
+      }
+    }
+    float nv;
+    if (v[0] == INFINITY && v[1] == INFINITY) break;
+    if (v[1] == INFINITY || (v[0] != INFINITY && v[0] <= v[1])) { nv = v[0]; ++i[0]; } else { nv = v[1]; ++i[1]; }
+    if (nv > last) {
+      emit(nseg++, last, nv);
+      last = nv;
+    }
+  }
+  if (t1 > last) emit(nseg++, last, t1);
+  return nseg;
+}
+
+__global__ void k_segment_count(SceneView s, const double* plen, uint32_t* counts) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= s.E) return;
+  uint32_t n = 0;
+  if (plen[e] > 0.0) n = (uint32_t)for_each_segment(s, e, [](int, float, float) {});
+  counts[e] = n;
+}
+
+__global__ void k_segment_fill(SceneView s, const double* plen, const uint32_t* offsets, int32_t* seg_edge,
+                               int32_t* seg_tile, float2* seg_s, double* seg_len) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= s.E || !(plen[e] > 0.0)) return;
+  const float4* row = reinterpret_cast<const float4*>(s.pedge + 8 * e);
+  float4 r0 = row[0];
+  float ax = r0.x, ay = r0.y;
+  float dx = fs(r0.z, ax), dy = fs(r0.w, ay);
+  double dl = __dsqrt_rn(da(dm((double)dx, (double)dx), dm((double)dy, (double)dy)));
+  int tiles_x = (int)ceilf((float)s.W / kTile), tiles_y = (int)ceilf((float)s.H / kTile);
+  uint32_t base = offsets[e];
+  for_each_segment(s, e, [&](int k, float s0, float s1) {
+    float mid = fa(s0, fm(0.5f, fs(s1, s0)));
+    float xm = fa(ax, fm(mid, dx)), ym = fa(ay, fm(mid, dy));
+    int tx = min(max((int)floorf(fdv(xm, kTile)), 0), tiles_x - 1);
+    int ty = min(max((int)floorf(fdv(ym, kTile)), 0), tiles_y - 1);
+    seg_edge[base + k] = e;
+    seg_tile[base + k] = ty * tiles_x + tx;
+    seg_s[base + k] = make_float2(s0, s1);
+    seg_len[base + k] = dm(ds((double)s1, (double)s0), dl);
+  });
+}
+
+__global__ void k_weights_to_f64(const float* w, int n, double* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = fmaxf(0.0f, w[i]);
+}
+
+// q = 1/2 len/L + 1/2 m/M (q = len/L if M == 0), from inclusive prefixes of
+// len and m (their last entries are L and M).
+__global__ void k_proposal_q(const double* len, const double* len_cdf, const double* m, const double* m_cdf, int n,
+                             double* q) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double L = len_cdf[n - 1], M = m_cdf[n - 1];
+  double ql = ddv(len[i], L);
+  q[i] = M > 0.0 ? da(dm(0.5, ql), dm(0.5, ddv(m[i], M))) : ql;
+}
+
 }  // namespace
+
+size_t scan_tmp_entries(int n) { return (size_t)(n + kScanTile - 1) / kScanTile + 1; }
+
+cudaError_t scan_exclusive_u32(uint32_t* data, uint32_t* tmp, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int nt = (n + kScanTile - 1) / kScanTile;
+  DRT_PROF_LAUNCH("scan_u32_tiles", st, k_hist_scan_tiles<<<nt, kBlock, 0, st>>>(data, tmp, n));
+  DRT_PROF_LAUNCH("scan_u32_sums", st, k_hist_scan_sums<<<1, kBlock, 0, st>>>(tmp, nt));
+  DRT_PROF_LAUNCH("scan_u32_add", st, k_hist_scan_add<<<nt, kBlock, 0, st>>>(data, tmp, n));
+  return cudaGetLastError();
+}
+
+cudaError_t scan_inclusive_f64(const double* in, double* out, double* tmp, int n, cudaStream_t st) {
+  return scan_inclusive(in, out, tmp, n, st);
+}
+
+cudaError_t launch_segment_count(const drt_scene* s, uint32_t* counts, cudaStream_t st) {
+  if (s->E > 0)
+    DRT_PROF_LAUNCH("segment_count", st, k_segment_count<<<(s->E + kBlock - 1) / kBlock, kBlock, 0, st>>>(
+                                            s->view(), s->plen, counts));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_segment_fill(const drt_scene* s, const uint32_t* offsets, cudaStream_t st) {
+  if (s->E > 0)
+    DRT_PROF_LAUNCH("segment_fill", st, k_segment_fill<<<(s->E + kBlock - 1) / kBlock, kBlock, 0, st>>>(
+                                           s->view(), s->plen, offsets, s->seg_edge, s->seg_tile, s->seg_s,
+                                           s->seg_len));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_proposal_cdf(drt_scene* s, const float* weights, cudaStream_t st) {
+  int n = (int)s->seg_n;
+  if (n <= 0) return cudaSuccess;
+  unsigned g = (unsigned)((n + kBlock - 1) / kBlock);
+  cudaError_t e = scan_inclusive(s->seg_len, s->seg_a, s->seg_tmp, n, st);  // seg_a = cumulative length
+  if (e != cudaSuccess) return e;
+  DRT_PROF_LAUNCH("proposal_weights", st, k_weights_to_f64<<<g, kBlock, 0, st>>>(weights, n, s->seg_b));
+  e = scan_inclusive(s->seg_b, s->seg_cdf, s->seg_tmp, n, st);  // seg_cdf = cumulative weight (temporarily)
+  if (e != cudaSuccess) return e;
+  DRT_PROF_LAUNCH("proposal_q", st, k_proposal_q<<<g, kBlock, 0, st>>>(s->seg_len, s->seg_a, s->seg_b, s->seg_cdf,
+                                                                       n, s->seg_b));
+  return scan_inclusive(s->seg_b, s->seg_cdf, s->seg_tmp, n, st);
+}
 
 size_t radix_hist_entries(int n) { return 256 * (size_t)((n + kSortTile - 1) / kSortTile); }
 size_t radix_hist_tmp_entries(int n) { return (radix_hist_entries(n) + kScanTile - 1) / kScanTile + 1; }

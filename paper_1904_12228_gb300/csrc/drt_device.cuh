@@ -44,6 +44,7 @@ constexpr float kNearZ = 1e-4f;        // camera depth below which a vertex is b
 constexpr float kShadowTmax = 0.9999f; // shadow rays stop short of the light point
 constexpr float kInvPi = 0.318309886f;
 constexpr int kStackSize = 64;
+constexpr float kTile = 16.0f;  // screen tile of the segment split, pixels
 // BVH leaves hold up to kLeafMax consecutive triangles of the leaf-order soup;
 // a leaf child is encoded as ~(first | (count-1) << 28).
 constexpr int kLeafMax = 1;  // measured: 4 costs more triangle tests than it saves in node visits on LBVH leaves
@@ -102,6 +103,12 @@ struct SceneView {
   const double* scdf;        // [E] inclusive prefix of 3D edge lengths
   int* err;                  // [2] device error flag (code, info)
   unsigned long long* counters;  // optional work counters [4] for this launch (or null)
+  // learned-proposal mode (null otherwise): tile segments and their proposal CDF
+  const double* seg_cdf;
+  const int32_t* seg_edge;
+  const float2* seg_s;
+  const double* seg_len;
+  int n_seg;
   int V, T, L, E, W, H, cam_type, root;
 };
 
@@ -122,7 +129,7 @@ __device__ __forceinline__ void count_trace(const SceneView& s, int kind, int no
 }
 
 struct Opts {
-  int spp, edge_spp, max_depth, primary_only, terms;
+  int spp, edge_spp, max_depth, primary_only, terms, proposal;
   uint2 key;
   float eps_rel;
   // debug restriction of the backward pass to sample ranges (full range by default)

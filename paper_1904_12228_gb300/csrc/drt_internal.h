@@ -50,6 +50,13 @@ struct drt_scene {
   float* partials = nullptr; // backward: per-block partial sums of global parameters
   size_t partials_cap = 0;
   drt::SortBuffers esort;    // backward: primary edge samples sorted by screen position
+  // tile segments of the primary edges (built on demand)
+  int32_t *seg_edge = nullptr, *seg_tile = nullptr;
+  uint32_t *seg_count = nullptr, *seg_scan_tmp = nullptr;
+  float2* seg_s = nullptr;
+  double *seg_len = nullptr, *seg_a = nullptr, *seg_b = nullptr, *seg_cdf = nullptr, *seg_tmp = nullptr;
+  int64_t seg_cap = 0, seg_n = -1;
+  uint64_t seg_generation = ~0ull;
   int sort_blocks = 0;
   drt::SceneView view() const;
 };
@@ -89,6 +96,13 @@ cudaError_t build_scene_derived(drt_scene* s, cudaStream_t st);   // w2c, lights
 bool radix_sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys2, int32_t* vals2, uint32_t* hist,
                       uint32_t* hist_tmp, int n, int bits, cudaStream_t st);
 size_t radix_hist_entries(int n);
+cudaError_t scan_exclusive_u32(uint32_t* data, uint32_t* tmp, int n, cudaStream_t st);
+size_t scan_tmp_entries(int n);
+cudaError_t scan_inclusive_f64(const double* in, double* out, double* tmp, int n, cudaStream_t st);
+// tile segments: count per edge, fill from exclusive offsets, proposal CDF
+cudaError_t launch_segment_count(const drt_scene* s, uint32_t* counts, cudaStream_t st);
+cudaError_t launch_segment_fill(const drt_scene* s, const uint32_t* offsets, cudaStream_t st);
+cudaError_t launch_proposal_cdf(drt_scene* s, const float* weights, cudaStream_t st);
 size_t radix_hist_tmp_entries(int n);
 cudaError_t build_bvh(drt_scene* s, cudaStream_t st);
 cudaError_t build_edge_cdfs(drt_scene* s, cudaStream_t st);

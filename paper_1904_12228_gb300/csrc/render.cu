@@ -1076,16 +1076,38 @@ __global__ void __launch_bounds__(kBlock) k_backward_path(SceneView s, Opts op, 
 // segment (exact decision-path arithmetic).
 struct EdgeSample {
   int e;
+  bool valid;
   float ax, ay, bx, by, dx, dy, x, y;
+  double inv_pdf_len;  // 1 / (point density per unit screen length)
 };
+// Plain sampler: edge by clipped length, uniform point.  Learned proposal:
+// tile segment by the mixture CDF, uniform point on the segment.
 __device__ __forceinline__ EdgeSample primary_sample(const SceneView& s, const Opts& op, int64_t j, double ptotal) {
   uint4 r = rng4(op.key, (uint32_t)j, 0u, kEdgePrimary, 0u, kPassPrimaryEdge, 0u);
   EdgeSample es;
-  es.e = cdf_pick(s.pcdf, s.E, dm(u01d(r.x, r.y), ptotal));
+  float t0, t1;
+  es.valid = true;
+  if (s.seg_cdf) {
+    double qt = s.seg_cdf[s.n_seg - 1];
+    int k = cdf_pick(s.seg_cdf, s.n_seg, dm(u01d(r.x, r.y), qt));
+    double q = s.seg_cdf[k] - (k > 0 ? s.seg_cdf[k - 1] : 0.0);
+    es.valid = q > 0.0;
+    es.e = s.seg_edge[k];
+    float2 ss = s.seg_s[k];
+    t0 = ss.x;
+    t1 = ss.y;
+    es.inv_pdf_len = ddv(s.seg_len[k], ddv(q, qt));
+  } else {
+    es.e = cdf_pick(s.pcdf, s.E, dm(u01d(r.x, r.y), ptotal));
+    es.inv_pdf_len = ptotal;
+  }
   const float4* row = reinterpret_cast<const float4*>(s.pedge + 8 * es.e);
   float4 r0 = row[0], r1 = row[1];
   es.ax = r0.x; es.ay = r0.y; es.bx = r0.z; es.by = r0.w;
-  float t0 = r1.x, t1 = r1.y;
+  if (!s.seg_cdf) {
+    t0 = r1.x;
+    t1 = r1.y;
+  }
   es.dx = fs(es.bx, es.ax);
   es.dy = fs(es.by, es.ay);
   float t = fa(t0, fm(u01f(r.z), fs(t1, t0)));
@@ -1134,8 +1156,12 @@ __global__ void __launch_bounds__(kBlock, 2) k_backward_primary(SceneView s, Opt
     bool active = j < n_edge && ptotal > 0.0 && j >= op.edge_begin && j < op.edge_end;
     float3 da3 = zero3(), db3 = zero3();
     int ia = 0, ib = 0;
+    EdgeSample es;
     if (active) {
-      EdgeSample es = primary_sample(s, op, j, ptotal);
+      es = primary_sample(s, op, j, ptotal);
+      active = es.valid;
+    }
+    if (active) {
       int e = es.e;
       float ax = es.ax, ay = es.ay, bx = es.bx, by = es.by, dx = es.dx, dy = es.dy, x = es.x, y = es.y;
       float nlen = fsq(fa(fm(dx, dx), fm(dy, dy)));
@@ -1152,7 +1178,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_backward_primary(SceneView s, Opt
       float diff = dot(w, L2[0] - L2[1]);
       if (diff != 0.f) {
         float gl = sqrtf((ax - bx) * (ax - bx) + (ay - by) * (ay - by));
-        float c = (float)((double)diff * ptotal / ((double)gl * (double)n_edge));
+        float c = (float)((double)diff * es.inv_pdf_len / ((double)gl * (double)n_edge));
         float dax = c * (by - y), day = c * (x - bx), dbx = c * (y - ay), dby = c * (ax - x);
         int2 ev = s.edges[e];
         ia = ev.x; ib = ev.y;
@@ -1205,6 +1231,7 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
                             float* d_verts, float* d_albedo, float* d_radiance, float* d_cam, float* d_cam_scale,
                             float* partials, const SortBuffers* sort, cudaStream_t st) {
   SceneView s = sc->view();
+  if (op.proposal != 1) s.seg_cdf = nullptr;
   int npix = s.W * s.H;
   int G = group_size(op.spp);
   int64_t warps = ((int64_t)npix + (32 / G) - 1) / (32 / G);

@@ -24,7 +24,7 @@ TERM_INTERIOR, TERM_PRIMARY, TERM_SECONDARY = 1, 2, 4
 EXPORTED = ("drt_create", "drt_destroy", "drt_scene_upload", "drt_scene_update_vertices", "drt_scene_update_params",
             "drt_scene_free", "drt_render", "drt_render_backward", "drt_tape_free", "drt_check_device",
             "drt_last_error", "drt_version", "drt_debug_closest", "drt_profile_enable", "drt_profile_read",
-            "drt_counters_enable", "drt_counters_read", "drt_render_backward_noalloc")
+            "drt_counters_enable", "drt_counters_read", "drt_render_backward_noalloc", "drt_scene_segments")
 
 
 class DrtError(RuntimeError):
@@ -44,7 +44,8 @@ class SceneDesc(ctypes.Structure):
 class RenderOpts(ctypes.Structure):
     _fields_ = [("spp", ctypes.c_int32), ("edge_spp", ctypes.c_int32), ("max_depth", ctypes.c_int32),
                 ("primary_only", ctypes.c_int32), ("seed", ctypes.c_uint64), ("eps_rel", ctypes.c_float),
-                ("terms", ctypes.c_int32)]
+                ("terms", ctypes.c_int32), ("proposal", ctypes.c_int32), ("seg_weights", ctypes.c_void_p),
+                ("n_seg_weights", ctypes.c_int64)]
 
 
 class Grads(ctypes.Structure):
@@ -82,6 +83,7 @@ def load(build_if_missing: bool = True):
         "drt_render": ([vp, vp, ctypes.POINTER(RenderOpts), vp, pp, vp], i32),
         "drt_render_backward": ([vp, vp, vp, ctypes.POINTER(RenderOpts), vp, ctypes.POINTER(Grads), vp], i32),
         "drt_tape_free": ([vp, vp], i32),
+        "drt_scene_segments": ([vp, vp, ctypes.POINTER(ctypes.c_int64), vp, vp, vp, ctypes.c_int64, vp], i32),
         "drt_render_backward_noalloc": ([vp, vp, vp, ctypes.POINTER(RenderOpts), vp, ctypes.POINTER(Grads), vp],
                                         i32),
         "drt_check_device": ([vp, vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], i32),
@@ -133,9 +135,14 @@ def _stream(stream):
     return 0
 
 
-def make_opts(spp, edge_spp=None, max_depth=1, primary_only=False, seed=0, eps_rel=0.0, terms=0) -> RenderOpts:
+def make_opts(spp, edge_spp=None, max_depth=1, primary_only=False, seed=0, eps_rel=0.0, terms=0,
+              seg_weights=None) -> RenderOpts:
+    """seg_weights: a CUDA float32 tensor of per-segment weights selects the
+    mixture proposal (it must stay alive until the backward call returns)."""
+    n = int(seg_weights.numel()) if seg_weights is not None else 0
     return RenderOpts(int(spp), int(spp if edge_spp is None else edge_spp), int(max_depth), int(bool(primary_only)),
-                      int(seed) & (2 ** 64 - 1), float(eps_rel), int(terms))
+                      int(seed) & (2 ** 64 - 1), float(eps_rel), int(terms), 1 if seg_weights is not None else 0,
+                      _ptr(seg_weights) if seg_weights is not None else None, n)
 
 
 class Context:
@@ -256,6 +263,19 @@ class Scene:
             self.free()
         except Exception:
             pass
+
+    def segments(self, stream=None):
+        """Tile segments of the clipped primary edges as numpy arrays:
+        (edge, tile) int32, (s0, s1) float32, lengths float64."""
+        n = ctypes.c_int64()
+        _check(self.ctx.lib.drt_scene_segments(self.ctx.handle, self.handle, ctypes.byref(n), None, None, None, 0,
+                                               _stream(stream)))
+        et = np.zeros((n.value, 2), np.int32)
+        s01 = np.zeros((n.value, 2), np.float32)
+        ln = np.zeros(n.value, np.float64)
+        _check(self.ctx.lib.drt_scene_segments(self.ctx.handle, self.handle, ctypes.byref(n), _ptr(et), _ptr(s01),
+                                               _ptr(ln), n.value, _stream(stream)))
+        return et[:, 0], et[:, 1], s01, ln
 
     def closest(self, o, d, tri, tb, stream=None):
         """Closest hits of rays o, d [n,3] into tri [n] (int32) and tb [n,3]."""

@@ -311,3 +311,41 @@ def test_full_size_gradient_invariants(drt, ctx):
     lhs = float((scene.radiance * dLe).sum())
     rhs = float((w.astype(np.float64) * img).sum())
     assert abs(lhs - rhs) <= 1e-4 * abs(rhs) + 1e-3
+
+
+# ---------------------------------------------------------------------------
+# Learned-proposal estimator: tile segments and the mixture proposal
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("W,H", [(40, 28), (256, 256)])
+def test_segments_match_oracle(drt, ctx, W, H):
+    scene = _small_lit(W=W, H=H, subdiv=2)
+    s = drt.Scene.from_arrays(ctx, scene)
+    e, t, s01, ln = s.segments()
+    we, wt, ws, wl = oracle.segments(scene)
+    assert len(e) == len(we)
+    assert np.array_equal(e, we) and np.array_equal(t, wt)
+    assert np.array_equal(s01, ws)
+    assert np.allclose(ln, wl, rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("spp", [4, 9])
+def test_mixture_proposal_gradient(drt, ctx, spp):
+    scene = _small_lit(W=40, H=28, subdiv=2)
+    s = drt.Scene.from_arrays(ctx, scene)
+    n_seg = len(s.segments()[0])
+    weights = (np.random.default_rng(spp).exponential(size=n_seg) ** 2).astype(np.float32)
+    wt = torch.from_numpy(weights).cuda()
+    img = torch.zeros((28, 40, 3), device="cuda")
+    tape = s.render(img, drt.make_opts(spp, spp, seed=3), want_tape=True)
+    dv = torch.zeros((len(scene.verts), 3), device="cuda")
+    w = sg.loss_adjoint(8, 40, 28)
+    s.backward(torch.from_numpy(w).cuda(), drt.make_opts(spp, spp, seed=3, terms=2, seg_weights=wt), tape=tape,
+               d_verts=dv)
+    torch.cuda.synchronize()
+    got = dv.double().cpu().numpy().ravel()
+    g, a = oracle.backward(scene, w, spp=spp, edge_spp=spp, seed=3, terms=oracle.TERM_PRIMARY, n_threads=NT,
+                           proposal_weights=weights)
+    V = len(scene.verts)
+    assert_grads(got, g[:3 * V], a[:3 * V], "mixture proposal")
+    plain, _ = oracle.backward(scene, w, spp=spp, edge_spp=spp, seed=3, terms=oracle.TERM_PRIMARY, n_threads=NT)
+    assert not np.allclose(plain[:3 * V], g[:3 * V])

@@ -364,3 +364,38 @@ def test_radiance_homogeneity():
     lhs = float((scene.radiance.astype(np.float64) * gr).sum())
     rhs = float((w.astype(np.float64) * img).sum())
     assert abs(lhs - rhs) <= 1e-9 * max(1.0, abs(rhs))
+
+
+# --------------------------------------------------------------------------
+# Mixture proposal over tile segments (learned-proposal estimator)
+# --------------------------------------------------------------------------
+def test_segments_partition_the_clipped_edges():
+    scene = sg.direct_lighting(1236, width=64, height=48, subdiv=2)
+    edge, tile, s01, lens = oracle.segments(scene)
+    pe = oracle.primary_edges(scene)
+    per_edge = np.bincount(edge, weights=lens, minlength=len(pe))
+    assert np.allclose(per_edge, pe[:, 6], rtol=0, atol=1e-9 * pe[:, 6].max())
+    assert np.all(s01[:, 1] > s01[:, 0])
+    assert tile.max() < 4 * 3 and tile.min() >= 0
+
+
+@pytest.mark.parametrize("seed", [1235, 91])
+def test_mixture_proposal_is_unbiased(seed):
+    """With arbitrary nonnegative segment weights m, sampling segments by
+    q = 1/2 len/L + 1/2 m/M and weighting by len/q keeps the primary edge
+    term unbiased: its mean equals the Reynolds closed form."""
+    scene = sg.single_triangle(seed)
+    W, H = scene.width, scene.height
+    w = sg.loss_adjoint(seed, W, H)
+    gpix = cf.coverage_gradient(_tri_pixels(scene), 0.7 * w.astype(np.float64).sum(axis=2), W, H)
+    want = np.stack([gpix[:, 0] * W / 2.0, -gpix[:, 1] * H / 2.0], axis=1)
+    n_seg = len(oracle.segments(scene)[0])
+    m = np.random.default_rng(seed + 5).exponential(size=n_seg).astype(np.float32) ** 3
+    runs = []
+    for k in range(12):
+        g, _ = oracle.backward(scene, w, spp=1, edge_spp=16, seed=2000 + k, primary_only=True,
+                               terms=oracle.TERM_PRIMARY, n_threads=NT, proposal_weights=m)
+        runs.append(oracle.split_params(scene, g)["verts"][:, :2])
+    runs = np.array(runs)
+    mean, se = runs.mean(0), runs.std(0, ddof=1) / np.sqrt(len(runs))
+    assert np.all(np.abs(mean - want) < 5 * se + 1e-3 * np.abs(want).max())
