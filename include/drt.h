@@ -55,7 +55,8 @@ enum {
   DRT_DEV_NONFINITE_INPUT = 2, /* NaN/Inf vertex coordinate (info = flat index) */
   DRT_DEV_BAD_INDEX = 3,       /* out-of-range index met on the device */
   DRT_DEV_TRAVERSAL_CAP = 4,   /* traversal visited more nodes than the tree has (malformed BVH) */
-  DRT_DEV_REFIT_CAP = 5        /* BVH refit climbed more levels than there are nodes */
+  DRT_DEV_REFIT_CAP = 5,       /* BVH refit climbed more levels than there are nodes */
+  DRT_DEV_TIMEOUT = 6          /* a bounded wait (tensor-core completion barrier) gave up (info = block) */
 };
 
 typedef struct drt_context drt_context;
@@ -102,6 +103,8 @@ typedef struct {
                            unbiased; see drt_scene_segments for the segment list) */
   const float* seg_weights;  /* [n_seg_weights] device array of nonnegative weights (proposal 1) */
   int64_t n_seg_weights;
+  float* seg_log;       /* proposal 1 only, may be NULL: device [n_seg]; each primary edge sample
+                           adds |w . (f_u - f_l)| to its segment (training data of the network) */
 } drt_render_opts;
 
 /* Gradient outputs: device or host arrays, each may be NULL (not wanted).
@@ -184,6 +187,46 @@ drt_status drt_tape_free(drt_context* ctx, drt_tape* tape);
 drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* scene, const drt_tape* tape,
                                        const drt_render_opts* opts, const float* d_image, const drt_grads* grads,
                                        void* stream);
+
+/* ---- Learned edge proposal ------------------------------------------------
+ * A 3-layer network scores screen-tile segments (drt_scene_segments); its
+ * scores, exponentiated, are the segment weights of proposal 1.  It takes
+ * the role of the edge importance of Sec. 5.3.1 (hierarchy with length,
+ * distance and BRDF bounds); the mixture with the length proposal keeps the
+ * estimator unbiased whatever the network outputs.
+ *   y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3,  x in R^32, hidden width 64,
+ * BF16 weights and activations (tcgen05 tensor cores), FP32 accumulation.
+ * All arrays are device memory; weights are [out, in] row-major. */
+typedef struct {
+  const void* w1;   /* [64,32] bf16 */
+  const float* b1;  /* [64] */
+  const void* w2;   /* [64,64] bf16 */
+  const float* b2;  /* [64] */
+  const float* w3;  /* [64] */
+  const float* b3;  /* [1] */
+} drt_mlp_weights;
+typedef struct {
+  float *w1, *b1, *w2, *b2, *w3, *b3;  /* FP32 gradients, same shapes; values are ADDED */
+} drt_mlp_grads;
+
+/* y [m] = network(x [m,32] bf16). */
+drt_status drt_mlp_forward(drt_context* ctx, const void* x, int64_t m, const drt_mlp_weights* w, float* y,
+                           void* stream);
+/* Gradient of L = inv_n/2 * sum_r mask_r (y_r - target_r)^2 added into g;
+ * L added into *loss (device scalar). */
+drt_status drt_mlp_backward(drt_context* ctx, const void* x, const float* target, const float* mask, int64_t m,
+                            float inv_n, const drt_mlp_weights* w, drt_mlp_grads* g, float* loss, void* stream);
+/* Adam with bias correction (step >= 1) on n FP32 parameters; if params_bf16
+ * is non-NULL its BF16 copy is refreshed. */
+drt_status drt_adam_step(drt_context* ctx, float* params, const float* grads, float* m1, float* m2, void* params_bf16,
+                         int64_t n, float lr, float beta1, float beta2, float eps, int32_t step, void* stream);
+
+/* Features of every tile segment for the network, [n_seg, 32] bf16 device
+ * array (n_seg from drt_scene_segments): tile centre, segment end points,
+ * lengths, camera-space normals of the edge's faces, silhouette and boundary
+ * flags, albedo difference, light flag, inverse depth, edge direction, and
+ * the mean |d_image| of the segment's tile (d_image [H,W,3] device). */
+drt_status drt_segment_features(drt_context* ctx, drt_scene* scene, const float* d_image, void* x, void* stream);
 
 /* Screen-tile segments of the clipped primary edges: every clipped edge is
  * cut where it crosses the 16-pixel tile grid (FP32 crossing parameters in

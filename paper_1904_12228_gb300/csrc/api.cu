@@ -122,7 +122,8 @@ drt_status unstage(Staged* arr, int n, cudaStream_t st) {
 
 void free_scene_buffers(drt_scene* s) {
   void* bufs[] = {s->verts, s->albedo, s->radiance, s->cam, s->cam_scale, s->tris, s->light_tris, s->light_of_tri,
-                  s->w2c, s->light_cdf, s->light_area, s->light_box, s->nodes, s->soup, s->edges, s->pedge, s->plen, s->pcdf,
+                  s->w2c, s->light_cdf, s->light_area, s->light_box, s->nodes, s->soup, s->edges, s->edge_faces,
+                  s->tile_w, s->pedge, s->plen, s->pcdf,
                   s->slen, s->scdf, s->scan_tmp, s->keys, s->keys2, s->vals, s->vals2, s->parent, s->leaf_parent,
                   s->flags, s->child_orig, s->hist, s->hist_tmp, s->bounds, s->partials, s->esort.keys, s->esort.keys2,
                   s->esort.hist, s->esort.hist_tmp, s->esort.vals, s->esort.vals2, s->seg_edge, s->seg_tile,
@@ -143,6 +144,7 @@ drt_status make_opts(const drt_render_opts* o, drt::Opts* op) {
   op->terms = o->terms == 0 ? 7 : o->terms;
   if (o->proposal < 0 || o->proposal > 1) return fail(DRT_ERR_INVALID_ARG, "proposal must be 0 or 1");
   op->proposal = o->proposal;
+  op->seg_log = o->proposal == 1 ? o->seg_log : nullptr;
   op->key = make_uint2((uint32_t)o->seed, (uint32_t)(o->seed >> 32));
   op->eps_rel = o->eps_rel > 0.0f ? o->eps_rel : 1.52587890625e-05f;
   // DRT_DEBUG_RANGES="pix_begin,pix_end,edge_begin,edge_end" restricts which
@@ -276,16 +278,22 @@ drt_status drt_scene_upload(drt_context* ctx, const drt_scene_desc* d, void* str
     if (lts[j] < 0 || lts[j] >= d->n_tris) return fail(DRT_ERR_INVALID_ARG, "light triangle %d out of range", lts[j]);
     light_of[lts[j]] = j;
   }
-  std::vector<uint64_t> keys(tris.size());
+  // unique undirected edges sorted by (min, max) vertex, with their first two faces
+  std::vector<std::pair<uint64_t, int32_t>> half(tris.size());
   for (int t = 0; t < d->n_tris; ++t)
     for (int k = 0; k < 3; ++k) {
       uint32_t a = (uint32_t)tris[3 * t + k], b = (uint32_t)tris[3 * t + (k + 1) % 3];
-      keys[3 * t + k] = ((uint64_t)std::min(a, b) << 32) | std::max(a, b);
+      half[3 * t + k] = {((uint64_t)std::min(a, b) << 32) | std::max(a, b), t};
     }
-  std::sort(keys.begin(), keys.end());
-  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
-  std::vector<int2> edges(keys.size());
-  for (size_t e = 0; e < keys.size(); ++e) edges[e] = make_int2((int)(keys[e] >> 32), (int)(keys[e] & 0xffffffffu));
+  std::sort(half.begin(), half.end());
+  std::vector<int2> edges, edge_faces;
+  for (size_t i = 0; i < half.size();) {
+    size_t j = i;
+    while (j < half.size() && half[j].first == half[i].first) ++j;
+    edges.push_back(make_int2((int)(half[i].first >> 32), (int)(half[i].first & 0xffffffffu)));
+    edge_faces.push_back(make_int2(half[i].second, j - i > 1 ? half[i + 1].second : -1));
+    i = j;
+  }
 
   drt_scene* s = new drt_scene();
   s->ctx = ctx;
@@ -301,6 +309,8 @@ drt_status drt_scene_upload(drt_context* ctx, const drt_scene_desc* d, void* str
   ALLOC(cam_scale, 1) ALLOC(tris, 3 * (size_t)T) ALLOC(light_tris, std::max(1, s->L)) ALLOC(light_of_tri, T)
   ALLOC(w2c, 12) ALLOC(light_cdf, std::max(1, s->L)) ALLOC(light_area, std::max(1, s->L)) ALLOC(light_box, 8)
   ALLOC(nodes, 4 * (size_t)std::max(1, T - 1)) ALLOC(soup, 3 * (size_t)T) ALLOC(edges, std::max(1, E))
+  ALLOC(edge_faces, std::max(1, E))
+  ALLOC(tile_w, (size_t)((s->W + 15) / 16) * ((s->H + 15) / 16) + 1)
   ALLOC(pedge, 8 * (size_t)std::max(1, E)) ALLOC(plen, std::max(1, E)) ALLOC(pcdf, std::max(1, E))
   ALLOC(slen, std::max(1, E)) ALLOC(scdf, std::max(1, E)) ALLOC(scan_tmp, std::max(1, E / 1024 + 2))
   ALLOC(keys, T) ALLOC(keys2, T) ALLOC(vals, T) ALLOC(vals2, T) ALLOC(parent, std::max(1, T))
@@ -325,6 +335,7 @@ drt_status drt_scene_upload(drt_context* ctx, const drt_scene_desc* d, void* str
   if (s->L > 0) cp(s->light_tris, lts.data(), 4 * (size_t)s->L);
   cp(s->light_of_tri, light_of.data(), 4 * (size_t)T);
   if (E > 0) cp(s->edges, edges.data(), sizeof(int2) * (size_t)E);
+  if (E > 0) cp(s->edge_faces, edge_faces.data(), sizeof(int2) * (size_t)E);
   // host vectors above are read by the copies; wait before they go away
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = drt::check_finite(s, st);
@@ -531,6 +542,15 @@ drt_status drt_scene_segments(drt_context* ctx, drt_scene* s, int64_t* n, int32_
   if (s01) CUDA_TRY(cudaMemcpyAsync(s01, s->seg_s, 8 * k, cudaMemcpyDefault, st));
   if (lens) CUDA_TRY(cudaMemcpyAsync(lens, s->seg_len, 8 * k, cudaMemcpyDefault, st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  return DRT_OK;
+}
+
+drt_status drt_segment_features(drt_context* ctx, drt_scene* s, const float* d_image, void* x, void* stream) {
+  if (!ctx || !s || !d_image || !x) return fail(DRT_ERR_INVALID_ARG, "NULL argument");
+  if (!is_device_ptr(d_image) || !is_device_ptr(x)) return fail(DRT_ERR_INVALID_ARG, "device arrays only");
+  cudaStream_t st = (cudaStream_t)stream;
+  DRT_TRY(build_segments(s, st));
+  CUDA_TRY(drt::launch_segment_features(s, d_image, x, st));
   return DRT_OK;
 }
 

@@ -10,6 +10,8 @@
 #include <climits>
 #include <cstdio>
 
+#include <cuda_bf16.h>
+
 #include "drt_internal.h"
 
 namespace drt {
@@ -581,7 +583,110 @@ __global__ void k_proposal_q(const double* len, const double* len_cdf, const dou
   q[i] = M > 0.0 ? da(dm(0.5, ql), dm(0.5, ddv(m[i], M))) : ql;
 }
 
+// Mean of |w_r|+|w_g|+|w_b| over each screen tile; the last entry receives
+// the mean over tiles.
+__global__ void k_tile_weights(const float* w, int W, int H, int tx, int ty, float* tile_w) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int nt = tx * ty;
+  if (t < nt) {
+    int x0 = (t % tx) * 16, y0 = (t / tx) * 16;
+    float acc = 0.f;
+    int n = 0;
+    for (int y = y0; y < min(y0 + 16, H); ++y)
+      for (int x = x0; x < min(x0 + 16, W); ++x, ++n) {
+        const float* p = w + 3 * ((size_t)y * W + x);
+        acc += fabsf(p[0]) + fabsf(p[1]) + fabsf(p[2]);
+      }
+    tile_w[t] = n > 0 ? acc / n : 0.f;
+  }
+}
+__global__ void k_tile_weight_mean(float* tile_w, int nt) {
+  __shared__ float sm[kBlock];
+  float acc = 0.f;
+  for (int i = threadIdx.x; i < nt; i += kBlock) acc += tile_w[i];
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = kBlock / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) tile_w[nt] = sm[0] / nt;
+}
+
+// 32 features per tile segment, stored as BF16 (zero-padded to 32).
+__global__ void k_segment_features(SceneView s, const int32_t* seg_edge, const int32_t* seg_tile, const float2* seg_s,
+                                   const double* seg_len, int n, const int2* edge_faces, const float* tile_w,
+                                   __nv_bfloat16* x) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int e = seg_edge[k], tile = seg_tile[k];
+  float2 ss = seg_s[k];
+  const float4* row = reinterpret_cast<const float4*>(s.pedge + 8 * e);
+  float4 r0 = row[0];
+  float ax = r0.x, ay = r0.y, dx = r0.z - r0.x, dy = r0.w - r0.y;
+  float W = (float)s.W, H = (float)s.H;
+  int tx = (s.W + 15) / 16, ntiles = tx * ((s.H + 15) / 16);
+  float f[32];
+  for (int i = 0; i < 32; ++i) f[i] = 0.f;
+  f[0] = ((tile % tx) + 0.5f) * 16.f / W;
+  f[1] = ((tile / tx) + 0.5f) * 16.f / H;
+  f[2] = (ax + ss.x * dx) / W;
+  f[3] = (ay + ss.x * dy) / H;
+  f[4] = (ax + ss.y * dx) / W;
+  f[5] = (ay + ss.y * dy) / H;
+  f[6] = (float)seg_len[k] / 16.f;
+  float el = sqrtf(dx * dx + dy * dy);
+  f[7] = el / fmaxf(W, H);
+  int2 ev = s.edges[e];
+  float3 v0 = ld3(s.verts + 3 * ev.x), v1 = ld3(s.verts + 3 * ev.y);
+  float3 mid = make_float3(0.5f * (v0.x + v1.x), 0.5f * (v0.y + v1.y), 0.5f * (v0.z + v1.z));
+  float3 cpos = make_float3(s.cam[3], s.cam[7], s.cam[11]);
+  float3 view = make_float3(cpos.x - mid.x, cpos.y - mid.y, cpos.z - mid.z);
+  int2 fc = edge_faces[e];
+  float side[2] = {0.f, 0.f};
+  for (int q = 0; q < 2; ++q) {
+    int t = q == 0 ? fc.x : fc.y;
+    if (t < 0) continue;
+    const int32_t* id = s.tris + 3 * t;
+    float3 a = ld3(s.verts + 3 * id[0]), b = ld3(s.verts + 3 * id[1]), c = ld3(s.verts + 3 * id[2]);
+    float3 e1 = make_float3(b.x - a.x, b.y - a.y, b.z - a.z), e2 = make_float3(c.x - a.x, c.y - a.y, c.z - a.z);
+    float3 nn = make_float3(e1.y * e2.z - e1.z * e2.y, e1.z * e2.x - e1.x * e2.z, e1.x * e2.y - e1.y * e2.x);
+    float inv = rsqrtf(fmaxf(nn.x * nn.x + nn.y * nn.y + nn.z * nn.z, 1e-30f));
+    nn = make_float3(nn.x * inv, nn.y * inv, nn.z * inv);
+    for (int i = 0; i < 3; ++i)
+      f[8 + 3 * q + i] = s.w2c[4 * i] * nn.x + s.w2c[4 * i + 1] * nn.y + s.w2c[4 * i + 2] * nn.z;
+    side[q] = nn.x * view.x + nn.y * view.y + nn.z * view.z;
+    if (s.light_of_tri[t] >= 0) f[19] = 1.f;
+  }
+  f[14] = (fc.y >= 0 && side[0] * side[1] < 0.f) ? 1.f : 0.f;
+  f[15] = fc.y < 0 ? 1.f : 0.f;
+  if (fc.x >= 0) {
+    int t1 = fc.y >= 0 ? fc.y : fc.x;
+    for (int i = 0; i < 3; ++i) f[16 + i] = fabsf(s.albedo[3 * fc.x + i] - (fc.y >= 0 ? s.albedo[3 * t1 + i] : 0.f));
+  }
+  float zc = s.w2c[8] * mid.x + s.w2c[9] * mid.y + s.w2c[10] * mid.z + s.w2c[11];
+  f[20] = 1.f / fmaxf(-zc, 1e-3f);
+  float wm = tile_w[ntiles];
+  f[21] = wm > 0.f ? tile_w[tile] / wm : 0.f;
+  f[22] = el > 0.f ? dx / el : 0.f;
+  f[23] = el > 0.f ? dy / el : 0.f;
+  for (int i = 0; i < 32; ++i) x[(size_t)k * 32 + i] = __float2bfloat16_rn(f[i]);
+}
+
 }  // namespace
+
+cudaError_t launch_segment_features(const drt_scene* s, const float* d_image, void* x, cudaStream_t st) {
+  int tx = (s->W + 15) / 16, ty = (s->H + 15) / 16, nt = tx * ty;
+  DRT_PROF_LAUNCH("tile_weights", st, k_tile_weights<<<(nt + kBlock - 1) / kBlock, kBlock, 0, st>>>(
+                                          d_image, s->W, s->H, tx, ty, s->tile_w));
+  DRT_PROF_LAUNCH("tile_weight_mean", st, k_tile_weight_mean<<<1, kBlock, 0, st>>>(s->tile_w, nt));
+  int n = (int)s->seg_n;
+  if (n > 0)
+    DRT_PROF_LAUNCH("segment_features", st, k_segment_features<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(
+                                                s->view(), s->seg_edge, s->seg_tile, s->seg_s, s->seg_len, n,
+                                                s->edge_faces, s->tile_w, (__nv_bfloat16*)x));
+  return cudaGetLastError();
+}
 
 size_t scan_tmp_entries(int n) { return (size_t)(n + kScanTile - 1) / kScanTile + 1; }
 

@@ -132,6 +132,7 @@ struct Opts {
   int spp, edge_spp, max_depth, primary_only, terms, proposal;
   uint2 key;
   float eps_rel;
+  float* seg_log;  // learned proposal training data: |w.(f_u - f_l)| summed per segment (or null)
   // debug restriction of the backward pass to sample ranges (full range by default)
   int pix_begin, pix_end;
   int64_t edge_begin, edge_end;

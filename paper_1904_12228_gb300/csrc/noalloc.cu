@@ -67,6 +67,7 @@ drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* s, const drt
   op.terms = opts->terms == 0 ? 7 : opts->terms;
   if (opts->proposal != 0) return fail_noalloc(DRT_ERR_INVALID_ARG, "drt_render_backward_noalloc supports proposal 0");
   op.proposal = 0;
+  op.seg_log = nullptr;
   op.key = make_uint2((uint32_t)opts->seed, (uint32_t)(opts->seed >> 32));
   op.eps_rel = opts->eps_rel > 0.0f ? opts->eps_rel : 1.52587890625e-05f;
   op.pix_begin = 0;

@@ -1075,7 +1075,7 @@ __global__ void __launch_bounds__(kBlock) k_backward_path(SceneView s, Opts op, 
 // Sample j: edge by the clipped-length CDF, uniform point on the clipped
 // segment (exact decision-path arithmetic).
 struct EdgeSample {
-  int e;
+  int e, seg;
   bool valid;
   float ax, ay, bx, by, dx, dy, x, y;
   double inv_pdf_len;  // 1 / (point density per unit screen length)
@@ -1087,11 +1087,13 @@ __device__ __forceinline__ EdgeSample primary_sample(const SceneView& s, const O
   EdgeSample es;
   float t0, t1;
   es.valid = true;
+  es.seg = -1;
   if (s.seg_cdf) {
     double qt = s.seg_cdf[s.n_seg - 1];
     int k = cdf_pick(s.seg_cdf, s.n_seg, dm(u01d(r.x, r.y), qt));
     double q = s.seg_cdf[k] - (k > 0 ? s.seg_cdf[k - 1] : 0.0);
     es.valid = q > 0.0;
+    es.seg = k;
     es.e = s.seg_edge[k];
     float2 ss = s.seg_s[k];
     t0 = ss.x;
@@ -1176,6 +1178,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_backward_primary(SceneView s, Opt
       float3 L2[2];
       path_value2(s, op, o2, d2, (uint32_t)j, 0u, kPassPrimaryEdge, L2);
       float diff = dot(w, L2[0] - L2[1]);
+      if (op.seg_log && es.seg >= 0) atomicAdd(op.seg_log + es.seg, fabsf(diff));
       if (diff != 0.f) {
         float gl = sqrtf((ax - bx) * (ax - bx) + (ay - by) * (ay - by));
         float c = (float)((double)diff * es.inv_pdf_len / ((double)gl * (double)n_edge));

@@ -24,7 +24,8 @@ TERM_INTERIOR, TERM_PRIMARY, TERM_SECONDARY = 1, 2, 4
 EXPORTED = ("drt_create", "drt_destroy", "drt_scene_upload", "drt_scene_update_vertices", "drt_scene_update_params",
             "drt_scene_free", "drt_render", "drt_render_backward", "drt_tape_free", "drt_check_device",
             "drt_last_error", "drt_version", "drt_debug_closest", "drt_profile_enable", "drt_profile_read",
-            "drt_counters_enable", "drt_counters_read", "drt_render_backward_noalloc", "drt_scene_segments")
+            "drt_counters_enable", "drt_counters_read", "drt_render_backward_noalloc", "drt_scene_segments",
+            "drt_mlp_forward", "drt_mlp_backward", "drt_adam_step", "drt_segment_features")
 
 
 class DrtError(RuntimeError):
@@ -45,7 +46,17 @@ class RenderOpts(ctypes.Structure):
     _fields_ = [("spp", ctypes.c_int32), ("edge_spp", ctypes.c_int32), ("max_depth", ctypes.c_int32),
                 ("primary_only", ctypes.c_int32), ("seed", ctypes.c_uint64), ("eps_rel", ctypes.c_float),
                 ("terms", ctypes.c_int32), ("proposal", ctypes.c_int32), ("seg_weights", ctypes.c_void_p),
-                ("n_seg_weights", ctypes.c_int64)]
+                ("n_seg_weights", ctypes.c_int64), ("seg_log", ctypes.c_void_p)]
+
+
+class MlpWeights(ctypes.Structure):
+    _fields_ = [("w1", ctypes.c_void_p), ("b1", ctypes.c_void_p), ("w2", ctypes.c_void_p), ("b2", ctypes.c_void_p),
+                ("w3", ctypes.c_void_p), ("b3", ctypes.c_void_p)]
+
+
+class MlpGrads(ctypes.Structure):
+    _fields_ = [("w1", ctypes.c_void_p), ("b1", ctypes.c_void_p), ("w2", ctypes.c_void_p), ("b2", ctypes.c_void_p),
+                ("w3", ctypes.c_void_p), ("b3", ctypes.c_void_p)]
 
 
 class Grads(ctypes.Structure):
@@ -83,6 +94,12 @@ def load(build_if_missing: bool = True):
         "drt_render": ([vp, vp, ctypes.POINTER(RenderOpts), vp, pp, vp], i32),
         "drt_render_backward": ([vp, vp, vp, ctypes.POINTER(RenderOpts), vp, ctypes.POINTER(Grads), vp], i32),
         "drt_tape_free": ([vp, vp], i32),
+        "drt_mlp_forward": ([vp, vp, ctypes.c_int64, ctypes.POINTER(MlpWeights), vp, vp], i32),
+        "drt_mlp_backward": ([vp, vp, vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.POINTER(MlpWeights),
+                              ctypes.POINTER(MlpGrads), vp, vp], i32),
+        "drt_adam_step": ([vp, vp, vp, vp, vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                           ctypes.c_float, ctypes.c_int32, vp], i32),
+        "drt_segment_features": ([vp, vp, vp, vp, vp], i32),
         "drt_scene_segments": ([vp, vp, ctypes.POINTER(ctypes.c_int64), vp, vp, vp, ctypes.c_int64, vp], i32),
         "drt_render_backward_noalloc": ([vp, vp, vp, ctypes.POINTER(RenderOpts), vp, ctypes.POINTER(Grads), vp],
                                         i32),
@@ -136,13 +153,14 @@ def _stream(stream):
 
 
 def make_opts(spp, edge_spp=None, max_depth=1, primary_only=False, seed=0, eps_rel=0.0, terms=0,
-              seg_weights=None) -> RenderOpts:
+              seg_weights=None, seg_log=None) -> RenderOpts:
     """seg_weights: a CUDA float32 tensor of per-segment weights selects the
     mixture proposal (it must stay alive until the backward call returns)."""
     n = int(seg_weights.numel()) if seg_weights is not None else 0
     return RenderOpts(int(spp), int(spp if edge_spp is None else edge_spp), int(max_depth), int(bool(primary_only)),
                       int(seed) & (2 ** 64 - 1), float(eps_rel), int(terms), 1 if seg_weights is not None else 0,
-                      _ptr(seg_weights) if seg_weights is not None else None, n)
+                      _ptr(seg_weights) if seg_weights is not None else None, n,
+                      _ptr(seg_log) if seg_log is not None else None)
 
 
 class Context:
@@ -203,6 +221,23 @@ class Context:
         _check(self.lib.drt_counters_read(self.handle, a.ctypes.data))
         return {nm: dict(closest_rays=int(a[i, 0]), shadow_rays=int(a[i, 1]), nodes=int(a[i, 2]), tris=int(a[i, 3]))
                 for i, nm in enumerate(self.COUNTER_SLOTS)}
+
+
+    def mlp_forward(self, x, w: "MlpWeights", y, stream=None):
+        """y [m] = network(x [m,32] bf16); w holds device pointers."""
+        _check(self.lib.drt_mlp_forward(self.handle, _ptr(x), int(x.shape[0]), ctypes.byref(w), _ptr(y),
+                                        _stream(stream)))
+
+    def mlp_backward(self, x, target, mask, inv_n, w: "MlpWeights", g: "MlpGrads", loss, stream=None):
+        _check(self.lib.drt_mlp_backward(self.handle, _ptr(x), _ptr(target), _ptr(mask), int(x.shape[0]),
+                                         float(inv_n), ctypes.byref(w), ctypes.byref(g), _ptr(loss),
+                                         _stream(stream)))
+
+    def adam_step(self, params, grads, m1, m2, params_bf16, lr, step, beta1=0.9, beta2=0.999, eps=1e-8,
+                  stream=None):
+        _check(self.lib.drt_adam_step(self.handle, _ptr(params), _ptr(grads), _ptr(m1), _ptr(m2),
+                                      _ptr(params_bf16), int(params.numel()), float(lr), float(beta1), float(beta2),
+                                      float(eps), int(step), _stream(stream)))
 
 
 class Tape:
@@ -276,6 +311,11 @@ class Scene:
         _check(self.ctx.lib.drt_scene_segments(self.ctx.handle, self.handle, ctypes.byref(n), _ptr(et), _ptr(s01),
                                                _ptr(ln), n.value, _stream(stream)))
         return et[:, 0], et[:, 1], s01, ln
+
+    def segment_features(self, d_image, x, stream=None):
+        """Features [n_seg, 32] (bf16 device tensor x) of the current segments."""
+        _check(self.ctx.lib.drt_segment_features(self.ctx.handle, self.handle, _ptr(d_image), _ptr(x),
+                                                 _stream(stream)))
 
     def closest(self, o, d, tri, tb, stream=None):
         """Closest hits of rays o, d [n,3] into tri [n] (int32) and tb [n,3]."""
