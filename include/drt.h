@@ -100,10 +100,14 @@ typedef struct {
   int32_t proposal;     /* primary edge proposal: 0 edge by clipped screen length (Sec. 5.2.1);
                            1 tile segment by q = 1/2 len/L + 1/2 w/W with the segment weights
                            below (every segment keeps q >= 1/2 len/L, so the estimator stays
-                           unbiased; see drt_scene_segments for the segment list) */
-  const float* seg_weights;  /* [n_seg_weights] device array of nonnegative weights (proposal 1) */
+                           unbiased; see drt_scene_segments for the segment list);
+                           2 the same mixture with w_k = len_k exp(clamp(s_k, -40, 40)), where
+                           s_k = seg_weights[k] is a network score (drt_mlp_forward), a log
+                           contribution density per unit screen length */
+  const float* seg_weights;  /* [n_seg_weights] device array: nonnegative weights (proposal 1) or
+                                scores (proposal 2) */
   int64_t n_seg_weights;
-  float* seg_log;       /* proposal 1 only, may be NULL: device [n_seg]; each primary edge sample
+  float* seg_log;       /* proposal 1 or 2, may be NULL: device [n_seg]; each primary edge sample
                            adds |w . (f_u - f_l)| to its segment (training data of the network) */
 } drt_render_opts;
 
@@ -157,8 +161,10 @@ drt_status drt_render(drt_context* ctx, drt_scene* scene, const drt_render_opts*
  * Primary edges: Eq. mc with the edge-equation derivatives of
  * Eq. redner_dirac_jacobian, chained through the projection.  Secondary
  * edges: Eq. dirac_3d_edge at every path vertex.  tape must come from
- * drt_render on this scene with the same opts (else DRT_ERR_STATE); tape may
- * be NULL, in which case the camera paths are traced again. */
+ * drt_render on this scene with the same opts (else DRT_ERR_STATE).  tape
+ * may be NULL when max_depth == 1 (the camera paths are traced again) or
+ * when neither the interior nor the secondary term is asked for; otherwise
+ * a NULL tape is DRT_ERR_INVALID_ARG. */
 drt_status drt_render_backward(drt_context* ctx, drt_scene* scene, const drt_tape* tape,
                                const drt_render_opts* opts, const float* d_image, const drt_grads* grads,
                                void* stream);
@@ -190,7 +196,7 @@ drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* scene, const
 
 /* ---- Learned edge proposal ------------------------------------------------
  * A 3-layer network scores screen-tile segments (drt_scene_segments); its
- * scores, exponentiated, are the segment weights of proposal 1.  It takes
+ * scores are the segment scores of proposal 2.  It takes
  * the role of the edge importance of Sec. 5.3.1 (hierarchy with length,
  * distance and BRDF bounds); the mixture with the length proposal keeps the
  * estimator unbiased whatever the network outputs.
@@ -224,8 +230,12 @@ drt_status drt_adam_step(drt_context* ctx, float* params, const float* grads, fl
 /* Features of every tile segment for the network, [n_seg, 32] bf16 device
  * array (n_seg from drt_scene_segments): tile centre, segment end points,
  * lengths, camera-space normals of the edge's faces, silhouette and boundary
- * flags, albedo difference, light flag, inverse depth, edge direction, and
- * the mean |d_image| of the segment's tile (d_image [H,W,3] device). */
+ * flags, albedo difference, light flag, inverse depth, edge direction, the
+ * mean |d_image| of the segment's tile (d_image [H,W,3] device), and camera
+ * rays traced at the segment midpoint (one through it, one half a pixel to
+ * each side of the edge): whether the edge is visible there, whether the two
+ * sides see different triangles or only one sees the background, the albedo
+ * difference of what they see and whether one sees a light. */
 drt_status drt_segment_features(drt_context* ctx, drt_scene* scene, const float* d_image, void* x, void* stream);
 
 /* Screen-tile segments of the clipped primary edges: every clipped edge is

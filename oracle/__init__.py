@@ -76,13 +76,13 @@ class _Pinned:
 
 
 def _opts(spp, edge_spp, max_depth, primary_only, seed, eps_rel, terms, pixels, edges, n_threads, scene_id,
-          weights=None):
+          weights=None, mode=1):
     pb, pe = pixels if pixels is not None else (0, 0)
     eb, ee = edges if edges is not None else (0, 0)
     wp, wn = (weights.ctypes.data, len(weights)) if weights is not None else (None, 0)
     return _Opts(int(spp), int(edge_spp), int(max_depth), int(bool(primary_only)), int(seed) & (2 ** 64 - 1),
                  float(eps_rel), int(terms), int(pb), int(pe), int(eb), int(ee),
-                 int(n_threads or n_threads_default()), int(scene_id), 1 if weights is not None else 0, wp, wn)
+                 int(n_threads or n_threads_default()), int(scene_id), mode if weights is not None else 0, wp, wn)
 
 
 def num_params(scene) -> int:
@@ -116,17 +116,24 @@ def render(scene, *, spp: int, seed: int, max_depth: int = 1, primary_only: bool
 
 def backward(scene, d_image: np.ndarray, *, spp: int, edge_spp: int, seed: int, max_depth: int = 1,
              primary_only: bool = False, terms: int = TERMS_ALL, eps_rel: float = EPS_REL, pixels=None,
-             edges=None, n_threads=None, scene_id: int = 0, proposal_weights=None):
+             edges=None, n_threads=None, scene_id: int = 0, proposal_weights=None, proposal_scores=None):
     """Gradient of sum(d_image * image) as a flat FP64 vector, and per entry
     the magnitude of the terms summed into it (absolute-value chain rule),
     which scales the rounding error an FP32 implementation may make.
     proposal_weights: per tile segment (see segments()), selects the mixture
-    proposal for primary edges."""
+    proposal for primary edges.  proposal_scores: per tile segment, network
+    scores s_k; the mixture then weighs segment k by len_k * exp(s_k), with
+    s_k clamped to [-40, 40]."""
+    if proposal_weights is not None and proposal_scores is not None:
+        raise ValueError("give proposal_weights or proposal_scores, not both")
     P = _Pinned(scene)
     w = np.ascontiguousarray(d_image, dtype=np.float32).reshape(scene.height, scene.width, 3)
-    pw = None if proposal_weights is None else np.ascontiguousarray(proposal_weights, np.float32)
+    mode, pw = 1, proposal_weights
+    if proposal_scores is not None:
+        mode, pw = 2, proposal_scores
+    pw = None if pw is None else np.ascontiguousarray(pw, np.float32)
     o = _opts(spp, edge_spp, max_depth, primary_only, seed, eps_rel, terms, pixels, edges, n_threads, scene_id,
-              pw)
+              pw, mode)
     n = num_params(scene)
     g = np.zeros(n, np.float64)
     a = np.zeros(n, np.float64)

@@ -213,7 +213,8 @@ typedef struct {
   int64_t edge_begin, edge_end;  /* primary edge sample subset; end<=0: all */
   int32_t n_threads;
   int32_t scene_id;          /* counter word c3 */
-  int32_t proposal;          /* 0: edge by clipped length; 1: tile segments by the mixture of length and seg_weights */
+  int32_t proposal;          /* 0: edge by clipped length; 1: tile segments by the mixture of length and seg_weights;
+                                2: the same with seg_weights read as network scores */
   const float* seg_weights;  /* [n_seg_weights] nonnegative weight per segment (proposal 1) */
   int64_t n_seg_weights;
 } or_opts_t;
@@ -568,19 +569,26 @@ void prepare(const or_scene_t* sc, Prep& P) {
 }
 
 /* Mixture proposal over segments: q = 1/2 len/L + 1/2 m/M (q = len/L when
- * every weight is zero); inclusive FP64 prefix of q in P.seg_cdf. */
-void build_proposal(Prep& P, const float* m, int64_t n) {
+ * every weight is zero); inclusive FP64 prefix of q in P.seg_cdf.
+ * mode 1: m_k = max(0, w_k);  mode 2 (network scores s_k, a log density per
+ * unit length): m_k = len_k * exp(min(max(s_k, -40), 40)), in FP64. */
+void build_proposal(Prep& P, const float* w, int64_t n, int mode) {
   size_t ns = P.seg_len.size();
+  std::vector<double> m(ns, 0.0);
   double L = 0.0, M = 0.0;
   for (size_t k = 0; k < ns; ++k) {
     L += P.seg_len[k];
-    if ((int64_t)k < n) M += std::max(0.0f, m[k]);
+    if ((int64_t)k < n) {
+      if (mode == 2) m[k] = P.seg_len[k] * std::exp(std::min(std::max((double)w[k], -40.0), 40.0));
+      else m[k] = (double)std::max(0.0f, w[k]);
+    }
+    M += m[k];
   }
   P.seg_cdf.assign(ns, 0.0);
   double acc = 0.0;
   for (size_t k = 0; k < ns; ++k) {
     double q = P.seg_len[k] / L;
-    if (M > 0.0) q = 0.5 * q + 0.5 * (double)std::max(0.0f, (int64_t)k < n ? m[k] : 0.0f) / M;
+    if (M > 0.0) q = 0.5 * q + 0.5 * m[k] / M;
     acc += q;
     P.seg_cdf[k] = acc;
   }
@@ -988,7 +996,7 @@ void primary_edge_sample(Ctx& C, int64_t jj) {
   int e;
   float t0, t1;
   double inv_pdf_len;  /* 1 / (pdf of the point per unit length) = len_seg / q_seg, or L for the plain sampler */
-  if (op.proposal == 1) {
+  if (op.proposal >= 1) {
     if (P.seg_cdf.empty() || !(P.seg_total > 0.0)) return;
     int k = cdf_pick(P.seg_cdf, u01d(r[0], r[1]) * P.seg_total);
     double q = P.seg_cdf[k] - (k > 0 ? P.seg_cdf[k - 1] : 0.0);
@@ -1183,7 +1191,7 @@ int or_backward(const or_scene_t* sc, const or_opts_t* op, const float* d_image,
       }
     });
   }
-  if (op->proposal == 1) build_proposal(P, op->seg_weights, op->n_seg_weights);
+  if (op->proposal >= 1) build_proposal(P, op->seg_weights, op->n_seg_weights, op->proposal);
   if (op->terms & 2) {
     int64_t N = (int64_t)op->edge_spp * npix;
     int64_t eb = op->edge_begin, ee = op->edge_end > 0 ? op->edge_end : N;

@@ -142,9 +142,9 @@ drt_status make_opts(const drt_render_opts* o, drt::Opts* op) {
   op->max_depth = o->max_depth;
   op->primary_only = o->primary_only ? 1 : 0;
   op->terms = o->terms == 0 ? 7 : o->terms;
-  if (o->proposal < 0 || o->proposal > 1) return fail(DRT_ERR_INVALID_ARG, "proposal must be 0 or 1");
+  if (o->proposal < 0 || o->proposal > 2) return fail(DRT_ERR_INVALID_ARG, "proposal must be 0, 1 or 2");
   op->proposal = o->proposal;
-  op->seg_log = o->proposal == 1 ? o->seg_log : nullptr;
+  op->seg_log = o->proposal >= 1 ? o->seg_log : nullptr;
   op->key = make_uint2((uint32_t)o->seed, (uint32_t)(o->seed >> 32));
   op->eps_rel = o->eps_rel > 0.0f ? o->eps_rel : 1.52587890625e-05f;
   // DRT_DEBUG_RANGES="pix_begin,pix_end,edge_begin,edge_end" restricts which
@@ -446,8 +446,8 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
   if (!ctx || !s || !d_image || !grads) return fail(DRT_ERR_INVALID_ARG, "NULL argument");
   drt::Opts op;
   DRT_TRY(make_opts(opts, &op));
-  if (!op.primary_only && op.max_depth > 1 && !tape)
-    return fail(DRT_ERR_INVALID_ARG, "backward with max_depth > 1 needs the tape of the forward pass");
+  if (!op.primary_only && op.max_depth > 1 && (op.terms & 5) && !tape)
+    return fail(DRT_ERR_INVALID_ARG, "interior or secondary terms with max_depth > 1 need the tape of the forward pass");
   if (tape) {
     const drt_render_opts& t = tape->opts;
     if (tape->scene != s || tape->generation != s->generation)
@@ -457,13 +457,13 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
       return fail(DRT_ERR_STATE, "tape was recorded with different sampling options");
   }
   cudaStream_t st = (cudaStream_t)stream;
-  if (op.proposal == 1) {
+  if (op.proposal >= 1) {
     DRT_TRY(build_segments(s, st));
     if (!opts->seg_weights || opts->n_seg_weights != s->seg_n)
-      return fail(DRT_ERR_INVALID_ARG, "proposal 1 needs %lld segment weights (got %lld)", (long long)s->seg_n,
-                  (long long)opts->n_seg_weights);
+      return fail(DRT_ERR_INVALID_ARG, "proposal %d needs %lld segment weights (got %lld)", op.proposal,
+                  (long long)s->seg_n, (long long)opts->n_seg_weights);
     if (!is_device_ptr(opts->seg_weights)) return fail(DRT_ERR_INVALID_ARG, "segment weights must be device memory");
-    CUDA_TRY(drt::launch_proposal_cdf(s, opts->seg_weights, st));
+    CUDA_TRY(drt::launch_proposal_cdf(s, opts->seg_weights, op.proposal, st));
   }
   Staged sg[6];
   size_t npix = (size_t)s->W * s->H;

@@ -567,9 +567,13 @@ __global__ void k_segment_fill(SceneView s, const double* plen, const uint32_t* 
   });
 }
 
-__global__ void k_weights_to_f64(const float* w, int n, double* out) {
+// Segment weights m_k of the mixture: max(0, w_k) (mode 1), or from network
+// scores s_k, a log density per unit length: len_k exp(clamp(s_k, -40, 40))
+// (mode 2), in FP64.
+__global__ void k_weights_to_f64(const float* w, const double* len, int n, int mode, double* out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = fmaxf(0.0f, w[i]);
+  if (i >= n) return;
+  out[i] = mode == 2 ? dm(len[i], exp(fmin(fmax((double)w[i], -40.0), 40.0))) : (double)fmaxf(0.0f, w[i]);
 }
 
 // q = 1/2 len/L + 1/2 m/M (q = len/L if M == 0), from inclusive prefixes of
@@ -670,6 +674,40 @@ __global__ void k_segment_features(SceneView s, const int32_t* seg_edge, const i
   f[21] = wm > 0.f ? tile_w[tile] / wm : 0.f;
   f[22] = el > 0.f ? dx / el : 0.f;
   f[23] = el > 0.f ? dy / el : 0.f;
+  // Visibility probes at the segment midpoint: a camera ray through it and
+  // one half a pixel to each side of the edge.
+  {
+    float mid = 0.5f * (ss.x + ss.y);
+    float xm = ax + mid * dx, ym = ay + mid * dy;
+    float nx = el > 0.f ? -dy / el : 0.f, ny = el > 0.f ? dx / el : 0.f;
+    float o[3], d[3];
+    camera_ray(s, xm, ym, o, d);
+    Hit hc = trace_closest(s, o, d, INFINITY, -1);
+    // ray parameter of the closest approach to the edge's line
+    float e3[3] = {v1.x - v0.x, v1.y - v0.y, v1.z - v0.z}, w0[3] = {o[0] - v0.x, o[1] - v0.y, o[2] - v0.z};
+    float A = d[0] * d[0] + d[1] * d[1] + d[2] * d[2], B = d[0] * e3[0] + d[1] * e3[1] + d[2] * e3[2];
+    float C = e3[0] * e3[0] + e3[1] * e3[1] + e3[2] * e3[2];
+    float D = d[0] * w0[0] + d[1] * w0[1] + d[2] * w0[2], E = e3[0] * w0[0] + e3[1] * w0[1] + e3[2] * w0[2];
+    float den = A * C - B * B;
+    float te = den > 0.f ? (B * E - C * D) / den : 0.f;
+    bool vis = hc.tri < 0 || hc.tri == fc.x || hc.tri == fc.y || hc.t >= te * (1.f - 1e-3f);
+    f[24] = vis ? 1.f : 0.f;
+    int side_tri[2];
+    for (int q = 0; q < 2; ++q) {
+      float sgn = q == 0 ? 0.5f : -0.5f;
+      camera_ray(s, xm + sgn * nx, ym + sgn * ny, o, d);
+      side_tri[q] = trace_closest(s, o, d, INFINITY, -1).tri;
+    }
+    f[25] = side_tri[0] != side_tri[1] ? 1.f : 0.f;
+    f[26] = (side_tri[0] < 0) != (side_tri[1] < 0) ? 1.f : 0.f;
+    float lum[2];
+    for (int q = 0; q < 2; ++q) {
+      int t = side_tri[q];
+      lum[q] = t < 0 ? 0.f : (s.albedo[3 * t] + s.albedo[3 * t + 1] + s.albedo[3 * t + 2]) * (1.f / 3.f);
+      if (t >= 0 && s.light_of_tri[t] >= 0) f[28] = 1.f;
+    }
+    f[27] = fabsf(lum[0] - lum[1]);
+  }
   for (int i = 0; i < 32; ++i) x[(size_t)k * 32 + i] = __float2bfloat16_rn(f[i]);
 }
 
@@ -718,13 +756,14 @@ cudaError_t launch_segment_fill(const drt_scene* s, const uint32_t* offsets, cud
   return cudaGetLastError();
 }
 
-cudaError_t launch_proposal_cdf(drt_scene* s, const float* weights, cudaStream_t st) {
+cudaError_t launch_proposal_cdf(drt_scene* s, const float* weights, int mode, cudaStream_t st) {
   int n = (int)s->seg_n;
   if (n <= 0) return cudaSuccess;
   unsigned g = (unsigned)((n + kBlock - 1) / kBlock);
   cudaError_t e = scan_inclusive(s->seg_len, s->seg_a, s->seg_tmp, n, st);  // seg_a = cumulative length
   if (e != cudaSuccess) return e;
-  DRT_PROF_LAUNCH("proposal_weights", st, k_weights_to_f64<<<g, kBlock, 0, st>>>(weights, n, s->seg_b));
+  DRT_PROF_LAUNCH("proposal_weights", st, k_weights_to_f64<<<g, kBlock, 0, st>>>(weights, s->seg_len, n, mode,
+                                                                                  s->seg_b));
   e = scan_inclusive(s->seg_b, s->seg_cdf, s->seg_tmp, n, st);  // seg_cdf = cumulative weight (temporarily)
   if (e != cudaSuccess) return e;
   DRT_PROF_LAUNCH("proposal_q", st, k_proposal_q<<<g, kBlock, 0, st>>>(s->seg_len, s->seg_a, s->seg_b, s->seg_cdf,

@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(128) k_mlp_backward(MlpArgs a, const float* ta
     float m = valid ? mask[row0 + r] : 0.f;
     float e = y - (valid ? target[row0 + r] : 0.f);
     dy = m * e * inv_n;
-    if (valid && m != 0.f) atomicAdd(loss, 0.5f * e * e * inv_n);
+    if (valid && m != 0.f) atomicAdd(loss, 0.5f * m * e * e * inv_n);
     for (int j = 0; j < kHid; ++j) {
       float h2 = fmaxf(z2[j], 0.f);
       gw3l[j] = dy * h2;

@@ -74,8 +74,9 @@ drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* s, const drt
   op.pix_end = INT32_MAX;
   op.edge_begin = 0;
   op.edge_end = INT64_MAX;
-  if (!op.primary_only && op.max_depth > 1 && !tape) {
-    return fail_noalloc(DRT_ERR_INVALID_ARG, "backward with max_depth > 1 needs the tape of the forward pass");
+  if (!op.primary_only && op.max_depth > 1 && (op.terms & 5) && !tape) {
+    return fail_noalloc(DRT_ERR_INVALID_ARG,
+                        "interior or secondary terms with max_depth > 1 need the tape of the forward pass");
   }
   if (tape) {
     const drt_render_opts& t = tape->opts;

@@ -1234,7 +1234,7 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
                             float* d_verts, float* d_albedo, float* d_radiance, float* d_cam, float* d_cam_scale,
                             float* partials, const SortBuffers* sort, cudaStream_t st) {
   SceneView s = sc->view();
-  if (op.proposal != 1) s.seg_cdf = nullptr;
+  if (op.proposal == 0) s.seg_cdf = nullptr;
   int npix = s.W * s.H;
   int G = group_size(op.spp);
   int64_t warps = ((int64_t)npix + (32 / G) - 1) / (32 / G);

@@ -153,13 +153,18 @@ def _stream(stream):
 
 
 def make_opts(spp, edge_spp=None, max_depth=1, primary_only=False, seed=0, eps_rel=0.0, terms=0,
-              seg_weights=None, seg_log=None) -> RenderOpts:
+              seg_weights=None, seg_log=None, seg_scores=None) -> RenderOpts:
     """seg_weights: a CUDA float32 tensor of per-segment weights selects the
-    mixture proposal (it must stay alive until the backward call returns)."""
-    n = int(seg_weights.numel()) if seg_weights is not None else 0
+    mixture proposal 1; seg_scores: per-segment network scores select the
+    mixture proposal 2.  The tensor must stay alive until the backward call
+    returns."""
+    if seg_weights is not None and seg_scores is not None:
+        raise ValueError("give seg_weights or seg_scores, not both")
+    mode, w = (1, seg_weights) if seg_weights is not None else ((2, seg_scores) if seg_scores is not None else (0, None))
+    n = int(w.numel()) if w is not None else 0
     return RenderOpts(int(spp), int(spp if edge_spp is None else edge_spp), int(max_depth), int(bool(primary_only)),
-                      int(seed) & (2 ** 64 - 1), float(eps_rel), int(terms), 1 if seg_weights is not None else 0,
-                      _ptr(seg_weights) if seg_weights is not None else None, n,
+                      int(seed) & (2 ** 64 - 1), float(eps_rel), int(terms), mode,
+                      _ptr(w) if w is not None else None, n,
                       _ptr(seg_log) if seg_log is not None else None)
 
 
@@ -311,6 +316,13 @@ class Scene:
         _check(self.ctx.lib.drt_scene_segments(self.ctx.handle, self.handle, ctypes.byref(n), _ptr(et), _ptr(s01),
                                                _ptr(ln), n.value, _stream(stream)))
         return et[:, 0], et[:, 1], s01, ln
+
+    def num_segments(self, stream=None) -> int:
+        """Number of tile segments of the current clipped primary edges."""
+        n = ctypes.c_int64()
+        _check(self.ctx.lib.drt_scene_segments(self.ctx.handle, self.handle, ctypes.byref(n), None, None, None, 0,
+                                               _stream(stream)))
+        return n.value
 
     def segment_features(self, d_image, x, stream=None):
         """Features [n_seg, 32] (bf16 device tensor x) of the current segments."""

@@ -1,0 +1,233 @@
+"""Learned proposal for primary edge samples.
+
+The plain sampler of Sec. 5.2.1 picks a clipped silhouette edge with
+probability proportional to its screen length.  Most of those samples land
+where the integrand does not jump (hidden edges, edges between faces of equal
+colour) and contribute nothing.  Here a 3-layer network (64 wide, BF16 weights
+on the tensor cores, FP32 accumulation; drt_mlp_forward) scores each screen
+tile segment of every clipped edge; the renderer's proposal 2 draws a segment
+with probability q = 1/2 len/L + 1/2 m/M, with m = len * exp(score), and a
+point uniformly on it, and divides the sample by its density (Eq. mc with
+that pdf).  Half the samples still follow the length distribution, so every
+point keeps a nonzero density and the estimator stays unbiased whatever the
+network outputs.  This plays the part of the edge importance of Sec. 5.3.1.
+
+Training data comes from the plain sampler itself: a backward pass with the
+length distribution over the same segments adds |w (f_u - f_l)| of every
+primary edge sample to its segment (seg_log), which estimates the segment's
+integral of the edge integrand's magnitude.  The network regresses the log of
+that integral per unit length, relative to the scene's mean, weighted by
+segment length; drt_mlp_backward and drt_adam_step train it on the GPU.
+
+The figure of merit is gradient variance x time at equal sample count
+against the plain sampler, on scenes the network did not see.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+import torch
+
+from . import drt
+
+NAMES = ("w1", "b1", "w2", "b2", "w3", "b3")
+N_IN, HIDDEN = 32, 64
+TERM_PRIMARY = 2
+
+
+def _bf16_bits(t: torch.Tensor) -> torch.Tensor:
+    return t.to(torch.bfloat16).view(torch.int16)
+
+
+class EdgeProposal:
+    """Network weights (FP32 masters + BF16 copies), Adam state, gradients."""
+
+    def __init__(self, ctx: drt.Context, seed: int = 0, device: str = "cuda"):
+        self.ctx = ctx
+        g = torch.Generator().manual_seed(seed)
+        shapes = {"w1": (HIDDEN, N_IN), "b1": (HIDDEN,), "w2": (HIDDEN, HIDDEN), "b2": (HIDDEN,), "w3": (HIDDEN,),
+                  "b3": (1,)}
+        fan_in = {"w1": N_IN, "w2": HIDDEN, "w3": HIDDEN}
+        p = {}
+        for k, shp in shapes.items():
+            if k in fan_in:  # uniform He initialisation for ReLU layers
+                lim = math.sqrt(6.0 / fan_in[k]) if k != "w3" else math.sqrt(3.0 / fan_in[k])
+                p[k] = (torch.rand(shp, generator=g) * 2 - 1) * lim
+            else:
+                p[k] = torch.zeros(shp)
+        self.p = {k: v.float().to(device).contiguous() for k, v in p.items()}
+        self.pb = {k: _bf16_bits(self.p[k]).contiguous() for k in ("w1", "w2")}
+        self.g = {k: torch.zeros_like(v) for k, v in self.p.items()}
+        self.m1 = {k: torch.zeros_like(v) for k, v in self.p.items()}
+        self.m2 = {k: torch.zeros_like(v) for k, v in self.p.items()}
+        self.steps = 0
+        self._w = drt.MlpWeights(self.pb["w1"].data_ptr(), self.p["b1"].data_ptr(), self.pb["w2"].data_ptr(),
+                                 self.p["b2"].data_ptr(), self.p["w3"].data_ptr(), self.p["b3"].data_ptr())
+        self._gp = drt.MlpGrads(*(self.g[k].data_ptr() for k in NAMES))
+
+    # -- inference ------------------------------------------------------------
+    def features(self, scene: drt.Scene, d_image: torch.Tensor, n: int | None = None, stream=None):
+        n = scene.num_segments(stream) if n is None else n
+        x = torch.empty((n, N_IN), dtype=torch.int16, device=d_image.device)
+        if n:
+            scene.segment_features(d_image, x, stream)
+        return x
+
+    def scores(self, scene: drt.Scene, d_image: torch.Tensor, n: int | None = None, stream=None):
+        """Network scores of the scene's current tile segments ([n] float32)."""
+        x = self.features(scene, d_image, n, stream)
+        y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        if x.shape[0]:
+            self.ctx.mlp_forward(x, self._w, y, stream)
+        return y
+
+    # -- training -------------------------------------------------------------
+    def train_step(self, x, target, mask, lr: float, loss: torch.Tensor, stream=None):
+        """One Adam step on rows x [m,32] (bf16 bits) with weights mask."""
+        for k in NAMES:
+            self.g[k].zero_()
+        inv_n = 1.0 / max(1, x.shape[0])
+        self.ctx.mlp_backward(x, target, mask, inv_n, self._w, self._gp, loss, stream)
+        self.steps += 1
+        for k in NAMES:
+            self.ctx.adam_step(self.p[k], self.g[k], self.m1[k], self.m2[k], self.pb.get(k), lr, self.steps,
+                               stream=stream)
+
+    def fit(self, data: "Dataset", steps: int, batch: int = 16384, lr: float = 3e-3, log_every: int = 200):
+        """Mini-batch Adam over the (pre-shuffled) dataset; returns the mean
+        loss of each block of log_every steps."""
+        n = data.x.shape[0]
+        batch = min(batch, n)
+        nb = max(1, n // batch)
+        hist = []
+        acc = torch.zeros(1, device=data.x.device)
+        for i in range(steps):
+            b = i % nb
+            sl = slice(b * batch, (b + 1) * batch)
+            # cosine decay to lr/10
+            lr_i = lr * (0.55 + 0.45 * math.cos(math.pi * i / max(1, steps)))
+            self.train_step(data.x[sl], data.target[sl], data.mask[sl], lr_i, acc)
+            if (i + 1) % log_every == 0 or i + 1 == steps:
+                k = (i % log_every) + 1
+                hist.append(acc.item() / k)
+                acc.zero_()
+        return hist
+
+
+@dataclasses.dataclass
+class Dataset:
+    x: torch.Tensor       # [n, 32] bf16 bits
+    target: torch.Tensor  # [n] log relative contribution density
+    mask: torch.Tensor    # [n] regression weight (segment length / mean length)
+
+    @staticmethod
+    def concat(parts, seed: int = 0) -> "Dataset":
+        x = torch.cat([p.x for p in parts])
+        t = torch.cat([p.target for p in parts])
+        m = torch.cat([p.mask for p in parts])
+        perm = torch.from_numpy(np.random.default_rng(seed).permutation(x.shape[0])).to(x.device)
+        return Dataset(x[perm].contiguous(), t[perm].contiguous(), m[perm].contiguous())
+
+
+def _zero(n, dev):
+    return torch.zeros(n, dtype=torch.float32, device=dev)
+
+
+def collect(ctx: drt.Context, scene: drt.Scene, d_image: torch.Tensor, *, edge_spp: int, passes: int, seed: int,
+            max_depth: int = 1, delta: float = 1e-3) -> Dataset:
+    """Training rows of one scene from the plain (length) distribution over
+    its tile segments: `passes` backward passes of the primary edge term, each
+    with edge_spp samples per pixel, log |w (f_u - f_l)| per segment."""
+    dev = d_image.device
+    _, _, _, seg_len = scene.segments()
+    n = len(seg_len)
+    log = _zero(n, dev)
+    zeros = _zero(n, dev)
+    dv = torch.zeros((scene.n_verts, 3), device=dev)
+    for p in range(passes):
+        o = drt.make_opts(1, edge_spp, max_depth=max_depth, seed=seed + p, terms=TERM_PRIMARY, seg_weights=zeros,
+                          seg_log=log)
+        scene.backward(d_image, o, d_verts=dv)
+    n_samples = float(passes) * edge_spp * scene.width * scene.height
+    L = float(seg_len.sum())
+    lens = torch.from_numpy(seg_len).to(dev)
+    # integral of |w (f_u - f_l)| over the segment, per unit length
+    dens = log.double() * (L / n_samples) / lens.clamp_min(1e-12)
+    mean = float(log.double().sum()) / n_samples  # = integral over all edges / L
+    rel = dens / max(mean, 1e-30)
+    target = torch.log(rel + delta).float()
+    mask = (lens / lens.mean()).float()
+    x = torch.empty((n, N_IN), dtype=torch.int16, device=dev)
+    scene.segment_features(d_image, x)
+    return Dataset(x, target, mask)
+
+
+# ---------------------------------------------------------------------------
+# Evaluation: gradient variance x time against the plain sampler
+# ---------------------------------------------------------------------------
+@dataclasses.dataclass
+class VarianceResult:
+    var: float           # mean over vertex entries of Var_k(g_k), over the mean of gbar^2
+    ms: float            # median milliseconds per gradient (proposal set-up included)
+    mean: np.ndarray     # mean gradient [V*3]
+    se: np.ndarray       # its standard error
+
+
+def _summarise(runs: torch.Tensor, times, norm: float) -> VarianceResult:
+    r = runs.double()
+    k = r.shape[0]
+    mean = r.mean(0)
+    var = r.var(0, unbiased=True)
+    return VarianceResult(float(var.mean()) / norm, float(np.median(times)), mean.cpu().numpy(),
+                          (var / k).sqrt().cpu().numpy())
+
+
+def gradient_runs(scene: drt.Scene, d_image: torch.Tensor, *, edge_spp: int, K: int, seed: int,
+                  proposal: EdgeProposal | None = None, max_depth: int = 1, tape=None):
+    """K primary-edge vertex gradients with independent seeds; per run the
+    device time of the whole estimate (segment features, network and
+    proposal CDF included for the learned proposal)."""
+    dev = d_image.device
+    runs = torch.zeros((K, scene.n_verts * 3), device=dev)
+    times = []
+    n = scene.num_segments() if proposal is not None else 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k in range(K):
+        dv = runs[k].view(scene.n_verts, 3)
+        e0.record()
+        if proposal is not None:
+            sc = proposal.scores(scene, d_image, n)
+            o = drt.make_opts(1, edge_spp, max_depth=max_depth, seed=seed + k, terms=TERM_PRIMARY, seg_scores=sc)
+        else:
+            o = drt.make_opts(1, edge_spp, max_depth=max_depth, seed=seed + k, terms=TERM_PRIMARY)
+        scene.backward(d_image, o, tape=tape, d_verts=dv)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return runs, times
+
+
+def compare(scene: drt.Scene, d_image: torch.Tensor, proposal: EdgeProposal, *, edge_spp: int, K: int, seed: int,
+            max_depth: int = 1, warmup: int = 2):
+    """Plain vs learned on one scene; returns (plain, learned, ratio, z2),
+    ratio = (var_l ms_l) / (var_p ms_p), z2 = mean squared z-score of the
+    difference of the two mean gradients (about 1 when both are unbiased)."""
+    tape = None
+    for prop in (None, proposal):  # warm-up (allocations, first launches)
+        gradient_runs(scene, d_image, edge_spp=edge_spp, K=warmup, seed=seed + 10_000, proposal=prop,
+                      max_depth=max_depth, tape=tape)
+    rp, tp = gradient_runs(scene, d_image, edge_spp=edge_spp, K=K, seed=seed, proposal=None, max_depth=max_depth,
+                           tape=tape)
+    rl, tl = gradient_runs(scene, d_image, edge_spp=edge_spp, K=K, seed=seed + 50_000, proposal=proposal,
+                           max_depth=max_depth, tape=tape)
+    norm = float(((rp.double().mean(0) + rl.double().mean(0)) * 0.5).pow(2).mean())
+    norm = norm if norm > 0 else 1.0
+    plain = _summarise(rp, tp, norm)
+    learned = _summarise(rl, tl, norm)
+    ratio = (learned.var * learned.ms) / max(plain.var * plain.ms, 1e-30)
+    se2 = plain.se ** 2 + learned.se ** 2
+    ok = se2 > 0
+    z2 = float(np.mean((plain.mean[ok] - learned.mean[ok]) ** 2 / se2[ok])) if ok.any() else 0.0
+    return plain, learned, ratio, z2

@@ -328,23 +328,30 @@ def test_segments_match_oracle(drt, ctx, W, H):
     assert np.allclose(ln, wl, rtol=1e-15, atol=0)
 
 
-@pytest.mark.parametrize("spp", [4, 9])
-def test_mixture_proposal_gradient(drt, ctx, spp):
+@pytest.mark.parametrize("spp,mode", [(4, "weights"), (9, "weights"), (5, "scores")])
+def test_mixture_proposal_gradient(drt, ctx, spp, mode):
     scene = _small_lit(W=40, H=28, subdiv=2)
     s = drt.Scene.from_arrays(ctx, scene)
     n_seg = len(s.segments()[0])
-    weights = (np.random.default_rng(spp).exponential(size=n_seg) ** 2).astype(np.float32)
+    rng = np.random.default_rng(spp)
+    if mode == "weights":
+        weights = (rng.exponential(size=n_seg) ** 2).astype(np.float32)
+    else:  # network scores, some beyond the clamp range
+        weights = (4.0 * rng.normal(size=n_seg)).astype(np.float32)
+        weights[::17] = 55.0
+        weights[5::17] = -70.0
     wt = torch.from_numpy(weights).cuda()
     img = torch.zeros((28, 40, 3), device="cuda")
     tape = s.render(img, drt.make_opts(spp, spp, seed=3), want_tape=True)
     dv = torch.zeros((len(scene.verts), 3), device="cuda")
     w = sg.loss_adjoint(8, 40, 28)
-    s.backward(torch.from_numpy(w).cuda(), drt.make_opts(spp, spp, seed=3, terms=2, seg_weights=wt), tape=tape,
-               d_verts=dv)
+    kw = {"seg_weights": wt} if mode == "weights" else {"seg_scores": wt}
+    s.backward(torch.from_numpy(w).cuda(), drt.make_opts(spp, spp, seed=3, terms=2, **kw), tape=tape, d_verts=dv)
     torch.cuda.synchronize()
     got = dv.double().cpu().numpy().ravel()
+    okw = {"proposal_weights": weights} if mode == "weights" else {"proposal_scores": weights}
     g, a = oracle.backward(scene, w, spp=spp, edge_spp=spp, seed=3, terms=oracle.TERM_PRIMARY, n_threads=NT,
-                           proposal_weights=weights)
+                           **okw)
     V = len(scene.verts)
     assert_grads(got, g[:3 * V], a[:3 * V], "mixture proposal")
     plain, _ = oracle.backward(scene, w, spp=spp, edge_spp=spp, seed=3, terms=oracle.TERM_PRIMARY, n_threads=NT)

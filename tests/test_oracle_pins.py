@@ -379,22 +379,25 @@ def test_segments_partition_the_clipped_edges():
     assert tile.max() < 4 * 3 and tile.min() >= 0
 
 
-@pytest.mark.parametrize("seed", [1235, 91])
-def test_mixture_proposal_is_unbiased(seed):
-    """With arbitrary nonnegative segment weights m, sampling segments by
-    q = 1/2 len/L + 1/2 m/M and weighting by len/q keeps the primary edge
-    term unbiased: its mean equals the Reynolds closed form."""
+@pytest.mark.parametrize("seed,mode", [(1235, "weights"), (91, "weights"), (77, "scores")])
+def test_mixture_proposal_is_unbiased(seed, mode):
+    """With arbitrary nonnegative segment weights m (or network scores s,
+    m = len exp(s)), sampling segments by q = 1/2 len/L + 1/2 m/M and
+    weighting by len/q keeps the primary edge term unbiased: its mean equals
+    the Reynolds closed form."""
     scene = sg.single_triangle(seed)
     W, H = scene.width, scene.height
     w = sg.loss_adjoint(seed, W, H)
     gpix = cf.coverage_gradient(_tri_pixels(scene), 0.7 * w.astype(np.float64).sum(axis=2), W, H)
     want = np.stack([gpix[:, 0] * W / 2.0, -gpix[:, 1] * H / 2.0], axis=1)
     n_seg = len(oracle.segments(scene)[0])
-    m = np.random.default_rng(seed + 5).exponential(size=n_seg).astype(np.float32) ** 3
+    rng = np.random.default_rng(seed + 5)
+    m = rng.exponential(size=n_seg).astype(np.float32) ** 3
+    kw = {"proposal_weights": m} if mode == "weights" else {"proposal_scores": 3.0 * rng.normal(size=n_seg)}
     runs = []
     for k in range(12):
         g, _ = oracle.backward(scene, w, spp=1, edge_spp=16, seed=2000 + k, primary_only=True,
-                               terms=oracle.TERM_PRIMARY, n_threads=NT, proposal_weights=m)
+                               terms=oracle.TERM_PRIMARY, n_threads=NT, **kw)
         runs.append(oracle.split_params(scene, g)["verts"][:, :2])
     runs = np.array(runs)
     mean, se = runs.mean(0), runs.std(0, ddof=1) / np.sqrt(len(runs))
