@@ -10,6 +10,11 @@ update (LBVH rebuild, edge CDFs), render with a checkpoint tape, and the
 backward pass (interior adjoint, secondary and primary edge terms, gradient
 scatter).  Inputs are synthetic and seeded.
 
+The second half of the metric, gradient variance x time of the learned
+edge proposal against the plain edge sampler, comes from the proposal
+module's protocol (train on logs of 20 scenes, score 4 held-out scenes) and
+is reported under "variance_x_time" (N=1; --no-proposal skips it).
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  For N > 1 (torchrun) every rank renders its
@@ -185,6 +190,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal variance x time part")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
@@ -315,6 +321,13 @@ def main():
     h2d = 12 * V + 12 * W_IMG * H_IMG + grad_bytes
     d2h = 12 * W_IMG * H_IMG + grad_bytes
 
+    # second half of the metric: gradient variance x time, learned proposal
+    # against the plain edge sampler (N=1 only)
+    vxt = None
+    if rank == 0 and world == 1 and not args.no_proposal:
+        from paper_1904_12228_gb300 import proposal
+        vxt = proposal.protocol(ctx)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -329,7 +342,7 @@ def main():
                            "triangles": T, "l2": "flushed between timed steps (256 MiB write)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "rays_per_s": world * rays / (ms_per_step / 1e3),
-                "roofline": roof, "cpu_baseline": cpu,
+                "roofline": roof, "cpu_baseline": cpu, "variance_x_time": vxt,
                 "e2e": {"value": world * n_samples / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": gpu_launches,

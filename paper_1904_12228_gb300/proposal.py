@@ -231,3 +231,71 @@ def compare(scene: drt.Scene, d_image: torch.Tensor, proposal: EdgeProposal, *, 
     ok = se2 > 0
     z2 = float(np.mean((plain.mean[ok] - learned.mean[ok]) ** 2 / se2[ok])) if ok.any() else 0.0
     return plain, learned, ratio, z2
+
+
+# ---------------------------------------------------------------------------
+# Train / evaluate protocol: network trained on logs of 16 direct-lighting
+# scenes (icosphere of 5120 triangles, 256x256) and 4 procedural scenes
+# (200k triangles, 512x512, depth 3); scored on 2 + 2 held-out scenes.
+# ---------------------------------------------------------------------------
+TRAIN_DIRECT = tuple(range(100, 116))
+TRAIN_PROCEDURAL = tuple(range(116, 120))
+HELD_OUT = ((200, "direct"), (201, "direct"), (202, "procedural"), (203, "procedural"))
+
+
+def _make_scene(ctx, kind, seed):
+    from . import scenegen as sg
+    sc = sg.direct_lighting(seed) if kind == "direct" else sg.procedural(seed)
+    s = drt.Scene.from_arrays(ctx, sc)
+    w = torch.from_numpy(sg.loss_adjoint(seed, sc.width, sc.height)).cuda()
+    return sc, s, w
+
+
+def protocol(ctx: drt.Context, *, steps: int = 3000, k_direct: int = 32, k_procedural: int = 24,
+             edge_spp_direct: int = 64, edge_spp_procedural: int = 32) -> dict:
+    """Collect, train and evaluate; returns a JSON-ready summary with the
+    learned/plain ratio of gradient variance x time per held-out scene and
+    their geometric mean."""
+    import time
+    t0 = time.perf_counter()
+    parts = []
+    for seed in TRAIN_DIRECT:
+        _, s, w = _make_scene(ctx, "direct", seed)
+        parts.append(collect(ctx, s, w, edge_spp=16, passes=4, seed=seed * 1000))
+        s.free()
+    for seed in TRAIN_PROCEDURAL:
+        _, s, w = _make_scene(ctx, "procedural", seed)
+        parts.append(collect(ctx, s, w, edge_spp=4, passes=2, seed=seed * 1000, max_depth=3))
+        s.free()
+    data = Dataset.concat(parts)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    net = EdgeProposal(ctx, 0)
+    hist = net.fit(data, steps=steps)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    scenes = []
+    for seed, kind in HELD_OUT:
+        sc, s, w = _make_scene(ctx, kind, seed)
+        direct = kind == "direct"
+        es = edge_spp_direct if direct else edge_spp_procedural
+        md = 1 if direct else 3
+        plain, learned, ratio, z2 = compare(s, w, net, edge_spp=es, K=k_direct if direct else k_procedural,
+                                            seed=seed * 7, max_depth=md)
+        scenes.append({"scene": "%s seed %d" % (kind, seed), "triangles": int(len(sc.tris)),
+                       "width": sc.width, "height": sc.height, "max_depth": md, "edge_spp": es,
+                       "runs": k_direct if direct else k_procedural, "var_plain": plain.var,
+                       "var_learned": learned.var, "ms_plain": plain.ms, "ms_learned": learned.ms,
+                       "ratio": ratio, "mean_z2": z2})
+        s.free()
+    code, info = ctx.check_device()
+    if code != 0:
+        raise RuntimeError("device error flag %d (%d) in the proposal protocol" % (code, info))
+    gm = float(np.exp(np.mean([np.log(max(r["ratio"], 1e-30)) for r in scenes])))
+    return {"ratio_geomean": gm, "ratio_unit": "learned/plain gradient variance x time (<1: learned wins)",
+            "scenes": scenes, "train_rows": int(data.x.shape[0]), "train_steps": steps,
+            "collect_s": t1 - t0, "train_s": t2 - t1, "loss_first": hist[0], "loss_last": hist[-1],
+            "variance": "mean over vertex entries of the run variance of the primary edge gradient, "
+                        "over the mean squared gradient",
+            "time": "median device ms of one gradient estimate; learned includes segment features, network "
+                    "forward and proposal CDF"}
