@@ -62,6 +62,7 @@ enum {
 typedef struct drt_context drt_context;
 typedef struct drt_scene drt_scene;
 typedef struct drt_tape drt_tape;
+typedef struct drt_batch drt_batch;
 
 enum { DRT_CAMERA_ORTHO = 0, DRT_CAMERA_PINHOLE = 1 };
 
@@ -109,6 +110,9 @@ typedef struct {
   int64_t n_seg_weights;
   float* seg_log;       /* proposal 1 or 2, may be NULL: device [n_seg]; each primary edge sample
                            adds |w . (f_u - f_l)| to its segment (training data of the network) */
+  int32_t scene_id;     /* >= 0: fourth word of every Philox counter.  A batch (drt_batch_*)
+                           gives scene k of the batch scene_id k, so a single-scene call
+                           with scene_id k reproduces it; 0 otherwise */
 } drt_render_opts;
 
 /* Gradient outputs: device or host arrays, each may be NULL (not wanted).
@@ -193,6 +197,64 @@ drt_status drt_tape_free(drt_context* ctx, drt_tape* tape);
 drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* scene, const drt_tape* tape,
                                        const drt_render_opts* opts, const float* d_image, const drt_grads* grads,
                                        void* stream);
+
+/* ---- Batched scenes ------------------------------------------------------
+ * A batch runs render and backward of n uploaded scenes as one step (a
+ * project addition: the thesis renders one scene per call).  Each pass
+ * (render; interior or path; secondary edges; primary edges) is one
+ * persistent launch whose CTAs take (scene, block) work items from an atomic
+ * counter; the primary edge samples of all scenes are sorted by screen
+ * position in one radix sort; the global gradients of each scene are reduced
+ * in a fixed order.  Scene k uses scene_id k for its random numbers: its
+ * image equals drt_render of that scene with opts.scene_id = k bit for bit,
+ * and its gradients equal drt_render_backward's with a tape, up to the order
+ * of floating-point atomic additions into vertex and albedo gradients (and,
+ * after autotuning of the edge budget, the grouping of the global partial
+ * sums).  A batch uses its own tapes and scratch; scenes may repeat.
+ * Arrays of a batch are device memory and must outlive it. */
+typedef struct {
+  drt_scene* scene;
+  float* image;            /* [H,W,3], written by every run */
+  const float* d_image;    /* [H,W,3] d loss / d image, or NULL: no backward pass for this scene */
+  drt_grads grads;         /* accumulated (+=) by every run; each array may be NULL */
+  const float* verts;      /* [V,3] or NULL; if set, every run first copies these vertices into the
+                              scene and rebuilds its BVH and edge tables, as
+                              drt_scene_update_vertices does */
+} drt_batch_item;
+
+typedef struct {
+  int32_t ctas_per_sm[5];  /* per pass (render, interior, secondary, path, primary edges):
+                              resident CTAs per SM of its persistent launch */
+  int32_t grid[5];         /* CTAs launched per pass (0: the pass does not run) */
+  int32_t chunk[5];        /* work items taken per counter increment */
+  int32_t edge_per_thread_mult;  /* primary edge samples per thread, over the single-scene value */
+  int32_t graph;           /* 1 once the step is a captured CUDA graph */
+  int32_t tuned;           /* 1 if the shapes above were chosen by timing */
+  int64_t items[5];        /* work items per pass */
+  int64_t edge_samples;    /* primary edge samples of all scenes */
+  double tune_ms;          /* host time spent tuning */
+} drt_batch_info;
+
+/* Plan a batch of n >= 1 items with shared options (proposal must be 0;
+ * scene_id is set per item).  use_graph: the first run captures the step
+ * into a CUDA graph, later runs replay it.  autotune: the first run times
+ * candidate launch shapes per pass (probe gradients go to scratch) and
+ * synchronises the stream; the result is reused by later batches of the
+ * same size class on the device.  Errors: DRT_ERR_INVALID_ARG (NULL items,
+ * host arrays, proposal != 0, too many samples), DRT_ERR_OOM. */
+drt_status drt_batch_create(drt_context* ctx, const drt_batch_item* items, int32_t n, const drt_render_opts* opts,
+                            int32_t use_graph, int32_t autotune, drt_batch** out);
+/* One step of the batch on `stream`. */
+drt_status drt_batch_run(drt_context* ctx, drt_batch* batch, void* stream);
+drt_status drt_batch_get_info(drt_context* ctx, const drt_batch* batch, drt_batch_info* info);
+/* Waits for the device, then frees the batch's buffers and graph. */
+drt_status drt_batch_free(drt_context* ctx, drt_batch* batch);
+/* One-shot batch without graph or tuning: images[k] (and, if d_images is
+ * non-NULL, a backward pass with d_images[k] into grads[k]) for scenes[k].
+ * Synchronises the stream. */
+drt_status drt_render_batch(drt_context* ctx, drt_scene* const* scenes, int32_t n, const drt_render_opts* opts,
+                            float* const* images, const float* const* d_images, const drt_grads* grads,
+                            void* stream);
 
 /* ---- Learned edge proposal ------------------------------------------------
  * A 3-layer network scores screen-tile segments (drt_scene_segments); its

@@ -146,6 +146,8 @@ drt_status make_opts(const drt_render_opts* o, drt::Opts* op) {
   op->proposal = o->proposal;
   op->seg_log = o->proposal >= 1 ? o->seg_log : nullptr;
   op->key = make_uint2((uint32_t)o->seed, (uint32_t)(o->seed >> 32));
+  if (o->scene_id < 0) return fail(DRT_ERR_INVALID_ARG, "scene_id must be >= 0");
+  op->scene_id = (uint32_t)o->scene_id;
   op->eps_rel = o->eps_rel > 0.0f ? o->eps_rel : 1.52587890625e-05f;
   // DRT_DEBUG_RANGES="pix_begin,pix_end,edge_begin,edge_end" restricts which
   // samples the backward pass evaluates (for bisecting against the oracle)
@@ -204,6 +206,10 @@ drt_status build_segments(drt_scene* s, cudaStream_t st) {
 
 namespace drt {
 void set_last_error(const char* msg) { g_err = msg; }
+drt_status convert_opts(const drt_render_opts* o, Opts* op) { return make_opts(o, op); }
+drt_status device_alloc(void** p, size_t bytes) { return dalloc(p, bytes); }
+void device_free(void* p) { dfree(p); }
+bool is_device_array(const void* p) { return is_device_ptr(p); }
 }  // namespace drt
 
 drt::SceneView drt_scene::view() const {

@@ -131,12 +131,44 @@ __device__ __forceinline__ void count_trace(const SceneView& s, int kind, int no
 struct Opts {
   int spp, edge_spp, max_depth, primary_only, terms, proposal;
   uint2 key;
+  uint32_t scene_id;  // fourth Philox counter word (the scene's index in a batch)
   float eps_rel;
   float* seg_log;  // learned proposal training data: |w.(f_u - f_l)| summed per segment (or null)
   // debug restriction of the backward pass to sample ranges (full range by default)
   int pix_begin, pix_end;
   int64_t edge_begin, edge_end;
 };
+
+// Passes of a batch, in launch order.
+enum BatchPhase { kPhaseRender = 0, kPhaseInterior = 1, kPhaseSecondary = 2, kPhasePath = 3, kPhasePrimary = 4,
+                  kPhases = 5 };
+
+// One scene of a batch (device array, one entry per scene): its view, its
+// options and where its outputs go.  The persistent batch kernels copy the
+// entry of the scene they work on into shared memory.
+struct BatchScene {
+  SceneView v;
+  Opts op;
+  float* image;            // [H,W,3]
+  int32_t* tape_tri;       // this scene's tape (W*H*spp entries per bounce)
+  float2* tape_bary;
+  const float* d_image;    // [H,W,3] loss adjoint, or null (no backward pass)
+  float* d_verts;
+  float* d_albedo;
+  float* partials;         // this scene's rows: interior rows, then primary edge rows
+  float* d_radiance;
+  float* d_cam;
+  float* d_scale;
+  const int32_t* order;    // screen order of the primary edge samples (null: sample order)
+  int64_t rows_i;          // interior rows (0 when no pixel pass of the backward runs)
+  int64_t n_edge;          // primary edge samples
+  int64_t per_thread;      // primary edge samples per thread and virtual block
+  int64_t blocks_e;        // primary edge virtual blocks
+  int G;                   // lanes per pixel
+  int rows_written;        // the secondary pass adds to rows the interior pass wrote
+  int pad_[2];
+};
+
 
 __device__ __forceinline__ void raise_flag(int* err, int code, int info) {
   if (atomicCAS(err, 0, code) == 0) err[1] = info;

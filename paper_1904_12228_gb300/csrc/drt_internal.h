@@ -75,6 +75,11 @@ struct drt_tape {
 
 namespace drt {
 void set_last_error(const char* msg);  // message returned by drt_last_error on this thread
+// api.cu helpers shared with the other entry points
+drt_status convert_opts(const drt_render_opts* o, Opts* op);  // validated device options
+drt_status device_alloc(void** p, size_t bytes);              // cudaMalloc with fault injection
+void device_free(void* p);
+bool is_device_array(const void* p);
 // prof.cu: event timing of launches (when enabled) and work-counter slots
 struct ProfToken {
   const char* name;
@@ -118,4 +123,16 @@ cudaError_t launch_backward(const drt_scene* s, const Opts& op, const drt_tape* 
 int64_t backward_partial_rows(const drt_scene* s, const Opts& op);
 cudaError_t launch_debug_closest(const drt_scene* s, int64_t n, const float* o, const float* d, int32_t* tri,
                                  float* tb, cudaStream_t st);
+// the single-scene launch shapes the batch reproduces
+int pixel_group(int spp);                          // lanes per pixel
+int64_t pixel_blocks(int W, int H, int spp);       // blocks of the pixel passes
+void primary_blocks(int64_t n_edge, int64_t* blocks_e, int64_t* per_thread);
+int screen_key_bits(int W, int H);                 // bits of a pixel's screen key
+// batched scenes (persistent kernels; phase = BatchPhase)
+cudaError_t launch_batch_phase(int phase, const BatchScene* bs, const int64_t* prefix, int n, int64_t n_items,
+                               int grid, int chunk, unsigned long long* counter, cudaStream_t st);
+int batch_phase_occupancy(int phase);              // resident CTAs per SM
+cudaError_t launch_batch_keys(const BatchScene* bs, const int64_t* eprefix, int n, int64_t total, int pix_bits,
+                              uint32_t* keys, int32_t* vals, cudaStream_t st);
+cudaError_t launch_batch_reduce(const BatchScene* bs, int n, cudaStream_t st);
 }  // namespace drt

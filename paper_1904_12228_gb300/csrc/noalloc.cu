@@ -69,6 +69,8 @@ drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* s, const drt
   op.proposal = 0;
   op.seg_log = nullptr;
   op.key = make_uint2((uint32_t)opts->seed, (uint32_t)(opts->seed >> 32));
+  if (opts->scene_id < 0) return fail_noalloc(DRT_ERR_INVALID_ARG, "scene_id must be >= 0");
+  op.scene_id = (uint32_t)opts->scene_id;
   op.eps_rel = opts->eps_rel > 0.0f ? opts->eps_rel : 1.52587890625e-05f;
   op.pix_begin = 0;
   op.pix_end = INT32_MAX;

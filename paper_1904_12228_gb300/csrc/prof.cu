@@ -38,6 +38,13 @@ unsigned long long* g_counters = nullptr;  // [kKernelSlots * 4]
 ProfToken prof_begin(const char* name, cudaStream_t st) {
   ProfToken t{nullptr, nullptr, nullptr};
   if (!g_prof) return t;
+  // launches recorded into a CUDA graph are not timed per launch
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return t;
+  }
+  if (cs != cudaStreamCaptureStatusNone) return t;
   t.name = name;
   t.a = get_event();
   t.b = get_event();

@@ -72,7 +72,7 @@ __device__ __forceinline__ void scatter3(float* arr, int id, float3 v, bool acti
 
 // Block reduction of the global parameters into one row of partials; the
 // rows are summed in a fixed order by k_reduce_globals (deterministic).
-__device__ __forceinline__ void block_globals(float g[kGlobals], float* partials, bool add) {
+__device__ __forceinline__ void block_globals(float g[kGlobals], float* row, bool add) {
   __shared__ float sm[kBlock / 32][kGlobals];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -84,14 +84,15 @@ __device__ __forceinline__ void block_globals(float g[kGlobals], float* partials
   if (threadIdx.x < kGlobals) {
     float acc = 0.f;
     for (int w = 0; w < kBlock / 32; ++w) acc += sm[w][threadIdx.x];
-    float* dst = partials + (size_t)blockIdx.x * kGlobals + threadIdx.x;
+    float* dst = row + threadIdx.x;
     *dst = add ? *dst + acc : acc;
   }
 }
 
 // One warp per column; each lane sums a fixed stride of rows, then a fixed
 // butterfly, so the result does not depend on scheduling.
-__global__ void k_reduce_globals(const float* partials, int rows, float* d_radiance, float* d_cam, float* d_scale) {
+__device__ __forceinline__ void reduce_globals(const float* partials, int rows, float* d_radiance, float* d_cam,
+                                               float* d_scale) {
   int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (i >= kGlobals) return;
   double acc = 0.0;
@@ -103,6 +104,9 @@ __global__ void k_reduce_globals(const float* partials, int rows, float* d_radia
   if (i < 3) { if (d_radiance) d_radiance[i] += v; }
   else if (i < 15) { if (d_cam) d_cam[i - 3] += v; }
   else if (d_scale) d_scale[0] += v;
+}
+__global__ void k_reduce_globals(const float* partials, int rows, float* d_radiance, float* d_cam, float* d_scale) {
+  reduce_globals(partials, rows, d_radiance, d_cam, d_scale);
 }
 
 // ---- shading data of a hit -------------------------------------------------
@@ -202,7 +206,7 @@ __device__ float3 path_value(const SceneView& s, const Opts& op, float o_in[3], 
     shading_normal32(x, n32);
     int vis = 0;
     if (s.L > 0) {
-      uint4 r = rng4(op.key, c0, c1, kLight, (uint32_t)b, pass, 0u);
+      uint4 r = rng4(op.key, c0, c1, kLight, (uint32_t)b, pass, op.scene_id);
       LightSample ls;
       sample_light(s, r, ls);
       float sd[3] = {fs(ls.y[0], x.p[0]), fs(ls.y[1], x.p[1]), fs(ls.y[2], x.p[2])};
@@ -217,7 +221,7 @@ __device__ float3 path_value(const SceneView& s, const Opts& op, float o_in[3], 
       tape_bary[b * n_stride + n_idx] = make_float2(h.b1, h.b2);
     }
     if (b + 1 >= md) { ++b; break; }
-    uint4 r = rng4(op.key, c0, c1, kBsdf, (uint32_t)b, pass, 0u);
+    uint4 r = rng4(op.key, c0, c1, kBsdf, (uint32_t)b, pass, op.scene_id);
     float nd[3];
     cosine_dir(n32, u01f(r.x), u01f(r.y), nd);
     if (!(dot(f3(n32), f3(nd)) > 0.f)) { ++b; break; }
@@ -262,7 +266,7 @@ __device__ void path_value2(const SceneView& s, const Opts& op, float o[2][3], f
     for (int q = 0; q < 2; ++q)
       if (alive[q]) shading_normal32(x[q], n32[q]);
     if (s.L > 0) {
-      uint4 r = rng4(op.key, c0, c1, kLight, (uint32_t)b, pass, 0u);
+      uint4 r = rng4(op.key, c0, c1, kLight, (uint32_t)b, pass, op.scene_id);
       LightSample ls;
       sample_light(s, r, ls);
       float sd[2][3];
@@ -279,7 +283,7 @@ __device__ void path_value2(const SceneView& s, const Opts& op, float o[2][3], f
         }
     }
     if (b + 1 >= md) break;
-    uint4 r = rng4(op.key, c0, c1, kBsdf, (uint32_t)b, pass, 0u);
+    uint4 r = rng4(op.key, c0, c1, kBsdf, (uint32_t)b, pass, op.scene_id);
     for (int q = 0; q < 2; ++q) {
       if (!alive[q]) continue;
       float nd[3];
@@ -294,7 +298,7 @@ __device__ void path_value2(const SceneView& s, const Opts& op, float o[2][3], f
 }
 
 __device__ __forceinline__ void jitter(const Opts& op, int pix, int sidx, int W, float* sx, float* sy) {
-  uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kCamera, 0u, kPassInterior, 0u);
+  uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kCamera, 0u, kPassInterior, op.scene_id);
   *sx = fa((float)(pix % W), u01f(r.x));
   *sy = fa((float)(pix / W), u01f(r.y));
 }
@@ -302,10 +306,10 @@ __device__ __forceinline__ void jitter(const Opts& op, int pix, int sidx, int W,
 // ---------------------------------------------------------------------------
 // Forward
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock) k_render(SceneView s, Opts op, float* image, int32_t* tape_tri,
-                                                   float2* tape_bary, int G) {
+__device__ __forceinline__ void render_block(const SceneView& s, const Opts& op, float* image, int32_t* tape_tri,
+                                                   float2* tape_bary, int G, int64_t blk) {
   int lane = threadIdx.x & 31;
-  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t gw = (blk * kBlock + threadIdx.x) >> 5;
   int ppw = 32 / G;
   int64_t pix = gw * ppw + lane / G;
   int npix = s.W * s.H;
@@ -332,6 +336,10 @@ __global__ void __launch_bounds__(kBlock) k_render(SceneView s, Opts op, float* 
     image[3 * pix + 1] = acc.y * inv;
     image[3 * pix + 2] = acc.z * inv;
   }
+}
+__global__ void __launch_bounds__(kBlock) k_render(SceneView s, Opts op, float* image, int32_t* tape_tri,
+                                                   float2* tape_bary, int G) {
+  render_block(s, op, image, tape_tri, tape_bary, G, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -528,11 +536,11 @@ __device__ __forceinline__ float3 shading_normal(const Vertex& x) {
 // Interior term (second integral of Eq. redner_product_rule): emission and
 // the NEE estimator F * A_j / P(j) at the camera hit, differentiated in
 // reverse with the random numbers and the pick probability held fixed.
-__global__ void __launch_bounds__(kBlock) k_backward_interior(SceneView s, Opts op, const int32_t* tape_tri,
+__device__ __forceinline__ void interior_block(const SceneView& s, const Opts& op, const int32_t* tape_tri,
                                                               const float2* tape_bary, const float* d_image, Grads gr,
-                                                              int G) {
+                                                              int G, int64_t blk) {
   int lane = threadIdx.x & 31;
-  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t gw = (blk * kBlock + threadIdx.x) >> 5;
   int ppw = 32 / G;
   int64_t pix = gw * ppw + lane / G;
   int npix = s.W * s.H;
@@ -568,7 +576,7 @@ __global__ void __launch_bounds__(kBlock) k_backward_interior(SceneView s, Opts 
         }
         float3 dp = zero3(), dn = zero3();
         if (s.L > 0) {
-          uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kLight, 0u, kPassInterior, 0u);
+          uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kLight, 0u, kPassInterior, op.scene_id);
           LightSample ls;
           sample_light(s, r, ls);
           bool vis = c.vis;
@@ -630,7 +638,12 @@ __global__ void __launch_bounds__(kBlock) k_backward_interior(SceneView s, Opts 
     scatter3(gr.verts, lid1, dl1, have_light);
     scatter3(gr.verts, lid2, dl2, have_light);
   }
-  block_globals(g, gr.partials, false);
+  block_globals(g, gr.partials + blk * kGlobals, false);
+}
+__global__ void __launch_bounds__(kBlock) k_backward_interior(SceneView s, Opts op, const int32_t* tape_tri,
+                                                              const float2* tape_bary, const float* d_image, Grads gr,
+                                                              int G) {
+  interior_block(s, op, tape_tri, tape_bary, d_image, gr, G, blockIdx.x);
 }
 
 // Could a ray from o along d reach a light triangle?  Conservative slab test
@@ -658,11 +671,11 @@ __device__ __forceinline__ bool may_reach_light(const SceneView& s, const float 
 // measure), so a side ray that cannot reach a light, or that leaves below the
 // shading horizon by more than the side offset, contributes exactly nothing
 // and is not traced.
-__global__ void __launch_bounds__(kBlock) k_backward_secondary(SceneView s, Opts op, const int32_t* tape_tri,
+__device__ __forceinline__ void secondary_block(const SceneView& s, const Opts& op, const int32_t* tape_tri,
                                                                const float2* tape_bary, const float* d_image, Grads gr,
-                                                               int G, int rows_written) {
+                                                               int G, int rows_written, int64_t blk) {
   int lane = threadIdx.x & 31;
-  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t gw = (blk * kBlock + threadIdx.x) >> 5;
   int ppw = 32 / G;
   int64_t pix = gw * ppw + lane / G;
   int npix = s.W * s.H;
@@ -687,7 +700,7 @@ __global__ void __launch_bounds__(kBlock) k_backward_secondary(SceneView s, Opts
     if (active && c.k >= 0) {
       Vertex x;
       load_vertex(s, c.k, c.b1, c.b2, c.d, x);
-      uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kEdgeSecondary, 0u, kPassInterior, 0u);
+      uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kEdgeSecondary, 0u, kPassInterior, op.scene_id);
       int e = cdf_pick(s.scdf, s.E, dm(u01d(r.x, r.y), stotal));
       double le = s.scdf[e] - (e > 0 ? s.scdf[e - 1] : 0.0);
       float t = u01f(r.z);
@@ -775,7 +788,12 @@ __global__ void __launch_bounds__(kBlock) k_backward_secondary(SceneView s, Opts
     for (int sd = 0; sd < 2; ++sd)
       for (int q = 0; q < 3; ++q) scatter3(gr.verts, mids[sd][q], dmv[sd][q], have_m[sd]);
   }
-  block_globals(g, gr.partials, rows_written != 0);
+  block_globals(g, gr.partials + blk * kGlobals, rows_written != 0);
+}
+__global__ void __launch_bounds__(kBlock) k_backward_secondary(SceneView s, Opts op, const int32_t* tape_tri,
+                                                               const float2* tape_bary, const float* d_image, Grads gr,
+                                                               int G, int rows_written) {
+  secondary_block(s, op, tape_tri, tape_bary, d_image, gr, G, rows_written, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -789,7 +807,7 @@ __device__ __forceinline__ float3 nee_adjoint(const SceneView& s, const Opts& op
                                               const Vertex& x, float3 n, float3 alb, float3 ab, float3 Le,
                                               float g[kGlobals], float3& dalb, float3& dp, float3& dn, float3 dl[3],
                                               int lid[3], bool& have_light) {
-  uint4 r = rng4(op.key, c0, c1, kLight, (uint32_t)b, kPassInterior, 0u);
+  uint4 r = rng4(op.key, c0, c1, kLight, (uint32_t)b, kPassInterior, op.scene_id);
   LightSample ls;
   sample_light(s, r, ls);
   float3 p = f3(x.p);
@@ -852,7 +870,7 @@ __device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Op
     for (int i = 0; i < 3; ++i) { so.dm[q][i] = zero3(); so.mid[q][i] = 0; }
   }
   double stotal = s.scdf[s.E - 1];
-  uint4 r = rng4(op.key, c0, c1, kEdgeSecondary, (uint32_t)b, kPassInterior, 0u);
+  uint4 r = rng4(op.key, c0, c1, kEdgeSecondary, (uint32_t)b, kPassInterior, op.scene_id);
   int e = cdf_pick(s.scdf, s.E, dm(u01d(r.x, r.y), stotal));
   double le = s.scdf[e] - (e > 0 ? s.scdf[e - 1] : 0.0);
   float t = u01f(r.z);
@@ -941,11 +959,11 @@ __device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Op
   so.eid1 = ev.y;
 }
 
-__global__ void __launch_bounds__(kBlock) k_backward_path(SceneView s, Opts op, const int32_t* tape_tri,
+__device__ __forceinline__ void path_block(const SceneView& s, const Opts& op, const int32_t* tape_tri,
                                                           const float2* tape_bary, const float* d_image, Grads gr,
-                                                          int G) {
+                                                          int G, int64_t blk) {
   int lane = threadIdx.x & 31;
-  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t gw = (blk * kBlock + threadIdx.x) >> 5;
   int ppw = 32 / G;
   int64_t pix = gw * ppw + lane / G;
   int npix = s.W * s.H;
@@ -992,7 +1010,7 @@ __global__ void __launch_bounds__(kBlock) k_backward_path(SceneView s, Opts op, 
         load_vertex(s, kk[b], bb1[b], bb2[b], d, x);
         float n32[3];
         shading_normal32(x, n32);
-        uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kBsdf, (uint32_t)b, kPassInterior, 0u);
+        uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kBsdf, (uint32_t)b, kPassInterior, op.scene_id);
         float nd[3];
         cosine_dir(n32, u01f(r.x), u01f(r.y), nd);
         if (!(dot(f3(n32), f3(nd)) > 0.f)) break;
@@ -1066,7 +1084,12 @@ __global__ void __launch_bounds__(kBlock) k_backward_path(SceneView s, Opts op, 
         for (int i = 0; i < 3; ++i) scatter3(gr.verts, so.mid[q][i], so.dm[q][i], so.have_m[q]);
     }
   }
-  block_globals(g, gr.partials, false);
+  block_globals(g, gr.partials + blk * kGlobals, false);
+}
+__global__ void __launch_bounds__(kBlock) k_backward_path(SceneView s, Opts op, const int32_t* tape_tri,
+                                                          const float2* tape_bary, const float* d_image, Grads gr,
+                                                          int G) {
+  path_block(s, op, tape_tri, tape_bary, d_image, gr, G, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1083,7 +1106,7 @@ struct EdgeSample {
 // Plain sampler: edge by clipped length, uniform point.  Learned proposal:
 // tile segment by the mixture CDF, uniform point on the segment.
 __device__ __forceinline__ EdgeSample primary_sample(const SceneView& s, const Opts& op, int64_t j, double ptotal) {
-  uint4 r = rng4(op.key, (uint32_t)j, 0u, kEdgePrimary, 0u, kPassPrimaryEdge, 0u);
+  uint4 r = rng4(op.key, (uint32_t)j, 0u, kEdgePrimary, 0u, kPassPrimaryEdge, op.scene_id);
   EdgeSample es;
   float t0, t1;
   es.valid = true;
@@ -1143,9 +1166,9 @@ __global__ void k_primary_keys(SceneView s, Opts op, int64_t n_edge, uint32_t* k
   keys[j] = key;
   vals[j] = (int32_t)j;
 }
-__global__ void __launch_bounds__(kBlock, 2) k_backward_primary(SceneView s, Opts op, const float* d_image, Grads gr,
+__device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op, const float* d_image, Grads gr,
                                                              int64_t n_edge, int64_t per_thread,
-                                                             const int32_t* order) {
+                                                             const int32_t* order, int64_t blk) {
   float g[kGlobals];
   for (int i = 0; i < kGlobals; ++i) g[i] = 0.f;
   double ptotal = s.pcdf[s.E - 1];
@@ -1153,7 +1176,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_backward_primary(SceneView s, Opt
   float eps = fm(op.eps_rel, fmaxf(W, H));
   for (int64_t it = 0; it < per_thread; ++it) {
     // consecutive threads take consecutive entries of the screen-ordered list
-    int64_t i = (int64_t)blockIdx.x * blockDim.x * per_thread + it * blockDim.x + threadIdx.x;
+    int64_t i = blk * kBlock * per_thread + it * kBlock + threadIdx.x;
     int64_t j = i < n_edge ? (order ? (int64_t)order[i] : i) : n_edge;
     bool active = j < n_edge && ptotal > 0.0 && j >= op.edge_begin && j < op.edge_end;
     float3 da3 = zero3(), db3 = zero3();
@@ -1194,7 +1217,12 @@ __global__ void __launch_bounds__(kBlock, 2) k_backward_primary(SceneView s, Opt
     scatter3(gr.verts, ia, da3, active);
     scatter3(gr.verts, ib, db3, active);
   }
-  block_globals(g, gr.partials, false);
+  block_globals(g, gr.partials + blk * kGlobals, false);
+}
+__global__ void __launch_bounds__(kBlock, 2) k_backward_primary(SceneView s, Opts op, const float* d_image, Grads gr,
+                                                             int64_t n_edge, int64_t per_thread,
+                                                             const int32_t* order) {
+  primary_block(s, op, d_image, gr, n_edge, per_thread, order, blockIdx.x);
 }
 
 __global__ void k_debug_closest(SceneView s, int64_t n, const float* o, const float* d, int32_t* tri, float* tb) {
@@ -1214,7 +1242,189 @@ int group_size(int spp) {
   return G;
 }
 
+// ---------------------------------------------------------------------------
+// Batched scenes: persistent kernels over (scene, virtual block) items.  A
+// virtual block is exactly the work of one block of the single-scene launch
+// (same pixels or samples, same partial-sum row), so every image and every
+// partial row of a batch equals the single-scene result.  CTAs take chunks of
+// items from an atomic counter until the items run out (no waiting).
+// ---------------------------------------------------------------------------
+// Scene of an item: the last k with prefix[k] <= item (prefix[0] = 0; a scene
+// without items has prefix[k] == prefix[k+1] and is never returned).
+__device__ __forceinline__ int batch_scene_of(const int64_t* prefix, int n, int64_t item) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int PH>
+struct PhaseMinBlocks {
+  // two resident CTAs per SM (128 registers), as the single-scene kernels
+  // have; the depth > 1 path pass needs more registers
+  static constexpr int value = PH == kPhasePath ? 1 : 2;
+};
+
+template <int PH>
+__global__ void __launch_bounds__(kBlock, PhaseMinBlocks<PH>::value)
+    k_batch(const BatchScene* bs, const int64_t* prefix, int n, int64_t n_items, int chunk,
+            unsigned long long* counter) {
+  __shared__ __align__(16) BatchScene sb;
+  __shared__ long long s_item;
+  int cur = -1;
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, (unsigned long long)chunk);
+    __syncthreads();
+    long long it0 = s_item;
+    if (it0 >= n_items) break;
+    long long it1 = it0 + chunk < n_items ? it0 + chunk : n_items;
+    for (long long it = it0; it < it1; ++it) {
+      int sc = batch_scene_of(prefix, n, it);
+      if (sc != cur) {  // same value in every thread
+        __syncthreads();
+        const int* src = reinterpret_cast<const int*>(bs + sc);
+        int* dst = reinterpret_cast<int*>(&sb);
+        for (int w = threadIdx.x; w < (int)(sizeof(BatchScene) / 4); w += kBlock) dst[w] = src[w];
+        __syncthreads();
+        cur = sc;
+      }
+      int64_t blk = it - prefix[sc];
+      if (PH == kPhaseRender) {
+        render_block(sb.v, sb.op, sb.image, sb.tape_tri, sb.tape_bary, sb.G, blk);
+      } else if (PH == kPhaseInterior) {
+        interior_block(sb.v, sb.op, sb.tape_tri, sb.tape_bary, sb.d_image, Grads{sb.d_verts, sb.d_albedo, sb.partials},
+                       sb.G, blk);
+      } else if (PH == kPhaseSecondary) {
+        secondary_block(sb.v, sb.op, sb.tape_tri, sb.tape_bary, sb.d_image,
+                        Grads{sb.d_verts, sb.d_albedo, sb.partials}, sb.G, sb.rows_written, blk);
+      } else if (PH == kPhasePath) {
+        path_block(sb.v, sb.op, sb.tape_tri, sb.tape_bary, sb.d_image, Grads{sb.d_verts, sb.d_albedo, sb.partials},
+                   sb.G, blk);
+      } else {
+        primary_block(sb.v, sb.op, sb.d_image, Grads{sb.d_verts, sb.d_albedo, sb.partials + sb.rows_i * kGlobals},
+                      sb.n_edge, sb.per_thread, sb.order, blk);
+      }
+    }
+  }
+}
+
+// Screen keys of the primary edge samples of all scenes, scene index in the
+// high bits: one stable sort orders every scene's samples exactly as the
+// single-scene sort does.  vals = index of the sample within its scene.
+__global__ void k_batch_keys(const BatchScene* bs, const int64_t* eprefix, int n, int64_t total, int pix_bits,
+                             uint32_t* keys, int32_t* vals) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  int sc = batch_scene_of(eprefix, n, g);
+  const SceneView& s = bs[sc].v;
+  int64_t j = g - eprefix[sc];
+  double ptotal = s.pcdf[s.E - 1];
+  uint32_t key = 0;
+  if (ptotal > 0.0) {
+    EdgeSample es = primary_sample(s, bs[sc].op, j, ptotal);
+    int px = min(max((int)floorf(es.x), 0), s.W - 1), py = min(max((int)floorf(es.y), 0), s.H - 1);
+    key = spread_bits16((uint32_t)px) | (spread_bits16((uint32_t)py) << 1);
+  }
+  keys[g] = ((uint32_t)sc << pix_bits) | key;
+  vals[g] = (int32_t)j;
+}
+
+// One block per scene: the fixed-order reduction of its partial rows.
+__global__ void k_batch_reduce(const BatchScene* bs) {
+  const BatchScene& b = bs[blockIdx.x];
+  int rows = (int)(b.rows_i + b.blocks_e);
+  if (b.d_image == nullptr || rows == 0) return;
+  reduce_globals(b.partials, rows, b.d_radiance, b.d_cam, b.d_scale);
+}
+
+template <int PH>
+cudaError_t launch_phase(const BatchScene* bs, const int64_t* prefix, int n, int64_t n_items, int grid, int chunk,
+                         unsigned long long* counter, cudaStream_t st) {
+  k_batch<PH><<<grid, kBlock, 0, st>>>(bs, prefix, n, n_items, chunk, counter);
+  return cudaGetLastError();
+}
+
+template <int PH>
+int phase_occupancy() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<PH>, kBlock, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb > 0 ? nb : 1;
+}
+
 }  // namespace
+
+int pixel_group(int spp) { return group_size(spp); }
+
+int64_t pixel_blocks(int W, int H, int spp) {
+  int G = group_size(spp);
+  int64_t warps = ((int64_t)W * H + (32 / G) - 1) / (32 / G);
+  return (warps * 32 + kBlock - 1) / kBlock;
+}
+
+void primary_blocks(int64_t n_edge, int64_t* blocks_e, int64_t* per_thread) {
+  *blocks_e = std::min<int64_t>((n_edge + kBlock - 1) / kBlock, 152 * 16);
+  *per_thread = *blocks_e > 0 ? (n_edge + *blocks_e * kBlock - 1) / (*blocks_e * kBlock) : 0;
+}
+
+int screen_key_bits(int W, int H) {
+  int bits = 2;
+  while ((1 << (bits / 2)) < std::max(W, H)) bits += 2;
+  return bits;
+}
+
+cudaError_t launch_batch_phase(int phase, const BatchScene* bs, const int64_t* prefix, int n, int64_t n_items,
+                               int grid, int chunk, unsigned long long* counter, cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  static const char* names[kPhases] = {"batch_render", "batch_backward_interior", "batch_backward_secondary_edges",
+                                       "batch_backward_path", "batch_backward_primary_edges"};
+  ProfToken pt = prof_begin(names[phase], st);
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) {
+    switch (phase) {
+      case kPhaseRender: e = launch_phase<kPhaseRender>(bs, prefix, n, n_items, grid, chunk, counter, st); break;
+      case kPhaseInterior: e = launch_phase<kPhaseInterior>(bs, prefix, n, n_items, grid, chunk, counter, st); break;
+      case kPhaseSecondary:
+        e = launch_phase<kPhaseSecondary>(bs, prefix, n, n_items, grid, chunk, counter, st);
+        break;
+      case kPhasePath: e = launch_phase<kPhasePath>(bs, prefix, n, n_items, grid, chunk, counter, st); break;
+      default: e = launch_phase<kPhasePrimary>(bs, prefix, n, n_items, grid, chunk, counter, st); break;
+    }
+  }
+  prof_end(pt, st);
+  return e;
+}
+
+int batch_phase_occupancy(int phase) {
+  switch (phase) {
+    case kPhaseRender: return phase_occupancy<kPhaseRender>();
+    case kPhaseInterior: return phase_occupancy<kPhaseInterior>();
+    case kPhaseSecondary: return phase_occupancy<kPhaseSecondary>();
+    case kPhasePath: return phase_occupancy<kPhasePath>();
+    default: return phase_occupancy<kPhasePrimary>();
+  }
+}
+
+cudaError_t launch_batch_keys(const BatchScene* bs, const int64_t* eprefix, int n, int64_t total, int pix_bits,
+                              uint32_t* keys, int32_t* vals, cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  DRT_PROF_LAUNCH("batch_primary_keys", st,
+                  k_batch_keys<<<(unsigned)((total + kBlock - 1) / kBlock), kBlock, 0, st>>>(bs, eprefix, n, total,
+                                                                                              pix_bits, keys, vals));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_reduce(const BatchScene* bs, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  DRT_PROF_LAUNCH("batch_reduce_globals", st, k_batch_reduce<<<n, 32 * kGlobals, 0, st>>>(bs));
+  return cudaGetLastError();
+}
 
 cudaError_t launch_render(const drt_scene* sc, const Opts& op, float* image, drt_tape* tape, cudaStream_t st) {
   SceneView s = sc->view();
@@ -1241,10 +1451,7 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
   int64_t blocks_i = (warps * 32 + kBlock - 1) / kBlock;
   int64_t n_edge = (int64_t)op.edge_spp * npix;
   int64_t blocks_e = 0, per_thread = 0;
-  if ((op.terms & 2) && s.E > 0 && n_edge > 0) {
-    blocks_e = std::min<int64_t>((n_edge + kBlock - 1) / kBlock, 152 * 16);
-    per_thread = (n_edge + blocks_e * kBlock - 1) / (blocks_e * kBlock);
-  }
+  if ((op.terms & 2) && s.E > 0 && n_edge > 0) primary_blocks(n_edge, &blocks_e, &per_thread);
   Grads gr{d_verts, d_albedo, partials};
   bool need_i = (op.terms & 5) != 0;
   const int32_t* tt = tape ? tape->tri : nullptr;
@@ -1276,8 +1483,7 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
   if (blocks_e > 0) {
     const int32_t* order = nullptr;
     if (sort && sort->cap >= n_edge) {
-      int bits = 2;
-      while ((1 << (bits / 2)) < std::max(s.W, s.H)) bits += 2;
+      int bits = screen_key_bits(s.W, s.H);
       DRT_PROF_LAUNCH("primary_keys", st,
                       k_primary_keys<<<(unsigned)((n_edge + kBlock - 1) / kBlock), kBlock, 0, st>>>(
                           s, op, n_edge, sort->keys, sort->vals));
@@ -1313,7 +1519,8 @@ int64_t backward_partial_rows(const drt_scene* sc, const Opts& op) {
   int64_t warps = ((int64_t)npix + (32 / G) - 1) / (32 / G);
   int64_t blocks_i = (warps * 32 + kBlock - 1) / kBlock;
   int64_t n_edge = (int64_t)op.edge_spp * npix;
-  int64_t blocks_e = std::min<int64_t>((n_edge + kBlock - 1) / kBlock, 152 * 16);
+  int64_t blocks_e = 0, per_thread = 0;
+  primary_blocks(n_edge, &blocks_e, &per_thread);
   return blocks_i + blocks_e;
 }
 

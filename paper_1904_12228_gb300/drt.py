@@ -25,7 +25,9 @@ EXPORTED = ("drt_create", "drt_destroy", "drt_scene_upload", "drt_scene_update_v
             "drt_scene_free", "drt_render", "drt_render_backward", "drt_tape_free", "drt_check_device",
             "drt_last_error", "drt_version", "drt_debug_closest", "drt_profile_enable", "drt_profile_read",
             "drt_counters_enable", "drt_counters_read", "drt_render_backward_noalloc", "drt_scene_segments",
-            "drt_mlp_forward", "drt_mlp_backward", "drt_adam_step", "drt_segment_features")
+            "drt_mlp_forward", "drt_mlp_backward", "drt_adam_step", "drt_segment_features", "drt_batch_create",
+            "drt_batch_run", "drt_batch_get_info", "drt_batch_free", "drt_render_batch")
+BATCH_PASSES = ("render", "interior", "secondary", "path", "primary")
 
 
 class DrtError(RuntimeError):
@@ -46,7 +48,7 @@ class RenderOpts(ctypes.Structure):
     _fields_ = [("spp", ctypes.c_int32), ("edge_spp", ctypes.c_int32), ("max_depth", ctypes.c_int32),
                 ("primary_only", ctypes.c_int32), ("seed", ctypes.c_uint64), ("eps_rel", ctypes.c_float),
                 ("terms", ctypes.c_int32), ("proposal", ctypes.c_int32), ("seg_weights", ctypes.c_void_p),
-                ("n_seg_weights", ctypes.c_int64), ("seg_log", ctypes.c_void_p)]
+                ("n_seg_weights", ctypes.c_int64), ("seg_log", ctypes.c_void_p), ("scene_id", ctypes.c_int32)]
 
 
 class MlpWeights(ctypes.Structure):
@@ -62,6 +64,17 @@ class MlpGrads(ctypes.Structure):
 class Grads(ctypes.Structure):
     _fields_ = [("d_verts", ctypes.c_void_p), ("d_albedo", ctypes.c_void_p), ("d_radiance", ctypes.c_void_p),
                 ("d_cam_to_world", ctypes.c_void_p), ("d_cam_scale", ctypes.c_void_p)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_void_p), ("image", ctypes.c_void_p), ("d_image", ctypes.c_void_p),
+                ("grads", Grads), ("verts", ctypes.c_void_p)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_int32 * 5), ("grid", ctypes.c_int32 * 5), ("chunk", ctypes.c_int32 * 5),
+                ("edge_per_thread_mult", ctypes.c_int32), ("graph", ctypes.c_int32), ("tuned", ctypes.c_int32),
+                ("items", ctypes.c_int64 * 5), ("edge_samples", ctypes.c_int64), ("tune_ms", ctypes.c_double)]
 
 
 _LIB = None
@@ -109,6 +122,11 @@ def load(build_if_missing: bool = True):
         "drt_profile_read": ([vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(ctypes.c_int)], i32),
         "drt_counters_enable": ([vp, ctypes.c_int], i32),
         "drt_counters_read": ([vp, vp], i32),
+        "drt_batch_create": ([vp, ctypes.POINTER(BatchItem), i32, ctypes.POINTER(RenderOpts), i32, i32, pp], i32),
+        "drt_batch_run": ([vp, vp, vp], i32),
+        "drt_batch_get_info": ([vp, vp, ctypes.POINTER(BatchInfo)], i32),
+        "drt_batch_free": ([vp, vp], i32),
+        "drt_render_batch": ([vp, pp, i32, ctypes.POINTER(RenderOpts), pp, pp, ctypes.POINTER(Grads), vp], i32),
         "drt_last_error": ([], ctypes.c_char_p),
         "drt_version": ([], ctypes.c_char_p),
     }
@@ -153,7 +171,7 @@ def _stream(stream):
 
 
 def make_opts(spp, edge_spp=None, max_depth=1, primary_only=False, seed=0, eps_rel=0.0, terms=0,
-              seg_weights=None, seg_log=None, seg_scores=None) -> RenderOpts:
+              seg_weights=None, seg_log=None, seg_scores=None, scene_id=0) -> RenderOpts:
     """seg_weights: a CUDA float32 tensor of per-segment weights selects the
     mixture proposal 1; seg_scores: per-segment network scores select the
     mixture proposal 2.  The tensor must stay alive until the backward call
@@ -165,7 +183,7 @@ def make_opts(spp, edge_spp=None, max_depth=1, primary_only=False, seed=0, eps_r
     return RenderOpts(int(spp), int(spp if edge_spp is None else edge_spp), int(max_depth), int(bool(primary_only)),
                       int(seed) & (2 ** 64 - 1), float(eps_rel), int(terms), mode,
                       _ptr(w) if w is not None else None, n,
-                      _ptr(seg_log) if seg_log is not None else None)
+                      _ptr(seg_log) if seg_log is not None else None, int(scene_id))
 
 
 class Context:
@@ -365,3 +383,65 @@ class Scene:
         _check(self.ctx.lib.drt_render_backward(self.ctx.handle, self.handle, tape.handle if tape else None,
                                                 ctypes.byref(opts), _ptr(d_image), ctypes.byref(g),
                                                 _stream(stream)))
+
+
+def _grads_of(g):
+    g = g or {}
+    return Grads(_ptr(g.get("d_verts")), _ptr(g.get("d_albedo")), _ptr(g.get("d_radiance")),
+                 _ptr(g.get("d_cam_to_world")), _ptr(g.get("d_cam_scale")))
+
+
+class Batch:
+    """Many scenes rendered and differentiated per step (drt_batch_* in
+    include/drt.h).  images[k], d_images[k] (or None), grads[k] (a dict of
+    gradient tensors, or None) and verts[k] (or None) are device tensors that
+    must stay alive with the batch; scene k samples with scene_id k."""
+
+    def __init__(self, ctx: Context, scenes, images, opts: RenderOpts, d_images=None, grads=None, verts=None,
+                 use_graph=True, autotune=True):
+        n = len(scenes)
+        self.ctx, self.handle = ctx, None
+        self._keep = (list(scenes), list(images), d_images, grads, verts, opts)
+        arr = (BatchItem * n)()
+        for k in range(n):
+            arr[k].scene = scenes[k].handle.value
+            arr[k].image = _ptr(images[k])
+            arr[k].d_image = _ptr(d_images[k]) if d_images is not None else None
+            arr[k].grads = _grads_of(grads[k] if grads is not None else None)
+            arr[k].verts = _ptr(verts[k]) if verts is not None else None
+        h = ctypes.c_void_p()
+        _check(ctx.lib.drt_batch_create(ctx.handle, arr, n, ctypes.byref(opts), int(bool(use_graph)),
+                                        int(bool(autotune)), ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, stream=None):
+        _check(self.ctx.lib.drt_batch_run(self.ctx.handle, self.handle, _stream(stream)))
+
+    def info(self) -> dict:
+        i = BatchInfo()
+        _check(self.ctx.lib.drt_batch_get_info(self.ctx.handle, self.handle, ctypes.byref(i)))
+        per = {nm: dict(ctas_per_sm=i.ctas_per_sm[p], grid=i.grid[p], chunk=i.chunk[p], items=i.items[p])
+               for p, nm in enumerate(BATCH_PASSES)}
+        return dict(passes=per, edge_per_thread_mult=i.edge_per_thread_mult, graph=bool(i.graph),
+                    tuned=bool(i.tuned), edge_samples=i.edge_samples, tune_ms=i.tune_ms)
+
+    def free(self):
+        if self.handle:
+            self.ctx.lib.drt_batch_free(self.ctx.handle, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def render_batch(ctx: Context, scenes, images, opts: RenderOpts, d_images=None, grads=None, stream=None):
+    """One-shot batch (no graph, no tuning); synchronises the stream."""
+    n = len(scenes)
+    sc = (ctypes.c_void_p * n)(*[s.handle.value for s in scenes])
+    im = (ctypes.c_void_p * n)(*[_ptr(x) for x in images])
+    di = (ctypes.c_void_p * n)(*[_ptr(x) for x in d_images]) if d_images is not None else None
+    gr = (Grads * n)(*[_grads_of(g) for g in grads]) if grads is not None else None
+    _check(ctx.lib.drt_render_batch(ctx.handle, sc, n, ctypes.byref(opts), im, di, gr, _stream(stream)))

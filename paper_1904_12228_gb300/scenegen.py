@@ -236,6 +236,20 @@ def procedural(seed: int, n_target: int = 200_000, width: int = 512, height: int
                  cam_scale=math.tan(math.radians(22.5)), cam_type=CAM_PINHOLE, width=width, height=height)
 
 
+def batch_workload(seed: int, n: int = 64, t_min: int = 1000, t_max: int = 100_000,
+                   resolutions=(128, 256, 512)) -> list:
+    """n procedural scenes (the generator above, direct lighting when
+    rendered at depth 1): triangle count log-uniform in [t_min, t_max],
+    square resolution drawn uniformly from `resolutions`."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        t = int(round(math.exp(rng.uniform(math.log(t_min), math.log(t_max)))))
+        res = int(rng.choice(np.asarray(resolutions)))
+        out.append(procedural(seed * 1000 + k, n_target=t, width=res, height=res))
+    return out
+
+
 def perturb_vertices(scene: Scene, seed: int, sigma: float = 0.02) -> np.ndarray:
     """Vertex positions + N(0, sigma) (the inverse-rendering start point)."""
     rng = np.random.default_rng(seed + 104729)
