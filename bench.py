@@ -13,7 +13,9 @@ scatter).  Inputs are synthetic and seeded.
 The second half of the metric, gradient variance x time of the learned
 edge proposal against the plain edge sampler, comes from the proposal
 module's protocol (train on logs of 20 scenes, score 4 held-out scenes) and
-is reported under "variance_x_time" (N=1; --no-proposal skips it).
+is reported under "variance_x_time" (N=1; --no-proposal skips it).  The
+64-scene batched workload (persistent launches in a CUDA graph) is reported
+under "batched" (N=1; --no-batched skips it).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -38,6 +40,7 @@ METRIC = "fwd+bwd samples/sec and gradient variance x time vs plain edge sampler
 UNIT = "samples/s"
 W_IMG, H_IMG, SPP, EDGE_SPP = 256, 256, 64, 64
 SCENE_SEED = 1236
+BATCH_SEED, BATCH_SPP = 1238, 16
 WORKLOAD = ("direct lighting 256x256: jittered icosphere (5120 tris) + 2-tri ground + 2-tri area light; "
             "64 spp with 1 shadow ray, 64 primary edge spp, 1 secondary edge sample per path vertex; "
             "step = vertex update (LBVH + edge CDFs) + render + backward (all gradient terms)")
@@ -127,6 +130,76 @@ class ClockSampler:
                 "reasons": seen, "samples": len(rows)}
 
 
+def run_batched(ctx, dev, replays=20):
+    """64 procedural scenes (1k-100k triangles, log-uniform; 128^2-512^2;
+    direct lighting, 16 spp + 16 edge spp) as one batch step: persistent
+    launches captured in a CUDA graph, launch shapes autotuned.  Median of
+    `replays` graph replays, against the same scenes issued one render and
+    one backward call at a time.  The BVHs, tapes and sort buffers (several
+    GB) exceed the 129 MB L2, so no flush is needed between replays."""
+    import torch
+    from paper_1904_12228_gb300 import drt
+    from paper_1904_12228_gb300 import scenegen as sg
+    scenes = sg.batch_workload(BATCH_SEED)
+    up = [drt.Scene.from_arrays(ctx, sc) for sc in scenes]
+    d_images = [torch.from_numpy(sg.loss_adjoint(BATCH_SEED + k, sc.width, sc.height)).to(dev)
+                for k, sc in enumerate(scenes)]
+    imgs = [torch.zeros((sc.height, sc.width, 3), device=dev) for sc in scenes]
+
+    def zeros_like_grads(sc):
+        return dict(d_verts=torch.zeros((len(sc.verts), 3), device=dev),
+                    d_albedo=torch.zeros((len(sc.tris), 3), device=dev), d_radiance=torch.zeros(3, device=dev),
+                    d_cam_to_world=torch.zeros((3, 4), device=dev), d_cam_scale=torch.zeros(1, device=dev))
+    grads = [zeros_like_grads(sc) for sc in scenes]
+    opts = drt.make_opts(BATCH_SPP, BATCH_SPP, seed=7)
+    t0 = time.perf_counter()
+    b = drt.Batch(ctx, up, imgs, opts, d_images=d_images, grads=grads, use_graph=True, autotune=True)
+    b.run()
+    torch.cuda.synchronize()
+    first_s = time.perf_counter() - t0
+    for _ in range(2):
+        b.run()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(replays)]
+    for e0, e1 in ev:
+        e0.record()
+        b.run()
+        e1.record()
+    torch.cuda.synchronize()
+    ms = statistics.median(e0.elapsed_time(e1) for e0, e1 in ev)
+    code, info = ctx.check_device()
+    if code != 0:
+        raise RuntimeError("device error flag %d (%d) in the batched workload" % (code, info))
+    # the same work as separate calls (same scene ids, tapes reused)
+    tapes = [None] * len(scenes)
+    for k, s in enumerate(up):
+        tapes[k] = s.render(imgs[k], drt.make_opts(BATCH_SPP, BATCH_SPP, seed=7, scene_id=k), want_tape=True)
+    single = []
+    for rep in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k, s in enumerate(up):
+            o = drt.make_opts(BATCH_SPP, BATCH_SPP, seed=7, scene_id=k)
+            s.render(imgs[k], o, reuse=tapes[k])
+            s.backward(d_images[k], o, tape=tapes[k], **grads[k])
+        e1.record()
+        torch.cuda.synchronize()
+        single.append(e0.elapsed_time(e1))
+    single_ms = statistics.median(single)
+    samples = sum(sc.width * sc.height * BATCH_SPP for sc in scenes)
+    inf = b.info()
+    b.free()
+    for t in tapes:
+        t.free()
+    return {"workload": "64 procedural scenes, triangles log-uniform in [1k,100k], resolution from {128,256,512}, "
+                        "direct lighting, 16 spp + 16 primary edge spp, all gradient terms",
+            "scenes": len(scenes), "triangles": int(sum(len(sc.tris) for sc in scenes)),
+            "pixels": int(sum(sc.width * sc.height for sc in scenes)), "samples_per_step": samples,
+            "ms_per_step": ms, "samples_per_s": samples / (ms / 1e3), "replays": replays,
+            "single_calls_ms_per_step": single_ms, "speedup_vs_single_calls": single_ms / ms,
+            "first_run_s": first_s, "launch_shapes": inf, "l2": "working set larger than L2 (no flush)"}
+
+
 def cpu_workload_sample(seconds_target, n_threads):
     """Time the CPU oracle on a bounded sample of the same workload: a block
     of pixels (all spp, interior + secondary edges) and a proportional range
@@ -191,6 +264,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal variance x time part")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-scene batched workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
@@ -323,6 +397,10 @@ def main():
 
     # second half of the metric: gradient variance x time, learned proposal
     # against the plain edge sampler (N=1 only)
+    batched = None
+    if rank == 0 and world == 1 and not args.no_batched:
+        batched = run_batched(ctx, dev)
+
     vxt = None
     if rank == 0 and world == 1 and not args.no_proposal:
         from paper_1904_12228_gb300 import proposal
@@ -342,7 +420,7 @@ def main():
                            "triangles": T, "l2": "flushed between timed steps (256 MiB write)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "rays_per_s": world * rays / (ms_per_step / 1e3),
-                "roofline": roof, "cpu_baseline": cpu, "variance_x_time": vxt,
+                "roofline": roof, "cpu_baseline": cpu, "variance_x_time": vxt, "batched": batched,
                 "e2e": {"value": world * n_samples / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": gpu_launches,
