@@ -232,24 +232,34 @@ def cpu_workload_sample(seconds_target, n_threads):
     return samples / dt, desc, n_threads, dt
 
 
+def bench_config(triangles, world):
+    return {"workload": WORKLOAD, "width": W_IMG, "height": H_IMG, "spp": SPP, "edge_spp": EDGE_SPP,
+            "triangles": triangles, "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
+    from paper_1904_12228_gb300 import scenegen as sg
     oracle.build()
     cores = oracle.n_threads_default()
     per_step = max(1.0, 150.0 / max(1, args.steps + args.warmup))
-    vals = []
+    vals, times = [], []
     desc = ""
     for i in range(args.warmup + args.steps):
         v, desc, cores, dt = cpu_workload_sample(per_step, cores)
         if i >= args.warmup:
             vals.append(v)
+            times.append(dt * 1e3)
     value = statistics.median(vals)
+    config = bench_config(len(sg.direct_lighting(SCENE_SEED).tris), world)
+    config["sample"] = desc
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": desc},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -267,9 +277,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-scene batched workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    rank = int(os.environ.get("RANK", 0))
-    world = int(os.environ.get("WORLD_SIZE", 1))
-    local = int(os.environ.get("LOCAL_RANK", 0))
+    from paper_1904_12228_gb300 import replicas
+    rank, world, local = replicas.rank_info()
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
@@ -286,11 +295,12 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     ctx = drt.Context(local)
-    scene = sg.direct_lighting(SCENE_SEED + rank)
+    scene_seed, adjoint_seed = replicas.replica_seeds(SCENE_SEED, 1, rank)
+    scene = sg.direct_lighting(scene_seed)
     S = drt.Scene.from_arrays(ctx, scene)
     V, T = len(scene.verts), len(scene.tris)
     verts = torch.from_numpy(scene.verts).to(dev)
-    d_image = torch.from_numpy(sg.loss_adjoint(1 + rank, W_IMG, H_IMG)).to(dev)
+    d_image = torch.from_numpy(sg.loss_adjoint(adjoint_seed, W_IMG, H_IMG)).to(dev)
     image = torch.zeros((H_IMG, W_IMG, 3), device=dev)
     g = dict(d_verts=torch.zeros((V, 3), device=dev), d_albedo=torch.zeros((T, 3), device=dev),
              d_radiance=torch.zeros(3, device=dev), d_cam_to_world=torch.zeros((3, 4), device=dev),
@@ -329,13 +339,9 @@ def main():
         dist.barrier()
     prof = ctx.profile_read()
     ctx.profile(False)
-    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = replicas.max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), dist, dev)
     ms_per_step = total_ms / args.steps
-    value = world * n_samples / (ms_per_step / 1e3)
+    value = replicas.aggregate_throughput(n_samples, world, ms_per_step)
 
     # work counters of one extra (untimed) step
     ctx.counters(True)
@@ -386,11 +392,7 @@ def main():
     for k in range(ke):
         e2e_step(k)
     torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / ke
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = replicas.max_over_ranks((time.perf_counter() - t0) * 1e3 / ke, dist, dev)
     grad_bytes = 4 * (3 * V + 3 * T + 3 + 12 + 1)
     h2d = 12 * V + 12 * W_IMG * H_IMG + grad_bytes
     d2h = 12 * W_IMG * H_IMG + grad_bytes
@@ -416,12 +418,11 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "width": W_IMG, "height": H_IMG, "spp": SPP, "edge_spp": EDGE_SPP,
-                           "triangles": T, "l2": "flushed between timed steps (256 MiB write)",
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "config": bench_config(T, world),
                 "rays_per_s": world * rays / (ms_per_step / 1e3),
                 "roofline": roof, "cpu_baseline": cpu, "variance_x_time": vxt, "batched": batched,
-                "e2e": {"value": world * n_samples / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                "e2e": {"value": replicas.aggregate_throughput(n_samples, world, e2e_ms), "unit": UNIT,
+                        "ms_per_step": e2e_ms,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": gpu_launches,
                 "kernels": {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items()},

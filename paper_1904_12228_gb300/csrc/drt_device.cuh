@@ -44,6 +44,7 @@ constexpr float kNearZ = 1e-4f;        // camera depth below which a vertex is b
 constexpr float kShadowTmax = 0.9999f; // shadow rays stop short of the light point
 constexpr float kInvPi = 0.318309886f;
 constexpr int kStackSize = 64;
+constexpr int kTraceWarps = 8;  // warps per CTA that the warp-cooperative traversals support
 constexpr float kTile = 16.0f;  // screen tile of the segment split, pixels
 // BVH leaves hold up to kLeafMax consecutive triangles of the leaf-order soup;
 // a leaf child is encoded as ~(first | (count-1) << 28).
@@ -688,6 +689,198 @@ __device__ __forceinline__ void trace_any2(const SceneView& s, const float o0[3]
     }
     if (sp == 0) break;
     node = stack[--sp];
+  }
+  count_trace(s, kCntAny, n_nodes, n_tris);
+}
+
+// ---------------------------------------------------------------------------
+// Warp-cooperative traversals.  The 32 lanes of a warp walk one tree
+// traversal together: the union of the nodes their rays enter, in one order,
+// with one stack in shared memory.  Control flow is uniform across the warp
+// and every node is one broadcast load.  Each lane tracks whether its own
+// rays enter the current node (a bit per stack entry) and tests only those
+// boxes and triangles.  The results equal the per-lane traversals: the
+// closest hit with ties to the lowest id, and the existence of an occluder,
+// do not depend on the order in which nodes are visited.  All 32 lanes must
+// call together, converged, in a CTA of at most kTraceWarps warps.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void trace_closest2_warp(const SceneView& s, const float o0[3], const float d0[3],
+                                                    const float o1[3], const float d1[3], bool act0, bool act1,
+                                                    int ex0, int ex1, Hit& h0, Hit& h1) {
+  __shared__ int wstack[kTraceWarps][kStackSize];
+  int* stk = wstack[threadIdx.x >> 5];
+  const unsigned full = 0xffffffffu;
+  const bool lane0 = (threadIdx.x & 31) == 0;
+  RayPre r0, r1;
+  ray_pre(r0, o0, d0);
+  ray_pre(r1, o1, d1);
+  h0.tri = -1; h0.t = INFINITY; h0.b1 = h0.b2 = 0.f;
+  h1.tri = -1; h1.t = INFINITY; h1.b1 = h1.b2 = 0.f;
+  if (!__any_sync(full, act0 || act1)) return;
+  bool in = act0 || act1;       // this lane's rays enter the current node
+  unsigned long long in_stk = 0;  // the same for every stacked node (bit = stack slot)
+  int sp = 0;
+  int node = s.root;
+  int budget = 2 * s.T + 8;
+  int n_nodes = 0, n_tris = 0;
+  while (true) {
+    if (--budget < 0) {
+      if (lane0) raise_flag(s.err, DRT_DEV_TRAVERSAL_CAP, s.T);
+      break;
+    }
+    if (node >= 0) {
+      const float4* n4 = s.nodes + 4 * node;
+      float4 a = __ldg(n4), b = __ldg(n4 + 1), c = __ldg(n4 + 2);
+      int4 ch = __ldg(reinterpret_cast<const int4*>(n4 + 3));
+      float tl0 = INFINITY, tr0 = INFINITY, tl1 = INFINITY, tr1 = INFINITY;
+      bool hl0 = false, hr0 = false, hl1 = false, hr1 = false;
+      if (in) {
+        ++n_nodes;
+        if (act0) slab2(r0, a, b, c, h0.t, &tl0, &hl0, &tr0, &hr0);
+        if (act1) slab2(r1, a, b, c, h1.t, &tl1, &hl1, &tr1, &hr1);
+      }
+      bool hl = hl0 || hl1, hr = hr0 || hr1;
+      float tl = fminf(hl0 ? tl0 : INFINITY, hl1 ? tl1 : INFINITY);
+      float tr = fminf(hr0 ? tr0 : INFINITY, hr1 ? tr1 : INFINITY);
+      unsigned ml = __ballot_sync(full, hl), mr = __ballot_sync(full, hr);
+      if (ml && mr) {
+        // the child most lanes reach first goes first
+        unsigned pl = __ballot_sync(full, hl && (!hr || tl <= tr));
+        unsigned pr = __ballot_sync(full, hr && (!hl || tr < tl));
+        bool left_first = __popc(pl) >= __popc(pr);
+        int nearc = left_first ? ch.x : ch.y, farc = left_first ? ch.y : ch.x;
+        bool near_in = left_first ? hl : hr, far_in = left_first ? hr : hl;
+        if (sp < kStackSize) {
+          if (lane0) stk[sp] = farc;
+          in_stk = far_in ? (in_stk | (1ull << sp)) : (in_stk & ~(1ull << sp));
+          ++sp;
+        } else if (lane0) {
+          raise_flag(s.err, DRT_DEV_STACK_OVERFLOW, node);
+        }
+        node = nearc;
+        in = near_in;
+        continue;
+      } else if (ml) {
+        node = ch.x;
+        in = hl;
+        continue;
+      } else if (mr) {
+        node = ch.y;
+        in = hr;
+        continue;
+      }
+    } else if (in) {
+      int enc = ~node, first = enc & 0x0fffffff, count = (enc >> 28) + 1;
+      for (int q = 0; q < count; ++q) {
+        const float4* t4 = s.soup + 3 * (first + q);
+        float4 p0 = __ldg(t4), p1 = __ldg(t4 + 1), p2 = __ldg(t4 + 2);
+        int id = __float_as_int(p0.w);
+        ++n_tris;
+        float3 v0 = make_float3(p0.x, p0.y, p0.z), v1 = make_float3(p1.x, p1.y, p1.z),
+               v2 = make_float3(p2.x, p2.y, p2.z);
+        float t, b1, b2;
+        if (act0 && id != ex0) {
+          float lim = (h0.tri >= 0 && id < h0.tri) ? __uint_as_float(__float_as_uint(h0.t) + 1u) : h0.t;
+          if (watertight(r0.sh, r0.o, v0, v1, v2, lim, &t, &b1, &b2)) { h0.tri = id; h0.t = t; h0.b1 = b1; h0.b2 = b2; }
+        }
+        if (act1 && id != ex1) {
+          float lim = (h1.tri >= 0 && id < h1.tri) ? __uint_as_float(__float_as_uint(h1.t) + 1u) : h1.t;
+          if (watertight(r1.sh, r1.o, v0, v1, v2, lim, &t, &b1, &b2)) { h1.tri = id; h1.t = t; h1.b1 = b1; h1.b2 = b2; }
+        }
+      }
+    }
+    if (sp == 0) break;
+    --sp;
+    __syncwarp();
+    node = stk[sp];
+    in = (in_stk >> sp) & 1ull;
+  }
+  count_trace(s, kCntClosest, n_nodes, n_tris);
+}
+
+// Warp-cooperative any-hit of two rays per lane (see trace_any2); the warp
+// stops when no lane has a ray left to resolve.
+__device__ __forceinline__ void trace_any2_warp(const SceneView& s, const float o0[3], const float d0[3], int a0x,
+                                                int a0y, const float o1[3], const float d1[3], int a1x, int a1y,
+                                                bool act0, bool act1, float tmax, bool& occ0, bool& occ1) {
+  __shared__ int wstack[kTraceWarps][kStackSize];
+  int* stk = wstack[threadIdx.x >> 5];
+  const unsigned full = 0xffffffffu;
+  const bool lane0 = (threadIdx.x & 31) == 0;
+  occ0 = occ1 = false;
+  RayPre r0, r1;
+  ray_pre(r0, o0, d0);
+  ray_pre(r1, o1, d1);
+  bool live0 = act0, live1 = act1;
+  bool in = live0 || live1;
+  unsigned long long in_stk = 0;
+  int sp = 0;
+  int node = s.root;
+  int budget = 2 * s.T + 8;
+  int n_nodes = 0, n_tris = 0;
+  while (__any_sync(full, live0 || live1)) {
+    if (--budget < 0) {
+      if (lane0) raise_flag(s.err, DRT_DEV_TRAVERSAL_CAP, s.T);
+      break;
+    }
+    if (node >= 0) {
+      const float4* n4 = s.nodes + 4 * node;
+      float4 a = __ldg(n4), b = __ldg(n4 + 1), c = __ldg(n4 + 2);
+      int4 ch = __ldg(reinterpret_cast<const int4*>(n4 + 3));
+      float tl, tr;
+      bool hl0 = false, hr0 = false, hl1 = false, hr1 = false;
+      if (in && (live0 || live1)) {
+        ++n_nodes;
+        if (live0) slab2(r0, a, b, c, tmax, &tl, &hl0, &tr, &hr0);
+        if (live1) slab2(r1, a, b, c, tmax, &tl, &hl1, &tr, &hr1);
+      }
+      bool hl = hl0 || hl1, hr = hr0 || hr1;
+      unsigned ml = __ballot_sync(full, hl), mr = __ballot_sync(full, hr);
+      if (ml && mr) {
+        if (sp < kStackSize) {
+          if (lane0) stk[sp] = ch.y;
+          in_stk = hr ? (in_stk | (1ull << sp)) : (in_stk & ~(1ull << sp));
+          ++sp;
+        } else if (lane0) {
+          raise_flag(s.err, DRT_DEV_STACK_OVERFLOW, node);
+        }
+        node = ch.x;
+        in = hl;
+        continue;
+      } else if (ml) {
+        node = ch.x;
+        in = hl;
+        continue;
+      } else if (mr) {
+        node = ch.y;
+        in = hr;
+        continue;
+      }
+    } else if (in) {
+      int enc = ~node, first = enc & 0x0fffffff, count = (enc >> 28) + 1;
+      for (int q = 0; q < count && (live0 || live1); ++q) {
+        const float4* t4 = s.soup + 3 * (first + q);
+        float4 p0 = __ldg(t4), p1 = __ldg(t4 + 1), p2 = __ldg(t4 + 2);
+        int id = __float_as_int(p0.w);
+        ++n_tris;
+        float3 v0 = make_float3(p0.x, p0.y, p0.z), v1 = make_float3(p1.x, p1.y, p1.z),
+               v2 = make_float3(p2.x, p2.y, p2.z);
+        float t, b1, b2;
+        if (live0 && id != a0x && id != a0y && watertight(r0.sh, r0.o, v0, v1, v2, tmax, &t, &b1, &b2)) {
+          occ0 = true;
+          live0 = false;
+        }
+        if (live1 && id != a1x && id != a1y && watertight(r1.sh, r1.o, v0, v1, v2, tmax, &t, &b1, &b2)) {
+          occ1 = true;
+          live1 = false;
+        }
+      }
+    }
+    if (sp == 0) break;
+    --sp;
+    __syncwarp();
+    node = stk[sp];
+    in = (in_stk >> sp) & 1ull;
   }
   count_trace(s, kCntAny, n_nodes, n_tris);
 }

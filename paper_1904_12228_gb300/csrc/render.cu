@@ -16,6 +16,21 @@ namespace drt {
 namespace {
 
 constexpr int kBlock = 256;
+// Resident CTAs per SM the primary edge kernel is compiled for (its register
+// cap is 65536 / (kBlock * this)).
+#ifndef DRT_PRIMARY_MIN_BLOCKS
+#define DRT_PRIMARY_MIN_BLOCKS 3
+#endif
+// Primary edge side paths traced by the warp-cooperative traversals (1) or
+// one traversal per lane (0); both give the same hits.
+#ifndef DRT_PRIMARY_WARP
+#define DRT_PRIMARY_WARP 1
+#endif
+// Camera paths of the forward pass traced warp-cooperatively (1) or per lane (0).
+#ifndef DRT_RENDER_WARP
+#define DRT_RENDER_WARP 1
+#endif
+static_assert(kBlock / 32 <= kTraceWarps, "warp-cooperative traversals support at most kTraceWarps warps per CTA");
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kGlobals = 16;  // d_radiance[3], d_cam[12], d_cam_scale[1]
 
@@ -234,19 +249,110 @@ __device__ float3 path_value(const SceneView& s, const Opts& op, float o_in[3], 
   return L;
 }
 
-// Radiance along the two side paths of an edge sample (same counters, so the
-// same light and BSDF random numbers on both sides), traced pairwise.
-__device__ void path_value2(const SceneView& s, const Opts& op, float o[2][3], float d[2][3], uint32_t c0,
-                            uint32_t c1, uint32_t pass, float3 L[2]) {
+// path_value of a camera path (from depth 0, first emission counted) for the
+// 32 lanes of a warp together, traced by the warp-cooperative traversals.
+// All lanes call; a lane with act = false traces nothing, writes no tape and
+// returns 0.  Same values and tape entries as path_value.
+__device__ float3 path_value_warp(const SceneView& s, const Opts& op, const float o_in[3], const float d_in[3],
+                                  bool act, uint32_t c0, uint32_t c1, uint32_t pass, int32_t* tape_tri,
+                                  float2* tape_bary, int64_t n_idx, int64_t n_stride) {
+  const unsigned full = 0xffffffffu;
+  float o[3] = {o_in[0], o_in[1], o_in[2]}, d[3] = {d_in[0], d_in[1], d_in[2]};
+  float3 L = zero3(), beta = make_float3(1.f, 1.f, 1.f);
   int md = op.primary_only ? 1 : op.max_depth;
   const float3 Le = ld3(s.radiance);
-  bool alive[2] = {true, true};
+  bool alive = act;
+  int exclude = -1;
+  int b_end = 0;  // first bounce whose tape entry is not written
+  for (int b = 0; b < md; ++b) {
+    if (!__any_sync(full, alive)) break;
+    Hit h, h_unused;
+    trace_closest2_warp(s, o, d, o, d, alive, false, exclude, -1, h, h_unused);
+    if (alive && h.tri < 0) alive = false;
+    Vertex x;
+    x.k = -1;
+    x.p[0] = x.p[1] = x.p[2] = 0.f;
+    float3 alb = zero3();
+    float n32[3] = {0.f, 0.f, 1.f};
+    if (alive) {
+      load_vertex(s, h.tri, h.b1, h.b2, d, x);
+      alb = ld3(s.albedo + 3 * x.k);
+      if (op.primary_only) {
+        L += beta * alb;
+        if (tape_tri) {
+          tape_tri[b * n_stride + n_idx] = x.k;
+          tape_bary[b * n_stride + n_idx] = make_float2(h.b1, h.b2);
+        }
+        b_end = b + 1;
+        alive = false;
+      } else {
+        if (b == 0 && s.light_of_tri[x.k] >= 0 && x.side < 0.0f) L += beta * Le;
+        shading_normal32(x, n32);
+      }
+    }
+    if (op.primary_only) continue;
+    int vis = 0;
+    if (s.L > 0) {
+      uint4 r = rng4(op.key, c0, c1, kLight, (uint32_t)b, pass, op.scene_id);
+      LightSample ls;
+      sample_light(s, r, ls);
+      float sd[3] = {0.f, 0.f, 1.f};
+      if (alive)
+        for (int i = 0; i < 3; ++i) sd[i] = fs(ls.y[i], x.p[i]);
+      bool occ, occ_unused;
+      trace_any2_warp(s, x.p, sd, x.k, ls.lt, x.p, sd, -1, -1, alive, false, kShadowTmax, occ, occ_unused);
+      if (alive && !occ) {
+        vis = 1;
+        float g = nee_geometry(s, f3(x.p), f3(n32), ls);
+        L += (kInvPi * g) * (beta * alb * Le);
+      }
+    }
+    if (alive) {
+      if (tape_tri) {
+        tape_tri[b * n_stride + n_idx] = x.k | (vis << 31);
+        tape_bary[b * n_stride + n_idx] = make_float2(h.b1, h.b2);
+      }
+      b_end = b + 1;
+    }
+    if (b + 1 >= md) break;
+    uint4 r = rng4(op.key, c0, c1, kBsdf, (uint32_t)b, pass, op.scene_id);
+    if (alive) {
+      float nd[3];
+      cosine_dir(n32, u01f(r.x), u01f(r.y), nd);
+      if (!(dot(f3(n32), f3(nd)) > 0.f)) {
+        alive = false;
+      } else {
+        beta = beta * alb;
+        for (int i = 0; i < 3; ++i) { o[i] = x.p[i]; d[i] = nd[i]; }
+        exclude = x.k;
+      }
+    }
+  }
+  if (tape_tri && act)
+    for (int b = b_end; b < md; ++b) tape_tri[b * n_stride + n_idx] = -1;
+  return L;
+}
+
+// Radiance along the two side paths of an edge sample (same counters, so the
+// same light and BSDF random numbers on both sides), traced pairwise.  With
+// kWarp all 32 lanes of the warp must call together (inactive lanes pass
+// act = false) and the rays are traced by the warp-cooperative traversals.
+template <bool kWarp>
+__device__ void path_value2(const SceneView& s, const Opts& op, float o[2][3], float d[2][3], uint32_t c0,
+                            uint32_t c1, uint32_t pass, float3 L[2], bool act) {
+  const unsigned full = 0xffffffffu;
+  int md = op.primary_only ? 1 : op.max_depth;
+  const float3 Le = ld3(s.radiance);
+  bool alive[2] = {act, act};
   int exclude[2] = {-1, -1};
   float3 beta[2] = {make_float3(1.f, 1.f, 1.f), make_float3(1.f, 1.f, 1.f)};
   L[0] = L[1] = zero3();
   for (int b = 0; b < md; ++b) {
     Hit h[2];
-    trace_closest2(s, o[0], d[0], o[1], d[1], alive[0], alive[1], exclude[0], exclude[1], h[0], h[1]);
+    if (kWarp)
+      trace_closest2_warp(s, o[0], d[0], o[1], d[1], alive[0], alive[1], exclude[0], exclude[1], h[0], h[1]);
+    else
+      trace_closest2(s, o[0], d[0], o[1], d[1], alive[0], alive[1], exclude[0], exclude[1], h[0], h[1]);
     Vertex x[2];
     float3 alb[2];
     for (int q = 0; q < 2; ++q) {
@@ -261,7 +367,7 @@ __device__ void path_value2(const SceneView& s, const Opts& op, float o[2][3], f
       }
       if (b == 0 && s.light_of_tri[x[q].k] >= 0 && x[q].side < 0.0f) L[q] += beta[q] * Le;
     }
-    if (!alive[0] && !alive[1]) break;
+    if (kWarp ? !__any_sync(full, alive[0] || alive[1]) : (!alive[0] && !alive[1])) break;
     float n32[2][3];
     for (int q = 0; q < 2; ++q)
       if (alive[q]) shading_normal32(x[q], n32[q]);
@@ -274,8 +380,12 @@ __device__ void path_value2(const SceneView& s, const Opts& op, float o[2][3], f
         if (alive[q])
           for (int i = 0; i < 3; ++i) sd[q][i] = fs(ls.y[i], x[q].p[i]);
       bool occ[2];
-      trace_any2(s, x[0].p, sd[0], x[0].k, ls.lt, x[1].p, sd[1], x[1].k, ls.lt, alive[0], alive[1], kShadowTmax,
-                 occ[0], occ[1]);
+      if (kWarp)
+        trace_any2_warp(s, x[0].p, sd[0], x[0].k, ls.lt, x[1].p, sd[1], x[1].k, ls.lt, alive[0], alive[1],
+                        kShadowTmax, occ[0], occ[1]);
+      else
+        trace_any2(s, x[0].p, sd[0], x[0].k, ls.lt, x[1].p, sd[1], x[1].k, ls.lt, alive[0], alive[1], kShadowTmax,
+                   occ[0], occ[1]);
       for (int q = 0; q < 2; ++q)
         if (alive[q] && !occ[q]) {
           float g = nee_geometry(s, f3(x[q].p), f3(n32[q]), ls);
@@ -293,7 +403,7 @@ __device__ void path_value2(const SceneView& s, const Opts& op, float o[2][3], f
       for (int i = 0; i < 3; ++i) { o[q][i] = x[q].p[i]; d[q][i] = nd[i]; }
       exclude[q] = x[q].k;
     }
-    if (!alive[0] && !alive[1]) break;
+    if (kWarp ? !__any_sync(full, alive[0] || alive[1]) : (!alive[0] && !alive[1])) break;
   }
 }
 
@@ -316,6 +426,24 @@ __device__ __forceinline__ void render_block(const SceneView& s, const Opts& op,
   bool active = pix < npix;
   int64_t n = (int64_t)npix * op.spp;
   float3 acc = zero3();
+#if DRT_RENDER_WARP
+  // the warp traces its lanes' samples together: every lane runs the same
+  // number of rounds
+  int iters = (op.spp + G - 1) / G;
+  for (int it = 0; it < iters; ++it) {
+    int sidx = lane % G + it * G;
+    bool act = active && sidx < op.spp;
+    float o[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 1.f};
+    if (act) {
+      float sx, sy;
+      jitter(op, (int)pix, sidx, s.W, &sx, &sy);
+      camera_ray(s, sx, sy, o, d);
+    }
+    float3 v = path_value_warp(s, op, o, d, act, (uint32_t)pix, (uint32_t)sidx, kPassInterior, tape_tri, tape_bary,
+                               pix * op.spp + sidx, n);
+    if (act) acc += v;
+  }
+#else
   if (active) {
     for (int sidx = lane % G; sidx < op.spp; sidx += G) {
       float sx, sy, o[3], d[3];
@@ -325,6 +453,7 @@ __device__ __forceinline__ void render_block(const SceneView& s, const Opts& op,
                         pix * op.spp + sidx, n);
     }
   }
+#endif
   for (int o = G >> 1; o > 0; o >>= 1) {
     acc.x += __shfl_xor_sync(kFull, acc.x, o);
     acc.y += __shfl_xor_sync(kFull, acc.y, o);
@@ -1186,20 +1315,26 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
       es = primary_sample(s, op, j, ptotal);
       active = es.valid;
     }
+    // side rays at +-eps along the edge normal (all lanes take part in the
+    // warp-cooperative tracing below; inactive lanes trace nothing)
+    float o2[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, d2[2][3] = {{0.f, 0.f, 1.f}, {0.f, 0.f, 1.f}};
+    float3 w = zero3();
     if (active) {
-      int e = es.e;
-      float ax = es.ax, ay = es.ay, bx = es.bx, by = es.by, dx = es.dx, dy = es.dy, x = es.x, y = es.y;
+      float dx = es.dx, dy = es.dy, x = es.x, y = es.y;
       float nlen = fsq(fa(fm(dx, dx), fm(dy, dy)));
       float nx = fdv(-dy, nlen), ny = fdv(dx, nlen);
       float xu = fa(x, fm(eps, nx)), yu = fa(y, fm(eps, ny));
       float xl = fs(x, fm(eps, nx)), yl = fs(y, fm(eps, ny));
       int px = min(max((int)floorf(x), 0), s.W - 1), py = min(max((int)floorf(y), 0), s.H - 1);
-      float3 w = ld3(d_image + 3 * ((int64_t)py * s.W + px));
-      float o2[2][3], d2[2][3];
+      w = ld3(d_image + 3 * ((int64_t)py * s.W + px));
       camera_ray(s, xu, yu, o2[0], d2[0]);
       camera_ray(s, xl, yl, o2[1], d2[1]);
-      float3 L2[2];
-      path_value2(s, op, o2, d2, (uint32_t)j, 0u, kPassPrimaryEdge, L2);
+    }
+    float3 L2[2];
+    path_value2<DRT_PRIMARY_WARP != 0>(s, op, o2, d2, (uint32_t)j, 0u, kPassPrimaryEdge, L2, active);
+    if (active) {
+      int e = es.e;
+      float ax = es.ax, ay = es.ay, bx = es.bx, by = es.by, x = es.x, y = es.y;
       float diff = dot(w, L2[0] - L2[1]);
       if (op.seg_log && es.seg >= 0) atomicAdd(op.seg_log + es.seg, fabsf(diff));
       if (diff != 0.f) {
@@ -1219,7 +1354,7 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
   }
   block_globals(g, gr.partials + blk * kGlobals, false);
 }
-__global__ void __launch_bounds__(kBlock, 2) k_backward_primary(SceneView s, Opts op, const float* d_image, Grads gr,
+__global__ void __launch_bounds__(kBlock, DRT_PRIMARY_MIN_BLOCKS) k_backward_primary(SceneView s, Opts op, const float* d_image, Grads gr,
                                                              int64_t n_edge, int64_t per_thread,
                                                              const int32_t* order) {
   primary_block(s, op, d_image, gr, n_edge, per_thread, order, blockIdx.x);
@@ -1263,9 +1398,9 @@ __device__ __forceinline__ int batch_scene_of(const int64_t* prefix, int n, int6
 
 template <int PH>
 struct PhaseMinBlocks {
-  // two resident CTAs per SM (128 registers), as the single-scene kernels
-  // have; the depth > 1 path pass needs more registers
-  static constexpr int value = PH == kPhasePath ? 1 : 2;
+  // resident CTAs per SM as the single-scene kernels have; the depth > 1
+  // path pass needs more registers
+  static constexpr int value = PH == kPhasePath ? 1 : (PH == kPhasePrimary ? DRT_PRIMARY_MIN_BLOCKS : 2);
 };
 
 template <int PH>
