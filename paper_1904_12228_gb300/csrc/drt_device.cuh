@@ -116,11 +116,12 @@ struct SceneView {
 // Work counters (enabled per launch): rays traced by trace_closest, rays
 // traced by trace_any, BVH nodes visited (two boxes each), triangle tests.
 enum { kCntClosest = 0, kCntAny = 1, kCntNodes = 2, kCntTris = 3 };
-__device__ __forceinline__ void count_trace(const SceneView& s, int kind, int nodes, int tris) {
+// `rays` = rays this lane traced in the query (0, 1 or 2).
+__device__ __forceinline__ void count_trace(const SceneView& s, int kind, int rays, int nodes, int tris) {
   if (s.counters == nullptr) return;
   unsigned m = __activemask();
   int lead = __ffs(m) - 1;
-  int nr = __popc(m);
+  unsigned nr = __reduce_add_sync(m, (unsigned)rays);
   unsigned tn = __reduce_add_sync(m, (unsigned)nodes), tt = __reduce_add_sync(m, (unsigned)tris);
   if ((int)(threadIdx.x & 31) == lead) {
     atomicAdd(s.counters + kind, (unsigned long long)nr);
@@ -391,6 +392,19 @@ struct Hit {
   float t, b1, b2;
 };
 
+// Three-input minimum / maximum (one instruction on sm_100 and later; exact,
+// like the two-input forms).
+__device__ __forceinline__ float fmax3f(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float fmin3f(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
 struct RayPre {
   float o[3], inv[3];
   Shear sh;
@@ -411,15 +425,15 @@ __device__ __forceinline__ void slab2(const RayPre& r, const float4& a, const fl
   float lx0 = (a.x - r.o[0]) * r.inv[0], lx1 = (a.w - r.o[0]) * r.inv[0];
   float ly0 = (a.y - r.o[1]) * r.inv[1], ly1 = (b.x - r.o[1]) * r.inv[1];
   float lz0 = (a.z - r.o[2]) * r.inv[2], lz1 = (b.y - r.o[2]) * r.inv[2];
-  float tin = fmaxf(fmaxf(fminf(lx0, lx1), fminf(ly0, ly1)), fmaxf(fminf(lz0, lz1), 0.0f));
-  float tout = fminf(fminf(fmaxf(lx0, lx1), fmaxf(ly0, ly1)), fminf(fmaxf(lz0, lz1), tmax));
+  float tin = fmax3f(fminf(lx0, lx1), fminf(ly0, ly1), fmaxf(fminf(lz0, lz1), 0.0f));
+  float tout = fmin3f(fmaxf(lx0, lx1), fmaxf(ly0, ly1), fminf(fmaxf(lz0, lz1), tmax));
   *tl = tin;
   *hl = tin <= tout * 1.00000024f;
   float rx0 = (b.z - r.o[0]) * r.inv[0], rx1 = (c.y - r.o[0]) * r.inv[0];
   float ry0 = (b.w - r.o[1]) * r.inv[1], ry1 = (c.z - r.o[1]) * r.inv[1];
   float rz0 = (c.x - r.o[2]) * r.inv[2], rz1 = (c.w - r.o[2]) * r.inv[2];
-  float tin2 = fmaxf(fmaxf(fminf(rx0, rx1), fminf(ry0, ry1)), fmaxf(fminf(rz0, rz1), 0.0f));
-  float tout2 = fminf(fminf(fmaxf(rx0, rx1), fmaxf(ry0, ry1)), fminf(fmaxf(rz0, rz1), tmax));
+  float tin2 = fmax3f(fminf(rx0, rx1), fminf(ry0, ry1), fmaxf(fminf(rz0, rz1), 0.0f));
+  float tout2 = fmin3f(fmaxf(rx0, rx1), fmaxf(ry0, ry1), fminf(fmaxf(rz0, rz1), tmax));
   *tr = tin2;
   *hr = tin2 <= tout2 * 1.00000024f;
 }
@@ -490,7 +504,7 @@ __device__ __forceinline__ Hit trace_closest(const SceneView& s, const float o[3
     if (sp == 0) break;
     node = stack[--sp];
   }
-  count_trace(s, kCntClosest, n_nodes, n_tris);
+  count_trace(s, kCntClosest, 1, n_nodes, n_tris);
   return h;
 }
 
@@ -548,7 +562,7 @@ __device__ __forceinline__ bool trace_any(const SceneView& s, const float o[3], 
     if (sp == 0) break;
     node = stack[--sp];
   }
-  count_trace(s, kCntAny, n_nodes, n_tris);
+  count_trace(s, kCntAny, 1, n_nodes, n_tris);
   return found;
 }
 
@@ -622,7 +636,7 @@ __device__ __forceinline__ void trace_closest2(const SceneView& s, const float o
     if (sp == 0) break;
     node = stack[--sp];
   }
-  count_trace(s, kCntClosest, n_nodes, n_tris);
+  count_trace(s, kCntClosest, (int)act0 + (int)act1, n_nodes, n_tris);
 }
 
 // Two any-hit queries through one traversal; occ0/occ1 report a hit with t in
@@ -690,7 +704,7 @@ __device__ __forceinline__ void trace_any2(const SceneView& s, const float o0[3]
     if (sp == 0) break;
     node = stack[--sp];
   }
-  count_trace(s, kCntAny, n_nodes, n_tris);
+  count_trace(s, kCntAny, (int)act0 + (int)act1, n_nodes, n_tris);
 }
 
 // ---------------------------------------------------------------------------
@@ -795,7 +809,7 @@ __device__ __forceinline__ void trace_closest2_warp(const SceneView& s, const fl
     node = stk[sp];
     in = (in_stk >> sp) & 1ull;
   }
-  count_trace(s, kCntClosest, n_nodes, n_tris);
+  count_trace(s, kCntClosest, (int)act0 + (int)act1, n_nodes, n_tris);
 }
 
 // Warp-cooperative any-hit of two rays per lane (see trace_any2); the warp
@@ -882,7 +896,7 @@ __device__ __forceinline__ void trace_any2_warp(const SceneView& s, const float 
     node = stk[sp];
     in = (in_stk >> sp) & 1ull;
   }
-  count_trace(s, kCntAny, n_nodes, n_tris);
+  count_trace(s, kCntAny, (int)act0 + (int)act1, n_nodes, n_tris);
 }
 
 __device__ __forceinline__ float3 ld3(const float* p) { return make_float3(p[0], p[1], p[2]); }
