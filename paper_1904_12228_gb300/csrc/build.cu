@@ -244,19 +244,30 @@ __device__ __forceinline__ uint32_t expand10(uint32_t x) {
   return x;
 }
 
+// Key of a triangle: 30-bit Morton code of its centroid in the scene box,
+// and above it one bit for triangles whose box is longer than 1/8 of the
+// scene's longest extent (floors, walls, large lights).  The hierarchy then
+// keeps those few large triangles in their own subtree below the root, so
+// their boxes do not enlarge the boxes around the small geometry (a tree of
+// Morton order alone places them by centroid, deep among small triangles).
 __global__ void k_morton(SceneView s, const int* b, uint32_t* keys, int32_t* vals) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= s.T) return;
   const int32_t* id = s.tris + 3 * t;
   float q[3];
+  float tri_ext = 0.0f, scene_ext = 0.0f;
   for (int k = 0; k < 3; ++k) {
     float lo = unord(b[k]), hi = unord(b[3 + k]);
-    float c = (s.verts[3 * id[0] + k] + s.verts[3 * id[1] + k] + s.verts[3 * id[2] + k]) * (1.0f / 3.0f);
+    float a = s.verts[3 * id[0] + k], bb = s.verts[3 * id[1] + k], cc = s.verts[3 * id[2] + k];
+    float c = (a + bb + cc) * (1.0f / 3.0f);
     float ext = hi - lo;
     float u = ext > 0.0f ? (c - lo) / ext : 0.5f;
     q[k] = fminf(fmaxf(u * 1024.0f, 0.0f), 1023.0f);
+    tri_ext = fmaxf(tri_ext, fmaxf(fmaxf(a, bb), cc) - fminf(fminf(a, bb), cc));
+    scene_ext = fmaxf(scene_ext, ext);
   }
-  keys[t] = (expand10((uint32_t)q[0]) << 2) | (expand10((uint32_t)q[1]) << 1) | expand10((uint32_t)q[2]);
+  uint32_t large = 8.0f * tri_ext > scene_ext ? 1u : 0u;
+  keys[t] = (large << 30) | (expand10((uint32_t)q[0]) << 2) | (expand10((uint32_t)q[1]) << 1) | expand10((uint32_t)q[2]);
   vals[t] = t;
 }
 
@@ -807,7 +818,7 @@ cudaError_t build_bvh(drt_scene* s, cudaStream_t st) {
   DRT_PROF_LAUNCH("bounds_init", st, k_bounds_init<<<1, 32, 0, st>>>(s->bounds));
   DRT_PROF_LAUNCH("bounds", st, k_bounds<<<std::min(1024, (s->V + kBlock - 1) / kBlock), kBlock, 0, st>>>(s->verts, s->V, s->bounds));
   DRT_PROF_LAUNCH("morton", st, k_morton<<<(T + kBlock - 1) / kBlock, kBlock, 0, st>>>(v, s->bounds, s->keys, s->vals));
-  bool alt = radix_sort_pairs(s->keys, s->vals, s->keys2, s->vals2, s->hist, s->hist_tmp, T, 30, st);
+  bool alt = radix_sort_pairs(s->keys, s->vals, s->keys2, s->vals2, s->hist, s->hist_tmp, T, 31, st);
   uint32_t* ka = alt ? s->keys2 : s->keys;
   int32_t* va = alt ? s->vals2 : s->vals;
   if (T > 1) {
