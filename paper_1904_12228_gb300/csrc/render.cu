@@ -26,6 +26,10 @@ constexpr int kBlock = 256;
 #ifndef DRT_PRIMARY_WARP
 #define DRT_PRIMARY_WARP 1
 #endif
+// Resident CTAs per SM the interior and secondary edge passes are compiled for.
+#ifndef DRT_PIXEL_MIN_BLOCKS
+#define DRT_PIXEL_MIN_BLOCKS 2
+#endif
 // Camera paths of the forward pass traced warp-cooperatively (1) or per lane (0).
 #ifndef DRT_RENDER_WARP
 #define DRT_RENDER_WARP 1
@@ -57,7 +61,40 @@ __device__ __forceinline__ float warp_sum(float x) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
   return x;
 }
-__device__ __forceinline__ void scatter3(float* arr, int id, float3 v, bool active) {
+// Block-level gradient cache.  A few entities receive gradient from almost
+// every pixel (the vertices of the light, of a floor, a floor's albedo); sent
+// straight to global memory, their atomic additions all land in one L2 slice
+// and serialise there, delaying every other access to that slice.  A block
+// first adds warp sums into a direct-mapped table in shared memory (shared
+// atomics; a key whose slot is taken goes to global memory directly) and
+// sends each table entry once, when the block ends.
+constexpr int kCacheSlots = 64;
+struct GradCache {
+  int key[kCacheSlots];
+  float val[kCacheSlots][3];
+};
+// All threads of the block; __syncthreads() before the first scatter.
+__device__ __forceinline__ void cache_init(GradCache& c) {
+  for (int i = threadIdx.x; i < kCacheSlots; i += kBlock) {
+    c.key[i] = -1;
+    c.val[i][0] = c.val[i][1] = c.val[i][2] = 0.f;
+  }
+}
+// All threads of the block, after a __syncthreads() that follows the last
+// scatter; a __syncthreads() must separate it from the next cache_init.
+__device__ __forceinline__ void cache_flush(const GradCache& c, float* arr) {
+  if (arr == nullptr) return;
+  for (int i = threadIdx.x; i < kCacheSlots; i += kBlock) {
+    int k = c.key[i];
+    if (k >= 0) {
+      atomicAdd(arr + 3 * k, c.val[i][0]);
+      atomicAdd(arr + 3 * k + 1, c.val[i][1]);
+      atomicAdd(arr + 3 * k + 2, c.val[i][2]);
+    }
+  }
+}
+
+__device__ __forceinline__ void scatter3(float* arr, int id, float3 v, bool active, GradCache* cache = nullptr) {
   if (arr == nullptr) return;
   int lane = threadIdx.x & 31;
   unsigned pending = __ballot_sync(kFull, active);
@@ -77,9 +114,22 @@ __device__ __forceinline__ void scatter3(float* arr, int id, float3 v, bool acti
       x.z = __shfl_sync(kFull, x.z, leader);
     }
     if (lane == leader) {
-      atomicAdd(arr + 3 * key, x.x);
-      atomicAdd(arr + 3 * key + 1, x.y);
-      atomicAdd(arr + 3 * key + 2, x.z);
+      bool cached = false;
+      if (cache) {
+        int slot = key & (kCacheSlots - 1);
+        int prev = atomicCAS(&cache->key[slot], -1, key);
+        if (prev == -1 || prev == key) {
+          atomicAdd(&cache->val[slot][0], x.x);
+          atomicAdd(&cache->val[slot][1], x.y);
+          atomicAdd(&cache->val[slot][2], x.z);
+          cached = true;
+        }
+      }
+      if (!cached) {
+        atomicAdd(arr + 3 * key, x.x);
+        atomicAdd(arr + 3 * key + 1, x.y);
+        atomicAdd(arr + 3 * key + 2, x.z);
+      }
     }
     pending &= ~peers;
   }
@@ -668,6 +718,10 @@ __device__ __forceinline__ float3 shading_normal(const Vertex& x) {
 __device__ __forceinline__ void interior_block(const SceneView& s, const Opts& op, const int32_t* tape_tri,
                                                               const float2* tape_bary, const float* d_image, Grads gr,
                                                               int G, int64_t blk) {
+  __shared__ GradCache cv, ca;
+  cache_init(cv);
+  cache_init(ca);
+  __syncthreads();
   int lane = threadIdx.x & 31;
   int64_t gw = (blk * kBlock + threadIdx.x) >> 5;
   int ppw = 32 / G;
@@ -759,17 +813,20 @@ __device__ __forceinline__ void interior_block(const SceneView& s, const Opts& o
         hit_point_adjoint(s, c, x, dp, dn, dv0, dv1, dv2, g);
       }
     }
-    scatter3(gr.verts, vid0, dv0, hit);
-    scatter3(gr.verts, vid1, dv1, hit);
-    scatter3(gr.verts, vid2, dv2, hit);
-    scatter3(gr.albedo, c.k, dalb, hit);
-    scatter3(gr.verts, lid0, dl0, have_light);
-    scatter3(gr.verts, lid1, dl1, have_light);
-    scatter3(gr.verts, lid2, dl2, have_light);
+    scatter3(gr.verts, vid0, dv0, hit, &cv);
+    scatter3(gr.verts, vid1, dv1, hit, &cv);
+    scatter3(gr.verts, vid2, dv2, hit, &cv);
+    scatter3(gr.albedo, c.k, dalb, hit, &ca);
+    scatter3(gr.verts, lid0, dl0, have_light, &cv);
+    scatter3(gr.verts, lid1, dl1, have_light, &cv);
+    scatter3(gr.verts, lid2, dl2, have_light, &cv);
   }
+  __syncthreads();
+  cache_flush(cv, gr.verts);
+  cache_flush(ca, gr.albedo);
   block_globals(g, gr.partials + blk * kGlobals, false);
 }
-__global__ void __launch_bounds__(kBlock) k_backward_interior(SceneView s, Opts op, const int32_t* tape_tri,
+__global__ void __launch_bounds__(kBlock, DRT_PIXEL_MIN_BLOCKS) k_backward_interior(SceneView s, Opts op, const int32_t* tape_tri,
                                                               const float2* tape_bary, const float* d_image, Grads gr,
                                                               int G) {
   interior_block(s, op, tape_tri, tape_bary, d_image, gr, G, blockIdx.x);
@@ -919,7 +976,7 @@ __device__ __forceinline__ void secondary_block(const SceneView& s, const Opts& 
   }
   block_globals(g, gr.partials + blk * kGlobals, rows_written != 0);
 }
-__global__ void __launch_bounds__(kBlock) k_backward_secondary(SceneView s, Opts op, const int32_t* tape_tri,
+__global__ void __launch_bounds__(kBlock, DRT_PIXEL_MIN_BLOCKS) k_backward_secondary(SceneView s, Opts op, const int32_t* tape_tri,
                                                                const float2* tape_bary, const float* d_image, Grads gr,
                                                                int G, int rows_written) {
   secondary_block(s, op, tape_tri, tape_bary, d_image, gr, G, rows_written, blockIdx.x);
@@ -1091,6 +1148,10 @@ __device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Op
 __device__ __forceinline__ void path_block(const SceneView& s, const Opts& op, const int32_t* tape_tri,
                                                           const float2* tape_bary, const float* d_image, Grads gr,
                                                           int G, int64_t blk) {
+  __shared__ GradCache cv, ca;
+  cache_init(cv);
+  cache_init(ca);
+  __syncthreads();
   int lane = threadIdx.x & 31;
   int64_t gw = (blk * kBlock + threadIdx.x) >> 5;
   int ppw = 32 / G;
@@ -1202,17 +1263,20 @@ __device__ __forceinline__ void path_block(const SceneView& s, const Opts& op, c
         pbar = do_;  // the origin of ray b is vertex b-1 (its direction is held fixed)
         D_next = Dv;
       }
-      scatter3(gr.verts, vid[0], dv0, av);
-      scatter3(gr.verts, vid[1], dv1, av);
-      scatter3(gr.verts, vid[2], dv2, av);
-      scatter3(gr.albedo, av ? kk[b] : 0, dalb, av && do_int);
-      for (int i = 0; i < 3; ++i) scatter3(gr.verts, lid[i], dl[i], have_light);
-      scatter3(gr.verts, so.eid0, so.de0, so.have_edge);
-      scatter3(gr.verts, so.eid1, so.de1, so.have_edge);
+      scatter3(gr.verts, vid[0], dv0, av, &cv);
+      scatter3(gr.verts, vid[1], dv1, av, &cv);
+      scatter3(gr.verts, vid[2], dv2, av, &cv);
+      scatter3(gr.albedo, av ? kk[b] : 0, dalb, av && do_int, &ca);
+      for (int i = 0; i < 3; ++i) scatter3(gr.verts, lid[i], dl[i], have_light, &cv);
+      scatter3(gr.verts, so.eid0, so.de0, so.have_edge, &cv);
+      scatter3(gr.verts, so.eid1, so.de1, so.have_edge, &cv);
       for (int q = 0; q < 2; ++q)
-        for (int i = 0; i < 3; ++i) scatter3(gr.verts, so.mid[q][i], so.dm[q][i], so.have_m[q]);
+        for (int i = 0; i < 3; ++i) scatter3(gr.verts, so.mid[q][i], so.dm[q][i], so.have_m[q], &cv);
     }
   }
+  __syncthreads();
+  cache_flush(cv, gr.verts);
+  cache_flush(ca, gr.albedo);
   block_globals(g, gr.partials + blk * kGlobals, false);
 }
 __global__ void __launch_bounds__(kBlock) k_backward_path(SceneView s, Opts op, const int32_t* tape_tri,
@@ -1400,7 +1464,10 @@ template <int PH>
 struct PhaseMinBlocks {
   // resident CTAs per SM as the single-scene kernels have; the depth > 1
   // path pass needs more registers
-  static constexpr int value = PH == kPhasePath ? 1 : (PH == kPhasePrimary ? DRT_PRIMARY_MIN_BLOCKS : 2);
+  static constexpr int value =
+      PH == kPhasePath ? 1
+                       : (PH == kPhasePrimary ? DRT_PRIMARY_MIN_BLOCKS
+                                              : (PH == kPhaseRender ? 2 : DRT_PIXEL_MIN_BLOCKS));
 };
 
 template <int PH>
