@@ -183,11 +183,13 @@ drt_status drt_tape_free(drt_context* ctx, drt_tape* tape);
  * drt_render_backward, except:
  *   - d_image and every non-NULL gradient array must be device memory (no
  *     host staging); otherwise DRT_ERR_INVALID_ARG.
- *   - The scratch (one row of 16 partial sums per thread block) is a fixed
- *     array of 65536 rows (4 MiB) compiled into the library, which every GPU
- *     that loads the library holds until the process exits.  Images needing
- *     more rows (about 2^21 pixels at spp >= 32) are rejected with
- *     DRT_ERR_INVALID_ARG and a message giving the sizes.
+ *   - The scratch (one row of 16 partial sums per thread block, plus the
+ *     totals of the first reduction stage) is a fixed array of 2^22 floats
+ *     (16 MiB) compiled into the library, which every GPU that loads the
+ *     library holds until the process exits.  It holds about 2^18 rows: a
+ *     512x512 image at 64 spp and 64 edge samples per pixel needs 98304.
+ *     Larger jobs are rejected with DRT_ERR_INVALID_ARG and a message
+ *     giving the sizes.
  *   - The first call on a device looks up the array's device address with
  *     cudaGetSymbolAddress (the context's device must be current); make that
  *     first call before any stream capture.

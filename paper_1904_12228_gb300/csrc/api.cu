@@ -482,7 +482,7 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
   // per-block partial sums of the global parameters: scene-owned scratch,
   // grown on demand (the stream is drained before the old buffer is freed)
   int64_t rows = drt::backward_partial_rows(s, op);
-  size_t need = (size_t)rows * 16 + 16;
+  size_t need = (size_t)drt::partial_floats(rows);
   if (r == DRT_OK && need > s->partials_cap) {
     cudaStreamSynchronize(st);
     dfree(s->partials);

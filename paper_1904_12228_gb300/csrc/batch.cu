@@ -98,7 +98,7 @@ struct drt_batch {
   std::vector<int64_t> prefix;   // kPhases x (n + 1)
   std::vector<int64_t> eprefix;  // n + 1
   int64_t n_items[drt::kPhases] = {};
-  int64_t total_edge = 0, total_tape = 0, total_rows = 0;
+  int64_t total_edge = 0, total_tape = 0, total_floats = 0;
   int pix_bits = 0, key_bits = 0;  // screen key bits; with the scene index above them
   std::vector<std::pair<float*, size_t>> zero_rows;
   // device
@@ -121,12 +121,6 @@ struct drt_batch {
 
 namespace {
 
-bool any_backward(const drt_batch* b) {
-  for (const auto& it : b->items)
-    if (it.d_image) return true;
-  return false;
-}
-
 // Work items, offsets and descriptors of every scene for the current shape.
 // With `bind` false only the totals are computed (before allocation).
 void plan(drt_batch* b, bool bind) {
@@ -139,7 +133,7 @@ void plan(drt_batch* b, bool bind) {
   b->eprefix.assign(n + 1, 0);
   b->desc.assign(n, BatchScene{});
   b->zero_rows.clear();
-  int64_t tape_off = 0, row_off = 0;
+  int64_t tape_off = 0, float_off = 0;
   int pix_bits = 2;
   for (int k = 0; k < n; ++k) {
     const drt_batch_item& it = b->items[k];
@@ -160,7 +154,7 @@ void plan(drt_batch* b, bool bind) {
     int64_t cnt[drt::kPhases] = {blocks_i, 0, 0, 0, 0};
     int64_t tape_here = tape_off;
     tape_off += npix * op.spp * depth;
-    int64_t row_here = row_off;
+    int64_t float_here = float_off;
     if (it.d_image) {
       d.d_image = it.d_image;
       d.d_verts = it.grads.d_verts;
@@ -189,8 +183,8 @@ void plan(drt_batch* b, bool bind) {
         pix_bits = std::max(pix_bits, drt::screen_key_bits(s->W, s->H));
       }
       if (bind && need_i && !path && !(op.terms & 1) && !sec)
-        b->zero_rows.push_back({b->partials + row_here * kRowFloats, (size_t)blocks_i * kRowFloats});
-      row_off += d.rows_i + d.blocks_e;
+        b->zero_rows.push_back({b->partials + float_here, (size_t)blocks_i * kRowFloats});
+      float_off += drt::partial_floats(d.rows_i + d.blocks_e);
     }
     for (int p = 0; p < drt::kPhases; ++p)
       b->prefix[(size_t)p * (n + 1) + k + 1] = b->prefix[(size_t)p * (n + 1) + k] + cnt[p];
@@ -198,7 +192,7 @@ void plan(drt_batch* b, bool bind) {
     if (bind) {
       d.tape_tri = b->tape_tri + tape_here;
       d.tape_bary = b->tape_bary + tape_here;
-      if (it.d_image) d.partials = b->partials + row_here * kRowFloats;
+      if (it.d_image) d.partials = b->partials + float_here;
     }
   }
   int sb = 0;
@@ -207,7 +201,7 @@ void plan(drt_batch* b, bool bind) {
   b->key_bits = pix_bits + sb;
   b->total_edge = b->eprefix[n];
   b->total_tape = tape_off;
-  b->total_rows = row_off;
+  b->total_floats = float_off;
   for (int p = 0; p < drt::kPhases; ++p) b->n_items[p] = b->prefix[(size_t)p * (n + 1) + n];
   if (bind) {
     // the sort leaves its result in vals2 after an odd number of 8-bit passes
@@ -274,7 +268,11 @@ cudaError_t enqueue(drt_batch* b, cudaStream_t st) {
   if (e == cudaSuccess) e = run_phase(b, drt::kPhaseSecondary, b->d_desc, st);
   if (e == cudaSuccess) e = sort_edges(b, b->d_desc, st);
   if (e == cudaSuccess) e = run_phase(b, drt::kPhasePrimary, b->d_desc, st);
-  if (e == cudaSuccess && any_backward(b)) e = drt::launch_batch_reduce(b->d_desc, b->n, st);
+  for (int k = 0; k < b->n && e == cudaSuccess; ++k) {
+    const BatchScene& d = b->desc[k];
+    if (d.d_image)
+      e = drt::launch_reduce_globals(d.partials, d.rows_i + d.blocks_e, d.d_radiance, d.d_cam, d.d_scale, st);
+  }
   return e;
 }
 
@@ -421,7 +419,7 @@ drt_status drt_batch_create(drt_context* ctx, const drt_batch_item* items, int32
   if (s == DRT_OK) s = balloc(&b->d_counter, drt::kPhases);
   if (s == DRT_OK) s = balloc(&b->tape_tri, (size_t)b->total_tape);
   if (s == DRT_OK) s = balloc(&b->tape_bary, (size_t)b->total_tape);
-  if (s == DRT_OK) s = balloc(&b->partials, (size_t)b->total_rows * kRowFloats);
+  if (s == DRT_OK) s = balloc(&b->partials, (size_t)b->total_floats);
   size_t ne = (size_t)b->total_edge;
   if (s == DRT_OK && ne > 0) {
     s = balloc(&b->keys, ne);

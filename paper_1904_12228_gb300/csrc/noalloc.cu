@@ -18,13 +18,14 @@
 
 namespace {
 
-// Maximum number of partial-sum rows (16 floats each): 65536 rows = 4 MiB.
-// A 512x512 image with spp >= 32 needs 32768 + 2432 rows.
-constexpr int64_t kNoAllocMaxRows = 65536;
-constexpr int kGlobalsPerRow = 16;
+// Capacity of the scratch: 2^22 floats = 16 MiB, about 2^18 partial-sum rows
+// of 16 floats (one row per thread block of the pixel passes and of the
+// primary edge pass) plus their stage-1 totals.  A 512x512 image at 64 spp
+// and 64 edge samples per pixel needs 32768 + 65536 rows.
+constexpr int64_t kNoAllocMaxFloats = int64_t(1) << 22;
 
 // Shared by every call on a device and kept until the process exits.
-static __device__ __align__(256) float g_backward_scratch[kNoAllocMaxRows * kGlobalsPerRow];
+static __device__ __align__(256) float g_backward_scratch[kNoAllocMaxFloats];
 
 constexpr int kMaxDevices = 64;
 float* g_scratch_addr[kMaxDevices] = {nullptr};
@@ -94,10 +95,10 @@ drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* s, const drt
       return fail_noalloc(DRT_ERR_INVALID_ARG, "drt_render_backward_noalloc takes device arrays only");
     }
   int64_t rows = drt::backward_partial_rows(s, op);
-  if (rows > kNoAllocMaxRows) {
+  if (drt::partial_floats(rows) > kNoAllocMaxFloats) {
     char buf[160];
-    std::snprintf(buf, sizeof(buf), "image too large for the fixed scratch: needs %lld rows, maximum %lld",
-                  (long long)rows, (long long)kNoAllocMaxRows);
+    std::snprintf(buf, sizeof(buf), "image too large for the fixed scratch: needs %lld floats, maximum %lld",
+                  (long long)drt::partial_floats(rows), (long long)kNoAllocMaxFloats);
     return fail_noalloc(DRT_ERR_INVALID_ARG, buf);
   }
   // first call on this device: look up the device address of the array

@@ -21,6 +21,12 @@ constexpr int kBlock = 256;
 #ifndef DRT_PRIMARY_MIN_BLOCKS
 #define DRT_PRIMARY_MIN_BLOCKS 3
 #endif
+// Most blocks of the primary edge kernel: one sample per thread up to this
+// many blocks (measured fastest: balanced blocks, no partial last wave), then
+// several per thread.
+#ifndef DRT_PRIMARY_BLOCK_CAP
+#define DRT_PRIMARY_BLOCK_CAP (1 << 20)
+#endif
 // Primary edge side paths traced by the warp-cooperative traversals (1) or
 // one traversal per lane (0); both give the same hits.
 #ifndef DRT_PRIMARY_WARP
@@ -41,7 +47,6 @@ constexpr int kGlobals = 16;  // d_radiance[3], d_cam[12], d_cam_scale[1]
 // ---- smooth float3 helpers (contraction allowed) ---------------------------
 __device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
 __device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ float3 operator-(float3 a) { return make_float3(-a.x, -a.y, -a.z); }
 __device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
 __device__ __forceinline__ float3 operator*(float3 a, float3 b) { return make_float3(a.x * b.x, a.y * b.y, a.z * b.z); }
 __device__ __forceinline__ void operator+=(float3& a, float3 b) { a.x += b.x; a.y += b.y; a.z += b.z; }
@@ -154,14 +159,32 @@ __device__ __forceinline__ void block_globals(float g[kGlobals], float* row, boo
   }
 }
 
-// One warp per column; each lane sums a fixed stride of rows, then a fixed
-// butterfly, so the result does not depend on scheduling.
-__device__ __forceinline__ void reduce_globals(const float* partials, int rows, float* d_radiance, float* d_cam,
-                                               float* d_scale) {
+// Deterministic two-stage sum of the partial rows (the result does not depend
+// on scheduling).  Stage 1: block c sums rows [c*kReduceRows, (c+1)*kReduceRows)
+// per column in FP64, 16 row groups in a fixed stride, then the groups in
+// order.  Stage 2: one warp per column sums the chunk totals in a fixed stride
+// and a fixed butterfly.
+constexpr int kReduceRows = 256;
+__global__ void k_reduce_rows(const float* partials, int64_t rows, double* chunks) {
+  __shared__ double sm[kBlock];
+  int col = threadIdx.x & (kGlobals - 1), grp = threadIdx.x / kGlobals;  // kBlock / kGlobals = 16 groups
+  int64_t r0 = (int64_t)blockIdx.x * kReduceRows;
+  int64_t r1 = r0 + kReduceRows < rows ? r0 + kReduceRows : rows;
+  double acc = 0.0;
+  for (int64_t r = r0 + grp; r < r1; r += kBlock / kGlobals) acc += partials[r * kGlobals + col];
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  if (grp == 0) {
+    double t = 0.0;
+    for (int g = 0; g < kBlock / kGlobals; ++g) t += sm[g * kGlobals + col];
+    chunks[(int64_t)blockIdx.x * kGlobals + col] = t;
+  }
+}
+__global__ void k_reduce_chunks(const double* chunks, int64_t n, float* d_radiance, float* d_cam, float* d_scale) {
   int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (i >= kGlobals) return;
   double acc = 0.0;
-  for (int r = lane; r < rows; r += 32) acc += partials[(size_t)r * kGlobals + i];
+  for (int64_t c = lane; c < n; c += 32) acc += chunks[c * kGlobals + i];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
   if (lane != 0) return;
@@ -169,9 +192,6 @@ __device__ __forceinline__ void reduce_globals(const float* partials, int rows, 
   if (i < 3) { if (d_radiance) d_radiance[i] += v; }
   else if (i < 15) { if (d_cam) d_cam[i - 3] += v; }
   else if (d_scale) d_scale[0] += v;
-}
-__global__ void k_reduce_globals(const float* partials, int rows, float* d_radiance, float* d_cam, float* d_scale) {
-  reduce_globals(partials, rows, d_radiance, d_cam, d_scale);
 }
 
 // ---- shading data of a hit -------------------------------------------------
@@ -1535,14 +1555,6 @@ __global__ void k_batch_keys(const BatchScene* bs, const int64_t* eprefix, int n
   vals[g] = (int32_t)j;
 }
 
-// One block per scene: the fixed-order reduction of its partial rows.
-__global__ void k_batch_reduce(const BatchScene* bs) {
-  const BatchScene& b = bs[blockIdx.x];
-  int rows = (int)(b.rows_i + b.blocks_e);
-  if (b.d_image == nullptr || rows == 0) return;
-  reduce_globals(b.partials, rows, b.d_radiance, b.d_cam, b.d_scale);
-}
-
 template <int PH>
 cudaError_t launch_phase(const BatchScene* bs, const int64_t* prefix, int n, int64_t n_items, int grid, int chunk,
                          unsigned long long* counter, cudaStream_t st) {
@@ -1571,7 +1583,7 @@ int64_t pixel_blocks(int W, int H, int spp) {
 }
 
 void primary_blocks(int64_t n_edge, int64_t* blocks_e, int64_t* per_thread) {
-  *blocks_e = std::min<int64_t>((n_edge + kBlock - 1) / kBlock, 152 * 16);
+  *blocks_e = std::min<int64_t>((n_edge + kBlock - 1) / kBlock, DRT_PRIMARY_BLOCK_CAP);
   *per_thread = *blocks_e > 0 ? (n_edge + *blocks_e * kBlock - 1) / (*blocks_e * kBlock) : 0;
 }
 
@@ -1622,9 +1634,20 @@ cudaError_t launch_batch_keys(const BatchScene* bs, const int64_t* eprefix, int 
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_reduce(const BatchScene* bs, int n, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  DRT_PROF_LAUNCH("batch_reduce_globals", st, k_batch_reduce<<<n, 32 * kGlobals, 0, st>>>(bs));
+int64_t partial_floats(int64_t rows) {
+  int64_t chunks = (rows + kReduceRows - 1) / kReduceRows;
+  return rows * kGlobals + 2 * kGlobals * chunks;  // rows, then FP64 chunk totals
+}
+
+cudaError_t launch_reduce_globals(float* partials, int64_t rows, float* d_radiance, float* d_cam, float* d_scale,
+                                  cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  int64_t chunks = (rows + kReduceRows - 1) / kReduceRows;
+  double* ch = reinterpret_cast<double*>(partials + rows * kGlobals);
+  ProfToken pt = prof_begin("reduce_globals", st);
+  k_reduce_rows<<<(unsigned)chunks, kBlock, 0, st>>>(partials, rows, ch);
+  k_reduce_chunks<<<1, 32 * kGlobals, 0, st>>>(ch, chunks, d_radiance, d_cam, d_scale);
+  prof_end(pt, st);
   return cudaGetLastError();
 }
 
@@ -1698,12 +1721,9 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
     k_backward_primary<<<(unsigned)blocks_e, kBlock, 0, st>>>(s, op, d_image, ge, n_edge, per_thread, order);
     prof_end(pt, st);
   }
-  int rows = (int)((need_i ? blocks_i : 0) + blocks_e);
-  if (rows > 0) {
-    ProfToken pt = prof_begin("reduce_globals", st);
-    k_reduce_globals<<<1, 32 * kGlobals, 0, st>>>(partials, rows, d_radiance, d_cam, d_cam_scale);
-    prof_end(pt, st);
-  }
+  cudaError_t e = launch_reduce_globals(partials, (need_i ? blocks_i : 0) + blocks_e, d_radiance, d_cam, d_cam_scale,
+                                        st);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
