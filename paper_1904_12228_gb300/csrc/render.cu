@@ -36,6 +36,14 @@ constexpr int kBlock = 256;
 #ifndef DRT_PIXEL_MIN_BLOCKS
 #define DRT_PIXEL_MIN_BLOCKS 2
 #endif
+// Resident CTAs per SM the render kernel is compiled for.
+#ifndef DRT_RENDER_MIN_BLOCKS
+#define DRT_RENDER_MIN_BLOCKS 4
+#endif
+// Resident CTAs per SM the depth > 1 path pass is compiled for.
+#ifndef DRT_PATH_MIN_BLOCKS
+#define DRT_PATH_MIN_BLOCKS 1
+#endif
 // Camera paths of the forward pass traced warp-cooperatively (1) or per lane (0).
 #ifndef DRT_RENDER_WARP
 #define DRT_RENDER_WARP 1
@@ -536,7 +544,7 @@ __device__ __forceinline__ void render_block(const SceneView& s, const Opts& op,
     image[3 * pix + 2] = acc.z * inv;
   }
 }
-__global__ void __launch_bounds__(kBlock) k_render(SceneView s, Opts op, float* image, int32_t* tape_tri,
+__global__ void __launch_bounds__(kBlock, DRT_RENDER_MIN_BLOCKS) k_render(SceneView s, Opts op, float* image, int32_t* tape_tri,
                                                    float2* tape_bary, int G) {
   render_block(s, op, image, tape_tri, tape_bary, G, blockIdx.x);
 }
@@ -1299,7 +1307,7 @@ __device__ __forceinline__ void path_block(const SceneView& s, const Opts& op, c
   cache_flush(ca, gr.albedo);
   block_globals(g, gr.partials + blk * kGlobals, false);
 }
-__global__ void __launch_bounds__(kBlock) k_backward_path(SceneView s, Opts op, const int32_t* tape_tri,
+__global__ void __launch_bounds__(kBlock, DRT_PATH_MIN_BLOCKS) k_backward_path(SceneView s, Opts op, const int32_t* tape_tri,
                                                           const float2* tape_bary, const float* d_image, Grads gr,
                                                           int G) {
   path_block(s, op, tape_tri, tape_bary, d_image, gr, G, blockIdx.x);
@@ -1485,9 +1493,9 @@ struct PhaseMinBlocks {
   // resident CTAs per SM as the single-scene kernels have; the depth > 1
   // path pass needs more registers
   static constexpr int value =
-      PH == kPhasePath ? 1
+      PH == kPhasePath ? DRT_PATH_MIN_BLOCKS
                        : (PH == kPhasePrimary ? DRT_PRIMARY_MIN_BLOCKS
-                                              : (PH == kPhaseRender ? 2 : DRT_PIXEL_MIN_BLOCKS));
+                                              : (PH == kPhaseRender ? DRT_RENDER_MIN_BLOCKS : DRT_PIXEL_MIN_BLOCKS));
 };
 
 template <int PH>
