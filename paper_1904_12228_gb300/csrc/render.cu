@@ -27,11 +27,6 @@ constexpr int kBlock = 256;
 #ifndef DRT_PRIMARY_BLOCK_CAP
 #define DRT_PRIMARY_BLOCK_CAP (1 << 20)
 #endif
-// Primary edge side paths traced by the warp-cooperative traversals (1) or
-// one traversal per lane (0); both give the same hits.
-#ifndef DRT_PRIMARY_WARP
-#define DRT_PRIMARY_WARP 1
-#endif
 // Resident CTAs per SM the interior and secondary edge passes are compiled for.
 #ifndef DRT_PIXEL_MIN_BLOCKS
 #define DRT_PIXEL_MIN_BLOCKS 2
@@ -43,10 +38,6 @@ constexpr int kBlock = 256;
 // Resident CTAs per SM the depth > 1 path pass is compiled for.
 #ifndef DRT_PATH_MIN_BLOCKS
 #define DRT_PATH_MIN_BLOCKS 1
-#endif
-// Camera paths of the forward pass traced warp-cooperatively (1) or per lane (0).
-#ifndef DRT_RENDER_WARP
-#define DRT_RENDER_WARP 1
 #endif
 static_assert(kBlock / 32 <= kTraceWarps, "warp-cooperative traversals support at most kTraceWarps warps per CTA");
 constexpr unsigned kFull = 0xffffffffu;
@@ -268,64 +259,6 @@ __device__ __forceinline__ float nee_geometry(const SceneView& s, float3 p, floa
   return cp * cy / r2 * (0.5f * nll) * invP;
 }
 
-// Radiance along a path (value only).  Vertices depth0..max_depth-1 are
-// shaded; emission is counted only at the first camera hit.  If tape_tri is
-// given, vertex b is stored at tape_tri[b*n_stride + n_idx].
-__device__ float3 path_value(const SceneView& s, const Opts& op, float o_in[3], float d_in[3], int exclude,
-                             bool emission_first, int depth0, uint32_t c0, uint32_t c1, uint32_t pass,
-                             int32_t* tape_tri, float2* tape_bary, int64_t n_idx, int64_t n_stride) {
-  float o[3] = {o_in[0], o_in[1], o_in[2]}, d[3] = {d_in[0], d_in[1], d_in[2]};
-  float3 L = zero3(), beta = make_float3(1.f, 1.f, 1.f);
-  int md = op.primary_only ? 1 : op.max_depth;
-  const float3 Le = ld3(s.radiance);
-  int b = depth0;
-  for (; b < md; ++b) {
-    Hit h = trace_closest(s, o, d, INFINITY, exclude);
-    if (h.tri < 0) break;
-    Vertex x;
-    load_vertex(s, h.tri, h.b1, h.b2, d, x);
-    float3 alb = ld3(s.albedo + 3 * x.k);
-    if (op.primary_only) {
-      L += beta * alb;
-      if (tape_tri) {
-        tape_tri[b * n_stride + n_idx] = x.k;
-        tape_bary[b * n_stride + n_idx] = make_float2(h.b1, h.b2);
-      }
-      ++b;
-      break;
-    }
-    if (b == depth0 && emission_first && s.light_of_tri[x.k] >= 0 && x.side < 0.0f) L += beta * Le;
-    float n32[3];
-    shading_normal32(x, n32);
-    int vis = 0;
-    if (s.L > 0) {
-      uint4 r = rng4(op.key, c0, c1, kLight, (uint32_t)b, pass, op.scene_id);
-      LightSample ls;
-      sample_light(s, r, ls);
-      float sd[3] = {fs(ls.y[0], x.p[0]), fs(ls.y[1], x.p[1]), fs(ls.y[2], x.p[2])};
-      if (!trace_any(s, x.p, sd, kShadowTmax, x.k, ls.lt)) {
-        vis = 1;
-        float g = nee_geometry(s, f3(x.p), f3(n32), ls);
-        L += (kInvPi * g) * (beta * alb * Le);
-      }
-    }
-    if (tape_tri) {
-      tape_tri[b * n_stride + n_idx] = x.k | (vis << 31);
-      tape_bary[b * n_stride + n_idx] = make_float2(h.b1, h.b2);
-    }
-    if (b + 1 >= md) { ++b; break; }
-    uint4 r = rng4(op.key, c0, c1, kBsdf, (uint32_t)b, pass, op.scene_id);
-    float nd[3];
-    cosine_dir(n32, u01f(r.x), u01f(r.y), nd);
-    if (!(dot(f3(n32), f3(nd)) > 0.f)) { ++b; break; }
-    beta = beta * alb;
-    for (int i = 0; i < 3; ++i) { o[i] = x.p[i]; d[i] = nd[i]; }
-    exclude = x.k;
-  }
-  if (tape_tri)
-    for (; b < md; ++b) tape_tri[b * n_stride + n_idx] = -1;
-  return L;
-}
 
 // path_value of a camera path (from depth 0, first emission counted) for the
 // 32 lanes of a warp together, traced by the warp-cooperative traversals.
@@ -412,10 +345,9 @@ __device__ float3 path_value_warp(const SceneView& s, const Opts& op, const floa
 }
 
 // Radiance along the two side paths of an edge sample (same counters, so the
-// same light and BSDF random numbers on both sides), traced pairwise.  With
-// kWarp all 32 lanes of the warp must call together (inactive lanes pass
-// act = false) and the rays are traced by the warp-cooperative traversals.
-template <bool kWarp>
+// same light and BSDF random numbers on both sides), traced pairwise by the
+// warp-cooperative traversals: all 32 lanes of the warp call together
+// (inactive lanes pass act = false).
 __device__ void path_value2(const SceneView& s, const Opts& op, float o[2][3], float d[2][3], uint32_t c0,
                             uint32_t c1, uint32_t pass, float3 L[2], bool act) {
   const unsigned full = 0xffffffffu;
@@ -427,10 +359,7 @@ __device__ void path_value2(const SceneView& s, const Opts& op, float o[2][3], f
   L[0] = L[1] = zero3();
   for (int b = 0; b < md; ++b) {
     Hit h[2];
-    if (kWarp)
-      trace_closest2_warp(s, o[0], d[0], o[1], d[1], alive[0], alive[1], exclude[0], exclude[1], h[0], h[1]);
-    else
-      trace_closest2(s, o[0], d[0], o[1], d[1], alive[0], alive[1], exclude[0], exclude[1], h[0], h[1]);
+    trace_closest2_warp(s, o[0], d[0], o[1], d[1], alive[0], alive[1], exclude[0], exclude[1], h[0], h[1]);
     Vertex x[2];
     float3 alb[2];
     for (int q = 0; q < 2; ++q) {
@@ -445,7 +374,7 @@ __device__ void path_value2(const SceneView& s, const Opts& op, float o[2][3], f
       }
       if (b == 0 && s.light_of_tri[x[q].k] >= 0 && x[q].side < 0.0f) L[q] += beta[q] * Le;
     }
-    if (kWarp ? !__any_sync(full, alive[0] || alive[1]) : (!alive[0] && !alive[1])) break;
+    if (!__any_sync(full, alive[0] || alive[1])) break;
     float n32[2][3];
     for (int q = 0; q < 2; ++q)
       if (alive[q]) shading_normal32(x[q], n32[q]);
@@ -458,12 +387,8 @@ __device__ void path_value2(const SceneView& s, const Opts& op, float o[2][3], f
         if (alive[q])
           for (int i = 0; i < 3; ++i) sd[q][i] = fs(ls.y[i], x[q].p[i]);
       bool occ[2];
-      if (kWarp)
-        trace_any2_warp(s, x[0].p, sd[0], x[0].k, ls.lt, x[1].p, sd[1], x[1].k, ls.lt, alive[0], alive[1],
-                        kShadowTmax, occ[0], occ[1]);
-      else
-        trace_any2(s, x[0].p, sd[0], x[0].k, ls.lt, x[1].p, sd[1], x[1].k, ls.lt, alive[0], alive[1], kShadowTmax,
-                   occ[0], occ[1]);
+      trace_any2_warp(s, x[0].p, sd[0], x[0].k, ls.lt, x[1].p, sd[1], x[1].k, ls.lt, alive[0], alive[1],
+                      kShadowTmax, occ[0], occ[1]);
       for (int q = 0; q < 2; ++q)
         if (alive[q] && !occ[q]) {
           float g = nee_geometry(s, f3(x[q].p), f3(n32[q]), ls);
@@ -481,7 +406,72 @@ __device__ void path_value2(const SceneView& s, const Opts& op, float o[2][3], f
       for (int i = 0; i < 3; ++i) { o[q][i] = x[q].p[i]; d[q][i] = nd[i]; }
       exclude[q] = x[q].k;
     }
-    if (kWarp ? !__any_sync(full, alive[0] || alive[1]) : (!alive[0] && !alive[1])) break;
+    if (!__any_sync(full, alive[0] || alive[1])) break;
+  }
+}
+
+// The two side paths of a secondary edge sample at path depth depth0 - 1,
+// continued from their first hits h[q] (traced by the caller from the vertex
+// along d[q], the vertex's triangle skipped): what path_value returns for each
+// side with emission_first = false, both sides with the same random numbers,
+// traced pairwise.  act[q] = false: side q contributes 0.
+__device__ void path_value2_from(const SceneView& s, const Opts& op, const float d_in[2][3], const Hit h_in[2],
+                                 const bool act[2], int depth0, uint32_t c0, uint32_t c1, uint32_t pass,
+                                 float3 L[2]) {
+  int md = op.primary_only ? 1 : op.max_depth;
+  const float3 Le = ld3(s.radiance);
+  bool alive[2] = {act[0], act[1]};
+  float o[2][3], d[2][3];
+  int exclude[2] = {-1, -1};
+  for (int q = 0; q < 2; ++q)
+    for (int i = 0; i < 3; ++i) { o[q][i] = 0.f; d[q][i] = d_in[q][i]; }
+  float3 beta[2] = {make_float3(1.f, 1.f, 1.f), make_float3(1.f, 1.f, 1.f)};
+  L[0] = L[1] = zero3();
+  Hit h[2] = {h_in[0], h_in[1]};
+  for (int b = depth0; b < md; ++b) {
+    if (b > depth0)
+      trace_closest2(s, o[0], d[0], o[1], d[1], alive[0], alive[1], exclude[0], exclude[1], h[0], h[1]);
+    Vertex x[2];
+    float3 alb[2];
+    for (int q = 0; q < 2; ++q) {
+      if (!alive[q]) continue;
+      if (h[q].tri < 0) { alive[q] = false; continue; }
+      load_vertex(s, h[q].tri, h[q].b1, h[q].b2, d[q], x[q]);
+      alb[q] = ld3(s.albedo + 3 * x[q].k);
+    }
+    if (!alive[0] && !alive[1]) break;
+    float n32[2][3];
+    for (int q = 0; q < 2; ++q)
+      if (alive[q]) shading_normal32(x[q], n32[q]);
+    if (s.L > 0) {
+      uint4 r = rng4(op.key, c0, c1, kLight, (uint32_t)b, pass, op.scene_id);
+      LightSample ls;
+      sample_light(s, r, ls);
+      float sd[2][3];
+      for (int q = 0; q < 2; ++q)
+        if (alive[q])
+          for (int i = 0; i < 3; ++i) sd[q][i] = fs(ls.y[i], x[q].p[i]);
+      bool occ[2];
+      trace_any2(s, x[0].p, sd[0], x[0].k, ls.lt, x[1].p, sd[1], x[1].k, ls.lt, alive[0], alive[1], kShadowTmax,
+                 occ[0], occ[1]);
+      for (int q = 0; q < 2; ++q)
+        if (alive[q] && !occ[q]) {
+          float g = nee_geometry(s, f3(x[q].p), f3(n32[q]), ls);
+          L[q] += (kInvPi * g) * (beta[q] * alb[q] * Le);
+        }
+    }
+    if (b + 1 >= md) break;
+    uint4 r = rng4(op.key, c0, c1, kBsdf, (uint32_t)b, pass, op.scene_id);
+    for (int q = 0; q < 2; ++q) {
+      if (!alive[q]) continue;
+      float nd[3];
+      cosine_dir(n32[q], u01f(r.x), u01f(r.y), nd);
+      if (!(dot(f3(n32[q]), f3(nd)) > 0.f)) { alive[q] = false; continue; }
+      beta[q] = beta[q] * alb[q];
+      for (int i = 0; i < 3; ++i) { o[q][i] = x[q].p[i]; d[q][i] = nd[i]; }
+      exclude[q] = x[q].k;
+    }
+    if (!alive[0] && !alive[1]) break;
   }
 }
 
@@ -504,7 +494,6 @@ __device__ __forceinline__ void render_block(const SceneView& s, const Opts& op,
   bool active = pix < npix;
   int64_t n = (int64_t)npix * op.spp;
   float3 acc = zero3();
-#if DRT_RENDER_WARP
   // the warp traces its lanes' samples together: every lane runs the same
   // number of rounds
   int iters = (op.spp + G - 1) / G;
@@ -521,17 +510,6 @@ __device__ __forceinline__ void render_block(const SceneView& s, const Opts& op,
                                pix * op.spp + sidx, n);
     if (act) acc += v;
   }
-#else
-  if (active) {
-    for (int sidx = lane % G; sidx < op.spp; sidx += G) {
-      float sx, sy, o[3], d[3];
-      jitter(op, (int)pix, sidx, s.W, &sx, &sy);
-      camera_ray(s, sx, sy, o, d);
-      acc += path_value(s, op, o, d, -1, true, 0, (uint32_t)pix, (uint32_t)sidx, kPassInterior, tape_tri, tape_bary,
-                        pix * op.spp + sidx, n);
-    }
-  }
-#endif
   for (int o = G >> 1; o > 0; o >>= 1) {
     acc.x += __shfl_xor_sync(kFull, acc.x, o);
     acc.y += __shfl_xor_sync(kFull, acc.y, o);
@@ -1112,22 +1090,40 @@ __device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Op
   float wl2 = dot(w, w);
   float3 what = (1.f / sqrtf(wl2)) * w;
   bool last = b + 1 >= md;
+  // both side rays in one traversal; sides that cannot contribute are not traced
+  float dsd[2][3];
+  bool act[2];
   for (int side = 0; side < 2; ++side) {
-    float sg = side == 0 ? 1.f : -1.f;
-    float dsd[3];
-    for (int i = 0; i < 3; ++i) dsd[i] = side == 0 ? fa(om[i], fm(sh, nh32[i])) : fs(om[i], fm(sh, nh32[i]));
-    if (dot(n, f3(dsd)) < -1e-5f * wl) continue;
-    if (last && !may_reach_light(s, x.p, dsd)) continue;
-    Hit hm = trace_closest(s, x.p, dsd, INFINITY, x.k);
-    if (hm.tri < 0) continue;
+    for (int i = 0; i < 3; ++i)
+      dsd[side][i] = side == 0 ? fa(om[i], fm(sh, nh32[i])) : fs(om[i], fm(sh, nh32[i]));
+    act[side] = !(dot(n, f3(dsd[side])) < -1e-5f * wl) && !(last && !may_reach_light(s, x.p, dsd[side]));
+  }
+  Hit hms[2];
+  trace_closest2(s, x.p, dsd[0], x.p, dsd[1], act[0], act[1], x.k, x.k, hms[0], hms[1]);
+  float cpms[2] = {0.f, 0.f};
+  for (int side = 0; side < 2; ++side) {
+    if (!act[side] || hms[side].tri < 0) { act[side] = false; continue; }
     Vertex mv;
-    load_vertex(s, hm.tri, hm.b1, hm.b2, dsd, mv);
+    load_vertex(s, hms[side].tri, hms[side].b1, hms[side].b2, dsd[side], mv);
+    float3 dmp = f3(mv.p) - p;
+    cpms[side] = dot(n, (1.f / sqrtf(dot(dmp, dmp))) * dmp);
+    if (!(cpms[side] > 0.f)) act[side] = false;
+  }
+  // radiance along both continuation paths, from the hits found above
+  float3 Lr[2] = {zero3(), zero3()};
+  if (!last && (act[0] || act[1]))
+    path_value2_from(s, op, dsd, hms, act, b + 1, c0, c1, kPassSecondaryBase + (uint32_t)b, Lr);
+  for (int side = 0; side < 2; ++side) {
+    if (!act[side]) continue;
+    float sg = side == 0 ? 1.f : -1.f;
+    const Hit& hm = hms[side];
+    Vertex mv;
+    load_vertex(s, hm.tri, hm.b1, hm.b2, dsd[side], mv);
     float3 m = f3(mv.p);
     float3 dmp = m - p;
     float mr2 = dot(dmp, dmp);
     float3 wh = (1.f / sqrtf(mr2)) * dmp;
     float cpm = dot(n, wh);
-    if (!(cpm > 0.f)) continue;
     if (s.light_of_tri[hm.tri] >= 0) {
       float3 nmu = f3(mv.nu);
       float3 nm = (1.f / len(nmu)) * nmu;
@@ -1155,10 +1151,8 @@ __device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Op
       }
     }
     if (!last) {
-      float o2[3] = {x.p[0], x.p[1], x.p[2]}, d2[3] = {dsd[0], dsd[1], dsd[2]};
-      float3 Lr = path_value(s, op, o2, d2, x.k, false, b + 1, c0, c1, kPassSecondaryBase + (uint32_t)b, nullptr,
-                             nullptr, 0, 0);
-      float hs = kInvPi * cpm * (ab.x * alb.x * Lr.x + ab.y * alb.y * Lr.y + ab.z * alb.z * Lr.z);
+      float3 lr = Lr[side];
+      float hs = kInvPi * cpm * (ab.x * alb.x * lr.x + ab.y * alb.y * lr.y + ab.z * alb.z * lr.z);
       if (hs != 0.f) {
         float cc = sg * hs / wl2 * invPE;
         float3 gv0 = cross(a1v, what), gv1 = cross(what, a0v);
@@ -1423,7 +1417,7 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
       camera_ray(s, xl, yl, o2[1], d2[1]);
     }
     float3 L2[2];
-    path_value2<DRT_PRIMARY_WARP != 0>(s, op, o2, d2, (uint32_t)j, 0u, kPassPrimaryEdge, L2, active);
+    path_value2(s, op, o2, d2, (uint32_t)j, 0u, kPassPrimaryEdge, L2, active);
     if (active) {
       int e = es.e;
       float ax = es.ax, ay = es.ay, bx = es.bx, by = es.by, x = es.x, y = es.y;
