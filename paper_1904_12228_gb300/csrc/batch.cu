@@ -39,7 +39,6 @@ namespace {
 
 constexpr int kMaxBatch = 1 << 16;
 constexpr int kRowFloats = 16;     // global parameters per partial-sum row
-constexpr int kBlockThreads = 256; // threads per CTA of the render kernels
 
 drt_status bfail(drt_status st, const char* msg) {
   drt::set_last_error(msg);
@@ -174,7 +173,7 @@ void plan(drt_batch* b, bool bind) {
         drt::primary_blocks(n_edge, &be, &pt);
         if (b->shape.edge_mult > 1) {
           pt *= b->shape.edge_mult;
-          be = (n_edge + kBlockThreads * pt - 1) / (kBlockThreads * pt);
+          be = drt::primary_blocks_for(n_edge, pt);
         }
         d.n_edge = n_edge;
         d.per_thread = pt;

@@ -127,6 +127,7 @@ cudaError_t launch_debug_closest(const drt_scene* s, int64_t n, const float* o, 
 int pixel_group(int spp);                          // lanes per pixel
 int64_t pixel_blocks(int W, int H, int spp);       // blocks of the pixel passes
 void primary_blocks(int64_t n_edge, int64_t* blocks_e, int64_t* per_thread);
+int64_t primary_blocks_for(int64_t n_edge, int64_t per_thread);  // blocks at a given samples per thread
 int screen_key_bits(int W, int H);                 // bits of a pixel's screen key
 // batched scenes (persistent kernels; phase = BatchPhase)
 cudaError_t launch_batch_phase(int phase, const BatchScene* bs, const int64_t* prefix, int n, int64_t n_items,

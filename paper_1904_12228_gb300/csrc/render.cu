@@ -19,7 +19,7 @@ constexpr int kBlock = 256;
 // Resident CTAs per SM the primary edge kernel is compiled for (its register
 // cap is 65536 / (kBlock * this)).
 #ifndef DRT_PRIMARY_MIN_BLOCKS
-#define DRT_PRIMARY_MIN_BLOCKS 3
+#define DRT_PRIMARY_MIN_BLOCKS 4
 #endif
 // Most blocks of the primary edge kernel: one sample per thread up to this
 // many blocks (measured fastest: balanced blocks, no partial last wave), then
@@ -342,72 +342,6 @@ __device__ float3 path_value_warp(const SceneView& s, const Opts& op, const floa
   if (tape_tri && act)
     for (int b = b_end; b < md; ++b) tape_tri[b * n_stride + n_idx] = -1;
   return L;
-}
-
-// Radiance along the two side paths of an edge sample (same counters, so the
-// same light and BSDF random numbers on both sides), traced pairwise by the
-// warp-cooperative traversals: all 32 lanes of the warp call together
-// (inactive lanes pass act = false).
-__device__ void path_value2(const SceneView& s, const Opts& op, float o[2][3], float d[2][3], uint32_t c0,
-                            uint32_t c1, uint32_t pass, float3 L[2], bool act) {
-  const unsigned full = 0xffffffffu;
-  int md = op.primary_only ? 1 : op.max_depth;
-  const float3 Le = ld3(s.radiance);
-  bool alive[2] = {act, act};
-  int exclude[2] = {-1, -1};
-  float3 beta[2] = {make_float3(1.f, 1.f, 1.f), make_float3(1.f, 1.f, 1.f)};
-  L[0] = L[1] = zero3();
-  for (int b = 0; b < md; ++b) {
-    Hit h[2];
-    trace_closest2_warp(s, o[0], d[0], o[1], d[1], alive[0], alive[1], exclude[0], exclude[1], h[0], h[1]);
-    Vertex x[2];
-    float3 alb[2];
-    for (int q = 0; q < 2; ++q) {
-      if (!alive[q]) continue;
-      if (h[q].tri < 0) { alive[q] = false; continue; }
-      load_vertex(s, h[q].tri, h[q].b1, h[q].b2, d[q], x[q]);
-      alb[q] = ld3(s.albedo + 3 * x[q].k);
-      if (op.primary_only) {
-        L[q] += beta[q] * alb[q];
-        alive[q] = false;
-        continue;
-      }
-      if (b == 0 && s.light_of_tri[x[q].k] >= 0 && x[q].side < 0.0f) L[q] += beta[q] * Le;
-    }
-    if (!__any_sync(full, alive[0] || alive[1])) break;
-    float n32[2][3];
-    for (int q = 0; q < 2; ++q)
-      if (alive[q]) shading_normal32(x[q], n32[q]);
-    if (s.L > 0) {
-      uint4 r = rng4(op.key, c0, c1, kLight, (uint32_t)b, pass, op.scene_id);
-      LightSample ls;
-      sample_light(s, r, ls);
-      float sd[2][3];
-      for (int q = 0; q < 2; ++q)
-        if (alive[q])
-          for (int i = 0; i < 3; ++i) sd[q][i] = fs(ls.y[i], x[q].p[i]);
-      bool occ[2];
-      trace_any2_warp(s, x[0].p, sd[0], x[0].k, ls.lt, x[1].p, sd[1], x[1].k, ls.lt, alive[0], alive[1],
-                      kShadowTmax, occ[0], occ[1]);
-      for (int q = 0; q < 2; ++q)
-        if (alive[q] && !occ[q]) {
-          float g = nee_geometry(s, f3(x[q].p), f3(n32[q]), ls);
-          L[q] += (kInvPi * g) * (beta[q] * alb[q] * Le);
-        }
-    }
-    if (b + 1 >= md) break;
-    uint4 r = rng4(op.key, c0, c1, kBsdf, (uint32_t)b, pass, op.scene_id);
-    for (int q = 0; q < 2; ++q) {
-      if (!alive[q]) continue;
-      float nd[3];
-      cosine_dir(n32[q], u01f(r.x), u01f(r.y), nd);
-      if (!(dot(f3(n32[q]), f3(nd)) > 0.f)) { alive[q] = false; continue; }
-      beta[q] = beta[q] * alb[q];
-      for (int i = 0; i < 3; ++i) { o[q][i] = x[q].p[i]; d[q][i] = nd[i]; }
-      exclude[q] = x[q].k;
-    }
-    if (!__any_sync(full, alive[0] || alive[1])) break;
-  }
 }
 
 // The two side paths of a secondary edge sample at path depth depth0 - 1,
@@ -1381,47 +1315,55 @@ __global__ void k_primary_keys(SceneView s, Opts op, int64_t n_edge, uint32_t* k
   keys[j] = key;
   vals[j] = (int32_t)j;
 }
+// Two lanes per edge sample: the even lane traces the side at +eps, the odd
+// lane the side at -eps, each a single-ray warp-cooperative path (as the
+// camera paths of the forward pass); the pair exchanges radiance with one
+// shuffle and the even lane forms the difference, the adjoint and the scatter.
+constexpr int kPrimaryPerRound = kBlock / 2;  // edge samples per block and round
 __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op, const float* d_image, Grads gr,
-                                                             int64_t n_edge, int64_t per_thread,
-                                                             const int32_t* order, int64_t blk) {
+                                              int64_t n_edge, int64_t per_thread, const int32_t* order,
+                                              int64_t blk) {
   float g[kGlobals];
   for (int i = 0; i < kGlobals; ++i) g[i] = 0.f;
   double ptotal = s.pcdf[s.E - 1];
   float W = (float)s.W, H = (float)s.H;
   float eps = fm(op.eps_rel, fmaxf(W, H));
+  const int side = threadIdx.x & 1;
   for (int64_t it = 0; it < per_thread; ++it) {
-    // consecutive threads take consecutive entries of the screen-ordered list
-    int64_t i = blk * kBlock * per_thread + it * kBlock + threadIdx.x;
+    // consecutive lane pairs take consecutive entries of the screen-ordered list
+    int64_t i = blk * kPrimaryPerRound * per_thread + it * kPrimaryPerRound + (threadIdx.x >> 1);
     int64_t j = i < n_edge ? (order ? (int64_t)order[i] : i) : n_edge;
     bool active = j < n_edge && ptotal > 0.0 && j >= op.edge_begin && j < op.edge_end;
     float3 da3 = zero3(), db3 = zero3();
     int ia = 0, ib = 0;
-    EdgeSample es;
-    if (active) {
+    EdgeSample es = {};
+    if (active && side == 0) {
       es = primary_sample(s, op, j, ptotal);
       active = es.valid;
     }
-    // side rays at +-eps along the edge normal (all lanes take part in the
-    // warp-cooperative tracing below; inactive lanes trace nothing)
-    float o2[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, d2[2][3] = {{0.f, 0.f, 1.f}, {0.f, 0.f, 1.f}};
+    // the odd lane takes the sample's point and direction from its pair
+    float x = __shfl_sync(kFull, es.x, threadIdx.x & ~1), y = __shfl_sync(kFull, es.y, threadIdx.x & ~1);
+    float dx = __shfl_sync(kFull, es.dx, threadIdx.x & ~1), dy = __shfl_sync(kFull, es.dy, threadIdx.x & ~1);
+    active = __shfl_sync(kFull, active, threadIdx.x & ~1);
+    float o[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 1.f};
     float3 w = zero3();
     if (active) {
-      float dx = es.dx, dy = es.dy, x = es.x, y = es.y;
       float nlen = fsq(fa(fm(dx, dx), fm(dy, dy)));
       float nx = fdv(-dy, nlen), ny = fdv(dx, nlen);
-      float xu = fa(x, fm(eps, nx)), yu = fa(y, fm(eps, ny));
-      float xl = fs(x, fm(eps, nx)), yl = fs(y, fm(eps, ny));
+      float xs = side == 0 ? fa(x, fm(eps, nx)) : fs(x, fm(eps, nx));
+      float ys = side == 0 ? fa(y, fm(eps, ny)) : fs(y, fm(eps, ny));
       int px = min(max((int)floorf(x), 0), s.W - 1), py = min(max((int)floorf(y), 0), s.H - 1);
       w = ld3(d_image + 3 * ((int64_t)py * s.W + px));
-      camera_ray(s, xu, yu, o2[0], d2[0]);
-      camera_ray(s, xl, yl, o2[1], d2[1]);
+      camera_ray(s, xs, ys, o, d);
     }
-    float3 L2[2];
-    path_value2(s, op, o2, d2, (uint32_t)j, 0u, kPassPrimaryEdge, L2, active);
+    float3 Lme = path_value_warp(s, op, o, d, active, (uint32_t)j, 0u, kPassPrimaryEdge, nullptr, nullptr, 0, 0);
+    float3 Lot = make_float3(__shfl_xor_sync(kFull, Lme.x, 1), __shfl_xor_sync(kFull, Lme.y, 1),
+                             __shfl_xor_sync(kFull, Lme.z, 1));
+    if (side != 0) active = false;
     if (active) {
       int e = es.e;
-      float ax = es.ax, ay = es.ay, bx = es.bx, by = es.by, x = es.x, y = es.y;
-      float diff = dot(w, L2[0] - L2[1]);
+      float ax = es.ax, ay = es.ay, bx = es.bx, by = es.by;
+      float diff = dot(w, Lme - Lot);
       if (op.seg_log && es.seg >= 0) atomicAdd(op.seg_log + es.seg, fabsf(diff));
       if (diff != 0.f) {
         float gl = sqrtf((ax - bx) * (ax - bx) + (ay - by) * (ay - by));
@@ -1585,8 +1527,12 @@ int64_t pixel_blocks(int W, int H, int spp) {
 }
 
 void primary_blocks(int64_t n_edge, int64_t* blocks_e, int64_t* per_thread) {
-  *blocks_e = std::min<int64_t>((n_edge + kBlock - 1) / kBlock, DRT_PRIMARY_BLOCK_CAP);
-  *per_thread = *blocks_e > 0 ? (n_edge + *blocks_e * kBlock - 1) / (*blocks_e * kBlock) : 0;
+  *blocks_e = std::min<int64_t>((n_edge + kPrimaryPerRound - 1) / kPrimaryPerRound, DRT_PRIMARY_BLOCK_CAP);
+  *per_thread = *blocks_e > 0 ? (n_edge + *blocks_e * kPrimaryPerRound - 1) / (*blocks_e * kPrimaryPerRound) : 0;
+}
+
+int64_t primary_blocks_for(int64_t n_edge, int64_t per_thread) {
+  return (n_edge + kPrimaryPerRound * per_thread - 1) / (kPrimaryPerRound * per_thread);
 }
 
 int screen_key_bits(int W, int H) {
