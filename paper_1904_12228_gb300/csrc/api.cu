@@ -127,7 +127,8 @@ void free_scene_buffers(drt_scene* s) {
                   s->slen, s->scdf, s->scan_tmp, s->keys, s->keys2, s->vals, s->vals2, s->parent, s->leaf_parent,
                   s->flags, s->child_orig, s->hist, s->hist_tmp, s->bounds, s->partials, s->esort.keys, s->esort.keys2,
                   s->esort.hist, s->esort.hist_tmp, s->esort.vals, s->esort.vals2, s->seg_edge, s->seg_tile,
-                  s->seg_count, s->seg_scan_tmp, s->seg_s, s->seg_len, s->seg_a, s->seg_b, s->seg_cdf, s->seg_tmp};
+                  s->seg_count, s->seg_scan_tmp, s->seg_s, s->seg_len, s->seg_a, s->seg_b, s->seg_cdf, s->seg_tmp,
+                  s->sec.dp, s->sec.queue, s->sec.count};
   for (void* b : bufs) dfree(b);
 }
 
@@ -520,9 +521,31 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
     }
     sort = &s->esort;
   }
+  // secondary edge samples that need rays are queued and traced apart
+  const drt::SecScratch* secs = nullptr;
+  if (!op.primary_only && (op.terms & 4) && s->E > 0 && s->L > 0) {
+    int64_t cap = drt::secondary_capacity(s->W, s->H, op);
+    if (cap > s->sec.cap) {
+      cudaStreamSynchronize(st);
+      drt::SecScratch& b = s->sec;
+      dfree(b.dp);
+      dfree(b.queue);
+      dfree(b.count);
+      b = drt::SecScratch();
+      drt_status a = dalloc_n(&b.dp, 3 * (size_t)cap);
+      if (a == DRT_OK) a = dalloc_n(&b.queue, (size_t)cap);
+      if (a == DRT_OK) a = dalloc_n(&b.count, 1);
+      if (a != DRT_OK) {
+        unstage(sg, 6, st);
+        return a;
+      }
+      b.cap = cap;
+    }
+    secs = &s->sec;
+  }
   cudaError_t e = drt::launch_backward(s, op, tape, (const float*)sg[0].dev, (float*)sg[1].dev, (float*)sg[2].dev,
                                        (float*)sg[3].dev, (float*)sg[4].dev, (float*)sg[5].dev, s->partials, sort,
-                                       st);
+                                       secs, st);
   r = unstage(sg, 6, st);
   if (e != cudaSuccess) return fail(DRT_ERR_CUDA, "backward launch: %s", cudaGetErrorString(e));
   return r;

@@ -4,9 +4,11 @@
 //
 // Plan.  Scene k of a batch does exactly the work of the single-scene calls
 // with opts.scene_id = k: the same pixels per virtual block, the same
-// partial-sum rows, the same sample order.  Each pass (render, interior,
-// secondary or path, primary edges) is one launch of a persistent kernel;
-// its CTAs take chunks of items from an atomic counter until none is left.
+// partial-sum rows, the same sample order.  Each pass (render, interior or
+// path, primary edges) is one launch of a persistent kernel; its CTAs take
+// chunks of items from an atomic counter until none is left.  Secondary edge
+// samples that need rays are queued and traced per scene between the render
+// and the interior or path pass, as in the single-scene backward.
 // The primary edge samples of all scenes are sorted once, with the scene
 // index above the screen key, which orders every scene's samples as its own
 // sort does.  Per-scene descriptors (scene view, options, output pointers)
@@ -38,7 +40,6 @@ using drt::BatchScene;
 namespace {
 
 constexpr int kMaxBatch = 1 << 16;
-constexpr int kRowFloats = 16;     // global parameters per partial-sum row
 
 drt_status bfail(drt_status st, const char* msg) {
   drt::set_last_error(msg);
@@ -97,9 +98,8 @@ struct drt_batch {
   std::vector<int64_t> prefix;   // kPhases x (n + 1)
   std::vector<int64_t> eprefix;  // n + 1
   int64_t n_items[drt::kPhases] = {};
-  int64_t total_edge = 0, total_tape = 0, total_floats = 0;
+  int64_t total_edge = 0, total_tape = 0, total_floats = 0, total_sec = 0;
   int pix_bits = 0, key_bits = 0;  // screen key bits; with the scene index above them
-  std::vector<std::pair<float*, size_t>> zero_rows;
   // device
   BatchScene* d_desc = nullptr;
   BatchScene* d_desc_tune = nullptr;
@@ -110,6 +110,9 @@ struct drt_batch {
   float2* tape_bary = nullptr;
   float* partials = nullptr;
   float* scratch = nullptr;  // gradient sink of the autotuner's probes
+  float* sec_dp = nullptr;   // secondary edge samples traced apart: vertex adjoints,
+  unsigned long long* sec_queue = nullptr;   // queues
+  unsigned long long* sec_counts = nullptr;  // and queue lengths (one per scene)
   uint32_t *keys = nullptr, *keys2 = nullptr, *hist = nullptr, *hist_tmp = nullptr;
   int32_t *vals = nullptr, *vals2 = nullptr;
   cudaStream_t cap = nullptr;
@@ -131,8 +134,7 @@ void plan(drt_batch* b, bool bind) {
   b->prefix.assign((size_t)drt::kPhases * (n + 1), 0);
   b->eprefix.assign(n + 1, 0);
   b->desc.assign(n, BatchScene{});
-  b->zero_rows.clear();
-  int64_t tape_off = 0, float_off = 0;
+  int64_t tape_off = 0, float_off = 0, sec_off = 0;
   int pix_bits = 2;
   for (int k = 0; k < n; ++k) {
     const drt_batch_item& it = b->items[k];
@@ -161,12 +163,24 @@ void plan(drt_batch* b, bool bind) {
       d.d_radiance = it.grads.d_radiance;
       d.d_cam = it.grads.d_cam_to_world;
       d.d_scale = it.grads.d_cam_scale;
-      const bool sec = !path && (op.terms & 4) && s->E > 0 && s->L > 0;
+      // secondary edge samples are queued and traced apart; the pixel pass
+      // (interior or path) adds their vertex adjoints
+      const bool sec = !op.primary_only && (op.terms & 4) && s->E > 0 && s->L > 0;
       if (path && need_i) cnt[drt::kPhasePath] = blocks_i;
-      else if (op.terms & 1) cnt[drt::kPhaseInterior] = blocks_i;
-      if (sec) cnt[drt::kPhaseSecondary] = blocks_i;
-      d.rows_written = op.terms & 1;
+      else if (need_i) cnt[drt::kPhaseInterior] = blocks_i;
+      d.rows_written = 0;
+      d.do_int = op.terms & 1;
       d.rows_i = need_i ? blocks_i : 0;
+      if (sec) {
+        int64_t cap = drt::secondary_capacity(s->W, s->H, op);
+        if (bind) {
+          d.dp_sec = b->sec_dp + 3 * sec_off;
+          d.sec_queue = b->sec_queue + sec_off;
+          d.sec_count = b->sec_counts + k;
+        }
+        d.sec_cap = cap;
+        sec_off += cap;
+      }
       const int64_t n_edge = (int64_t)op.edge_spp * npix;
       if ((op.terms & 2) && s->E > 0 && n_edge > 0) {
         int64_t be = 0, pt = 0;
@@ -181,8 +195,6 @@ void plan(drt_batch* b, bool bind) {
         cnt[drt::kPhasePrimary] = be;
         pix_bits = std::max(pix_bits, drt::screen_key_bits(s->W, s->H));
       }
-      if (bind && need_i && !path && !(op.terms & 1) && !sec)
-        b->zero_rows.push_back({b->partials + float_here, (size_t)blocks_i * kRowFloats});
       float_off += drt::partial_floats(d.rows_i + d.blocks_e);
     }
     for (int p = 0; p < drt::kPhases; ++p)
@@ -201,6 +213,7 @@ void plan(drt_batch* b, bool bind) {
   b->total_edge = b->eprefix[n];
   b->total_tape = tape_off;
   b->total_floats = float_off;
+  b->total_sec = sec_off;
   for (int p = 0; p < drt::kPhases; ++p) b->n_items[p] = b->prefix[(size_t)p * (n + 1) + n];
   if (bind) {
     // the sort leaves its result in vals2 after an odd number of 8-bit passes
@@ -259,9 +272,13 @@ cudaError_t enqueue(drt_batch* b, cudaStream_t st) {
     if (e == cudaSuccess) e = drt::check_finite(s, st);
     if (e == cudaSuccess) e = drt::build_scene_derived(s, st);
   }
-  for (const auto& z : b->zero_rows)
-    if (e == cudaSuccess) e = cudaMemsetAsync(z.first, 0, sizeof(float) * z.second, st);
   if (e == cudaSuccess) e = run_phase(b, drt::kPhaseRender, b->d_desc, st);
+  if (b->total_sec > 0) {
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->sec_dp, 0, sizeof(float) * 3 * (size_t)b->total_sec, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->sec_counts, 0, sizeof(unsigned long long) * b->n, st);
+    for (int k = 0; k < b->n && e == cudaSuccess; ++k)
+      if (b->desc[k].dp_sec) e = drt::launch_secondary_apart(b->desc[k], st);
+  }
   if (e == cudaSuccess) e = run_phase(b, drt::kPhasePath, b->d_desc, st);
   if (e == cudaSuccess) e = run_phase(b, drt::kPhaseInterior, b->d_desc, st);
   if (e == cudaSuccess) e = run_phase(b, drt::kPhaseSecondary, b->d_desc, st);
@@ -361,7 +378,8 @@ void free_batch(drt_batch* b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->cap) cudaStreamDestroy(b->cap);
   void* bufs[] = {b->d_desc, b->d_desc_tune, b->d_prefix, b->d_eprefix, b->d_counter, b->tape_tri, b->tape_bary,
-                  b->partials, b->scratch, b->keys, b->keys2, b->hist, b->hist_tmp, b->vals, b->vals2};
+                  b->partials, b->scratch, b->keys, b->keys2, b->hist, b->hist_tmp, b->vals, b->vals2,
+                  b->sec_dp, b->sec_queue, b->sec_counts};
   for (void* p : bufs) drt::device_free(p);
   delete b;
 }
@@ -419,6 +437,11 @@ drt_status drt_batch_create(drt_context* ctx, const drt_batch_item* items, int32
   if (s == DRT_OK) s = balloc(&b->tape_tri, (size_t)b->total_tape);
   if (s == DRT_OK) s = balloc(&b->tape_bary, (size_t)b->total_tape);
   if (s == DRT_OK) s = balloc(&b->partials, (size_t)b->total_floats);
+  if (s == DRT_OK && b->total_sec > 0) {
+    s = balloc(&b->sec_dp, 3 * (size_t)b->total_sec);
+    if (s == DRT_OK) s = balloc(&b->sec_queue, (size_t)b->total_sec);
+    if (s == DRT_OK) s = balloc(&b->sec_counts, (size_t)b->n);
+  }
   size_t ne = (size_t)b->total_edge;
   if (s == DRT_OK && ne > 0) {
     s = balloc(&b->keys, ne);

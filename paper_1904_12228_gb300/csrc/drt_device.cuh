@@ -168,7 +168,13 @@ struct BatchScene {
   int64_t blocks_e;        // primary edge virtual blocks
   int G;                   // lanes per pixel
   int rows_written;        // the secondary pass adds to rows the interior pass wrote
-  int pad_[2];
+  int do_int;              // the pixel pass adds the interior term (else only secondary adjoints)
+  int pad_;
+  // secondary edge samples that need rays, queued and traced apart
+  float* dp_sec;                  // [W*H*spp, depth] adjoint of each path vertex from its secondary sample
+  unsigned long long* sec_queue;  // (sample << 3 | vertex) of the queued samples
+  unsigned long long* sec_count;  // number queued
+  int64_t sec_cap;                // queue capacity = W*H*spp*depth
 };
 
 

@@ -17,6 +17,14 @@ struct drt_context {
 };
 
 namespace drt {
+// Scratch for the secondary edge samples traced apart: per (sample, vertex)
+// the vertex adjoint, the queue of samples to trace and its length.
+struct SecScratch {
+  float* dp = nullptr;
+  unsigned long long* queue = nullptr;
+  unsigned long long* count = nullptr;
+  int64_t cap = 0;  // (sample, vertex) pairs the buffers hold
+};
 // Scratch for sorting primary edge samples by screen position (key, index).
 struct SortBuffers {
   uint32_t *keys = nullptr, *keys2 = nullptr, *hist = nullptr, *hist_tmp = nullptr;
@@ -52,6 +60,7 @@ struct drt_scene {
   float* partials = nullptr; // backward: per-block partial sums of global parameters
   size_t partials_cap = 0;
   drt::SortBuffers esort;    // backward: primary edge samples sorted by screen position
+  drt::SecScratch sec;       // backward: secondary edge samples queued and traced apart
   // tile segments of the primary edges (built on demand)
   int32_t *seg_edge = nullptr, *seg_tile = nullptr;
   uint32_t *seg_count = nullptr, *seg_scan_tmp = nullptr;
@@ -119,7 +128,13 @@ cudaError_t check_finite(drt_scene* s, cudaStream_t st);
 cudaError_t launch_render(const drt_scene* s, const Opts& op, float* image, drt_tape* tape, cudaStream_t st);
 cudaError_t launch_backward(const drt_scene* s, const Opts& op, const drt_tape* tape, const float* d_image,
                             float* d_verts, float* d_albedo, float* d_radiance, float* d_cam, float* d_cam_scale,
-                            float* scratch_global, const SortBuffers* sort, cudaStream_t st);
+                            float* scratch_global, const SortBuffers* sort, const SecScratch* secs,
+                            cudaStream_t st);
+// (sample, vertex) pairs of the secondary edge samples of a W x H image
+int64_t secondary_capacity(int W, int H, const Opts& op);
+// queue the secondary edge samples that need rays and trace them (b.dp_sec
+// and *b.sec_count zeroed by the caller)
+cudaError_t launch_secondary_apart(const BatchScene& b, cudaStream_t st);
 int64_t backward_partial_rows(const drt_scene* s, const Opts& op);
 cudaError_t launch_debug_closest(const drt_scene* s, int64_t n, const float* o, const float* d, int32_t* tri,
                                  float* tb, cudaStream_t st);

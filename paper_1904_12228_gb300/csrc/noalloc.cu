@@ -1,7 +1,8 @@
 // noalloc.cu -- a backward pass that allocates no memory.
 //
 // drt_render_backward keeps its scratch (one row of per-block partial sums of
-// the global parameters per thread block) in a scene-owned buffer that it
+// the global parameters per thread block, the screen sort of the primary edge
+// samples, the queue of secondary edge samples) in scene-owned buffers that it
 // grows with cudaMalloc, and copies host arrays through temporary device
 // buffers.  Some callers cannot allow an allocation inside their step: a
 // training or serving loop that reserved the device memory up front through
@@ -9,7 +10,9 @@
 // give memory back and stall), or a process that runs under a fixed device
 // memory budget.  drt_render_backward_noalloc serves them: its scratch lives
 // in a fixed-size array compiled into this library, and it accepts device
-// arrays only.
+// arrays only.  Without scratch for them, it evaluates the primary edge
+// samples in sample order and the secondary edge samples inside the pixel
+// passes (same arithmetic, other order of the floating-point sums).
 #include <climits>
 #include <cstdint>
 #include <cstdio>
@@ -116,7 +119,7 @@ drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* s, const drt
   }
   cudaError_t e = drt::launch_backward(s, op, tape, d_image, grads->d_verts, grads->d_albedo, grads->d_radiance,
                                        grads->d_cam_to_world, grads->d_cam_scale, g_scratch_addr[dev],
-                                       nullptr, (cudaStream_t)stream);
+                                       nullptr, nullptr, (cudaStream_t)stream);
   if (e != cudaSuccess) {
     return fail_noalloc(DRT_ERR_CUDA, cudaGetErrorString(e));
   }

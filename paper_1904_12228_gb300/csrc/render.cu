@@ -9,6 +9,7 @@
 // 32 rays of a warp start in the same pixel, so traversal is coherent, and
 // the per-pixel sum is a fixed-order butterfly (images are bit-reproducible).
 #include <cstdio>
+#include <cstring>
 
 #include "drt_internal.h"
 
@@ -656,8 +657,8 @@ __device__ __forceinline__ float3 shading_normal(const Vertex& x) {
 // the NEE estimator F * A_j / P(j) at the camera hit, differentiated in
 // reverse with the random numbers and the pick probability held fixed.
 __device__ __forceinline__ void interior_block(const SceneView& s, const Opts& op, const int32_t* tape_tri,
-                                                              const float2* tape_bary, const float* d_image, Grads gr,
-                                                              int G, int64_t blk) {
+                                               const float2* tape_bary, const float* d_image, Grads gr, int G,
+                                               const float* dp_sec, int do_int, int64_t blk) {
   __shared__ GradCache cv, ca;
   cache_init(cv);
   cache_init(ca);
@@ -692,13 +693,13 @@ __device__ __forceinline__ void interior_block(const SceneView& s, const Opts& o
       vid0 = vid[0]; vid1 = vid[1]; vid2 = vid[2];
       float3 alb = ld3(s.albedo + 3 * c.k);
       if (op.primary_only) {
-        dalb = a;
+        if (do_int) dalb = a;
       } else {
-        if (s.light_of_tri[c.k] >= 0 && x.side < 0.0f) {
+        if (do_int && s.light_of_tri[c.k] >= 0 && x.side < 0.0f) {
           g[0] += a.x; g[1] += a.y; g[2] += a.z;
         }
         float3 dp = zero3(), dn = zero3();
-        if (s.L > 0) {
+        if (do_int && s.L > 0) {
           uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kLight, 0u, kPassInterior, op.scene_id);
           LightSample ls;
           sample_light(s, r, ls);
@@ -750,13 +751,15 @@ __device__ __forceinline__ void interior_block(const SceneView& s, const Opts& o
             }
           }
         }
+        // adjoint of the hit point from its secondary edge sample (traced apart)
+        if (dp_sec) dp += ld3(dp_sec + 3 * (pix * op.spp + sidx));
         hit_point_adjoint(s, c, x, dp, dn, dv0, dv1, dv2, g);
       }
     }
     scatter3(gr.verts, vid0, dv0, hit, &cv);
     scatter3(gr.verts, vid1, dv1, hit, &cv);
     scatter3(gr.verts, vid2, dv2, hit, &cv);
-    scatter3(gr.albedo, c.k, dalb, hit, &ca);
+    scatter3(gr.albedo, c.k, dalb, hit && do_int, &ca);
     scatter3(gr.verts, lid0, dl0, have_light, &cv);
     scatter3(gr.verts, lid1, dl1, have_light, &cv);
     scatter3(gr.verts, lid2, dl2, have_light, &cv);
@@ -766,10 +769,10 @@ __device__ __forceinline__ void interior_block(const SceneView& s, const Opts& o
   cache_flush(ca, gr.albedo);
   block_globals(g, gr.partials + blk * kGlobals, false);
 }
-__global__ void __launch_bounds__(kBlock, DRT_PIXEL_MIN_BLOCKS) k_backward_interior(SceneView s, Opts op, const int32_t* tape_tri,
-                                                              const float2* tape_bary, const float* d_image, Grads gr,
-                                                              int G) {
-  interior_block(s, op, tape_tri, tape_bary, d_image, gr, G, blockIdx.x);
+__global__ void __launch_bounds__(kBlock, DRT_PIXEL_MIN_BLOCKS)
+    k_backward_interior(SceneView s, Opts op, const int32_t* tape_tri, const float2* tape_bary, const float* d_image,
+                        Grads gr, int G, const float* dp_sec, int do_int) {
+  interior_block(s, op, tape_tri, tape_bary, d_image, gr, G, dp_sec, do_int, blockIdx.x);
 }
 
 // Could a ray from o along d reach a light triangle?  Conservative slab test
@@ -985,16 +988,19 @@ struct SecOut {
   int eid0, eid1, mid[2][3];
   bool have_edge, have_m[2];
 };
-__device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Opts& op, uint32_t c0, uint32_t c1,
-                                                    int b, int md, const Vertex& x, float3 n, float3 alb, float3 ab,
-                                                    float3 Le, float3& dp, SecOut& so) {
-  so.de0 = so.de1 = zero3();
-  so.eid0 = so.eid1 = 0;
-  so.have_edge = false;
-  for (int q = 0; q < 2; ++q) {
-    so.have_m[q] = false;
-    for (int i = 0; i < 3; ++i) { so.dm[q][i] = zero3(); so.mid[q][i] = 0; }
-  }
+// Secondary edge sample at path vertex b (Sec. 5.2.2): the edge by the 3D
+// length CDF, the point on it, the side directions omega +- eps|omega| n_h,
+// and which sides can contribute (above the shading horizon; at the last
+// vertex only a side that may reach a light).  False: nothing to evaluate.
+struct SecGeom {
+  int2 ev;
+  float invPE, Nlen, wl, wl2;
+  float3 E, w, nh, p, a0v, a1v, Ne, what;
+  float dsd[2][3];
+  bool act[2], last;
+};
+__device__ __forceinline__ bool secondary_sides(const SceneView& s, const Opts& op, uint32_t c0, uint32_t c1, int b,
+                                                int md, const Vertex& x, float3 n, SecGeom& gm) {
   double stotal = s.scdf[s.E - 1];
   uint4 r = rng4(op.key, c0, c1, kEdgeSecondary, (uint32_t)b, kPassInterior, op.scene_id);
   int e = cdf_pick(s.scdf, s.E, dm(u01d(r.x, r.y), stotal));
@@ -1011,27 +1017,54 @@ __device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Op
   float N32[3] = {fs(fm(a0[1], a1[2]), fm(a0[2], a1[1])), fs(fm(a0[2], a1[0]), fm(a0[0], a1[2])),
                   fs(fm(a0[0], a1[1]), fm(a0[1], a1[0]))};
   float nlen32 = fsq(dot3x(N32, N32));
-  if (!(le > 0.0 && nlen32 > 0.0f)) return;
-  float invPE = (float)(stotal / le);
+  if (!(le > 0.0 && nlen32 > 0.0f)) return false;
+  gm.ev = ev;
+  gm.invPE = (float)(stotal / le);
   float nh32[3] = {fdv(N32[0], nlen32), fdv(N32[1], nlen32), fdv(N32[2], nlen32)};
-  float wl = fsq(dot3x(om, om));
-  float sh = fm(op.eps_rel, wl);
-  float3 E = ve1 - ve0, w = f3(om), nh = f3(nh32);
-  float Nlen = len(f3(N32));
-  float3 p = f3(x.p);
-  float3 a0v = ve0 - p, a1v = ve1 - p;
-  float3 Ne = cross(a0v, a1v);
-  float wl2 = dot(w, w);
-  float3 what = (1.f / sqrtf(wl2)) * w;
-  bool last = b + 1 >= md;
-  // both side rays in one traversal; sides that cannot contribute are not traced
-  float dsd[2][3];
-  bool act[2];
+  gm.wl = fsq(dot3x(om, om));
+  float sh = fm(op.eps_rel, gm.wl);
+  gm.E = ve1 - ve0;
+  gm.w = f3(om);
+  gm.nh = f3(nh32);
+  gm.Nlen = len(f3(N32));
+  gm.p = f3(x.p);
+  gm.a0v = ve0 - gm.p;
+  gm.a1v = ve1 - gm.p;
+  gm.Ne = cross(gm.a0v, gm.a1v);
+  gm.wl2 = dot(gm.w, gm.w);
+  gm.what = (1.f / sqrtf(gm.wl2)) * gm.w;
+  gm.last = b + 1 >= md;
   for (int side = 0; side < 2; ++side) {
     for (int i = 0; i < 3; ++i)
-      dsd[side][i] = side == 0 ? fa(om[i], fm(sh, nh32[i])) : fs(om[i], fm(sh, nh32[i]));
-    act[side] = !(dot(n, f3(dsd[side])) < -1e-5f * wl) && !(last && !may_reach_light(s, x.p, dsd[side]));
+      gm.dsd[side][i] = side == 0 ? fa(om[i], fm(sh, nh32[i])) : fs(om[i], fm(sh, nh32[i]));
+    gm.act[side] = !(dot(n, f3(gm.dsd[side])) < -1e-5f * gm.wl) &&
+                   !(gm.last && !may_reach_light(s, x.p, gm.dsd[side]));
   }
+  return gm.act[0] || gm.act[1];
+}
+
+// Evaluate the secondary edge sample at vertex b: trace both side rays (one
+// traversal), their continuation paths below the last vertex, and the edge
+// term's contributions: edge vertices and light vertices into so, the
+// adjoint of the vertex position into dp.
+__device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Opts& op, uint32_t c0, uint32_t c1,
+                                                    int b, int md, const Vertex& x, float3 n, float3 alb, float3 ab,
+                                                    float3 Le, float3& dp, SecOut& so) {
+  so.de0 = so.de1 = zero3();
+  so.eid0 = so.eid1 = 0;
+  so.have_edge = false;
+  for (int q = 0; q < 2; ++q) {
+    so.have_m[q] = false;
+    for (int i = 0; i < 3; ++i) { so.dm[q][i] = zero3(); so.mid[q][i] = 0; }
+  }
+  SecGeom gm;
+  if (!secondary_sides(s, op, c0, c1, b, md, x, n, gm)) return;
+  const int2 ev = gm.ev;
+  const float invPE = gm.invPE, Nlen = gm.Nlen, wl2 = gm.wl2;
+  const float3 E = gm.E, w = gm.w, nh = gm.nh, p = gm.p, a0v = gm.a0v, a1v = gm.a1v, Ne = gm.Ne, what = gm.what;
+  const bool last = gm.last;
+  float (*dsd)[3] = gm.dsd;
+  bool* act = gm.act;
   Hit hms[2];
   trace_closest2(s, x.p, dsd[0], x.p, dsd[1], act[0], act[1], x.k, x.k, hms[0], hms[1]);
   float cpms[2] = {0.f, 0.f};
@@ -1102,8 +1135,8 @@ __device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Op
 }
 
 __device__ __forceinline__ void path_block(const SceneView& s, const Opts& op, const int32_t* tape_tri,
-                                                          const float2* tape_bary, const float* d_image, Grads gr,
-                                                          int G, int64_t blk) {
+                                           const float2* tape_bary, const float* d_image, Grads gr, int G,
+                                           const float* dp_sec, int64_t blk) {
   __shared__ GradCache cv, ca;
   cache_init(cv);
   cache_init(ca);
@@ -1211,7 +1244,12 @@ __device__ __forceinline__ void path_block(const SceneView& s, const Opts& op, c
             Dv += alb * D_next;
           }
         }
-        if (do_sec) secondary_at_vertex(s, op, (uint32_t)pix, (uint32_t)sidx, b, md, x, n, alb, ab, Le, dp, so);
+        if (do_sec) {
+          if (dp_sec)  // evaluated apart (queued samples only)
+            dp += ld3(dp_sec + 3 * (ti * md + b));
+          else
+            secondary_at_vertex(s, op, (uint32_t)pix, (uint32_t)sidx, b, md, x, n, alb, ab, Le, dp, so);
+        }
         for (int i = 0; i < kGlobals; ++i) g[i] += gl[i];
         float3 do_, dd_;
         plane_hit_adjoint(orig[b], din[b], x, dp, dn, dv0, dv1, dv2, do_, dd_);
@@ -1235,10 +1273,182 @@ __device__ __forceinline__ void path_block(const SceneView& s, const Opts& op, c
   cache_flush(ca, gr.albedo);
   block_globals(g, gr.partials + blk * kGlobals, false);
 }
-__global__ void __launch_bounds__(kBlock, DRT_PATH_MIN_BLOCKS) k_backward_path(SceneView s, Opts op, const int32_t* tape_tri,
-                                                          const float2* tape_bary, const float* d_image, Grads gr,
-                                                          int G) {
-  path_block(s, op, tape_tri, tape_bary, d_image, gr, G, blockIdx.x);
+__global__ void __launch_bounds__(kBlock, DRT_PATH_MIN_BLOCKS)
+    k_backward_path(SceneView s, Opts op, const int32_t* tape_tri, const float2* tape_bary, const float* d_image,
+                    Grads gr, int G, const float* dp_sec) {
+  path_block(s, op, tape_tri, tape_bary, d_image, gr, G, dp_sec, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Secondary edge samples traced apart from the pixel passes.  Only a small
+// share of them can contribute (most side rays leave below the shading
+// horizon or, at the last vertex, cannot reach a light); traced inside the
+// pixel passes, those few lanes hold back their warps and blocks.  A first
+// pass queues the (sample, vertex) pairs that have a side to trace; a second
+// traces only those, scatters the edge and light-vertex gradients and writes
+// the adjoint of the vertex position, which the pixel pass adds where it
+// chains hit-point adjoints back to the camera.  Same arithmetic as the
+// evaluation inside the pixel passes.
+// ---------------------------------------------------------------------------
+// Vertex b of the camera path of sample (pix, sidx), re-evaluated from the
+// tape (vertex 0 from the camera ray; traced when there is no tape, which
+// only depth 1 allows).  beta = throughput before vertex b.  False: the path
+// has no vertex b.
+__device__ __forceinline__ bool tape_vertex(const SceneView& s, const Opts& op, const int32_t* tape_tri,
+                                            const float2* tape_bary, int64_t pix, int sidx, int b, int md, Vertex& x,
+                                            float3& beta) {
+  CamHit c;
+  camera_hit(s, op, tape_tri, tape_bary, pix, sidx, c);
+  if (c.k < 0) return false;
+  int64_t n = (int64_t)s.W * s.H * op.spp, ti = pix * op.spp + sidx;
+  float d[3] = {c.d[0], c.d[1], c.d[2]};
+  int k = c.k;
+  float b1 = c.b1, b2 = c.b2;
+  float3 bt = make_float3(1.f, 1.f, 1.f);
+  for (int q = 0;; ++q) {
+    load_vertex(s, k, b1, b2, d, x);
+    if (q == b) {
+      beta = bt;
+      return true;
+    }
+    if (q + 1 >= md) return false;
+    float n32[3];
+    shading_normal32(x, n32);
+    uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kBsdf, (uint32_t)q, kPassInterior, op.scene_id);
+    float nd[3];
+    cosine_dir(n32, u01f(r.x), u01f(r.y), nd);
+    if (!(dot(f3(n32), f3(nd)) > 0.f)) return false;
+    bt = bt * ld3(s.albedo + 3 * k);
+    for (int i = 0; i < 3; ++i) d[i] = nd[i];
+    int32_t tt = tape_tri[(q + 1) * n + ti];
+    if (tt == -1) return false;
+    k = tt & 0x7fffffff;
+    float2 bb = tape_bary[(q + 1) * n + ti];
+    b1 = bb.x;
+    b2 = bb.y;
+  }
+}
+
+// Pass 1: one thread per sample walks its path and queues each vertex whose
+// secondary sample has a side to trace (pixels with a zero loss adjoint
+// contribute nothing and are skipped).  Warp-aggregated appends.
+__global__ void __launch_bounds__(kBlock) k_sec_queue(BatchScene bs) {
+  const SceneView& s = bs.v;
+  const Opts& op = bs.op;
+  int lane = threadIdx.x & 31;
+  int64_t n = (int64_t)s.W * s.H * op.spp;
+  int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  int md = op.primary_only ? 1 : min(op.max_depth, kMaxDepth);
+  bool alive = i < n;
+  int64_t pix = alive ? i / op.spp : 0;
+  int sidx = alive ? (int)(i % op.spp) : 0;
+  alive = alive && pix >= op.pix_begin && pix < op.pix_end;
+  if (alive) {
+    float3 w = ld3(bs.d_image + 3 * pix);
+    alive = w.x != 0.f || w.y != 0.f || w.z != 0.f;
+  }
+  CamHit c;
+  c.k = -1;
+  if (alive) {
+    camera_hit(s, op, bs.tape_tri, bs.tape_bary, pix, sidx, c);
+    alive = c.k >= 0;
+  }
+  float d[3] = {c.d[0], c.d[1], c.d[2]};
+  int k = c.k;
+  float b1 = c.b1, b2 = c.b2;
+  for (int b = 0; b < md; ++b) {
+    Vertex x;
+    bool need = false;
+    if (alive) {
+      load_vertex(s, k, b1, b2, d, x);
+      SecGeom gm;
+      need = secondary_sides(s, op, (uint32_t)pix, (uint32_t)sidx, b, md, x, shading_normal(x), gm);
+    }
+    unsigned m = __ballot_sync(kFull, need);
+    if (m) {
+      int leader = __ffs(m) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(bs.sec_count, (unsigned long long)__popc(m));
+      base = __shfl_sync(kFull, base, leader);
+      if (need) bs.sec_queue[base + __popc(m & ((1u << lane) - 1u))] = ((unsigned long long)i << 3) | (unsigned)b;
+    }
+    if (alive) {  // on to vertex b + 1
+      if (b + 1 >= md) {
+        alive = false;
+      } else {
+        float n32[3];
+        shading_normal32(x, n32);
+        uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kBsdf, (uint32_t)b, kPassInterior, op.scene_id);
+        float nd[3];
+        cosine_dir(n32, u01f(r.x), u01f(r.y), nd);
+        if (!(dot(f3(n32), f3(nd)) > 0.f)) {
+          alive = false;
+        } else {
+          for (int q = 0; q < 3; ++q) d[q] = nd[q];
+          int32_t tt = bs.tape_tri[(int64_t)(b + 1) * n + i];
+          if (tt == -1) {
+            alive = false;
+          } else {
+            k = tt & 0x7fffffff;
+            float2 bb = bs.tape_bary[(int64_t)(b + 1) * n + i];
+            b1 = bb.x;
+            b2 = bb.y;
+          }
+        }
+      }
+    }
+  }
+}
+
+// Pass 2: the queued (sample, vertex) pairs, a block-stride loop over the
+// queue; vertex gradients through the block cache (the light's vertices take
+// contributions from most samples).
+__global__ void __launch_bounds__(kBlock, DRT_PIXEL_MIN_BLOCKS) k_sec_trace(BatchScene bs) {
+  __shared__ GradCache cv;
+  const SceneView& s = bs.v;
+  const Opts& op = bs.op;
+  int md = op.primary_only ? 1 : min(op.max_depth, kMaxDepth);
+  const float3 Le = ld3(s.radiance);
+  unsigned long long count = *bs.sec_count;
+  for (unsigned long long base = (unsigned long long)blockIdx.x * kBlock; base < count;
+       base += (unsigned long long)gridDim.x * kBlock) {
+    cache_init(cv);
+    __syncthreads();
+    unsigned long long q = base + threadIdx.x;
+    SecOut so;
+    so.have_edge = false;
+    so.have_m[0] = so.have_m[1] = false;
+    so.eid0 = so.eid1 = 0;
+    so.de0 = so.de1 = zero3();
+    for (int h = 0; h < 2; ++h)
+      for (int j = 0; j < 3; ++j) { so.dm[h][j] = zero3(); so.mid[h][j] = 0; }
+    if (q < count) {
+      unsigned long long item = bs.sec_queue[q];
+      int64_t i = (int64_t)(item >> 3);
+      int b = (int)(item & 7u);
+      int64_t pix = i / op.spp;
+      int sidx = (int)(i % op.spp);
+      Vertex x;
+      float3 beta;
+      if (tape_vertex(s, op, bs.tape_tri, bs.tape_bary, pix, sidx, b, md, x, beta)) {
+        float3 ab = ((1.0f / (float)op.spp) * ld3(bs.d_image + 3 * pix)) * beta;
+        float3 dp = zero3();
+        secondary_at_vertex(s, op, (uint32_t)pix, (uint32_t)sidx, b, md, x, shading_normal(x),
+                            ld3(s.albedo + 3 * x.k), ab, Le, dp, so);
+        float* o = bs.dp_sec + 3 * (i * md + b);
+        o[0] = dp.x;
+        o[1] = dp.y;
+        o[2] = dp.z;
+      }
+    }
+    scatter3(bs.d_verts, so.eid0, so.de0, so.have_edge, &cv);
+    scatter3(bs.d_verts, so.eid1, so.de1, so.have_edge, &cv);
+    for (int h = 0; h < 2; ++h)
+      for (int j = 0; j < 3; ++j) scatter3(bs.d_verts, so.mid[h][j], so.dm[h][j], so.have_m[h], &cv);
+    __syncthreads();
+    cache_flush(cv, bs.d_verts);
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1463,13 +1673,13 @@ __global__ void __launch_bounds__(kBlock, PhaseMinBlocks<PH>::value)
         render_block(sb.v, sb.op, sb.image, sb.tape_tri, sb.tape_bary, sb.G, blk);
       } else if (PH == kPhaseInterior) {
         interior_block(sb.v, sb.op, sb.tape_tri, sb.tape_bary, sb.d_image, Grads{sb.d_verts, sb.d_albedo, sb.partials},
-                       sb.G, blk);
+                       sb.G, sb.dp_sec, sb.do_int, blk);
       } else if (PH == kPhaseSecondary) {
         secondary_block(sb.v, sb.op, sb.tape_tri, sb.tape_bary, sb.d_image,
                         Grads{sb.d_verts, sb.d_albedo, sb.partials}, sb.G, sb.rows_written, blk);
       } else if (PH == kPhasePath) {
         path_block(sb.v, sb.op, sb.tape_tri, sb.tape_bary, sb.d_image, Grads{sb.d_verts, sb.d_albedo, sb.partials},
-                   sb.G, blk);
+                   sb.G, sb.dp_sec, blk);
       } else {
         primary_block(sb.v, sb.op, sb.d_image, Grads{sb.d_verts, sb.d_albedo, sb.partials + sb.rows_i * kGlobals},
                       sb.n_edge, sb.per_thread, sb.order, blk);
@@ -1613,9 +1823,28 @@ cudaError_t launch_render(const drt_scene* sc, const Opts& op, float* image, drt
   return cudaGetLastError();
 }
 
+int64_t secondary_capacity(int W, int H, const Opts& op) {
+  int md = op.primary_only ? 1 : std::min(op.max_depth, kMaxDepth);
+  return (int64_t)W * H * op.spp * md;
+}
+
+cudaError_t launch_secondary_apart(const BatchScene& b, cudaStream_t st) {
+  int64_t n = (int64_t)b.v.W * b.v.H * b.op.spp;
+  if (n <= 0) return cudaSuccess;
+  BatchScene q = b;
+  q.v.counters = nullptr;
+  DRT_PROF_LAUNCH("backward_secondary_queue", st,
+                  k_sec_queue<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, st>>>(q));
+  BatchScene t = b;
+  t.v.counters = counter_slot(kSlotBwdSecondary);
+  int64_t grid = std::min<int64_t>((b.sec_cap + kBlock - 1) / kBlock, 152 * 8);
+  DRT_PROF_LAUNCH("backward_secondary_edges", st, k_sec_trace<<<(unsigned)grid, kBlock, 0, st>>>(t));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape* tape, const float* d_image,
                             float* d_verts, float* d_albedo, float* d_radiance, float* d_cam, float* d_cam_scale,
-                            float* partials, const SortBuffers* sort, cudaStream_t st) {
+                            float* partials, const SortBuffers* sort, const SecScratch* secs, cudaStream_t st) {
   SceneView s = sc->view();
   if (op.proposal == 0) s.seg_cdf = nullptr;
   int npix = s.W * s.H;
@@ -1630,20 +1859,44 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
   const int32_t* tt = tape ? tape->tri : nullptr;
   const float2* tb = tape ? tape->bary : nullptr;
   bool path = !op.primary_only && op.max_depth > 1;
+  bool sec = !op.primary_only && (op.terms & 4) && s.E > 0 && s.L > 0;
+  // secondary edge samples traced apart (queued) when scratch is given, else
+  // inside the pixel passes
+  bool apart = sec && secs != nullptr;
+  const float* dps = nullptr;
+  if (apart) {
+    BatchScene bsd;
+    std::memset(&bsd, 0, sizeof(bsd));
+    bsd.v = s;
+    bsd.op = op;
+    bsd.tape_tri = const_cast<int32_t*>(tt);
+    bsd.tape_bary = const_cast<float2*>(tb);
+    bsd.d_image = d_image;
+    bsd.d_verts = d_verts;
+    bsd.dp_sec = secs->dp;
+    bsd.sec_queue = secs->queue;
+    bsd.sec_count = secs->count;
+    bsd.sec_cap = secondary_capacity(sc->W, sc->H, op);
+    cudaError_t e = cudaMemsetAsync(secs->dp, 0, sizeof(float) * 3 * bsd.sec_cap, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(secs->count, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = launch_secondary_apart(bsd, st);
+    if (e != cudaSuccess) return e;
+    dps = secs->dp;
+  }
   if (path && need_i) {
     s.counters = counter_slot(kSlotBwdInterior);
     ProfToken pt = prof_begin("backward_path", st);
-    k_backward_path<<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tt, tb, d_image, gr, G);
+    k_backward_path<<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tt, tb, d_image, gr, G, dps);
     prof_end(pt, st);
-  } else if (op.terms & 1) {
+  } else if ((op.terms & 1) || apart) {
     s.counters = counter_slot(kSlotBwdInterior);
     ProfToken pt = prof_begin("backward_interior", st);
-    k_backward_interior<<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tt, tb, d_image, gr, G);
+    k_backward_interior<<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tt, tb, d_image, gr, G, dps, op.terms & 1);
     prof_end(pt, st);
   }
-  if (path) {
-    // the path kernel covers the interior and secondary terms
-  } else if ((op.terms & 4) && s.E > 0 && s.L > 0) {
+  if (path || apart) {
+    // the path or interior pass covered the secondary term
+  } else if (sec) {
     s.counters = counter_slot(kSlotBwdSecondary);
     ProfToken pt = prof_begin("backward_secondary_edges", st);
     k_backward_secondary<<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tt, tb, d_image, gr, G, op.terms & 1);
