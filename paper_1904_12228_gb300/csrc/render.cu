@@ -36,6 +36,11 @@ constexpr int kBlock = 256;
 #ifndef DRT_RENDER_MIN_BLOCKS
 #define DRT_RENDER_MIN_BLOCKS 4
 #endif
+// Resident CTAs per SM the kernel tracing the queued secondary edge samples
+// is compiled for.
+#ifndef DRT_SEC_MIN_BLOCKS
+#define DRT_SEC_MIN_BLOCKS 2
+#endif
 // Resident CTAs per SM the depth > 1 path pass is compiled for.
 #ifndef DRT_PATH_MIN_BLOCKS
 #define DRT_PATH_MIN_BLOCKS 1
@@ -1403,7 +1408,7 @@ __global__ void __launch_bounds__(kBlock) k_sec_queue(BatchScene bs) {
 // Pass 2: the queued (sample, vertex) pairs, a block-stride loop over the
 // queue; vertex gradients through the block cache (the light's vertices take
 // contributions from most samples).
-__global__ void __launch_bounds__(kBlock, DRT_PIXEL_MIN_BLOCKS) k_sec_trace(BatchScene bs) {
+__global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_trace(BatchScene bs) {
   __shared__ GradCache cv;
   const SceneView& s = bs.v;
   const Opts& op = bs.op;
