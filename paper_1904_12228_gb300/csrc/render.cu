@@ -283,8 +283,18 @@ __device__ float3 path_value_warp(const SceneView& s, const Opts& op, const floa
   int b_end = 0;  // first bounce whose tape entry is not written
   for (int b = 0; b < md; ++b) {
     if (!__any_sync(full, alive)) break;
-    Hit h, h_unused;
-    trace_closest2_warp(s, o, d, o, d, alive, false, exclude, -1, h, h_unused);
+    // the warp's camera rays are coherent; after a diffuse bounce its rays
+    // point anywhere, and each lane traces its own
+    Hit h;
+    if (b == 0) {
+      Hit h_unused;
+      trace_closest2_warp(s, o, d, o, d, alive, false, exclude, -1, h, h_unused);
+    } else if (alive) {
+      h = trace_closest(s, o, d, INFINITY, exclude);
+    } else {
+      h.tri = -1;
+      h.t = h.b1 = h.b2 = 0.f;
+    }
     if (alive && h.tri < 0) alive = false;
     Vertex x;
     x.k = -1;
@@ -316,8 +326,11 @@ __device__ float3 path_value_warp(const SceneView& s, const Opts& op, const floa
       float sd[3] = {0.f, 0.f, 1.f};
       if (alive)
         for (int i = 0; i < 3; ++i) sd[i] = fs(ls.y[i], x.p[i]);
-      bool occ, occ_unused;
-      trace_any2_warp(s, x.p, sd, x.k, ls.lt, x.p, sd, -1, -1, alive, false, kShadowTmax, occ, occ_unused);
+      bool occ = false, occ_unused;
+      if (b == 0)
+        trace_any2_warp(s, x.p, sd, x.k, ls.lt, x.p, sd, -1, -1, alive, false, kShadowTmax, occ, occ_unused);
+      else if (alive)
+        occ = trace_any(s, x.p, sd, kShadowTmax, x.k, ls.lt);
       if (alive && !occ) {
         vis = 1;
         float g = nee_geometry(s, f3(x.p), f3(n32), ls);
