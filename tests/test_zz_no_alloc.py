@@ -56,6 +56,32 @@ def test_noalloc_backward_matches_backward_on_consecutive_calls():
     assert ctx.check_device() == (0, 0)
 
 
+def test_noalloc_backward_matches_backward_at_depth_two():
+    """The allocation-free backward evaluates the secondary edge samples inside
+    the path pass; the regular backward queues and traces them apart."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1904_12228_gb300 import drt
+    ctx = drt.Context(0)
+    scene = sg.direct_lighting(1237, width=24, height=20, subdiv=1)
+    S = drt.Scene.from_arrays(ctx, scene)
+    opts = drt.make_opts(6, 6, max_depth=2, seed=5)
+    img = torch.zeros((20, 24, 3), device="cuda")
+    tape = S.render(img, opts, want_tape=True)
+    w = torch.from_numpy(sg.loss_adjoint(4, 24, 20)).cuda()
+    ref = _zeros(scene)
+    S.backward(w, opts, tape=tape, **ref)
+    got = _zeros(scene)
+    S.backward_noalloc(w, opts, tape=tape, **got)
+    torch.cuda.synchronize()
+    want, g = _flat(*ref.values()), _flat(*got.values())
+    _, absum = oracle.backward(scene, w.cpu().numpy(), spp=6, edge_spp=6, seed=5, max_depth=2)
+    bound = 1e-4 * np.abs(want) + 1e-6 * absum + 1e-12
+    assert np.all(np.abs(g - want) <= bound), int((np.abs(g - want) > bound).sum())
+    assert np.abs(g).max() > 0
+    assert ctx.check_device() == (0, 0)
+
+
 def test_noalloc_backward_rejects_host_arrays_and_oversize_images():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
