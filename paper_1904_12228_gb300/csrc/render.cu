@@ -32,6 +32,11 @@ constexpr int kBlock = 256;
 #ifndef DRT_PIXEL_MIN_BLOCKS
 #define DRT_PIXEL_MIN_BLOCKS 2
 #endif
+// Screen keys of the primary edge samples resolve 1/DRT_KEY_SUB of a pixel.
+#ifndef DRT_KEY_SUB
+#define DRT_KEY_SUB 4
+#endif
+constexpr int kKeySub = DRT_KEY_SUB;
 // Resident CTAs per SM the render kernel is compiled for.
 #ifndef DRT_RENDER_MIN_BLOCKS
 #define DRT_RENDER_MIN_BLOCKS 4
@@ -812,136 +817,6 @@ __device__ __forceinline__ bool may_reach_light(const SceneView& s, const float 
   return t0 <= t1 * 1.0001f;
 }
 
-// Secondary edge sample at the camera hit (Sec. 5.2.2): edge by the 3D length
-// CDF, point t, side rays omega +- eps|omega| n_h.  With one scattering vertex
-// only radiance arriving from a light matters (area form, reading of the
-// measure), so a side ray that cannot reach a light, or that leaves below the
-// shading horizon by more than the side offset, contributes exactly nothing
-// and is not traced.
-__device__ __forceinline__ void secondary_block(const SceneView& s, const Opts& op, const int32_t* tape_tri,
-                                                               const float2* tape_bary, const float* d_image, Grads gr,
-                                                               int G, int rows_written, int64_t blk) {
-  int lane = threadIdx.x & 31;
-  int64_t gw = (blk * kBlock + threadIdx.x) >> 5;
-  int ppw = 32 / G;
-  int64_t pix = gw * ppw + lane / G;
-  int npix = s.W * s.H;
-  bool pix_ok = pix < npix && pix >= op.pix_begin && pix < op.pix_end;
-  float g[kGlobals];
-  for (int i = 0; i < kGlobals; ++i) g[i] = 0.f;
-  float3 wpix = pix_ok ? ld3(d_image + 3 * pix) : zero3();
-  float3 a = (1.0f / (float)op.spp) * wpix;
-  const float3 Le = ld3(s.radiance);
-  int iters = (op.spp + G - 1) / G;
-  double stotal = s.scdf[s.E - 1];
-  for (int it = 0; it < iters; ++it) {
-    int sidx = lane % G + it * G;
-    bool active = pix_ok && sidx < op.spp && !op.primary_only;
-    CamHit c;
-    c.k = -1;
-    if (active) camera_hit(s, op, tape_tri, tape_bary, pix, sidx, c);
-    float3 dv0 = zero3(), dv1 = zero3(), dv2 = zero3(), de0 = zero3(), de1 = zero3();
-    float3 dmv[2][3] = {{zero3(), zero3(), zero3()}, {zero3(), zero3(), zero3()}};
-    int vid0 = 0, vid1 = 0, vid2 = 0, eid0 = 0, eid1 = 0, mids[2][3] = {{0, 0, 0}, {0, 0, 0}};
-    bool have_edge = false, have_m[2] = {false, false};
-    if (active && c.k >= 0) {
-      Vertex x;
-      load_vertex(s, c.k, c.b1, c.b2, c.d, x);
-      uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kEdgeSecondary, 0u, kPassInterior, op.scene_id);
-      int e = cdf_pick(s.scdf, s.E, dm(u01d(r.x, r.y), stotal));
-      double le = s.scdf[e] - (e > 0 ? s.scdf[e - 1] : 0.0);
-      float t = u01f(r.z);
-      int2 ev = s.edges[e];
-      float3 ve0 = ld3(s.verts + 3 * ev.x), ve1 = ld3(s.verts + 3 * ev.y);
-      float om[3], a0[3], a1[3];
-      om[0] = fs(fa(ve0.x, fm(t, fs(ve1.x, ve0.x))), x.p[0]);
-      om[1] = fs(fa(ve0.y, fm(t, fs(ve1.y, ve0.y))), x.p[1]);
-      om[2] = fs(fa(ve0.z, fm(t, fs(ve1.z, ve0.z))), x.p[2]);
-      a0[0] = fs(ve0.x, x.p[0]); a0[1] = fs(ve0.y, x.p[1]); a0[2] = fs(ve0.z, x.p[2]);
-      a1[0] = fs(ve1.x, x.p[0]); a1[1] = fs(ve1.y, x.p[1]); a1[2] = fs(ve1.z, x.p[2]);
-      float N32[3] = {fs(fm(a0[1], a1[2]), fm(a0[2], a1[1])), fs(fm(a0[2], a1[0]), fm(a0[0], a1[2])),
-                      fs(fm(a0[0], a1[1]), fm(a0[1], a1[0]))};
-      float nlen32 = fsq(dot3x(N32, N32));
-      float3 n = shading_normal(x);
-      if (le > 0.0 && nlen32 > 0.0f) {
-        float invPE = (float)(stotal / le);
-        float nh32[3] = {fdv(N32[0], nlen32), fdv(N32[1], nlen32), fdv(N32[2], nlen32)};
-        float wl = fsq(dot3x(om, om));
-        float sh = fm(op.eps_rel, wl);
-        float3 E = ve1 - ve0, w = f3(om), nh = f3(nh32);
-        float Nlen = len(f3(N32));
-        float3 p = f3(x.p);
-        float3 a0v = ve0 - p, a1v = ve1 - p;
-        float3 Ne = cross(a0v, a1v);
-        float3 alb = ld3(s.albedo + 3 * c.k);
-        float3 dp = zero3();
-        for (int side = 0; side < 2; ++side) {
-          float sg = side == 0 ? 1.f : -1.f;
-          float dsd[3];
-          for (int i = 0; i < 3; ++i) dsd[i] = side == 0 ? fa(om[i], fm(sh, nh32[i])) : fs(om[i], fm(sh, nh32[i]));
-          if (dot(n, f3(dsd)) < -1e-5f * wl) continue;  // below the horizon: cos_p < 0 at the hit
-          if (!may_reach_light(s, x.p, dsd)) continue;  // cannot hit a light
-          Hit hm = trace_closest(s, x.p, dsd, INFINITY, c.k);
-          if (hm.tri < 0 || s.light_of_tri[hm.tri] < 0) continue;
-          Vertex mv;
-          load_vertex(s, hm.tri, hm.b1, hm.b2, dsd, mv);
-          float3 m = f3(mv.p);
-          float3 dmp = m - p;
-          float mr2 = dot(dmp, dmp);
-          float3 wh = (1.f / sqrtf(mr2)) * dmp;
-          float cpm = dot(n, wh);
-          if (!(cpm > 0.f)) continue;
-          float3 nmu = f3(mv.nu);
-          float3 nm = (1.f / len(nmu)) * nmu;
-          float cm = -dot(nm, wh);
-          if (!(cm > 0.f)) continue;
-          float Gm = cpm * cm / mr2;
-          float hs = kInvPi * Gm * (a.x * alb.x * Le.x + a.y * alb.y * Le.y + a.z * alb.z * Le.z);
-          float wn = dot(w, nm);
-          float tm = dot(dmp, nm) / wn;
-          float3 J = tm * (E - (dot(E, nm) / wn) * w);
-          float cr = len(cross(nm, nh));
-          if (!(cr > 0.f)) continue;
-          float cc = sg * hs * (len(J) / (Nlen * cr)) * invPE;
-          // alpha = (m-p).(v0-p)x(v1-p): d/dv0 = v1' x m', d/dv1 = m' x v0',
-          // d/dm = v0' x v1', d/dp = -(sum of the three)
-          float3 gv0 = cross(a1v, dmp), gv1 = cross(dmp, a0v);
-          de0 += cc * gv0;
-          de1 += cc * gv1;
-          dp -= cc * (Ne + gv0 + gv1);
-          float bw1 = hm.b1, bw2 = hm.b2, bw0 = 1.f - bw1 - bw2;  // m attached to its light triangle
-          const int32_t* mid = s.tris + 3 * hm.tri;
-          mids[side][0] = mid[0]; mids[side][1] = mid[1]; mids[side][2] = mid[2];
-          dmv[side][0] = (cc * bw0) * Ne;
-          dmv[side][1] = (cc * bw1) * Ne;
-          dmv[side][2] = (cc * bw2) * Ne;
-          have_m[side] = true;
-        }
-        if (have_m[0] || have_m[1]) {
-          eid0 = ev.x;
-          eid1 = ev.y;
-          have_edge = true;
-          const int32_t* vid = s.tris + 3 * c.k;
-          vid0 = vid[0]; vid1 = vid[1]; vid2 = vid[2];
-          hit_point_adjoint(s, c, x, dp, zero3(), dv0, dv1, dv2, g);
-        }
-      }
-    }
-    scatter3(gr.verts, eid0, de0, have_edge);
-    scatter3(gr.verts, eid1, de1, have_edge);
-    scatter3(gr.verts, vid0, dv0, have_edge);
-    scatter3(gr.verts, vid1, dv1, have_edge);
-    scatter3(gr.verts, vid2, dv2, have_edge);
-    for (int sd = 0; sd < 2; ++sd)
-      for (int q = 0; q < 3; ++q) scatter3(gr.verts, mids[sd][q], dmv[sd][q], have_m[sd]);
-  }
-  block_globals(g, gr.partials + blk * kGlobals, rows_written != 0);
-}
-__global__ void __launch_bounds__(kBlock, DRT_PIXEL_MIN_BLOCKS) k_backward_secondary(SceneView s, Opts op, const int32_t* tape_tri,
-                                                               const float2* tape_bary, const float* d_image, Grads gr,
-                                                               int G, int rows_written) {
-  secondary_block(s, op, tape_tri, tape_bary, d_image, gr, G, rows_written, blockIdx.x);
-}
 
 // ---------------------------------------------------------------------------
 // Backward for paths with several scattering vertices (path tracing)
@@ -1150,6 +1025,79 @@ __device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Op
   }
   so.eid0 = ev.x;
   so.eid1 = ev.y;
+}
+
+// Secondary edge samples at the camera hits (depth 1), evaluated inside the
+// pixel pass: the form the allocation-free backward uses, having no scratch
+// for the queue of k_sec_queue / k_sec_trace.  With one scattering vertex
+// only radiance arriving from a light matters (area form, reading of the
+// measure), so a side ray that cannot reach a light, or that leaves below the
+// shading horizon by more than the side offset, contributes exactly nothing
+// and is not traced (secondary_sides).
+__device__ __forceinline__ void secondary_block(const SceneView& s, const Opts& op, const int32_t* tape_tri,
+                                                               const float2* tape_bary, const float* d_image, Grads gr,
+                                                               int G, int rows_written, int64_t blk) {
+  int lane = threadIdx.x & 31;
+  int64_t gw = (blk * kBlock + threadIdx.x) >> 5;
+  int ppw = 32 / G;
+  int64_t pix = gw * ppw + lane / G;
+  int npix = s.W * s.H;
+  bool pix_ok = pix < npix && pix >= op.pix_begin && pix < op.pix_end;
+  float g[kGlobals];
+  for (int i = 0; i < kGlobals; ++i) g[i] = 0.f;
+  float3 wpix = pix_ok ? ld3(d_image + 3 * pix) : zero3();
+  float3 a = (1.0f / (float)op.spp) * wpix;
+  const float3 Le = ld3(s.radiance);
+  int iters = (op.spp + G - 1) / G;
+  for (int it = 0; it < iters; ++it) {
+    int sidx = lane % G + it * G;
+    bool active = pix_ok && sidx < op.spp && !op.primary_only;
+    CamHit c;
+    c.k = -1;
+    if (active) camera_hit(s, op, tape_tri, tape_bary, pix, sidx, c);
+    float3 dv0 = zero3(), dv1 = zero3(), dv2 = zero3(), de0 = zero3(), de1 = zero3();
+    float3 dmv[2][3] = {{zero3(), zero3(), zero3()}, {zero3(), zero3(), zero3()}};
+    int vid0 = 0, vid1 = 0, vid2 = 0, eid0 = 0, eid1 = 0, mids[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    bool have_edge = false, have_m[2] = {false, false};
+    if (active && c.k >= 0) {
+      Vertex x;
+      load_vertex(s, c.k, c.b1, c.b2, c.d, x);
+      float3 dp = zero3();
+      SecOut so;
+      secondary_at_vertex(s, op, (uint32_t)pix, (uint32_t)sidx, 0, 1, x, shading_normal(x),
+                          ld3(s.albedo + 3 * c.k), a, Le, dp, so);
+      if (so.have_edge) {
+        de0 = so.de0;
+        de1 = so.de1;
+        eid0 = so.eid0;
+        eid1 = so.eid1;
+        for (int sd = 0; sd < 2; ++sd) {
+          have_m[sd] = so.have_m[sd];
+          for (int q = 0; q < 3; ++q) {
+            dmv[sd][q] = so.dm[sd][q];
+            mids[sd][q] = so.mid[sd][q];
+          }
+        }
+        have_edge = true;
+        const int32_t* vid = s.tris + 3 * c.k;
+        vid0 = vid[0]; vid1 = vid[1]; vid2 = vid[2];
+        hit_point_adjoint(s, c, x, dp, zero3(), dv0, dv1, dv2, g);
+      }
+    }
+    scatter3(gr.verts, eid0, de0, have_edge);
+    scatter3(gr.verts, eid1, de1, have_edge);
+    scatter3(gr.verts, vid0, dv0, have_edge);
+    scatter3(gr.verts, vid1, dv1, have_edge);
+    scatter3(gr.verts, vid2, dv2, have_edge);
+    for (int sd = 0; sd < 2; ++sd)
+      for (int q = 0; q < 3; ++q) scatter3(gr.verts, mids[sd][q], dmv[sd][q], have_m[sd]);
+  }
+  block_globals(g, gr.partials + blk * kGlobals, rows_written != 0);
+}
+__global__ void __launch_bounds__(kBlock, DRT_PIXEL_MIN_BLOCKS) k_backward_secondary(SceneView s, Opts op, const int32_t* tape_tri,
+                                                               const float2* tape_bary, const float* d_image, Grads gr,
+                                                               int G, int rows_written) {
+  secondary_block(s, op, tape_tri, tape_bary, d_image, gr, G, rows_written, blockIdx.x);
 }
 
 __device__ __forceinline__ void path_block(const SceneView& s, const Opts& op, const int32_t* tape_tri,
@@ -1537,7 +1485,9 @@ __global__ void k_primary_keys(SceneView s, Opts op, int64_t n_edge, uint32_t* k
   uint32_t key = 0;
   if (ptotal > 0.0) {
     EdgeSample es = primary_sample(s, op, j, ptotal);
-    int px = min(max((int)floorf(es.x), 0), s.W - 1), py = min(max((int)floorf(es.y), 0), s.H - 1);
+    // position at 1/kKeySub of a pixel
+    int px = min(max((int)floorf(es.x * kKeySub), 0), s.W * kKeySub - 1);
+    int py = min(max((int)floorf(es.y * kKeySub), 0), s.H * kKeySub - 1);
     key = spread_bits16((uint32_t)px) | (spread_bits16((uint32_t)py) << 1);
   }
   keys[j] = key;
@@ -1720,7 +1670,9 @@ __global__ void k_batch_keys(const BatchScene* bs, const int64_t* eprefix, int n
   uint32_t key = 0;
   if (ptotal > 0.0) {
     EdgeSample es = primary_sample(s, bs[sc].op, j, ptotal);
-    int px = min(max((int)floorf(es.x), 0), s.W - 1), py = min(max((int)floorf(es.y), 0), s.H - 1);
+    // position at 1/kKeySub of a pixel
+    int px = min(max((int)floorf(es.x * kKeySub), 0), s.W * kKeySub - 1);
+    int py = min(max((int)floorf(es.y * kKeySub), 0), s.H * kKeySub - 1);
     key = spread_bits16((uint32_t)px) | (spread_bits16((uint32_t)py) << 1);
   }
   keys[g] = ((uint32_t)sc << pix_bits) | key;
@@ -1765,7 +1717,7 @@ int64_t primary_blocks_for(int64_t n_edge, int64_t per_thread) {
 
 int screen_key_bits(int W, int H) {
   int bits = 2;
-  while ((1 << (bits / 2)) < std::max(W, H)) bits += 2;
+  while ((1 << (bits / 2)) < std::max(W, H) * kKeySub) bits += 2;
   return bits;
 }
 
