@@ -34,7 +34,7 @@ constexpr int kBlock = 256;
 #endif
 // Screen keys of the primary edge samples resolve 1/DRT_KEY_SUB of a pixel.
 #ifndef DRT_KEY_SUB
-#define DRT_KEY_SUB 4
+#define DRT_KEY_SUB 8
 #endif
 constexpr int kKeySub = DRT_KEY_SUB;
 // Resident CTAs per SM the render kernel is compiled for.
