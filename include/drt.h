@@ -299,8 +299,14 @@ drt_status drt_adam_step(drt_context* ctx, float* params, const float* grads, fl
  * rays traced at the segment midpoint (one through it, one half a pixel to
  * each side of the edge): whether the edge is visible there, whether the two
  * sides see different triangles or only one sees the background, the albedo
- * difference of what they see and whether one sees a light. */
-drt_status drt_segment_features(drt_context* ctx, drt_scene* scene, const float* d_image, void* x, void* stream);
+ * difference of what they see and whether one sees a light; the mean
+ * |d_image| at four points along the segment over the image mean; and, if
+ * image ([H,W,3] device, the rendered image of the step; may be NULL) is
+ * given, the radiance contrast across the edge read from it 1.5 pixels to
+ * each side of the segment midpoint, relative and log-compressed (zero
+ * without an image). */
+drt_status drt_segment_features(drt_context* ctx, drt_scene* scene, const float* d_image, const float* image, void* x,
+                                void* stream);
 
 /* Screen-tile segments of the clipped primary edges: every clipped edge is
  * cut where it crosses the 16-pixel tile grid (FP32 crossing parameters in

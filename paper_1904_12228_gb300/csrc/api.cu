@@ -574,12 +574,14 @@ drt_status drt_scene_segments(drt_context* ctx, drt_scene* s, int64_t* n, int32_
   return DRT_OK;
 }
 
-drt_status drt_segment_features(drt_context* ctx, drt_scene* s, const float* d_image, void* x, void* stream) {
+drt_status drt_segment_features(drt_context* ctx, drt_scene* s, const float* d_image, const float* image, void* x,
+                                void* stream) {
   if (!ctx || !s || !d_image || !x) return fail(DRT_ERR_INVALID_ARG, "NULL argument");
-  if (!is_device_ptr(d_image) || !is_device_ptr(x)) return fail(DRT_ERR_INVALID_ARG, "device arrays only");
+  if (!is_device_ptr(d_image) || !is_device_ptr(x) || (image && !is_device_ptr(image)))
+    return fail(DRT_ERR_INVALID_ARG, "device arrays only");
   cudaStream_t st = (cudaStream_t)stream;
   DRT_TRY(build_segments(s, st));
-  CUDA_TRY(drt::launch_segment_features(s, d_image, x, st));
+  CUDA_TRY(drt::launch_segment_features(s, d_image, image, x, st));
   return DRT_OK;
 }
 

@@ -629,9 +629,15 @@ __global__ void k_tile_weight_mean(float* tile_w, int nt) {
 }
 
 // 32 features per tile segment, stored as BF16 (zero-padded to 32).
+__device__ __forceinline__ float3 pixel_at(const float* img, int W, int H, float x, float y) {
+  int px = min(max((int)floorf(x), 0), W - 1), py = min(max((int)floorf(y), 0), H - 1);
+  const float* p = img + 3 * ((size_t)py * W + px);
+  return make_float3(p[0], p[1], p[2]);
+}
+
 __global__ void k_segment_features(SceneView s, const int32_t* seg_edge, const int32_t* seg_tile, const float2* seg_s,
                                    const double* seg_len, int n, const int2* edge_faces, const float* tile_w,
-                                   __nv_bfloat16* x) {
+                                   const float* d_image, const float* image, __nv_bfloat16* x) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   int e = seg_edge[k], tile = seg_tile[k];
@@ -718,13 +724,31 @@ __global__ void k_segment_features(SceneView s, const int32_t* seg_edge, const i
       if (t >= 0 && s.light_of_tri[t] >= 0) f[28] = 1.f;
     }
     f[27] = fabsf(lum[0] - lum[1]);
+    // loss adjoint along the segment, over its image mean
+    float wsum = 0.f;
+    for (int q = 0; q < 4; ++q) {
+      float u = ss.x + (ss.y - ss.x) * (0.125f + 0.25f * q);
+      float3 wv = pixel_at(d_image, s.W, s.H, ax + u * dx, ay + u * dy);
+      wsum += fabsf(wv.x) + fabsf(wv.y) + fabsf(wv.z);
+    }
+    f[29] = wm > 0.f ? 0.25f * wsum / wm : 0.f;
+    // radiance contrast across the edge in the rendered image
+    if (image) {
+      float3 iu = pixel_at(image, s.W, s.H, xm + 1.5f * nx, ym + 1.5f * ny);
+      float3 il = pixel_at(image, s.W, s.H, xm - 1.5f * nx, ym - 1.5f * ny);
+      float dif = fabsf(iu.x - il.x) + fabsf(iu.y - il.y) + fabsf(iu.z - il.z);
+      float sum = fabsf(iu.x) + fabsf(iu.y) + fabsf(iu.z) + fabsf(il.x) + fabsf(il.y) + fabsf(il.z);
+      f[30] = dif / (sum + 1e-6f);
+      f[31] = log1pf(dif);
+    }
   }
   for (int i = 0; i < 32; ++i) x[(size_t)k * 32 + i] = __float2bfloat16_rn(f[i]);
 }
 
 }  // namespace
 
-cudaError_t launch_segment_features(const drt_scene* s, const float* d_image, void* x, cudaStream_t st) {
+cudaError_t launch_segment_features(const drt_scene* s, const float* d_image, const float* image, void* x,
+                                    cudaStream_t st) {
   int tx = (s->W + 15) / 16, ty = (s->H + 15) / 16, nt = tx * ty;
   DRT_PROF_LAUNCH("tile_weights", st, k_tile_weights<<<(nt + kBlock - 1) / kBlock, kBlock, 0, st>>>(
                                           d_image, s->W, s->H, tx, ty, s->tile_w));
@@ -733,7 +757,7 @@ cudaError_t launch_segment_features(const drt_scene* s, const float* d_image, vo
   if (n > 0)
     DRT_PROF_LAUNCH("segment_features", st, k_segment_features<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(
                                                 s->view(), s->seg_edge, s->seg_tile, s->seg_s, s->seg_len, n,
-                                                s->edge_faces, s->tile_w, (__nv_bfloat16*)x));
+                                                s->edge_faces, s->tile_w, d_image, image, (__nv_bfloat16*)x));
   return cudaGetLastError();
 }
 

@@ -119,7 +119,8 @@ cudaError_t scan_inclusive_f64(const double* in, double* out, double* tmp, int n
 cudaError_t launch_segment_count(const drt_scene* s, uint32_t* counts, cudaStream_t st);
 cudaError_t launch_segment_fill(const drt_scene* s, const uint32_t* offsets, cudaStream_t st);
 cudaError_t launch_proposal_cdf(drt_scene* s, const float* weights, int mode, cudaStream_t st);
-cudaError_t launch_segment_features(const drt_scene* s, const float* d_image, void* x, cudaStream_t st);
+cudaError_t launch_segment_features(const drt_scene* s, const float* d_image, const float* image, void* x,
+                                    cudaStream_t st);
 size_t radix_hist_tmp_entries(int n);
 cudaError_t build_bvh(drt_scene* s, cudaStream_t st);
 cudaError_t build_edge_cdfs(drt_scene* s, cudaStream_t st);

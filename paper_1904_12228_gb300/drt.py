@@ -112,7 +112,7 @@ def load(build_if_missing: bool = True):
                               ctypes.POINTER(MlpGrads), vp, vp], i32),
         "drt_adam_step": ([vp, vp, vp, vp, vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                            ctypes.c_float, ctypes.c_int32, vp], i32),
-        "drt_segment_features": ([vp, vp, vp, vp, vp], i32),
+        "drt_segment_features": ([vp, vp, vp, vp, vp, vp], i32),
         "drt_scene_segments": ([vp, vp, ctypes.POINTER(ctypes.c_int64), vp, vp, vp, ctypes.c_int64, vp], i32),
         "drt_render_backward_noalloc": ([vp, vp, vp, ctypes.POINTER(RenderOpts), vp, ctypes.POINTER(Grads), vp],
                                         i32),
@@ -342,10 +342,11 @@ class Scene:
                                                _stream(stream)))
         return n.value
 
-    def segment_features(self, d_image, x, stream=None):
-        """Features [n_seg, 32] (bf16 device tensor x) of the current segments."""
-        _check(self.ctx.lib.drt_segment_features(self.ctx.handle, self.handle, _ptr(d_image), _ptr(x),
-                                                 _stream(stream)))
+    def segment_features(self, d_image, x, image=None, stream=None):
+        """Features [n_seg, 32] (bf16 device tensor x) of the current segments;
+        ``image`` is the step's rendered image (optional)."""
+        _check(self.ctx.lib.drt_segment_features(self.ctx.handle, self.handle, _ptr(d_image), _ptr(image),
+                                                 _ptr(x), _stream(stream)))
 
     def closest(self, o, d, tri, tb, stream=None):
         """Closest hits of rays o, d [n,3] into tri [n] (int32) and tb [n,3]."""

@@ -68,16 +68,18 @@ class EdgeProposal:
         self._gp = drt.MlpGrads(*(self.g[k].data_ptr() for k in NAMES))
 
     # -- inference ------------------------------------------------------------
-    def features(self, scene: drt.Scene, d_image: torch.Tensor, n: int | None = None, stream=None):
+    def features(self, scene: drt.Scene, d_image: torch.Tensor, n: int | None = None, image=None, stream=None):
         n = scene.num_segments(stream) if n is None else n
         x = torch.empty((n, N_IN), dtype=torch.int16, device=d_image.device)
         if n:
-            scene.segment_features(d_image, x, stream)
+            scene.segment_features(d_image, x, image, stream)
         return x
 
-    def scores(self, scene: drt.Scene, d_image: torch.Tensor, n: int | None = None, stream=None):
-        """Network scores of the scene's current tile segments ([n] float32)."""
-        x = self.features(scene, d_image, n, stream)
+    def scores(self, scene: drt.Scene, d_image: torch.Tensor, n: int | None = None, image=None, stream=None):
+        """Network scores of the scene's current tile segments ([n] float32);
+        ``image``: the rendered image of the step (its contrast across edges
+        is a feature)."""
+        x = self.features(scene, d_image, n, image, stream)
         y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
         if x.shape[0]:
             self.ctx.mlp_forward(x, self._w, y, stream)
@@ -160,8 +162,19 @@ def collect(ctx: drt.Context, scene: drt.Scene, d_image: torch.Tensor, *, edge_s
     target = torch.log(rel + delta).float()
     mask = (lens / lens.mean()).float()
     x = torch.empty((n, N_IN), dtype=torch.int16, device=dev)
-    scene.segment_features(d_image, x)
+    scene.segment_features(d_image, x, step_image(scene, seed, max_depth))
     return Dataset(x, target, mask)
+
+
+IMAGE_SPP = 16
+
+
+def step_image(scene: drt.Scene, seed: int, max_depth: int = 1) -> torch.Tensor:
+    """The rendered image an optimisation step has before its backward pass
+    (here IMAGE_SPP samples per pixel)."""
+    img = torch.empty((scene.height, scene.width, 3), device="cuda")
+    scene.render(img, drt.make_opts(IMAGE_SPP, IMAGE_SPP, max_depth=max_depth, seed=seed + 777))
+    return img
 
 
 # ---------------------------------------------------------------------------
@@ -193,12 +206,15 @@ def gradient_runs(scene: drt.Scene, d_image: torch.Tensor, *, edge_spp: int, K: 
     runs = torch.zeros((K, scene.n_verts * 3), device=dev)
     times = []
     n = scene.num_segments() if proposal is not None else 0
+    # the forward image the step rendered before its backward pass (not timed:
+    # the plain sampler's step renders it too)
+    image = step_image(scene, seed, max_depth) if proposal is not None else None
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for k in range(K):
         dv = runs[k].view(scene.n_verts, 3)
         e0.record()
         if proposal is not None:
-            sc = proposal.scores(scene, d_image, n)
+            sc = proposal.scores(scene, d_image, n, image)
             o = drt.make_opts(1, edge_spp, max_depth=max_depth, seed=seed + k, terms=TERM_PRIMARY, seg_scores=sc)
         else:
             o = drt.make_opts(1, edge_spp, max_depth=max_depth, seed=seed + k, terms=TERM_PRIMARY)

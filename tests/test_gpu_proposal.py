@@ -69,3 +69,11 @@ def test_scores_cover_every_segment(trained):
     torch.cuda.synchronize()
     assert y.shape[0] == s.num_segments() == len(s.segments()[0])
     assert torch.isfinite(y).all()
+    # the image features are zero without an image and present with one
+    x0 = net.features(s, w).view(torch.bfloat16).float()
+    x1 = net.features(s, w, image=P.step_image(s, 3)).view(torch.bfloat16).float()
+    torch.cuda.synchronize()
+    assert torch.isfinite(x1).all()
+    assert float(x0[:, 30:32].abs().max()) == 0.0 and float(x1[:, 30:32].abs().max()) > 0.0
+    assert torch.equal(x0[:, :30], x1[:, :30])
+    assert float(x1[:, 29].min()) >= 0.0 and float(x1[:, 29].max()) > 0.0
