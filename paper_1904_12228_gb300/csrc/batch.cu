@@ -100,6 +100,7 @@ struct drt_batch {
   int64_t n_items[drt::kPhases] = {};
   int64_t total_edge = 0, total_tape = 0, total_floats = 0, total_sec = 0;
   int pix_bits = 0, key_bits = 0;  // screen key bits; with the scene index above them
+  int key_shift = 0;               // screen key bits dropped to fit 32-bit keys
   // device
   BatchScene* d_desc = nullptr;
   BatchScene* d_desc_tune = nullptr;
@@ -208,8 +209,11 @@ void plan(drt_batch* b, bool bind) {
   }
   int sb = 0;
   while ((1 << sb) < n) ++sb;
-  b->pix_bits = pix_bits;
-  b->key_bits = pix_bits + sb;
+  // the scene index goes above the screen key; drop low screen bits (a
+  // coarser sample order) if both do not fit in 32 bits
+  b->key_shift = std::max(0, pix_bits + sb - 32);
+  b->pix_bits = pix_bits - b->key_shift;
+  b->key_bits = b->pix_bits + sb;
   b->total_edge = b->eprefix[n];
   b->total_tape = tape_off;
   b->total_floats = float_off;
@@ -254,7 +258,8 @@ cudaError_t run_phase(drt_batch* b, int phase, const BatchScene* desc, cudaStrea
 
 cudaError_t sort_edges(drt_batch* b, const BatchScene* desc, cudaStream_t st) {
   if (b->total_edge <= 0) return cudaSuccess;
-  cudaError_t e = drt::launch_batch_keys(desc, b->d_eprefix, b->n, b->total_edge, b->pix_bits, b->keys, b->vals, st);
+  cudaError_t e = drt::launch_batch_keys(desc, b->d_eprefix, b->n, b->total_edge, b->pix_bits, b->key_shift, b->keys,
+                                         b->vals, st);
   if (e != cudaSuccess) return e;
   drt::radix_sort_pairs(b->keys, b->vals, b->keys2, b->vals2, b->hist, b->hist_tmp, (int)b->total_edge,
                         b->key_bits, st);
@@ -424,9 +429,9 @@ drt_status drt_batch_create(drt_context* ctx, const drt_batch_item* items, int32
   b->autotune = autotune != 0;
   for (int p = 0; p < drt::kPhases; ++p) b->occupancy[p] = drt::batch_phase_occupancy(p);
   plan(b, false);  // totals at the largest edge budget
-  if (b->key_bits > 32 || b->total_edge > (int64_t)INT32_MAX) {
+  if (b->total_edge > (int64_t)INT32_MAX || b->key_bits > 32) {
     free_batch(b);
-    return bfail(DRT_ERR_INVALID_ARG, "batch too large: screen keys need more than 32 bits or 2^31 edge samples");
+    return bfail(DRT_ERR_INVALID_ARG, "batch too large: more than 2^31 primary edge samples");
   }
   drt_status s = balloc(&b->d_desc, n);
   if (s == DRT_OK && b->autotune) s = balloc(&b->d_desc_tune, n);

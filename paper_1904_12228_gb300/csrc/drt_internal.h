@@ -150,7 +150,7 @@ cudaError_t launch_batch_phase(int phase, const BatchScene* bs, const int64_t* p
                                int grid, int chunk, unsigned long long* counter, cudaStream_t st);
 int batch_phase_occupancy(int phase);              // resident CTAs per SM
 cudaError_t launch_batch_keys(const BatchScene* bs, const int64_t* eprefix, int n, int64_t total, int pix_bits,
-                              uint32_t* keys, int32_t* vals, cudaStream_t st);
+                              int shift, uint32_t* keys, int32_t* vals, cudaStream_t st);
 // fixed-order sum of `rows` partial rows into the global gradients; the
 // buffer holds partial_floats(rows) floats (the rows, then stage-1 totals)
 int64_t partial_floats(int64_t rows);

@@ -1658,9 +1658,11 @@ __global__ void __launch_bounds__(kBlock, PhaseMinBlocks<PH>::value)
 
 // Screen keys of the primary edge samples of all scenes, scene index in the
 // high bits: one stable sort orders every scene's samples exactly as the
-// single-scene sort does.  vals = index of the sample within its scene.
+// single-scene sort does (with shift > 0, when the 32-bit key has no room
+// for all screen bits, on a coarser grid).  vals = index of the sample
+// within its scene.
 __global__ void k_batch_keys(const BatchScene* bs, const int64_t* eprefix, int n, int64_t total, int pix_bits,
-                             uint32_t* keys, int32_t* vals) {
+                             int shift, uint32_t* keys, int32_t* vals) {
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
   int sc = batch_scene_of(eprefix, n, g);
@@ -1675,7 +1677,7 @@ __global__ void k_batch_keys(const BatchScene* bs, const int64_t* eprefix, int n
     int py = min(max((int)floorf(es.y * kKeySub), 0), s.H * kKeySub - 1);
     key = spread_bits16((uint32_t)px) | (spread_bits16((uint32_t)py) << 1);
   }
-  keys[g] = ((uint32_t)sc << pix_bits) | key;
+  keys[g] = ((uint32_t)sc << pix_bits) | (key >> shift);
   vals[g] = (int32_t)j;
 }
 
@@ -1754,11 +1756,11 @@ int batch_phase_occupancy(int phase) {
 }
 
 cudaError_t launch_batch_keys(const BatchScene* bs, const int64_t* eprefix, int n, int64_t total, int pix_bits,
-                              uint32_t* keys, int32_t* vals, cudaStream_t st) {
+                              int shift, uint32_t* keys, int32_t* vals, cudaStream_t st) {
   if (total <= 0) return cudaSuccess;
   DRT_PROF_LAUNCH("batch_primary_keys", st,
-                  k_batch_keys<<<(unsigned)((total + kBlock - 1) / kBlock), kBlock, 0, st>>>(bs, eprefix, n, total,
-                                                                                              pix_bits, keys, vals));
+                  k_batch_keys<<<(unsigned)((total + kBlock - 1) / kBlock), kBlock, 0, st>>>(
+                      bs, eprefix, n, total, pix_bits, shift, keys, vals));
   return cudaGetLastError();
 }
 
