@@ -128,7 +128,7 @@ void free_scene_buffers(drt_scene* s) {
                   s->flags, s->child_orig, s->hist, s->hist_tmp, s->bounds, s->partials, s->esort.keys, s->esort.keys2,
                   s->esort.hist, s->esort.hist_tmp, s->esort.vals, s->esort.vals2, s->seg_edge, s->seg_tile,
                   s->seg_count, s->seg_scan_tmp, s->seg_s, s->seg_len, s->seg_a, s->seg_b, s->seg_cdf, s->seg_tmp,
-                  s->sec.dp, s->sec.queue, s->sec.count};
+                  s->sec.dp, s->sec.queue, s->sec.count, s->pguide, s->sguide};
   for (void* b : bufs) dfree(b);
 }
 
@@ -218,7 +218,7 @@ drt::SceneView drt_scene::view() const {
   v.verts = verts; v.tris = tris; v.albedo = albedo; v.radiance = radiance; v.cam = cam; v.cam_scale = cam_scale;
   v.w2c = w2c; v.light_tris = light_tris; v.light_of_tri = light_of_tri; v.light_cdf = light_cdf;
   v.light_area = light_area; v.light_box = light_box; v.nodes = nodes; v.soup = soup; v.edges = edges; v.pedge = pedge; v.pcdf = pcdf;
-  v.scdf = scdf; v.err = ctx->err; v.counters = nullptr;
+  v.scdf = scdf; v.pguide = pguide; v.sguide = sguide; v.err = ctx->err; v.counters = nullptr;
   v.seg_cdf = seg_n > 0 ? seg_cdf : nullptr; v.seg_edge = seg_edge; v.seg_s = seg_s; v.seg_len = seg_len;
   v.n_seg = (int)std::max<int64_t>(0, seg_n);
   v.V = V; v.T = T; v.L = L; v.E = E; v.W = W; v.H = H; v.cam_type = cam_type;
@@ -320,6 +320,7 @@ drt_status drt_scene_upload(drt_context* ctx, const drt_scene_desc* d, void* str
   ALLOC(tile_w, (size_t)((s->W + 15) / 16) * ((s->H + 15) / 16) + 1)
   ALLOC(pedge, 8 * (size_t)std::max(1, E)) ALLOC(plen, std::max(1, E)) ALLOC(pcdf, std::max(1, E))
   ALLOC(slen, std::max(1, E)) ALLOC(scdf, std::max(1, E)) ALLOC(scan_tmp, std::max(1, E / 1024 + 2))
+  ALLOC(pguide, drt::kGuide + 1) ALLOC(sguide, drt::kGuide + 1)
   ALLOC(keys, T) ALLOC(keys2, T) ALLOC(vals, T) ALLOC(vals2, T) ALLOC(parent, std::max(1, T))
   ALLOC(leaf_parent, T) ALLOC(flags, std::max(1, T)) ALLOC(child_orig, std::max(1, T)) ALLOC(hist, drt::radix_hist_entries(T))
   ALLOC(hist_tmp, drt::radix_hist_tmp_entries(T)) ALLOC(bounds, 8)

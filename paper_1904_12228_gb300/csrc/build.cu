@@ -853,12 +853,35 @@ cudaError_t build_bvh(drt_scene* s, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Guide table of an inclusive CDF: g[b] = first index whose value exceeds
+// b * total / kGuide (b < kGuide), g[kGuide] = n.
+__global__ void k_cdf_guide(const double* cdf, int n, int* guide) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b > kGuide) return;
+  if (b == kGuide) {
+    guide[b] = n;
+    return;
+  }
+  double thr = (double)b * (cdf[n - 1] / (double)kGuide);
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (cdf[mid] > thr) hi = mid; else lo = mid + 1;
+  }
+  guide[b] = lo;
+}
+
 cudaError_t build_edge_cdfs(drt_scene* s, cudaStream_t st) {
   if (s->E <= 0) return cudaSuccess;
   DRT_PROF_LAUNCH("edge_tables", st, k_edge_tables<<<(s->E + kBlock - 1) / kBlock, kBlock, 0, st>>>(s->view(), s->pedge, s->plen, s->slen));
   cudaError_t e = scan_inclusive(s->plen, s->pcdf, s->scan_tmp, s->E, st);
   if (e != cudaSuccess) return e;
-  return scan_inclusive(s->slen, s->scdf, s->scan_tmp, s->E, st);
+  e = scan_inclusive(s->slen, s->scdf, s->scan_tmp, s->E, st);
+  if (e != cudaSuccess) return e;
+  unsigned gb = (kGuide + 1 + kBlock - 1) / kBlock;
+  DRT_PROF_LAUNCH("cdf_guides", st, k_cdf_guide<<<gb, kBlock, 0, st>>>(s->pcdf, s->E, s->pguide));
+  DRT_PROF_LAUNCH("cdf_guides", st, k_cdf_guide<<<gb, kBlock, 0, st>>>(s->scdf, s->E, s->sguide));
+  return cudaGetLastError();
 }
 
 cudaError_t build_scene_derived(drt_scene* s, cudaStream_t st) {

@@ -102,6 +102,8 @@ struct SceneView {
   const float* pedge;        // [E,8] primary edge table: ax ay bx by t0 t1 (2 pad)
   const double* pcdf;        // [E] inclusive prefix of clipped screen lengths
   const double* scdf;        // [E] inclusive prefix of 3D edge lengths
+  const int* pguide;         // [kGuide+1] guide table of pcdf
+  const int* sguide;         // [kGuide+1] guide table of scdf
   int* err;                  // [2] device error flag (code, info)
   unsigned long long* counters;  // optional work counters [4] for this launch (or null)
   // learned-proposal mode (null otherwise): tile segments and their proposal CDF
@@ -261,8 +263,32 @@ __device__ __forceinline__ bool clip_screen(float ax, float ay, float bx, float 
 }
 
 // Upper bound in an inclusive CDF; falls back to the last entry with mass.
+// Guide tables of the edge CDFs: g[b] = cdf_pick's answer for the target
+// b * total / kGuide (b < kGuide), g[kGuide] = n.
+constexpr int kGuide = 1024;
+
 __device__ __forceinline__ int cdf_pick(const double* cdf, int n, double target) {
   int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (cdf[mid] > target) hi = mid; else lo = mid + 1;
+  }
+  if (lo >= n) {
+    lo = n - 1;
+    while (lo > 0 && cdf[lo] == cdf[lo - 1]) --lo;
+  }
+  return lo;
+}
+
+// cdf_pick with the search narrowed by a guide table (same answer): the
+// target's bucket, computed to within one bucket, and its neighbours bound
+// the first index whose value exceeds the target (the thresholds of buckets
+// b - 1 and b + 2 lie below and above it; the answer is monotone).
+__device__ __forceinline__ int cdf_pick_guided(const double* cdf, int n, double target, const int* guide,
+                                               double total) {
+  int b = (int)(target * ((double)kGuide / total));
+  b = min(max(b, 0), kGuide - 1);
+  int lo = guide[max(b - 1, 0)], hi = guide[min(b + 2, kGuide)];
   while (lo < hi) {
     int mid = (lo + hi) >> 1;
     if (cdf[mid] > target) hi = mid; else lo = mid + 1;

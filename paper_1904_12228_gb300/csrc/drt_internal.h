@@ -50,6 +50,7 @@ struct drt_scene {
   float* tile_w = nullptr;     // mean |d_image| per screen tile (features)
   float* pedge = nullptr;
   double *plen = nullptr, *pcdf = nullptr, *slen = nullptr, *scdf = nullptr, *scan_tmp = nullptr;
+  int *pguide = nullptr, *sguide = nullptr;  // guide tables of pcdf and scdf
   // LBVH build scratch
   uint32_t *keys = nullptr, *keys2 = nullptr;
   int32_t *vals = nullptr, *vals2 = nullptr, *parent = nullptr, *leaf_parent = nullptr, *flags = nullptr;

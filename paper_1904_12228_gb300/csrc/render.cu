@@ -896,7 +896,7 @@ __device__ __forceinline__ bool secondary_sides(const SceneView& s, const Opts& 
                                                 int md, const Vertex& x, float3 n, SecGeom& gm) {
   double stotal = s.scdf[s.E - 1];
   uint4 r = rng4(op.key, c0, c1, kEdgeSecondary, (uint32_t)b, kPassInterior, op.scene_id);
-  int e = cdf_pick(s.scdf, s.E, dm(u01d(r.x, r.y), stotal));
+  int e = cdf_pick_guided(s.scdf, s.E, dm(u01d(r.x, r.y), stotal), s.sguide, stotal);
   double le = s.scdf[e] - (e > 0 ? s.scdf[e - 1] : 0.0);
   float t = u01f(r.z);
   int2 ev = s.edges[e];
@@ -1448,7 +1448,7 @@ __device__ __forceinline__ EdgeSample primary_sample(const SceneView& s, const O
     t1 = ss.y;
     es.inv_pdf_len = ddv(s.seg_len[k], ddv(q, qt));
   } else {
-    es.e = cdf_pick(s.pcdf, s.E, dm(u01d(r.x, r.y), ptotal));
+    es.e = cdf_pick_guided(s.pcdf, s.E, dm(u01d(r.x, r.y), ptotal), s.pguide, ptotal);
     es.inv_pdf_len = ptotal;
   }
   const float4* row = reinterpret_cast<const float4*>(s.pedge + 8 * es.e);
@@ -1506,6 +1506,7 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
   double ptotal = s.pcdf[s.E - 1];
   float W = (float)s.W, H = (float)s.H;
   float eps = fm(op.eps_rel, fmaxf(W, H));
+  const double inv_n = 1.0 / (double)n_edge;  // Eq. mc averages over the N edge samples
   const int side = threadIdx.x & 1;
   for (int64_t it = 0; it < per_thread; ++it) {
     // consecutive lane pairs take consecutive entries of the screen-ordered list
@@ -1545,7 +1546,7 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
       if (op.seg_log && es.seg >= 0) atomicAdd(op.seg_log + es.seg, fabsf(diff));
       if (diff != 0.f) {
         float gl = sqrtf((ax - bx) * (ax - bx) + (ay - by) * (ay - by));
-        float c = (float)((double)diff * es.inv_pdf_len / ((double)gl * (double)n_edge));
+        float c = diff * (float)(es.inv_pdf_len * inv_n) / gl;
         float dax = c * (by - y), day = c * (x - bx), dbx = c * (y - ay), dby = c * (ax - x);
         int2 ev = s.edges[e];
         ia = ev.x; ib = ev.y;
