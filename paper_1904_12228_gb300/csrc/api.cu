@@ -247,12 +247,19 @@ drt_status drt_create(int device, drt_context** out) {
     return s;
   }
   CUDA_TRY(cudaMemset(c->err, 0, 2 * sizeof(int)));
+  CUDA_TRY(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  CUDA_TRY(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming));
   *out = c;
   return DRT_OK;
 }
 
 drt_status drt_destroy(drt_context* ctx) {
   if (!ctx) return DRT_OK;
+  if (ctx->side) cudaStreamSynchronize(ctx->side);
+  if (ctx->fork) cudaEventDestroy(ctx->fork);
+  if (ctx->join) cudaEventDestroy(ctx->join);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   dfree(ctx->err);
   delete ctx;
   return DRT_OK;

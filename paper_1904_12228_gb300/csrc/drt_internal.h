@@ -14,6 +14,10 @@ struct drt_context {
   int device = 0;
   int* err = nullptr;        // device error flag [2]
   int num_sms = 0;
+  // second stream for work that can run beside the caller's stream, joined
+  // back by events before its results are read
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 namespace drt {

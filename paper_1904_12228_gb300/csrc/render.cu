@@ -1829,6 +1829,32 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
   if ((op.terms & 2) && s.E > 0 && n_edge > 0) primary_blocks(n_edge, &blocks_e, &per_thread);
   Grads gr{d_verts, d_albedo, partials};
   bool need_i = (op.terms & 5) != 0;
+  // The screen keys of the primary edge samples and their sort depend on
+  // nothing the other passes compute: they run on the context's side stream,
+  // beside the secondary and interior passes, and are joined back before the
+  // primary edge kernel.
+  const int32_t* order = nullptr;
+  bool forked = false;
+  if (blocks_e > 0 && sort && sort->cap >= n_edge) {
+    cudaStream_t ss = st;
+    drt_context* cx = sc->ctx;
+    if (cx && cx->side) {
+      if (cudaEventRecord(cx->fork, st) == cudaSuccess && cudaStreamWaitEvent(cx->side, cx->fork, 0) == cudaSuccess) {
+        ss = cx->side;
+        forked = true;
+      } else {
+        cudaGetLastError();
+      }
+    }
+    int bits = screen_key_bits(s.W, s.H);
+    DRT_PROF_LAUNCH("primary_keys", ss,
+                    k_primary_keys<<<(unsigned)((n_edge + kBlock - 1) / kBlock), kBlock, 0, ss>>>(
+                        s, op, n_edge, sort->keys, sort->vals));
+    bool alt = radix_sort_pairs(sort->keys, sort->vals, sort->keys2, sort->vals2, sort->hist, sort->hist_tmp,
+                                (int)n_edge, bits, ss);
+    order = alt ? sort->vals2 : sort->vals;
+    if (forked) cudaEventRecord(cx->join, ss);
+  }
   const int32_t* tt = tape ? tape->tri : nullptr;
   const float2* tb = tape ? tape->bary : nullptr;
   bool path = !op.primary_only && op.max_depth > 1;
@@ -1880,16 +1906,7 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
   }
   Grads ge{d_verts, d_albedo, partials + (need_i ? blocks_i : 0) * kGlobals};
   if (blocks_e > 0) {
-    const int32_t* order = nullptr;
-    if (sort && sort->cap >= n_edge) {
-      int bits = screen_key_bits(s.W, s.H);
-      DRT_PROF_LAUNCH("primary_keys", st,
-                      k_primary_keys<<<(unsigned)((n_edge + kBlock - 1) / kBlock), kBlock, 0, st>>>(
-                          s, op, n_edge, sort->keys, sort->vals));
-      bool alt = radix_sort_pairs(sort->keys, sort->vals, sort->keys2, sort->vals2, sort->hist, sort->hist_tmp,
-                                  (int)n_edge, bits, st);
-      order = alt ? sort->vals2 : sort->vals;
-    }
+    if (forked) cudaStreamWaitEvent(st, sc->ctx->join, 0);
     s.counters = counter_slot(kSlotBwdPrimary);
     ProfToken pt = prof_begin("backward_primary_edges", st);
     k_backward_primary<<<(unsigned)blocks_e, kBlock, 0, st>>>(s, op, d_image, ge, n_edge, per_thread, order);
