@@ -46,9 +46,10 @@ constexpr int kKeySub = DRT_KEY_SUB;
 #ifndef DRT_SEC_MIN_BLOCKS
 #define DRT_SEC_MIN_BLOCKS 2
 #endif
-// Resident CTAs per SM the depth > 1 path pass is compiled for.
+// Resident CTAs per SM the depth > 1 path pass is compiled for (its variant
+// with the secondary edge samples inside the pass stays at one: it spills).
 #ifndef DRT_PATH_MIN_BLOCKS
-#define DRT_PATH_MIN_BLOCKS 1
+#define DRT_PATH_MIN_BLOCKS 2
 #endif
 static_assert(kBlock / 32 <= kTraceWarps, "warp-cooperative traversals support at most kTraceWarps warps per CTA");
 constexpr unsigned kFull = 0xffffffffu;
@@ -1100,6 +1101,9 @@ __global__ void __launch_bounds__(kBlock, DRT_PIXEL_MIN_BLOCKS) k_backward_secon
   secondary_block(s, op, tape_tri, tape_bary, d_image, gr, G, rows_written, blockIdx.x);
 }
 
+// kInPass: the secondary edge samples are evaluated inside this pass (no
+// scratch for the queue); else their vertex adjoints come in dp_sec.
+template <bool kInPass>
 __device__ __forceinline__ void path_block(const SceneView& s, const Opts& op, const int32_t* tape_tri,
                                            const float2* tape_bary, const float* d_image, Grads gr, int G,
                                            const float* dp_sec, int64_t blk) {
@@ -1211,10 +1215,10 @@ __device__ __forceinline__ void path_block(const SceneView& s, const Opts& op, c
           }
         }
         if (do_sec) {
-          if (dp_sec)  // evaluated apart (queued samples only)
-            dp += ld3(dp_sec + 3 * (ti * md + b));
-          else
+          if (kInPass)
             secondary_at_vertex(s, op, (uint32_t)pix, (uint32_t)sidx, b, md, x, n, alb, ab, Le, dp, so);
+          else if (dp_sec)  // evaluated apart (queued samples only)
+            dp += ld3(dp_sec + 3 * (ti * md + b));
         }
         for (int i = 0; i < kGlobals; ++i) g[i] += gl[i];
         float3 do_, dd_;
@@ -1239,10 +1243,15 @@ __device__ __forceinline__ void path_block(const SceneView& s, const Opts& op, c
   cache_flush(ca, gr.albedo);
   block_globals(g, gr.partials + blk * kGlobals, false);
 }
+__global__ void __launch_bounds__(kBlock, 1)
+    k_backward_path_in_pass(SceneView s, Opts op, const int32_t* tape_tri, const float2* tape_bary,
+                            const float* d_image, Grads gr, int G) {
+  path_block<true>(s, op, tape_tri, tape_bary, d_image, gr, G, nullptr, blockIdx.x);
+}
 __global__ void __launch_bounds__(kBlock, DRT_PATH_MIN_BLOCKS)
     k_backward_path(SceneView s, Opts op, const int32_t* tape_tri, const float2* tape_bary, const float* d_image,
                     Grads gr, int G, const float* dp_sec) {
-  path_block(s, op, tape_tri, tape_bary, d_image, gr, G, dp_sec, blockIdx.x);
+  path_block<false>(s, op, tape_tri, tape_bary, d_image, gr, G, dp_sec, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1647,7 +1656,8 @@ __global__ void __launch_bounds__(kBlock, PhaseMinBlocks<PH>::value)
         secondary_block(sb.v, sb.op, sb.tape_tri, sb.tape_bary, sb.d_image,
                         Grads{sb.d_verts, sb.d_albedo, sb.partials}, sb.G, sb.rows_written, blk);
       } else if (PH == kPhasePath) {
-        path_block(sb.v, sb.op, sb.tape_tri, sb.tape_bary, sb.d_image, Grads{sb.d_verts, sb.d_albedo, sb.partials},
+        path_block<false>(sb.v, sb.op, sb.tape_tri, sb.tape_bary, sb.d_image,
+                          Grads{sb.d_verts, sb.d_albedo, sb.partials},
                    sb.G, sb.dp_sec, blk);
       } else {
         primary_block(sb.v, sb.op, sb.d_image, Grads{sb.d_verts, sb.d_albedo, sb.partials + sb.rows_i * kGlobals},
@@ -1885,7 +1895,10 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
   if (path && need_i) {
     s.counters = counter_slot(kSlotBwdInterior);
     ProfToken pt = prof_begin("backward_path", st);
-    k_backward_path<<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tt, tb, d_image, gr, G, dps);
+    if (apart || !sec)
+      k_backward_path<<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tt, tb, d_image, gr, G, dps);
+    else
+      k_backward_path_in_pass<<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tt, tb, d_image, gr, G);
     prof_end(pt, st);
   } else if ((op.terms & 1) || apart) {
     s.counters = counter_slot(kSlotBwdInterior);
