@@ -267,7 +267,7 @@ def _make_scene(ctx, kind, seed):
     return sc, s, w
 
 
-def protocol(ctx: drt.Context, *, steps: int = 3000, k_direct: int = 32, k_procedural: int = 24,
+def protocol(ctx: drt.Context, *, steps: int = 6000, k_direct: int = 32, k_procedural: int = 24,
              edge_spp_direct: int = 64, edge_spp_procedural: int = 32) -> dict:
     """Collect, train and evaluate; returns a JSON-ready summary with the
     learned/plain ratio of gradient variance x time per held-out scene and
