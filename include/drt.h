@@ -226,7 +226,9 @@ typedef struct {
 
 typedef struct {
   int32_t ctas_per_sm[5];  /* per pass (render, interior, secondary, path, primary edges):
-                              resident CTAs per SM of its persistent launch */
+                              resident CTAs per SM of its persistent launch (the secondary
+                              pass has no items: a batch queues its secondary edge samples
+                              and traces them per scene) */
   int32_t grid[5];         /* CTAs launched per pass (0: the pass does not run) */
   int32_t chunk[5];        /* work items taken per counter increment */
   int32_t edge_per_thread_mult;  /* primary edge samples per thread, over the single-scene value */

@@ -286,7 +286,6 @@ cudaError_t enqueue(drt_batch* b, cudaStream_t st) {
   }
   if (e == cudaSuccess) e = run_phase(b, drt::kPhasePath, b->d_desc, st);
   if (e == cudaSuccess) e = run_phase(b, drt::kPhaseInterior, b->d_desc, st);
-  if (e == cudaSuccess) e = run_phase(b, drt::kPhaseSecondary, b->d_desc, st);
   if (e == cudaSuccess) e = sort_edges(b, b->d_desc, st);
   if (e == cudaSuccess) e = run_phase(b, drt::kPhasePrimary, b->d_desc, st);
   for (int k = 0; k < b->n && e == cudaSuccess; ++k) {

@@ -143,7 +143,8 @@ struct Opts {
   int64_t edge_begin, edge_end;
 };
 
-// Passes of a batch, in launch order.
+// Passes of a batch, in launch order (a batch queues its secondary edge
+// samples, so its secondary pass has no items).
 enum BatchPhase { kPhaseRender = 0, kPhaseInterior = 1, kPhaseSecondary = 2, kPhasePath = 3, kPhasePrimary = 4,
                   kPhases = 5 };
 

@@ -1652,9 +1652,6 @@ __global__ void __launch_bounds__(kBlock, PhaseMinBlocks<PH>::value)
       } else if (PH == kPhaseInterior) {
         interior_block(sb.v, sb.op, sb.tape_tri, sb.tape_bary, sb.d_image, Grads{sb.d_verts, sb.d_albedo, sb.partials},
                        sb.G, sb.dp_sec, sb.do_int, blk);
-      } else if (PH == kPhaseSecondary) {
-        secondary_block(sb.v, sb.op, sb.tape_tri, sb.tape_bary, sb.d_image,
-                        Grads{sb.d_verts, sb.d_albedo, sb.partials}, sb.G, sb.rows_written, blk);
       } else if (PH == kPhasePath) {
         path_block<false>(sb.v, sb.op, sb.tape_tri, sb.tape_bary, sb.d_image,
                           Grads{sb.d_verts, sb.d_albedo, sb.partials},
@@ -1745,8 +1742,7 @@ cudaError_t launch_batch_phase(int phase, const BatchScene* bs, const int64_t* p
     switch (phase) {
       case kPhaseRender: e = launch_phase<kPhaseRender>(bs, prefix, n, n_items, grid, chunk, counter, st); break;
       case kPhaseInterior: e = launch_phase<kPhaseInterior>(bs, prefix, n, n_items, grid, chunk, counter, st); break;
-      case kPhaseSecondary:
-        e = launch_phase<kPhaseSecondary>(bs, prefix, n, n_items, grid, chunk, counter, st);
+      case kPhaseSecondary:  // a batch queues its secondary edge samples (launch_secondary_apart)
         break;
       case kPhasePath: e = launch_phase<kPhasePath>(bs, prefix, n, n_items, grid, chunk, counter, st); break;
       default: e = launch_phase<kPhasePrimary>(bs, prefix, n, n_items, grid, chunk, counter, st); break;
@@ -1760,7 +1756,7 @@ int batch_phase_occupancy(int phase) {
   switch (phase) {
     case kPhaseRender: return phase_occupancy<kPhaseRender>();
     case kPhaseInterior: return phase_occupancy<kPhaseInterior>();
-    case kPhaseSecondary: return phase_occupancy<kPhaseSecondary>();
+    case kPhaseSecondary: return 1;
     case kPhasePath: return phase_occupancy<kPhasePath>();
     default: return phase_occupancy<kPhasePrimary>();
   }
