@@ -41,6 +41,9 @@ UNIT = "samples/s"
 W_IMG, H_IMG, SPP, EDGE_SPP = 256, 256, 64, 64
 SCENE_SEED = 1236
 BATCH_SEED, BATCH_SPP = 1238, 16
+# Two triangles per BVH leaf: both timed workloads are direct lighting, whose
+# rays are mostly coherent first-vertex rays (one per leaf suits path tracing).
+BVH_LEAF = 2
 WORKLOAD = ("direct lighting 256x256: jittered icosphere (5120 tris) + 2-tri ground + 2-tri area light; "
             "64 spp with 1 shadow ray, 64 primary edge spp, 1 secondary edge sample per path vertex; "
             "step = vertex update (LBVH + edge CDFs) + render + backward (all gradient terms)")
@@ -141,7 +144,7 @@ def run_batched(ctx, dev, replays=20):
     from paper_1904_12228_gb300 import drt
     from paper_1904_12228_gb300 import scenegen as sg
     scenes = sg.batch_workload(BATCH_SEED)
-    up = [drt.Scene.from_arrays(ctx, sc) for sc in scenes]
+    up = [drt.Scene.from_arrays(ctx, sc, bvh_leaf_size=BVH_LEAF) for sc in scenes]
     d_images = [torch.from_numpy(sg.loss_adjoint(BATCH_SEED + k, sc.width, sc.height)).to(dev)
                 for k, sc in enumerate(scenes)]
     imgs = [torch.zeros((sc.height, sc.width, 3), device=dev) for sc in scenes]
@@ -234,7 +237,7 @@ def cpu_workload_sample(seconds_target, n_threads):
 
 def bench_config(triangles, world):
     return {"workload": WORKLOAD, "width": W_IMG, "height": H_IMG, "spp": SPP, "edge_spp": EDGE_SPP,
-            "triangles": triangles, "l2": "flushed between timed steps (256 MiB write)",
+            "triangles": triangles, "bvh_leaf_size": BVH_LEAF, "l2": "flushed between timed steps (256 MiB write)",
             "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
@@ -297,7 +300,7 @@ def main():
     ctx = drt.Context(local)
     scene_seed, adjoint_seed = replicas.replica_seeds(SCENE_SEED, 1, rank)
     scene = sg.direct_lighting(scene_seed)
-    S = drt.Scene.from_arrays(ctx, scene)
+    S = drt.Scene.from_arrays(ctx, scene, bvh_leaf_size=BVH_LEAF)
     V, T = len(scene.verts), len(scene.tris)
     verts = torch.from_numpy(scene.verts).to(dev)
     d_image = torch.from_numpy(sg.loss_adjoint(adjoint_seed, W_IMG, H_IMG)).to(dev)

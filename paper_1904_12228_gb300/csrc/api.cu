@@ -222,7 +222,7 @@ drt::SceneView drt_scene::view() const {
   v.seg_cdf = seg_n > 0 ? seg_cdf : nullptr; v.seg_edge = seg_edge; v.seg_s = seg_s; v.seg_len = seg_len;
   v.n_seg = (int)std::max<int64_t>(0, seg_n);
   v.V = V; v.T = T; v.L = L; v.E = E; v.W = W; v.H = H; v.cam_type = cam_type;
-  v.root = T > drt::kLeafMax ? 0 : drt::leaf_enc(0, T);
+  v.root = T > leaf_max ? 0 : drt::leaf_enc(0, T);
   return v;
 }
 
@@ -277,6 +277,8 @@ drt_status drt_scene_upload(drt_context* ctx, const drt_scene_desc* d, void* str
   if (d->n_light_tris < 0 || (d->n_light_tris > 0 && !d->light_tris))
     return fail(DRT_ERR_INVALID_ARG, "bad light list");
   if (!(d->cam_scale > 0.0f)) return fail(DRT_ERR_INVALID_ARG, "cam_scale must be > 0");
+  if (d->bvh_leaf_size < 0 || d->bvh_leaf_size > drt::kLeafLimit)
+    return fail(DRT_ERR_INVALID_ARG, "bvh_leaf_size %d outside 0..%d", d->bvh_leaf_size, drt::kLeafLimit);
   cudaStream_t st = (cudaStream_t)stream;
   CUDA_TRY(cudaSetDevice(ctx->device));
   // topology on the host: index validation and the unique edge list
@@ -313,6 +315,7 @@ drt_status drt_scene_upload(drt_context* ctx, const drt_scene_desc* d, void* str
   s->ctx = ctx;
   s->V = d->n_verts; s->T = d->n_tris; s->L = d->n_light_tris; s->E = (int)edges.size();
   s->W = d->width; s->H = d->height; s->cam_type = d->cam_type;
+  s->leaf_max = d->bvh_leaf_size > 0 ? d->bvh_leaf_size : 1;
   int T = s->T, E = s->E;
   int nb = (T + 2047) / 2048;
   s->sort_blocks = nb;

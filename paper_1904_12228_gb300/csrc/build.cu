@@ -406,8 +406,8 @@ __device__ __forceinline__ int delta(const uint32_t* k, int n, int i, int j) {
 
 // Karras (HPG 2012): internal node i covers a key range; its split is the
 // highest differing bit; children are leaves when the range has one key.
-__global__ void k_karras(const uint32_t* keys, int n, float4* nodes, int2* child_orig, int32_t* parent,
-                         int32_t* leaf_parent) {
+__global__ void k_karras(const uint32_t* keys, int n, int leaf_max, float4* nodes, int2* child_orig,
+                         int32_t* parent, int32_t* leaf_parent) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n - 1) return;
   int d = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
@@ -429,10 +429,10 @@ __global__ void k_karras(const uint32_t* keys, int n, float4* nodes, int2* child
   int lo = min(i, j), hi = max(i, j);
   int left = (lo == gamma) ? ~gamma : gamma;
   int right = (hi == gamma + 1) ? ~(gamma + 1) : gamma + 1;
-  // traversal sees a subtree of at most kLeafMax triangles as one leaf range
+  // traversal sees a subtree of at most leaf_max triangles as one leaf range
   int lcount = gamma - lo + 1, rcount = hi - gamma;
-  int left_enc = lcount <= kLeafMax ? leaf_enc(lo, lcount) : left;
-  int right_enc = rcount <= kLeafMax ? leaf_enc(gamma + 1, rcount) : right;
+  int left_enc = lcount <= leaf_max ? leaf_enc(lo, lcount) : left;
+  int right_enc = rcount <= leaf_max ? leaf_enc(gamma + 1, rcount) : right;
   reinterpret_cast<int4*>(nodes)[4 * i + 3] = make_int4(left_enc, right_enc, 0, 0);
   child_orig[i] = make_int2(left, right);
   if (left < 0) leaf_parent[~left] = i; else parent[left] = i;
@@ -847,7 +847,7 @@ cudaError_t build_bvh(drt_scene* s, cudaStream_t st) {
   int32_t* va = alt ? s->vals2 : s->vals;
   if (T > 1) {
     cudaMemsetAsync(s->flags, 0, sizeof(int32_t) * (T - 1), st);
-    DRT_PROF_LAUNCH("karras", st, k_karras<<<(T - 1 + kBlock - 1) / kBlock, kBlock, 0, st>>>(ka, T, s->nodes, s->child_orig, s->parent, s->leaf_parent));
+    DRT_PROF_LAUNCH("karras", st, k_karras<<<(T - 1 + kBlock - 1) / kBlock, kBlock, 0, st>>>(ka, T, s->leaf_max, s->nodes, s->child_orig, s->parent, s->leaf_parent));
   }
   DRT_PROF_LAUNCH("refit", st, k_refit<<<(T + kBlock - 1) / kBlock, kBlock, 0, st>>>(v, va, s->nodes, s->soup, s->child_orig, s->parent, s->leaf_parent, s->flags));
   return cudaGetLastError();

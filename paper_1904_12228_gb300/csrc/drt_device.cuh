@@ -46,9 +46,11 @@ constexpr float kInvPi = 0.318309886f;
 constexpr int kStackSize = 64;
 constexpr int kTraceWarps = 8;  // warps per CTA that the warp-cooperative traversals support
 constexpr float kTile = 16.0f;  // screen tile of the segment split, pixels
-// BVH leaves hold up to kLeafMax consecutive triangles of the leaf-order soup;
-// a leaf child is encoded as ~(first | (count-1) << 28).
-constexpr int kLeafMax = 1;  // measured: 4 costs more triangle tests than it saves in node visits on LBVH leaves
+// BVH leaves hold up to a scene-chosen number (at most kLeafLimit) of
+// consecutive triangles of the leaf-order soup; a leaf child is encoded as
+// ~(first | (count-1) << 28).  One per leaf suits incoherent rays; two cut the
+// node visits of coherent first-vertex rays by more than the extra tests cost.
+constexpr int kLeafLimit = 8;
 __host__ __device__ __forceinline__ int leaf_enc(int first, int count) { return ~(first | ((count - 1) << 28)); }
 // device error-flag codes (mirrors the public enum in drt.h)
 

@@ -40,6 +40,7 @@ struct SortBuffers {
 struct drt_scene {
   drt_context* ctx = nullptr;
   int V = 0, T = 0, L = 0, E = 0, W = 0, H = 0, cam_type = 0;
+  int leaf_max = 1;          // most triangles per BVH leaf range (1..kLeafLimit)
   uint64_t generation = 0;   // bumped on every update; tapes remember it
   // parameters (library copies)
   float *verts = nullptr, *albedo = nullptr, *radiance = nullptr, *cam = nullptr, *cam_scale = nullptr;

@@ -41,7 +41,7 @@ class SceneDesc(ctypes.Structure):
                 ("n_tris", ctypes.c_int32), ("albedo", ctypes.c_void_p), ("light_tris", ctypes.c_void_p),
                 ("n_light_tris", ctypes.c_int32), ("radiance", ctypes.c_void_p), ("cam_to_world", ctypes.c_void_p),
                 ("cam_scale", ctypes.c_float), ("cam_type", ctypes.c_int32), ("width", ctypes.c_int32),
-                ("height", ctypes.c_int32)]
+                ("height", ctypes.c_int32), ("bvh_leaf_size", ctypes.c_int32)]
 
 
 class RenderOpts(ctypes.Structure):
@@ -283,23 +283,23 @@ class Scene:
     """An uploaded scene.  ``arrays`` are kept alive until the upload returns."""
 
     def __init__(self, ctx: Context, verts, tris, albedo, light_tris, radiance, cam_to_world, cam_scale, cam_type,
-                 width, height, stream=None):
+                 width, height, stream=None, bvh_leaf_size=0):
         self.ctx = ctx
         self.n_verts, self.n_tris = int(verts.shape[0]), int(tris.shape[0])
         self.width, self.height = int(width), int(height)
         nl = int(light_tris.shape[0]) if light_tris is not None else 0
         desc = SceneDesc(_ptr(verts), self.n_verts, _ptr(tris), self.n_tris, _ptr(albedo),
                          _ptr(light_tris) if nl else None, nl, _ptr(radiance), _ptr(cam_to_world),
-                         float(cam_scale), int(cam_type), self.width, self.height)
+                         float(cam_scale), int(cam_type), self.width, self.height, int(bvh_leaf_size))
         h = ctypes.c_void_p()
         _check(ctx.lib.drt_scene_upload(ctx.handle, ctypes.byref(desc), _stream(stream), ctypes.byref(h)))
         self.handle = h
 
     @classmethod
-    def from_arrays(cls, ctx, sc, stream=None):
+    def from_arrays(cls, ctx, sc, stream=None, bvh_leaf_size=0):
         """Upload a ``scenegen.Scene`` (host numpy arrays)."""
         return cls(ctx, sc.verts, sc.tris, sc.albedo, sc.light_tris, sc.radiance, sc.cam_to_world, sc.cam_scale,
-                   sc.cam_type, sc.width, sc.height, stream)
+                   sc.cam_type, sc.width, sc.height, stream, bvh_leaf_size)
 
     def update_vertices(self, verts, stream=None):
         _check(self.ctx.lib.drt_scene_update_vertices(self.ctx.handle, self.handle, _ptr(verts), _stream(stream)))
