@@ -48,7 +48,7 @@ class _Opts(ctypes.Structure):
                 ("terms", ctypes.c_int32), ("pix_begin", ctypes.c_int32), ("pix_end", ctypes.c_int32),
                 ("edge_begin", ctypes.c_int64), ("edge_end", ctypes.c_int64), ("n_threads", ctypes.c_int32),
                 ("scene_id", ctypes.c_int32), ("proposal", ctypes.c_int32), ("seg_weights", ctypes.c_void_p),
-                ("n_seg_weights", ctypes.c_int64)]
+                ("n_seg_weights", ctypes.c_int64), ("sec_sampler", ctypes.c_int32), ("sec_tree_samples", ctypes.c_int32)]
 
 
 def lib():
@@ -76,13 +76,14 @@ class _Pinned:
 
 
 def _opts(spp, edge_spp, max_depth, primary_only, seed, eps_rel, terms, pixels, edges, n_threads, scene_id,
-          weights=None, mode=1):
+          weights=None, mode=1, sec_tree_samples=0):
     pb, pe = pixels if pixels is not None else (0, 0)
     eb, ee = edges if edges is not None else (0, 0)
     wp, wn = (weights.ctypes.data, len(weights)) if weights is not None else (None, 0)
     return _Opts(int(spp), int(edge_spp), int(max_depth), int(bool(primary_only)), int(seed) & (2 ** 64 - 1),
                  float(eps_rel), int(terms), int(pb), int(pe), int(eb), int(ee),
-                 int(n_threads or n_threads_default()), int(scene_id), mode if weights is not None else 0, wp, wn)
+                 int(n_threads or n_threads_default()), int(scene_id), mode if weights is not None else 0, wp, wn,
+                 1 if sec_tree_samples > 0 else 0, int(sec_tree_samples))
 
 
 def num_params(scene) -> int:
@@ -116,14 +117,16 @@ def render(scene, *, spp: int, seed: int, max_depth: int = 1, primary_only: bool
 
 def backward(scene, d_image: np.ndarray, *, spp: int, edge_spp: int, seed: int, max_depth: int = 1,
              primary_only: bool = False, terms: int = TERMS_ALL, eps_rel: float = EPS_REL, pixels=None,
-             edges=None, n_threads=None, scene_id: int = 0, proposal_weights=None, proposal_scores=None):
+             edges=None, n_threads=None, scene_id: int = 0, proposal_weights=None, proposal_scores=None,
+             sec_tree_samples: int = 0):
     """Gradient of sum(d_image * image) as a flat FP64 vector, and per entry
     the magnitude of the terms summed into it (absolute-value chain rule),
     which scales the rounding error an FP32 implementation may make.
     proposal_weights: per tile segment (see segments()), selects the mixture
     proposal for primary edges.  proposal_scores: per tile segment, network
     scores s_k; the mixture then weighs segment k by len_k * exp(s_k), with
-    s_k clamped to [-40, 40]."""
+    s_k clamped to [-40, 40].  sec_tree_samples > 0 picks secondary edges
+    through the edge hierarchy with that many root samples (else by length)."""
     if proposal_weights is not None and proposal_scores is not None:
         raise ValueError("give proposal_weights or proposal_scores, not both")
     P = _Pinned(scene)
@@ -133,7 +136,7 @@ def backward(scene, d_image: np.ndarray, *, spp: int, edge_spp: int, seed: int, 
         mode, pw = 2, proposal_scores
     pw = None if pw is None else np.ascontiguousarray(pw, np.float32)
     o = _opts(spp, edge_spp, max_depth, primary_only, seed, eps_rel, terms, pixels, edges, n_threads, scene_id,
-              pw, mode)
+              pw, mode, sec_tree_samples)
     n = num_params(scene)
     g = np.zeros(n, np.float64)
     a = np.zeros(n, np.float64)
@@ -214,3 +217,54 @@ def sec_edge_forms(p, v0, v1, t, nm, plane_d) -> np.ndarray:
                             arr[3].ctypes.data_as(ctypes.c_void_p), ctypes.c_double(plane_d),
                             out.ctypes.data_as(ctypes.c_void_p))
     return out
+
+
+def edge_tree(scene):
+    """The secondary edge hierarchy: children [n,2] (>= 0 node, < 0 ~leaf
+    position), slots [n,2,14] = (lo, hi, Hough lo, Hough hi, total length,
+    all class B), leaves [E,3] = (edge id, class B, boundary), root code."""
+    P = _Pinned(scene)
+    cap = 3 * len(scene.tris)
+    nodes = np.zeros((cap, 2), np.int32)
+    slots = np.zeros((cap, 2, 14), np.float32)
+    leaves = np.zeros((cap, 3), np.int32)
+    root = ctypes.c_int32()
+    n = lib().or_edge_tree(ctypes.byref(P.s), nodes.ctypes.data_as(ctypes.c_void_p),
+                           slots.ctypes.data_as(ctypes.c_void_p), leaves.ctypes.data_as(ctypes.c_void_p),
+                           ctypes.c_int(cap), ctypes.byref(root))
+    n_edges = len(edges(scene))
+    return nodes[:n], slots[:n], leaves[:n_edges], root.value
+
+
+def edge_tree_vsphere(scene, p) -> np.ndarray:
+    """[n,2] bool: the v-sphere of shading point p clears the slot's Hough box."""
+    P = _Pinned(scene)
+    nodes, _, _, _ = edge_tree(scene)
+    out = np.zeros((max(1, len(nodes)), 2), np.uint8)
+    pa = np.ascontiguousarray(p, np.float32)
+    lib().or_edge_tree_vsphere(ctypes.byref(P.s), pa.ctypes.data_as(ctypes.c_void_p),
+                               out.ctypes.data_as(ctypes.c_void_p))
+    return out[:len(nodes)].astype(bool)
+
+
+def edge_tree_cos_bound(p, n, lo, hi) -> float:
+    arr = [np.ascontiguousarray(x, np.float32) for x in (p, n, lo, hi)]
+    f = lib().or_edge_tree_cos_bound
+    f.restype = ctypes.c_float
+    return float(f(*[a.ctypes.data_as(ctypes.c_void_p) for a in arr]))
+
+
+def edge_tree_picks(scene, p, n, *, last: bool, samples: int, n_picks: int, seed: int = 0, bounce: int = 0,
+                    scene_id: int = 0, eps_rel: float = EPS_REL):
+    """n_picks hierarchical picks at shading point p (unit normal n), with
+    Philox counters (0, i): edge ids (-1: none) and resampling weights."""
+    P = _Pinned(scene)
+    pa = np.ascontiguousarray(p, np.float32)
+    na = np.ascontiguousarray(n, np.float32)
+    eid = np.zeros(n_picks, np.int32)
+    w = np.zeros(n_picks, np.float32)
+    lib().or_edge_tree_picks(ctypes.byref(P.s), pa.ctypes.data_as(ctypes.c_void_p), na.ctypes.data_as(ctypes.c_void_p),
+                             ctypes.c_int(int(last)), ctypes.c_int(samples), ctypes.c_float(eps_rel),
+                             ctypes.c_uint64(int(seed) & (2 ** 64 - 1)), ctypes.c_int(bounce), ctypes.c_int(scene_id),
+                             ctypes.c_int(n_picks), eid.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p))
+    return eid, w

@@ -39,6 +39,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <functional>
 #include <thread>
 #include <vector>
 
@@ -217,6 +218,8 @@ typedef struct {
                                 2: the same with seg_weights read as network scores */
   const float* seg_weights;  /* [n_seg_weights] nonnegative weight per segment (proposal 1) */
   int64_t n_seg_weights;
+  int32_t sec_sampler;       /* secondary edge: 0 by 3D length (Sec. 5.2.2); 1 the edge hierarchy (Sec. 5.3.1) */
+  int32_t sec_tree_samples;  /* samples distributed from the hierarchy's root */
 } or_opts_t;
 }
 
@@ -696,6 +699,8 @@ D3 hit_point_dual(const D3& O, const D3& D, const D3& V0, const D3& V1, const D3
   return O + tau * D;
 }
 
+#include "edge_tree.h"
+
 struct Ctx {
   const Prep* P;
   const or_opts_t* opt;
@@ -703,6 +708,7 @@ struct Ctx {
   const float* w;        /* d_image [H,W,3] (backward) */
   double* g;             /* gradient accumulator [P] */
   double* ga;            /* sum of |contribution| per parameter [P] */
+  const EdgeTree* tree = nullptr;  /* secondary edge hierarchy (sec_sampler 1) */
 };
 
 /* grad += coef * x';  tolerance scale += coef_abs * |x|' (see Dual). */
@@ -750,22 +756,34 @@ void light_point(const Prep& P, int j, float r1, float r2, bool track, float y32
  *  indirect part (solid-angle measure, matching cosine-sampled continuation):
  *     sign_s * f_r cos_p L_r,s / |omega|^2 * d alpha_dir/d theta,
  *     alpha_dir = omega_hat.(v0-p)x(v1-p) with omega_hat held fixed.
- * Everything is divided by P(E) = |E| / total length.                         */
+ * Everything is divided by P(E) = |E| / total length, or, with the edge
+ * hierarchy (Sec. 5.3.1), multiplied by the pick's resampling weight.      */
 void path_radiance(Ctx& C, int depth0, int max_depth, const float o32_in[3], const float d32_in[3],
                    const D3& O_in, const D3& D_in, int exclude_in, bool emission_first, uint32_t c0, uint32_t c1,
                    uint32_t pass, const double wscale[3], const double beta_in[3], bool backward, RGB* out);
 
 void secondary_edge(Ctx& C, int b, uint32_t c0, uint32_t c1, uint32_t pass, const float p32[3], const D3& Pd,
-                    V3 ns, int k, const double albedo_k[3], const double beta[3],
+                    V3 ns, const float ns32[3], int k, const double albedo_k[3], const double beta[3],
                     const double wscale[3], int max_depth) {
   const Prep& P = *C.P;
   if (P.stotal <= 0.0) return;
   uint32_t r[4];
   rng(C.opt->seed, c0, c1, K_EDGE_SECONDARY, (uint32_t)b, pass, (uint32_t)C.opt->scene_id, r);
-  int e = cdf_pick(P.scdf, u01d(r[0], r[1]) * P.stotal);
-  double le = P.scdf[e] - (e > 0 ? P.scdf[e - 1] : 0.0);
-  if (le <= 0.0) return;
-  double inv_pe = P.stotal / le;
+  int e;
+  double inv_pe;
+  if (C.opt->sec_sampler == 1) {
+    ETQuery q = et_query(*C.tree, p32, ns32, b + 1 >= max_depth, C.opt->eps_rel);
+    float wgt;
+    if (!et_pick(*C.tree, q, C.opt->sec_tree_samples, C.opt->seed, c0, c1, (uint32_t)b,
+                 (uint32_t)C.opt->scene_id, &e, &wgt))
+      return;
+    inv_pe = (double)wgt;
+  } else {
+    e = cdf_pick(P.scdf, u01d(r[0], r[1]) * P.stotal);
+    double le = P.scdf[e] - (e > 0 ? P.scdf[e - 1] : 0.0);
+    if (le <= 0.0) return;
+    inv_pe = P.stotal / le;
+  }
   float t = u01f(r[2]);
   const float *v0 = vtx(P, P.e0[e]), *v1 = vtx(P, P.e1[e]);
   float om[3], a0[3], a1[3];
@@ -939,15 +957,15 @@ void path_radiance(Ctx& C, int depth0, int max_depth, const float o32_in[3], con
         }
       }
     }
-    if (backward && (op.terms & 4)) {
-      double albv[3] = {sc.albedo[3 * k], sc.albedo[3 * k + 1], sc.albedo[3 * k + 2]};
-      secondary_edge(C, b, c0, c1, pass, p32, Pd, val(ns), k, albv, betav, wscale, max_depth);
-    }
-    if (b + 1 >= max_depth) break;
-    /* continuation: cosine-weighted direction, world direction held fixed */
     float nl32 = std::sqrt(dot32(nu32, nu32));
     float fl = side > 0.0f ? -1.0f : 1.0f;
     float ns32[3] = {fl * (nu32[0] / nl32), fl * (nu32[1] / nl32), fl * (nu32[2] / nl32)};
+    if (backward && (op.terms & 4)) {
+      double albv[3] = {sc.albedo[3 * k], sc.albedo[3 * k + 1], sc.albedo[3 * k + 2]};
+      secondary_edge(C, b, c0, c1, pass, p32, Pd, val(ns), ns32, k, albv, betav, wscale, max_depth);
+    }
+    if (b + 1 >= max_depth) break;
+    /* continuation: cosine-weighted direction, world direction held fixed */
     uint32_t r[4];
     rng(op.seed, c0, c1, K_BSDF, (uint32_t)b, pass, (uint32_t)op.scene_id, r);
     float nd[3];
@@ -1102,6 +1120,77 @@ int or_edges(const or_scene_t* sc, int32_t* out, int cap) {
   for (int e = 0; e < E && e < cap; ++e) { out[2 * e] = P.e0[e]; out[2 * e + 1] = P.e1[e]; }
   return E;
 }
+/* Secondary edge hierarchy (Sec. 5.3.1), for the tests.
+ * nodes [n_nodes, 2] children (>= 0 node, < 0 ~leaf position); slots
+ * [n_nodes, 2, 14] = (lo[3], hi[3], hlo[3], hhi[3], L, allB); leaves [E, 3] =
+ * (edge id, class B, boundary).  Returns the node count (writes at most cap)
+ * and the root code in *root. */
+int or_edge_tree(const or_scene_t* sc, int32_t* nodes, float* slots, int32_t* leaves, int cap, int32_t* root) {
+  Prep P;
+  prepare(sc, P);
+  EdgeTree T;
+  build_edge_tree(P, T);
+  int n = (int)T.node.size();
+  for (int i = 0; i < n && i < cap; ++i)
+    for (int c = 0; c < 2; ++c) {
+      nodes[2 * i + c] = T.node[i].child[c];
+      const ETSlot& s = T.node[i].slot[c];
+      float* o = slots + 28 * i + 14 * c;
+      for (int k = 0; k < 3; ++k) { o[k] = s.lo[k]; o[3 + k] = s.hi[k]; o[6 + k] = s.hlo[k]; o[9 + k] = s.hhi[k]; }
+      o[12] = s.L;
+      o[13] = s.allB ? 1.0f : 0.0f;
+    }
+  for (size_t i = 0; i < T.leaf.size(); ++i) {
+    leaves[3 * i] = T.leaf[i].eid;
+    leaves[3 * i + 1] = T.leaf[i].classB;
+    leaves[3 * i + 2] = T.leaf[i].boundary;
+  }
+  *root = T.root;
+  return n;
+}
+
+/* For a shading point p: per node and child slot, 1 if the slot holds only
+ * class-B edges and the v-sphere clears its Hough box. */
+void or_edge_tree_vsphere(const or_scene_t* sc, const float* p, uint8_t* out) {
+  Prep P;
+  prepare(sc, P);
+  EdgeTree T;
+  build_edge_tree(P, T);
+  float n[3] = {0.0f, 0.0f, 1.0f};
+  ETQuery q = et_query(T, p, n, true, 0.0f);
+  for (size_t i = 0; i < T.node.size(); ++i)
+    for (int c = 0; c < 2; ++c)
+      out[2 * i + c] = T.node[i].slot[c].allB && et_vsphere_clears(q, T.node[i].slot[c]);
+}
+
+/* Upper bound of the cosine over a box seen from p with unit normal n. */
+float or_edge_tree_cos_bound(const float* p, const float* n, const float* lo, const float* hi) {
+  EdgeTree T;
+  for (int i = 0; i < 3; ++i) T.O[i] = 0.0f;
+  ETQuery q = et_query(T, p, n, false, 0.0f);
+  return et_cos_bound(q, lo, hi);
+}
+
+/* N picks at one shading point with counters (0, i): edge ids and weights
+ * (-1 and 0 where no edge was picked). */
+void or_edge_tree_picks(const or_scene_t* sc, const float* p, const float* n, int last, int S, float eps,
+                        uint64_t seed, int bounce, int scene_id, int N, int32_t* eid, float* w) {
+  Prep P;
+  prepare(sc, P);
+  EdgeTree T;
+  build_edge_tree(P, T);
+  ETQuery q = et_query(T, p, n, last != 0, eps);
+  for (int i = 0; i < N; ++i) {
+    int e;
+    float x;
+    if (et_pick(T, q, S, seed, 0u, (uint32_t)i, (uint32_t)bounce, (uint32_t)scene_id, &e, &x)) {
+      eid[i] = e; w[i] = x;
+    } else {
+      eid[i] = -1; w[i] = 0.0f;
+    }
+  }
+}
+
 /* Primary edge table [E,7] = (ax, ay, bx, by, t0, t1, clipped length). */
 int or_primary_edges(const or_scene_t* sc, double* out, int cap) {
   Prep P;
@@ -1168,10 +1257,12 @@ int or_backward(const or_scene_t* sc, const or_opts_t* op, const float* d_image,
   std::vector<std::vector<double>> g(nt, std::vector<double>(NP, 0.0)), ga(nt, std::vector<double>(NP, 0.0));
   g_dual_overflow = false;
   int npix = sc->width * sc->height;
+  EdgeTree tree;
+  if (op->sec_sampler == 1) build_edge_tree(P, tree);
   if (op->terms & 5) {
     int pb = op->pix_begin, pe = op->pix_end > 0 ? op->pix_end : npix;
     parallel_for(pb, pe, nt, [&](int tid, int64_t b, int64_t e) {
-      Ctx C{&P, op, true, d_image, g[tid].data(), ga[tid].data()};
+      Ctx C{&P, op, true, d_image, g[tid].data(), ga[tid].data(), &tree};
       for (int64_t pix = b; pix < e; ++pix) {
         const float* w = d_image + 3 * pix;
         double ws[3] = {w[0] / (double)op->spp, w[1] / (double)op->spp, w[2] / (double)op->spp};
