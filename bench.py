@@ -15,7 +15,9 @@ edge proposal against the plain edge sampler, comes from the proposal
 module's protocol (train on logs of 20 scenes, score 4 held-out scenes) and
 is reported under "variance_x_time" (N=1; --no-proposal skips it).  The
 64-scene batched workload (persistent launches in a CUDA graph) is reported
-under "batched" (N=1; --no-batched skips it).
+under "batched" (N=1; --no-batched skips it).  The secondary-edge hierarchy
+(Sec. 5.3.1) against 3D length sampling, as gradient variance x time, is
+reported under "secondary_hierarchy" (N=1; --no-hierarchy skips it).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -203,6 +205,62 @@ def run_batched(ctx, dev, replays=20):
             "first_run_s": first_s, "launch_shapes": inf, "l2": "working set larger than L2 (no flush)"}
 
 
+def run_secondary_hierarchy(ctx, dev, K=24, samples=16):
+    """Secondary edge term (Sec. 5.2.2): the 3D length sampler against the edge
+    hierarchy of Sec. 5.3.1 (`samples` root samples), as gradient variance x
+    time.  Per scene, K runs with independent seeds; each run renders its
+    tape (untimed, shared by both samplers), re-uploads the vertices (so the
+    hierarchy is rebuilt inside the timed backward, as in an optimisation
+    step) and times the backward pass of the secondary term alone.  Variance:
+    mean over vertex entries of the run variance, over the mean squared
+    gradient; z2: mean squared z-score of the difference of the two mean
+    gradients (about 1 when both estimate the same term)."""
+    import numpy as np
+    import torch
+    from paper_1904_12228_gb300 import drt
+    from paper_1904_12228_gb300 import scenegen as sg
+    out = []
+    cases = (("direct lighting 256x256, 5124 tris, 64 spp", sg.direct_lighting(SCENE_SEED), 1, 64, 2),
+             ("procedural 512x512, 200k tris, depth 3, 32 spp", sg.procedural(1237), 3, 32, 1))
+    for name, sc, depth, spp, leaf in cases:
+        S = drt.Scene.from_arrays(ctx, sc, bvh_leaf_size=leaf)
+        verts = torch.from_numpy(sc.verts).to(dev)
+        w = torch.from_numpy(sg.loss_adjoint(SCENE_SEED, sc.width, sc.height)).to(dev)
+        img = torch.zeros((sc.height, sc.width, 3), device=dev)
+        res = {}
+        for label, tree in (("length", 0), ("hierarchy", samples)):
+            runs = torch.zeros((K, 3 * len(sc.verts)), device=dev)
+            times = []
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for k in range(-2, K):  # two warm-up runs
+                o = drt.make_opts(spp, 0, max_depth=depth, seed=7000 + k, terms=4, sec_tree_samples=tree)
+                tape = S.render(img, o, want_tape=True)
+                S.update_vertices(verts)
+                dv = runs[max(k, 0)].view(-1, 3)
+                dv.zero_()
+                e0.record()
+                S.backward(w, o, tape=tape, d_verts=dv)
+                e1.record()
+                e1.synchronize()
+                if k >= 0:
+                    times.append(e0.elapsed_time(e1))
+            res[label] = (runs.double().cpu().numpy(), float(np.median(times)))
+        (ra, ta), (rb, tb) = res["length"], res["hierarchy"]
+        norm = float((((ra.mean(0) + rb.mean(0)) * 0.5) ** 2).mean()) or 1.0
+        va, vb = float(ra.var(0, ddof=1).mean() / norm), float(rb.var(0, ddof=1).mean() / norm)
+        se2 = ra.var(0, ddof=1) / K + rb.var(0, ddof=1) / K
+        ok = se2 > 0
+        z2 = float(np.mean((ra.mean(0)[ok] - rb.mean(0)[ok]) ** 2 / se2[ok])) if ok.any() else 0.0
+        out.append({"scene": name, "triangles": len(sc.tris), "max_depth": depth, "spp": spp, "runs": K,
+                    "var_length": va, "var_hierarchy": vb, "ms_length": ta, "ms_hierarchy": tb,
+                    "ratio": (vb * tb) / max(va * ta, 1e-30), "mean_z2": z2})
+        S.free()
+    geo = float(np.exp(np.mean([np.log(max(o["ratio"], 1e-30)) for o in out])))
+    return {"ratio_geomean": geo, "root_samples": samples,
+            "ratio_unit": "hierarchy/length secondary-edge gradient variance x time (<1: hierarchy wins)",
+            "scenes": out}
+
+
 def cpu_workload_sample(seconds_target, n_threads):
     """Time the CPU oracle on a bounded sample of the same workload: a block
     of pixels (all spp, interior + secondary edges) and a proportional range
@@ -278,6 +336,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal variance x time part")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-scene batched workload")
+    ap.add_argument("--no-hierarchy", action="store_true",
+                    help="skip the secondary-edge hierarchy against length sampling comparison")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     from paper_1904_12228_gb300 import replicas
@@ -406,6 +466,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_batched:
         batched = run_batched(ctx, dev)
 
+    sec_h = None
+    if rank == 0 and world == 1 and not args.no_hierarchy:
+        sec_h = run_secondary_hierarchy(ctx, dev)
+
     vxt = None
     if rank == 0 and world == 1 and not args.no_proposal:
         from paper_1904_12228_gb300 import proposal
@@ -424,6 +488,7 @@ def main():
                 "config": bench_config(T, world),
                 "rays_per_s": world * rays / (ms_per_step / 1e3),
                 "roofline": roof, "cpu_baseline": cpu, "variance_x_time": vxt, "batched": batched,
+                "secondary_hierarchy": sec_h,
                 "e2e": {"value": replicas.aggregate_throughput(n_samples, world, e2e_ms), "unit": UNIT,
                         "ms_per_step": e2e_ms,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

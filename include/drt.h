@@ -116,6 +116,18 @@ typedef struct {
   int32_t scene_id;     /* >= 0: fourth word of every Philox counter.  A batch (drt_batch_*)
                            gives scene k of the batch scene_id k, so a single-scene call
                            with scene_id k reproduces it; 0 otherwise */
+  int32_t sec_sampler;  /* secondary edge selection at a shading vertex: 0 by 3D edge length
+                           (Sec. 5.2.2); 1 through the edge hierarchy of Sec. 5.3.1 (camera-
+                           silhouette edges by 3D position, the rest by position and the Hough
+                           points of their face planes; v-sphere culling of non-silhouettes at
+                           the last vertex; importance length x cosine bound / distance;
+                           samples split between children, one edge kept by weighted
+                           reservoir sampling and weighted by its resampling weight).  The
+                           hierarchy is built on the backward call's stream when the scene is
+                           new or changed (device memory about 200 bytes per edge).  A batch
+                           takes 0 only. */
+  int32_t sec_tree_samples;  /* sec_sampler 1: samples distributed from the root, 1..64;
+                                0 selects 16 */
 } drt_render_opts;
 
 /* Gradient outputs: device or host arrays, each may be NULL (not wanted).

@@ -14,6 +14,7 @@
 #include <climits>
 
 #include "drt_internal.h"
+#include "edge_tree.cuh"
 
 namespace {
 
@@ -128,7 +129,9 @@ void free_scene_buffers(drt_scene* s) {
                   s->flags, s->child_orig, s->hist, s->hist_tmp, s->bounds, s->partials, s->esort.keys, s->esort.keys2,
                   s->esort.hist, s->esort.hist_tmp, s->esort.vals, s->esort.vals2, s->seg_edge, s->seg_tile,
                   s->seg_count, s->seg_scan_tmp, s->seg_s, s->seg_len, s->seg_a, s->seg_b, s->seg_cdf, s->seg_tmp,
-                  s->sec.dp, s->sec.queue, s->sec.count, s->pguide, s->sguide};
+                  s->sec.dp, s->sec.queue, s->sec.count, s->sec.pick, s->pguide, s->sguide, s->edge_opp,
+                  s->et_nodes, s->et_leaf, s->et_keys, s->et_keys2, s->et_hist, s->et_hist_tmp, s->et_vals,
+                  s->et_vals2, s->et_parent, s->et_leaf_parent, s->et_flags, s->et_child};
   for (void* b : bufs) dfree(b);
 }
 
@@ -150,6 +153,11 @@ drt_status make_opts(const drt_render_opts* o, drt::Opts* op) {
   if (o->scene_id < 0) return fail(DRT_ERR_INVALID_ARG, "scene_id must be >= 0");
   op->scene_id = (uint32_t)o->scene_id;
   op->eps_rel = o->eps_rel > 0.0f ? o->eps_rel : 1.52587890625e-05f;
+  if (o->sec_sampler < 0 || o->sec_sampler > 1) return fail(DRT_ERR_INVALID_ARG, "sec_sampler must be 0 or 1");
+  if (o->sec_tree_samples < 0 || o->sec_tree_samples > drt::kEtMaxSamples)
+    return fail(DRT_ERR_INVALID_ARG, "sec_tree_samples must be in [0,%d]", drt::kEtMaxSamples);
+  op->sec_sampler = o->sec_sampler;
+  op->sec_samples = o->sec_tree_samples > 0 ? o->sec_tree_samples : drt::kEtDefaultSamples;
   // DRT_DEBUG_RANGES="pix_begin,pix_end,edge_begin,edge_end" restricts which
   // samples the backward pass evaluates (for bisecting against the oracle)
   op->pix_begin = 0;
@@ -162,6 +170,44 @@ drt_status make_opts(const drt_render_opts* o, drt::Opts* op) {
       op->pix_begin = (int)a; op->pix_end = (int)b; op->edge_begin = c; op->edge_end = d;
     }
   }
+  return DRT_OK;
+}
+
+// Secondary edge hierarchy for the scene's current state: allocated on first
+// use (unless alloc is false), rebuilt on the stream when the scene changed.
+drt_status ensure_edge_tree(drt_scene* s, bool alloc, cudaStream_t st) {
+  int E = s->E;
+  if (E <= 0) return DRT_OK;
+  if (!s->et_leaf) {
+    if (!alloc) return fail(DRT_ERR_STATE, "the edge hierarchy is not allocated (run one backward with it first)");
+    drt_status a = DRT_OK;
+    size_t n = (size_t)E, m = (size_t)std::max(1, E - 1);
+    if (a == DRT_OK) a = dalloc_n(&s->et_nodes, drt::kEtNodeF4 * m);
+    if (a == DRT_OK) a = dalloc_n(&s->et_leaf, drt::kEtLeafF4 * n);
+    if (a == DRT_OK) a = dalloc_n(&s->et_keys, n);
+    if (a == DRT_OK) a = dalloc_n(&s->et_keys2, n);
+    if (a == DRT_OK) a = dalloc_n(&s->et_vals, n);
+    if (a == DRT_OK) a = dalloc_n(&s->et_vals2, n);
+    if (a == DRT_OK) a = dalloc_n(&s->et_hist, drt::radix_hist_entries(E));
+    if (a == DRT_OK) a = dalloc_n(&s->et_hist_tmp, drt::radix_hist_tmp_entries(E));
+    if (a == DRT_OK) a = dalloc_n(&s->et_child, m);
+    if (a == DRT_OK) a = dalloc_n(&s->et_parent, m);
+    if (a == DRT_OK) a = dalloc_n(&s->et_leaf_parent, n);
+    if (a == DRT_OK) a = dalloc_n(&s->et_flags, m);
+    if (a != DRT_OK) {
+      void* bufs[] = {s->et_nodes, s->et_leaf, s->et_keys, s->et_keys2, s->et_vals, s->et_vals2, s->et_hist,
+                      s->et_hist_tmp, s->et_child, s->et_parent, s->et_leaf_parent, s->et_flags};
+      for (void* b : bufs) dfree(b);
+      s->et_nodes = s->et_leaf = nullptr;
+      s->et_keys = s->et_keys2 = s->et_hist = s->et_hist_tmp = nullptr;
+      s->et_vals = s->et_vals2 = s->et_parent = s->et_leaf_parent = s->et_flags = nullptr;
+      s->et_child = nullptr;
+      return a;
+    }
+  }
+  if (s->et_generation == s->generation) return DRT_OK;
+  CUDA_TRY(drt::build_edge_tree(s, st));
+  s->et_generation = s->generation;
   return DRT_OK;
 }
 
@@ -223,6 +269,9 @@ drt::SceneView drt_scene::view() const {
   v.n_seg = (int)std::max<int64_t>(0, seg_n);
   v.V = V; v.T = T; v.L = L; v.E = E; v.W = W; v.H = H; v.cam_type = cam_type;
   v.root = T > leaf_max ? 0 : drt::leaf_enc(0, T);
+  v.et_nodes = et_nodes;
+  v.et_leaf = et_leaf;
+  v.et_root = (et_leaf && et_generation == generation && E > 0) ? (E >= 2 ? 0 : ~0) : -1;
   return v;
 }
 
@@ -302,12 +351,22 @@ drt_status drt_scene_upload(drt_context* ctx, const drt_scene_desc* d, void* str
       half[3 * t + k] = {((uint64_t)std::min(a, b) << 32) | std::max(a, b), t};
     }
   std::sort(half.begin(), half.end());
-  std::vector<int2> edges, edge_faces;
+  std::vector<int2> edges, edge_faces, edge_opp;
+  auto third = [&](int t, int a, int b) {
+    int v = tris[3 * (size_t)t];
+    for (int k = 0; k < 3; ++k)
+      if (tris[3 * (size_t)t + k] != a && tris[3 * (size_t)t + k] != b) v = tris[3 * (size_t)t + k];
+    return v;
+  };
   for (size_t i = 0; i < half.size();) {
     size_t j = i;
     while (j < half.size() && half[j].first == half[i].first) ++j;
-    edges.push_back(make_int2((int)(half[i].first >> 32), (int)(half[i].first & 0xffffffffu)));
+    int a = (int)(half[i].first >> 32), b = (int)(half[i].first & 0xffffffffu);
+    edges.push_back(make_int2(a, b));
     edge_faces.push_back(make_int2(half[i].second, j - i > 1 ? half[i + 1].second : -1));
+    // the edge hierarchy compares exactly two faces (first in triangle order)
+    edge_opp.push_back(j - i == 2 ? make_int2(third(half[i].second, a, b), third(half[i + 1].second, a, b))
+                                  : make_int2(-1, -1));
     i = j;
   }
 
@@ -326,7 +385,7 @@ drt_status drt_scene_upload(drt_context* ctx, const drt_scene_desc* d, void* str
   ALLOC(cam_scale, 1) ALLOC(tris, 3 * (size_t)T) ALLOC(light_tris, std::max(1, s->L)) ALLOC(light_of_tri, T)
   ALLOC(w2c, 12) ALLOC(light_cdf, std::max(1, s->L)) ALLOC(light_area, std::max(1, s->L)) ALLOC(light_box, 8)
   ALLOC(nodes, 4 * (size_t)std::max(1, T - 1)) ALLOC(soup, 3 * (size_t)T) ALLOC(edges, std::max(1, E))
-  ALLOC(edge_faces, std::max(1, E))
+  ALLOC(edge_faces, std::max(1, E)) ALLOC(edge_opp, std::max(1, E))
   ALLOC(tile_w, (size_t)((s->W + 15) / 16) * ((s->H + 15) / 16) + 1)
   ALLOC(pedge, 8 * (size_t)std::max(1, E)) ALLOC(plen, std::max(1, E)) ALLOC(pcdf, std::max(1, E))
   ALLOC(slen, std::max(1, E)) ALLOC(scdf, std::max(1, E)) ALLOC(scan_tmp, std::max(1, E / 1024 + 2))
@@ -354,6 +413,7 @@ drt_status drt_scene_upload(drt_context* ctx, const drt_scene_desc* d, void* str
   cp(s->light_of_tri, light_of.data(), 4 * (size_t)T);
   if (E > 0) cp(s->edges, edges.data(), sizeof(int2) * (size_t)E);
   if (E > 0) cp(s->edge_faces, edge_faces.data(), sizeof(int2) * (size_t)E);
+  if (E > 0) cp(s->edge_opp, edge_opp.data(), sizeof(int2) * (size_t)E);
   // host vectors above are read by the copies; wait before they go away
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = drt::check_finite(s, st);
@@ -532,6 +592,13 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
     }
     sort = &s->esort;
   }
+  if (op.sec_sampler == 1 && !op.primary_only && (op.terms & 4) && s->E > 0 && s->L > 0) {
+    drt_status a = ensure_edge_tree(s, true, st);
+    if (a != DRT_OK) {
+      unstage(sg, 6, st);
+      return a;
+    }
+  }
   // secondary edge samples that need rays are queued and traced apart
   const drt::SecScratch* secs = nullptr;
   if (!op.primary_only && (op.terms & 4) && s->E > 0 && s->L > 0) {
@@ -542,6 +609,7 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
       dfree(b.dp);
       dfree(b.queue);
       dfree(b.count);
+      dfree(b.pick);
       b = drt::SecScratch();
       drt_status a = dalloc_n(&b.dp, 3 * (size_t)cap);
       if (a == DRT_OK) a = dalloc_n(&b.queue, (size_t)cap);
@@ -551,6 +619,18 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
         return a;
       }
       b.cap = cap;
+    }
+    if (op.sec_sampler == 1 && cap > s->sec.pick_cap) {
+      cudaStreamSynchronize(st);
+      dfree(s->sec.pick);
+      s->sec.pick = nullptr;
+      s->sec.pick_cap = 0;
+      drt_status a = dalloc_n(&s->sec.pick, (size_t)cap);
+      if (a != DRT_OK) {
+        unstage(sg, 6, st);
+        return a;
+      }
+      s->sec.pick_cap = cap;
     }
     secs = &s->sec;
   }

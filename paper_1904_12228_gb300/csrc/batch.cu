@@ -393,6 +393,13 @@ drt_status balloc(T** p, size_t n) {
   return drt::device_alloc(reinterpret_cast<void**>(p), std::max<size_t>(1, n) * sizeof(T));
 }
 
+// A run that copies in new vertices changes those scenes: tapes and derived
+// tables built for the old vertices no longer apply.
+void bump_generations(drt_batch* b) {
+  for (const auto& it : b->items)
+    if (it.verts) ++it.scene->generation;
+}
+
 }  // namespace
 
 extern "C" {
@@ -405,6 +412,7 @@ drt_status drt_batch_create(drt_context* ctx, const drt_batch_item* items, int32
   drt::Opts op;
   BATCH_TRY(drt::convert_opts(opts, &op));
   if (op.proposal != 0) return bfail(DRT_ERR_INVALID_ARG, "a batch samples primary edges by length (proposal 0)");
+  if (op.sec_sampler != 0) return bfail(DRT_ERR_INVALID_ARG, "a batch samples secondary edges by length (sec_sampler 0)");
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != ctx->device)
     return bfail(DRT_ERR_STATE, "the context's device must be the current device");
@@ -482,6 +490,7 @@ drt_status drt_batch_run(drt_context* ctx, drt_batch* b, void* stream) {
   if (!b->use_graph) {
     BATCH_CUDA(enqueue(b, st));
     ++b->runs;
+    bump_generations(b);
     return DRT_OK;
   }
   if (!b->exec) {
@@ -502,6 +511,7 @@ drt_status drt_batch_run(drt_context* ctx, drt_batch* b, void* stream) {
   }
   BATCH_CUDA(cudaGraphLaunch(b->exec, st));
   ++b->runs;
+  bump_generations(b);
   return DRT_OK;
 }
 

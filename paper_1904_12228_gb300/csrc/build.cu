@@ -6,13 +6,15 @@
 //
 // Sec. 5.3.1 builds its edge hierarchies with this construction (a radix tree
 // over sorted Morton codes of box centroids); here it serves the ray-casting
-// BVH, which the thesis took from Embree / OptiX Prime.
+// BVH, which the thesis took from Embree / OptiX Prime, and the secondary
+// edge hierarchy (built on demand, edge_tree.cuh).
 #include <climits>
 #include <cstdio>
 
 #include <cuda_bf16.h>
 
 #include "drt_internal.h"
+#include "edge_tree.cuh"
 
 namespace drt {
 namespace {
@@ -433,7 +435,7 @@ __global__ void k_karras(const uint32_t* keys, int n, int leaf_max, float4* node
   int lcount = gamma - lo + 1, rcount = hi - gamma;
   int left_enc = lcount <= leaf_max ? leaf_enc(lo, lcount) : left;
   int right_enc = rcount <= leaf_max ? leaf_enc(gamma + 1, rcount) : right;
-  reinterpret_cast<int4*>(nodes)[4 * i + 3] = make_int4(left_enc, right_enc, 0, 0);
+  if (nodes) reinterpret_cast<int4*>(nodes)[4 * i + 3] = make_int4(left_enc, right_enc, 0, 0);
   child_orig[i] = make_int2(left, right);
   if (left < 0) leaf_parent[~left] = i; else parent[left] = i;
   if (right < 0) leaf_parent[~right] = i; else parent[right] = i;
@@ -745,6 +747,101 @@ __global__ void k_segment_features(SceneView s, const int32_t* seg_edge, const i
   for (int i = 0; i < 32; ++i) x[(size_t)k * 32 + i] = __float2bfloat16_rn(f[i]);
 }
 
+// ---------------------------------------------------------------------------
+// Secondary edge hierarchy (Sec. 5.3.1; layouts and arithmetic in edge_tree.cuh)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void et_frame_of_scene(const SceneView& s, const int* b, float O[3], float blo[3],
+                                                  float bhi[3], float* R) {
+  for (int k = 0; k < 3; ++k) {
+    O[k] = s.cam[4 * k + 3];
+    blo[k] = unord(b[k]);
+    bhi[k] = unord(b[3 + k]);
+  }
+  *R = et_hough_radius(blo, bhi, O);
+}
+
+// One thread per edge: its key (class bit over the Morton code) and id.
+__global__ void k_etree_keys(SceneView s, const int2* opp, const int* b, uint32_t* keys, int32_t* vals) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= s.E) return;
+  float O[3], blo[3], bhi[3], R;
+  et_frame_of_scene(s, b, O, blo, bhi, &R);
+  EtLeafData L;
+  et_leaf_data(s.verts, s.edges[e], opp[e], O, L);
+  keys[e] = et_key(L, blo, bhi, R);
+  vals[e] = e;
+}
+
+__device__ __forceinline__ void et_store_slot(float4* nodes, int node, int c, const float lo[3], const float hi[3],
+                                              const float hlo[3], const float hhi[3], float L, bool allB, int code) {
+  float4* r = nodes + (size_t)kEtNodeF4 * node + 4 * c;
+  r[0] = make_float4(lo[0], lo[1], lo[2], L);
+  r[1] = make_float4(hi[0], hi[1], hi[2], allB ? 1.0f : 0.0f);
+  r[2] = make_float4(hlo[0], hlo[1], hlo[2], __int_as_float(code));
+  r[3] = make_float4(hhi[0], hhi[1], hhi[2], 0.0f);
+}
+
+// One thread per key position: the leaf record, then a bottom-up climb that
+// writes each child's slot into its parent; the second child to arrive at a
+// node merges both slots (left then right, so sums are order-independent of
+// arrival) and continues.
+__global__ void k_etree_refit(SceneView s, const int2* opp, const int32_t* vals, const int2* child,
+                              const int32_t* parent, const int32_t* leaf_parent, int32_t* flags, float4* nodes,
+                              float4* leaf) {
+  int pos = blockIdx.x * blockDim.x + threadIdx.x;
+  int E = s.E;
+  if (pos >= E) return;
+  int e = vals[pos];
+  float O[3];
+  for (int k = 0; k < 3; ++k) O[k] = s.cam[4 * k + 3];
+  EtLeafData L;
+  et_leaf_data(s.verts, s.edges[e], opp[e], O, L);
+  float4* lr = leaf + (size_t)kEtLeafF4 * pos;
+  lr[0] = make_float4(L.v0[0], L.v0[1], L.v0[2], L.len);
+  lr[1] = make_float4(L.v1[0], L.v1[1], L.v1[2], __int_as_float(e));
+  lr[2] = make_float4(L.c0[0], L.c0[1], L.c0[2], __int_as_float((L.boundary ? 1 : 0) | (L.classB ? 2 : 0)));
+  lr[3] = make_float4(L.c1[0], L.c1[1], L.c1[2], 0.0f);
+  if (E == 1) return;
+  float lo[3], hi[3], hlo[3], hhi[3];
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = et_min(L.v0[k], L.v1[k]);
+    hi[k] = et_max(L.v0[k], L.v1[k]);
+    hlo[k] = L.classB ? et_min(L.h0[k], L.h1[k]) : INFINITY;
+    hhi[k] = L.classB ? et_max(L.h0[k], L.h1[k]) : -INFINITY;
+  }
+  float Ls = L.len;
+  bool allB = L.classB;
+  int code = ~pos;
+  int node = leaf_parent[pos];
+  int climb = 0;
+  while (node >= 0) {
+    if (++climb > E) {  // deeper than the tree can be: parent links are broken
+      raise_flag(s.err, DRT_DEV_REFIT_CAP, pos);
+      return;
+    }
+    int2 ch = child[node];
+    int c = ch.x == code ? 0 : 1;
+    et_store_slot(nodes, node, c, lo, hi, hlo, hhi, Ls, allB, code);
+    __threadfence();
+    if (atomicAdd(flags + node, 1) == 0) return;  // the sibling finishes this node
+    __threadfence();
+    const float* a = reinterpret_cast<const float*>(nodes + (size_t)kEtNodeF4 * node);
+    const float* bq = a + 16;
+    float aL = __ldcg(a + 3), bL = __ldcg(bq + 3);
+    bool aB = __ldcg(a + 7) != 0.0f, bB = __ldcg(bq + 7) != 0.0f;
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = et_min(__ldcg(a + k), __ldcg(bq + k));
+      hi[k] = et_max(__ldcg(a + 4 + k), __ldcg(bq + 4 + k));
+      hlo[k] = et_min(__ldcg(a + 8 + k), __ldcg(bq + 8 + k));
+      hhi[k] = et_max(__ldcg(a + 12 + k), __ldcg(bq + 12 + k));
+    }
+    Ls = fa(aL, bL);
+    allB = aB && bB;
+    code = node;
+    node = parent[node];
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_segment_features(const drt_scene* s, const float* d_image, const float* image, void* x,
@@ -881,6 +978,27 @@ cudaError_t build_edge_cdfs(drt_scene* s, cudaStream_t st) {
   unsigned gb = (kGuide + 1 + kBlock - 1) / kBlock;
   DRT_PROF_LAUNCH("cdf_guides", st, k_cdf_guide<<<gb, kBlock, 0, st>>>(s->pcdf, s->E, s->pguide));
   DRT_PROF_LAUNCH("cdf_guides", st, k_cdf_guide<<<gb, kBlock, 0, st>>>(s->scdf, s->E, s->sguide));
+  return cudaGetLastError();
+}
+
+cudaError_t build_edge_tree(drt_scene* s, cudaStream_t st) {
+  int E = s->E;
+  if (E <= 0) return cudaSuccess;
+  SceneView v = s->view();
+  // the scene box (s->bounds) is the one the triangle LBVH build computed
+  DRT_PROF_LAUNCH("etree_keys", st, k_etree_keys<<<(E + kBlock - 1) / kBlock, kBlock, 0, st>>>(
+                                        v, s->edge_opp, s->bounds, s->et_keys, s->et_vals));
+  bool alt = radix_sort_pairs(s->et_keys, s->et_vals, s->et_keys2, s->et_vals2, s->et_hist, s->et_hist_tmp, E, 31, st);
+  uint32_t* ka = alt ? s->et_keys2 : s->et_keys;
+  int32_t* va = alt ? s->et_vals2 : s->et_vals;
+  if (E > 1) {
+    cudaMemsetAsync(s->et_flags, 0, sizeof(int32_t) * (E - 1), st);
+    DRT_PROF_LAUNCH("etree_karras", st, k_karras<<<(E - 1 + kBlock - 1) / kBlock, kBlock, 0, st>>>(
+                                            ka, E, 1, nullptr, s->et_child, s->et_parent, s->et_leaf_parent));
+  }
+  DRT_PROF_LAUNCH("etree_refit", st, k_etree_refit<<<(E + kBlock - 1) / kBlock, kBlock, 0, st>>>(
+                                         v, s->edge_opp, va, s->et_child, s->et_parent, s->et_leaf_parent,
+                                         s->et_flags, s->et_nodes, s->et_leaf));
   return cudaGetLastError();
 }
 

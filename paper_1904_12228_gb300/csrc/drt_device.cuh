@@ -113,8 +113,13 @@ struct SceneView {
   const int32_t* seg_edge;
   const float2* seg_s;
   const double* seg_len;
+  // secondary edge hierarchy (Sec. 5.3.1), when built: internal nodes and
+  // leaf records in key order (layouts in edge_tree.cuh)
+  const float4* et_nodes;
+  const float4* et_leaf;
   int n_seg;
   int V, T, L, E, W, H, cam_type, root;
+  int et_root;  // 0: node 0; ~0: a single leaf; -1: not built
 };
 
 // Work counters (enabled per launch): rays traced by trace_closest, rays
@@ -138,6 +143,8 @@ struct Opts {
   int spp, edge_spp, max_depth, primary_only, terms, proposal;
   uint2 key;
   uint32_t scene_id;  // fourth Philox counter word (the scene's index in a batch)
+  int sec_sampler;    // secondary edge: 0 by 3D length, 1 through the edge hierarchy
+  int sec_samples;    // root samples of the hierarchy
   float eps_rel;
   float* seg_log;  // learned proposal training data: |w.(f_u - f_l)| summed per segment (or null)
   // debug restriction of the backward pass to sample ranges (full range by default)
@@ -179,6 +186,7 @@ struct BatchScene {
   float* dp_sec;                  // [W*H*spp, depth] adjoint of each path vertex from its secondary sample
   unsigned long long* sec_queue;  // (sample << 3 | vertex) of the queued samples
   unsigned long long* sec_count;  // number queued
+  int2* sec_pick;                 // hierarchy sampler: (edge, weight bits) of each queued sample, or null
   int64_t sec_cap;                // queue capacity = W*H*spp*depth
 };
 

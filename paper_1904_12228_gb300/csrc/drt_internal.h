@@ -28,6 +28,8 @@ struct SecScratch {
   unsigned long long* queue = nullptr;
   unsigned long long* count = nullptr;
   int64_t cap = 0;  // (sample, vertex) pairs the buffers hold
+  int2* pick = nullptr;  // edge hierarchy: (edge, weight bits) per queued pair
+  int64_t pick_cap = 0;
 };
 // Scratch for sorting primary edge samples by screen position (key, index).
 struct SortBuffers {
@@ -52,6 +54,13 @@ struct drt_scene {
   float4 *nodes = nullptr, *soup = nullptr;
   int2* edges = nullptr;
   int2* edge_faces = nullptr;  // up to two faces per edge (-1 if none)
+  int2* edge_opp = nullptr;    // third vertices of the two faces (y = -1 unless exactly two faces)
+  // secondary edge hierarchy (built on demand, rebuilt when the scene changes)
+  float4 *et_nodes = nullptr, *et_leaf = nullptr;
+  uint32_t *et_keys = nullptr, *et_keys2 = nullptr, *et_hist = nullptr, *et_hist_tmp = nullptr;
+  int32_t *et_vals = nullptr, *et_vals2 = nullptr, *et_parent = nullptr, *et_leaf_parent = nullptr, *et_flags = nullptr;
+  int2* et_child = nullptr;
+  uint64_t et_generation = ~0ull;
   float* tile_w = nullptr;     // mean |d_image| per screen tile (features)
   float* pedge = nullptr;
   double *plen = nullptr, *pcdf = nullptr, *slen = nullptr, *scdf = nullptr, *scan_tmp = nullptr;
@@ -118,6 +127,9 @@ cudaError_t build_scene_derived(drt_scene* s, cudaStream_t st);   // w2c, lights
 bool radix_sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys2, int32_t* vals2, uint32_t* hist,
                       uint32_t* hist_tmp, int n, int bits, cudaStream_t st);
 size_t radix_hist_entries(int n);
+// Secondary edge hierarchy (Sec. 5.3.1) for the scene's current vertices and
+// camera; the buffers must be allocated.
+cudaError_t build_edge_tree(drt_scene* s, cudaStream_t st);
 cudaError_t scan_exclusive_u32(uint32_t* data, uint32_t* tmp, int n, cudaStream_t st);
 size_t scan_tmp_entries(int n);
 cudaError_t scan_inclusive_f64(const double* in, double* out, double* tmp, int n, cudaStream_t st);

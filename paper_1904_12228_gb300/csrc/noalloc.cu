@@ -18,6 +18,7 @@
 #include <cstdio>
 
 #include "drt_internal.h"
+#include "edge_tree.cuh"
 
 namespace {
 
@@ -76,6 +77,12 @@ drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* s, const drt
   if (opts->scene_id < 0) return fail_noalloc(DRT_ERR_INVALID_ARG, "scene_id must be >= 0");
   op.scene_id = (uint32_t)opts->scene_id;
   op.eps_rel = opts->eps_rel > 0.0f ? opts->eps_rel : 1.52587890625e-05f;
+  if (opts->sec_sampler < 0 || opts->sec_sampler > 1 || opts->sec_tree_samples < 0 ||
+      opts->sec_tree_samples > drt::kEtMaxSamples) {
+    return fail_noalloc(DRT_ERR_INVALID_ARG, "invalid secondary edge sampler options");
+  }
+  op.sec_sampler = opts->sec_sampler;
+  op.sec_samples = opts->sec_tree_samples > 0 ? opts->sec_tree_samples : drt::kEtDefaultSamples;
   op.pix_begin = 0;
   op.pix_end = INT32_MAX;
   op.edge_begin = 0;
@@ -116,6 +123,18 @@ drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* s, const drt
       return fail_noalloc(DRT_ERR_CUDA, cudaGetErrorString(e));
     }
     g_scratch_addr[dev] = static_cast<float*>(p);
+  }
+  // the edge hierarchy's buffers come from an earlier backward; a scene that
+  // changed since is rebuilt in place (kernel launches only)
+  if (op.sec_sampler == 1 && !op.primary_only && (op.terms & 4) && s->E > 0 && s->L > 0) {
+    if (!s->et_leaf) {
+      return fail_noalloc(DRT_ERR_STATE, "the edge hierarchy is not allocated: run one drt_render_backward with it first");
+    }
+    if (s->et_generation != s->generation) {
+      cudaError_t eb = drt::build_edge_tree(s, (cudaStream_t)stream);
+      if (eb != cudaSuccess) return fail_noalloc(DRT_ERR_CUDA, cudaGetErrorString(eb));
+      s->et_generation = s->generation;
+    }
   }
   cudaError_t e = drt::launch_backward(s, op, tape, d_image, grads->d_verts, grads->d_albedo, grads->d_radiance,
                                        grads->d_cam_to_world, grads->d_cam_scale, g_scratch_addr[dev],

@@ -12,6 +12,7 @@
 #include <cstring>
 
 #include "drt_internal.h"
+#include "edge_tree.cuh"
 
 namespace drt {
 namespace {
@@ -882,23 +883,50 @@ struct SecOut {
   int eid0, eid1, mid[2][3];
   bool have_edge, have_m[2];
 };
-// Secondary edge sample at path vertex b (Sec. 5.2.2): the edge by the 3D
-// length CDF, the point on it, the side directions omega +- eps|omega| n_h,
-// and which sides can contribute (above the shading horizon; at the last
-// vertex only a side that may reach a light).  False: nothing to evaluate.
+// How a secondary edge is selected: by the 3D length CDF, through the edge
+// hierarchy (Sec. 5.3.1), or taken from a hierarchy pick made earlier for the
+// same sample (`pre`).  A template parameter, so kernels of the length sampler
+// carry no call into the hierarchy.
+enum { kSelLength = 0, kSelTree = 1, kSelTreePre = 2 };
+
+// Secondary edge sample at path vertex b (Sec. 5.2.2): the edge (see above),
+// the point on it, the side
+// directions omega +- eps|omega| n_h, and which sides can contribute (above the
+// shading horizon; at the last vertex only a side that may reach a light).
+// False: nothing to evaluate.
 struct SecGeom {
+  int e;
   int2 ev;
   float invPE, Nlen, wl, wl2;
   float3 E, w, nh, p, a0v, a1v, Ne, what;
   float dsd[2][3];
   bool act[2], last;
 };
+template <int kSel>
 __device__ __forceinline__ bool secondary_sides(const SceneView& s, const Opts& op, uint32_t c0, uint32_t c1, int b,
-                                                int md, const Vertex& x, float3 n, SecGeom& gm) {
-  double stotal = s.scdf[s.E - 1];
+                                                int md, const Vertex& x, float3 n, SecGeom& gm,
+                                                const int2* pre = nullptr) {
   uint4 r = rng4(op.key, c0, c1, kEdgeSecondary, (uint32_t)b, kPassInterior, op.scene_id);
-  int e = cdf_pick_guided(s.scdf, s.E, dm(u01d(r.x, r.y), stotal), s.sguide, stotal);
-  double le = s.scdf[e] - (e > 0 ? s.scdf[e - 1] : 0.0);
+  int e;
+  float inv_pe;
+  if (kSel == kSelTreePre) {
+    int2 pk = *pre;
+    e = pk.x;
+    inv_pe = __int_as_float(pk.y);
+    if (e < 0) return false;
+  } else if (kSel == kSelTree) {
+    float n32[3];
+    shading_normal32(x, n32);
+    EtQuery q;
+    et_query(s, x.p, n32, b + 1 >= md, op.eps_rel, q);
+    if (!et_pick(s, q, op.sec_samples, op.key, c0, c1, (uint32_t)b, op.scene_id, e, inv_pe)) return false;
+  } else {
+    double stotal = s.scdf[s.E - 1];
+    e = cdf_pick_guided(s.scdf, s.E, dm(u01d(r.x, r.y), stotal), s.sguide, stotal);
+    double le = s.scdf[e] - (e > 0 ? s.scdf[e - 1] : 0.0);
+    if (!(le > 0.0)) return false;
+    inv_pe = (float)(stotal / le);
+  }
   float t = u01f(r.z);
   int2 ev = s.edges[e];
   float3 ve0 = ld3(s.verts + 3 * ev.x), ve1 = ld3(s.verts + 3 * ev.y);
@@ -911,9 +939,10 @@ __device__ __forceinline__ bool secondary_sides(const SceneView& s, const Opts& 
   float N32[3] = {fs(fm(a0[1], a1[2]), fm(a0[2], a1[1])), fs(fm(a0[2], a1[0]), fm(a0[0], a1[2])),
                   fs(fm(a0[0], a1[1]), fm(a0[1], a1[0]))};
   float nlen32 = fsq(dot3x(N32, N32));
-  if (!(le > 0.0 && nlen32 > 0.0f)) return false;
+  if (!(nlen32 > 0.0f)) return false;
+  gm.e = e;
   gm.ev = ev;
-  gm.invPE = (float)(stotal / le);
+  gm.invPE = inv_pe;
   float nh32[3] = {fdv(N32[0], nlen32), fdv(N32[1], nlen32), fdv(N32[2], nlen32)};
   gm.wl = fsq(dot3x(om, om));
   float sh = fm(op.eps_rel, gm.wl);
@@ -941,9 +970,10 @@ __device__ __forceinline__ bool secondary_sides(const SceneView& s, const Opts& 
 // traversal), their continuation paths below the last vertex, and the edge
 // term's contributions: edge vertices and light vertices into so, the
 // adjoint of the vertex position into dp.
+template <int kSel>
 __device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Opts& op, uint32_t c0, uint32_t c1,
                                                     int b, int md, const Vertex& x, float3 n, float3 alb, float3 ab,
-                                                    float3 Le, float3& dp, SecOut& so) {
+                                                    float3 Le, float3& dp, SecOut& so, const int2* pre = nullptr) {
   so.de0 = so.de1 = zero3();
   so.eid0 = so.eid1 = 0;
   so.have_edge = false;
@@ -952,7 +982,7 @@ __device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Op
     for (int i = 0; i < 3; ++i) { so.dm[q][i] = zero3(); so.mid[q][i] = 0; }
   }
   SecGeom gm;
-  if (!secondary_sides(s, op, c0, c1, b, md, x, n, gm)) return;
+  if (!secondary_sides<kSel>(s, op, c0, c1, b, md, x, n, gm, pre)) return;
   const int2 ev = gm.ev;
   const float invPE = gm.invPE, Nlen = gm.Nlen, wl2 = gm.wl2;
   const float3 E = gm.E, w = gm.w, nh = gm.nh, p = gm.p, a0v = gm.a0v, a1v = gm.a1v, Ne = gm.Ne, what = gm.what;
@@ -1035,6 +1065,7 @@ __device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Op
 // measure), so a side ray that cannot reach a light, or that leaves below the
 // shading horizon by more than the side offset, contributes exactly nothing
 // and is not traced (secondary_sides).
+template <int kSel>
 __device__ __forceinline__ void secondary_block(const SceneView& s, const Opts& op, const int32_t* tape_tri,
                                                                const float2* tape_bary, const float* d_image, Grads gr,
                                                                int G, int rows_written, int64_t blk) {
@@ -1065,7 +1096,7 @@ __device__ __forceinline__ void secondary_block(const SceneView& s, const Opts& 
       load_vertex(s, c.k, c.b1, c.b2, c.d, x);
       float3 dp = zero3();
       SecOut so;
-      secondary_at_vertex(s, op, (uint32_t)pix, (uint32_t)sidx, 0, 1, x, shading_normal(x),
+      secondary_at_vertex<kSel>(s, op, (uint32_t)pix, (uint32_t)sidx, 0, 1, x, shading_normal(x),
                           ld3(s.albedo + 3 * c.k), a, Le, dp, so);
       if (so.have_edge) {
         de0 = so.de0;
@@ -1095,15 +1126,16 @@ __device__ __forceinline__ void secondary_block(const SceneView& s, const Opts& 
   }
   block_globals(g, gr.partials + blk * kGlobals, rows_written != 0);
 }
+template <int kSel>
 __global__ void __launch_bounds__(kBlock, DRT_PIXEL_MIN_BLOCKS) k_backward_secondary(SceneView s, Opts op, const int32_t* tape_tri,
                                                                const float2* tape_bary, const float* d_image, Grads gr,
                                                                int G, int rows_written) {
-  secondary_block(s, op, tape_tri, tape_bary, d_image, gr, G, rows_written, blockIdx.x);
+  secondary_block<kSel>(s, op, tape_tri, tape_bary, d_image, gr, G, rows_written, blockIdx.x);
 }
 
 // kInPass: the secondary edge samples are evaluated inside this pass (no
 // scratch for the queue); else their vertex adjoints come in dp_sec.
-template <bool kInPass>
+template <bool kInPass, int kSel = kSelLength>
 __device__ __forceinline__ void path_block(const SceneView& s, const Opts& op, const int32_t* tape_tri,
                                            const float2* tape_bary, const float* d_image, Grads gr, int G,
                                            const float* dp_sec, int64_t blk) {
@@ -1216,7 +1248,7 @@ __device__ __forceinline__ void path_block(const SceneView& s, const Opts& op, c
         }
         if (do_sec) {
           if (kInPass)
-            secondary_at_vertex(s, op, (uint32_t)pix, (uint32_t)sidx, b, md, x, n, alb, ab, Le, dp, so);
+            secondary_at_vertex<kSel>(s, op, (uint32_t)pix, (uint32_t)sidx, b, md, x, n, alb, ab, Le, dp, so);
           else if (dp_sec)  // evaluated apart (queued samples only)
             dp += ld3(dp_sec + 3 * (ti * md + b));
         }
@@ -1243,10 +1275,11 @@ __device__ __forceinline__ void path_block(const SceneView& s, const Opts& op, c
   cache_flush(ca, gr.albedo);
   block_globals(g, gr.partials + blk * kGlobals, false);
 }
+template <int kSel>
 __global__ void __launch_bounds__(kBlock, 1)
     k_backward_path_in_pass(SceneView s, Opts op, const int32_t* tape_tri, const float2* tape_bary,
                             const float* d_image, Grads gr, int G) {
-  path_block<true>(s, op, tape_tri, tape_bary, d_image, gr, G, nullptr, blockIdx.x);
+  path_block<true, kSel>(s, op, tape_tri, tape_bary, d_image, gr, G, nullptr, blockIdx.x);
 }
 __global__ void __launch_bounds__(kBlock, DRT_PATH_MIN_BLOCKS)
     k_backward_path(SceneView s, Opts op, const int32_t* tape_tri, const float2* tape_bary, const float* d_image,
@@ -1307,6 +1340,7 @@ __device__ __forceinline__ bool tape_vertex(const SceneView& s, const Opts& op, 
 // Pass 1: one thread per sample walks its path and queues each vertex whose
 // secondary sample has a side to trace (pixels with a zero loss adjoint
 // contribute nothing and are skipped).  Warp-aggregated appends.
+template <int kSel>
 __global__ void __launch_bounds__(kBlock) k_sec_queue(BatchScene bs) {
   const SceneView& s = bs.v;
   const Opts& op = bs.op;
@@ -1334,10 +1368,10 @@ __global__ void __launch_bounds__(kBlock) k_sec_queue(BatchScene bs) {
   for (int b = 0; b < md; ++b) {
     Vertex x;
     bool need = false;
+    SecGeom gm;
     if (alive) {
       load_vertex(s, k, b1, b2, d, x);
-      SecGeom gm;
-      need = secondary_sides(s, op, (uint32_t)pix, (uint32_t)sidx, b, md, x, shading_normal(x), gm);
+      need = secondary_sides<kSel>(s, op, (uint32_t)pix, (uint32_t)sidx, b, md, x, shading_normal(x), gm);
     }
     unsigned m = __ballot_sync(kFull, need);
     if (m) {
@@ -1345,7 +1379,11 @@ __global__ void __launch_bounds__(kBlock) k_sec_queue(BatchScene bs) {
       unsigned long long base = 0;
       if (lane == leader) base = atomicAdd(bs.sec_count, (unsigned long long)__popc(m));
       base = __shfl_sync(kFull, base, leader);
-      if (need) bs.sec_queue[base + __popc(m & ((1u << lane) - 1u))] = ((unsigned long long)i << 3) | (unsigned)b;
+      if (need) {
+        unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
+        bs.sec_queue[slot] = ((unsigned long long)i << 3) | (unsigned)b;
+        if (kSel == kSelTree) bs.sec_pick[slot] = make_int2(gm.e, __float_as_int(gm.invPE));
+      }
     }
     if (alive) {  // on to vertex b + 1
       if (b + 1 >= md) {
@@ -1378,6 +1416,7 @@ __global__ void __launch_bounds__(kBlock) k_sec_queue(BatchScene bs) {
 // Pass 2: the queued (sample, vertex) pairs, a block-stride loop over the
 // queue; vertex gradients through the block cache (the light's vertices take
 // contributions from most samples).
+template <int kSel>
 __global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_trace(BatchScene bs) {
   __shared__ GradCache cv;
   const SceneView& s = bs.v;
@@ -1408,8 +1447,8 @@ __global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_trace(BatchS
       if (tape_vertex(s, op, bs.tape_tri, bs.tape_bary, pix, sidx, b, md, x, beta)) {
         float3 ab = ((1.0f / (float)op.spp) * ld3(bs.d_image + 3 * pix)) * beta;
         float3 dp = zero3();
-        secondary_at_vertex(s, op, (uint32_t)pix, (uint32_t)sidx, b, md, x, shading_normal(x),
-                            ld3(s.albedo + 3 * x.k), ab, Le, dp, so);
+        secondary_at_vertex<kSel>(s, op, (uint32_t)pix, (uint32_t)sidx, b, md, x, shading_normal(x),
+                                  ld3(s.albedo + 3 * x.k), ab, Le, dp, so, bs.sec_pick + q);
         float* o = bs.dp_sec + 3 * (i * md + b);
         o[0] = dp.x;
         o[1] = dp.y;
@@ -1812,12 +1851,19 @@ cudaError_t launch_secondary_apart(const BatchScene& b, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   BatchScene q = b;
   q.v.counters = nullptr;
-  DRT_PROF_LAUNCH("backward_secondary_queue", st,
-                  k_sec_queue<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, st>>>(q));
+  bool tree = b.op.sec_sampler == 1 && b.sec_pick;
+  unsigned gq = (unsigned)((n + kBlock - 1) / kBlock);
+  if (tree)
+    DRT_PROF_LAUNCH("backward_secondary_queue", st, k_sec_queue<kSelTree><<<gq, kBlock, 0, st>>>(q));
+  else
+    DRT_PROF_LAUNCH("backward_secondary_queue", st, k_sec_queue<kSelLength><<<gq, kBlock, 0, st>>>(q));
   BatchScene t = b;
   t.v.counters = counter_slot(kSlotBwdSecondary);
   int64_t grid = std::min<int64_t>((b.sec_cap + kBlock - 1) / kBlock, 152 * 8);
-  DRT_PROF_LAUNCH("backward_secondary_edges", st, k_sec_trace<<<(unsigned)grid, kBlock, 0, st>>>(t));
+  if (tree)
+    DRT_PROF_LAUNCH("backward_secondary_edges", st, k_sec_trace<kSelTreePre><<<(unsigned)grid, kBlock, 0, st>>>(t));
+  else
+    DRT_PROF_LAUNCH("backward_secondary_edges", st, k_sec_trace<kSelLength><<<(unsigned)grid, kBlock, 0, st>>>(t));
   return cudaGetLastError();
 }
 
@@ -1881,6 +1927,7 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
     bsd.dp_sec = secs->dp;
     bsd.sec_queue = secs->queue;
     bsd.sec_count = secs->count;
+    bsd.sec_pick = op.sec_sampler == 1 ? secs->pick : nullptr;
     bsd.sec_cap = secondary_capacity(sc->W, sc->H, op);
     cudaError_t e = cudaMemsetAsync(secs->dp, 0, sizeof(float) * 3 * bsd.sec_cap, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(secs->count, 0, sizeof(unsigned long long), st);
@@ -1894,7 +1941,10 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
     if (apart || !sec)
       k_backward_path<<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tt, tb, d_image, gr, G, dps);
     else
-      k_backward_path_in_pass<<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tt, tb, d_image, gr, G);
+      if (op.sec_sampler == 1)
+        k_backward_path_in_pass<kSelTree><<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tt, tb, d_image, gr, G);
+      else
+        k_backward_path_in_pass<kSelLength><<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tt, tb, d_image, gr, G);
     prof_end(pt, st);
   } else if ((op.terms & 1) || apart) {
     s.counters = counter_slot(kSlotBwdInterior);
@@ -1907,7 +1957,12 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
   } else if (sec) {
     s.counters = counter_slot(kSlotBwdSecondary);
     ProfToken pt = prof_begin("backward_secondary_edges", st);
-    k_backward_secondary<<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tt, tb, d_image, gr, G, op.terms & 1);
+    if (op.sec_sampler == 1)
+      k_backward_secondary<kSelTree><<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tt, tb, d_image, gr, G,
+                                                                             op.terms & 1);
+    else
+      k_backward_secondary<kSelLength><<<(unsigned)blocks_i, kBlock, 0, st>>>(s, op, tt, tb, d_image, gr, G,
+                                                                               op.terms & 1);
     prof_end(pt, st);
   } else if (need_i && !(op.terms & 1)) {
     // secondary requested but nothing to sample: rows still need zeros
