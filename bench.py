@@ -208,10 +208,10 @@ def run_batched(ctx, dev, replays=20):
 def run_secondary_hierarchy(ctx, dev, K=24, samples=16):
     """Secondary edge term (Sec. 5.2.2): the 3D length sampler against the edge
     hierarchy of Sec. 5.3.1 (`samples` root samples), as gradient variance x
-    time.  Per scene, K runs with independent seeds; each run renders its
-    tape (untimed, shared by both samplers), re-uploads the vertices (so the
-    hierarchy is rebuilt inside the timed backward, as in an optimisation
-    step) and times the backward pass of the secondary term alone.  Variance:
+    time.  Per scene, K runs with independent seeds; each run re-uploads the
+    vertices (so the hierarchy is rebuilt inside the timed backward, as in an
+    optimisation step), renders its tape (untimed) and times the backward pass
+    of the secondary term alone.  Variance:
     mean over vertex entries of the run variance, over the mean squared
     gradient; z2: mean squared z-score of the difference of the two mean
     gradients (about 1 when both estimate the same term)."""
@@ -234,8 +234,8 @@ def run_secondary_hierarchy(ctx, dev, K=24, samples=16):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             for k in range(-2, K):  # two warm-up runs
                 o = drt.make_opts(spp, 0, max_depth=depth, seed=7000 + k, terms=4, sec_tree_samples=tree)
+                S.update_vertices(verts)  # new scene version: the backward rebuilds the hierarchy
                 tape = S.render(img, o, want_tape=True)
-                S.update_vertices(verts)
                 dv = runs[max(k, 0)].view(-1, 3)
                 dv.zero_()
                 e0.record()

@@ -167,6 +167,14 @@ Dual dsqrt(const Dual& a) {
 
 struct D3 { Dual x, y, z; };
 D3 d3(double x, double y, double z) { return D3{Dual(x), Dual(y), Dual(z)}; }
+/* The same tangents at another value (a rounded copy of the point). */
+D3 at_value(const D3& a, const float v[3]) {
+  D3 r = a;
+  r.x.v = v[0];
+  r.y.v = v[1];
+  r.z.v = v[2];
+  return r;
+}
 D3 operator+(const D3& a, const D3& b) { return D3{a.x + b.x, a.y + b.y, a.z + b.z}; }
 D3 operator-(const D3& a, const D3& b) { return D3{a.x - b.x, a.y - b.y, a.z - b.z}; }
 D3 operator*(const Dual& s, const D3& a) { return D3{s * a.x, s * a.y, s * a.z}; }
@@ -812,51 +820,62 @@ void secondary_edge(Ctx& C, int b, uint32_t c0, uint32_t c1, uint32_t pass, cons
   double wl2 = vdot(w, w);
   V3 what = (1.0 / std::sqrt(wl2)) * w;
   D3 V0d = vert_dual(P, P.e0[e], C.track), V1d = vert_dual(P, P.e1[e], C.track);
-  D3 A0 = V0d - Pd, A1 = V1d - Pd;
+  /* alpha and its derivatives are evaluated at the FP32 points the sample
+   * uses (p32, and m32 below), the points the side rays leave from and hit;
+   * the tangents are those of the exact hit points */
+  D3 Ps = at_value(Pd, p32);
+  D3 A0 = V0d - Ps, A1 = V1d - Ps;
   D3 Nd = cross(A0, A1);
   const float* Le = P.sc->radiance;
   for (int side = 0; side < 2; ++side) {
     const float* ds = side == 0 ? du : dl;
     double sgn = side == 0 ? 1.0 : -1.0;
+    /* a side leaving below the shading horizon by more than 1e-5 |omega| is
+     * not traced (FP32 decision, fixed order) */
+    if (dot32(ns32, ds) < -1e-5f * wl) continue;
     Hit h = closest(P, p32, ds, k);
     if (h.tri < 0) continue;
     TriV M = tri_of(P, h.tri);
     float m32[3];
     bary_point32(M.v0, M.v1, M.v2, h.b1, h.b2, m32);
+    float dm32[3] = {m32[0] - p32[0], m32[1] - p32[1], m32[2] - p32[2]};
+    float nf32[3];
+    face_normal32(M.v0, M.v1, M.v2, nf32);
+    /* the hit must lie above the shading horizon; the direct part also needs
+     * the light's front face toward p: both decided in FP32 from the hit */
+    if (!(dot32(ns32, dm32) > 0.0f)) continue;
+    bool front = dot32(nf32, dm32) < 0.0f;
     V3 m{m32[0], m32[1], m32[2]};
     V3 dm = m - p;
     double r2 = vdot(dm, dm), rr = std::sqrt(r2);
     V3 wh = (1.0 / rr) * dm;
     double cos_p = vdot(ns, wh);
-    if (!(cos_p > 0.0)) continue;
     V3 nm = V3{0, 0, 0};
     {
-      float n32[3];
-      face_normal32(M.v0, M.v1, M.v2, n32);
-      V3 nn{n32[0], n32[1], n32[2]};
+      V3 nn{nf32[0], nf32[1], nf32[2]};
       nm = (1.0 / vlen(nn)) * nn;
     }
     /* direct part: m on a light, front face toward p */
     int lj = P.light_of_tri[h.tri];
-    if (lj >= 0) {
+    if (front && lj >= 0) {
       double cos_m = -vdot(nm, wh);
-      if (cos_m > 0.0) {
+      {
         double G = cos_p * cos_m / r2;
-        double hs = 0.0, hs_abs = 0.0;
-        for (int c = 0; c < 3; ++c) {
-          hs += wscale[c] * beta[c] * albedo_k[c] * INV_PI * Le[c] * G;
-          hs_abs += std::fabs(wscale[c]) * beta[c] * albedo_k[c] * INV_PI * Le[c] * G;
-        }
         double wn = vdot(w, nm);
         double tau = vdot(dm, nm) / wn;
         V3 J = tau * (E - (vdot(E, nm) / wn) * w);
         double cr = vlen(vcross(nm, nh));
+        double hs = 0.0, hs_abs = 0.0;
+        for (int c = 0; c < 3; ++c) {
+          hs += wscale[c] * beta[c] * albedo_k[c] * INV_PI * Le[c] * G;
+          hs_abs += std::fabs(wscale[c]) * beta[c] * albedo_k[c] * INV_PI * Le[c] * std::fabs(G);
+        }
         if (cr > 0.0) {
           double W = vlen(J) / (Nl * cr);
           double w1 = h.b1, w2 = h.b2, w0 = 1.0 - w1 - w2;
           D3 Md = w0 * vert_dual(P, M.i0, C.track) + w1 * vert_dual(P, M.i1, C.track) +
                   w2 * vert_dual(P, M.i2, C.track);
-          Dual alpha = dot(Md - Pd, Nd);
+          Dual alpha = dot(at_value(Md, m32) - Ps, Nd);
           accumulate(C, sgn * hs * W * inv_pe, hs_abs * W * inv_pe, alpha);
         }
       }

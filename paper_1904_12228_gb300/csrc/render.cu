@@ -878,6 +878,30 @@ __device__ __forceinline__ float3 nee_adjoint(const SceneView& s, const Opts& op
 // form for radiance arriving from lights, and for b+1 < max_depth the
 // solid-angle form for reflected radiance (a traced sub-path from the side
 // hit with the remaining depth, the same counters on both sides).
+// a - b exactly, as hi + lo (Knuth's TwoSum, operations never contracted).
+__device__ __forceinline__ void two_diff(float a, float b, float& hi, float& lo) {
+  hi = fs(a, b);
+  float bv = fs(hi, a);
+  float av = fs(hi, bv);
+  lo = fa(fs(a, av), fs(-b, bv));
+}
+__device__ __forceinline__ void two_diff3(float3 a, float3 b, float3& hi, float3& lo) {
+  two_diff(a.x, b.x, hi.x, lo.x);
+  two_diff(a.y, b.y, hi.y, lo.y);
+  two_diff(a.z, b.z, hi.z, lo.z);
+}
+// a b - c d to about one rounding of the result (Kahan's FMA form).
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
+  float w = fm(c, d);
+  float e = __fmaf_rn(c, d, -w);
+  float f = __fmaf_rn(a, b, -w);
+  return fs(f, e);
+}
+__device__ __forceinline__ float3 cross_comp(float3 a, float3 b) {
+  return make_float3(diff_of_products(a.y, b.z, a.z, b.y), diff_of_products(a.z, b.x, a.x, b.z),
+                     diff_of_products(a.x, b.y, a.y, b.x));
+}
+
 struct SecOut {
   float3 de0, de1, dm[2][3];
   int eid0, eid1, mid[2][3];
@@ -897,9 +921,10 @@ enum { kSelLength = 0, kSelTree = 1, kSelTreePre = 2 };
 struct SecGeom {
   int e;
   int2 ev;
-  float invPE, Nlen, wl, wl2;
-  float3 E, w, nh, p, a0v, a1v, Ne, what;
+  float invPE, wl, t;
+  float3 ve0, ve1;
   float dsd[2][3];
+  float n32[3];  // shading normal (decision path)
   bool act[2], last;
 };
 template <int kSel>
@@ -946,21 +971,16 @@ __device__ __forceinline__ bool secondary_sides(const SceneView& s, const Opts& 
   float nh32[3] = {fdv(N32[0], nlen32), fdv(N32[1], nlen32), fdv(N32[2], nlen32)};
   gm.wl = fsq(dot3x(om, om));
   float sh = fm(op.eps_rel, gm.wl);
-  gm.E = ve1 - ve0;
-  gm.w = f3(om);
-  gm.nh = f3(nh32);
-  gm.Nlen = len(f3(N32));
-  gm.p = f3(x.p);
-  gm.a0v = ve0 - gm.p;
-  gm.a1v = ve1 - gm.p;
-  gm.Ne = cross(gm.a0v, gm.a1v);
-  gm.wl2 = dot(gm.w, gm.w);
-  gm.what = (1.f / sqrtf(gm.wl2)) * gm.w;
+  gm.t = t;
+  gm.ve0 = ve0;
+  gm.ve1 = ve1;
   gm.last = b + 1 >= md;
+  // which sides are traced is a discrete decision: FP32 in a fixed order
+  shading_normal32(x, gm.n32);
   for (int side = 0; side < 2; ++side) {
     for (int i = 0; i < 3; ++i)
       gm.dsd[side][i] = side == 0 ? fa(om[i], fm(sh, nh32[i])) : fs(om[i], fm(sh, nh32[i]));
-    gm.act[side] = !(dot(n, f3(gm.dsd[side])) < -1e-5f * gm.wl) &&
+    gm.act[side] = !(dot3x(gm.n32, gm.dsd[side]) < fm(-1e-5f, gm.wl)) &&
                    !(gm.last && !may_reach_light(s, x.p, gm.dsd[side]));
   }
   return gm.act[0] || gm.act[1];
@@ -984,26 +1004,42 @@ __device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Op
   SecGeom gm;
   if (!secondary_sides<kSel>(s, op, c0, c1, b, md, x, n, gm, pre)) return;
   const int2 ev = gm.ev;
-  const float invPE = gm.invPE, Nlen = gm.Nlen, wl2 = gm.wl2;
-  const float3 E = gm.E, w = gm.w, nh = gm.nh, p = gm.p, a0v = gm.a0v, a1v = gm.a1v, Ne = gm.Ne, what = gm.what;
   const bool last = gm.last;
   float (*dsd)[3] = gm.dsd;
   bool* act = gm.act;
   Hit hms[2];
   trace_closest2(s, x.p, dsd[0], x.p, dsd[1], act[0], act[1], x.k, x.k, hms[0], hms[1]);
-  float cpms[2] = {0.f, 0.f};
+  // a side counts when its hit lies above the shading horizon and, for the
+  // direct part, on the front face of a light: both decided in FP32 in a fixed
+  // order from the hit point, so the oracle takes the same decisions
+  bool front[2] = {false, false};
   for (int side = 0; side < 2; ++side) {
     if (!act[side] || hms[side].tri < 0) { act[side] = false; continue; }
     Vertex mv;
     load_vertex(s, hms[side].tri, hms[side].b1, hms[side].b2, dsd[side], mv);
-    float3 dmp = f3(mv.p) - p;
-    cpms[side] = dot(n, (1.f / sqrtf(dot(dmp, dmp))) * dmp);
-    if (!(cpms[side] > 0.f)) act[side] = false;
+    float dm32[3] = {fs(mv.p[0], x.p[0]), fs(mv.p[1], x.p[1]), fs(mv.p[2], x.p[2])};
+    if (!(dot3x(gm.n32, dm32) > 0.f)) act[side] = false;
+    front[side] = dot3x(mv.nu, dm32) < 0.f;
   }
   // radiance along both continuation paths, from the hits found above
   float3 Lr[2] = {zero3(), zero3()};
   if (!last && (act[0] || act[1]))
     path_value2_from(s, op, dsd, hms, act, b + 1, c0, c1, kPassSecondaryBase + (uint32_t)b, Lr);
+  if (!act[0] && !act[1]) return;
+  // Geometry of the sample.  The vectors a0, a1 from p to the edge's end
+  // points are nearly parallel when the edge subtends a small angle at p, so
+  // their cross product is taken in the equal, well-conditioned form
+  // a0 x E (E = v1 - v0); with omega = a0 + t E the indirect part's
+  // derivative vectors a1 x omega_hat and omega_hat x a0 are
+  // -(1 - t) a0 x E / |omega| and -t a0 x E / |omega|.
+  const float3 p = f3(x.p), E = gm.ve1 - gm.ve0;
+  const float3 a0v = gm.ve0 - p, a1v = gm.ve1 - p;
+  const float3 Ne = cross(a0v, E);
+  const float Nlen = len(Ne);
+  const float3 nh = (1.f / Nlen) * Ne;
+  const float3 w = a0v + gm.t * E;
+  const float wl2 = dot(w, w), wl = sqrtf(wl2);
+  const float invPE = gm.invPE;
   for (int side = 0; side < 2; ++side) {
     if (!act[side]) continue;
     float sg = side == 0 ? 1.f : -1.f;
@@ -1015,19 +1051,26 @@ __device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Op
     float mr2 = dot(dmp, dmp);
     float3 wh = (1.f / sqrtf(mr2)) * dmp;
     float cpm = dot(n, wh);
-    if (s.light_of_tri[hm.tri] >= 0) {
+    if (front[side] && s.light_of_tri[hm.tri] >= 0) {
       float3 nmu = f3(mv.nu);
       float3 nm = (1.f / len(nmu)) * nmu;
       float cm = -dot(nm, wh);
       float wn = dot(w, nm);
       float cr = len(cross(nm, nh));
-      if (cm > 0.f && cr > 0.f) {
+      if (cr > 0.f) {
         float Gm = cpm * cm / mr2;
         float hs = kInvPi * Gm * (ab.x * alb.x * Le.x + ab.y * alb.y * Le.y + ab.z * alb.z * Le.z);
         float tm = dot(dmp, nm) / wn;
         float3 J = tm * (E - (dot(E, nm) / wn) * w);
         float cc = sg * hs * (len(J) / (Nlen * cr)) * invPE;
-        float3 gv0 = cross(a1v, dmp), gv1 = cross(dmp, a0v);
+        // a1 x (m - p) and (m - p) x a0 are cross products of nearly parallel
+        // vectors: exact differences and the compensated form
+        float3 a0h, a0l, a1h, a1l, dmh, dml;
+        two_diff3(gm.ve0, p, a0h, a0l);
+        two_diff3(gm.ve1, p, a1h, a1l);
+        two_diff3(m, p, dmh, dml);
+        float3 gv0 = cross_comp(a1h, dmh) + (cross(a1h, dml) + cross(a1l, dmh));
+        float3 gv1 = cross_comp(dmh, a0h) + (cross(dmh, a0l) + cross(dml, a0h));
         so.de0 += cc * gv0;
         so.de1 += cc * gv1;
         dp -= cc * (Ne + gv0 + gv1);
@@ -1046,10 +1089,10 @@ __device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Op
       float hs = kInvPi * cpm * (ab.x * alb.x * lr.x + ab.y * alb.y * lr.y + ab.z * alb.z * lr.z);
       if (hs != 0.f) {
         float cc = sg * hs / wl2 * invPE;
-        float3 gv0 = cross(a1v, what), gv1 = cross(what, a0v);
-        so.de0 += cc * gv0;
-        so.de1 += cc * gv1;
-        dp -= cc * (gv0 + gv1);
+        float cw = cc / wl;
+        so.de0 -= (cw * (1.f - gm.t)) * Ne;
+        so.de1 -= (cw * gm.t) * Ne;
+        dp += cw * Ne;
         so.have_edge = true;
       }
     }
