@@ -208,6 +208,18 @@ def test_path_tracing_gradient_terms(drt, ctx, depth, terms):
     assert np.abs(want).max() > 0
 
 
+@pytest.mark.parametrize("depth", [2, 3])
+def test_path_tracing_procedural(drt, ctx, depth):
+    # many short, distant edges: the secondary term's cross products of nearly
+    # parallel vectors and near-cancelling side pairs
+    scene = sg.procedural(41, n_target=3000, width=29, height=27)
+    w = sg.loss_adjoint(3, scene.width, scene.height)
+    got, _ = gpu_grads_depth(drt, ctx, scene, w, 6, 12, depth, 4)
+    want, absum = oracle.backward(scene, w, spp=6, edge_spp=6, seed=12, max_depth=depth, terms=4, n_threads=NT)
+    assert_grads(got, want, absum, "procedural depth %d secondary" % depth)
+    assert np.abs(want).max() > 0
+
+
 def test_backward_without_tape_matches_with_tape(drt, ctx):
     scene = _small_lit(W=24, H=16)
     w = sg.loss_adjoint(5, scene.width, scene.height)
