@@ -48,7 +48,8 @@ class _Opts(ctypes.Structure):
                 ("terms", ctypes.c_int32), ("pix_begin", ctypes.c_int32), ("pix_end", ctypes.c_int32),
                 ("edge_begin", ctypes.c_int64), ("edge_end", ctypes.c_int64), ("n_threads", ctypes.c_int32),
                 ("scene_id", ctypes.c_int32), ("proposal", ctypes.c_int32), ("seg_weights", ctypes.c_void_p),
-                ("n_seg_weights", ctypes.c_int64), ("sec_sampler", ctypes.c_int32), ("sec_tree_samples", ctypes.c_int32)]
+                ("n_seg_weights", ctypes.c_int64), ("sec_sampler", ctypes.c_int32), ("sec_tree_samples", ctypes.c_int32),
+                ("sec_point", ctypes.c_int32)]
 
 
 def lib():
@@ -76,14 +77,14 @@ class _Pinned:
 
 
 def _opts(spp, edge_spp, max_depth, primary_only, seed, eps_rel, terms, pixels, edges, n_threads, scene_id,
-          weights=None, mode=1, sec_tree_samples=0):
+          weights=None, mode=1, sec_tree_samples=0, sec_point=0):
     pb, pe = pixels if pixels is not None else (0, 0)
     eb, ee = edges if edges is not None else (0, 0)
     wp, wn = (weights.ctypes.data, len(weights)) if weights is not None else (None, 0)
     return _Opts(int(spp), int(edge_spp), int(max_depth), int(bool(primary_only)), int(seed) & (2 ** 64 - 1),
                  float(eps_rel), int(terms), int(pb), int(pe), int(eb), int(ee),
                  int(n_threads or n_threads_default()), int(scene_id), mode if weights is not None else 0, wp, wn,
-                 1 if sec_tree_samples > 0 else 0, int(sec_tree_samples))
+                 1 if sec_tree_samples > 0 else 0, int(sec_tree_samples), int(sec_point))
 
 
 def num_params(scene) -> int:
@@ -118,7 +119,7 @@ def render(scene, *, spp: int, seed: int, max_depth: int = 1, primary_only: bool
 def backward(scene, d_image: np.ndarray, *, spp: int, edge_spp: int, seed: int, max_depth: int = 1,
              primary_only: bool = False, terms: int = TERMS_ALL, eps_rel: float = EPS_REL, pixels=None,
              edges=None, n_threads=None, scene_id: int = 0, proposal_weights=None, proposal_scores=None,
-             sec_tree_samples: int = 0):
+             sec_tree_samples: int = 0, sec_point: int = 0):
     """Gradient of sum(d_image * image) as a flat FP64 vector, and per entry
     the magnitude of the terms summed into it (absolute-value chain rule),
     which scales the rounding error an FP32 implementation may make.
@@ -126,7 +127,9 @@ def backward(scene, d_image: np.ndarray, *, spp: int, edge_spp: int, seed: int, 
     proposal for primary edges.  proposal_scores: per tile segment, network
     scores s_k; the mixture then weighs segment k by len_k * exp(s_k), with
     s_k clamped to [-40, 40].  sec_tree_samples > 0 picks secondary edges
-    through the edge hierarchy with that many root samples (else by length)."""
+    through the edge hierarchy with that many root samples (else by length).
+    sec_point = 1 samples the point on a secondary edge by the clamped-cosine
+    density over the edge's arc, mixed with uniform (else uniform)."""
     if proposal_weights is not None and proposal_scores is not None:
         raise ValueError("give proposal_weights or proposal_scores, not both")
     P = _Pinned(scene)
@@ -136,7 +139,7 @@ def backward(scene, d_image: np.ndarray, *, spp: int, edge_spp: int, seed: int, 
         mode, pw = 2, proposal_scores
     pw = None if pw is None else np.ascontiguousarray(pw, np.float32)
     o = _opts(spp, edge_spp, max_depth, primary_only, seed, eps_rel, terms, pixels, edges, n_threads, scene_id,
-              pw, mode, sec_tree_samples)
+              pw, mode, sec_tree_samples, sec_point)
     n = num_params(scene)
     g = np.zeros(n, np.float64)
     a = np.zeros(n, np.float64)
@@ -145,6 +148,18 @@ def backward(scene, d_image: np.ndarray, *, spp: int, edge_spp: int, seed: int, 
     if rc != 0:
         raise RuntimeError("oracle backward failed (%d)" % rc)
     return g, a
+
+
+def edge_point(p, n, v0, v1, u: float, usel: float):
+    """Point t on the edge v0 -> v1 seen from p with unit normal n, drawn by
+    the clamped-cosine arc density mixed with uniform from the uniforms u
+    (position) and usel (mixture component); returns (t, q(t))."""
+    arrs = [np.ascontiguousarray(a, np.float32) for a in (p, n, v0, v1)]
+    t = ctypes.c_float()
+    q = ctypes.c_double()
+    lib().or_edge_point(*[a.ctypes.data_as(ctypes.c_void_p) for a in arrs], ctypes.c_float(u), ctypes.c_float(usel),
+                        ctypes.byref(t), ctypes.byref(q))
+    return float(t.value), float(q.value)
 
 
 def philox(ctr, key) -> np.ndarray:

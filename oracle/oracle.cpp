@@ -228,6 +228,8 @@ typedef struct {
   int64_t n_seg_weights;
   int32_t sec_sampler;       /* secondary edge: 0 by 3D length (Sec. 5.2.2); 1 the edge hierarchy (Sec. 5.3.1) */
   int32_t sec_tree_samples;  /* samples distributed from the hierarchy's root */
+  int32_t sec_point;         /* point on a secondary edge: 0 uniform (Sec. 5.2.2); 1 the clamped-cosine
+                                density over the edge's arc mixed with uniform (Sec. 5.3.2) */
 } or_opts_t;
 }
 
@@ -766,6 +768,96 @@ void light_point(const Prep& P, int j, float r1, float r2, bool track, float y32
  *     alpha_dir = omega_hat.(v0-p)x(v1-p) with omega_hat held fixed.
  * Everything is divided by P(E) = |E| / total length, or, with the edge
  * hierarchy (Sec. 5.3.1), multiplied by the pick's resampling weight.      */
+/* Importance sampling of the point on a secondary edge (Sec. 5.3.2).  The
+ * thesis integrates the BRDF over the edge as a linear light in the frame of a
+ * fitted linearly transformed cosine and inverts the integral numerically.
+ * For a Lambertian surface that distribution is the clamped cosine itself,
+ * and its integral along the edge's arc (the edge seen from p as a piece of a
+ * great circle) has a closed form with a closed-form inverse:
+ *
+ *   Let f be the unit vector from p to the foot of the perpendicular on the
+ *   edge's line, e the edge direction, h the distance to the line and
+ *   theta the angle from f toward e, so omega_hat = cos(theta) f + sin(theta) e
+ *   and s = h tan(theta) along the line.  With n_p = n.f, n_e = n.e,
+ *   rho = |(n_p, n_e)| and psi the angle of (n_p, n_e):
+ *     n.omega_hat = rho cos(theta - psi),   d theta = h ds / r^2,
+ *     G(theta) = n_p sin(theta) - n_e cos(theta) = rho sin(theta - psi)
+ *   is an antiderivative of the cosine on its support, G = -rho and +rho at
+ *   the support's ends.  A uniform y in [G(a), G(b)] gives sin(theta - psi) =
+ *   y / rho, cos(theta - psi) = sqrt(1 - (y/rho)^2), hence cos(theta),
+ *   sin(theta), s and t by rotation by psi: no angle is ever formed.
+ *
+ * The density in t is q_c(t) = (n.omega_hat)^+ h |E| / (r(t)^2 Z) with
+ * Z = G(b) - G(a).  Mixed with uniform, q = 1/4 + 3/4 q_c, every point keeps a
+ * positive density (also the sliver below the horizon that side rays offset
+ * by eps can still reach).  The point t is an FP32 decision (fixed operation
+ * order); q is evaluated in FP64 at that t.  Degenerate cases (the line
+ * through p, n normal to the plane of p and the edge, an arc below the
+ * horizon) keep t uniform with q = 1. */
+struct EdgePoint {
+  float t;
+  double q;
+};
+
+EdgePoint edge_point_sample(const float p[3], const float n[3], const float v0[3], const float v1[3], float u,
+                            float usel) {
+  EdgePoint out{u, 1.0};
+  float a0[3], E[3];
+  for (int i = 0; i < 3; ++i) { a0[i] = v0[i] - p[i]; E[i] = v1[i] - v0[i]; }
+  float N[3] = {a0[1] * E[2] - a0[2] * E[1], a0[2] * E[0] - a0[0] * E[2], a0[0] * E[1] - a0[1] * E[0]};
+  float lE = std::sqrt(dot32(E, E)), nN = std::sqrt(dot32(N, N));
+  if (!(lE > 0.0f) || !(nN > 0.0f)) return out;
+  float h = nN / lE;
+  float e[3] = {E[0] / lE, E[1] / lE, E[2] / lE};
+  float k[3] = {e[1] * N[2] - e[2] * N[1], e[2] * N[0] - e[0] * N[2], e[0] * N[1] - e[1] * N[0]};
+  float f[3] = {k[0] / nN, k[1] / nN, k[2] / nN};
+  float s0 = dot32(a0, e), s1 = s0 + lE;
+  float np = dot32(n, f), ne = dot32(n, e);
+  float rho = std::sqrt(np * np + ne * ne);
+  if (!(rho > 1e-6f)) return out;
+  float r0 = std::sqrt(s0 * s0 + h * h), r1 = std::sqrt(s1 * s1 + h * h);
+  float c0 = h / r0, g0 = s0 / r0, c1 = h / r1, g1 = s1 / r1;
+  bool in0 = np * c0 + ne * g0 > 0.0f, in1 = np * c1 + ne * g1 > 0.0f;
+  if (!in0 && !in1) return out;
+  float Ga = in0 ? g0 * np - c0 * ne : -rho;
+  float Gb = in1 ? g1 * np - c1 * ne : rho;
+  float Z = Gb - Ga;
+  if (!(Z > 1e-6f * rho)) return out;
+  float t = u;
+  if (!(usel < 0.25f)) {
+    float Y = (Ga + u * Z) / rho;
+    Y = std::min(std::max(Y, -1.0f), 1.0f);
+    float C = std::sqrt(std::max(1.0f - Y * Y, 0.0f));
+    float ct = (C * np - Y * ne) / rho;
+    float st = (Y * np + C * ne) / rho;
+    ct = std::max(ct, 1e-30f);
+    float sl = (h * st) / ct;
+    t = (sl - s0) / lE;
+    t = std::min(std::max(t, 0.0f), 0.99999994f);
+  }
+  out.t = t;
+  /* density at t, FP64 from the same FP32 inputs and clipping decisions */
+  double A0[3], Ed[3];
+  for (int i = 0; i < 3; ++i) { A0[i] = (double)v0[i] - p[i]; Ed[i] = (double)v1[i] - v0[i]; }
+  V3 a0d{A0[0], A0[1], A0[2]}, Ev{Ed[0], Ed[1], Ed[2]}, nd{n[0], n[1], n[2]};
+  V3 Nd = vcross(a0d, Ev);
+  double lEd = vlen(Ev), nNd = vlen(Nd), hd = nNd / lEd;
+  V3 ed = (1.0 / lEd) * Ev;
+  V3 fd = (1.0 / nNd) * vcross(ed, Nd);
+  double s0d = vdot(a0d, ed), s1d = s0d + lEd;
+  double npd = vdot(nd, fd), ned = vdot(nd, ed), rhod = std::sqrt(npd * npd + ned * ned);
+  double r0d = std::sqrt(s0d * s0d + hd * hd), r1d = std::sqrt(s1d * s1d + hd * hd);
+  double Gad = in0 ? (s0d / r0d) * npd - (hd / r0d) * ned : -rhod;
+  double Gbd = in1 ? (s1d / r1d) * npd - (hd / r1d) * ned : rhod;
+  double Zd = Gbd - Gad;
+  V3 w = a0d + (double)t * Ev;
+  double r2 = vdot(w, w);
+  double cw = vdot(nd, w) / std::sqrt(r2);
+  double qc = cw > 0.0 ? cw * hd * lEd / (r2 * Zd) : 0.0;
+  out.q = 0.25 + 0.75 * qc;
+  return out;
+}
+
 void path_radiance(Ctx& C, int depth0, int max_depth, const float o32_in[3], const float d32_in[3],
                    const D3& O_in, const D3& D_in, int exclude_in, bool emission_first, uint32_t c0, uint32_t c1,
                    uint32_t pass, const double wscale[3], const double beta_in[3], bool backward, RGB* out);
@@ -792,8 +884,13 @@ void secondary_edge(Ctx& C, int b, uint32_t c0, uint32_t c1, uint32_t pass, cons
     if (le <= 0.0) return;
     inv_pe = P.stotal / le;
   }
-  float t = u01f(r[2]);
   const float *v0 = vtx(P, P.e0[e]), *v1 = vtx(P, P.e1[e]);
+  float t = u01f(r[2]);
+  if (C.opt->sec_point == 1) {
+    EdgePoint ep = edge_point_sample(p32, ns32, v0, v1, t, u01f(r[3]));
+    t = ep.t;
+    inv_pe = inv_pe / ep.q;
+  }
   float om[3], a0[3], a1[3];
   for (int i = 0; i < 3; ++i) {
     float ei = v1[i] - v0[i];
@@ -1105,6 +1202,14 @@ extern "C" {
 void or_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out) { philox4x32_10(ctr, key, out); }
 
 int or_num_params(const or_scene_t* sc) { return 3 * sc->n_verts + 3 * sc->n_tris + 3 + 13; }
+
+/* Point on a secondary edge by the clamped-cosine density (test hook). */
+void or_edge_point(const float* p, const float* n, const float* v0, const float* v1, float u, float usel, float* t,
+                   double* q) {
+  EdgePoint ep = edge_point_sample(p, n, v0, v1, u, usel);
+  *t = ep.t;
+  *q = ep.q;
+}
 
 /* Brute-force closest hit; returns the triangle index or -1. */
 int or_closest(const or_scene_t* sc, const float* o, const float* d, int exclude, float* t_b1_b2) {
