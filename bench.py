@@ -16,8 +16,10 @@ module's protocol (train on logs of 20 scenes, score 4 held-out scenes) and
 is reported under "variance_x_time" (N=1; --no-proposal skips it).  The
 64-scene batched workload (persistent launches in a CUDA graph) is reported
 under "batched" (N=1; --no-batched skips it).  The secondary-edge hierarchy
-(Sec. 5.3.1) against 3D length sampling, as gradient variance x time, is
-reported under "secondary_hierarchy" (N=1; --no-hierarchy skips it).
+(Sec. 5.3.1) and the importance-sampled point on an edge (Sec. 5.3.2)
+against 3D length sampling with a uniform point, as gradient variance x
+time, are reported under "secondary_samplers" (N=1; --no-hierarchy skips
+it).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -205,16 +207,19 @@ def run_batched(ctx, dev, replays=20):
             "first_run_s": first_s, "launch_shapes": inf, "l2": "working set larger than L2 (no flush)"}
 
 
-def run_secondary_hierarchy(ctx, dev, K=24, samples=16):
-    """Secondary edge term (Sec. 5.2.2): the 3D length sampler against the edge
-    hierarchy of Sec. 5.3.1 (`samples` root samples), as gradient variance x
-    time.  Per scene, K runs with independent seeds; each run re-uploads the
-    vertices (so the hierarchy is rebuilt inside the timed backward, as in an
-    optimisation step), renders its tape (untimed) and times the backward pass
-    of the secondary term alone.  Variance:
-    mean over vertex entries of the run variance, over the mean squared
-    gradient; z2: mean squared z-score of the difference of the two mean
-    gradients (about 1 when both estimate the same term)."""
+def run_secondary_samplers(ctx, dev, K=24, samples=16):
+    """Secondary edge term (Sec. 5.2.2) under three samplers, as gradient
+    variance x time against the plain one (3D length CDF, uniform point): the
+    edge hierarchy of Sec. 5.3.1 (`samples` root samples), and the
+    importance-sampled point on the edge of Sec. 5.3.2 (clamped cosine over
+    the edge's arc, mixed with uniform).  Per scene, K runs with independent
+    seeds; each run re-uploads the vertices (so the hierarchy is rebuilt
+    inside the timed backward, as in an optimisation step), renders its tape
+    (untimed) and times the backward pass of the secondary term alone.
+    Variance: mean over vertex entries of the run variance, over the mean
+    squared gradient; z2: mean squared z-score of the difference of a
+    sampler's mean gradient and the plain one's (about 1 when both estimate
+    the same term)."""
     import numpy as np
     import torch
     from paper_1904_12228_gb300 import drt
@@ -222,18 +227,20 @@ def run_secondary_hierarchy(ctx, dev, K=24, samples=16):
     out = []
     cases = (("direct lighting 256x256, 5124 tris, 64 spp", sg.direct_lighting(SCENE_SEED), 1, 64, 2),
              ("procedural 512x512, 200k tris, depth 3, 32 spp", sg.procedural(1237), 3, 32, 1))
+    samplers = (("length", 0, 0), ("hierarchy", samples, 0), ("point", 0, 1))
     for name, sc, depth, spp, leaf in cases:
         S = drt.Scene.from_arrays(ctx, sc, bvh_leaf_size=leaf)
         verts = torch.from_numpy(sc.verts).to(dev)
         w = torch.from_numpy(sg.loss_adjoint(SCENE_SEED, sc.width, sc.height)).to(dev)
         img = torch.zeros((sc.height, sc.width, 3), device=dev)
         res = {}
-        for label, tree in (("length", 0), ("hierarchy", samples)):
+        for label, tree, point in samplers:
             runs = torch.zeros((K, 3 * len(sc.verts)), device=dev)
             times = []
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             for k in range(-2, K):  # two warm-up runs
-                o = drt.make_opts(spp, 0, max_depth=depth, seed=7000 + k, terms=4, sec_tree_samples=tree)
+                o = drt.make_opts(spp, 0, max_depth=depth, seed=7000 + k, terms=4, sec_tree_samples=tree,
+                                  sec_point=point)
                 S.update_vertices(verts)  # new scene version: the backward rebuilds the hierarchy
                 tape = S.render(img, o, want_tape=True)
                 dv = runs[max(k, 0)].view(-1, 3)
@@ -245,19 +252,29 @@ def run_secondary_hierarchy(ctx, dev, K=24, samples=16):
                 if k >= 0:
                     times.append(e0.elapsed_time(e1))
             res[label] = (runs.double().cpu().numpy(), float(np.median(times)))
-        (ra, ta), (rb, tb) = res["length"], res["hierarchy"]
-        norm = float((((ra.mean(0) + rb.mean(0)) * 0.5) ** 2).mean()) or 1.0
-        va, vb = float(ra.var(0, ddof=1).mean() / norm), float(rb.var(0, ddof=1).mean() / norm)
-        se2 = ra.var(0, ddof=1) / K + rb.var(0, ddof=1) / K
-        ok = se2 > 0
-        z2 = float(np.mean((ra.mean(0)[ok] - rb.mean(0)[ok]) ** 2 / se2[ok])) if ok.any() else 0.0
-        out.append({"scene": name, "triangles": len(sc.tris), "max_depth": depth, "spp": spp, "runs": K,
-                    "var_length": va, "var_hierarchy": vb, "ms_length": ta, "ms_hierarchy": tb,
-                    "ratio": (vb * tb) / max(va * ta, 1e-30), "mean_z2": z2})
+        ra, ta = res["length"]
+        entry = {"scene": name, "triangles": len(sc.tris), "max_depth": depth, "spp": spp, "runs": K,
+                 "var": {}, "ms": {}, "ratio": {}, "mean_z2": {}}
+        mean_sq = {lab: (r.mean(0) ** 2).mean() for lab, (r, _) in res.items()}
+        norm = float(np.mean(list(mean_sq.values()))) or 1.0
+        va = float(ra.var(0, ddof=1).mean() / norm)
+        for label, (rb, tb) in res.items():
+            vb = float(rb.var(0, ddof=1).mean() / norm)
+            entry["var"][label] = vb
+            entry["ms"][label] = tb
+            if label == "length":
+                continue
+            se2 = ra.var(0, ddof=1) / K + rb.var(0, ddof=1) / K
+            ok = se2 > 0
+            entry["mean_z2"][label] = float(np.mean((ra.mean(0)[ok] - rb.mean(0)[ok]) ** 2 / se2[ok])) if ok.any() else 0.0
+            entry["ratio"][label] = (vb * tb) / max(va * ta, 1e-30)
+        out.append(entry)
         S.free()
-    geo = float(np.exp(np.mean([np.log(max(o["ratio"], 1e-30)) for o in out])))
+    geo = {lab: float(np.exp(np.mean([np.log(max(o["ratio"][lab], 1e-30)) for o in out])))
+           for lab in ("hierarchy", "point")}
     return {"ratio_geomean": geo, "root_samples": samples,
-            "ratio_unit": "hierarchy/length secondary-edge gradient variance x time (<1: hierarchy wins)",
+            "ratio_unit": "sampler/plain secondary-edge gradient variance x time (<1: the sampler wins); plain = "
+                          "3D length CDF and uniform point; hierarchy = Sec. 5.3.1; point = Sec. 5.3.2 (Lambertian)",
             "scenes": out}
 
 
@@ -337,7 +354,7 @@ def main():
     ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal variance x time part")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-scene batched workload")
     ap.add_argument("--no-hierarchy", action="store_true",
-                    help="skip the secondary-edge hierarchy against length sampling comparison")
+                    help="skip the secondary-edge sampler comparison (hierarchy, point sampling, length)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     from paper_1904_12228_gb300 import replicas
@@ -468,7 +485,7 @@ def main():
 
     sec_h = None
     if rank == 0 and world == 1 and not args.no_hierarchy:
-        sec_h = run_secondary_hierarchy(ctx, dev)
+        sec_h = run_secondary_samplers(ctx, dev)
 
     vxt = None
     if rank == 0 and world == 1 and not args.no_proposal:
@@ -488,7 +505,7 @@ def main():
                 "config": bench_config(T, world),
                 "rays_per_s": world * rays / (ms_per_step / 1e3),
                 "roofline": roof, "cpu_baseline": cpu, "variance_x_time": vxt, "batched": batched,
-                "secondary_hierarchy": sec_h,
+                "secondary_samplers": sec_h,
                 "e2e": {"value": replicas.aggregate_throughput(n_samples, world, e2e_ms), "unit": UNIT,
                         "ms_per_step": e2e_ms,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -128,6 +128,12 @@ typedef struct {
                            takes 0 only. */
   int32_t sec_tree_samples;  /* sec_sampler 1: samples distributed from the root, 1..64;
                                 0 selects 16 */
+  int32_t sec_point;    /* point on a secondary edge (Sec. 5.3.2): 0 uniform in the edge
+                           parameter (Sec. 5.2.2); 1 by the clamped cosine of the shading point
+                           integrated along the edge's arc (the linearly transformed cosine of
+                           a Lambertian surface is the cosine itself), closed-form CDF and
+                           inverse, mixed 1/4 with uniform so every point keeps a positive
+                           density.  A batch takes 0 only. */
 } drt_render_opts;
 
 /* Gradient outputs: device or host arrays, each may be NULL (not wanted).

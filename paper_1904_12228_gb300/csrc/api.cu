@@ -156,7 +156,9 @@ drt_status make_opts(const drt_render_opts* o, drt::Opts* op) {
   if (o->sec_sampler < 0 || o->sec_sampler > 1) return fail(DRT_ERR_INVALID_ARG, "sec_sampler must be 0 or 1");
   if (o->sec_tree_samples < 0 || o->sec_tree_samples > drt::kEtMaxSamples)
     return fail(DRT_ERR_INVALID_ARG, "sec_tree_samples must be in [0,%d]", drt::kEtMaxSamples);
+  if (o->sec_point < 0 || o->sec_point > 1) return fail(DRT_ERR_INVALID_ARG, "sec_point must be 0 or 1");
   op->sec_sampler = o->sec_sampler;
+  op->sec_point = o->sec_point;
   op->sec_samples = o->sec_tree_samples > 0 ? o->sec_tree_samples : drt::kEtDefaultSamples;
   // DRT_DEBUG_RANGES="pix_begin,pix_end,edge_begin,edge_end" restricts which
   // samples the backward pass evaluates (for bisecting against the oracle)

@@ -145,6 +145,7 @@ struct Opts {
   uint32_t scene_id;  // fourth Philox counter word (the scene's index in a batch)
   int sec_sampler;    // secondary edge: 0 by 3D length, 1 through the edge hierarchy
   int sec_samples;    // root samples of the hierarchy
+  int sec_point;      // point on a secondary edge: 0 uniform, 1 clamped-cosine arc density mixed with uniform
   float eps_rel;
   float* seg_log;  // learned proposal training data: |w.(f_u - f_l)| summed per segment (or null)
   // debug restriction of the backward pass to sample ranges (full range by default)

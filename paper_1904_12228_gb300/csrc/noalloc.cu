@@ -78,10 +78,11 @@ drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* s, const drt
   op.scene_id = (uint32_t)opts->scene_id;
   op.eps_rel = opts->eps_rel > 0.0f ? opts->eps_rel : 1.52587890625e-05f;
   if (opts->sec_sampler < 0 || opts->sec_sampler > 1 || opts->sec_tree_samples < 0 ||
-      opts->sec_tree_samples > drt::kEtMaxSamples) {
+      opts->sec_tree_samples > drt::kEtMaxSamples || opts->sec_point < 0 || opts->sec_point > 1) {
     return fail_noalloc(DRT_ERR_INVALID_ARG, "invalid secondary edge sampler options");
   }
   op.sec_sampler = opts->sec_sampler;
+  op.sec_point = opts->sec_point;
   op.sec_samples = opts->sec_tree_samples > 0 ? opts->sec_tree_samples : drt::kEtDefaultSamples;
   op.pix_begin = 0;
   op.pix_end = INT32_MAX;

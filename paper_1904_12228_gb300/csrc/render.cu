@@ -925,8 +925,89 @@ struct SecGeom {
   float3 ve0, ve1;
   float dsd[2][3];
   float n32[3];  // shading normal (decision path)
+  int pt;        // point density: bit 0 clamped-cosine mixture in use, bits 1, 2 ends inside the support
   bool act[2], last;
 };
+
+// Point on a secondary edge by importance (Sec. 5.3.2).  For a Lambertian
+// surface the linearly transformed cosine is the clamped cosine itself; its
+// integral along the edge's arc seen from p has a closed form and a
+// closed-form inverse.  With f the unit vector from p to the foot of the
+// perpendicular on the edge's line, e the edge direction, h the distance to
+// the line and theta the angle from f toward e (s = h tan theta along the
+// line): n . omega_hat = n_p cos(theta) + n_e sin(theta) = rho cos(theta - psi)
+// and G = n_p sin(theta) - n_e cos(theta) = rho sin(theta - psi) is its
+// antiderivative over d theta = h ds / r^2 (G = -rho, +rho at the support's
+// ends).  A uniform y in [G(a), G(b)] gives sin and cos of theta - psi, then
+// of theta by a rotation, then s and t: no angle is formed.  Mixed 1/4 with
+// uniform (usel < 1/4 keeps t = u).  Every step is FP32 with one rounding per
+// operation: t is a decision.  Degenerate cases keep t = u with density 1.
+__device__ __forceinline__ float edge_point_sample(const float p[3], const float n[3], float3 v0, float3 v1, float u,
+                                                   float usel, int& pt) {
+  pt = 0;
+  float a0[3] = {fs(v0.x, p[0]), fs(v0.y, p[1]), fs(v0.z, p[2])};
+  float E[3] = {fs(v1.x, v0.x), fs(v1.y, v0.y), fs(v1.z, v0.z)};
+  float N[3] = {fs(fm(a0[1], E[2]), fm(a0[2], E[1])), fs(fm(a0[2], E[0]), fm(a0[0], E[2])),
+                fs(fm(a0[0], E[1]), fm(a0[1], E[0]))};
+  float lE = fsq(dot3x(E, E)), nN = fsq(dot3x(N, N));
+  if (!(lE > 0.0f) || !(nN > 0.0f)) return u;
+  float h = fdv(nN, lE);
+  float e[3] = {fdv(E[0], lE), fdv(E[1], lE), fdv(E[2], lE)};
+  float k[3] = {fs(fm(e[1], N[2]), fm(e[2], N[1])), fs(fm(e[2], N[0]), fm(e[0], N[2])),
+                fs(fm(e[0], N[1]), fm(e[1], N[0]))};
+  float f[3] = {fdv(k[0], nN), fdv(k[1], nN), fdv(k[2], nN)};
+  float s0 = dot3x(a0, e), s1 = fa(s0, lE);
+  float np = dot3x(n, f), ne = dot3x(n, e);
+  float rho = fsq(fa(fm(np, np), fm(ne, ne)));
+  if (!(rho > 1e-6f)) return u;
+  float hh = fm(h, h);
+  float r0 = fsq(fa(fm(s0, s0), hh)), r1 = fsq(fa(fm(s1, s1), hh));
+  float c0 = fdv(h, r0), g0 = fdv(s0, r0), c1 = fdv(h, r1), g1 = fdv(s1, r1);
+  bool in0 = fa(fm(np, c0), fm(ne, g0)) > 0.0f, in1 = fa(fm(np, c1), fm(ne, g1)) > 0.0f;
+  if (!in0 && !in1) return u;
+  float Ga = in0 ? fs(fm(g0, np), fm(c0, ne)) : -rho;
+  float Gb = in1 ? fs(fm(g1, np), fm(c1, ne)) : rho;
+  float Z = fs(Gb, Ga);
+  if (!(Z > fm(1e-6f, rho))) return u;
+  pt = 1 | (in0 ? 2 : 0) | (in1 ? 4 : 0);
+  if (usel < 0.25f) return u;
+  float Y = fdv(fa(Ga, fm(u, Z)), rho);
+  Y = fminf(fmaxf(Y, -1.0f), 1.0f);
+  float C = fsq(fmaxf(fs(1.0f, fm(Y, Y)), 0.0f));
+  float ct = fdv(fs(fm(C, np), fm(Y, ne)), rho);
+  float st = fdv(fa(fm(Y, np), fm(C, ne)), rho);
+  ct = fmaxf(ct, 1e-30f);
+  float sl = fdv(fm(h, st), ct);
+  float t = fdv(fs(sl, s0), lE);
+  return fminf(fmaxf(t, 0.0f), 0.99999994f);
+}
+
+// Density of that point at t: 1/4 + 3/4 (n.omega_hat)^+ h |E| / (r^2 Z), in
+// FP64 from the same FP32 inputs and support decisions (pt).  Called only for
+// samples with a traced side.
+static __device__ __noinline__ double edge_point_pdf(const float p[3], const float n[3], float3 v0, float3 v1, float t,
+                                                     int pt) {
+  double a0[3] = {(double)v0.x - p[0], (double)v0.y - p[1], (double)v0.z - p[2]};
+  double E[3] = {(double)v1.x - v0.x, (double)v1.y - v0.y, (double)v1.z - v0.z};
+  double N[3] = {a0[1] * E[2] - a0[2] * E[1], a0[2] * E[0] - a0[0] * E[2], a0[0] * E[1] - a0[1] * E[0]};
+  double lE = sqrt(E[0] * E[0] + E[1] * E[1] + E[2] * E[2]);
+  double nN = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+  double h = nN / lE;
+  double e[3] = {E[0] / lE, E[1] / lE, E[2] / lE};
+  double k[3] = {e[1] * N[2] - e[2] * N[1], e[2] * N[0] - e[0] * N[2], e[0] * N[1] - e[1] * N[0]};
+  double np = (n[0] * k[0] + n[1] * k[1] + n[2] * k[2]) / nN;
+  double ne = n[0] * e[0] + n[1] * e[1] + n[2] * e[2];
+  double rho = sqrt(np * np + ne * ne);
+  double s0 = a0[0] * e[0] + a0[1] * e[1] + a0[2] * e[2], s1 = s0 + lE;
+  double r0 = sqrt(s0 * s0 + h * h), r1 = sqrt(s1 * s1 + h * h);
+  double Ga = (pt & 2) ? (s0 / r0) * np - (h / r0) * ne : -rho;
+  double Gb = (pt & 4) ? (s1 / r1) * np - (h / r1) * ne : rho;
+  double w[3] = {a0[0] + (double)t * E[0], a0[1] + (double)t * E[1], a0[2] + (double)t * E[2]};
+  double r2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  double cw = (n[0] * w[0] + n[1] * w[1] + n[2] * w[2]) / sqrt(r2);
+  double qc = cw > 0.0 ? cw * h * lE / (r2 * (Gb - Ga)) : 0.0;
+  return 0.25 + 0.75 * qc;
+}
 template <int kSel>
 __device__ __forceinline__ bool secondary_sides(const SceneView& s, const Opts& op, uint32_t c0, uint32_t c1, int b,
                                                 int md, const Vertex& x, float3 n, SecGeom& gm,
@@ -955,6 +1036,10 @@ __device__ __forceinline__ bool secondary_sides(const SceneView& s, const Opts& 
   float t = u01f(r.z);
   int2 ev = s.edges[e];
   float3 ve0 = ld3(s.verts + 3 * ev.x), ve1 = ld3(s.verts + 3 * ev.y);
+  // which sides are traced is a discrete decision: FP32 in a fixed order
+  shading_normal32(x, gm.n32);
+  gm.pt = 0;
+  if (op.sec_point == 1) t = edge_point_sample(x.p, gm.n32, ve0, ve1, t, u01f(r.w), gm.pt);
   float om[3], a0[3], a1[3];
   om[0] = fs(fa(ve0.x, fm(t, fs(ve1.x, ve0.x))), x.p[0]);
   om[1] = fs(fa(ve0.y, fm(t, fs(ve1.y, ve0.y))), x.p[1]);
@@ -975,8 +1060,6 @@ __device__ __forceinline__ bool secondary_sides(const SceneView& s, const Opts& 
   gm.ve0 = ve0;
   gm.ve1 = ve1;
   gm.last = b + 1 >= md;
-  // which sides are traced is a discrete decision: FP32 in a fixed order
-  shading_normal32(x, gm.n32);
   for (int side = 0; side < 2; ++side) {
     for (int i = 0; i < 3; ++i)
       gm.dsd[side][i] = side == 0 ? fa(om[i], fm(sh, nh32[i])) : fs(om[i], fm(sh, nh32[i]));
@@ -1039,7 +1122,8 @@ __device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Op
   const float3 nh = (1.f / Nlen) * Ne;
   const float3 w = a0v + gm.t * E;
   const float wl2 = dot(w, w), wl = sqrtf(wl2);
-  const float invPE = gm.invPE;
+  float invPE = gm.invPE;
+  if (gm.pt & 1) invPE = (float)((double)invPE / edge_point_pdf(x.p, gm.n32, gm.ve0, gm.ve1, gm.t, gm.pt));
   for (int side = 0; side < 2; ++side) {
     if (!act[side]) continue;
     float sg = side == 0 ? 1.f : -1.f;

@@ -49,7 +49,7 @@ class RenderOpts(ctypes.Structure):
                 ("primary_only", ctypes.c_int32), ("seed", ctypes.c_uint64), ("eps_rel", ctypes.c_float),
                 ("terms", ctypes.c_int32), ("proposal", ctypes.c_int32), ("seg_weights", ctypes.c_void_p),
                 ("n_seg_weights", ctypes.c_int64), ("seg_log", ctypes.c_void_p), ("scene_id", ctypes.c_int32),
-                ("sec_sampler", ctypes.c_int32), ("sec_tree_samples", ctypes.c_int32)]
+                ("sec_sampler", ctypes.c_int32), ("sec_tree_samples", ctypes.c_int32), ("sec_point", ctypes.c_int32)]
 
 
 class MlpWeights(ctypes.Structure):
@@ -172,12 +172,15 @@ def _stream(stream):
 
 
 def make_opts(spp, edge_spp=None, max_depth=1, primary_only=False, seed=0, eps_rel=0.0, terms=0,
-              seg_weights=None, seg_log=None, seg_scores=None, scene_id=0, sec_tree_samples=0) -> RenderOpts:
+              seg_weights=None, seg_log=None, seg_scores=None, scene_id=0, sec_tree_samples=0,
+              sec_point=0) -> RenderOpts:
     """seg_weights: a CUDA float32 tensor of per-segment weights selects the
     mixture proposal 1; seg_scores: per-segment network scores select the
     mixture proposal 2.  The tensor must stay alive until the backward call
     returns.  sec_tree_samples > 0 picks secondary edges through the edge
-    hierarchy with that many root samples (0: by 3D length)."""
+    hierarchy with that many root samples (0: by 3D length).  sec_point=1
+    samples the point on a secondary edge by the clamped-cosine density over
+    the edge's arc mixed with uniform (0: uniform)."""
     if seg_weights is not None and seg_scores is not None:
         raise ValueError("give seg_weights or seg_scores, not both")
     mode, w = (1, seg_weights) if seg_weights is not None else ((2, seg_scores) if seg_scores is not None else (0, None))
@@ -186,7 +189,7 @@ def make_opts(spp, edge_spp=None, max_depth=1, primary_only=False, seed=0, eps_r
                       int(seed) & (2 ** 64 - 1), float(eps_rel), int(terms), mode,
                       _ptr(w) if w is not None else None, n,
                       _ptr(seg_log) if seg_log is not None else None, int(scene_id),
-                      1 if sec_tree_samples > 0 else 0, int(sec_tree_samples))
+                      1 if sec_tree_samples > 0 else 0, int(sec_tree_samples), int(sec_point))
 
 
 class Context:
