@@ -15,6 +15,11 @@
  *    box centroids (Karras 2012; Lauterbach et al. 2009), with the class as the
  *    top key bit so the root separates the two hierarchies.  The treelet SAH
  *    optimisation of Karras and Aila is not applied.
+ *  - Light cone.  At the last vertex (next-event estimation) an edge's term is
+ *    nonzero only where a side ray reaches a light, so a box whose cone of
+ *    directions from the shading point misses the cone to the lights' bounding
+ *    sphere (by more than 1e-3 rad) gets importance zero.  The thesis leaves
+ *    incoming radiance to its next-event edge sampler; this bound is exact.
  *  - Node importance: total edge length x inverse distance from the shading
  *    point to the box centre x an upper bound of the clamped cosine over the box
  *    (Walter et al. 2005: the box in the frame of the shading normal; the
@@ -74,7 +79,16 @@ struct EdgeTree {
   std::vector<ETNode> node;
   int root = -1;             /* node index, or ~0 when there is a single edge */
   float O[3];
+  bool has_light = false;    /* sphere around all light triangles (padded) */
+  float lc[3], lr;
 };
+
+/* Sphere around a box: centre and padded half diagonal (FP32, fixed order). */
+void et_sphere(const float lo[3], const float hi[3], float c[3], float* r) {
+  float d[3];
+  for (int i = 0; i < 3; ++i) { c[i] = (lo[i] + hi[i]) * 0.5f; d[i] = hi[i] - lo[i]; }
+  *r = (0.5f * std::sqrt(dot32(d, d))) * 1.0001f + 1e-6f;
+}
 
 float et_min(float a, float b) { return b < a ? b : a; }
 float et_max(float a, float b) { return b > a ? b : a; }
@@ -103,6 +117,16 @@ void build_edge_tree(const Prep& P, EdgeTree& T) {
   const or_scene_t& sc = *P.sc;
   int E = (int)P.e0.size();
   for (int i = 0; i < 3; ++i) T.O[i] = sc.cam_to_world[4 * i + 3];
+  T.has_light = sc.n_light_tris > 0;
+  if (T.has_light) {
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int j = 0; j < sc.n_light_tris; ++j)
+      for (int k = 0; k < 3; ++k) {
+        const float* v = vtx(P, sc.tris[3 * sc.light_tris[j] + k]);
+        for (int i = 0; i < 3; ++i) { lo[i] = et_min(lo[i], v[i]); hi[i] = et_max(hi[i], v[i]); }
+      }
+    et_sphere(lo, hi, T.lc, &T.lr);
+  }
   /* faces of every edge, in increasing triangle order */
   std::vector<std::vector<int>> faces(E);
   for (int t = 0; t < P.T; ++t)
@@ -318,10 +342,30 @@ bool et_silhouette(const ETQuery& q, const ETLeaf& L) {
   return !((s0 > 0.0f && s1 < 0.0f) || (s0 < 0.0f && s1 > 0.0f));
 }
 
+/* At the last vertex only radiance that arrives from a light counts.  True
+ * if the cone of directions from p to the box's sphere and the cone to the
+ * lights' sphere are apart by more than 1e-3 rad (side rays leave an edge
+ * point by about eps): then no edge of the box has a nonzero term. */
+bool et_light_cone_clears(const EdgeTree& T, const ETQuery& q, const float lo[3], const float hi[3]) {
+  float cb[3], rb, vb[3], vl[3];
+  et_sphere(lo, hi, cb, &rb);
+  for (int i = 0; i < 3; ++i) { vb[i] = cb[i] - q.p[i]; vl[i] = T.lc[i] - q.p[i]; }
+  float db = std::sqrt(dot32(vb, vb)), dl = std::sqrt(dot32(vl, vl));
+  if (!(db > rb) || !(dl > T.lr)) return false;
+  float sb = rb / db, sl = T.lr / dl;
+  float kb = std::sqrt(1.0f - sb * sb), kl = std::sqrt(1.0f - sl * sl);
+  float cosA = kb * kl - sb * sl, sinA = sb * kl + kb * sl;  /* A = sum of the half-angles */
+  float cosAm = cosA * 0.9999995f - sinA * 1e-3f, sinAm = sinA * 0.9999995f + cosA * 1e-3f;
+  if (!(sinAm > 0.0f)) return false;
+  float cg = dot32(vb, vl) / (db * dl);
+  return cg < cosAm;
+}
+
 /* Importance of a child (slot s; leaf position `leaf` if a leaf, else -1)
  * of a parent with box [plo, phi]. */
 float et_importance(const EdgeTree& T, const ETQuery& q, const ETSlot& s, int leaf, const float plo[3],
                     const float phi[3]) {
+  if (q.last && T.has_light && et_light_cone_clears(T, q, s.lo, s.hi)) return 0.0f;
   if (q.last) {
     if (leaf >= 0) {
       if (!et_silhouette(q, T.leaf[leaf])) return 0.0f;

@@ -144,11 +144,33 @@ def test_cos_bound_bounds_the_cosine():
         assert abs(oracle.edge_tree_cos_bound(p, n, q, q) - want) <= 1e-5
 
 
+def _reaches_light(scene, V, p, pts, spread):
+    """FP64 brute force: does a ray from p toward any of pts, or tilted by up
+    to `spread` rad, hit a light triangle?  (Rays toward the light triangles'
+    points within that angle of a ray through pts.)"""
+    d = pts - p
+    d = d / np.linalg.norm(d, axis=1)[:, None]
+    rng = np.random.default_rng(0)
+    for lt in np.asarray(scene.light_tris):
+        a, b, c = (V[int(i)] for i in scene.tris[lt])
+        uv = rng.random((4000, 2))
+        flip = uv.sum(1) > 1
+        uv[flip] = 1 - uv[flip]
+        y = a + uv[:, :1] * (b - a) + uv[:, 1:] * (c - a)
+        y = np.concatenate([y, np.array([a, b, c])])
+        dy = y - p
+        dy = dy / np.linalg.norm(dy, axis=1)[:, None]
+        if (d @ dy.T).max() >= np.cos(spread):
+            return True
+    return False
+
+
 @pytest.mark.parametrize("where,last,samples", [("ground", True, 1), ("ground", True, 16), ("ground", False, 4),
                                                  ("sphere", True, 16), ("sphere", False, 16)])
 def test_resampling_weights_count_every_edge_once(where, last, samples):
     """E[w 1{pick = e}] = 1 for every edge the importance keeps; edges the
-    silhouette gate or the horizon removes are never picked."""
+    silhouette gate or the horizon removes are never picked, and an edge the
+    light-cone bound removes sends no ray to a light."""
     scene = _scene()
     V, faces = _topology(scene)
     ed = oracle.edges(scene)
@@ -178,6 +200,11 @@ def test_resampling_weights_count_every_edge_once(where, last, samples):
         sil = _silhouette64(scene, V, faces, ed, e, p64)
         if last and not sil:  # the silhouette gate: never picked
             assert est[e] == 0.0, (e, est[e])
+            continue
+        if last and est[e] == 0.0 and cmax > 1e-3:
+            # the light-cone bound removed it: no ray from p through the edge
+            # (nor 1e-3 rad around it) reaches a light triangle
+            assert not _reaches_light(scene, V, p64, pts, 1e-3), e
             continue
         # clearly above the horizon edges must be kept; every kept edge counts once
         if cmax > 1e-3 or est[e] > 0.0:
