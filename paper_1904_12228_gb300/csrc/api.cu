@@ -185,7 +185,7 @@ drt_status ensure_edge_tree(drt_scene* s, bool alloc, cudaStream_t st) {
     drt_status a = DRT_OK;
     size_t n = (size_t)E, m = (size_t)std::max(1, E - 1);
     if (a == DRT_OK) a = dalloc_n(&s->et_nodes, drt::kEtNodeF4 * m);
-    if (a == DRT_OK) a = dalloc_n(&s->et_leaf, drt::kEtLeafF4 * n);
+    if (a == DRT_OK) a = dalloc_n(&s->et_leaf, drt::kEtLeafF4 * n + 1);  // + the lights' sphere
     if (a == DRT_OK) a = dalloc_n(&s->et_keys, n);
     if (a == DRT_OK) a = dalloc_n(&s->et_keys2, n);
     if (a == DRT_OK) a = dalloc_n(&s->et_vals, n);
@@ -273,6 +273,7 @@ drt::SceneView drt_scene::view() const {
   v.root = T > leaf_max ? 0 : drt::leaf_enc(0, T);
   v.et_nodes = et_nodes;
   v.et_leaf = et_leaf;
+  v.et_light = (et_leaf && L > 0) ? et_leaf + (size_t)drt::kEtLeafF4 * E : nullptr;
   v.et_root = (et_leaf && et_generation == generation && E > 0) ? (E >= 2 ? 0 : ~0) : -1;
   return v;
 }

@@ -761,6 +761,20 @@ __device__ __forceinline__ void et_frame_of_scene(const SceneView& s, const int*
 }
 
 // One thread per edge: its key (class bit over the Morton code) and id.
+// Sphere around all light triangles (the light-cone bound of the hierarchy).
+__global__ void k_etree_light(const float* verts, const int32_t* tris, const int32_t* light_tris, int L, float4* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int j = 0; j < L; ++j)
+    for (int k = 0; k < 3; ++k) {
+      const float* v = verts + 3 * tris[3 * light_tris[j] + k];
+      for (int i = 0; i < 3; ++i) { lo[i] = et_min(lo[i], v[i]); hi[i] = et_max(hi[i], v[i]); }
+    }
+  float c[3], r;
+  et_sphere(lo, hi, c, r);
+  *out = make_float4(c[0], c[1], c[2], r);
+}
+
 __global__ void k_etree_keys(SceneView s, const int2* opp, const int* b, uint32_t* keys, int32_t* vals) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= s.E) return;
@@ -985,6 +999,9 @@ cudaError_t build_edge_tree(drt_scene* s, cudaStream_t st) {
   int E = s->E;
   if (E <= 0) return cudaSuccess;
   SceneView v = s->view();
+  if (s->L > 0)
+    DRT_PROF_LAUNCH("etree_light", st, k_etree_light<<<1, 1, 0, st>>>(s->verts, s->tris, s->light_tris, s->L,
+                                                                        s->et_leaf + (size_t)kEtLeafF4 * E));
   // the scene box (s->bounds) is the one the triangle LBVH build computed
   DRT_PROF_LAUNCH("etree_keys", st, k_etree_keys<<<(E + kBlock - 1) / kBlock, kBlock, 0, st>>>(
                                         v, s->edge_opp, s->bounds, s->et_keys, s->et_vals));

@@ -117,6 +117,7 @@ struct SceneView {
   // leaf records in key order (layouts in edge_tree.cuh)
   const float4* et_nodes;
   const float4* et_leaf;
+  const float4* et_light;  // sphere around the light triangles (centre, padded radius), or null
   int n_seg;
   int V, T, L, E, W, H, cam_type, root;
   int et_root;  // 0: node 0; ~0: a single leaf; -1: not built

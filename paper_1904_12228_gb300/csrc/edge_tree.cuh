@@ -10,8 +10,10 @@
 // the class as the top key bit.
 //
 // At a shading point p with normal n, a child's importance is zero when it
-// cannot hold a contributing edge (at the last vertex: no silhouette seen from
-// p, by the v-sphere test in Hough space for 6D nodes and exactly at leaves;
+// cannot hold a contributing edge (at the last vertex: its cone of directions
+// from p misses the cone to the lights' bounding sphere, or it holds no
+// silhouette seen from p, by the v-sphere test in Hough space for 6D nodes and
+// exactly at leaves;
 // anywhere: the whole box lies below the horizon by more than the side offset),
 // one when p lies inside the parent's box, and otherwise total length x
 // max(cosine bound, eps) / distance to the box centre.  S samples start at the
@@ -142,9 +144,36 @@ __device__ __forceinline__ void et_load_slot(const float4* nodes, int node, int 
 struct EtQuery {
   float p[3], n[3], t[3], u[3];
   float C[3], r;  // v-sphere about O: centre (p - O)/2, radius |p - O|/2
+  float lc[3], lr;  // sphere around the lights
   float eps;
-  bool last;
+  bool last, has_light;
 };
+
+// Sphere around a box: centre and padded half diagonal.
+__device__ __forceinline__ void et_sphere(const float lo[3], const float hi[3], float c[3], float& r) {
+  float d[3];
+  for (int i = 0; i < 3; ++i) { c[i] = fm(fa(lo[i], hi[i]), 0.5f); d[i] = fs(hi[i], lo[i]); }
+  r = fa(fm(fm(0.5f, fsq(dot3x(d, d))), 1.0001f), 1e-6f);
+}
+
+// At the last vertex only radiance that arrives from a light counts.  True if
+// the cone of directions from p to the box's sphere and the cone to the
+// lights' sphere are apart by more than 1e-3 rad (side rays leave an edge
+// point by about eps): then no edge of the box has a nonzero term.
+__device__ __forceinline__ bool et_light_cone_clears(const EtQuery& q, const float lo[3], const float hi[3]) {
+  float cb[3], rb, vb[3], vl[3];
+  et_sphere(lo, hi, cb, rb);
+  for (int i = 0; i < 3; ++i) { vb[i] = fs(cb[i], q.p[i]); vl[i] = fs(q.lc[i], q.p[i]); }
+  float db = fsq(dot3x(vb, vb)), dl = fsq(dot3x(vl, vl));
+  if (!(db > rb) || !(dl > q.lr)) return false;
+  float sb = fdv(rb, db), sl = fdv(q.lr, dl);
+  float kb = fsq(fs(1.0f, fm(sb, sb))), kl = fsq(fs(1.0f, fm(sl, sl)));
+  float cosA = fs(fm(kb, kl), fm(sb, sl)), sinA = fa(fm(sb, kl), fm(kb, sl));  // A = sum of the half-angles
+  float cosAm = fs(fm(cosA, 0.9999995f), fm(sinA, 1e-3f)), sinAm = fa(fm(sinA, 0.9999995f), fm(cosA, 1e-3f));
+  if (!(sinAm > 0.0f)) return false;
+  float cg = fdv(dot3x(vb, vl), fm(db, dl));
+  return cg < cosAm;
+}
 
 // Orthonormal frame of a unit normal (Duff et al., JCGT 2017).
 __device__ __forceinline__ void et_frame(const float n[3], float t[3], float u[3]) {
@@ -166,6 +195,11 @@ __device__ __forceinline__ void et_query(const SceneView& s, const float p[3], c
   const float O[3] = {s.cam[3], s.cam[7], s.cam[11]};
   for (int i = 0; i < 3; ++i) q.C[i] = fm(fs(p[i], O[i]), 0.5f);
   q.r = fsq(dot3x(q.C, q.C));
+  q.has_light = s.et_light != nullptr;
+  if (q.has_light) {
+    float4 l = __ldg(s.et_light);
+    q.lc[0] = l.x; q.lc[1] = l.y; q.lc[2] = l.z; q.lr = l.w;
+  }
   q.last = last;
   q.eps = eps;
 }
@@ -231,6 +265,7 @@ __device__ __forceinline__ bool et_silhouette(const float4* leaf, int pos, const
 
 __device__ __forceinline__ float et_importance(const float4* leaf, const EtQuery& q, const EtSlot& s,
                                                const float plo[3], const float phi[3], bool has_parent) {
+  if (q.last && q.has_light && et_light_cone_clears(q, s.lo, s.hi)) return 0.0f;
   if (q.last) {
     if (s.child < 0) {
       if (!et_silhouette(leaf, ~s.child, q)) return 0.0f;
