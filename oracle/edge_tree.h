@@ -18,9 +18,8 @@
  *  - Light cone.  At the last vertex (next-event estimation) an edge's term is
  *    nonzero only where a side ray reaches a light, so a box whose cone of
  *    directions from the shading point misses the cone to the lights' bounding
- *    sphere (by more than 1e-3 rad) gets importance zero, where the node still
- *    splits two or more samples.  The thesis leaves incoming radiance to its
- *    next-event edge sampler; this bound is exact.
+ *    sphere (by more than 1e-3 rad) gets importance zero.  The thesis leaves
+ *    incoming radiance to its next-event edge sampler; this bound is exact.
  *  - Node importance: total edge length x inverse distance from the shading
  *    point to the box centre x an upper bound of the clamped cosine over the box
  *    (Walter et al. 2005: the box in the frame of the shading normal; the
@@ -365,8 +364,8 @@ bool et_light_cone_clears(const EdgeTree& T, const ETQuery& q, const float lo[3]
 /* Importance of a child (slot s; leaf position `leaf` if a leaf, else -1)
  * of a parent with box [plo, phi]. */
 float et_importance(const EdgeTree& T, const ETQuery& q, const ETSlot& s, int leaf, const float plo[3],
-                    const float phi[3], bool cone) {
-  if (cone && q.last && T.has_light && et_light_cone_clears(T, q, s.lo, s.hi)) return 0.0f;
+                    const float phi[3]) {
+  if (q.last && T.has_light && et_light_cone_clears(T, q, s.lo, s.hi)) return 0.0f;
   if (q.last) {
     if (leaf >= 0) {
       if (!et_silhouette(q, T.leaf[leaf])) return 0.0f;
@@ -413,7 +412,7 @@ bool et_pick(const EdgeTree& T, const ETQuery& q, int S, uint64_t seed, uint32_t
     for (int i = 0; i < 3; ++i) { s.lo[i] = et_min(L.v0[i], L.v1[i]); s.hi[i] = et_max(L.v0[i], L.v1[i]); }
     s.L = L.len;
     s.allB = L.classB;
-    float I = et_importance(T, q, s, 0, none_lo, none_hi, S >= 2);
+    float I = et_importance(T, q, s, 0, none_lo, none_hi);
     if (!(I > 0.0f)) return false;
     stack.push_back({~0, S, 1.0f, I});
   } else {
@@ -442,9 +441,8 @@ bool et_pick(const EdgeTree& T, const ETQuery& q, int S, uint64_t seed, uint32_t
       plo[i] = et_min(N.slot[0].lo[i], N.slot[1].lo[i]);
       phi[i] = et_max(N.slot[0].hi[i], N.slot[1].hi[i]);
     }
-    /* the light-cone bound only where samples still split */
-    float I0 = et_importance(T, q, N.slot[0], N.child[0] < 0 ? ~N.child[0] : -1, plo, phi, it.n >= 2);
-    float I1 = et_importance(T, q, N.slot[1], N.child[1] < 0 ? ~N.child[1] : -1, plo, phi, it.n >= 2);
+    float I0 = et_importance(T, q, N.slot[0], N.child[0] < 0 ? ~N.child[0] : -1, plo, phi);
+    float I1 = et_importance(T, q, N.slot[1], N.child[1] < 0 ? ~N.child[1] : -1, plo, phi);
     float sum = I0 + I1;
     if (!(sum > 0.0f)) continue;
     float p0 = I0 / sum, p1 = I1 / sum;
