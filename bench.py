@@ -212,7 +212,8 @@ def run_secondary_samplers(ctx, dev, K=24, samples=16):
     variance x time against the plain one (3D length CDF, uniform point): the
     edge hierarchy of Sec. 5.3.1 (`samples` root samples), and the
     importance-sampled point on the edge of Sec. 5.3.2 (clamped cosine over
-    the edge's arc, mixed with uniform).  Per scene, K runs with independent
+    the edge's arc, mixed with uniform); the hierarchy also with 4 root
+    samples.  Per scene, K runs with independent
     seeds; each run re-uploads the vertices (so the hierarchy is rebuilt
     inside the timed backward, as in an optimisation step), renders its tape
     (untimed) and times the backward pass of the secondary term alone.
@@ -227,7 +228,7 @@ def run_secondary_samplers(ctx, dev, K=24, samples=16):
     out = []
     cases = (("direct lighting 256x256, 5124 tris, 64 spp", sg.direct_lighting(SCENE_SEED), 1, 64, 2),
              ("procedural 512x512, 200k tris, depth 3, 32 spp", sg.procedural(1237), 3, 32, 1))
-    samplers = (("length", 0, 0), ("hierarchy", samples, 0), ("point", 0, 1))
+    samplers = (("length", 0, 0), ("hierarchy", samples, 0), ("hierarchy_4", 4, 0), ("point", 0, 1))
     for name, sc, depth, spp, leaf in cases:
         S = drt.Scene.from_arrays(ctx, sc, bvh_leaf_size=leaf)
         verts = torch.from_numpy(sc.verts).to(dev)
@@ -271,10 +272,11 @@ def run_secondary_samplers(ctx, dev, K=24, samples=16):
         out.append(entry)
         S.free()
     geo = {lab: float(np.exp(np.mean([np.log(max(o["ratio"][lab], 1e-30)) for o in out])))
-           for lab in ("hierarchy", "point")}
+           for lab in ("hierarchy", "hierarchy_4", "point")}
     return {"ratio_geomean": geo, "root_samples": samples,
             "ratio_unit": "sampler/plain secondary-edge gradient variance x time (<1: the sampler wins); plain = "
-                          "3D length CDF and uniform point; hierarchy = Sec. 5.3.1; point = Sec. 5.3.2 (Lambertian)",
+                          "3D length CDF and uniform point; hierarchy = Sec. 5.3.1 with `root_samples` (hierarchy_4: "
+                          "4) root samples; point = Sec. 5.3.2 (Lambertian)",
             "scenes": out}
 
 

@@ -1468,7 +1468,7 @@ __device__ __forceinline__ bool tape_vertex(const SceneView& s, const Opts& op, 
 // secondary sample has a side to trace (pixels with a zero loss adjoint
 // contribute nothing and are skipped).  Warp-aggregated appends.
 template <int kSel>
-__global__ void __launch_bounds__(kBlock) k_sec_queue(BatchScene bs) {
+__global__ void __launch_bounds__(kBlock, kSel == kSelLength ? 4 : 1) k_sec_queue(BatchScene bs) {
   const SceneView& s = bs.v;
   const Opts& op = bs.op;
   int lane = threadIdx.x & 31;
