@@ -38,6 +38,14 @@ constexpr int kBlock = 256;
 #define DRT_KEY_SUB 8
 #endif
 constexpr int kKeySub = DRT_KEY_SUB;
+// Resident CTAs per SM of the kernel queueing secondary edge samples: with
+// the length sampler, and with the edge hierarchy's pick (a per-thread stack).
+#ifndef DRT_QUEUE_MIN_BLOCKS
+#define DRT_QUEUE_MIN_BLOCKS 4
+#endif
+#ifndef DRT_TREE_QUEUE_MIN_BLOCKS
+#define DRT_TREE_QUEUE_MIN_BLOCKS 4
+#endif
 // Resident CTAs per SM the render kernel is compiled for.
 #ifndef DRT_RENDER_MIN_BLOCKS
 #define DRT_RENDER_MIN_BLOCKS 4
@@ -1468,7 +1476,7 @@ __device__ __forceinline__ bool tape_vertex(const SceneView& s, const Opts& op, 
 // secondary sample has a side to trace (pixels with a zero loss adjoint
 // contribute nothing and are skipped).  Warp-aggregated appends.
 template <int kSel>
-__global__ void __launch_bounds__(kBlock, kSel == kSelLength ? 4 : 1) k_sec_queue(BatchScene bs) {
+__global__ void __launch_bounds__(kBlock, kSel == kSelLength ? DRT_QUEUE_MIN_BLOCKS : DRT_TREE_QUEUE_MIN_BLOCKS) k_sec_queue(BatchScene bs) {
   const SceneView& s = bs.v;
   const Opts& op = bs.op;
   int lane = threadIdx.x & 31;
