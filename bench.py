@@ -15,7 +15,8 @@ edge proposal against the plain edge sampler, comes from the proposal
 module's protocol (train on logs of 20 scenes, score 4 held-out scenes) and
 is reported under "variance_x_time" (N=1; --no-proposal skips it).  The
 64-scene batched workload (persistent launches in a CUDA graph) is reported
-under "batched" (N=1; --no-batched skips it).  The secondary-edge hierarchy
+under "batched", and the same with 64 small scenes under "batched_small"
+(N=1; --no-batched skips both).  The secondary-edge hierarchy
 (Sec. 5.3.1) and the importance-sampled point on an edge (Sec. 5.3.2)
 against 3D length sampling with a uniform point, as gradient variance x
 time, are reported under "secondary_samplers" (N=1; --no-hierarchy skips
@@ -137,17 +138,19 @@ class ClockSampler:
                 "reasons": seen, "samples": len(rows)}
 
 
-def run_batched(ctx, dev, replays=20):
-    """64 procedural scenes (1k-100k triangles, log-uniform; 128^2-512^2;
-    direct lighting, 16 spp + 16 edge spp) as one batch step: persistent
-    launches captured in a CUDA graph, launch shapes autotuned.  Median of
-    `replays` graph replays, against the same scenes issued one render and
-    one backward call at a time.  The BVHs, tapes and sort buffers (several
-    GB) exceed the 129 MB L2, so no flush is needed between replays."""
+def run_batched(ctx, dev, replays=20, t_min=1000, t_max=100_000, resolutions=(128, 256, 512)):
+    """64 procedural scenes (t_min-t_max triangles, log-uniform; square
+    resolutions drawn from `resolutions`; direct lighting, 16 spp + 16 edge
+    spp) as one batch step: persistent launches captured in a CUDA graph,
+    launch shapes autotuned.  Median of `replays` graph replays, against the
+    same scenes issued one render and one backward call at a time.  For the
+    default workload the BVHs, tapes and sort buffers (several GB) exceed the
+    129 MB L2, so no flush is needed between replays; the small-scene
+    workload is reported as L2-resident."""
     import torch
     from paper_1904_12228_gb300 import drt
     from paper_1904_12228_gb300 import scenegen as sg
-    scenes = sg.batch_workload(BATCH_SEED)
+    scenes = sg.batch_workload(BATCH_SEED, t_min=t_min, t_max=t_max, resolutions=resolutions)
     up = [drt.Scene.from_arrays(ctx, sc, bvh_leaf_size=BVH_LEAF) for sc in scenes]
     d_images = [torch.from_numpy(sg.loss_adjoint(BATCH_SEED + k, sc.width, sc.height)).to(dev)
                 for k, sc in enumerate(scenes)]
@@ -198,13 +201,15 @@ def run_batched(ctx, dev, replays=20):
     b.free()
     for t in tapes:
         t.free()
-    return {"workload": "64 procedural scenes, triangles log-uniform in [1k,100k], resolution from {128,256,512}, "
-                        "direct lighting, 16 spp + 16 primary edge spp, all gradient terms",
+    return {"workload": "64 procedural scenes, triangles log-uniform in [%d,%d], resolution from {%s}, "
+                        "direct lighting, 16 spp + 16 primary edge spp, all gradient terms"
+                        % (t_min, t_max, ",".join(str(r) for r in resolutions)),
             "scenes": len(scenes), "triangles": int(sum(len(sc.tris) for sc in scenes)),
             "pixels": int(sum(sc.width * sc.height for sc in scenes)), "samples_per_step": samples,
             "ms_per_step": ms, "samples_per_s": samples / (ms / 1e3), "replays": replays,
             "single_calls_ms_per_step": single_ms, "speedup_vs_single_calls": single_ms / ms,
-            "first_run_s": first_s, "launch_shapes": inf, "l2": "working set larger than L2 (no flush)"}
+            "first_run_s": first_s, "launch_shapes": inf,
+            "l2": "working set larger than L2 (no flush)" if t_min >= 1000 else "small scenes: L2-resident, no flush"}
 
 
 def run_secondary_samplers(ctx, dev, K=24, samples=16):
@@ -479,16 +484,19 @@ def main():
     h2d = 12 * V + 12 * W_IMG * H_IMG + grad_bytes
     d2h = 12 * W_IMG * H_IMG + grad_bytes
 
-    # second half of the metric: gradient variance x time, learned proposal
-    # against the plain edge sampler (N=1 only)
-    batched = None
+    # the 64-scene batch (N=1 only), and the same with small scenes, where
+    # per-call overheads dominate separate calls
+    batched = batched_small = None
     if rank == 0 and world == 1 and not args.no_batched:
         batched = run_batched(ctx, dev)
+        batched_small = run_batched(ctx, dev, t_min=300, t_max=3000, resolutions=(64, 96, 128))
 
     sec_h = None
     if rank == 0 and world == 1 and not args.no_hierarchy:
         sec_h = run_secondary_samplers(ctx, dev)
 
+    # second half of the metric: gradient variance x time, learned proposal
+    # against the plain edge sampler (N=1 only)
     vxt = None
     if rank == 0 and world == 1 and not args.no_proposal:
         from paper_1904_12228_gb300 import proposal
@@ -507,6 +515,7 @@ def main():
                 "config": bench_config(T, world),
                 "rays_per_s": world * rays / (ms_per_step / 1e3),
                 "roofline": roof, "cpu_baseline": cpu, "variance_x_time": vxt, "batched": batched,
+                "batched_small": batched_small,
                 "secondary_samplers": sec_h,
                 "e2e": {"value": replicas.aggregate_throughput(n_samples, world, e2e_ms), "unit": UNIT,
                         "ms_per_step": e2e_ms,
