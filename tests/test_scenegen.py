@@ -43,6 +43,13 @@ def test_batch_workload():
     assert lt.max() - lt.min() > 0.8 * math.log(100)                 # spread over the log range
 
 
+def test_small_batch_workload():
+    scenes = sg.batch_workload(1238, t_min=300, t_max=3000, resolutions=(64, 96, 128))
+    t = np.array([len(sc.tris) for sc in scenes])
+    assert len(scenes) == 64 and {sc.width for sc in scenes} <= {64, 96, 128}
+    assert t.min() >= 300 and t.max() < 3000 + 1280 + 8
+
+
 def test_loss_adjoint_and_perturbation():
     w = sg.loss_adjoint(3, 40, 30)
     assert w.shape == (30, 40, 3) and w.dtype == np.float32
