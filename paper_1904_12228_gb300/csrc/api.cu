@@ -318,6 +318,7 @@ drt_status drt_destroy(drt_context* ctx) {
 }
 
 drt_status drt_scene_upload(drt_context* ctx, const drt_scene_desc* d, void* stream, drt_scene** out) {
+  NvtxRange nvtx_range("drt_scene_upload");
   if (!ctx || !d || !out) return fail(DRT_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
   if (d->n_verts < 3 || d->n_tris < 1) return fail(DRT_ERR_INVALID_ARG, "need >= 3 vertices and >= 1 triangle");
@@ -431,6 +432,7 @@ drt_status drt_scene_upload(drt_context* ctx, const drt_scene_desc* d, void* str
 }
 
 drt_status drt_scene_update_vertices(drt_context* ctx, drt_scene* s, const float* verts, void* stream) {
+  NvtxRange nvtx_range("drt_scene_update_vertices");
   if (!ctx || !s || !verts) return fail(DRT_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t st = (cudaStream_t)stream;
   CUDA_TRY(cudaMemcpyAsync(s->verts, verts, 12 * (size_t)s->V, cudaMemcpyDefault, st));
@@ -442,6 +444,7 @@ drt_status drt_scene_update_vertices(drt_context* ctx, drt_scene* s, const float
 
 drt_status drt_scene_update_params(drt_context* ctx, drt_scene* s, const float* albedo, const float* radiance,
                                    const float* cam_to_world, const float* cam_scale, void* stream) {
+  NvtxRange nvtx_range("drt_scene_update_params");
   if (!ctx || !s) return fail(DRT_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t st = (cudaStream_t)stream;
   if (albedo) CUDA_TRY(cudaMemcpyAsync(s->albedo, albedo, 12 * (size_t)s->T, cudaMemcpyDefault, st));
@@ -473,6 +476,7 @@ drt_status drt_tape_free(drt_context* ctx, drt_tape* t) {
 
 drt_status drt_render(drt_context* ctx, drt_scene* s, const drt_render_opts* opts, float* image, drt_tape** tape,
                       void* stream) {
+  NvtxRange nvtx_range("drt_render");
   if (!ctx || !s || !image) return fail(DRT_ERR_INVALID_ARG, "NULL argument");
   drt::Opts op;
   DRT_TRY(make_opts(opts, &op));
@@ -524,6 +528,7 @@ drt_status drt_render(drt_context* ctx, drt_scene* s, const drt_render_opts* opt
 
 drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* tape, const drt_render_opts* opts,
                                const float* d_image, const drt_grads* grads, void* stream) {
+  NvtxRange nvtx_range("drt_render_backward");
   if (!ctx || !s || !d_image || !grads) return fail(DRT_ERR_INVALID_ARG, "NULL argument");
   drt::Opts op;
   DRT_TRY(make_opts(opts, &op));
@@ -670,6 +675,7 @@ drt_status drt_scene_segments(drt_context* ctx, drt_scene* s, int64_t* n, int32_
 
 drt_status drt_segment_features(drt_context* ctx, drt_scene* s, const float* d_image, const float* image, void* x,
                                 void* stream) {
+  NvtxRange nvtx_range("drt_segment_features");
   if (!ctx || !s || !d_image || !x) return fail(DRT_ERR_INVALID_ARG, "NULL argument");
   if (!is_device_ptr(d_image) || !is_device_ptr(x) || (image && !is_device_ptr(image)))
     return fail(DRT_ERR_INVALID_ARG, "device arrays only");

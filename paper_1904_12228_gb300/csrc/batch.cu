@@ -482,6 +482,7 @@ drt_status drt_batch_create(drt_context* ctx, const drt_batch_item* items, int32
 }
 
 drt_status drt_batch_run(drt_context* ctx, drt_batch* b, void* stream) {
+  NvtxRange nvtx_range("drt_batch_run");
   if (!ctx || !b || b->ctx != ctx) return bfail(DRT_ERR_INVALID_ARG, "NULL or foreign batch");
   cudaStream_t st = (cudaStream_t)stream;
   if (b->autotune && !b->tuned) {
@@ -544,6 +545,7 @@ drt_status drt_batch_free(drt_context* ctx, drt_batch* b) {
 drt_status drt_render_batch(drt_context* ctx, drt_scene* const* scenes, int32_t n, const drt_render_opts* opts,
                             float* const* images, const float* const* d_images, const drt_grads* grads,
                             void* stream) {
+  NvtxRange nvtx_range("drt_render_batch");
   if (!ctx || !scenes || !images || !opts) return bfail(DRT_ERR_INVALID_ARG, "NULL argument");
   if (n < 1 || n > kMaxBatch) return bfail(DRT_ERR_INVALID_ARG, "a batch holds 1 to 65536 scenes");
   std::vector<drt_batch_item> items((size_t)n);

@@ -6,6 +6,7 @@
 #include <string>
 #include <vector>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/drt.h"
 #include "drt_device.cuh"
@@ -18,6 +19,15 @@ struct drt_context {
   // back by events before its results are read
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+// NVTX range over one C-ABI call (header-only NVTX; a no-op unless a profiler
+// is attached), so a timeline shows which library call launched what.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 namespace drt {

@@ -435,6 +435,7 @@ extern "C" {
 
 drt_status drt_mlp_forward(drt_context* ctx, const void* x, int64_t m, const drt_mlp_weights* w, float* y,
                            void* stream) {
+  NvtxRange nvtx_range("drt_mlp_forward");
   if (!ctx || !w || (m > 0 && (!x || !y)) || m < 0 || m > INT32_MAX) return DRT_ERR_INVALID_ARG;
   if (m == 0) return DRT_OK;
   drt::MlpArgs a{(const __nv_bfloat16*)x, (const __nv_bfloat16*)w->w1, w->b1, (const __nv_bfloat16*)w->w2, w->b2,
@@ -454,6 +455,7 @@ drt_status drt_mlp_forward(drt_context* ctx, const void* x, int64_t m, const drt
 
 drt_status drt_mlp_backward(drt_context* ctx, const void* x, const float* target, const float* mask, int64_t m,
                             float inv_n, const drt_mlp_weights* w, drt_mlp_grads* g, float* loss, void* stream) {
+  NvtxRange nvtx_range("drt_mlp_backward");
   if (!ctx || !w || !g || !loss || m < 0 || m > INT32_MAX || (m > 0 && (!x || !target || !mask)))
     return DRT_ERR_INVALID_ARG;
   if (m == 0) return DRT_OK;
@@ -475,6 +477,7 @@ drt_status drt_mlp_backward(drt_context* ctx, const void* x, const float* target
 
 drt_status drt_adam_step(drt_context* ctx, float* params, const float* grads, float* m1, float* m2, void* params_bf16,
                          int64_t n, float lr, float beta1, float beta2, float eps, int32_t step, void* stream) {
+  NvtxRange nvtx_range("drt_adam_step");
   if (!ctx || n < 0 || n > INT32_MAX || step < 1 || (n > 0 && (!params || !grads || !m1 || !m2)))
     return DRT_ERR_INVALID_ARG;
   if (n == 0) return DRT_OK;

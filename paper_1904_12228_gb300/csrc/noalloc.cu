@@ -56,6 +56,7 @@ extern "C" {
 drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* s, const drt_tape* tape,
                                        const drt_render_opts* opts, const float* d_image, const drt_grads* grads,
                                        void* stream) {
+  NvtxRange nvtx_range("drt_render_backward_noalloc");
   if (!ctx || !s || !opts || !d_image || !grads) {
     return fail_noalloc(DRT_ERR_INVALID_ARG, "NULL argument");
   }

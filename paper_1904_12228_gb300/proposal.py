@@ -67,6 +67,44 @@ class EdgeProposal:
                                  self.p["b2"].data_ptr(), self.p["w3"].data_ptr(), self.p["b3"].data_ptr())
         self._gp = drt.MlpGrads(*(self.g[k].data_ptr() for k in NAMES))
 
+    # -- training resume ------------------------------------------------------
+    _MAGIC = b"DRTMLP01"
+
+    def save(self, path: str) -> None:
+        """Weights and Adam state as one raw little-endian file: the 8-byte
+        tag DRTMLP01, the Adam step count (int64), then for w1 b1 w2 b2 w3 b3
+        in turn the FP32 master weights, first moments and second moments
+        (row-major, the shapes of the network)."""
+        with open(path, "wb") as f:
+            f.write(self._MAGIC)
+            f.write(np.asarray([self.steps], "<i8").tobytes())
+            for k in NAMES:
+                for d in (self.p, self.m1, self.m2):
+                    f.write(d[k].detach().cpu().numpy().astype("<f4").tobytes())
+
+    def load(self, path: str) -> None:
+        """Read a file written by save() into this network, in place (the
+        library holds pointers to these arrays), and refresh the BF16 copies
+        the forward pass reads."""
+        with open(path, "rb") as f:
+            raw = f.read()
+        if raw[:8] != self._MAGIC:
+            raise ValueError("not a network file: bad tag")
+        need = 16 + 4 * 3 * sum(self.p[k].numel() for k in NAMES)
+        if len(raw) != need:
+            raise ValueError("network file of %d bytes, expected %d" % (len(raw), need))
+        steps = int(np.frombuffer(raw[8:16], "<i8")[0])
+        off = 16
+        for k in NAMES:
+            for d in (self.p, self.m1, self.m2):
+                n = d[k].numel()
+                arr = np.frombuffer(raw[off:off + 4 * n], "<f4").astype(np.float32).reshape(tuple(d[k].shape))
+                d[k].copy_(torch.from_numpy(arr))
+                off += 4 * n
+        self.steps = steps
+        for k in ("w1", "w2"):
+            self.pb[k].copy_(_bf16_bits(self.p[k]))
+
     # -- inference ------------------------------------------------------------
     def features(self, scene: drt.Scene, d_image: torch.Tensor, n: int | None = None, image=None, stream=None):
         n = scene.num_segments(stream) if n is None else n
