@@ -119,8 +119,10 @@ typedef struct {
   int32_t sec_sampler;  /* secondary edge selection at a shading vertex: 0 by 3D edge length
                            (Sec. 5.2.2); 1 through the edge hierarchy of Sec. 5.3.1 (camera-
                            silhouette edges by 3D position, the rest by position and the Hough
-                           points of their face planes; v-sphere culling of non-silhouettes at
-                           the last vertex; importance length x cosine bound / distance;
+                           points of their face planes; at the last vertex, v-sphere culling of
+                           non-silhouettes and a light-cone bound (boxes whose directions from
+                           the shading point miss the lights' bounding sphere); importance
+                           length x cosine bound / distance;
                            samples split between children, one edge kept by weighted
                            reservoir sampling and weighted by its resampling weight).  The
                            hierarchy is built on the backward call's stream when the scene is
