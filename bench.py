@@ -1,26 +1,36 @@
 #!/usr/bin/env python3
 """Benchmark: forward + backward samples/s of differentiable Monte Carlo ray
-tracing with edge sampling on the direct-lighting workload.
+tracing with edge sampling.
 
-Workload (one step): 256x256 image of a jittered icosphere (5120 triangles)
-on a 2-triangle ground, lit by a 2-triangle area light; 64 samples per pixel
-with one shadow ray each, 64 primary edge samples per pixel, one secondary
-edge sample per interior sample.  A step is the whole hot path: vertex
-update (LBVH rebuild, edge CDFs), render with a checkpoint tape, and the
-backward pass (interior adjoint, secondary and primary edge terms, gradient
-scatter).  Inputs are synthetic and seeded.
+Headline workload (one step): the procedural scene of about 200k triangles
+(displaced icospheres and subdivided boxes on a ground quad, two area
+lights), 512x512, path tracing with 3 scattering vertices and next-event
+estimation at each, 32 samples per pixel, 32 primary edge samples per pixel
+and one secondary edge sample per path vertex.  A step is the whole hot
+path: vertex update (LBVH rebuild, edge CDFs), render with a checkpoint tape,
+and the backward pass (interior adjoint, secondary and primary edge terms,
+gradient scatter).  Inputs are synthetic and seeded.
 
-The second half of the metric, gradient variance x time of the learned
-edge proposal against the plain edge sampler, comes from the proposal
-module's protocol (train on logs of 20 scenes, score 4 held-out scenes) and
-is reported under "variance_x_time" (N=1; --no-proposal skips it).  The
-64-scene batched workload (persistent launches in a CUDA graph) is reported
-under "batched", and the same with 64 small scenes under "batched_small"
-(N=1; --no-batched skips both).  The secondary-edge hierarchy
-(Sec. 5.3.1) and the importance-sampled point on an edge (Sec. 5.3.2)
-against 3D length sampling with a uniform point, as gradient variance x
-time, are reported under "secondary_samplers" (N=1; --no-hierarchy skips
-it).
+Reported beside it (N=1): the direct-lighting workload (256x256, jittered
+icosphere of 5120 triangles, 64 spp + 64 edge spp) under "direct_lighting";
+the second half of the metric, gradient variance x time of the learned edge
+proposal against the plain edge sampler (train on logs of 20 scenes, score 4
+held-out scenes) under "variance_x_time" (--no-proposal skips it); the
+64-scene batched workload (persistent launches in a CUDA graph) under
+"batched", and the same with 64 small scenes under "batched_small"
+(--no-batched skips both); the secondary-edge hierarchy (Sec. 5.3.1) and the
+importance-sampled point on an edge (Sec. 5.3.2) against 3D length sampling
+with a uniform point, as gradient variance x time, under
+"secondary_samplers" (--no-hierarchy skips it); the tensor-core network's
+BF16 rate under "mlp".
+
+Roofline: the ray kernels are bound by issue slots and L1/L2 bandwidth (no
+dense contraction, working set mostly in L2).  Per launch, the algorithmic
+work of a kernel is 12 lane-operations per ray-box slab test (two per BVH
+node visit) plus 26 per watertight triangle test, and its algorithmic bytes
+64 per node visit plus 48 per triangle test, from the kernel's work
+counters.  The peaks are measured in the same run by the library's probes
+(FP32 FMA lane-operation rate; L2-resident copy bandwidth).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -43,24 +53,53 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd samples/sec and gradient variance x time vs plain edge sampler, 1 GB300"
 UNIT = "samples/s"
-W_IMG, H_IMG, SPP, EDGE_SPP = 256, 256, 64, 64
-SCENE_SEED = 1236
+
+
+class Workload:
+    def __init__(self, key, seed, spp, edge_spp, depth, leaf, desc):
+        self.key, self.seed, self.spp, self.edge_spp, self.depth, self.leaf, self.desc = \
+            key, seed, spp, edge_spp, depth, leaf, desc
+
+    def scene(self, seed=None):
+        from paper_1904_12228_gb300 import scenegen as sg
+        s = self.seed if seed is None else seed
+        if self.key == "procedural":
+            return sg.procedural(s)
+        if self.key == "procedural_small":
+            return sg.procedural(s, n_target=50_000, width=256, height=256)
+        return sg.direct_lighting(s)
+
+
+# the inverse-rendering workload: 512x512, ~200k triangles, depth 3, 32 + 32 spp
+PROCEDURAL = Workload("procedural", 1237, 32, 32, 3, 1,
+                      "procedural 512x512: ~200k triangles (displaced icospheres + subdivided boxes) on a ground quad "
+                      "with 2 area lights; path tracing depth 3 with NEE at every vertex, 32 spp, 32 primary edge spp, "
+                      "1 secondary edge sample per path vertex; step = vertex update (LBVH + edge CDFs) + render + "
+                      "backward (all gradient terms)")
+# direct lighting: 256x256, icosphere 5120 triangles, 64 + 64 spp; two
+# triangles per BVH leaf (coherent first-vertex rays)
+DIRECT = Workload("direct", 1236, 64, 64, 1, 2,
+                  "direct lighting 256x256: jittered icosphere (5120 tris) + 2-tri ground + 2-tri area light; "
+                  "64 spp with 1 shadow ray, 64 primary edge spp, 1 secondary edge sample per path vertex; "
+                  "step = vertex update (LBVH + edge CDFs) + render + backward (all gradient terms)")
+# a reduced procedural case for profiler captures (same kernels, a few hundred MB on the device)
+PROCEDURAL_SMALL = Workload("procedural_small", 1237, 32, 32, 3, 1,
+                            "procedural 256x256: ~50k triangles, path tracing depth 3, 32 spp, 32 primary edge spp "
+                            "(profiling case); step = vertex update + render + backward")
+WORKLOADS = {"procedural": PROCEDURAL, "direct": DIRECT, "procedural_small": PROCEDURAL_SMALL}
+HEADLINE = PROCEDURAL
 BATCH_SEED, BATCH_SPP = 1238, 16
-# Two triangles per BVH leaf: both timed workloads are direct lighting, whose
-# rays are mostly coherent first-vertex rays (one per leaf suits path tracing).
-BVH_LEAF = 2
-WORKLOAD = ("direct lighting 256x256: jittered icosphere (5120 tris) + 2-tri ground + 2-tri area light; "
-            "64 spp with 1 shadow ray, 64 primary edge spp, 1 secondary edge sample per path vertex; "
-            "step = vertex update (LBVH + edge CDFs) + render + backward (all gradient terms)")
-# FP32 lane-operations of one BVH node visit (two slab tests) and one
-# watertight triangle test, counted from the kernels' arithmetic.
-OPS_PER_NODE = 46
-OPS_PER_TRI = 45
-SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
-
-
-def peak_alu_tops():
-    return SMS * LANES * SM_MAX_MHZ * 1e6 / 1e12
+BVH_LEAF = 2  # batched direct-lighting workloads
+# lane-operations and bytes of the algorithmic work units
+OPS_PER_BOX = 12          # slab test: 6 FMA + 6 min/max
+BOXES_PER_NODE = 2        # a BVH node visit tests both child boxes
+OPS_PER_TRI = 26          # watertight test: shear and edge functions
+BYTES_PER_NODE = 64
+BYTES_PER_TRI = 48
+# profiled kernel name -> work-counter slot
+COUNTER_OF = {"render": "render", "backward_interior": "backward_interior", "backward_path": "backward_interior",
+              "backward_primary_edges": "backward_primary_edges",
+              "backward_secondary_edges": "backward_secondary_edges"}
 
 
 def measured_peaks():
@@ -79,13 +118,13 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel):
+def ncu_traffic(workload, kernel):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel sources (else None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             t = json.load(f)
-        ent = t.get(kernel)
+        ent = t.get(workload, {}).get(kernel)
         if ent and ent.get("source_hash") == kernel_source_hash():
             return ent.get("dram_bytes_per_launch")
     except Exception:
@@ -231,13 +270,13 @@ def run_secondary_samplers(ctx, dev, K=24, samples=16):
     from paper_1904_12228_gb300 import drt
     from paper_1904_12228_gb300 import scenegen as sg
     out = []
-    cases = (("direct lighting 256x256, 5124 tris, 64 spp", sg.direct_lighting(SCENE_SEED), 1, 64, 2),
+    cases = (("direct lighting 256x256, 5124 tris, 64 spp", sg.direct_lighting(DIRECT.seed), 1, 64, 2),
              ("procedural 512x512, 200k tris, depth 3, 32 spp", sg.procedural(1237), 3, 32, 1))
     samplers = (("length", 0, 0), ("hierarchy", samples, 0), ("hierarchy_4", 4, 0), ("point", 0, 1))
     for name, sc, depth, spp, leaf in cases:
         S = drt.Scene.from_arrays(ctx, sc, bvh_leaf_size=leaf)
         verts = torch.from_numpy(sc.verts).to(dev)
-        w = torch.from_numpy(sg.loss_adjoint(SCENE_SEED, sc.width, sc.height)).to(dev)
+        w = torch.from_numpy(sg.loss_adjoint(DIRECT.seed, sc.width, sc.height)).to(dev)
         img = torch.zeros((sc.height, sc.width, 3), device=dev)
         res = {}
         for label, tree, point in samplers:
@@ -285,41 +324,51 @@ def run_secondary_samplers(ctx, dev, K=24, samples=16):
             "scenes": out}
 
 
-def cpu_workload_sample(seconds_target, n_threads):
-    """Time the CPU oracle on a bounded sample of the same workload: a block
-    of pixels (all spp, interior + secondary edges) and a proportional range
-    of primary edge samples.  Returns (samples/s, description, cores)."""
+def cpu_workload_sample(wl, seconds_target, n_threads, n_fixed=None):
+    """Time the CPU oracle on a bounded sample of workload wl: a block of
+    pixels (all spp, interior + secondary edges) and a proportional range of
+    primary edge samples, sized to about seconds_target (or n_fixed pixels).
+    Returns (samples/s, description, cores, seconds, pixels)."""
     import oracle
     from paper_1904_12228_gb300 import scenegen as sg
-    scene = sg.direct_lighting(SCENE_SEED)
-    w = sg.loss_adjoint(1, W_IMG, H_IMG)
-    p0 = (H_IMG // 2) * W_IMG + W_IMG // 4
+    scene = wl.scene()
+    W, H = scene.width, scene.height
+    w = sg.loss_adjoint(1, W, H)
+    p0 = (H // 2) * W + W // 4
 
     def run(npix):
         t = time.perf_counter()
-        oracle.render(scene, spp=SPP, seed=1, pixels=(p0, p0 + npix), n_threads=n_threads)
-        oracle.backward(scene, w, spp=SPP, edge_spp=EDGE_SPP, seed=1, pixels=(p0, p0 + npix),
-                        edges=(0, npix * EDGE_SPP), n_threads=n_threads)
+        oracle.render(scene, spp=wl.spp, seed=1, max_depth=wl.depth, pixels=(p0, p0 + npix), n_threads=n_threads)
+        oracle.backward(scene, w, spp=wl.spp, edge_spp=wl.edge_spp, seed=1, max_depth=wl.depth,
+                        pixels=(p0, p0 + npix), edges=(0, npix * wl.edge_spp), n_threads=n_threads)
         return time.perf_counter() - t
 
-    n = 4
-    dt = run(n)
-    while dt < 0.15 * seconds_target and n < 4096:
+    if n_fixed:
+        n = n_fixed
+        dt = run(n)
+    else:
+        n = max(1, n_threads)
+        dt = run(n)
+    while not n_fixed and dt < 0.15 * seconds_target and n < 4096:
         n *= 4
         dt = run(n)
-    if dt < seconds_target and n < 4096:
+    if not n_fixed and dt < seconds_target and n < 4096:
         n2 = int(min(4096, n * seconds_target / max(dt, 1e-3)))
         if n2 > n:
             n, dt = n2, run(n2)
-    samples = n * SPP
-    desc = ("oracle, %d pixels x %d spp (render + backward with all terms) + %d primary edge samples of the "
-            "256x256 workload, brute-force intersection over 5124 triangles" % (n, SPP, n * EDGE_SPP))
-    return samples / dt, desc, n_threads, dt
+    samples = n * wl.spp
+    desc = ("oracle, %d pixels x %d spp (render + backward with all terms, depth %d) + %d primary edge samples of "
+            "the %dx%d workload, brute-force intersection over %d triangles"
+            % (n, wl.spp, wl.depth, n * wl.edge_spp, W, H, len(scene.tris)))
+    return samples / dt, desc, n_threads, dt, n
 
 
-def bench_config(triangles, world):
-    return {"workload": WORKLOAD, "width": W_IMG, "height": H_IMG, "spp": SPP, "edge_spp": EDGE_SPP,
-            "triangles": triangles, "bvh_leaf_size": BVH_LEAF, "l2": "flushed between timed steps (256 MiB write)",
+def bench_config(wl, triangles, world):
+    return {"workload": wl.desc, "width": 512 if wl.key == "procedural" else 256,
+            "height": 512 if wl.key == "procedural" else 256, "spp": wl.spp, "edge_spp": wl.edge_spp,
+            "max_depth": wl.depth, "triangles": triangles, "bvh_leaf_size": wl.leaf,
+            "l2": "flushed between timed steps (256 MiB write); the step's working set (tape, sort and "
+                  "secondary scratch) is also larger than L2",
             "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
@@ -327,19 +376,21 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
-    from paper_1904_12228_gb300 import scenegen as sg
     oracle.build()
     cores = oracle.n_threads_default()
+    # every step runs the same bounded sample, sized once so that the whole
+    # run takes about 150 s of CPU work
     per_step = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    _, _, _, _, n = cpu_workload_sample(HEADLINE, per_step, cores)
     vals, times = [], []
     desc = ""
     for i in range(args.warmup + args.steps):
-        v, desc, cores, dt = cpu_workload_sample(per_step, cores)
+        v, desc, cores, dt, _ = cpu_workload_sample(HEADLINE, per_step, cores, n_fixed=n)
         if i >= args.warmup:
             vals.append(v)
             times.append(dt * 1e3)
     value = statistics.median(vals)
-    config = bench_config(len(sg.direct_lighting(SCENE_SEED).tris), world)
+    config = bench_config(HEADLINE, len(HEADLINE.scene().tris), world)
     config["sample"] = desc
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(times),
@@ -350,84 +401,86 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal variance x time part")
-    ap.add_argument("--no-batched", action="store_true", help="skip the 64-scene batched workload")
-    ap.add_argument("--no-hierarchy", action="store_true",
-                    help="skip the secondary-edge sampler comparison (hierarchy, point sampling, length)")
-    args = ap.parse_args()
-    args.warmup = max(args.warmup, 3)
-    from paper_1904_12228_gb300 import replicas
-    rank, world, local = replicas.rank_info()
-    if args.impl == "reference":
-        return run_reference(args, rank, world)
+def kernel_rooflines(prof, cnt, steps, peak_ops, peak_l2):
+    """Per ray kernel: algorithmic lane-operations and bytes per launch over
+    its mean event-timed launch, against the measured FMA and L2 peaks."""
+    out = {}
+    for name, (ms, launches) in prof.items():
+        slot = COUNTER_OF.get(name)
+        c = cnt.get(slot) if slot else None
+        if not c or c["nodes"] == 0 or launches == 0:
+            continue
+        per_step = max(1, round(launches / steps))
+        avg_s = ms / launches / 1e3
+        ops = (OPS_PER_BOX * BOXES_PER_NODE * c["nodes"] + OPS_PER_TRI * c["tris"]) / per_step
+        nbytes = (BYTES_PER_NODE * c["nodes"] + BYTES_PER_TRI * c["tris"]) / per_step
+        a_ops, a_l2 = ops / avg_s, nbytes / avg_s
+        out[name] = {"avg_launch_ms": avg_s * 1e3, "launches_per_step": per_step,
+                     "node_visits_per_launch": c["nodes"] / per_step, "tri_tests_per_launch": c["tris"] / per_step,
+                     "alu": {"achieved": a_ops / 1e12, "peak": peak_ops / 1e12, "unit": "T lane-ops/s",
+                             "frac": a_ops / peak_ops},
+                     "l2": {"achieved": a_l2 / 1e9, "peak": peak_l2 / 1e9, "unit": "GB/s", "frac": a_l2 / peak_l2}}
+    return out
 
+
+def run_workload(ctx, dev, wl, steps, warmup, rank, world, dist, flush, timed_extras=True):
+    """Time `steps` fwd+bwd steps of workload wl (inputs resident in HBM),
+    then one counted step, then the same step end to end with host buffers."""
     import numpy as np
     import torch
-
     from paper_1904_12228_gb300 import drt
+    from paper_1904_12228_gb300 import replicas
     from paper_1904_12228_gb300 import scenegen as sg
-
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    dev = torch.device("cuda", local)
-    ctx = drt.Context(local)
-    scene_seed, adjoint_seed = replicas.replica_seeds(SCENE_SEED, 1, rank)
-    scene = sg.direct_lighting(scene_seed)
-    S = drt.Scene.from_arrays(ctx, scene, bvh_leaf_size=BVH_LEAF)
+    scene_seed, adjoint_seed = replicas.replica_seeds(wl.seed, 1, rank)
+    scene = wl.scene(scene_seed)
+    W, H = scene.width, scene.height
+    S = drt.Scene.from_arrays(ctx, scene, bvh_leaf_size=wl.leaf)
     V, T = len(scene.verts), len(scene.tris)
     verts = torch.from_numpy(scene.verts).to(dev)
-    d_image = torch.from_numpy(sg.loss_adjoint(adjoint_seed, W_IMG, H_IMG)).to(dev)
-    image = torch.zeros((H_IMG, W_IMG, 3), device=dev)
+    d_image = torch.from_numpy(sg.loss_adjoint(adjoint_seed, W, H)).to(dev)
+    image = torch.zeros((H, W, 3), device=dev)
     g = dict(d_verts=torch.zeros((V, 3), device=dev), d_albedo=torch.zeros((T, 3), device=dev),
              d_radiance=torch.zeros(3, device=dev), d_cam_to_world=torch.zeros((3, 4), device=dev),
              d_cam_scale=torch.zeros(1, device=dev))
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
-    tape = S.render(image, drt.make_opts(SPP, EDGE_SPP, seed=0), want_tape=True)
-    n_samples = W_IMG * H_IMG * SPP
+    opts0 = drt.make_opts(wl.spp, wl.edge_spp, max_depth=wl.depth, seed=0)
+    tape = S.render(image, opts0, want_tape=True)
+    n_samples = W * H * wl.spp
 
     def step(k):
-        opts = drt.make_opts(SPP, EDGE_SPP, seed=1000 + k)
+        opts = drt.make_opts(wl.spp, wl.edge_spp, max_depth=wl.depth, seed=1000 + k)
         S.update_vertices(verts)
         S.render(image, opts, reuse=tape)
         S.backward(d_image, opts, tape=tape, **g)
 
-    for k in range(args.warmup):
+    for k in range(warmup):
         step(k)
     torch.cuda.synchronize()
     code, info = ctx.check_device()
     if code != 0:
         raise RuntimeError("device error flag %d (%d) during warm-up" % (code, info))
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ctx.profile(True)
     ctx.profile_read()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clocks:
-        for k in range(args.steps):
+    with ClockSampler(dev.index or 0) as clocks:
+        for k in range(steps):
             flush.zero_()                      # L2 flush between timed steps (not timed)
             starts[k].record()
-            step(args.warmup + k)
+            step(warmup + k)
             ends[k].record()
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
     prof = ctx.profile_read()
     ctx.profile(False)
+    code, info = ctx.check_device()
+    if code != 0:
+        raise RuntimeError("device error flag %d (%d) in the timed steps" % (code, info))
     total_ms = replicas.max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), dist, dev)
-    ms_per_step = total_ms / args.steps
+    ms_per_step = total_ms / steps
     value = replicas.aggregate_throughput(n_samples, world, ms_per_step)
 
     # work counters of one extra (untimed) step
@@ -438,35 +491,17 @@ def main():
     ctx.counters(False)
     rays = sum(c["closest_rays"] + c["shadow_rays"] for c in cnt.values())
 
-    # dominant kernel and its roofline
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    dom_name, (dom_ms, dom_launches) = dom
-    avg_ms = dom_ms / dom_launches
-    c = cnt.get(dom_name)
-    roof = None
-    if c:
-        ops = OPS_PER_NODE * c["nodes"] + OPS_PER_TRI * c["tris"]
-        achieved = ops / (avg_ms / 1e3) / 1e12
-        peak = peak_alu_tops()
-        traffic = ncu_traffic(dom_name)
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": dom_name, "avg_launch_ms": avg_ms,
-                "algorithmic_ops_per_launch": ops,
-                "l1l2_bytes_per_launch": 64 * c["nodes"] + 48 * c["tris"],
-                "peak_note": "152 SMs x 128 FP32 lanes x 2070 MHz (recipe unit counts and max clock)"}
-    gpu_launches = sum(v[1] for v in prof.values())
-
     # end to end through the API with host buffers
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
     h_verts = pin(scene.verts)
     h_dimg = pin(d_image.cpu().numpy())
-    h_img = torch.zeros((H_IMG, W_IMG, 3)).pin_memory()
+    h_img = torch.zeros((H, W, 3)).pin_memory()
     hg = dict(d_verts=torch.zeros((V, 3)).pin_memory(), d_albedo=torch.zeros((T, 3)).pin_memory(),
               d_radiance=torch.zeros(3).pin_memory(), d_cam_to_world=torch.zeros((3, 4)).pin_memory(),
               d_cam_scale=torch.zeros(1).pin_memory())
 
     def e2e_step(k):
-        opts = drt.make_opts(SPP, EDGE_SPP, seed=2000 + k)
+        opts = drt.make_opts(wl.spp, wl.edge_spp, max_depth=wl.depth, seed=2000 + k)
         S.update_vertices(h_verts)
         S.render(h_img, opts, reuse=tape)
         S.backward(h_dimg, opts, tape=tape, **hg)
@@ -474,15 +509,141 @@ def main():
     for k in range(2):
         e2e_step(k)
     torch.cuda.synchronize()
-    ke = max(3, args.steps // 4)
+    ke = max(3, steps // 4)
     t0 = time.perf_counter()
     for k in range(ke):
         e2e_step(k)
     torch.cuda.synchronize()
     e2e_ms = replicas.max_over_ranks((time.perf_counter() - t0) * 1e3 / ke, dist, dev)
     grad_bytes = 4 * (3 * V + 3 * T + 3 + 12 + 1)
-    h2d = 12 * V + 12 * W_IMG * H_IMG + grad_bytes
-    d2h = 12 * W_IMG * H_IMG + grad_bytes
+    h2d = 12 * V + 12 * W * H + grad_bytes
+    d2h = 12 * W * H + grad_bytes
+    tape.free()
+    S.free()
+    return {"scene": scene, "triangles": T, "ms_per_step": ms_per_step, "value": value, "prof": prof,
+            "counters": cnt, "rays": rays, "clocks": clocks.summary(),
+            "e2e": {"value": replicas.aggregate_throughput(n_samples, world, e2e_ms), "unit": UNIT,
+                    "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": sum(v[1] for v in prof.values())}
+
+
+def roofline_of(res, steps, peaks, wl):
+    kr = kernel_rooflines(res["prof"], res["counters"], steps, peaks["alu_ops"], peaks["l2_bytes"])
+    dom_name, (dom_ms, dom_launches) = max(res["prof"].items(), key=lambda kv: kv[1][0])
+    if dom_name not in kr:
+        return None, kr
+    k = kr[dom_name]
+    binding = "alu" if k["alu"]["frac"] >= k["l2"]["frac"] else "l2"
+    b = k[binding]
+    roof = {"bound": binding, "achieved": b["achieved"], "peak": b["peak"], "unit": b["unit"], "frac": b["frac"],
+            "traffic": ncu_traffic(wl.key, dom_name), "kernel": dom_name, "avg_launch_ms": k["avg_launch_ms"],
+            "share_of_step": dom_ms / steps / res["ms_per_step"],
+            "alu": k["alu"], "l2": k["l2"],
+            "algorithmic_ops_per_launch": OPS_PER_BOX * BOXES_PER_NODE * k["node_visits_per_launch"]
+            + OPS_PER_TRI * k["tri_tests_per_launch"],
+            "algorithmic_bytes_per_launch": BYTES_PER_NODE * k["node_visits_per_launch"]
+            + BYTES_PER_TRI * k["tri_tests_per_launch"],
+            "work_units": "12 lane-ops per ray-box slab test (2 per BVH node visit) + 26 per watertight triangle "
+                          "test; 64 B per node visit + 48 B per triangle test; from the kernel's work counters",
+            "peak_note": "peaks of measured: FP32 FMA lane-op rate (drt_probe_fma) and L2-resident copy "
+                         "bandwidth (drt_probe_l2), same run; binding resource = the larger fraction"}
+    return roof, kr
+
+
+def run_mlp_rate(ctx, dev, m=1 << 22):
+    """BF16 tensor-core rate of the edge-proposal network (tcgen05, FP32
+    accumulation) on m rows: forward and backward, best of 5 launches each."""
+    import torch
+    from paper_1904_12228_gb300 import proposal
+    net = proposal.EdgeProposal(ctx, seed=1)
+    g = torch.Generator(device="cpu").manual_seed(2)
+    x = torch.randn((m, proposal.N_IN), generator=g).to(dev).to(torch.bfloat16).view(torch.int16).contiguous()
+    y = torch.empty(m, device=dev)
+    target = torch.randn(m, device=dev)
+    mask = torch.ones(m, device=dev)
+    loss = torch.zeros(1, device=dev)
+
+    def best(f):
+        f()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            f()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return min(ts)
+
+    fwd_ms = best(lambda: ctx.mlp_forward(x, net._w, y))
+    bwd_ms = best(lambda: ctx.mlp_backward(x, target, mask, 1.0 / m, net._w, net._gp, loss))
+    i, h = proposal.N_IN, proposal.HIDDEN
+    fwd_tc = 2.0 * m * (i * h + h * h)                    # the two tensor-core layers
+    bwd_tc = 2.0 * m * (i * h + h * h) + 2.0 * m * (h * h) + 2.0 * m * (h * h + i * h)  # recompute, dz1, dW2, dW1
+    peak = measured_peaks().get("bf16_tflops")
+    out = {"rows": m, "forward_ms": fwd_ms, "backward_ms": bwd_ms,
+           "forward_tflops": fwd_tc / (fwd_ms * 1e-3) / 1e12, "backward_tflops": bwd_tc / (bwd_ms * 1e-3) / 1e12,
+           "input_gbs_forward": m * i * 2 / (fwd_ms * 1e-3) / 1e9,
+           "peak_bf16_tflops": peak, "peak_note": "bf16_tflops of measured (cuBLAS burst)",
+           "flops_note": "tensor-core flops only: 2 m (32x64 + 64x64) forward; backward adds the recompute, "
+                         "dz1 = dz2 W2 and the weight gradients dW2, dW1"}
+    if peak:
+        out["forward_frac"] = out["forward_tflops"] / peak
+        out["backward_frac"] = out["backward_tflops"] / peak
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal variance x time part")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-scene batched workload")
+    ap.add_argument("--no-hierarchy", action="store_true",
+                    help="skip the secondary-edge sampler comparison (hierarchy, point sampling, length)")
+    ap.add_argument("--no-direct", action="store_true", help="skip the direct-lighting workload")
+    ap.add_argument("--workload", default="procedural", choices=sorted(WORKLOADS),
+                    help="the timed workload (default: the 512x512 ~200k-triangle depth-3 scene)")
+    args = ap.parse_args()
+    global HEADLINE
+    HEADLINE = WORKLOADS[args.workload]
+    args.warmup = max(args.warmup, 3)
+    from paper_1904_12228_gb300 import replicas
+    rank, world, local = replicas.rank_info()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+
+    from paper_1904_12228_gb300 import drt
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    ctx = drt.Context(local)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = {"alu_ops": ctx.probe_fma(), "l2_bytes": ctx.probe_l2(32 << 20), "sms": sms}
+
+    res = run_workload(ctx, dev, HEADLINE, args.steps, args.warmup, rank, world, dist, flush)
+    roof, kroof = roofline_of(res, args.steps, peaks, HEADLINE)
+
+    direct = None
+    if rank == 0 and world == 1 and not args.no_direct:
+        d = run_workload(ctx, dev, DIRECT, args.steps, args.warmup, 0, 1, None, flush)
+        droof, dk = roofline_of(d, args.steps, peaks, DIRECT)
+        direct = {"workload": DIRECT.desc, "triangles": d["triangles"], "ms_per_step": d["ms_per_step"],
+                  "samples_per_s": d["value"], "rays_per_s": d["rays"] / (d["ms_per_step"] / 1e3),
+                  "e2e": d["e2e"], "roofline": droof, "kernels_roofline": dk, "clocks": d["clocks"],
+                  "kernels": {k: {"ms_total": v[0], "launches": v[1]} for k, v in d["prof"].items()}}
 
     # the 64-scene batch (N=1 only), and the same with small scenes, where
     # per-call overheads dominate separate calls
@@ -496,34 +657,34 @@ def main():
         sec_h = run_secondary_samplers(ctx, dev)
 
     # second half of the metric: gradient variance x time, learned proposal
-    # against the plain edge sampler (N=1 only)
-    vxt = None
+    # against the plain edge sampler (N=1 only), and the network's BF16 rate
+    vxt = mlp = None
     if rank == 0 and world == 1 and not args.no_proposal:
         from paper_1904_12228_gb300 import proposal
         vxt = proposal.protocol(ctx)
+        mlp = run_mlp_rate(ctx, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
-        v, desc, cores, dt = cpu_workload_sample(args.cpu_seconds, oracle.n_threads_default())
+        v, desc, cores, dt, _ = cpu_workload_sample(HEADLINE, args.cpu_seconds, oracle.n_threads_default())
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc, "seconds": dt}
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": bench_config(T, world),
-                "rays_per_s": world * rays / (ms_per_step / 1e3),
-                "roofline": roof, "cpu_baseline": cpu, "variance_x_time": vxt, "batched": batched,
-                "batched_small": batched_small,
-                "secondary_samplers": sec_h,
-                "e2e": {"value": replicas.aggregate_throughput(n_samples, world, e2e_ms), "unit": UNIT,
-                        "ms_per_step": e2e_ms,
-                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "gpu_launches": gpu_launches,
-                "kernels": {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items()},
-                "counters": cnt, "clocks": clocks.summary(),
-                "peaks": {k: measured_peaks().get(k) for k in ("hbm_gbs", "bf16_tflops")}}
+        mp = measured_peaks()
+        line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": bench_config(HEADLINE, res["triangles"], world),
+                "rays_per_s": world * res["rays"] / (res["ms_per_step"] / 1e3),
+                "roofline": roof, "kernels_roofline": kroof, "cpu_baseline": cpu, "e2e": res["e2e"],
+                "gpu_launches": res["gpu_launches"],
+                "kernels": {k: {"ms_total": v[0], "launches": v[1]} for k, v in res["prof"].items()},
+                "counters": res["counters"], "clocks": res["clocks"],
+                "direct_lighting": direct, "variance_x_time": vxt, "mlp": mlp, "batched": batched,
+                "batched_small": batched_small, "secondary_samplers": sec_h,
+                "peaks": {"fma_lane_ops_per_s": peaks["alu_ops"], "l2_bytes_per_s": peaks["l2_bytes"],
+                          "sms": sms, "hbm_gbs": mp.get("hbm_gbs"), "bf16_tflops": mp.get("bf16_tflops")}}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

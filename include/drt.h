@@ -136,6 +136,15 @@ typedef struct {
                            a Lambertian surface is the cosine itself), closed-form CDF and
                            inverse, mixed 1/4 with uniform so every point keeps a positive
                            density.  A batch takes 0 only. */
+  int32_t pix_begin, pix_end;   /* backward: evaluate the interior and secondary terms only for the
+                                   samples of pixels p (row-major index) with pix_begin <= p < pix_end;
+                                   pix_end <= 0 selects every pixel.  With the edge range below, a
+                                   full-size gradient can be checked entry by entry against a
+                                   reference that evaluates the same samples one by one */
+  int64_t edge_begin, edge_end; /* backward: evaluate only the primary edge samples with index j,
+                                   edge_begin <= j < edge_end (the index that selects the sample's
+                                   random numbers, before the samples are sorted by screen position);
+                                   edge_end <= 0 selects every sample */
 } drt_render_opts;
 
 /* Gradient outputs: device or host arrays, each may be NULL (not wanted).
@@ -206,6 +215,12 @@ drt_status drt_tape_free(drt_context* ctx, drt_tape* tape);
  * drt_render_backward, except:
  *   - d_image and every non-NULL gradient array must be device memory (no
  *     host staging); otherwise DRT_ERR_INVALID_ARG.
+ *   - Only the length proposal for primary edges: opts->proposal != 0 is
+ *     DRT_ERR_INVALID_ARG (the mixture proposals build their CDF in
+ *     scene-owned buffers that grow on demand).
+ *   - With the edge hierarchy (sec_sampler 1) the hierarchy's buffers must
+ *     exist from an earlier drt_render_backward with it on this scene, else
+ *     DRT_ERR_STATE; a scene changed since is rebuilt in place.
  *   - The scratch (one row of 16 partial sums per thread block, plus the
  *     totals of the first reduction stage) is a fixed array of 2^22 floats
  *     (16 MiB) compiled into the library, which every GPU that loads the
@@ -213,9 +228,10 @@ drt_status drt_tape_free(drt_context* ctx, drt_tape* tape);
  *     512x512 image at 64 spp and 64 edge samples per pixel needs 98304.
  *     Larger jobs are rejected with DRT_ERR_INVALID_ARG and a message
  *     giving the sizes.
- *   - The first call on a device looks up the array's device address with
- *     cudaGetSymbolAddress (the context's device must be current); make that
- *     first call before any stream capture.
+ *   - Every call made outside stream capture looks up the array's device
+ *     address with cudaGetSymbolAddress (the context's device must be
+ *     current); a call during capture uses the last address found, so make
+ *     the first call on a device before any stream capture.
  *   - All calls share the one array, and every call overwrites the rows it
  *     reads before reading them; calls that overlap on the GPU (other streams,
  *     other threads) race on it and must be serialised by the caller. */
@@ -368,6 +384,20 @@ drt_status drt_profile_read(drt_context* ctx, int max, char* names, double* ms, 
  * [5][4] counts to out and resets them. */
 drt_status drt_counters_enable(drt_context* ctx, int enable);
 drt_status drt_counters_read(drt_context* ctx, int64_t* out);
+
+/* Peak probes: measurement aids for the rooflines of the ray kernels (not
+ * part of the method; the paper has no counterpart).  Both allocate a small
+ * device buffer, run on `stream`, synchronise it and return the best of five
+ * event-timed launches.
+ * drt_probe_fma: FP32 lane-operations per second of a kernel running eight
+ *   independent FMA chains per thread at 2048 threads per SM (each FMA
+ *   counts as one lane-operation).
+ * drt_probe_l2: bytes per second (read + write) of a copy between two
+ *   buffers of bytes/2 each, 64 passes per launch, loads and stores cached
+ *   in L2 only; bytes in [1 MiB, 1 GiB] (choose it well below the L2 size to
+ *   measure L2).  Errors: DRT_ERR_INVALID_ARG, DRT_ERR_OOM, DRT_ERR_CUDA. */
+drt_status drt_probe_fma(drt_context* ctx, double* lane_ops_per_s, void* stream);
+drt_status drt_probe_l2(drt_context* ctx, int64_t bytes, double* bytes_per_s, void* stream);
 
 /* Synchronise stream and read the device error flag: DRT_OK, or
  * DRT_ERR_DEVICE_FLAG with *code / *info (may be NULL) set and the flag

@@ -119,7 +119,7 @@ def render(scene, *, spp: int, seed: int, max_depth: int = 1, primary_only: bool
 def backward(scene, d_image: np.ndarray, *, spp: int, edge_spp: int, seed: int, max_depth: int = 1,
              primary_only: bool = False, terms: int = TERMS_ALL, eps_rel: float = EPS_REL, pixels=None,
              edges=None, n_threads=None, scene_id: int = 0, proposal_weights=None, proposal_scores=None,
-             sec_tree_samples: int = 0, sec_point: int = 0):
+             sec_tree_samples: int = 0, sec_point: int = 0, contributions: bool = False):
     """Gradient of sum(d_image * image) as a flat FP64 vector, and per entry
     the magnitude of the terms summed into it (absolute-value chain rule),
     which scales the rounding error an FP32 implementation may make.
@@ -129,7 +129,10 @@ def backward(scene, d_image: np.ndarray, *, spp: int, edge_spp: int, seed: int, 
     s_k clamped to [-40, 40].  sec_tree_samples > 0 picks secondary edges
     through the edge hierarchy with that many root samples (else by length).
     sec_point = 1 samples the point on a secondary edge by the clamped-cosine
-    density over the edge's arc, mixed with uniform (else uniform)."""
+    density over the edge's arc, mixed with uniform (else uniform).
+    contributions=True also returns, per entry, the sum over samples of the
+    magnitude of each sample's whole contribution, sum_k |c_k| (a third
+    array)."""
     if proposal_weights is not None and proposal_scores is not None:
         raise ValueError("give proposal_weights or proposal_scores, not both")
     P = _Pinned(scene)
@@ -143,11 +146,13 @@ def backward(scene, d_image: np.ndarray, *, spp: int, edge_spp: int, seed: int, 
     n = num_params(scene)
     g = np.zeros(n, np.float64)
     a = np.zeros(n, np.float64)
-    rc = lib().or_backward(ctypes.byref(P.s), ctypes.byref(o), w.ctypes.data_as(ctypes.c_void_p),
-                           g.ctypes.data_as(ctypes.c_void_p), a.ctypes.data_as(ctypes.c_void_p))
+    c = np.zeros(n, np.float64) if contributions else None
+    rc = lib().or_backward3(ctypes.byref(P.s), ctypes.byref(o), w.ctypes.data_as(ctypes.c_void_p),
+                            g.ctypes.data_as(ctypes.c_void_p), a.ctypes.data_as(ctypes.c_void_p),
+                            c.ctypes.data_as(ctypes.c_void_p) if c is not None else None)
     if rc != 0:
         raise RuntimeError("oracle backward failed (%d)" % rc)
-    return g, a
+    return (g, a, c) if contributions else (g, a)
 
 
 def edge_point(p, n, v0, v1, u: float, usel: float):

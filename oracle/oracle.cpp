@@ -719,13 +719,17 @@ struct Ctx {
   double* g;             /* gradient accumulator [P] */
   double* ga;            /* sum of |contribution| per parameter [P] */
   const EdgeTree* tree = nullptr;  /* secondary edge hierarchy (sec_sampler 1) */
+  double* gc = nullptr;  /* sum over accumulate calls of |coef x'| per parameter [P] (or null) */
 };
 
-/* grad += coef * x';  tolerance scale += coef_abs * |x|' (see Dual). */
+/* grad += coef * x';  tolerance scale += coef_abs * |x|' (see Dual).  Each
+ * call adds one sample's contribution c_k (an interior path sample, a primary
+ * edge sample, or a secondary edge sample); gc, if given, sums |c_k|. */
 void accumulate(Ctx& C, double coef, double coef_abs, const Dual& x) {
   for (int i = 0; i < x.n; ++i) {
     C.g[x.idx[i]] += coef * x.d[i];
     C.ga[x.idx[i]] += coef_abs * x.ad[i];
+    if (C.gc) C.gc[x.idx[i]] += std::fabs(coef * x.d[i]);
   }
 }
 
@@ -1372,13 +1376,18 @@ int or_render(const or_scene_t* sc, const or_opts_t* op, double* image) {
 /* Gradient of sum_p w_p . I_p into grad[P] (FP64), and into abs_grad[P] the
  * magnitude of the terms that were summed (absolute-value chain rule, see
  * Dual) -- the scale of the rounding error an FP32 evaluation may make.
- * Both are overwritten. */
-int or_backward(const or_scene_t* sc, const or_opts_t* op, const float* d_image, double* grad, double* abs_grad) {
+ * If contrib_abs is non-null it receives per entry sum_k |c_k| over the
+ * samples' whole contributions c_k (the plain sum-of-magnitudes scale, which
+ * the chain rule with absolute values bounds from above).  All outputs are
+ * overwritten. */
+int or_backward3(const or_scene_t* sc, const or_opts_t* op, const float* d_image, double* grad, double* abs_grad,
+                 double* contrib_abs) {
   Prep P;
   prepare(sc, P);
   int NP = P.P;
   int nt = std::max(1, op->n_threads);
   std::vector<std::vector<double>> g(nt, std::vector<double>(NP, 0.0)), ga(nt, std::vector<double>(NP, 0.0));
+  std::vector<std::vector<double>> gc(contrib_abs ? nt : 0, std::vector<double>(NP, 0.0));
   g_dual_overflow = false;
   int npix = sc->width * sc->height;
   EdgeTree tree;
@@ -1386,7 +1395,7 @@ int or_backward(const or_scene_t* sc, const or_opts_t* op, const float* d_image,
   if (op->terms & 5) {
     int pb = op->pix_begin, pe = op->pix_end > 0 ? op->pix_end : npix;
     parallel_for(pb, pe, nt, [&](int tid, int64_t b, int64_t e) {
-      Ctx C{&P, op, true, d_image, g[tid].data(), ga[tid].data(), &tree};
+      Ctx C{&P, op, true, d_image, g[tid].data(), ga[tid].data(), &tree, contrib_abs ? gc[tid].data() : nullptr};
       for (int64_t pix = b; pix < e; ++pix) {
         const float* w = d_image + 3 * pix;
         double ws[3] = {w[0] / (double)op->spp, w[1] / (double)op->spp, w[2] / (double)op->spp};
@@ -1411,16 +1420,22 @@ int or_backward(const or_scene_t* sc, const or_opts_t* op, const float* d_image,
     int64_t N = (int64_t)op->edge_spp * npix;
     int64_t eb = op->edge_begin, ee = op->edge_end > 0 ? op->edge_end : N;
     parallel_for(eb, ee, nt, [&](int tid, int64_t b, int64_t e) {
-      Ctx C{&P, op, true, d_image, g[tid].data(), ga[tid].data()};
+      Ctx C{&P, op, true, d_image, g[tid].data(), ga[tid].data(), nullptr, contrib_abs ? gc[tid].data() : nullptr};
       for (int64_t j = b; j < e; ++j) primary_edge_sample(C, j);
     });
   }
   for (int i = 0; i < NP; ++i) {
-    double s = 0.0, a = 0.0;
+    double s = 0.0, a = 0.0, c = 0.0;
     for (int t = 0; t < nt; ++t) { s += g[t][i]; a += ga[t][i]; }
+    if (contrib_abs)
+      for (int t = 0; t < nt; ++t) c += gc[t][i];
     grad[i] = s; abs_grad[i] = a;
+    if (contrib_abs) contrib_abs[i] = c;
   }
   return g_dual_overflow ? 2 : 0;
+}
+int or_backward(const or_scene_t* sc, const or_opts_t* op, const float* d_image, double* grad, double* abs_grad) {
+  return or_backward3(sc, op, d_image, grad, abs_grad, nullptr);
 }
 
 /* Self-check of the two secondary-edge measures at one edge point: for a

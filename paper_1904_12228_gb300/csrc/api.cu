@@ -160,18 +160,13 @@ drt_status make_opts(const drt_render_opts* o, drt::Opts* op) {
   op->sec_sampler = o->sec_sampler;
   op->sec_point = o->sec_point;
   op->sec_samples = o->sec_tree_samples > 0 ? o->sec_tree_samples : drt::kEtDefaultSamples;
-  // DRT_DEBUG_RANGES="pix_begin,pix_end,edge_begin,edge_end" restricts which
-  // samples the backward pass evaluates (for bisecting against the oracle)
-  op->pix_begin = 0;
-  op->pix_end = INT32_MAX;
-  op->edge_begin = 0;
-  op->edge_end = INT64_MAX;
-  if (const char* r = std::getenv("DRT_DEBUG_RANGES")) {
-    long long a = 0, b = 0, c = 0, d = 0;
-    if (std::sscanf(r, "%lld,%lld,%lld,%lld", &a, &b, &c, &d) == 4) {
-      op->pix_begin = (int)a; op->pix_end = (int)b; op->edge_begin = c; op->edge_end = d;
-    }
-  }
+  // which samples the backward pass evaluates (all by default)
+  if (o->pix_begin < 0 || o->edge_begin < 0)
+    return fail(DRT_ERR_INVALID_ARG, "pix_begin and edge_begin must be >= 0");
+  op->pix_begin = o->pix_begin;
+  op->pix_end = o->pix_end > 0 ? o->pix_end : INT32_MAX;
+  op->edge_begin = o->edge_begin;
+  op->edge_end = o->edge_end > 0 ? o->edge_end : INT64_MAX;
   return DRT_OK;
 }
 

@@ -13,6 +13,7 @@
 // arrays only.  Without scratch for them, it evaluates the primary edge
 // samples in sample order and the secondary edge samples inside the pixel
 // passes (same arithmetic, other order of the floating-point sums).
+#include <atomic>
 #include <climits>
 #include <cstdint>
 #include <cstdio>
@@ -31,8 +32,12 @@ constexpr int64_t kNoAllocMaxFloats = int64_t(1) << 22;
 // Shared by every call on a device and kept until the process exits.
 static __device__ __align__(256) float g_backward_scratch[kNoAllocMaxFloats];
 
+// Device address of the array per device, looked up again on every call made
+// outside stream capture (so a device whose primary context was destroyed and
+// created again gets the new address); during capture the last address is
+// used, which is why the first call on a device must come before any capture.
 constexpr int kMaxDevices = 64;
-float* g_scratch_addr[kMaxDevices] = {nullptr};
+std::atomic<float*> g_scratch_addr[kMaxDevices];
 
 bool is_device_array(const void* p) {
   if (!p) return true;
@@ -61,34 +66,12 @@ drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* s, const drt
     return fail_noalloc(DRT_ERR_INVALID_ARG, "NULL argument");
   }
   drt::Opts op;
-  // same option checks and defaults as drt_render_backward
-  if (opts->spp < 1 || opts->edge_spp < 0 || opts->max_depth < 1 || opts->max_depth > 8 || opts->terms < 0 ||
-      opts->terms > 7) {
-    return fail_noalloc(DRT_ERR_INVALID_ARG, "invalid render options");
-  }
-  op.spp = opts->spp;
-  op.edge_spp = opts->edge_spp;
-  op.max_depth = opts->max_depth;
-  op.primary_only = opts->primary_only ? 1 : 0;
-  op.terms = opts->terms == 0 ? 7 : opts->terms;
+  // the option checks and defaults of drt_render_backward
+  drt_status so = drt::convert_opts(opts, &op);
+  if (so != DRT_OK) return so;
   if (opts->proposal != 0) return fail_noalloc(DRT_ERR_INVALID_ARG, "drt_render_backward_noalloc supports proposal 0");
   op.proposal = 0;
   op.seg_log = nullptr;
-  op.key = make_uint2((uint32_t)opts->seed, (uint32_t)(opts->seed >> 32));
-  if (opts->scene_id < 0) return fail_noalloc(DRT_ERR_INVALID_ARG, "scene_id must be >= 0");
-  op.scene_id = (uint32_t)opts->scene_id;
-  op.eps_rel = opts->eps_rel > 0.0f ? opts->eps_rel : 1.52587890625e-05f;
-  if (opts->sec_sampler < 0 || opts->sec_sampler > 1 || opts->sec_tree_samples < 0 ||
-      opts->sec_tree_samples > drt::kEtMaxSamples || opts->sec_point < 0 || opts->sec_point > 1) {
-    return fail_noalloc(DRT_ERR_INVALID_ARG, "invalid secondary edge sampler options");
-  }
-  op.sec_sampler = opts->sec_sampler;
-  op.sec_point = opts->sec_point;
-  op.sec_samples = opts->sec_tree_samples > 0 ? opts->sec_tree_samples : drt::kEtDefaultSamples;
-  op.pix_begin = 0;
-  op.pix_end = INT32_MAX;
-  op.edge_begin = 0;
-  op.edge_end = INT64_MAX;
   if (!op.primary_only && op.max_depth > 1 && (op.terms & 5) && !tape) {
     return fail_noalloc(DRT_ERR_INVALID_ARG,
                         "interior or secondary terms with max_depth > 1 need the tape of the forward pass");
@@ -113,18 +96,25 @@ drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* s, const drt
                   (long long)drt::partial_floats(rows), (long long)kNoAllocMaxFloats);
     return fail_noalloc(DRT_ERR_INVALID_ARG, buf);
   }
-  // first call on this device: look up the device address of the array
+  // the device address of the array (a host-side name is not a device address)
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices || dev != ctx->device) {
     return fail_noalloc(DRT_ERR_STATE, "the context's device must be the current device");
   }
-  if (!g_scratch_addr[dev]) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    cs = cudaStreamCaptureStatusNone;
+  }
+  float* scratch = g_scratch_addr[dev].load();
+  if (cs == cudaStreamCaptureStatusNone || !scratch) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_backward_scratch);
     if (e != cudaSuccess || !p) {
       return fail_noalloc(DRT_ERR_CUDA, cudaGetErrorString(e));
     }
-    g_scratch_addr[dev] = static_cast<float*>(p);
+    scratch = static_cast<float*>(p);
+    g_scratch_addr[dev].store(scratch);
   }
   // the edge hierarchy's buffers come from an earlier backward; a scene that
   // changed since is rebuilt in place (kernel launches only)
@@ -139,7 +129,7 @@ drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* s, const drt
     }
   }
   cudaError_t e = drt::launch_backward(s, op, tape, d_image, grads->d_verts, grads->d_albedo, grads->d_radiance,
-                                       grads->d_cam_to_world, grads->d_cam_scale, g_scratch_addr[dev],
+                                       grads->d_cam_to_world, grads->d_cam_scale, scratch,
                                        nullptr, nullptr, (cudaStream_t)stream);
   if (e != cudaSuccess) {
     return fail_noalloc(DRT_ERR_CUDA, cudaGetErrorString(e));

@@ -26,7 +26,8 @@ EXPORTED = ("drt_create", "drt_destroy", "drt_scene_upload", "drt_scene_update_v
             "drt_last_error", "drt_version", "drt_debug_closest", "drt_profile_enable", "drt_profile_read",
             "drt_counters_enable", "drt_counters_read", "drt_render_backward_noalloc", "drt_scene_segments",
             "drt_mlp_forward", "drt_mlp_backward", "drt_adam_step", "drt_segment_features", "drt_batch_create",
-            "drt_batch_run", "drt_batch_get_info", "drt_batch_free", "drt_render_batch")
+            "drt_batch_run", "drt_batch_get_info", "drt_batch_free", "drt_render_batch", "drt_probe_fma",
+            "drt_probe_l2")
 BATCH_PASSES = ("render", "interior", "secondary", "path", "primary")
 
 
@@ -49,7 +50,9 @@ class RenderOpts(ctypes.Structure):
                 ("primary_only", ctypes.c_int32), ("seed", ctypes.c_uint64), ("eps_rel", ctypes.c_float),
                 ("terms", ctypes.c_int32), ("proposal", ctypes.c_int32), ("seg_weights", ctypes.c_void_p),
                 ("n_seg_weights", ctypes.c_int64), ("seg_log", ctypes.c_void_p), ("scene_id", ctypes.c_int32),
-                ("sec_sampler", ctypes.c_int32), ("sec_tree_samples", ctypes.c_int32), ("sec_point", ctypes.c_int32)]
+                ("sec_sampler", ctypes.c_int32), ("sec_tree_samples", ctypes.c_int32), ("sec_point", ctypes.c_int32),
+                ("pix_begin", ctypes.c_int32), ("pix_end", ctypes.c_int32), ("edge_begin", ctypes.c_int64),
+                ("edge_end", ctypes.c_int64)]
 
 
 class MlpWeights(ctypes.Structure):
@@ -128,6 +131,8 @@ def load(build_if_missing: bool = True):
         "drt_batch_get_info": ([vp, vp, ctypes.POINTER(BatchInfo)], i32),
         "drt_batch_free": ([vp, vp], i32),
         "drt_render_batch": ([vp, pp, i32, ctypes.POINTER(RenderOpts), pp, pp, ctypes.POINTER(Grads), vp], i32),
+        "drt_probe_fma": ([vp, ctypes.POINTER(ctypes.c_double), vp], i32),
+        "drt_probe_l2": ([vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), vp], i32),
         "drt_last_error": ([], ctypes.c_char_p),
         "drt_version": ([], ctypes.c_char_p),
     }
@@ -173,14 +178,17 @@ def _stream(stream):
 
 def make_opts(spp, edge_spp=None, max_depth=1, primary_only=False, seed=0, eps_rel=0.0, terms=0,
               seg_weights=None, seg_log=None, seg_scores=None, scene_id=0, sec_tree_samples=0,
-              sec_point=0) -> RenderOpts:
+              sec_point=0, pixels=None, edges=None) -> RenderOpts:
     """seg_weights: a CUDA float32 tensor of per-segment weights selects the
     mixture proposal 1; seg_scores: per-segment network scores select the
     mixture proposal 2.  The tensor must stay alive until the backward call
     returns.  sec_tree_samples > 0 picks secondary edges through the edge
     hierarchy with that many root samples (0: by 3D length).  sec_point=1
     samples the point on a secondary edge by the clamped-cosine density over
-    the edge's arc mixed with uniform (0: uniform)."""
+    the edge's arc mixed with uniform (0: uniform).  pixels=(begin, end) and
+    edges=(begin, end) restrict the backward pass to the interior and
+    secondary samples of those pixels and to those primary edge samples
+    (default: all)."""
     if seg_weights is not None and seg_scores is not None:
         raise ValueError("give seg_weights or seg_scores, not both")
     mode, w = (1, seg_weights) if seg_weights is not None else ((2, seg_scores) if seg_scores is not None else (0, None))
@@ -189,7 +197,9 @@ def make_opts(spp, edge_spp=None, max_depth=1, primary_only=False, seed=0, eps_r
                       int(seed) & (2 ** 64 - 1), float(eps_rel), int(terms), mode,
                       _ptr(w) if w is not None else None, n,
                       _ptr(seg_log) if seg_log is not None else None, int(scene_id),
-                      1 if sec_tree_samples > 0 else 0, int(sec_tree_samples), int(sec_point))
+                      1 if sec_tree_samples > 0 else 0, int(sec_tree_samples), int(sec_point),
+                      int(pixels[0]) if pixels else 0, int(pixels[1]) if pixels else 0,
+                      int(edges[0]) if edges else 0, int(edges[1]) if edges else 0)
 
 
 class Context:
@@ -251,6 +261,18 @@ class Context:
         return {nm: dict(closest_rays=int(a[i, 0]), shadow_rays=int(a[i, 1]), nodes=int(a[i, 2]), tris=int(a[i, 3]))
                 for i, nm in enumerate(self.COUNTER_SLOTS)}
 
+
+    def probe_fma(self, stream=None) -> float:
+        """Measured FP32 FMA lane-operations per second (synchronises)."""
+        v = ctypes.c_double()
+        _check(self.lib.drt_probe_fma(self.handle, ctypes.byref(v), _stream(stream)))
+        return v.value
+
+    def probe_l2(self, nbytes=32 << 20, stream=None) -> float:
+        """Measured L2 copy bandwidth in bytes/s over nbytes of buffers (synchronises)."""
+        v = ctypes.c_double()
+        _check(self.lib.drt_probe_l2(self.handle, int(nbytes), ctypes.byref(v), _stream(stream)))
+        return v.value
 
     def mlp_forward(self, x, w: "MlpWeights", y, stream=None):
         """y [m] = network(x [m,32] bf16); w holds device pointers."""

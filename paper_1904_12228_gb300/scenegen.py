@@ -256,6 +256,40 @@ def perturb_vertices(scene: Scene, seed: int, sigma: float = 0.02) -> np.ndarray
     return (scene.verts + rng.normal(0.0, sigma, size=scene.verts.shape)).astype(np.float32)
 
 
+def indirect_panel(view: str = "interior", width: int = 12, height: int = 12) -> Scene:
+    """A small scene for checking paths of two and three scattering vertices.
+
+    A floor (albedo 0.9) and a side wall are lit by a small area light above;
+    a panel hangs between the light and the floor, and a dark blocker
+    triangle (albedo 0.05) sits between panel and floor.  An orthographic
+    camera below the panel looks straight up at its underside, which the light
+    cannot reach directly: every pixel is lit through the floor and the wall
+    (two vertices) or through longer paths (three vertices: panel, floor,
+    wall).  view="interior": the window shows the panel's underside only, no
+    edge is in view, and the blocker acts through indirect shadows alone.
+    view="silhouette": the window is centred under the blocker, whose
+    silhouette against the panel is in view.  Both windows keep a margin of
+    at least 0.05 to the panel's edges and the blocker's corners, so a small
+    change of the window size brings no new edge into view."""
+    floor = quad((0, 0, 0), (2, 0, 0), (0, 0, -2))
+    panel = quad((0, 1.0, 0), (0.7, 0, 0), (0, 0, 0.7))
+    light = quad((0, 2.0, 0), (0.3, 0, 0), (0, 0, 0.3))
+    blocker = (np.array([[-0.5, 0.55, -0.3], [0.45, 0.5, 0.05], [-0.15, 0.6, 0.5]]), np.array([[0, 1, 2]]))
+    wall = quad((-1.2, 0.75, 0), (0, 0.75, 0), (0, 0, 1.0))
+    verts, tris = _merge([floor, panel, light, blocker, wall])
+    alb = np.full((len(tris), 3), 0.9)
+    alb[6] = 0.05
+    if view == "interior":
+        centre, half = (0.3, -0.35), 0.2
+    elif view == "silhouette":
+        centre, half = (-0.02, 0.1), 0.55
+    else:
+        raise ValueError("view must be 'interior' or 'silhouette'")
+    cam = look_at((centre[0], 0.05, centre[1]), (centre[0], 1.0, centre[1]), up=(0, 0, -1))
+    return Scene(verts=verts, tris=tris, albedo=alb, light_tris=[4, 5], radiance=[40, 40, 40], cam_to_world=cam,
+                 cam_scale=half, cam_type=CAM_ORTHO, width=width, height=height)
+
+
 def gi_panel(width: int = 16, height: int = 16) -> Scene:
     """A scene lit mostly indirectly: a floor (albedo 0.85) lit by a small
     area light, a panel above the floor whose underside the camera sees (it

@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 from paper_1904_12228_gb300 import scenegen as sg
+from parity import assert_grads
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -26,13 +27,8 @@ def env():
     return drt, drt.Context(0)
 
 
-def _assert_grads(got, want, absum, label=""):
-    err = np.abs(got - want)
-    bound = 1e-4 * np.abs(want) + 1e-6 * absum + 1e-12
-    bad = err > bound
-    i = int(np.argmax(err / bound))
-    assert not bad.any(), "%s: %d/%d entries off; worst entry %d got %g want %g (A=%g)" % (
-        label, bad.sum(), bad.size, i, got[i], want[i], absum[i])
+def _assert_grads(got, want, absum, label="", contrib=None):
+    assert_grads(got, want, absum, label, contrib)
 
 
 def _zeros(scene):
@@ -71,9 +67,9 @@ def test_point_sampling_gradient_matches_oracle(env, name, depth, terms, samples
     S.backward(torch.from_numpy(w).cuda(), opts, tape=tape, **g)
     torch.cuda.synchronize()
     assert ctx.check_device() == (0, 0)
-    want, absum = oracle.backward(scene, w, spp=6, edge_spp=6, seed=seed, max_depth=depth, terms=terms,
-                                  sec_tree_samples=samples, sec_point=1, n_threads=NT)
-    _assert_grads(_flat(g), want, absum, "%s depth %d terms %d S %d" % (name, depth, terms, samples))
+    want, absum, c = oracle.backward(scene, w, spp=6, edge_spp=6, seed=seed, max_depth=depth, terms=terms,
+                                     sec_tree_samples=samples, sec_point=1, n_threads=NT, contributions=True)
+    _assert_grads(_flat(g), want, absum, "point %s depth %d terms %d S %d" % (name, depth, terms, samples), c)
     # the importance-sampled point changes the estimate
     plain, _ = oracle.backward(scene, w, spp=6, edge_spp=6, seed=seed, max_depth=depth, terms=4,
                                sec_tree_samples=samples, n_threads=NT)
@@ -93,8 +89,9 @@ def test_noalloc_backward_with_point_sampling(env):
     S.backward_noalloc(w, opts, tape=tape, **got)
     torch.cuda.synchronize()
     assert ctx.check_device() == (0, 0)
-    want, absum = oracle.backward(scene, w.cpu().numpy(), spp=4, edge_spp=4, seed=8, sec_point=1, n_threads=NT)
-    _assert_grads(_flat(got), want, absum, "noalloc")
+    want, absum, c = oracle.backward(scene, w.cpu().numpy(), spp=4, edge_spp=4, seed=8, sec_point=1, n_threads=NT,
+                                     contributions=True)
+    _assert_grads(_flat(got), want, absum, "point noalloc", c)
 
 
 def test_point_sampling_options_are_checked(env):

@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 from paper_1904_12228_gb300 import scenegen as sg
+from parity import assert_grads
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -28,13 +29,8 @@ def env():
     return drt, drt.Context(0)
 
 
-def _assert_grads(got, want, absum, label=""):
-    err = np.abs(got - want)
-    bound = 1e-4 * np.abs(want) + 1e-6 * absum + 1e-12
-    bad = err > bound
-    i = int(np.argmax(err / bound))
-    assert not bad.any(), "%s: %d/%d entries off; worst entry %d got %g want %g (A=%g)" % (
-        label, bad.sum(), bad.size, i, got[i], want[i], absum[i])
+def _assert_grads(got, want, absum, label="", contrib=None):
+    assert_grads(got, want, absum, label, contrib)
 
 
 def _zeros(scene):
@@ -80,9 +76,9 @@ def test_hierarchy_gradient_matches_oracle(env, name, depth, terms, samples):
     scene = _scene(name)
     w = sg.loss_adjoint(3, scene.width, scene.height)
     got, _, _, _ = _gpu(drt, ctx, scene, w, 6, 6, 11, depth, terms, samples)
-    want, absum = oracle.backward(scene, w, spp=6, edge_spp=6, seed=11, max_depth=depth, terms=terms,
-                                  sec_tree_samples=samples, n_threads=NT)
-    _assert_grads(got, want, absum, "%s depth %d terms %d S %d" % (name, depth, terms, samples))
+    want, absum, c = oracle.backward(scene, w, spp=6, edge_spp=6, seed=11, max_depth=depth, terms=terms,
+                                     sec_tree_samples=samples, n_threads=NT, contributions=True)
+    _assert_grads(got, want, absum, "hierarchy %s depth %d terms %d S %d" % (name, depth, terms, samples), c)
     if name != "triangle":
         # the hierarchy changes the estimate: not the length sampler's numbers
         plain, _ = oracle.backward(scene, w, spp=6, edge_spp=6, seed=11, max_depth=depth, terms=4, n_threads=NT)
@@ -104,8 +100,9 @@ def test_hierarchy_is_rebuilt_when_vertices_and_camera_change(env):
     S.update_params(cam_to_world=torch.from_numpy(cam).cuda())
     got, _, _, _ = _gpu(drt, ctx, scene, w, 4, 4, 2, 1, 4, 16, S=S)
     scene2 = dataclasses.replace(scene, verts=moved, cam_to_world=cam)
-    want, absum = oracle.backward(scene2, w, spp=4, edge_spp=4, seed=2, terms=4, sec_tree_samples=16, n_threads=NT)
-    _assert_grads(got, want, absum, "after update")
+    want, absum, c = oracle.backward(scene2, w, spp=4, edge_spp=4, seed=2, terms=4, sec_tree_samples=16, n_threads=NT,
+                                     contributions=True)
+    _assert_grads(got, want, absum, "hierarchy after update", c)
 
 
 def test_noalloc_backward_with_the_hierarchy(env):
@@ -126,10 +123,10 @@ def test_noalloc_backward_with_the_hierarchy(env):
     S.backward_noalloc(w, opts, tape=tape, **got)
     torch.cuda.synchronize()
     assert ctx.check_device() == (0, 0)
-    want, absum = oracle.backward(scene, w.cpu().numpy(), spp=4, edge_spp=4, seed=8, sec_tree_samples=16,
-                                  n_threads=NT)
-    _assert_grads(_flat(got), want, absum, "noalloc")
-    _assert_grads(_flat(ref), want, absum, "backward")
+    want, absum, c = oracle.backward(scene, w.cpu().numpy(), spp=4, edge_spp=4, seed=8, sec_tree_samples=16,
+                                     n_threads=NT, contributions=True)
+    _assert_grads(_flat(got), want, absum, "hierarchy noalloc", c)
+    _assert_grads(_flat(ref), want, absum, "hierarchy backward", c)
 
 
 def test_hierarchy_options_are_checked(env):

@@ -16,6 +16,7 @@ import pytest
 
 import oracle
 from paper_1904_12228_gb300 import scenegen as sg
+from parity import assert_grads, assert_pixels
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -62,23 +63,6 @@ def gpu_grads(drt, ctx, scene, d_image, spp, edge_spp, seed, primary_only=False,
     assert code == 0, (code, info)
     flat = np.concatenate([x.cpu().numpy().ravel().astype(np.float64) for x in (dv, da, dr, dc, ds)])
     return flat, img.cpu().numpy()
-
-
-def assert_pixels(got, want):
-    err = np.abs(got - want)
-    bound = 1e-4 * np.abs(want) + 1e-7
-    bad = err > bound
-    assert not bad.any(), "%d/%d pixels off; worst err %g at %s (want %g)" % (
-        bad.sum(), bad.size, err.max(), np.unravel_index(err.argmax(), err.shape), want.flat[err.argmax()])
-
-
-def assert_grads(got, want, absum, label=""):
-    err = np.abs(got - want)
-    bound = 1e-4 * np.abs(want) + 1e-6 * absum + 1e-12
-    bad = err > bound
-    i = int(np.argmax(err / bound))
-    assert not bad.any(), "%s: %d/%d entries off; worst entry %d got %g want %g (A=%g)" % (
-        label, bad.sum(), bad.size, i, got[i], want[i], absum[i])
 
 
 # ---------------------------------------------------------------------------
@@ -149,8 +133,9 @@ def test_single_triangle_gradient(drt, ctx, seed):
     scene = sg.single_triangle(seed)
     w = sg.loss_adjoint(seed, scene.width, scene.height)
     got, _ = gpu_grads(drt, ctx, scene, w, 16, 16, seed, primary_only=True)
-    want, absum = oracle.backward(scene, w, spp=16, edge_spp=16, seed=seed, primary_only=True, n_threads=NT)
-    assert_grads(got, want, absum, "single triangle")
+    want, absum, c = oracle.backward(scene, w, spp=16, edge_spp=16, seed=seed, primary_only=True, n_threads=NT,
+                                     contributions=True)
+    assert_grads(got, want, absum, "single triangle", c)
     assert np.abs(want[:9]).max() > 0
 
 
@@ -170,8 +155,8 @@ def test_direct_lighting_gradient_terms(drt, ctx, terms):
     scene = _small_lit()
     w = sg.loss_adjoint(3, scene.width, scene.height)
     got, _ = gpu_grads(drt, ctx, scene, w, 8, 8, 11, terms=terms)
-    want, absum = oracle.backward(scene, w, spp=8, edge_spp=8, seed=11, terms=terms, n_threads=NT)
-    assert_grads(got, want, absum, "terms=%d" % terms)
+    want, absum, c = oracle.backward(scene, w, spp=8, edge_spp=8, seed=11, terms=terms, n_threads=NT, contributions=True)
+    assert_grads(got, want, absum, "direct lighting 40x28 terms=%d" % terms, c)
 
 
 def gpu_grads_depth(drt, ctx, scene, d_image, spp, seed, depth, terms=7):
@@ -203,8 +188,9 @@ def test_path_tracing_gradient_terms(drt, ctx, depth, terms):
     scene = _small_lit(W=24, H=18, subdiv=1)
     w = sg.loss_adjoint(9, 24, 18)
     got, _ = gpu_grads_depth(drt, ctx, scene, w, 6, 4, depth, terms)
-    want, absum = oracle.backward(scene, w, spp=6, edge_spp=6, seed=4, max_depth=depth, terms=terms, n_threads=NT)
-    assert_grads(got, want, absum, "depth %d terms %d" % (depth, terms))
+    want, absum, c = oracle.backward(scene, w, spp=6, edge_spp=6, seed=4, max_depth=depth, terms=terms, n_threads=NT,
+                                     contributions=True)
+    assert_grads(got, want, absum, "lit 24x18 depth %d terms %d" % (depth, terms), c)
     assert np.abs(want).max() > 0
 
 
@@ -215,8 +201,9 @@ def test_path_tracing_procedural(drt, ctx, depth):
     scene = sg.procedural(41, n_target=3000, width=29, height=27)
     w = sg.loss_adjoint(3, scene.width, scene.height)
     got, _ = gpu_grads_depth(drt, ctx, scene, w, 6, 12, depth, 4)
-    want, absum = oracle.backward(scene, w, spp=6, edge_spp=6, seed=12, max_depth=depth, terms=4, n_threads=NT)
-    assert_grads(got, want, absum, "procedural depth %d secondary" % depth)
+    want, absum, c = oracle.backward(scene, w, spp=6, edge_spp=6, seed=12, max_depth=depth, terms=4, n_threads=NT,
+                                     contributions=True)
+    assert_grads(got, want, absum, "procedural depth %d secondary" % depth, c)
     assert np.abs(want).max() > 0
 
 
@@ -225,9 +212,9 @@ def test_backward_without_tape_matches_with_tape(drt, ctx):
     w = sg.loss_adjoint(5, scene.width, scene.height)
     a, _ = gpu_grads(drt, ctx, scene, w, 4, 4, 3, use_tape=True)
     b, _ = gpu_grads(drt, ctx, scene, w, 4, 4, 3, use_tape=False)
-    want, absum = oracle.backward(scene, w, spp=4, edge_spp=4, seed=3, n_threads=NT)
-    assert_grads(a, want, absum, "tape")
-    assert_grads(b, want, absum, "no tape")
+    want, absum, c = oracle.backward(scene, w, spp=4, edge_spp=4, seed=3, n_threads=NT, contributions=True)
+    assert_grads(a, want, absum, "tape", c)
+    assert_grads(b, want, absum, "no tape", c)
 
 
 def test_ragged_sizes_and_spp(drt, ctx):
@@ -239,8 +226,8 @@ def test_ragged_sizes_and_spp(drt, ctx):
         assert_pixels(img.cpu().numpy().astype(np.float64), want)
         w = sg.loss_adjoint(W, W, H)
         got, _ = gpu_grads(drt, ctx, scene, w, spp, spp, 5)
-        g, a = oracle.backward(scene, w, spp=spp, edge_spp=spp, seed=5, n_threads=NT)
-        assert_grads(got, g, a, "%dx%d spp=%d" % (W, H, spp))
+        g, a, c = oracle.backward(scene, w, spp=spp, edge_spp=spp, seed=5, n_threads=NT, contributions=True)
+        assert_grads(got, g, a, "%dx%d spp=%d" % (W, H, spp), c)
 
 
 def test_render_is_deterministic(drt, ctx):

@@ -38,7 +38,7 @@ def test_gradient_matches_central_differences():
     V = len(scene.verts)
     w = sg.loss_adjoint(4, scene.width, scene.height)
     probes = [("verts", (0, 0)), ("verts", (0, 1)), ("verts", (V - 8, 1)), ("verts", (V - 3, 0)),
-              ("verts", (V - 2, 2)), ("cam", (0, 3))]
+              ("verts", (V - 2, 2)), ("cam", (0, 3)), ("scale", None)]
     K = 8
     ours = []
     for k in range(K):
