@@ -99,7 +99,9 @@ BYTES_PER_TRI = 48
 # profiled kernel name -> work-counter slot
 COUNTER_OF = {"render": "render", "backward_interior": "backward_interior", "backward_path": "backward_interior",
               "backward_primary_edges": "backward_primary_edges",
-              "backward_secondary_edges": "backward_secondary_edges"}
+              "backward_secondary_edges": "backward_secondary_edges",
+              "backward_secondary_sides": "backward_secondary_sides",
+              "backward_secondary_bounce": "backward_secondary_bounce"}
 
 
 def measured_peaks():

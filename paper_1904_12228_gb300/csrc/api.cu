@@ -129,7 +129,8 @@ void free_scene_buffers(drt_scene* s) {
                   s->flags, s->child_orig, s->hist, s->hist_tmp, s->bounds, s->partials, s->esort.keys, s->esort.keys2,
                   s->esort.hist, s->esort.hist_tmp, s->esort.vals, s->esort.vals2, s->seg_edge, s->seg_tile,
                   s->seg_count, s->seg_scan_tmp, s->seg_s, s->seg_len, s->seg_a, s->seg_b, s->seg_cdf, s->seg_tmp,
-                  s->sec.dp, s->sec.queue, s->sec.count, s->sec.pick, s->pguide, s->sguide, s->edge_opp,
+                  s->sec.dp, s->sec.queue, s->sec.count, s->sec.pick, s->sec.hits, s->sec.lr, s->sec.path[0],
+                  s->sec.path[1], s->sec.path_count, s->pguide, s->sguide, s->edge_opp,
                   s->et_nodes, s->et_leaf, s->et_keys, s->et_keys2, s->et_hist, s->et_hist_tmp, s->et_vals,
                   s->et_vals2, s->et_parent, s->et_leaf_parent, s->et_flags, s->et_child};
   for (void* b : bufs) dfree(b);
@@ -613,15 +614,49 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
       dfree(b.queue);
       dfree(b.count);
       dfree(b.pick);
+      dfree(b.hits);
+      dfree(b.lr);
+      dfree(b.path[0]);
+      dfree(b.path[1]);
+      dfree(b.path_count);
       b = drt::SecScratch();
       drt_status a = dalloc_n(&b.dp, 3 * (size_t)cap);
       if (a == DRT_OK) a = dalloc_n(&b.queue, (size_t)cap);
-      if (a == DRT_OK) a = dalloc_n(&b.count, 1);
+      if (a == DRT_OK) a = dalloc_n(&b.count, drt::kSecCounters);
       if (a != DRT_OK) {
         unstage(sg, 6, st);
         return a;
       }
       b.cap = cap;
+    }
+    // beyond depth 1 the queued samples are evaluated in stages (side rays,
+    // continuation paths one vertex per launch, contributions), which keep
+    // per-sample hits and radiance and the continuation states
+    int64_t pcap = drt::secondary_path_capacity(s->W, s->H, op);
+    if (pcap > 0 && (cap > s->sec.wave_cap || pcap > s->sec.path_cap)) {
+      cudaStreamSynchronize(st);
+      drt::SecScratch& b = s->sec;
+      dfree(b.hits);
+      dfree(b.lr);
+      dfree(b.path[0]);
+      dfree(b.path[1]);
+      dfree(b.path_count);
+      b.hits = nullptr;
+      b.lr = nullptr;
+      b.path[0] = b.path[1] = nullptr;
+      b.path_count = nullptr;
+      b.wave_cap = b.path_cap = 0;
+      drt_status a = dalloc_n(&b.hits, 2 * (size_t)cap);
+      if (a == DRT_OK) a = dalloc_n(&b.lr, 6 * (size_t)cap);
+      if (a == DRT_OK) a = dalloc_n(&b.path[0], 5 * (size_t)pcap);
+      if (a == DRT_OK) a = dalloc_n(&b.path[1], 5 * (size_t)pcap);
+      if (a == DRT_OK) a = dalloc_n(&b.path_count, 2);
+      if (a != DRT_OK) {
+        unstage(sg, 6, st);
+        return a;
+      }
+      b.wave_cap = cap;
+      b.path_cap = pcap;
     }
     if (op.sec_sampler == 1 && cap > s->sec.pick_cap) {
       cudaStreamSynchronize(st);

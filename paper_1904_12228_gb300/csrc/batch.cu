@@ -177,7 +177,7 @@ void plan(drt_batch* b, bool bind) {
         if (bind) {
           d.dp_sec = b->sec_dp + 3 * sec_off;
           d.sec_queue = b->sec_queue + sec_off;
-          d.sec_count = b->sec_counts + k;
+          d.sec_count = b->sec_counts + (size_t)k * drt::kSecCounters;
         }
         d.sec_cap = cap;
         sec_off += cap;
@@ -280,7 +280,8 @@ cudaError_t enqueue(drt_batch* b, cudaStream_t st) {
   if (e == cudaSuccess) e = run_phase(b, drt::kPhaseRender, b->d_desc, st);
   if (b->total_sec > 0) {
     if (e == cudaSuccess) e = cudaMemsetAsync(b->sec_dp, 0, sizeof(float) * 3 * (size_t)b->total_sec, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->sec_counts, 0, sizeof(unsigned long long) * b->n, st);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(b->sec_counts, 0, sizeof(unsigned long long) * b->n * drt::kSecCounters, st);
     for (int k = 0; k < b->n && e == cudaSuccess; ++k)
       if (b->desc[k].dp_sec) e = drt::launch_secondary_apart(b->desc[k], st);
   }
@@ -453,7 +454,7 @@ drt_status drt_batch_create(drt_context* ctx, const drt_batch_item* items, int32
   if (s == DRT_OK && b->total_sec > 0) {
     s = balloc(&b->sec_dp, 3 * (size_t)b->total_sec);
     if (s == DRT_OK) s = balloc(&b->sec_queue, (size_t)b->total_sec);
-    if (s == DRT_OK) s = balloc(&b->sec_counts, (size_t)b->n);
+    if (s == DRT_OK) s = balloc(&b->sec_counts, (size_t)b->n * drt::kSecCounters);
   }
   size_t ne = (size_t)b->total_edge;
   if (s == DRT_OK && ne > 0) {

@@ -187,9 +187,15 @@ struct BatchScene {
   // secondary edge samples that need rays, queued and traced apart
   float* dp_sec;                  // [W*H*spp, depth] adjoint of each path vertex from its secondary sample
   unsigned long long* sec_queue;  // (sample << 3 | vertex) of the queued samples
-  unsigned long long* sec_count;  // number queued
+  unsigned long long* sec_count;  // number queued per path vertex [8]; vertex b's samples in slots [b n, b n + count)
   int2* sec_pick;                 // hierarchy sampler: (edge, weight bits) of each queued sample, or null
   int64_t sec_cap;                // queue capacity = W*H*spp*depth
+  // beyond depth 1, the queued samples in stages (null: one fused kernel)
+  int4* sec_hits;                 // [sec_cap, 2] side hits (tri, b1, b2, flags) per queue slot
+  float* sec_lr;                  // [sec_cap, 6] radiance along the two continuation paths
+  float4* sec_path[2];            // [sec_path_cap, 5] continuation states, ping-pong between bounces
+  unsigned long long* sec_path_count;  // [2] entries in sec_path[0], sec_path[1]
+  int64_t sec_path_cap;           // entries each state buffer holds = W*H*spp*(depth-1)
 };
 
 

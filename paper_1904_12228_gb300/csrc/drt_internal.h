@@ -31,6 +31,9 @@ struct NvtxRange {
 };
 
 namespace drt {
+// Counters of the queue of secondary edge samples: one per path vertex (the
+// queue holds one region per vertex; max_depth <= 8).
+constexpr int kSecCounters = 8;
 // Scratch for the secondary edge samples traced apart: per (sample, vertex)
 // the vertex adjoint, the queue of samples to trace and its length.
 struct SecScratch {
@@ -40,6 +43,13 @@ struct SecScratch {
   int64_t cap = 0;  // (sample, vertex) pairs the buffers hold
   int2* pick = nullptr;  // edge hierarchy: (edge, weight bits) per queued pair
   int64_t pick_cap = 0;
+  // beyond depth 1: side hits and continuation radiance per queue slot, and
+  // two buffers of continuation-path states (5 float4 each)
+  int4* hits = nullptr;
+  float* lr = nullptr;
+  float4* path[2] = {nullptr, nullptr};
+  unsigned long long* path_count = nullptr;
+  int64_t wave_cap = 0, path_cap = 0;
 };
 // Scratch for sorting primary edge samples by screen position (key, index).
 struct SortBuffers {
@@ -122,7 +132,7 @@ struct ProfToken {
 ProfToken prof_begin(const char* name, cudaStream_t st);
 void prof_end(const ProfToken& t, cudaStream_t st);
 enum { kSlotRender = 0, kSlotBwdInterior = 1, kSlotBwdPrimary = 2, kSlotDebug = 3, kSlotBwdSecondary = 4,
-       kKernelSlots = 5 };
+       kSlotBwdSecSides = 5, kSlotBwdSecBounce = 6, kKernelSlots = 7 };
 unsigned long long* counter_slot(int kernel);  // null unless counters are enabled
 #define DRT_PROF_LAUNCH(name, st, ...)                      \
   do {                                                      \
@@ -161,6 +171,8 @@ cudaError_t launch_backward(const drt_scene* s, const Opts& op, const drt_tape* 
                             cudaStream_t st);
 // (sample, vertex) pairs of the secondary edge samples of a W x H image
 int64_t secondary_capacity(int W, int H, const Opts& op);
+// continuation-path states the staged secondary evaluation needs (0 at depth 1)
+int64_t secondary_path_capacity(int W, int H, const Opts& op);
 // queue the secondary edge samples that need rays and trace them (b.dp_sec
 // and *b.sec_count zeroed by the caller)
 cudaError_t launch_secondary_apart(const BatchScene& b, cudaStream_t st);

@@ -1077,33 +1077,21 @@ __device__ __forceinline__ bool secondary_sides(const SceneView& s, const Opts& 
   return gm.act[0] || gm.act[1];
 }
 
-// Evaluate the secondary edge sample at vertex b: trace both side rays (one
-// traversal), their continuation paths below the last vertex, and the edge
-// term's contributions: edge vertices and light vertices into so, the
-// adjoint of the vertex position into dp.
+// The side rays of the secondary edge sample at vertex b: the sample's edge,
+// point and side directions (secondary_sides), both side rays traced in one
+// traversal, and which sides count: a side counts when its hit lies above
+// the shading horizon and, for the direct part, on the front face of a
+// light, both decided in FP32 in a fixed order from the hit point, so the
+// oracle takes the same decisions.  False: no side counts.
 template <int kSel>
-__device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Opts& op, uint32_t c0, uint32_t c1,
-                                                    int b, int md, const Vertex& x, float3 n, float3 alb, float3 ab,
-                                                    float3 Le, float3& dp, SecOut& so, const int2* pre = nullptr) {
-  so.de0 = so.de1 = zero3();
-  so.eid0 = so.eid1 = 0;
-  so.have_edge = false;
-  for (int q = 0; q < 2; ++q) {
-    so.have_m[q] = false;
-    for (int i = 0; i < 3; ++i) { so.dm[q][i] = zero3(); so.mid[q][i] = 0; }
-  }
-  SecGeom gm;
-  if (!secondary_sides<kSel>(s, op, c0, c1, b, md, x, n, gm, pre)) return;
-  const int2 ev = gm.ev;
-  const bool last = gm.last;
+__device__ __forceinline__ bool secondary_side_hits(const SceneView& s, const Opts& op, uint32_t c0, uint32_t c1,
+                                                    int b, int md, const Vertex& x, float3 n, SecGeom& gm,
+                                                    Hit hms[2], bool front[2], const int2* pre = nullptr) {
+  front[0] = front[1] = false;
+  if (!secondary_sides<kSel>(s, op, c0, c1, b, md, x, n, gm, pre)) return false;
   float (*dsd)[3] = gm.dsd;
   bool* act = gm.act;
-  Hit hms[2];
   trace_closest2(s, x.p, dsd[0], x.p, dsd[1], act[0], act[1], x.k, x.k, hms[0], hms[1]);
-  // a side counts when its hit lies above the shading horizon and, for the
-  // direct part, on the front face of a light: both decided in FP32 in a fixed
-  // order from the hit point, so the oracle takes the same decisions
-  bool front[2] = {false, false};
   for (int side = 0; side < 2; ++side) {
     if (!act[side] || hms[side].tri < 0) { act[side] = false; continue; }
     Vertex mv;
@@ -1112,11 +1100,20 @@ __device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Op
     if (!(dot3x(gm.n32, dm32) > 0.f)) act[side] = false;
     front[side] = dot3x(mv.nu, dm32) < 0.f;
   }
-  // radiance along both continuation paths, from the hits found above
-  float3 Lr[2] = {zero3(), zero3()};
-  if (!last && (act[0] || act[1]))
-    path_value2_from(s, op, dsd, hms, act, b + 1, c0, c1, kPassSecondaryBase + (uint32_t)b, Lr);
-  if (!act[0] && !act[1]) return;
+  return act[0] || act[1];
+}
+
+// The edge term's contributions of a secondary edge sample whose side hits
+// (and, below the last vertex, the radiance Lr arriving along each side's
+// continuation path) are known: edge vertices and light vertices into so,
+// the adjoint of the vertex position into dp.
+__device__ __forceinline__ void secondary_contrib(const SceneView& s, const Vertex& x, float3 n, float3 alb,
+                                                  float3 ab, float3 Le, const SecGeom& gm, const Hit hms[2],
+                                                  const bool front[2], const float3 Lr[2], float3& dp, SecOut& so) {
+  const int2 ev = gm.ev;
+  const bool last = gm.last;
+  const float (*dsd)[3] = gm.dsd;
+  const bool* act = gm.act;
   // Geometry of the sample.  The vectors a0, a1 from p to the edge's end
   // points are nearly parallel when the edge subtends a small angle at p, so
   // their cross product is taken in the equal, well-conditioned form
@@ -1191,6 +1188,31 @@ __device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Op
   }
   so.eid0 = ev.x;
   so.eid1 = ev.y;
+}
+
+// Evaluate the secondary edge sample at vertex b: trace both side rays (one
+// traversal), their continuation paths below the last vertex, and the edge
+// term's contributions: edge vertices and light vertices into so, the
+// adjoint of the vertex position into dp.
+template <int kSel>
+__device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Opts& op, uint32_t c0, uint32_t c1,
+                                                    int b, int md, const Vertex& x, float3 n, float3 alb, float3 ab,
+                                                    float3 Le, float3& dp, SecOut& so, const int2* pre = nullptr) {
+  so.de0 = so.de1 = zero3();
+  so.eid0 = so.eid1 = 0;
+  so.have_edge = false;
+  for (int q = 0; q < 2; ++q) {
+    so.have_m[q] = false;
+    for (int i = 0; i < 3; ++i) { so.dm[q][i] = zero3(); so.mid[q][i] = 0; }
+  }
+  SecGeom gm;
+  Hit hms[2];
+  bool front[2];
+  if (!secondary_side_hits<kSel>(s, op, c0, c1, b, md, x, n, gm, hms, front, pre)) return;
+  // radiance along both continuation paths, from the hits found above
+  float3 Lr[2] = {zero3(), zero3()};
+  if (!gm.last) path_value2_from(s, op, gm.dsd, hms, gm.act, b + 1, c0, c1, kPassSecondaryBase + (uint32_t)b, Lr);
+  secondary_contrib(s, x, n, alb, ab, Le, gm, hms, front, Lr, dp, so);
 }
 
 // Secondary edge samples at the camera hits (depth 1), evaluated inside the
@@ -1512,10 +1534,14 @@ __global__ void __launch_bounds__(kBlock, kSel == kSelLength ? DRT_QUEUE_MIN_BLO
     if (m) {
       int leader = __ffs(m) - 1;
       unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(bs.sec_count, (unsigned long long)__popc(m));
+      if (lane == leader) base = atomicAdd(bs.sec_count + b, (unsigned long long)__popc(m));
       base = __shfl_sync(kFull, base, leader);
       if (need) {
-        unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
+        // the queue holds one region of n slots per path vertex, so the
+        // trace kernel's warps take samples of one vertex (equal remaining
+        // depth, similar work) together
+        unsigned long long slot = (unsigned long long)b * (unsigned long long)n + base +
+                                  __popc(m & ((1u << lane) - 1u));
         bs.sec_queue[slot] = ((unsigned long long)i << 3) | (unsigned)b;
         if (kSel == kSelTree) bs.sec_pick[slot] = make_int2(gm.e, __float_as_int(gm.invPE));
       }
@@ -1549,8 +1575,9 @@ __global__ void __launch_bounds__(kBlock, kSel == kSelLength ? DRT_QUEUE_MIN_BLO
 }
 
 // Pass 2: the queued (sample, vertex) pairs, a block-stride loop over the
-// queue; vertex gradients through the block cache (the light's vertices take
-// contributions from most samples).
+// vertex regions of the queue in order (first vertex first: its samples
+// carry the longest continuation paths); vertex gradients through the block
+// cache (the light's vertices take contributions from most samples).
 template <int kSel>
 __global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_trace(BatchScene bs) {
   __shared__ GradCache cv;
@@ -1558,12 +1585,25 @@ __global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_trace(BatchS
   const Opts& op = bs.op;
   int md = op.primary_only ? 1 : min(op.max_depth, kMaxDepth);
   const float3 Le = ld3(s.radiance);
-  unsigned long long count = *bs.sec_count;
+  const unsigned long long n_region = (unsigned long long)s.W * s.H * op.spp;
+  __shared__ unsigned long long cnt[kMaxDepth];
+  if (threadIdx.x < kMaxDepth) cnt[threadIdx.x] = (int)threadIdx.x < md ? bs.sec_count[threadIdx.x] : 0ull;
+  __syncthreads();
+  unsigned long long count = 0;
+  for (int b = 0; b < md; ++b) count += cnt[b];
   for (unsigned long long base = (unsigned long long)blockIdx.x * kBlock; base < count;
        base += (unsigned long long)gridDim.x * kBlock) {
     cache_init(cv);
     __syncthreads();
-    unsigned long long q = base + threadIdx.x;
+    unsigned long long qq = base + threadIdx.x, q = qq;
+    // queue slot of the qq-th queued sample: region b, offset within it
+    for (int b = 0; b < md; ++b) {
+      if (qq < cnt[b]) {
+        q = (unsigned long long)b * n_region + qq;
+        break;
+      }
+      qq -= cnt[b];
+    }
     SecOut so;
     so.have_edge = false;
     so.have_m[0] = so.have_m[1] = false;
@@ -1571,7 +1611,7 @@ __global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_trace(BatchS
     so.de0 = so.de1 = zero3();
     for (int h = 0; h < 2; ++h)
       for (int j = 0; j < 3; ++j) { so.dm[h][j] = zero3(); so.mid[h][j] = 0; }
-    if (q < count) {
+    if (base + threadIdx.x < count) {
       unsigned long long item = bs.sec_queue[q];
       int64_t i = (int64_t)(item >> 3);
       int b = (int)(item & 7u);
@@ -1588,6 +1628,285 @@ __global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_trace(BatchS
         o[0] = dp.x;
         o[1] = dp.y;
         o[2] = dp.z;
+      }
+    }
+    scatter3(bs.d_verts, so.eid0, so.de0, so.have_edge, &cv);
+    scatter3(bs.d_verts, so.eid1, so.de1, so.have_edge, &cv);
+    for (int h = 0; h < 2; ++h)
+      for (int j = 0; j < 3; ++j) scatter3(bs.d_verts, so.mid[h][j], so.dm[h][j], so.have_m[h], &cv);
+    __syncthreads();
+    cache_flush(cv, bs.d_verts);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Queued secondary edge samples beyond depth 1, in stages.  With one thread
+// per queued sample carrying both side paths to the last vertex, a warp's
+// lanes trace from one to five traversals each (side rays, then next-event
+// and continuation rays at every later vertex) and most lanes idle while a
+// few finish their paths.  Here (1) k_sec_sides traces the side rays of every
+// queued sample and stores the hits; (2) k_sec_bounce, launched once per
+// remaining vertex, advances every live pair of continuation paths by one
+// vertex (next-event ray pair, then the continuation ray pair) and adds the
+// radiance they gather; (3) k_sec_finish evaluates the edge term from the
+// stored hits and radiance.  Same random numbers and arithmetic as
+// path_value2_from and secondary_at_vertex; the sample's geometry is
+// recomputed in stage 3 (a pure function of the sample and its vertex).
+// ---------------------------------------------------------------------------
+struct SecPathState {
+  float4 a;  // d0.xyz, beta0.x
+  float4 b;  // d1.xyz, beta0.y
+  float4 c;  // beta0.z, beta1.xyz
+  float4 d;  // b1_0, b2_0, b1_1, b2_1
+  int4 e;    // queue slot, tri0, tri1, vertex | alive0 << 8 | alive1 << 9
+};
+static_assert(sizeof(SecPathState) == 5 * sizeof(float4), "path state is five float4");
+
+__device__ __forceinline__ void sec_push_path(const BatchScene& bs, int buf, bool push, const SecPathState& st) {
+  int lane = threadIdx.x & 31;
+  unsigned m = __ballot_sync(kFull, push);
+  if (!m) return;
+  int leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(bs.sec_path_count + buf, (unsigned long long)__popc(m));
+  base = __shfl_sync(kFull, base, leader);
+  if (push) {
+    unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
+    reinterpret_cast<SecPathState*>(bs.sec_path[buf])[slot] = st;
+  }
+}
+
+// queue slot of the qq-th queued sample (regions per vertex, in order)
+__device__ __forceinline__ unsigned long long sec_slot(const unsigned long long* cnt, int md, unsigned long long n,
+                                                       unsigned long long qq) {
+  for (int b = 0; b < md; ++b) {
+    if (qq < cnt[b]) return (unsigned long long)b * n + qq;
+    qq -= cnt[b];
+  }
+  return qq;
+}
+
+// Stage 1: side rays of every queued sample; samples above the last vertex
+// start their continuation paths in state buffer 0.
+template <int kSel>
+__global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_sides(BatchScene bs) {
+  const SceneView& s = bs.v;
+  const Opts& op = bs.op;
+  int md = op.primary_only ? 1 : min(op.max_depth, kMaxDepth);
+  const unsigned long long n_region = (unsigned long long)s.W * s.H * op.spp;
+  __shared__ unsigned long long cnt[kMaxDepth];
+  if (threadIdx.x < kMaxDepth) cnt[threadIdx.x] = (int)threadIdx.x < md ? bs.sec_count[threadIdx.x] : 0ull;
+  __syncthreads();
+  unsigned long long count = 0;
+  for (int b = 0; b < md; ++b) count += cnt[b];
+  for (unsigned long long base = (unsigned long long)blockIdx.x * kBlock; base < count;
+       base += (unsigned long long)gridDim.x * kBlock) {
+    bool in = base + threadIdx.x < count;
+    unsigned long long q = in ? sec_slot(cnt, md, n_region, base + threadIdx.x) : 0ull;
+    bool push = false;
+    SecPathState st;
+    if (in) {
+      unsigned long long item = bs.sec_queue[q];
+      int64_t i = (int64_t)(item >> 3);
+      int b = (int)(item & 7u);
+      int64_t pix = i / op.spp;
+      int sidx = (int)(i % op.spp);
+      Vertex x;
+      float3 beta;
+      int flags = 0;
+      Hit hms[2];
+      hms[0].tri = hms[1].tri = -1;
+      hms[0].b1 = hms[0].b2 = hms[1].b1 = hms[1].b2 = 0.f;
+      bool last = b + 1 >= md;
+      if (tape_vertex(s, op, bs.tape_tri, bs.tape_bary, pix, sidx, b, md, x, beta)) {
+        SecGeom gm;
+        bool front[2];
+        if (secondary_side_hits<kSel>(s, op, (uint32_t)pix, (uint32_t)sidx, b, md, x, shading_normal(x), gm, hms,
+                                      front, bs.sec_pick + q)) {
+          flags = (gm.act[0] ? 1 : 0) | (gm.act[1] ? 2 : 0) | (front[0] ? 4 : 0) | (front[1] ? 8 : 0);
+          if (!last) {
+            push = true;
+            st.a = make_float4(gm.dsd[0][0], gm.dsd[0][1], gm.dsd[0][2], 1.f);
+            st.b = make_float4(gm.dsd[1][0], gm.dsd[1][1], gm.dsd[1][2], 1.f);
+            st.c = make_float4(1.f, 1.f, 1.f, 1.f);
+            st.d = make_float4(hms[0].b1, hms[0].b2, hms[1].b1, hms[1].b2);
+            st.e = make_int4((int)(uint32_t)q, hms[0].tri, hms[1].tri,
+                             (b + 1) | (gm.act[0] ? 256 : 0) | (gm.act[1] ? 512 : 0));
+          }
+        }
+      }
+      bs.sec_hits[2 * q] = make_int4(hms[0].tri, __float_as_int(hms[0].b1), __float_as_int(hms[0].b2), flags);
+      bs.sec_hits[2 * q + 1] = make_int4(hms[1].tri, __float_as_int(hms[1].b1), __float_as_int(hms[1].b2), 0);
+      if (!last) {
+        float* lr = bs.sec_lr + 6 * q;
+        for (int k = 0; k < 6; ++k) lr[k] = 0.f;
+      }
+    }
+    sec_push_path(bs, 0, push, st);
+  }
+}
+
+// Stage 2: every live pair of continuation paths in state buffer `in`
+// advances by one vertex: next-event estimation at the vertex (both sides in
+// one any-hit traversal) and, above the last vertex, the continuation
+// direction and its closest hit (both sides in one traversal); pairs with a
+// side still alive go to the other buffer.
+__global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_bounce(BatchScene bs, int in) {
+  const SceneView& s = bs.v;
+  const Opts& op = bs.op;
+  int md = op.primary_only ? 1 : min(op.max_depth, kMaxDepth);
+  const float3 Le = ld3(s.radiance);
+  unsigned long long count = bs.sec_path_count[in];
+  const SecPathState* src = reinterpret_cast<const SecPathState*>(bs.sec_path[in]);
+  for (unsigned long long base = (unsigned long long)blockIdx.x * kBlock; base < count;
+       base += (unsigned long long)gridDim.x * kBlock) {
+    unsigned long long e = base + threadIdx.x;
+    bool push = false;
+    SecPathState st;
+    if (e < count) {
+      st = src[e];
+      unsigned long long q = (uint32_t)st.e.x;
+      unsigned long long item = bs.sec_queue[q];
+      int64_t i = (int64_t)(item >> 3);
+      int b0 = (int)(item & 7u);
+      uint32_t c0 = (uint32_t)(i / op.spp), c1 = (uint32_t)(i % op.spp);
+      uint32_t pass = kPassSecondaryBase + (uint32_t)b0;
+      int bb = st.e.w & 255;
+      bool alive[2] = {(st.e.w & 256) != 0, (st.e.w & 512) != 0};
+      float d[2][3] = {{st.a.x, st.a.y, st.a.z}, {st.b.x, st.b.y, st.b.z}};
+      float3 beta[2] = {make_float3(st.a.w, st.b.w, st.c.x), make_float3(st.c.y, st.c.z, st.c.w)};
+      Hit h[2];
+      h[0].tri = st.e.y; h[0].b1 = st.d.x; h[0].b2 = st.d.y; h[0].t = 0.f;
+      h[1].tri = st.e.z; h[1].b1 = st.d.z; h[1].b2 = st.d.w; h[1].t = 0.f;
+      Vertex x[2];
+      float3 alb[2];
+      for (int k = 0; k < 2; ++k) {
+        alb[k] = zero3();
+        if (!alive[k]) continue;
+        if (h[k].tri < 0) { alive[k] = false; continue; }
+        load_vertex(s, h[k].tri, h[k].b1, h[k].b2, d[k], x[k]);
+        alb[k] = ld3(s.albedo + 3 * x[k].k);
+      }
+      if (alive[0] || alive[1]) {
+        float n32[2][3];
+        for (int k = 0; k < 2; ++k)
+          if (alive[k]) shading_normal32(x[k], n32[k]);
+        if (s.L > 0) {
+          uint4 r = rng4(op.key, c0, c1, kLight, (uint32_t)bb, pass, op.scene_id);
+          LightSample ls;
+          sample_light(s, r, ls);
+          float sd[2][3];
+          for (int k = 0; k < 2; ++k)
+            if (alive[k])
+              for (int j = 0; j < 3; ++j) sd[k][j] = fs(ls.y[j], x[k].p[j]);
+          bool occ[2];
+          trace_any2(s, x[0].p, sd[0], x[0].k, ls.lt, x[1].p, sd[1], x[1].k, ls.lt, alive[0], alive[1],
+                     kShadowTmax, occ[0], occ[1]);
+          float* lr = bs.sec_lr + 6 * q;
+          for (int k = 0; k < 2; ++k)
+            if (alive[k] && !occ[k]) {
+              float g = nee_geometry(s, f3(x[k].p), f3(n32[k]), ls);
+              float3 add = (kInvPi * g) * (beta[k] * alb[k] * Le);
+              lr[3 * k] += add.x;
+              lr[3 * k + 1] += add.y;
+              lr[3 * k + 2] += add.z;
+            }
+        }
+        if (bb + 1 < md) {
+          uint4 r = rng4(op.key, c0, c1, kBsdf, (uint32_t)bb, pass, op.scene_id);
+          int exclude[2] = {-1, -1};
+          float o[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+          for (int k = 0; k < 2; ++k) {
+            if (!alive[k]) continue;
+            float nd[3];
+            cosine_dir(n32[k], u01f(r.x), u01f(r.y), nd);
+            if (!(dot(f3(n32[k]), f3(nd)) > 0.f)) { alive[k] = false; continue; }
+            beta[k] = beta[k] * alb[k];
+            for (int j = 0; j < 3; ++j) { o[k][j] = x[k].p[j]; d[k][j] = nd[j]; }
+            exclude[k] = x[k].k;
+          }
+          if (alive[0] || alive[1]) {
+            trace_closest2(s, o[0], d[0], o[1], d[1], alive[0], alive[1], exclude[0], exclude[1], h[0], h[1]);
+            for (int k = 0; k < 2; ++k)
+              if (alive[k] && h[k].tri < 0) alive[k] = false;
+            if (alive[0] || alive[1]) {
+              push = true;
+              st.a = make_float4(d[0][0], d[0][1], d[0][2], beta[0].x);
+              st.b = make_float4(d[1][0], d[1][1], d[1][2], beta[0].y);
+              st.c = make_float4(beta[0].z, beta[1].x, beta[1].y, beta[1].z);
+              st.d = make_float4(h[0].b1, h[0].b2, h[1].b1, h[1].b2);
+              st.e = make_int4(st.e.x, h[0].tri, h[1].tri, (bb + 1) | (alive[0] ? 256 : 0) | (alive[1] ? 512 : 0));
+            }
+          }
+        }
+      }
+    }
+    sec_push_path(bs, in ^ 1, push, st);
+  }
+}
+
+// Stage 3: the edge term of every queued sample from its stored side hits
+// and continuation radiance; vertex gradients through the block cache.
+template <int kSel>
+__global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_finish(BatchScene bs) {
+  __shared__ GradCache cv;
+  const SceneView& s = bs.v;
+  const Opts& op = bs.op;
+  int md = op.primary_only ? 1 : min(op.max_depth, kMaxDepth);
+  const float3 Le = ld3(s.radiance);
+  const unsigned long long n_region = (unsigned long long)s.W * s.H * op.spp;
+  __shared__ unsigned long long cnt[kMaxDepth];
+  if (threadIdx.x < kMaxDepth) cnt[threadIdx.x] = (int)threadIdx.x < md ? bs.sec_count[threadIdx.x] : 0ull;
+  __syncthreads();
+  unsigned long long count = 0;
+  for (int b = 0; b < md; ++b) count += cnt[b];
+  for (unsigned long long base = (unsigned long long)blockIdx.x * kBlock; base < count;
+       base += (unsigned long long)gridDim.x * kBlock) {
+    cache_init(cv);
+    __syncthreads();
+    SecOut so;
+    so.have_edge = false;
+    so.have_m[0] = so.have_m[1] = false;
+    so.eid0 = so.eid1 = 0;
+    so.de0 = so.de1 = zero3();
+    for (int h = 0; h < 2; ++h)
+      for (int j = 0; j < 3; ++j) { so.dm[h][j] = zero3(); so.mid[h][j] = 0; }
+    if (base + threadIdx.x < count) {
+      unsigned long long q = sec_slot(cnt, md, n_region, base + threadIdx.x);
+      int4 h0 = bs.sec_hits[2 * q], h1 = bs.sec_hits[2 * q + 1];
+      int flags = h0.w;
+      unsigned long long item = bs.sec_queue[q];
+      int64_t i = (int64_t)(item >> 3);
+      int b = (int)(item & 7u);
+      int64_t pix = i / op.spp;
+      int sidx = (int)(i % op.spp);
+      Vertex x;
+      float3 beta;
+      SecGeom gm;
+      if ((flags & 3) && tape_vertex(s, op, bs.tape_tri, bs.tape_bary, pix, sidx, b, md, x, beta)) {
+        float3 n = shading_normal(x);
+        if (secondary_sides<kSel>(s, op, (uint32_t)pix, (uint32_t)sidx, b, md, x, n, gm, bs.sec_pick + q)) {
+          gm.act[0] = (flags & 1) != 0;
+          gm.act[1] = (flags & 2) != 0;
+          bool front[2] = {(flags & 4) != 0, (flags & 8) != 0};
+          Hit hms[2];
+          hms[0].tri = h0.x; hms[0].b1 = __int_as_float(h0.y); hms[0].b2 = __int_as_float(h0.z); hms[0].t = 0.f;
+          hms[1].tri = h1.x; hms[1].b1 = __int_as_float(h1.y); hms[1].b2 = __int_as_float(h1.z); hms[1].t = 0.f;
+          float3 Lr[2] = {zero3(), zero3()};
+          if (!gm.last) {
+            const float* lr = bs.sec_lr + 6 * q;
+            Lr[0] = make_float3(lr[0], lr[1], lr[2]);
+            Lr[1] = make_float3(lr[3], lr[4], lr[5]);
+          }
+          float3 ab = ((1.0f / (float)op.spp) * ld3(bs.d_image + 3 * pix)) * beta;
+          float3 dp = zero3();
+          secondary_contrib(s, x, n, ld3(s.albedo + 3 * x.k), ab, Le, gm, hms, front, Lr, dp, so);
+          float* o = bs.dp_sec + 3 * (i * md + b);
+          o[0] = dp.x;
+          o[1] = dp.y;
+          o[2] = dp.z;
+        }
       }
     }
     scatter3(bs.d_verts, so.eid0, so.de0, so.have_edge, &cv);
@@ -1995,11 +2314,46 @@ cudaError_t launch_secondary_apart(const BatchScene& b, cudaStream_t st) {
   BatchScene t = b;
   t.v.counters = counter_slot(kSlotBwdSecondary);
   int64_t grid = std::min<int64_t>((b.sec_cap + kBlock - 1) / kBlock, 152 * 8);
+  int md = b.op.primary_only ? 1 : std::min(b.op.max_depth, kMaxDepth);
+  bool staged = md > 1 && b.sec_hits && b.sec_lr && b.sec_path[0] && b.sec_path[1] && b.sec_path_count &&
+                b.sec_cap < (int64_t(1) << 31);
+  if (!staged) {
+    if (tree)
+      DRT_PROF_LAUNCH("backward_secondary_edges", st,
+                      k_sec_trace<kSelTreePre><<<(unsigned)grid, kBlock, 0, st>>>(t));
+    else
+      DRT_PROF_LAUNCH("backward_secondary_edges", st, k_sec_trace<kSelLength><<<(unsigned)grid, kBlock, 0, st>>>(t));
+    return cudaGetLastError();
+  }
+  cudaError_t e = cudaMemsetAsync(b.sec_path_count, 0, 2 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  t.v.counters = counter_slot(kSlotBwdSecSides);
   if (tree)
-    DRT_PROF_LAUNCH("backward_secondary_edges", st, k_sec_trace<kSelTreePre><<<(unsigned)grid, kBlock, 0, st>>>(t));
+    DRT_PROF_LAUNCH("backward_secondary_sides", st, k_sec_sides<kSelTreePre><<<(unsigned)grid, kBlock, 0, st>>>(t));
   else
-    DRT_PROF_LAUNCH("backward_secondary_edges", st, k_sec_trace<kSelLength><<<(unsigned)grid, kBlock, 0, st>>>(t));
+    DRT_PROF_LAUNCH("backward_secondary_sides", st, k_sec_sides<kSelLength><<<(unsigned)grid, kBlock, 0, st>>>(t));
+  int64_t grid_p = std::min<int64_t>((b.sec_path_cap + kBlock - 1) / kBlock, 152 * 8);
+  t.v.counters = counter_slot(kSlotBwdSecBounce);
+  for (int level = 0; level + 1 < md; ++level) {
+    int in = level & 1;
+    e = cudaMemsetAsync(b.sec_path_count + (in ^ 1), 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    DRT_PROF_LAUNCH("backward_secondary_bounce", st,
+                    k_sec_bounce<<<(unsigned)std::max<int64_t>(grid_p, 1), kBlock, 0, st>>>(t, in));
+  }
+  BatchScene f = b;
+  f.v.counters = nullptr;
+  if (tree)
+    DRT_PROF_LAUNCH("backward_secondary_finish", st,
+                    k_sec_finish<kSelTreePre><<<(unsigned)grid, kBlock, 0, st>>>(f));
+  else
+    DRT_PROF_LAUNCH("backward_secondary_finish", st, k_sec_finish<kSelLength><<<(unsigned)grid, kBlock, 0, st>>>(f));
   return cudaGetLastError();
+}
+
+int64_t secondary_path_capacity(int W, int H, const Opts& op) {
+  int md = op.primary_only ? 1 : std::min(op.max_depth, kMaxDepth);
+  return md > 1 ? (int64_t)W * H * op.spp * (md - 1) : 0;
 }
 
 cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape* tape, const float* d_image,
@@ -2064,8 +2418,16 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
     bsd.sec_count = secs->count;
     bsd.sec_pick = op.sec_sampler == 1 ? secs->pick : nullptr;
     bsd.sec_cap = secondary_capacity(sc->W, sc->H, op);
+    if (secs->wave_cap >= bsd.sec_cap && secs->path_cap >= secondary_path_capacity(sc->W, sc->H, op)) {
+      bsd.sec_hits = secs->hits;
+      bsd.sec_lr = secs->lr;
+      bsd.sec_path[0] = secs->path[0];
+      bsd.sec_path[1] = secs->path[1];
+      bsd.sec_path_count = secs->path_count;
+      bsd.sec_path_cap = secondary_path_capacity(sc->W, sc->H, op);
+    }
     cudaError_t e = cudaMemsetAsync(secs->dp, 0, sizeof(float) * 3 * bsd.sec_cap, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(secs->count, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(secs->count, 0, sizeof(unsigned long long) * kSecCounters, st);
     if (e == cudaSuccess) e = launch_secondary_apart(bsd, st);
     if (e != cudaSuccess) return e;
     dps = secs->dp;
