@@ -101,7 +101,9 @@ COUNTER_OF = {"render": "render", "backward_interior": "backward_interior", "bac
               "backward_primary_edges": "backward_primary_edges",
               "backward_secondary_edges": "backward_secondary_edges",
               "backward_secondary_sides": "backward_secondary_sides",
-              "backward_secondary_bounce": "backward_secondary_bounce"}
+              "backward_secondary_bounce": "backward_secondary_bounce",
+              "backward_primary_first": "backward_primary_edges",
+              "backward_primary_bounce": "backward_primary_bounce"}
 
 
 def measured_peaks():

@@ -130,7 +130,8 @@ void free_scene_buffers(drt_scene* s) {
                   s->esort.hist, s->esort.hist_tmp, s->esort.vals, s->esort.vals2, s->seg_edge, s->seg_tile,
                   s->seg_count, s->seg_scan_tmp, s->seg_s, s->seg_len, s->seg_a, s->seg_b, s->seg_cdf, s->seg_tmp,
                   s->sec.dp, s->sec.queue, s->sec.count, s->sec.pick, s->sec.hits, s->sec.lr, s->sec.path[0],
-                  s->sec.path[1], s->sec.path_count, s->pguide, s->sguide, s->edge_opp,
+                  s->sec.path[1], s->sec.path_count, s->prim.lr, s->prim.path[0], s->prim.path[1], s->prim.count,
+                  s->pguide, s->sguide, s->edge_opp,
                   s->et_nodes, s->et_leaf, s->et_keys, s->et_keys2, s->et_hist, s->et_hist_tmp, s->et_vals,
                   s->et_vals2, s->et_parent, s->et_leaf_parent, s->et_flags, s->et_child};
   for (void* b : bufs) dfree(b);
@@ -672,9 +673,34 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
     }
     secs = &s->sec;
   }
+  // primary edge samples beyond depth 1 are evaluated in stages: radiance per
+  // sample and side, continuation-path states
+  const drt::PrimScratch* prims = nullptr;
+  int md = op.primary_only ? 1 : std::min(op.max_depth, 8);
+  if (sort && md > 1) {
+    if (n_edge > s->prim.cap) {
+      cudaStreamSynchronize(st);
+      drt::PrimScratch& b = s->prim;
+      dfree(b.lr);
+      dfree(b.path[0]);
+      dfree(b.path[1]);
+      dfree(b.count);
+      b = drt::PrimScratch();
+      drt_status a = dalloc_n(&b.lr, 6 * (size_t)n_edge);
+      if (a == DRT_OK) a = dalloc_n(&b.path[0], 5 * (size_t)n_edge);
+      if (a == DRT_OK) a = dalloc_n(&b.path[1], 5 * (size_t)n_edge);
+      if (a == DRT_OK) a = dalloc_n(&b.count, 2);
+      if (a != DRT_OK) {
+        unstage(sg, 6, st);
+        return a;
+      }
+      b.cap = n_edge;
+    }
+    prims = &s->prim;
+  }
   cudaError_t e = drt::launch_backward(s, op, tape, (const float*)sg[0].dev, (float*)sg[1].dev, (float*)sg[2].dev,
                                        (float*)sg[3].dev, (float*)sg[4].dev, (float*)sg[5].dev, s->partials, sort,
-                                       secs, st);
+                                       secs, prims, st);
   r = unstage(sg, 6, st);
   if (e != cudaSuccess) return fail(DRT_ERR_CUDA, "backward launch: %s", cudaGetErrorString(e));
   return r;

@@ -51,6 +51,15 @@ struct SecScratch {
   unsigned long long* path_count = nullptr;
   int64_t wave_cap = 0, path_cap = 0;
 };
+// Scratch of the primary edge samples beyond depth 1, evaluated in stages:
+// radiance of both side paths per sample (screen order) and two buffers of
+// continuation-path states (5 float4 each).
+struct PrimScratch {
+  float* lr = nullptr;
+  float4* path[2] = {nullptr, nullptr};
+  unsigned long long* count = nullptr;
+  int64_t cap = 0;  // edge samples the buffers hold
+};
 // Scratch for sorting primary edge samples by screen position (key, index).
 struct SortBuffers {
   uint32_t *keys = nullptr, *keys2 = nullptr, *hist = nullptr, *hist_tmp = nullptr;
@@ -96,6 +105,7 @@ struct drt_scene {
   size_t partials_cap = 0;
   drt::SortBuffers esort;    // backward: primary edge samples sorted by screen position
   drt::SecScratch sec;       // backward: secondary edge samples queued and traced apart
+  drt::PrimScratch prim;     // backward: primary edge samples beyond depth 1 in stages
   // tile segments of the primary edges (built on demand)
   int32_t *seg_edge = nullptr, *seg_tile = nullptr;
   uint32_t *seg_count = nullptr, *seg_scan_tmp = nullptr;
@@ -132,7 +142,7 @@ struct ProfToken {
 ProfToken prof_begin(const char* name, cudaStream_t st);
 void prof_end(const ProfToken& t, cudaStream_t st);
 enum { kSlotRender = 0, kSlotBwdInterior = 1, kSlotBwdPrimary = 2, kSlotDebug = 3, kSlotBwdSecondary = 4,
-       kSlotBwdSecSides = 5, kSlotBwdSecBounce = 6, kKernelSlots = 7 };
+       kSlotBwdSecSides = 5, kSlotBwdSecBounce = 6, kSlotBwdPrimBounce = 7, kKernelSlots = 8 };
 unsigned long long* counter_slot(int kernel);  // null unless counters are enabled
 #define DRT_PROF_LAUNCH(name, st, ...)                      \
   do {                                                      \
@@ -168,7 +178,7 @@ cudaError_t launch_render(const drt_scene* s, const Opts& op, float* image, drt_
 cudaError_t launch_backward(const drt_scene* s, const Opts& op, const drt_tape* tape, const float* d_image,
                             float* d_verts, float* d_albedo, float* d_radiance, float* d_cam, float* d_cam_scale,
                             float* scratch_global, const SortBuffers* sort, const SecScratch* secs,
-                            cudaStream_t st);
+                            const PrimScratch* prims, cudaStream_t st);
 // (sample, vertex) pairs of the secondary edge samples of a W x H image
 int64_t secondary_capacity(int W, int H, const Opts& op);
 // continuation-path states the staged secondary evaluation needs (0 at depth 1)

@@ -130,7 +130,7 @@ drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* s, const drt
   }
   cudaError_t e = drt::launch_backward(s, op, tape, d_image, grads->d_verts, grads->d_albedo, grads->d_radiance,
                                        grads->d_cam_to_world, grads->d_cam_scale, scratch,
-                                       nullptr, nullptr, (cudaStream_t)stream);
+                                       nullptr, nullptr, nullptr, (cudaStream_t)stream);
   if (e != cudaSuccess) {
     return fail_noalloc(DRT_ERR_CUDA, cudaGetErrorString(e));
   }

@@ -55,6 +55,18 @@ constexpr int kKeySub = DRT_KEY_SUB;
 #ifndef DRT_SEC_MIN_BLOCKS
 #define DRT_SEC_MIN_BLOCKS 2
 #endif
+// Resident CTAs per SM of the staged evaluation beyond depth 1: the side-ray
+// stage of the secondary samples, the continuation stage (one launch per
+// vertex) and the secondary contributions.
+#ifndef DRT_SIDES_MIN_BLOCKS
+#define DRT_SIDES_MIN_BLOCKS 2
+#endif
+#ifndef DRT_BOUNCE_MIN_BLOCKS
+#define DRT_BOUNCE_MIN_BLOCKS 2
+#endif
+#ifndef DRT_FINISH_MIN_BLOCKS
+#define DRT_FINISH_MIN_BLOCKS 2
+#endif
 // Resident CTAs per SM the depth > 1 path pass is compiled for (its variant
 // with the secondary edge samples inside the pass stays at one: it spills).
 #ifndef DRT_PATH_MIN_BLOCKS
@@ -375,6 +387,58 @@ __device__ float3 path_value_warp(const SceneView& s, const Opts& op, const floa
   }
   if (tape_tri && act)
     for (int b = b_end; b < md; ++b) tape_tri[b * n_stride + n_idx] = -1;
+  return L;
+}
+
+// Vertex 0 of a camera path for the 32 lanes of a warp together, exactly as
+// the first iteration of path_value_warp (all lanes call; warp-cooperative
+// traversals): emission at the hit, next-event estimation, and, when the path
+// goes on (cont), its continuation direction nd, the hit h0 and the hit's
+// albedo (the throughput of what follows).
+__device__ float3 path_first_vertex_warp(const SceneView& s, const Opts& op, const float o[3], const float d[3],
+                                         bool act, uint32_t c0, uint32_t c1, uint32_t pass, bool& cont, Hit& h0,
+                                         float nd[3], float3& alb) {
+  int md = op.primary_only ? 1 : op.max_depth;
+  const float3 Le = ld3(s.radiance);
+  float3 L = zero3();
+  bool alive = act;
+  cont = false;
+  alb = zero3();
+  nd[0] = nd[1] = 0.f;
+  nd[2] = 1.f;
+  Hit h, h_unused;
+  trace_closest2_warp(s, o, d, o, d, alive, false, -1, -1, h, h_unused);
+  if (alive && h.tri < 0) alive = false;
+  h0 = h;
+  Vertex x;
+  x.k = -1;
+  x.p[0] = x.p[1] = x.p[2] = 0.f;
+  float n32[3] = {0.f, 0.f, 1.f};
+  if (alive) {
+    load_vertex(s, h.tri, h.b1, h.b2, d, x);
+    alb = ld3(s.albedo + 3 * x.k);
+    if (s.light_of_tri[x.k] >= 0 && x.side < 0.0f) L += Le;
+    shading_normal32(x, n32);
+  }
+  if (s.L > 0) {
+    uint4 r = rng4(op.key, c0, c1, kLight, 0u, pass, op.scene_id);
+    LightSample ls;
+    sample_light(s, r, ls);
+    float sd[3] = {0.f, 0.f, 1.f};
+    if (alive)
+      for (int i = 0; i < 3; ++i) sd[i] = fs(ls.y[i], x.p[i]);
+    bool occ = false, occ_unused;
+    trace_any2_warp(s, x.p, sd, x.k, ls.lt, x.p, sd, -1, -1, alive, false, kShadowTmax, occ, occ_unused);
+    if (alive && !occ) {
+      float g = nee_geometry(s, f3(x.p), f3(n32), ls);
+      L += (kInvPi * g) * (alb * Le);
+    }
+  }
+  if (alive && md > 1) {
+    uint4 r = rng4(op.key, c0, c1, kBsdf, 0u, pass, op.scene_id);
+    cosine_dir(n32, u01f(r.x), u01f(r.y), nd);
+    cont = dot(f3(n32), f3(nd)) > 0.f;
+  }
   return L;
 }
 
@@ -1690,7 +1754,7 @@ __device__ __forceinline__ unsigned long long sec_slot(const unsigned long long*
 // Stage 1: side rays of every queued sample; samples above the last vertex
 // start their continuation paths in state buffer 0.
 template <int kSel>
-__global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_sides(BatchScene bs) {
+__global__ void __launch_bounds__(kBlock, DRT_SIDES_MIN_BLOCKS) k_sec_sides(BatchScene bs) {
   const SceneView& s = bs.v;
   const Opts& op = bs.op;
   int md = op.primary_only ? 1 : min(op.max_depth, kMaxDepth);
@@ -1747,18 +1811,49 @@ __global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_sides(BatchS
   }
 }
 
-// Stage 2: every live pair of continuation paths in state buffer `in`
-// advances by one vertex: next-event estimation at the vertex (both sides in
-// one any-hit traversal) and, above the last vertex, the continuation
-// direction and its closest hit (both sides in one traversal); pairs with a
-// side still alive go to the other buffer.
-__global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_bounce(BatchScene bs, int in) {
+// Continuation paths in stages, shared by the secondary and the primary edge
+// samples: one launch per path vertex advances every live pair of side paths
+// (both sides of one edge sample, a tiny offset apart, with the same random
+// numbers) by one vertex.  An entry holds either the hits at its vertex or,
+// when `pending`, the rays leaving the previous vertex (origin = that
+// vertex's FP32 hit point, recomputed from its triangle and barycentrics);
+// pending rays are traced first, both sides in one traversal.
+struct PathStage {
+  float4* path[2];             // state buffers (SecPathState), ping-pong
+  unsigned long long* count;   // [2] entries in each buffer
+  float* lr;                   // [slots, 6] radiance gathered by each side
+};
+enum { kSrcSecondary = 0, kSrcPrimary = 1 };
+constexpr int kPathPending = 1024;
+
+__device__ __forceinline__ void path_push(const PathStage& ps, int buf, bool push, const SecPathState& st) {
+  int lane = threadIdx.x & 31;
+  unsigned m = __ballot_sync(kFull, push);
+  if (!m) return;
+  int leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(ps.count + buf, (unsigned long long)__popc(m));
+  base = __shfl_sync(kFull, base, leader);
+  if (push) {
+    unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
+    reinterpret_cast<SecPathState*>(ps.path[buf])[slot] = st;
+  }
+}
+
+// Every live pair in buffer `in`: (pending rays traced first) next-event
+// estimation at its vertex, and above the last vertex the continuation
+// directions, pushed as pending rays to the other buffer.  Random numbers:
+// secondary samples use the counters of their queued (sample, vertex) and
+// pass kPassSecondaryBase + vertex; primary samples (slot = position in
+// screen order) the edge sample's index and kPassPrimaryEdge.
+template <int kSrc>
+__global__ void __launch_bounds__(kBlock, DRT_BOUNCE_MIN_BLOCKS) k_path_bounce(BatchScene bs, PathStage ps, int in) {
   const SceneView& s = bs.v;
   const Opts& op = bs.op;
   int md = op.primary_only ? 1 : min(op.max_depth, kMaxDepth);
   const float3 Le = ld3(s.radiance);
-  unsigned long long count = bs.sec_path_count[in];
-  const SecPathState* src = reinterpret_cast<const SecPathState*>(bs.sec_path[in]);
+  unsigned long long count = ps.count[in];
+  const SecPathState* src = reinterpret_cast<const SecPathState*>(ps.path[in]);
   for (unsigned long long base = (unsigned long long)blockIdx.x * kBlock; base < count;
        base += (unsigned long long)gridDim.x * kBlock) {
     unsigned long long e = base + threadIdx.x;
@@ -1767,11 +1862,18 @@ __global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_bounce(Batch
     if (e < count) {
       st = src[e];
       unsigned long long q = (uint32_t)st.e.x;
-      unsigned long long item = bs.sec_queue[q];
-      int64_t i = (int64_t)(item >> 3);
-      int b0 = (int)(item & 7u);
-      uint32_t c0 = (uint32_t)(i / op.spp), c1 = (uint32_t)(i % op.spp);
-      uint32_t pass = kPassSecondaryBase + (uint32_t)b0;
+      uint32_t c0, c1, pass;
+      if (kSrc == kSrcSecondary) {
+        unsigned long long item = bs.sec_queue[q];
+        int64_t i = (int64_t)(item >> 3);
+        c0 = (uint32_t)(i / op.spp);
+        c1 = (uint32_t)(i % op.spp);
+        pass = kPassSecondaryBase + (uint32_t)(item & 7u);
+      } else {
+        c0 = bs.order ? (uint32_t)bs.order[q] : (uint32_t)q;
+        c1 = 0u;
+        pass = kPassPrimaryEdge;
+      }
       int bb = st.e.w & 255;
       bool alive[2] = {(st.e.w & 256) != 0, (st.e.w & 512) != 0};
       float d[2][3] = {{st.a.x, st.a.y, st.a.z}, {st.b.x, st.b.y, st.b.z}};
@@ -1779,6 +1881,18 @@ __global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_bounce(Batch
       Hit h[2];
       h[0].tri = st.e.y; h[0].b1 = st.d.x; h[0].b2 = st.d.y; h[0].t = 0.f;
       h[1].tri = st.e.z; h[1].b1 = st.d.z; h[1].b2 = st.d.w; h[1].t = 0.f;
+      if (st.e.w & kPathPending) {
+        float o[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        int exclude[2] = {-1, -1};
+        for (int k = 0; k < 2; ++k) {
+          if (!alive[k]) continue;
+          Vertex xo;
+          load_vertex(s, h[k].tri, h[k].b1, h[k].b2, d[k], xo);
+          for (int j = 0; j < 3; ++j) o[k][j] = xo.p[j];
+          exclude[k] = h[k].tri;
+        }
+        trace_closest2(s, o[0], d[0], o[1], d[1], alive[0], alive[1], exclude[0], exclude[1], h[0], h[1]);
+      }
       Vertex x[2];
       float3 alb[2];
       for (int k = 0; k < 2; ++k) {
@@ -1803,7 +1917,7 @@ __global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_bounce(Batch
           bool occ[2];
           trace_any2(s, x[0].p, sd[0], x[0].k, ls.lt, x[1].p, sd[1], x[1].k, ls.lt, alive[0], alive[1],
                      kShadowTmax, occ[0], occ[1]);
-          float* lr = bs.sec_lr + 6 * q;
+          float* lr = ps.lr + 6 * q;
           for (int k = 0; k < 2; ++k)
             if (alive[k] && !occ[k]) {
               float g = nee_geometry(s, f3(x[k].p), f3(n32[k]), ls);
@@ -1815,41 +1929,34 @@ __global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_bounce(Batch
         }
         if (bb + 1 < md) {
           uint4 r = rng4(op.key, c0, c1, kBsdf, (uint32_t)bb, pass, op.scene_id);
-          int exclude[2] = {-1, -1};
-          float o[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
           for (int k = 0; k < 2; ++k) {
             if (!alive[k]) continue;
             float nd[3];
             cosine_dir(n32[k], u01f(r.x), u01f(r.y), nd);
             if (!(dot(f3(n32[k]), f3(nd)) > 0.f)) { alive[k] = false; continue; }
             beta[k] = beta[k] * alb[k];
-            for (int j = 0; j < 3; ++j) { o[k][j] = x[k].p[j]; d[k][j] = nd[j]; }
-            exclude[k] = x[k].k;
+            for (int j = 0; j < 3; ++j) d[k][j] = nd[j];
           }
           if (alive[0] || alive[1]) {
-            trace_closest2(s, o[0], d[0], o[1], d[1], alive[0], alive[1], exclude[0], exclude[1], h[0], h[1]);
-            for (int k = 0; k < 2; ++k)
-              if (alive[k] && h[k].tri < 0) alive[k] = false;
-            if (alive[0] || alive[1]) {
-              push = true;
-              st.a = make_float4(d[0][0], d[0][1], d[0][2], beta[0].x);
-              st.b = make_float4(d[1][0], d[1][1], d[1][2], beta[0].y);
-              st.c = make_float4(beta[0].z, beta[1].x, beta[1].y, beta[1].z);
-              st.d = make_float4(h[0].b1, h[0].b2, h[1].b1, h[1].b2);
-              st.e = make_int4(st.e.x, h[0].tri, h[1].tri, (bb + 1) | (alive[0] ? 256 : 0) | (alive[1] ? 512 : 0));
-            }
+            push = true;
+            st.a = make_float4(d[0][0], d[0][1], d[0][2], beta[0].x);
+            st.b = make_float4(d[1][0], d[1][1], d[1][2], beta[0].y);
+            st.c = make_float4(beta[0].z, beta[1].x, beta[1].y, beta[1].z);
+            st.d = make_float4(h[0].b1, h[0].b2, h[1].b1, h[1].b2);
+            st.e = make_int4(st.e.x, alive[0] ? h[0].tri : -1, alive[1] ? h[1].tri : -1,
+                             (bb + 1) | (alive[0] ? 256 : 0) | (alive[1] ? 512 : 0) | kPathPending);
           }
         }
       }
     }
-    sec_push_path(bs, in ^ 1, push, st);
+    path_push(ps, in ^ 1, push, st);
   }
 }
 
 // Stage 3: the edge term of every queued sample from its stored side hits
 // and continuation radiance; vertex gradients through the block cache.
 template <int kSel>
-__global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_finish(BatchScene bs) {
+__global__ void __launch_bounds__(kBlock, DRT_FINISH_MIN_BLOCKS) k_sec_finish(BatchScene bs) {
   __shared__ GradCache cv;
   const SceneView& s = bs.v;
   const Opts& op = bs.op;
@@ -2000,9 +2107,15 @@ __global__ void k_primary_keys(SceneView s, Opts op, int64_t n_edge, uint32_t* k
 // camera paths of the forward pass); the pair exchanges radiance with one
 // shuffle and the even lane forms the difference, the adjoint and the scatter.
 constexpr int kPrimaryPerRound = kBlock / 2;  // edge samples per block and round
+// kStage: the fused evaluation (kPrimFused); or, for paths beyond one
+// vertex, the first vertex of both side paths with their continuation pushed
+// to the path stages (kPrimFirst), and the edge term from the radiance the
+// stages gathered (kPrimFinish).  Same samples, lanes and partial-sum rows.
+enum { kPrimFused = 0, kPrimFirst = 1, kPrimFinish = 2 };
+template <int kStage = kPrimFused>
 __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op, const float* d_image, Grads gr,
                                               int64_t n_edge, int64_t per_thread, const int32_t* order,
-                                              int64_t blk) {
+                                              int64_t blk, PathStage ps = PathStage{}) {
   float g[kGlobals];
   for (int i = 0; i < kGlobals; ++i) g[i] = 0.f;
   double ptotal = s.pcdf[s.E - 1];
@@ -2035,11 +2148,55 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
       float ys = side == 0 ? fa(y, fm(eps, ny)) : fs(y, fm(eps, ny));
       int px = min(max((int)floorf(x), 0), s.W - 1), py = min(max((int)floorf(y), 0), s.H - 1);
       w = ld3(d_image + 3 * ((int64_t)py * s.W + px));
-      camera_ray(s, xs, ys, o, d);
+      if (kStage != kPrimFinish) camera_ray(s, xs, ys, o, d);
     }
-    float3 Lme = path_value_warp(s, op, o, d, active, (uint32_t)j, 0u, kPassPrimaryEdge, nullptr, nullptr, 0, 0);
-    float3 Lot = make_float3(__shfl_xor_sync(kFull, Lme.x, 1), __shfl_xor_sync(kFull, Lme.y, 1),
-                             __shfl_xor_sync(kFull, Lme.z, 1));
+    float3 Lme, Lot;
+    if (kStage == kPrimFused) {
+      Lme = path_value_warp(s, op, o, d, active, (uint32_t)j, 0u, kPassPrimaryEdge, nullptr, nullptr, 0, 0);
+      Lot = make_float3(__shfl_xor_sync(kFull, Lme.x, 1), __shfl_xor_sync(kFull, Lme.y, 1),
+                        __shfl_xor_sync(kFull, Lme.z, 1));
+    } else if (kStage == kPrimFirst) {
+      bool cont;
+      Hit h0;
+      float nd[3];
+      float3 alb;
+      float3 L0 = path_first_vertex_warp(s, op, o, d, active, (uint32_t)j, 0u, kPassPrimaryEdge, cont, h0, nd, alb);
+      if (active) {
+        float* lr = ps.lr + 6 * i + 3 * side;
+        lr[0] = L0.x;
+        lr[1] = L0.y;
+        lr[2] = L0.z;
+      }
+      // the pair's two continuation rays become one pending entry of the
+      // path stages, pushed by the even lane
+      cont = cont && active;
+      bool cont1 = __shfl_xor_sync(kFull, cont, 1);
+      int tri1 = __shfl_xor_sync(kFull, h0.tri, 1);
+      float b11 = __shfl_xor_sync(kFull, h0.b1, 1), b21 = __shfl_xor_sync(kFull, h0.b2, 1);
+      float nd1[3] = {__shfl_xor_sync(kFull, nd[0], 1), __shfl_xor_sync(kFull, nd[1], 1),
+                      __shfl_xor_sync(kFull, nd[2], 1)};
+      float3 alb1 = make_float3(__shfl_xor_sync(kFull, alb.x, 1), __shfl_xor_sync(kFull, alb.y, 1),
+                                __shfl_xor_sync(kFull, alb.z, 1));
+      bool push = side == 0 && (cont || cont1);
+      SecPathState st;
+      if (push) {
+        st.a = make_float4(nd[0], nd[1], nd[2], alb.x);
+        st.b = make_float4(nd1[0], nd1[1], nd1[2], alb.y);
+        st.c = make_float4(alb.z, alb1.x, alb1.y, alb1.z);
+        st.d = make_float4(h0.b1, h0.b2, b11, b21);
+        st.e = make_int4((int)(uint32_t)i, cont ? h0.tri : -1, cont1 ? tri1 : -1,
+                         1 | (cont ? 256 : 0) | (cont1 ? 512 : 0) | kPathPending);
+      }
+      path_push(ps, 0, push, st);
+      continue;
+    } else {
+      Lme = Lot = zero3();
+      if (active && side == 0) {
+        const float* lr = ps.lr + 6 * i;
+        Lme = make_float3(lr[0], lr[1], lr[2]);
+        Lot = make_float3(lr[3], lr[4], lr[5]);
+      }
+    }
     if (side != 0) active = false;
     if (active) {
       int e = es.e;
@@ -2061,12 +2218,22 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
     scatter3(gr.verts, ia, da3, active);
     scatter3(gr.verts, ib, db3, active);
   }
-  block_globals(g, gr.partials + blk * kGlobals, false);
+  if (kStage != kPrimFirst) block_globals(g, gr.partials + blk * kGlobals, false);
 }
 __global__ void __launch_bounds__(kBlock, DRT_PRIMARY_MIN_BLOCKS) k_backward_primary(SceneView s, Opts op, const float* d_image, Grads gr,
                                                              int64_t n_edge, int64_t per_thread,
                                                              const int32_t* order) {
   primary_block(s, op, d_image, gr, n_edge, per_thread, order, blockIdx.x);
+}
+__global__ void __launch_bounds__(kBlock, DRT_PRIMARY_MIN_BLOCKS)
+    k_primary_first(SceneView s, Opts op, const float* d_image, Grads gr, int64_t n_edge, int64_t per_thread,
+                    const int32_t* order, PathStage ps) {
+  primary_block<kPrimFirst>(s, op, d_image, gr, n_edge, per_thread, order, blockIdx.x, ps);
+}
+__global__ void __launch_bounds__(kBlock, DRT_PRIMARY_MIN_BLOCKS)
+    k_primary_finish(SceneView s, Opts op, const float* d_image, Grads gr, int64_t n_edge, int64_t per_thread,
+                     const int32_t* order, PathStage ps) {
+  primary_block<kPrimFinish>(s, op, d_image, gr, n_edge, per_thread, order, blockIdx.x, ps);
 }
 
 __global__ void k_debug_closest(SceneView s, int64_t n, const float* o, const float* d, int32_t* tri, float* tb) {
@@ -2334,12 +2501,14 @@ cudaError_t launch_secondary_apart(const BatchScene& b, cudaStream_t st) {
     DRT_PROF_LAUNCH("backward_secondary_sides", st, k_sec_sides<kSelLength><<<(unsigned)grid, kBlock, 0, st>>>(t));
   int64_t grid_p = std::min<int64_t>((b.sec_path_cap + kBlock - 1) / kBlock, 152 * 8);
   t.v.counters = counter_slot(kSlotBwdSecBounce);
+  PathStage ps{{b.sec_path[0], b.sec_path[1]}, b.sec_path_count, b.sec_lr};
   for (int level = 0; level + 1 < md; ++level) {
     int in = level & 1;
     e = cudaMemsetAsync(b.sec_path_count + (in ^ 1), 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     DRT_PROF_LAUNCH("backward_secondary_bounce", st,
-                    k_sec_bounce<<<(unsigned)std::max<int64_t>(grid_p, 1), kBlock, 0, st>>>(t, in));
+                    k_path_bounce<kSrcSecondary><<<(unsigned)std::max<int64_t>(grid_p, 1), kBlock, 0, st>>>(
+                        t, ps, in));
   }
   BatchScene f = b;
   f.v.counters = nullptr;
@@ -2358,7 +2527,8 @@ int64_t secondary_path_capacity(int W, int H, const Opts& op) {
 
 cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape* tape, const float* d_image,
                             float* d_verts, float* d_albedo, float* d_radiance, float* d_cam, float* d_cam_scale,
-                            float* partials, const SortBuffers* sort, const SecScratch* secs, cudaStream_t st) {
+                            float* partials, const SortBuffers* sort, const SecScratch* secs, const PrimScratch* prims,
+                            cudaStream_t st) {
   SceneView s = sc->view();
   if (op.proposal == 0) s.seg_cdf = nullptr;
   int npix = s.W * s.H;
@@ -2466,12 +2636,46 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
     cudaMemsetAsync(partials, 0, sizeof(float) * kGlobals * blocks_i, st);
   }
   Grads ge{d_verts, d_albedo, partials + (need_i ? blocks_i : 0) * kGlobals};
-  if (blocks_e > 0) {
+  int md = op.primary_only ? 1 : std::min(op.max_depth, kMaxDepth);
+  bool prim_staged = blocks_e > 0 && md > 1 && prims && prims->cap >= n_edge && prims->lr && prims->path[0] &&
+                     prims->path[1] && prims->count && n_edge < (int64_t(1) << 31);
+  if (blocks_e > 0 && !prim_staged) {
     if (forked) cudaStreamWaitEvent(st, sc->ctx->join, 0);
     s.counters = counter_slot(kSlotBwdPrimary);
     ProfToken pt = prof_begin("backward_primary_edges", st);
     k_backward_primary<<<(unsigned)blocks_e, kBlock, 0, st>>>(s, op, d_image, ge, n_edge, per_thread, order);
     prof_end(pt, st);
+  } else if (prim_staged) {
+    // beyond one vertex: the first vertex of both side paths (coherent rays in
+    // screen order, warp-cooperative traversal), the rest of the paths one
+    // vertex per launch, then the edge term from the gathered radiance
+    if (forked) cudaStreamWaitEvent(st, sc->ctx->join, 0);
+    PathStage ps{{prims->path[0], prims->path[1]}, prims->count, prims->lr};
+    cudaError_t e = cudaMemsetAsync(prims->count, 0, 2 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    s.counters = counter_slot(kSlotBwdPrimary);
+    DRT_PROF_LAUNCH("backward_primary_first", st,
+                    k_primary_first<<<(unsigned)blocks_e, kBlock, 0, st>>>(s, op, d_image, ge, n_edge, per_thread,
+                                                                            order, ps));
+    BatchScene t;
+    std::memset(&t, 0, sizeof(t));
+    t.v = s;
+    t.v.counters = counter_slot(kSlotBwdPrimBounce);
+    t.op = op;
+    t.order = order;
+    int64_t grid_p = std::min<int64_t>((n_edge + kBlock - 1) / kBlock, 152 * 8);
+    for (int level = 0; level + 1 < md; ++level) {
+      int in = level & 1;
+      e = cudaMemsetAsync(prims->count + (in ^ 1), 0, sizeof(unsigned long long), st);
+      if (e != cudaSuccess) return e;
+      DRT_PROF_LAUNCH("backward_primary_bounce", st,
+                      k_path_bounce<kSrcPrimary><<<(unsigned)std::max<int64_t>(grid_p, 1), kBlock, 0, st>>>(
+                          t, ps, in));
+    }
+    s.counters = nullptr;
+    DRT_PROF_LAUNCH("backward_primary_finish", st,
+                    k_primary_finish<<<(unsigned)blocks_e, kBlock, 0, st>>>(s, op, d_image, ge, n_edge, per_thread,
+                                                                             order, ps));
   }
   cudaError_t e = launch_reduce_globals(partials, (need_i ? blocks_i : 0) + blocks_e, d_radiance, d_cam, d_cam_scale,
                                         st);
