@@ -22,8 +22,8 @@
  *     work of a call is enqueued on it, in order.
  *   - Arrays are C-order float32 / int32 unless stated.  Images are [H,W,3],
  *     row 0 at the top of the view.
- *   - Every call returns a drt_status; none throws.  drt_last_error() gives a
- *     message for the last failing call on this thread.
+ *   - Every call returns a drt_status; none throws.  drt_last_error(ctx)
+ *     gives a message for the last failing call on this thread.
  *   - Objects (context, scene, tape) are owned by the library and freed with
  *     the matching *_free / drt_destroy call.  Caller arrays are borrowed for
  *     the duration of the call only; the library keeps its own copies.
@@ -145,16 +145,39 @@ typedef struct {
                                    edge_begin <= j < edge_end (the index that selects the sample's
                                    random numbers, before the samples are sorted by screen position);
                                    edge_end <= 0 selects every sample */
+  int32_t aov;                  /* geometry buffers (the AOV extension of Sec. 5.4): 0 the image as set
+                                   by primary_only; 1 the albedo of the first hit (same as
+                                   primary_only = 1); 2 the world position of the first hit; 3 its
+                                   unit shading normal, flipped to face the ray; 4 its distance from
+                                   the ray origin (in all three channels).  Pixels without a hit are
+                                   0.  aov > 0 implies primary_only; the backward pass returns the
+                                   interior derivative of the buffer and the primary edge term of
+                                   its discontinuities, so a deferred shading of the buffers written
+                                   by the caller differentiates end to end */
 } drt_render_opts;
 
 /* Gradient outputs: device or host arrays, each may be NULL (not wanted).
- * Values are ADDED to what the arrays hold. */
+ * Values are ADDED to what the arrays hold.
+ * Flat parameter layout (jac_param): [0, 3V) vertex coordinates (vertex-
+ * major), [3V, 3V+3T) albedo, then radiance (3), camera rows 0..2 (12),
+ * camera scale (1). */
 typedef struct {
   float* d_verts;        /* [n_verts,3] */
   float* d_albedo;       /* [n_tris,3] */
   float* d_radiance;     /* [3] */
   float* d_cam_to_world; /* [3,4] rows 0..2 of the camera matrix */
   float* d_cam_scale;    /* [1] */
+  float* dimage_dparam;  /* [n_jac,H,W] or NULL: per-pixel gradient image (drt_render_backward only): for
+                            each listed parameter k and pixel p, the part of d loss / d theta_k that the
+                            samples of pixel p contribute (interior and secondary samples by their camera
+                            path's pixel, primary edge samples by the pixel containing their point; summed
+                            over the pixels it is the gradient entry).  With d_image set to one pixel's
+                            channel weights it is that pixel's derivative; with d_image = 1 it is the
+                            derivative image of the summed channels, the per-pixel images of the
+                            finite-difference validation of Sec. 5.4.1 */
+  int32_t n_jac;         /* 0..8 listed parameters */
+  int32_t pad_;
+  int64_t jac_param[8];  /* their flat indices (layout above) */
 } drt_grads;
 
 /* Create a context on CUDA device `device` (owns the device error flag and
@@ -332,6 +355,64 @@ drt_status drt_mlp_backward(drt_context* ctx, const void* x, const float* target
 drt_status drt_adam_step(drt_context* ctx, float* params, const float* grads, float* m1, float* m2, void* params_bf16,
                          int64_t n, float lr, float beta1, float beta2, float eps, int32_t step, void* stream);
 
+/* ---- Training the network from logged edge contributions ----------------
+ * The training data come from the plain sampler itself: backward passes of
+ * the primary edge term with proposal 1 and all segment weights 0 (the
+ * length distribution over the tile segments) add |w . (f_u - f_l)| of every
+ * primary edge sample to its segment (opts.seg_log).  One drt_mlp_log holds
+ * one scene's record. */
+typedef struct {
+  const void* x;          /* [n,32] bf16 features of the segments (drt_segment_features), device */
+  const float* seg_log;   /* [n] logged sums of |w . (f_u - f_l)| per segment, device */
+  const double* seg_len;  /* [n] screen lengths of the segments (drt_scene_segments), device */
+  int64_t n;              /* segments (rows) */
+  double n_samples;       /* primary edge samples behind seg_log (passes x edge_spp x W x H) */
+} drt_mlp_log;
+
+/* The network's parameters and optimiser state, all device arrays in the
+ * order w1 [64,32], b1 [64], w2 [64,64], b2 [64], w3 [64], b3 [1]. */
+typedef struct {
+  float* p[6];      /* FP32 master weights, updated in place */
+  float* m1[6];     /* Adam first moments */
+  float* m2[6];     /* Adam second moments */
+  float* g[6];      /* gradients of the last step (overwritten every step) */
+  void* w1_bf16;    /* [64,32] BF16 copy of w1 read by drt_mlp_forward, refreshed every step */
+  void* w2_bf16;    /* [64,64] BF16 copy of w2 */
+  int64_t step;     /* Adam steps taken so far; advanced by drt_mlp_train */
+} drt_mlp_state;
+
+typedef struct {
+  int32_t steps;        /* Adam steps of this call (>= 0) */
+  int32_t batch;        /* rows per step; 0 selects 16384 (at most the number of rows) */
+  float lr;             /* peak learning rate; 0 selects 3e-3 (cosine decay to lr/10 over the call) */
+  float delta;          /* offset of the target's logarithm; 0 selects 1e-3 */
+  uint64_t seed;        /* shuffle of the rows */
+  float* loss;          /* device [1] or NULL: the steps' losses are added to it */
+  float* rows_target;   /* device or host [rows] or NULL: the training targets in shuffled order */
+  float* rows_mask;     /* device or host [rows] or NULL: the regression weights in shuffled order */
+  int64_t* rows_index;  /* device [rows] or NULL: the concatenated row behind each training row */
+} drt_mlp_train_opts;
+
+/* Train the network on the rows of n_logs logged scenes (the project's
+ * counterpart of the thesis's edge importance of Sec. 5.3.1, learned from the
+ * plain sampler's edge contributions).  For a segment of screen length len
+ * with logged sum S out of N logging samples, in a scene whose segments total
+ * screen length L and logged sum S_tot, S L / N estimates the segment's
+ * integral of |w . (f_u - f_l)|; the target is
+ *   log( (S L / (N len)) / (S_tot / N) + delta )
+ * (the log contribution density per unit length relative to the scene's
+ * mean) and the regression weight len / (L / n).  The rows of all scenes are
+ * concatenated in order and shuffled by sorting one Philox draw per row
+ * (counter (row, 0, 0x4D4C5054, 0), key = seed); training step i uses the
+ * batch (i mod floor(rows/batch)) of the shuffled rows, the loss of
+ * drt_mlp_backward with inv_n = 1/batch and bias-corrected Adam (0.9, 0.999,
+ * 1e-8) at lr (0.55 + 0.45 cos(pi i / steps)).  Allocates its scratch,
+ * synchronises `stream` before returning.  Errors: DRT_ERR_INVALID_ARG (NULL
+ * arrays, host log arrays, empty logs, more than 2^31 - 1 rows), DRT_ERR_OOM,
+ * DRT_ERR_CUDA, DRT_ERR_TIMEOUT-class device flags through drt_check_device. */
+drt_status drt_mlp_train(drt_context* ctx, const drt_mlp_log* logs, int32_t n_logs, const drt_mlp_train_opts* o,
+                         drt_mlp_state* state, void* stream);
+
 /* Features of every tile segment for the network, [n_seg, 32] bf16 device
  * array (n_seg from drt_scene_segments): tile centre, segment end points,
  * lengths, camera-space normals of the edge's faces, silhouette and boundary
@@ -407,8 +488,11 @@ drt_status drt_probe_l2(drt_context* ctx, int64_t bytes, double* bytes_per_s, vo
  * cleared. */
 drt_status drt_check_device(drt_context* ctx, void* stream, int32_t* code, int32_t* info);
 
-/* Message of the last failing call on this thread (static storage). */
-const char* drt_last_error(void);
+/* Message of the last failing call on this thread (thread-local storage,
+ * valid until the next failing call on the thread).  ctx may be NULL: the
+ * message is kept per thread, so a failure before a context exists (e.g. in
+ * drt_create) is reported too. */
+const char* drt_last_error(drt_context* ctx);
 
 /* Library version string. */
 const char* drt_version(void);

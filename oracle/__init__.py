@@ -49,7 +49,8 @@ class _Opts(ctypes.Structure):
                 ("edge_begin", ctypes.c_int64), ("edge_end", ctypes.c_int64), ("n_threads", ctypes.c_int32),
                 ("scene_id", ctypes.c_int32), ("proposal", ctypes.c_int32), ("seg_weights", ctypes.c_void_p),
                 ("n_seg_weights", ctypes.c_int64), ("sec_sampler", ctypes.c_int32), ("sec_tree_samples", ctypes.c_int32),
-                ("sec_point", ctypes.c_int32)]
+                ("sec_point", ctypes.c_int32), ("n_jac", ctypes.c_int32), ("jac_param", ctypes.c_int64 * 8),
+                ("aov", ctypes.c_int32)]
 
 
 def lib():
@@ -76,15 +77,20 @@ class _Pinned:
                         float(scene.cam_scale))
 
 
+AOV_ALBEDO, AOV_POSITION, AOV_NORMAL, AOV_DEPTH = 1, 2, 3, 4
+
+
 def _opts(spp, edge_spp, max_depth, primary_only, seed, eps_rel, terms, pixels, edges, n_threads, scene_id,
-          weights=None, mode=1, sec_tree_samples=0, sec_point=0):
+          weights=None, mode=1, sec_tree_samples=0, sec_point=0, aov=0):
     pb, pe = pixels if pixels is not None else (0, 0)
     eb, ee = edges if edges is not None else (0, 0)
     wp, wn = (weights.ctypes.data, len(weights)) if weights is not None else (None, 0)
-    return _Opts(int(spp), int(edge_spp), int(max_depth), int(bool(primary_only)), int(seed) & (2 ** 64 - 1),
-                 float(eps_rel), int(terms), int(pb), int(pe), int(eb), int(ee),
-                 int(n_threads or n_threads_default()), int(scene_id), mode if weights is not None else 0, wp, wn,
-                 1 if sec_tree_samples > 0 else 0, int(sec_tree_samples), int(sec_point))
+    o = _Opts(int(spp), int(edge_spp), int(max_depth), int(bool(primary_only) or aov > 0), int(seed) & (2 ** 64 - 1),
+              float(eps_rel), int(terms), int(pb), int(pe), int(eb), int(ee),
+              int(n_threads or n_threads_default()), int(scene_id), mode if weights is not None else 0, wp, wn,
+              1 if sec_tree_samples > 0 else 0, int(sec_tree_samples), int(sec_point))
+    o.aov = int(aov)
+    return o
 
 
 def num_params(scene) -> int:
@@ -104,11 +110,12 @@ def split_params(scene, g: np.ndarray) -> dict:
 
 
 def render(scene, *, spp: int, seed: int, max_depth: int = 1, primary_only: bool = False,
-           pixels=None, n_threads=None, scene_id: int = 0) -> np.ndarray:
+           pixels=None, n_threads=None, scene_id: int = 0, aov: int = 0) -> np.ndarray:
     """Image [H,W,3] (FP64).  ``pixels=(begin,end)`` restricts to a linear
-    pixel range; other pixels are NaN."""
+    pixel range; other pixels are NaN.  aov > 0 renders a geometry buffer of
+    the first hit (AOV_ALBEDO, AOV_POSITION, AOV_NORMAL, AOV_DEPTH)."""
     P = _Pinned(scene)
-    o = _opts(spp, spp, max_depth, primary_only, seed, EPS_REL, 0, pixels, None, n_threads, scene_id)
+    o = _opts(spp, spp, max_depth, primary_only, seed, EPS_REL, 0, pixels, None, n_threads, scene_id, aov=aov)
     img = np.full((scene.height, scene.width, 3), np.nan, np.float64)
     rc = lib().or_render(ctypes.byref(P.s), ctypes.byref(o), img.ctypes.data_as(ctypes.c_void_p))
     if rc != 0:
@@ -119,7 +126,8 @@ def render(scene, *, spp: int, seed: int, max_depth: int = 1, primary_only: bool
 def backward(scene, d_image: np.ndarray, *, spp: int, edge_spp: int, seed: int, max_depth: int = 1,
              primary_only: bool = False, terms: int = TERMS_ALL, eps_rel: float = EPS_REL, pixels=None,
              edges=None, n_threads=None, scene_id: int = 0, proposal_weights=None, proposal_scores=None,
-             sec_tree_samples: int = 0, sec_point: int = 0, contributions: bool = False):
+             sec_tree_samples: int = 0, sec_point: int = 0, contributions: bool = False, jacobian=None,
+             aov: int = 0):
     """Gradient of sum(d_image * image) as a flat FP64 vector, and per entry
     the magnitude of the terms summed into it (absolute-value chain rule),
     which scales the rounding error an FP32 implementation may make.
@@ -132,7 +140,9 @@ def backward(scene, d_image: np.ndarray, *, spp: int, edge_spp: int, seed: int, 
     density over the edge's arc, mixed with uniform (else uniform).
     contributions=True also returns, per entry, the sum over samples of the
     magnitude of each sample's whole contribution, sum_k |c_k| (a third
-    array)."""
+    array).  jacobian: up to 8 flat parameter indices; then the per-pixel
+    shares of those gradient entries, [n, H, W], are returned last.  aov > 0:
+    the gradient of a geometry buffer of the first hit (see render)."""
     if proposal_weights is not None and proposal_scores is not None:
         raise ValueError("give proposal_weights or proposal_scores, not both")
     P = _Pinned(scene)
@@ -142,17 +152,28 @@ def backward(scene, d_image: np.ndarray, *, spp: int, edge_spp: int, seed: int, 
         mode, pw = 2, proposal_scores
     pw = None if pw is None else np.ascontiguousarray(pw, np.float32)
     o = _opts(spp, edge_spp, max_depth, primary_only, seed, eps_rel, terms, pixels, edges, n_threads, scene_id,
-              pw, mode, sec_tree_samples, sec_point)
+              pw, mode, sec_tree_samples, sec_point, aov)
     n = num_params(scene)
     g = np.zeros(n, np.float64)
     a = np.zeros(n, np.float64)
     c = np.zeros(n, np.float64) if contributions else None
-    rc = lib().or_backward3(ctypes.byref(P.s), ctypes.byref(o), w.ctypes.data_as(ctypes.c_void_p),
+    jac = None
+    if jacobian is not None:
+        idx = [int(i) for i in jacobian]
+        if not 1 <= len(idx) <= 8 or min(idx) < 0 or max(idx) >= n:
+            raise ValueError("jacobian takes 1 to 8 parameter indices in [0, %d)" % n)
+        o.n_jac = len(idx)
+        for k, i in enumerate(idx):
+            o.jac_param[k] = i
+        jac = np.zeros((len(idx), scene.height, scene.width), np.float64)
+    rc = lib().or_backward4(ctypes.byref(P.s), ctypes.byref(o), w.ctypes.data_as(ctypes.c_void_p),
                             g.ctypes.data_as(ctypes.c_void_p), a.ctypes.data_as(ctypes.c_void_p),
-                            c.ctypes.data_as(ctypes.c_void_p) if c is not None else None)
+                            c.ctypes.data_as(ctypes.c_void_p) if c is not None else None,
+                            jac.ctypes.data_as(ctypes.c_void_p) if jac is not None else None)
     if rc != 0:
         raise RuntimeError("oracle backward failed (%d)" % rc)
-    return (g, a, c) if contributions else (g, a)
+    out = (g, a, c) if contributions else (g, a)
+    return out + (jac,) if jac is not None else out
 
 
 def edge_point(p, n, v0, v1, u: float, usel: float):
@@ -219,6 +240,33 @@ def segments(scene):
                           lens.ctypes.data_as(ctypes.c_void_p), ctypes.c_int64(cap))
     out = out[:n]
     return out[:, 0].astype(np.int32), out[:, 1].astype(np.int32), out[:, 2:].astype(np.float32), lens[:n]
+
+
+def atan2_pos(y: float, x: float) -> float:
+    """FP32 atan2 for y >= 0 with the oracle's fixed operation order."""
+    f = lib().or_atan2_pos
+    f.restype = ctypes.c_float
+    return float(f(ctypes.c_float(y), ctypes.c_float(x)))
+
+
+def camera_ray(scene, sx: float, sy: float):
+    """FP32 camera ray (origin, direction) through screen point (sx, sy)."""
+    P = _Pinned(scene)
+    o = np.zeros(3, np.float32)
+    d = np.zeros(3, np.float32)
+    lib().or_camera_ray(ctypes.byref(P.s), ctypes.c_float(sx), ctypes.c_float(sy), o.ctypes.data_as(ctypes.c_void_p),
+                        d.ctypes.data_as(ctypes.c_void_p))
+    return o, d
+
+
+def fisheye_project(scene, v):
+    """FP32 screen point of world point v under the fisheye camera, or None."""
+    P = _Pinned(scene)
+    va = np.ascontiguousarray(v, np.float32)
+    sx, sy = ctypes.c_float(), ctypes.c_float()
+    ok = lib().or_fisheye_project(ctypes.byref(P.s), va.ctypes.data_as(ctypes.c_void_p), ctypes.byref(sx),
+                                  ctypes.byref(sy))
+    return (sx.value, sy.value) if ok else None
 
 
 def sincos_2pi(r: float):

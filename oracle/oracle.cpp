@@ -165,6 +165,14 @@ Dual dsqrt(const Dual& a) {
   return scaled(s, s > 0.0 ? 0.5 / s : 0.0, a);
 }
 
+Dual dsin(const Dual& a) { return scaled(std::sin(a.v), std::cos(a.v), a); }
+Dual dcos(const Dual& a) { return scaled(std::cos(a.v), -std::sin(a.v), a); }
+/* atan2(y, x) with d = (x dy - y dx) / (x^2 + y^2). */
+Dual datan2(const Dual& y, const Dual& x) {
+  double r2 = x.v * x.v + y.v * y.v;
+  return lin(std::atan2(y.v, x.v), -y.v / r2, x, x.v / r2, y);
+}
+
 struct D3 { Dual x, y, z; };
 D3 d3(double x, double y, double z) { return D3{Dual(x), Dual(y), Dual(z)}; }
 /* The same tangents at another value (a rounded copy of the point). */
@@ -230,6 +238,11 @@ typedef struct {
   int32_t sec_tree_samples;  /* samples distributed from the hierarchy's root */
   int32_t sec_point;         /* point on a secondary edge: 0 uniform (Sec. 5.2.2); 1 the clamped-cosine
                                 density over the edge's arc mixed with uniform (Sec. 5.3.2) */
+  int32_t n_jac;             /* 0..8 parameters of the per-pixel gradient image */
+  int64_t jac_param[8];      /* their flat indices in the gradient layout */
+  int32_t aov;               /* with primary_only: 0, 1 albedo; 2 world position; 3 unit shading normal
+                                (facing the ray); 4 distance from the ray origin (Sec. 5.4, geometry
+                                buffers) */
 } or_opts_t;
 }
 
@@ -243,16 +256,64 @@ constexpr double INV_PI = 0.31830988618379067;
 
 struct R32 { float o[3], d[3]; };
 
+void sincos_2pi32(float r, float* c_out, float* s_out);
+
+/* atan2(y, x) for y >= 0, in [0, pi], FP32 in a fixed order (no library
+ * call, so both implementations take the same value): the ratio of the
+ * smaller to the larger magnitude in [0, 1]; above tan(pi/12) it is reduced
+ * by atan(a) = pi/6 + atan((sqrt(3) a - 1) / (a + sqrt(3))); then the Taylor
+ * series of atan about 0 to z^13 by Horner's rule (|z| <= tan(pi/12), so the
+ * first omitted term is below 2e-10); then the octant is restored. */
+float atan2_pos32(float y, float x) {
+  float ax = std::fabs(x);
+  bool swap = y > ax;
+  float num = swap ? ax : y, den = swap ? y : ax;
+  float a = den > 0.0f ? num / den : 0.0f;
+  bool red = a > 0.267949194f;
+  float z = red ? (a * 1.73205078f - 1.0f) / (a + 1.73205078f) : a;
+  float z2 = z * z;
+  float p = 0.0769230798f;
+  p = z2 * p + -0.0909090936f;
+  p = z2 * p + 0.111111112f;
+  p = z2 * p + -0.142857149f;
+  p = z2 * p + 0.200000003f;
+  p = z2 * p + -0.333333343f;
+  float r = z + (z * z2) * p;
+  if (red) r = 0.523598790f + r;
+  if (swap) r = 1.57079637f - r;
+  if (x < 0.0f) r = 3.14159274f - r;
+  return r;
+}
+
 /* Camera ray through screen point (sx, sy) in pixel units, y down.  Sec. 5.2.1
- * restricts primary edges to cameras whose projection maps lines to lines:
- * pinhole (looks down -z, y up) and orthographic (spans
- * [-aspect*s, aspect*s] x [-s, s] in camera xy). */
+ * restricts its screen-space edge sampling to cameras whose projection maps
+ * lines to lines: pinhole (looks down -z, y up) and orthographic (spans
+ * [-aspect*s, aspect*s] x [-s, s] in camera xy).  The equidistant fisheye
+ * (cam_type 2, Sec. 5.2 "Cameras with Non-linear Projections") maps the
+ * screen point at distance r from the centre (in units of half the image
+ * height) to the direction at angle theta = r s from the optical axis (-z),
+ * in the azimuth of the screen point; its edges are sampled in 3D. */
 R32 camera_ray32(const or_scene_t& sc, float sx, float sy) {
   const float* M = sc.cam_to_world;
   float fw = (float)sc.width, fh = (float)sc.height;
   float xn = (2.0f * sx - fw) / fw;
   float yn = (fh - 2.0f * sy) / fh;
   float aspect = fw / fh;
+  if (sc.cam_type == 2) {
+    float a = xn * aspect, b = yn;
+    float r = std::sqrt(a * a + b * b);
+    float th = r * sc.cam_scale;
+    float c, sn;
+    sincos_2pi32(th * 0.159154937f, &c, &sn);
+    float k = r > 0.0f ? sn / r : 0.0f;
+    float dc[3] = {a * k, b * k, -c};
+    R32 r32;
+    for (int i = 0; i < 3; ++i) {
+      r32.o[i] = M[4 * i + 3];
+      r32.d[i] = (M[4 * i + 0] * dc[0] + M[4 * i + 1] * dc[1]) + M[4 * i + 2] * dc[2];
+    }
+    return r32;
+  }
   float sxs = aspect * sc.cam_scale;
   float lx = xn * sxs;
   float ly = yn * sc.cam_scale;
@@ -442,6 +503,26 @@ bool project32(const Prep& P, const float v[3], float* sx, float* sy) {
   return true;
 }
 
+/* Equidistant fisheye projection of a world point to screen pixels (FP32,
+ * the inverse of camera_ray32 for cam_type 2).  False near the direction
+ * opposite the optical axis (theta >= 3.1), which no pixel sees. */
+bool fisheye_project32(const Prep& P, const float v[3], float* sx, float* sy) {
+  const float* W = P.w2c;
+  float vc[3];
+  for (int i = 0; i < 3; ++i) vc[i] = ((W[4 * i + 0] * v[0] + W[4 * i + 1] * v[1]) + W[4 * i + 2] * v[2]) + W[4 * i + 3];
+  const or_scene_t& sc = *P.sc;
+  float rho = std::sqrt(vc[0] * vc[0] + vc[1] * vc[1]);
+  float th = atan2_pos32(rho, -vc[2]);
+  if (!(th < 3.1f)) return false;
+  float k = rho > 0.0f ? th / (sc.cam_scale * rho) : 0.0f;
+  float a = k * vc[0], b = k * vc[1];
+  float fw = (float)sc.width, fh = (float)sc.height;
+  float xn = a / (fw / fh);
+  *sx = (xn + 1.0f) * (0.5f * fw);
+  *sy = (1.0f - b) * (0.5f * fh);
+  return true;
+}
+
 /* Liang-Barsky clip of a + t(b-a) to [0,W]x[0,H] (FP32, planes in the order
  * x>=0, x<=W, y>=0, y<=H).  Returns false when nothing is left. */
 bool clip32(float ax, float ay, float bx, float by, float W, float H, float* t0o, float* t1o) {
@@ -515,7 +596,21 @@ void prepare(const or_scene_t* sc, Prep& P) {
   for (int e = 0; e < E; ++e) {
     float ax, ay, bx, by, t0, t1;
     double len = 0.0;
-    if (project32(P, vtx(P, P.e0[e]), &ax, &ay) && project32(P, vtx(P, P.e1[e]), &bx, &by) &&
+    if (sc->cam_type == 2) {
+      /* fisheye: edges are sampled in 3D, by the chord between the unit
+       * directions from the camera to their end points (FP64) */
+      const float *va = vtx(P, P.e0[e]), *vb = vtx(P, P.e1[e]);
+      const float* M = sc->cam_to_world;
+      double da_[3], db_[3];
+      for (int i = 0; i < 3; ++i) { da_[i] = (double)va[i] - (double)M[4 * i + 3]; db_[i] = (double)vb[i] - (double)M[4 * i + 3]; }
+      double la = std::sqrt((da_[0] * da_[0] + da_[1] * da_[1]) + da_[2] * da_[2]);
+      double lb = std::sqrt((db_[0] * db_[0] + db_[1] * db_[1]) + db_[2] * db_[2]);
+      if (la > 0.0 && lb > 0.0) {
+        double u[3];
+        for (int i = 0; i < 3; ++i) u[i] = da_[i] / la - db_[i] / lb;
+        len = std::sqrt((u[0] * u[0] + u[1] * u[1]) + u[2] * u[2]);
+      }
+    } else if (project32(P, vtx(P, P.e0[e]), &ax, &ay) && project32(P, vtx(P, P.e1[e]), &bx, &by) &&
         clip32(ax, ay, bx, by, (float)sc->width, (float)sc->height, &t0, &t1)) {
       P.pax[e] = ax; P.pay[e] = ay; P.pbx[e] = bx; P.pby[e] = by; P.pt0[e] = t0; P.pt1[e] = t1;
       float dx = bx - ax, dy = by - ay;
@@ -540,7 +635,7 @@ void prepare(const or_scene_t* sc, Prep& P) {
   int tiles_x = (int)std::ceil(sc->width / TILE), tiles_y = (int)std::ceil(sc->height / TILE);
   for (int e = 0; e < E; ++e) {
     double le = P.pcdf[e] - (e > 0 ? P.pcdf[e - 1] : 0.0);
-    if (!(le > 0.0)) continue;
+    if (!(le > 0.0) || sc->cam_type == 2) continue;  /* no screen segments for the fisheye */
     float ax = P.pax[e], ay = P.pay[e], t0 = P.pt0[e], t1 = P.pt1[e];
     float dx = P.pbx[e] - ax, dy = P.pby[e] - ay;
     std::vector<float> ts[2];
@@ -657,6 +752,22 @@ void camera_ray_dual(const Prep& P, float sx, float sy, bool track, D3* O, D3* D
   double fw = sc.width, fh = sc.height;
   double xn = (2.0 * sx - fw) / fw, yn = (fh - 2.0 * sy) / fh;
   Dual S = scale_dual(P, track);
+  if (sc.cam_type == 2) {
+    double a = xn * (fw / fh), b = yn, r = std::sqrt(a * a + b * b);
+    Dual th = r * S;
+    Dual sn = dsin(th), cs = dcos(th);
+    Dual dc[3] = {r > 0.0 ? (a / r) * sn : Dual(0.0), r > 0.0 ? (b / r) * sn : Dual(0.0), -cs};
+    Dual Mo[3], Md[3];
+    for (int i = 0; i < 3; ++i) {
+      Dual m0 = cam_dual(P, i, 0, track), m1 = cam_dual(P, i, 1, track), m2 = cam_dual(P, i, 2, track),
+           m3 = cam_dual(P, i, 3, track);
+      Mo[i] = m3;
+      Md[i] = m0 * dc[0] + m1 * dc[1] + m2 * dc[2];
+    }
+    *O = D3{Mo[0], Mo[1], Mo[2]};
+    *D = D3{Md[0], Md[1], Md[2]};
+    return;
+  }
   Dual lx = (xn * (fw / fh)) * S, ly = yn * S;
   Dual Mo[3], Md[3];
   for (int i = 0; i < 3; ++i) {
@@ -701,6 +812,39 @@ void project_dual(const Prep& P, const D3& v, bool track, Dual* sx, Dual* sy) {
   *sy = (1.0 - yn) * (0.5 * fh);
 }
 
+/* Equidistant fisheye projection of a world point (duals; the smooth
+ * counterpart of fisheye_project32). */
+void project_fisheye_dual(const Prep& P, const D3& v, bool track, Dual* sx, Dual* sy) {
+  Dual R[3][3], t[3];
+  for (int i = 0; i < 3; ++i) { for (int j = 0; j < 3; ++j) R[i][j] = cam_dual(P, i, j, track); t[i] = cam_dual(P, i, 3, track); }
+  Dual c00 = R[1][1] * R[2][2] - R[1][2] * R[2][1];
+  Dual c01 = R[1][2] * R[2][0] - R[1][0] * R[2][2];
+  Dual c02 = R[1][0] * R[2][1] - R[1][1] * R[2][0];
+  Dual det = R[0][0] * c00 + R[0][1] * c01 + R[0][2] * c02;
+  Dual inv[3][3];
+  inv[0][0] = c00 / det;
+  inv[0][1] = (R[0][2] * R[2][1] - R[0][1] * R[2][2]) / det;
+  inv[0][2] = (R[0][1] * R[1][2] - R[0][2] * R[1][1]) / det;
+  inv[1][0] = c01 / det;
+  inv[1][1] = (R[0][0] * R[2][2] - R[0][2] * R[2][0]) / det;
+  inv[1][2] = (R[0][2] * R[1][0] - R[0][0] * R[1][2]) / det;
+  inv[2][0] = c02 / det;
+  inv[2][1] = (R[0][1] * R[2][0] - R[0][0] * R[2][1]) / det;
+  inv[2][2] = (R[0][0] * R[1][1] - R[0][1] * R[1][0]) / det;
+  D3 q{v.x - t[0], v.y - t[1], v.z - t[2]};
+  Dual vc[3];
+  for (int i = 0; i < 3; ++i) vc[i] = inv[i][0] * q.x + inv[i][1] * q.y + inv[i][2] * q.z;
+  const or_scene_t& sc = *P.sc;
+  double fw = sc.width, fh = sc.height;
+  Dual S = scale_dual(P, track);
+  Dual rho = dsqrt(vc[0] * vc[0] + vc[1] * vc[1]);
+  Dual th = datan2(rho, -vc[2]);
+  Dual k = th / (S * rho);
+  Dual a = k * vc[0], b = k * vc[1];
+  *sx = (a / (fw / fh) + 1.0) * (0.5 * fw);
+  *sy = (1.0 - b) * (0.5 * fh);
+}
+
 /* Ray/plane hit point of a fixed or moving ray with the (moving) triangle:
  * p = O + tau D, tau = ((v0 - O).N)/(D.N), N the unnormalised face normal. */
 D3 hit_point_dual(const D3& O, const D3& D, const D3& V0, const D3& V1, const D3& V2) {
@@ -720,6 +864,8 @@ struct Ctx {
   double* ga;            /* sum of |contribution| per parameter [P] */
   const EdgeTree* tree = nullptr;  /* secondary edge hierarchy (sec_sampler 1) */
   double* gc = nullptr;  /* sum over accumulate calls of |coef x'| per parameter [P] (or null) */
+  double* jac = nullptr; /* [n_jac, H, W] per-pixel share of the gradient (or null) */
+  int64_t pix = 0;       /* pixel the current sample's contributions belong to */
 };
 
 /* grad += coef * x';  tolerance scale += coef_abs * |x|' (see Dual).  Each
@@ -730,6 +876,10 @@ void accumulate(Ctx& C, double coef, double coef_abs, const Dual& x) {
     C.g[x.idx[i]] += coef * x.d[i];
     C.ga[x.idx[i]] += coef_abs * x.ad[i];
     if (C.gc) C.gc[x.idx[i]] += std::fabs(coef * x.d[i]);
+    if (C.jac)
+      for (int k = 0; k < C.opt->n_jac; ++k)
+        if (C.opt->jac_param[k] == x.idx[i])
+          C.jac[(int64_t)k * C.P->sc->width * C.P->sc->height + C.pix] += coef * x.d[i];
   }
 }
 
@@ -1040,7 +1190,25 @@ void path_radiance(Ctx& C, int depth0, int max_depth, const float o32_in[3], con
     Dual alb[3];
     for (int c = 0; c < 3; ++c) alb[c] = Dual::param(sc.albedo[3 * k + c], P.pA + 3 * k + c, C.track);
     if (op.primary_only) {
-      for (int c = 0; c < 3; ++c) out->c[c] = out->c[c] + beta[c] * alb[c];
+      /* geometry buffers of the first hit (Sec. 5.4): the value is a smooth
+       * function of the hit point and triangle, discontinuous only where the
+       * visible triangle changes, so the primary edge term covers its
+       * discontinuities as for shaded images */
+      if (op.aov == 2) {
+        out->c[0] = out->c[0] + Pd.x;
+        out->c[1] = out->c[1] + Pd.y;
+        out->c[2] = out->c[2] + Pd.z;
+      } else if (op.aov == 3) {
+        out->c[0] = out->c[0] + ns.x;
+        out->c[1] = out->c[1] + ns.y;
+        out->c[2] = out->c[2] + ns.z;
+      } else if (op.aov == 4) {
+        D3 dv = Pd - O;
+        Dual dist = length(dv);
+        for (int c = 0; c < 3; ++c) out->c[c] = out->c[c] + dist;
+      } else {
+        for (int c = 0; c < 3; ++c) out->c[c] = out->c[c] + beta[c] * alb[c];
+      }
       break;
     }
     Dual Le[3];
@@ -1122,6 +1290,81 @@ void jitter(const or_opts_t& op, int pix, int s, int W, float* sx, float* sy) {
   *sy = (float)(pix / W) + u01f(r[1]);
 }
 
+/* ---- primary edge sample of the fisheye (Sec. 5.2, non-linear projections) --
+ * The image of an edge is a curve x(t) = pi(v0 + t (v1 - v0)).  The edge is
+ * picked by its chord on the unit sphere of directions (prepare), t
+ * uniformly in [0, 1), and the two sides are evaluated a small offset apart
+ * across the curve (the offset direction perpendicular to the FP32 chord of
+ * x(t - 1/1024) and x(t + 1/1024), clamped to the edge).  By Reynolds
+ * transport over the pixel integral, a parameter moving the curve with
+ * screen velocity V changes sum_p w_p I_p by -(f_u - f_l) (V . n_u) ds along
+ * it; with ds n_u = perp(x'(t)) dt, the sample contributes
+ * w (f_u - f_l) d(-perp(x'(t)) . x)/d theta / (P(e) N), perp(x') = (-x'_y,
+ * x'_x) pointing to the u side.  Points outside the image contribute zero. */
+void primary_edge_sample_fisheye(Ctx& C, int64_t jj, const uint32_t r[4]) {
+  const Prep& P = *C.P;
+  const or_scene_t& sc = *P.sc;
+  const or_opts_t& op = *C.opt;
+  uint32_t j = (uint32_t)jj;
+  int e = cdf_pick(P.pcdf, u01d(r[0], r[1]) * P.ptotal);
+  double pe = P.pcdf[e] - (e > 0 ? P.pcdf[e - 1] : 0.0);
+  if (!(pe > 0.0)) return;
+  const float *v0 = vtx(P, P.e0[e]), *v1 = vtx(P, P.e1[e]);
+  float t = u01f(r[2]);
+  auto point = [&](float tt, float out[3]) {
+    for (int i = 0; i < 3; ++i) out[i] = v0[i] + tt * (v1[i] - v0[i]);
+  };
+  float p32[3], q0[3], q1[3];
+  point(t, p32);
+  float x, y, x0, y0, x1, y1;
+  if (!fisheye_project32(P, p32, &x, &y)) return;
+  float W = (float)sc.width, H = (float)sc.height;
+  if (!(x >= 0.0f && x < W && y >= 0.0f && y < H)) return;
+  float ta = t - 0.0009765625f, tb = t + 0.0009765625f;
+  if (ta < 0.0f) ta = 0.0f;
+  if (tb > 1.0f) tb = 1.0f;
+  point(ta, q0);
+  point(tb, q1);
+  if (!fisheye_project32(P, q0, &x0, &y0) || !fisheye_project32(P, q1, &x1, &y1)) return;
+  float cx = x1 - x0, cy = y1 - y0;
+  float cl = std::sqrt(cx * cx + cy * cy);
+  if (!(cl > 0.0f)) return;
+  float nx = -cy / cl, ny = cx / cl;
+  float eps = op.eps_rel * std::max(W, H);
+  float xu = x + eps * nx, yu = y + eps * ny, xl = x - eps * nx, yl = y - eps * ny;
+  int px = (int)std::floor(x), py = (int)std::floor(y);
+  C.pix = (int64_t)py * sc.width + px;
+  const float* w = C.w + 3 * ((size_t)py * sc.width + px);
+  double zero[3] = {0, 0, 0};
+  bool saved = C.track;
+  C.track = false;
+  RGB Lu, Ll;
+  camera_path(C, xu, yu, j, 0, PASS_PRIMARY_EDGE, zero, false, &Lu);
+  camera_path(C, xl, yl, j, 0, PASS_PRIMARY_EDGE, zero, false, &Ll);
+  C.track = saved;
+  double diff = 0.0, diff_abs = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    diff += (double)w[c] * (Lu.c[c].v - Ll.c[c].v);
+    diff_abs += std::fabs((double)w[c]) * (std::fabs(Lu.c[c].v) + std::fabs(Ll.c[c].v));
+  }
+  if (diff == 0.0) return;
+  /* the curve point as a function of the parameters, and its tangent */
+  D3 V0 = vert_dual(P, P.e0[e], C.track), V1 = vert_dual(P, P.e1[e], C.track);
+  D3 Pt = V0 + (double)t * (V1 - V0);
+  Dual X, Y;
+  project_fisheye_dual(P, Pt, C.track, &X, &Y);
+  D3 C0 = d3(v0[0], v0[1], v0[2]), C1 = d3(v1[0], v1[1], v1[2]);
+  Dual tt = Dual::param((double)t, 0, true);
+  D3 Pt_t = C0 + tt * (C1 - C0);
+  Dual Xt, Yt;
+  project_fisheye_dual(P, Pt_t, false, &Xt, &Yt);
+  double dxt = Xt.n > 0 ? Xt.d[0] : 0.0, dyt = Yt.n > 0 ? Yt.d[0] : 0.0;
+  Dual alpha = dyt * X - dxt * Y;  /* -perp(x') . x */
+  int64_t N_edge = (int64_t)op.edge_spp * sc.width * sc.height;
+  double k = (P.ptotal / pe) / (double)N_edge;
+  accumulate(C, diff * k, diff_abs * k, alpha);
+}
+
 /* ---- primary edge sample j (Eq. mc with Eq. redner_dirac_jacobian) ------- */
 void primary_edge_sample(Ctx& C, int64_t jj) {
   const Prep& P = *C.P;
@@ -1131,6 +1374,10 @@ void primary_edge_sample(Ctx& C, int64_t jj) {
   uint32_t j = (uint32_t)jj;
   uint32_t r[4];
   rng(op.seed, j, 0, K_EDGE_PRIMARY, 0, PASS_PRIMARY_EDGE, (uint32_t)op.scene_id, r);
+  if (sc.cam_type == 2) {
+    primary_edge_sample_fisheye(C, jj, r);
+    return;
+  }
   int e;
   float t0, t1;
   double inv_pdf_len;  /* 1 / (pdf of the point per unit length) = len_seg / q_seg, or L for the plain sampler */
@@ -1161,6 +1408,7 @@ void primary_edge_sample(Ctx& C, int64_t jj) {
   int px = (int)std::floor(x), py = (int)std::floor(y);
   px = std::min(std::max(px, 0), sc.width - 1);
   py = std::min(std::max(py, 0), sc.height - 1);
+  C.pix = (int64_t)py * sc.width + px;  /* the sample belongs to the pixel containing its point */
   const float* w = C.w + 3 * ((size_t)py * sc.width + px);
   double zero[3] = {0, 0, 0};
   bool saved = C.track;
@@ -1238,6 +1486,19 @@ int or_closest_batch(const or_scene_t* sc, int n, const float* o, const float* d
 }
 
 void or_sincos_2pi(float r, float* c, float* s) { sincos_2pi32(r, c, s); }
+float or_atan2_pos(float y, float x) { return atan2_pos32(y, x); }
+
+/* Camera ray through a screen point, and the fisheye projection of a world
+ * point (test hooks; the projection returns 0 where no pixel sees the point). */
+void or_camera_ray(const or_scene_t* sc, float sx, float sy, float* o, float* d) {
+  R32 r = camera_ray32(*sc, sx, sy);
+  for (int i = 0; i < 3; ++i) { o[i] = r.o[i]; d[i] = r.d[i]; }
+}
+int or_fisheye_project(const or_scene_t* sc, const float* v, float* sx, float* sy) {
+  Prep P;
+  prepare(sc, P);
+  return fisheye_project32(P, v, sx, sy) ? 1 : 0;
+}
 void or_cosine_dir(const float* n, float r1, float r2, float* out) { cosine_dir32(n, r1, r2, out); }
 
 /* Unique edges [E,2]; returns E (writes at most cap). */
@@ -1378,16 +1639,23 @@ int or_render(const or_scene_t* sc, const or_opts_t* op, double* image) {
  * Dual) -- the scale of the rounding error an FP32 evaluation may make.
  * If contrib_abs is non-null it receives per entry sum_k |c_k| over the
  * samples' whole contributions c_k (the plain sum-of-magnitudes scale, which
- * the chain rule with absolute values bounds from above).  All outputs are
+ * the chain rule with absolute values bounds from above).  If jac is non-null
+ * it receives [n_jac, H, W]: for each listed parameter, the contributions of
+ * the samples of each pixel (interior and secondary samples by their camera
+ * path's pixel, primary edge samples by the pixel containing their point),
+ * which sum over the pixels to the gradient entry.  All outputs are
  * overwritten. */
-int or_backward3(const or_scene_t* sc, const or_opts_t* op, const float* d_image, double* grad, double* abs_grad,
-                 double* contrib_abs) {
+int or_backward4(const or_scene_t* sc, const or_opts_t* op, const float* d_image, double* grad, double* abs_grad,
+                 double* contrib_abs, double* jac) {
   Prep P;
   prepare(sc, P);
   int NP = P.P;
   int nt = std::max(1, op->n_threads);
   std::vector<std::vector<double>> g(nt, std::vector<double>(NP, 0.0)), ga(nt, std::vector<double>(NP, 0.0));
   std::vector<std::vector<double>> gc(contrib_abs ? nt : 0, std::vector<double>(NP, 0.0));
+  int64_t npix_all = (int64_t)sc->width * sc->height;
+  int n_jac = jac ? std::max(0, std::min(8, (int)op->n_jac)) : 0;
+  std::vector<std::vector<double>> gj(n_jac > 0 ? nt : 0, std::vector<double>((size_t)n_jac * npix_all, 0.0));
   g_dual_overflow = false;
   int npix = sc->width * sc->height;
   EdgeTree tree;
@@ -1395,8 +1663,10 @@ int or_backward3(const or_scene_t* sc, const or_opts_t* op, const float* d_image
   if (op->terms & 5) {
     int pb = op->pix_begin, pe = op->pix_end > 0 ? op->pix_end : npix;
     parallel_for(pb, pe, nt, [&](int tid, int64_t b, int64_t e) {
-      Ctx C{&P, op, true, d_image, g[tid].data(), ga[tid].data(), &tree, contrib_abs ? gc[tid].data() : nullptr};
+      Ctx C{&P, op, true, d_image, g[tid].data(), ga[tid].data(), &tree, contrib_abs ? gc[tid].data() : nullptr,
+            n_jac > 0 ? gj[tid].data() : nullptr};
       for (int64_t pix = b; pix < e; ++pix) {
+        C.pix = pix;
         const float* w = d_image + 3 * pix;
         double ws[3] = {w[0] / (double)op->spp, w[1] / (double)op->spp, w[2] / (double)op->spp};
         for (int s = 0; s < op->spp; ++s) {
@@ -1420,7 +1690,8 @@ int or_backward3(const or_scene_t* sc, const or_opts_t* op, const float* d_image
     int64_t N = (int64_t)op->edge_spp * npix;
     int64_t eb = op->edge_begin, ee = op->edge_end > 0 ? op->edge_end : N;
     parallel_for(eb, ee, nt, [&](int tid, int64_t b, int64_t e) {
-      Ctx C{&P, op, true, d_image, g[tid].data(), ga[tid].data(), nullptr, contrib_abs ? gc[tid].data() : nullptr};
+      Ctx C{&P, op, true, d_image, g[tid].data(), ga[tid].data(), nullptr, contrib_abs ? gc[tid].data() : nullptr,
+            n_jac > 0 ? gj[tid].data() : nullptr};
       for (int64_t j = b; j < e; ++j) primary_edge_sample(C, j);
     });
   }
@@ -1432,10 +1703,19 @@ int or_backward3(const or_scene_t* sc, const or_opts_t* op, const float* d_image
     grad[i] = s; abs_grad[i] = a;
     if (contrib_abs) contrib_abs[i] = c;
   }
+  for (int64_t q = 0; q < (int64_t)n_jac * npix_all; ++q) {
+    double v = 0.0;
+    for (int t = 0; t < nt; ++t) v += gj[t][q];
+    jac[q] = v;
+  }
   return g_dual_overflow ? 2 : 0;
 }
+int or_backward3(const or_scene_t* sc, const or_opts_t* op, const float* d_image, double* grad, double* abs_grad,
+                 double* contrib_abs) {
+  return or_backward4(sc, op, d_image, grad, abs_grad, contrib_abs, nullptr);
+}
 int or_backward(const or_scene_t* sc, const or_opts_t* op, const float* d_image, double* grad, double* abs_grad) {
-  return or_backward3(sc, op, d_image, grad, abs_grad, nullptr);
+  return or_backward4(sc, op, d_image, grad, abs_grad, nullptr, nullptr);
 }
 
 /* Self-check of the two secondary-edge measures at one edge point: for a

@@ -146,7 +146,9 @@ drt_status make_opts(const drt_render_opts* o, drt::Opts* op) {
   op->spp = o->spp;
   op->edge_spp = o->edge_spp;
   op->max_depth = o->max_depth;
-  op->primary_only = o->primary_only ? 1 : 0;
+  if (o->aov < 0 || o->aov > 4) return fail(DRT_ERR_INVALID_ARG, "aov must be in [0,4]");
+  op->aov = o->aov;
+  op->primary_only = (o->primary_only || o->aov > 0) ? 1 : 0;
   op->terms = o->terms == 0 ? 7 : o->terms;
   if (o->proposal < 0 || o->proposal > 2) return fail(DRT_ERR_INVALID_ARG, "proposal must be 0, 1 or 2");
   op->proposal = o->proposal;
@@ -169,6 +171,11 @@ drt_status make_opts(const drt_render_opts* o, drt::Opts* op) {
   op->pix_end = o->pix_end > 0 ? o->pix_end : INT32_MAX;
   op->edge_begin = o->edge_begin;
   op->edge_end = o->edge_end > 0 ? o->edge_end : INT64_MAX;
+  op->jac.out = nullptr;
+  op->jac.n = 0;
+  op->jac.npix = 0;
+  op->jac.v3 = op->jac.t3 = 0;
+  for (int k = 0; k < 8; ++k) op->jac.param[k] = -1;
   return DRT_OK;
 }
 
@@ -277,7 +284,10 @@ drt::SceneView drt_scene::view() const {
 
 extern "C" {
 
-const char* drt_last_error(void) { return g_err.c_str(); }
+const char* drt_last_error(drt_context* ctx) {
+  (void)ctx;
+  return g_err.c_str();
+}
 const char* drt_version(void) { return "drt 0.1 (sm_103a)"; }
 
 drt_status drt_create(int device, drt_context** out) {
@@ -548,7 +558,15 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
     if (!is_device_ptr(opts->seg_weights)) return fail(DRT_ERR_INVALID_ARG, "segment weights must be device memory");
     CUDA_TRY(drt::launch_proposal_cdf(s, opts->seg_weights, op.proposal, st));
   }
-  Staged sg[6];
+  // per-pixel gradient image of up to 8 listed parameters (optional)
+  int64_t n_params = 3 * (int64_t)s->V + 3 * (int64_t)s->T + 16;
+  if (grads->n_jac < 0 || grads->n_jac > 8 || (grads->n_jac > 0 && !grads->dimage_dparam))
+    return fail(DRT_ERR_INVALID_ARG, "n_jac must be in [0,8] and needs dimage_dparam");
+  for (int k = 0; k < grads->n_jac; ++k)
+    if (grads->jac_param[k] < 0 || grads->jac_param[k] >= n_params)
+      return fail(DRT_ERR_INVALID_ARG, "jac_param[%d] = %lld outside [0,%lld)", k, (long long)grads->jac_param[k],
+                  (long long)n_params);
+  Staged sg[7];
   size_t npix = (size_t)s->W * s->H;
   drt_status r = stage(sg[0], d_image, 12 * npix, true, false, st);
   if (r == DRT_OK) r = stage(sg[1], grads->d_verts, 12 * (size_t)s->V, true, true, st);
@@ -556,6 +574,16 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
   if (r == DRT_OK) r = stage(sg[3], grads->d_radiance, 12, true, true, st);
   if (r == DRT_OK) r = stage(sg[4], grads->d_cam_to_world, 48, true, true, st);
   if (r == DRT_OK) r = stage(sg[5], grads->d_cam_scale, 4, true, true, st);
+  if (r == DRT_OK && grads->n_jac > 0)
+    r = stage(sg[6], grads->dimage_dparam, 4 * npix * (size_t)grads->n_jac, true, true, st);
+  if (grads->n_jac > 0) {
+    op.jac.out = (float*)sg[6].dev;
+    op.jac.n = grads->n_jac;
+    op.jac.npix = (int)npix;
+    op.jac.v3 = 3 * (int64_t)s->V;
+    op.jac.t3 = 3 * (int64_t)s->T;
+    for (int k = 0; k < grads->n_jac; ++k) op.jac.param[k] = grads->jac_param[k];
+  }
   // per-block partial sums of the global parameters: scene-owned scratch,
   // grown on demand (the stream is drained before the old buffer is freed)
   int64_t rows = drt::backward_partial_rows(s, op);
@@ -569,7 +597,7 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
     if (r == DRT_OK) s->partials_cap = need;
   }
   if (r != DRT_OK) {
-    unstage(sg, 6, st);
+    unstage(sg, 7, st);
     return r;
   }
   // primary edge samples are evaluated in screen order: grow the sort scratch
@@ -590,7 +618,7 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
       if (a == DRT_OK) a = dalloc_n(&b.hist, drt::radix_hist_entries(n));
       if (a == DRT_OK) a = dalloc_n(&b.hist_tmp, drt::radix_hist_tmp_entries(n));
       if (a != DRT_OK) {
-        unstage(sg, 6, st);
+        unstage(sg, 7, st);
         return a;
       }
       b.cap = n_edge;
@@ -600,7 +628,7 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
   if (op.sec_sampler == 1 && !op.primary_only && (op.terms & 4) && s->E > 0 && s->L > 0) {
     drt_status a = ensure_edge_tree(s, true, st);
     if (a != DRT_OK) {
-      unstage(sg, 6, st);
+      unstage(sg, 7, st);
       return a;
     }
   }
@@ -625,7 +653,7 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
       if (a == DRT_OK) a = dalloc_n(&b.queue, (size_t)cap);
       if (a == DRT_OK) a = dalloc_n(&b.count, drt::kSecCounters);
       if (a != DRT_OK) {
-        unstage(sg, 6, st);
+        unstage(sg, 7, st);
         return a;
       }
       b.cap = cap;
@@ -653,7 +681,7 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
       if (a == DRT_OK) a = dalloc_n(&b.path[1], 5 * (size_t)pcap);
       if (a == DRT_OK) a = dalloc_n(&b.path_count, 2);
       if (a != DRT_OK) {
-        unstage(sg, 6, st);
+        unstage(sg, 7, st);
         return a;
       }
       b.wave_cap = cap;
@@ -666,7 +694,7 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
       s->sec.pick_cap = 0;
       drt_status a = dalloc_n(&s->sec.pick, (size_t)cap);
       if (a != DRT_OK) {
-        unstage(sg, 6, st);
+        unstage(sg, 7, st);
         return a;
       }
       s->sec.pick_cap = cap;
@@ -691,7 +719,7 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
       if (a == DRT_OK) a = dalloc_n(&b.path[1], 5 * (size_t)n_edge);
       if (a == DRT_OK) a = dalloc_n(&b.count, 2);
       if (a != DRT_OK) {
-        unstage(sg, 6, st);
+        unstage(sg, 7, st);
         return a;
       }
       b.cap = n_edge;
@@ -701,7 +729,7 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
   cudaError_t e = drt::launch_backward(s, op, tape, (const float*)sg[0].dev, (float*)sg[1].dev, (float*)sg[2].dev,
                                        (float*)sg[3].dev, (float*)sg[4].dev, (float*)sg[5].dev, s->partials, sort,
                                        secs, prims, st);
-  r = unstage(sg, 6, st);
+  r = unstage(sg, 7, st);
   if (e != cudaSuccess) return fail(DRT_ERR_CUDA, "backward launch: %s", cudaGetErrorString(e));
   return r;
 }

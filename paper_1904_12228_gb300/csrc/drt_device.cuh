@@ -152,6 +152,14 @@ struct Opts {
   // debug restriction of the backward pass to sample ranges (full range by default)
   int pix_begin, pix_end;
   int64_t edge_begin, edge_end;
+  int aov;  // with primary_only: 0, 1 albedo; 2 world position; 3 unit shading normal; 4 distance from the ray origin
+  // per-pixel gradient image of up to 8 parameters (n = 0: none)
+  struct {
+    float* out;         // [n, H, W]
+    int n, npix;
+    int64_t v3, t3;     // 3V, 3T: the albedo and global parameters start at v3 and v3 + t3
+    int64_t param[8];   // flat parameter indices
+  } jac;
 };
 
 // Passes of a batch, in launch order (a batch queues its secondary edge

@@ -15,7 +15,9 @@
 // mbarrier; all threads wait (bounded), then each warp reads its 32 TMEM
 // lanes with tcgen05.ld.  Every wait has an iteration limit: on timeout the
 // kernel raises the device error flag, frees its TMEM and returns.
+#include <cmath>
 #include <cstdint>
+#include <vector>
 #include <cuda_bf16.h>
 
 #include "drt_internal.h"
@@ -428,6 +430,127 @@ __global__ void k_adam(float* p, const float* g, float* m, float* v, __nv_bfloat
 
 constexpr size_t kBackwardSmem = 8192 * 2 + 4096 + 8192 * 2 + 16384 * 3 + 32768 * 2 + kRows * kHid * 4;
 
+// ---- training from logged edge contributions (drt_mlp_train) --------------
+// Network parameters in the order w1, b1, w2, b2, w3, b3.
+constexpr int kNumParamArrays = 6;
+constexpr int kParamTotal = kHid * kIn + kHid + kHid * kHid + kHid + kHid + 1;
+
+struct ParamArrays {
+  float* p[kNumParamArrays];
+  float* m1[kNumParamArrays];
+  float* m2[kNumParamArrays];
+  float* g[kNumParamArrays];
+  __nv_bfloat16* w1b;
+  __nv_bfloat16* w2b;
+};
+
+__device__ __forceinline__ int param_slot(int i, int* off) {
+  const int sizes[kNumParamArrays] = {kHid * kIn, kHid, kHid * kHid, kHid, kHid, 1};
+  int a = 0;
+#pragma unroll
+  for (int k = 0; k < kNumParamArrays; ++k) {
+    if (i < sizes[k]) {
+      a = k;
+      break;
+    }
+    i -= sizes[k];
+  }
+  *off = i;
+  return a;
+}
+
+__global__ void k_zero_grads(ParamArrays pa) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kParamTotal) return;
+  int off;
+  int a = param_slot(i, &off);
+  pa.g[a][off] = 0.f;
+}
+
+// Adam on all six arrays at once (same update as k_adam).
+__global__ void k_adam_all(ParamArrays pa, float lr, float b1, float b2, float eps, float c1, float c2) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kParamTotal) return;
+  int off;
+  int a = param_slot(i, &off);
+  float gi = pa.g[a][off];
+  float mi = b1 * pa.m1[a][off] + (1.f - b1) * gi;
+  float vi = b2 * pa.m2[a][off] + (1.f - b2) * gi * gi;
+  pa.m1[a][off] = mi;
+  pa.m2[a][off] = vi;
+  float pi = pa.p[a][off] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  pa.p[a][off] = pi;
+  if (a == 0) pa.w1b[off] = __float2bfloat16_rn(pi);
+  if (a == 2) pa.w2b[off] = __float2bfloat16_rn(pi);
+}
+
+// Per logged scene: sum of the logged magnitudes and of the segment lengths,
+// in FP64, in a fixed order (one block per scene).
+__global__ void k_log_sums(const drt_mlp_log* logs, double* sums) {
+  __shared__ double sa[256], sb[256];
+  const drt_mlp_log& lg = logs[blockIdx.x];
+  double a = 0.0, b = 0.0;
+  for (int64_t r = threadIdx.x; r < lg.n; r += blockDim.x) {
+    a += (double)lg.seg_log[r];
+    b += lg.seg_len[r];
+  }
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      sa[threadIdx.x] += sa[threadIdx.x + h];
+      sb[threadIdx.x] += sb[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sums[2 * blockIdx.x] = sa[0];
+    sums[2 * blockIdx.x + 1] = sb[0];
+  }
+}
+
+// Shuffle keys: a Philox draw per row (counter (row, 0, 0x4D4C5054, 0), key =
+// seed), sorted with the row index as value.
+__global__ void k_shuffle_keys(int64_t rows, uint2 key, uint32_t* keys, int32_t* vals) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  keys[r] = philox(make_uint4((uint32_t)r, 0u, 0x4D4C5054u, 0u), key).x;
+  vals[r] = (int32_t)r;
+}
+
+// Training row p = concatenated row perm[p]: its features, and the target
+// and weight of the regression.  For a segment of length len with logged
+// magnitude S out of N logging samples over screen length L, S L / N
+// estimates the segment's integral of |w . (f_u - f_l)|; the target is the
+// log of that integral per unit length relative to the scene's mean density
+// (sum S / N over all segments per unit length), offset by delta; the
+// weight is the segment's length over the scene's mean segment length.
+__global__ void k_training_rows(const drt_mlp_log* logs, const int64_t* offs, int n_logs, const double* sums,
+                                const int32_t* perm, int64_t rows, float delta, __nv_bfloat16* x, float* target,
+                                float* mask, int64_t* index_out) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= rows) return;
+  int64_t r = perm[p];
+  int k = 0;
+  while (k + 1 < n_logs && r >= offs[k + 1]) ++k;
+  const drt_mlp_log& lg = logs[k];
+  int64_t j = r - offs[k];
+  double S = sums[2 * k], L = sums[2 * k + 1];
+  double N = lg.n_samples;
+  double len = lg.seg_len[j];
+  double dens = (double)lg.seg_log[j] * (L / N) / fmax(len, 1e-12);
+  double mean = S / N;
+  double rel = dens / fmax(mean, 1e-30);
+  target[p] = (float)log(rel + (double)delta);
+  mask[p] = (float)(len / (L / (double)lg.n));
+  const uint4* src = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(lg.x) + j * kIn);
+  uint4* dst = reinterpret_cast<uint4*>(x + p * kIn);
+#pragma unroll
+  for (int q = 0; q < kIn * 2 / 16; ++q) dst[q] = src[q];
+  if (index_out) index_out[p] = r;
+}
+
 }  // namespace
 }  // namespace drt
 
@@ -473,6 +596,121 @@ drt_status drt_mlp_backward(drt_context* ctx, const void* x, const float* target
   DRT_PROF_LAUNCH("mlp_backward", st, drt::k_mlp_backward<<<gr, 128, drt::kBackwardSmem, st>>>(
                                           a, target, mask, inv_n, g->w1, g->b1, g->w2, g->b2, g->w3, g->b3, loss));
   return cudaGetLastError() == cudaSuccess ? DRT_OK : DRT_ERR_CUDA;
+}
+
+drt_status drt_mlp_train(drt_context* ctx, const drt_mlp_log* logs, int32_t n_logs, const drt_mlp_train_opts* o,
+                         drt_mlp_state* state, void* stream) {
+  NvtxRange nvtx_range("drt_mlp_train");
+  if (!ctx || !logs || n_logs < 1 || !o || !state || o->steps < 0 || o->batch < 0)
+    return DRT_ERR_INVALID_ARG;
+  for (int k = 0; k < drt::kNumParamArrays; ++k)
+    if (!state->p[k] || !state->m1[k] || !state->m2[k] || !state->g[k]) return DRT_ERR_INVALID_ARG;
+  if (!state->w1_bf16 || !state->w2_bf16 || state->step < 0) return DRT_ERR_INVALID_ARG;
+  std::vector<int64_t> offs(n_logs + 1, 0);
+  for (int k = 0; k < n_logs; ++k) {
+    const drt_mlp_log& lg = logs[k];
+    if (lg.n < 1 || !lg.x || !lg.seg_log || !lg.seg_len || !(lg.n_samples > 0.0)) {
+      drt::set_last_error("drt_mlp_train: every log needs n >= 1 rows, its arrays and n_samples > 0");
+      return DRT_ERR_INVALID_ARG;
+    }
+    if (!drt::is_device_array(lg.x) || !drt::is_device_array(lg.seg_log) || !drt::is_device_array(lg.seg_len)) {
+      drt::set_last_error("drt_mlp_train: the logs' arrays must be device memory");
+      return DRT_ERR_INVALID_ARG;
+    }
+    offs[k + 1] = offs[k] + lg.n;
+  }
+  int64_t rows = offs[n_logs];
+  if (rows > INT32_MAX) {
+    drt::set_last_error("drt_mlp_train: more than 2^31 - 1 rows");
+    return DRT_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int batch = o->batch > 0 ? o->batch : 16384;
+  if (batch > rows) batch = (int)rows;
+  float lr = o->lr > 0.f ? o->lr : 3e-3f;
+  float delta = o->delta > 0.f ? o->delta : 1e-3f;
+  // scratch of this call (training is not a hot path): the logs' table, the
+  // per-log sums, the shuffle and the training rows
+  void *d_logs = nullptr, *d_offs = nullptr, *d_sums = nullptr, *keys = nullptr, *keys2 = nullptr, *vals = nullptr,
+       *vals2 = nullptr, *hist = nullptr, *hist_tmp = nullptr, *x = nullptr, *target = nullptr, *mask = nullptr,
+       *loss_tmp = nullptr;
+  auto release = [&]() {
+    void* all[] = {d_logs, d_offs, d_sums, keys, keys2, vals, vals2, hist, hist_tmp, x, target, mask, loss_tmp};
+    for (void* q : all) drt::device_free(q);
+  };
+  drt_status a = drt::device_alloc(&d_logs, sizeof(drt_mlp_log) * n_logs);
+  if (a == DRT_OK) a = drt::device_alloc(&d_offs, sizeof(int64_t) * (n_logs + 1));
+  if (a == DRT_OK) a = drt::device_alloc(&d_sums, sizeof(double) * 2 * n_logs);
+  if (a == DRT_OK) a = drt::device_alloc(&keys, sizeof(uint32_t) * rows);
+  if (a == DRT_OK) a = drt::device_alloc(&keys2, sizeof(uint32_t) * rows);
+  if (a == DRT_OK) a = drt::device_alloc(&vals, sizeof(int32_t) * rows);
+  if (a == DRT_OK) a = drt::device_alloc(&vals2, sizeof(int32_t) * rows);
+  if (a == DRT_OK) a = drt::device_alloc(&hist, sizeof(uint32_t) * drt::radix_hist_entries((int)rows));
+  if (a == DRT_OK) a = drt::device_alloc(&hist_tmp, sizeof(uint32_t) * drt::radix_hist_tmp_entries((int)rows));
+  if (a == DRT_OK) a = drt::device_alloc(&x, sizeof(__nv_bfloat16) * drt::kIn * rows);
+  if (a == DRT_OK) a = drt::device_alloc(&target, sizeof(float) * rows);
+  if (a == DRT_OK) a = drt::device_alloc(&mask, sizeof(float) * rows);
+  if (a == DRT_OK && !o->loss) a = drt::device_alloc(&loss_tmp, sizeof(float));
+  if (a != DRT_OK) {
+    release();
+    return a;
+  }
+  cudaError_t e = cudaMemcpyAsync(d_logs, logs, sizeof(drt_mlp_log) * n_logs, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_offs, offs.data(), sizeof(int64_t) * (n_logs + 1), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && loss_tmp) e = cudaMemsetAsync(loss_tmp, 0, sizeof(float), st);
+  if (e == cudaSuccess) {
+    drt::k_log_sums<<<n_logs, 256, 0, st>>>((const drt_mlp_log*)d_logs, (double*)d_sums);
+    uint2 key = make_uint2((uint32_t)o->seed, (uint32_t)(o->seed >> 32));
+    unsigned gr = (unsigned)((rows + 255) / 256);
+    drt::k_shuffle_keys<<<gr, 256, 0, st>>>(rows, key, (uint32_t*)keys, (int32_t*)vals);
+    bool alt = drt::radix_sort_pairs((uint32_t*)keys, (int32_t*)vals, (uint32_t*)keys2, (int32_t*)vals2,
+                                     (uint32_t*)hist, (uint32_t*)hist_tmp, (int)rows, 32, st);
+    const int32_t* perm = alt ? (const int32_t*)vals2 : (const int32_t*)vals;
+    drt::k_training_rows<<<gr, 256, 0, st>>>((const drt_mlp_log*)d_logs, (const int64_t*)d_offs, n_logs,
+                                             (const double*)d_sums, perm, rows, delta, (__nv_bfloat16*)x,
+                                             (float*)target, (float*)mask, o->rows_index);
+    if (o->rows_target) e = cudaMemcpyAsync(o->rows_target, target, sizeof(float) * rows, cudaMemcpyDefault, st);
+    if (e == cudaSuccess && o->rows_mask)
+      e = cudaMemcpyAsync(o->rows_mask, mask, sizeof(float) * rows, cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+  }
+  // mini-batch Adam over the shuffled rows, cosine decay to lr/10
+  drt::ParamArrays pa;
+  for (int k = 0; k < drt::kNumParamArrays; ++k) {
+    pa.p[k] = state->p[k];
+    pa.m1[k] = state->m1[k];
+    pa.m2[k] = state->m2[k];
+    pa.g[k] = state->g[k];
+  }
+  pa.w1b = (__nv_bfloat16*)state->w1_bf16;
+  pa.w2b = (__nv_bfloat16*)state->w2_bf16;
+  drt_mlp_weights w{state->w1_bf16, state->p[1], state->w2_bf16, state->p[3], state->p[4], state->p[5]};
+  drt_mlp_grads g{state->g[0], state->g[1], state->g[2], state->g[3], state->g[4], state->g[5]};
+  float* loss = o->loss ? o->loss : (float*)loss_tmp;
+  int64_t nb = rows / batch > 0 ? rows / batch : 1;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  unsigned gp = (unsigned)((drt::kParamTotal + 255) / 256);
+  drt_status r = DRT_OK;
+  for (int i = 0; i < o->steps && e == cudaSuccess && r == DRT_OK; ++i) {
+    int64_t b = i % nb;
+    float lr_i = lr * (0.55f + 0.45f * cosf(3.14159265358979f * (float)i / (float)o->steps));
+    drt::k_zero_grads<<<gp, 256, 0, st>>>(pa);
+    r = drt_mlp_backward(ctx, (const __nv_bfloat16*)x + b * batch * drt::kIn, (const float*)target + b * batch,
+                         (const float*)mask + b * batch, batch, 1.0f / (float)batch, &w, &g, loss, stream);
+    int64_t step = state->step + 1;
+    float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    DRT_PROF_LAUNCH("adam", st, drt::k_adam_all<<<gp, 256, 0, st>>>(pa, lr_i, b1, b2, eps, c1, c2));
+    state->step = step;
+    e = cudaGetLastError();
+  }
+  cudaError_t es = cudaStreamSynchronize(st);
+  release();
+  if (r != DRT_OK) return r;
+  if (e != cudaSuccess || es != cudaSuccess) {
+    drt::set_last_error(cudaGetErrorString(e != cudaSuccess ? e : es));
+    return DRT_ERR_CUDA;
+  }
+  return DRT_OK;
 }
 
 drt_status drt_adam_step(drt_context* ctx, float* params, const float* grads, float* m1, float* m2, void* params_bf16,

@@ -83,6 +83,9 @@ drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* s, const drt
       return fail_noalloc(DRT_ERR_STATE, "tape does not match this scene and these options");
     }
   }
+  if (grads->dimage_dparam || grads->n_jac != 0) {
+    return fail_noalloc(DRT_ERR_INVALID_ARG, "drt_render_backward_noalloc writes no per-pixel gradient image");
+  }
   const void* arrays[] = {d_image, grads->d_verts, grads->d_albedo, grads->d_radiance, grads->d_cam_to_world,
                           grads->d_cam_scale};
   for (const void* a : arrays)

@@ -59,7 +59,7 @@ constexpr int kKeySub = DRT_KEY_SUB;
 // stage of the secondary samples, the continuation stage (one launch per
 // vertex) and the secondary contributions.
 #ifndef DRT_SIDES_MIN_BLOCKS
-#define DRT_SIDES_MIN_BLOCKS 2
+#define DRT_SIDES_MIN_BLOCKS 4
 #endif
 #ifndef DRT_BOUNCE_MIN_BLOCKS
 #define DRT_BOUNCE_MIN_BLOCKS 2
@@ -169,6 +169,31 @@ __device__ __forceinline__ void scatter3(float* arr, int id, float3 v, bool acti
       }
     }
     pending &= ~peers;
+  }
+}
+
+// Per-pixel gradient image (drt_grads.dimage_dparam): a sample's
+// contribution to a listed parameter is also added to the image of that
+// parameter at the sample's pixel.  op.jac.n is uniform, so the hooks cost a
+// branch when no image is asked for.
+__device__ __forceinline__ void jac_add3(const Opts& op, int64_t base, int id, float3 v, int64_t pix, bool active) {
+  if (op.jac.n == 0 || !active) return;
+  for (int k = 0; k < op.jac.n; ++k) {
+    int64_t q = op.jac.param[k] - base - 3 * (int64_t)id;
+    if (q >= 0 && q < 3) atomicAdd(op.jac.out + (int64_t)k * op.jac.npix + pix, q == 0 ? v.x : (q == 1 ? v.y : v.z));
+  }
+}
+__device__ __forceinline__ void jac_globals(const Opts& op, const float g[kGlobals], int64_t pix, bool active) {
+  if (op.jac.n == 0 || !active) return;
+  for (int k = 0; k < op.jac.n; ++k) {
+    int64_t q = op.jac.param[k] - op.jac.v3 - op.jac.t3;
+    if (q >= 0 && q < kGlobals) {
+      float v = 0.f;
+#pragma unroll
+      for (int i = 0; i < kGlobals; ++i)
+        if (i == q) v = g[i];
+      if (v != 0.f) atomicAdd(op.jac.out + (int64_t)k * op.jac.npix + pix, v);
+    }
   }
 }
 
@@ -293,6 +318,23 @@ __device__ __forceinline__ float nee_geometry(const SceneView& s, float3 p, floa
 }
 
 
+// Geometry buffers of the first hit (Sec. 5.4): with primary_only the path's
+// value is the hit's albedo, or (op.aov) its world position, its unit shading
+// normal (facing the ray) or its distance from the ray origin o.
+__device__ __forceinline__ float3 aov_value(const Opts& op, const Vertex& x, float3 alb, const float o[3]) {
+  if (op.aov == 2) return f3(x.p);
+  if (op.aov == 3) {
+    float3 Nk = cross(x.v1 - x.v0, x.v2 - x.v0);
+    float fl = x.side > 0.0f ? -1.f : 1.f;
+    return (fl / len(Nk)) * Nk;
+  }
+  if (op.aov == 4) {
+    float dd = len(f3(x.p) - f3(o));
+    return make_float3(dd, dd, dd);
+  }
+  return alb;
+}
+
 // path_value of a camera path (from depth 0, first emission counted) for the
 // 32 lanes of a warp together, traced by the warp-cooperative traversals.
 // All lanes call; a lane with act = false traces nothing, writes no tape and
@@ -332,7 +374,7 @@ __device__ float3 path_value_warp(const SceneView& s, const Opts& op, const floa
       load_vertex(s, h.tri, h.b1, h.b2, d, x);
       alb = ld3(s.albedo + 3 * x.k);
       if (op.primary_only) {
-        L += beta * alb;
+        L += beta * aov_value(op, x, alb, o);
         if (tape_tri) {
           tape_tri[b * n_stride + n_idx] = x.k;
           tape_bary[b * n_stride + n_idx] = make_float2(h.b1, h.b2);
@@ -717,7 +759,7 @@ __device__ __forceinline__ void plane_hit_adjoint(const float o[3], const float 
 
 __device__ __forceinline__ void hit_point_adjoint(const SceneView& s, const CamHit& c, const Vertex& x, float3 dp,
                                                   float3 dn, float3& dv0, float3& dv1, float3& dv2,
-                                                  float g[kGlobals]) {
+                                                  float g[kGlobals], float3 do_extra = float3{0.f, 0.f, 0.f}) {
   float3 ov = f3(c.o), dvv = f3(c.d);
   float3 e1 = x.v1 - x.v0, e2 = x.v2 - x.v0;
   float3 Nk = cross(e1, e2);
@@ -730,7 +772,7 @@ __device__ __forceinline__ void hit_point_adjoint(const SceneView& s, const CamH
   float3 dnh = flip * dn;
   dNk += (1.f / nkl) * (dnh - dot(dnh, nhat) * nhat);
   float dtau = dot(dp, dvv);
-  float3 do_ = dp, dd_ = tau * dp;
+  float3 do_ = dp + do_extra, dd_ = tau * dp;
   float dnum = dtau / den, dden = -dtau * tau / den;
   dv0 += dnum * Nk;
   do_ -= dnum * Nk;
@@ -790,7 +832,25 @@ __device__ __forceinline__ void interior_block(const SceneView& s, const Opts& o
       vid0 = vid[0]; vid1 = vid[1]; vid2 = vid[2];
       float3 alb = ld3(s.albedo + 3 * c.k);
       if (op.primary_only) {
-        if (do_int) dalb = a;
+        if (do_int && op.aov <= 1) {
+          dalb = a;
+        } else if (do_int) {
+          // geometry buffers: the value moves with the hit point, the face
+          // normal or the ray origin (the albedo does not enter)
+          float3 dp = zero3(), dn = zero3(), dox = zero3();
+          if (op.aov == 2) {
+            dp = a;
+          } else if (op.aov == 3) {
+            dn = a;
+          } else {
+            float3 u = f3(x.p) - f3(c.o);
+            u = (1.f / len(u)) * u;
+            float as = a.x + a.y + a.z;
+            dp = as * u;
+            dox = -as * u;
+          }
+          hit_point_adjoint(s, c, x, dp, dn, dv0, dv1, dv2, g, dox);
+        }
       } else {
         if (do_int && s.light_of_tri[c.k] >= 0 && x.side < 0.0f) {
           g[0] += a.x; g[1] += a.y; g[2] += a.z;
@@ -860,10 +920,20 @@ __device__ __forceinline__ void interior_block(const SceneView& s, const Opts& o
     scatter3(gr.verts, lid0, dl0, have_light, &cv);
     scatter3(gr.verts, lid1, dl1, have_light, &cv);
     scatter3(gr.verts, lid2, dl2, have_light, &cv);
+    if (op.jac.n) {
+      jac_add3(op, 0, vid0, dv0, pix, hit);
+      jac_add3(op, 0, vid1, dv1, pix, hit);
+      jac_add3(op, 0, vid2, dv2, pix, hit);
+      jac_add3(op, op.jac.v3, c.k, dalb, pix, hit && do_int);
+      jac_add3(op, 0, lid0, dl0, pix, have_light);
+      jac_add3(op, 0, lid1, dl1, pix, have_light);
+      jac_add3(op, 0, lid2, dl2, pix, have_light);
+    }
   }
   __syncthreads();
   cache_flush(cv, gr.verts);
   cache_flush(ca, gr.albedo);
+  jac_globals(op, g, pix, pix_ok);
   block_globals(g, gr.partials + blk * kGlobals, false);
 }
 __global__ void __launch_bounds__(kBlock, DRT_PIXEL_MIN_BLOCKS)
@@ -1344,7 +1414,17 @@ __device__ __forceinline__ void secondary_block(const SceneView& s, const Opts& 
     scatter3(gr.verts, vid2, dv2, have_edge);
     for (int sd = 0; sd < 2; ++sd)
       for (int q = 0; q < 3; ++q) scatter3(gr.verts, mids[sd][q], dmv[sd][q], have_m[sd]);
+    if (op.jac.n) {
+      jac_add3(op, 0, eid0, de0, pix, have_edge);
+      jac_add3(op, 0, eid1, de1, pix, have_edge);
+      jac_add3(op, 0, vid0, dv0, pix, have_edge);
+      jac_add3(op, 0, vid1, dv1, pix, have_edge);
+      jac_add3(op, 0, vid2, dv2, pix, have_edge);
+      for (int sd = 0; sd < 2; ++sd)
+        for (int q = 0; q < 3; ++q) jac_add3(op, 0, mids[sd][q], dmv[sd][q], pix, have_m[sd]);
+    }
   }
+  jac_globals(op, g, pix, pix_ok);
   block_globals(g, gr.partials + blk * kGlobals, rows_written != 0);
 }
 template <int kSel>
@@ -1489,11 +1569,23 @@ __device__ __forceinline__ void path_block(const SceneView& s, const Opts& op, c
       scatter3(gr.verts, so.eid1, so.de1, so.have_edge, &cv);
       for (int q = 0; q < 2; ++q)
         for (int i = 0; i < 3; ++i) scatter3(gr.verts, so.mid[q][i], so.dm[q][i], so.have_m[q], &cv);
+      if (op.jac.n) {
+        jac_add3(op, 0, vid[0], dv0, pix, av);
+        jac_add3(op, 0, vid[1], dv1, pix, av);
+        jac_add3(op, 0, vid[2], dv2, pix, av);
+        jac_add3(op, op.jac.v3, av ? kk[b] : 0, dalb, pix, av && do_int);
+        for (int i = 0; i < 3; ++i) jac_add3(op, 0, lid[i], dl[i], pix, have_light);
+        jac_add3(op, 0, so.eid0, so.de0, pix, so.have_edge);
+        jac_add3(op, 0, so.eid1, so.de1, pix, so.have_edge);
+        for (int q = 0; q < 2; ++q)
+          for (int i = 0; i < 3; ++i) jac_add3(op, 0, so.mid[q][i], so.dm[q][i], pix, so.have_m[q]);
+      }
     }
   }
   __syncthreads();
   cache_flush(cv, gr.verts);
   cache_flush(ca, gr.albedo);
+  jac_globals(op, g, pix, pix_ok);
   block_globals(g, gr.partials + blk * kGlobals, false);
 }
 template <int kSel>
@@ -1660,6 +1752,7 @@ __global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_trace(BatchS
     cache_init(cv);
     __syncthreads();
     unsigned long long qq = base + threadIdx.x, q = qq;
+    int64_t jpix = 0;  // pixel of the queued sample (per-pixel gradient image)
     // queue slot of the qq-th queued sample: region b, offset within it
     for (int b = 0; b < md; ++b) {
       if (qq < cnt[b]) {
@@ -1680,6 +1773,7 @@ __global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_trace(BatchS
       int64_t i = (int64_t)(item >> 3);
       int b = (int)(item & 7u);
       int64_t pix = i / op.spp;
+      jpix = pix;
       int sidx = (int)(i % op.spp);
       Vertex x;
       float3 beta;
@@ -1698,6 +1792,12 @@ __global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_trace(BatchS
     scatter3(bs.d_verts, so.eid1, so.de1, so.have_edge, &cv);
     for (int h = 0; h < 2; ++h)
       for (int j = 0; j < 3; ++j) scatter3(bs.d_verts, so.mid[h][j], so.dm[h][j], so.have_m[h], &cv);
+    if (op.jac.n) {
+      jac_add3(op, 0, so.eid0, so.de0, jpix, so.have_edge);
+      jac_add3(op, 0, so.eid1, so.de1, jpix, so.have_edge);
+      for (int h = 0; h < 2; ++h)
+        for (int j = 0; j < 3; ++j) jac_add3(op, 0, so.mid[h][j], so.dm[h][j], jpix, so.have_m[h]);
+    }
     __syncthreads();
     cache_flush(cv, bs.d_verts);
     __syncthreads();
@@ -1979,6 +2079,7 @@ __global__ void __launch_bounds__(kBlock, DRT_FINISH_MIN_BLOCKS) k_sec_finish(Ba
     so.de0 = so.de1 = zero3();
     for (int h = 0; h < 2; ++h)
       for (int j = 0; j < 3; ++j) { so.dm[h][j] = zero3(); so.mid[h][j] = 0; }
+    int64_t jpix = 0;  // pixel of the queued sample (per-pixel gradient image)
     if (base + threadIdx.x < count) {
       unsigned long long q = sec_slot(cnt, md, n_region, base + threadIdx.x);
       int4 h0 = bs.sec_hits[2 * q], h1 = bs.sec_hits[2 * q + 1];
@@ -1987,6 +2088,7 @@ __global__ void __launch_bounds__(kBlock, DRT_FINISH_MIN_BLOCKS) k_sec_finish(Ba
       int64_t i = (int64_t)(item >> 3);
       int b = (int)(item & 7u);
       int64_t pix = i / op.spp;
+      jpix = pix;
       int sidx = (int)(i % op.spp);
       Vertex x;
       float3 beta;
@@ -2020,6 +2122,12 @@ __global__ void __launch_bounds__(kBlock, DRT_FINISH_MIN_BLOCKS) k_sec_finish(Ba
     scatter3(bs.d_verts, so.eid1, so.de1, so.have_edge, &cv);
     for (int h = 0; h < 2; ++h)
       for (int j = 0; j < 3; ++j) scatter3(bs.d_verts, so.mid[h][j], so.dm[h][j], so.have_m[h], &cv);
+    if (op.jac.n) {
+      jac_add3(op, 0, so.eid0, so.de0, jpix, so.have_edge);
+      jac_add3(op, 0, so.eid1, so.de1, jpix, so.have_edge);
+      for (int h = 0; h < 2; ++h)
+        for (int j = 0; j < 3; ++j) jac_add3(op, 0, so.mid[h][j], so.dm[h][j], jpix, so.have_m[h]);
+    }
     __syncthreads();
     cache_flush(cv, bs.d_verts);
     __syncthreads();
@@ -2130,6 +2238,9 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
     bool active = j < n_edge && ptotal > 0.0 && j >= op.edge_begin && j < op.edge_end;
     float3 da3 = zero3(), db3 = zero3();
     int ia = 0, ib = 0;
+    int64_t jpix = 0;  // pixel containing the sample's point (per-pixel gradient image)
+    float gs[kGlobals];  // this sample's share of the global parameters
+    for (int q = 0; q < kGlobals; ++q) gs[q] = 0.f;
     EdgeSample es = {};
     if (active && side == 0) {
       es = primary_sample(s, op, j, ptotal);
@@ -2147,7 +2258,8 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
       float xs = side == 0 ? fa(x, fm(eps, nx)) : fs(x, fm(eps, nx));
       float ys = side == 0 ? fa(y, fm(eps, ny)) : fs(y, fm(eps, ny));
       int px = min(max((int)floorf(x), 0), s.W - 1), py = min(max((int)floorf(y), 0), s.H - 1);
-      w = ld3(d_image + 3 * ((int64_t)py * s.W + px));
+      jpix = (int64_t)py * s.W + px;
+      w = ld3(d_image + 3 * jpix);
       if (kStage != kPrimFinish) camera_ray(s, xs, ys, o, d);
     }
     float3 Lme, Lot;
@@ -2209,14 +2321,20 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
         float dax = c * (by - y), day = c * (x - bx), dbx = c * (y - ay), dby = c * (ax - x);
         int2 ev = s.edges[e];
         ia = ev.x; ib = ev.y;
-        da3 = project_adjoint(s, ld3(s.verts + 3 * ia), dax, day, g);
-        db3 = project_adjoint(s, ld3(s.verts + 3 * ib), dbx, dby, g);
+        da3 = project_adjoint(s, ld3(s.verts + 3 * ia), dax, day, gs);
+        db3 = project_adjoint(s, ld3(s.verts + 3 * ib), dbx, dby, gs);
+        for (int q = 0; q < kGlobals; ++q) g[q] += gs[q];
       } else {
         active = false;
       }
     }
     scatter3(gr.verts, ia, da3, active);
     scatter3(gr.verts, ib, db3, active);
+    if (op.jac.n) {
+      jac_add3(op, 0, ia, da3, jpix, active);
+      jac_add3(op, 0, ib, db3, jpix, active);
+      jac_globals(op, gs, jpix, active);
+    }
   }
   if (kStage != kPrimFirst) block_globals(g, gr.partials + blk * kGlobals, false);
 }

@@ -20,6 +20,7 @@ from . import build as _build
 DRT_OK = 0
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "DEVICE_FLAG", 6: "STATE"}
 TERM_INTERIOR, TERM_PRIMARY, TERM_SECONDARY = 1, 2, 4
+AOV_ALBEDO, AOV_POSITION, AOV_NORMAL, AOV_DEPTH = 1, 2, 3, 4
 
 EXPORTED = ("drt_create", "drt_destroy", "drt_scene_upload", "drt_scene_update_vertices", "drt_scene_update_params",
             "drt_scene_free", "drt_render", "drt_render_backward", "drt_tape_free", "drt_check_device",
@@ -27,7 +28,7 @@ EXPORTED = ("drt_create", "drt_destroy", "drt_scene_upload", "drt_scene_update_v
             "drt_counters_enable", "drt_counters_read", "drt_render_backward_noalloc", "drt_scene_segments",
             "drt_mlp_forward", "drt_mlp_backward", "drt_adam_step", "drt_segment_features", "drt_batch_create",
             "drt_batch_run", "drt_batch_get_info", "drt_batch_free", "drt_render_batch", "drt_probe_fma",
-            "drt_probe_l2")
+            "drt_probe_l2", "drt_mlp_train")
 BATCH_PASSES = ("render", "interior", "secondary", "path", "primary")
 
 
@@ -52,7 +53,7 @@ class RenderOpts(ctypes.Structure):
                 ("n_seg_weights", ctypes.c_int64), ("seg_log", ctypes.c_void_p), ("scene_id", ctypes.c_int32),
                 ("sec_sampler", ctypes.c_int32), ("sec_tree_samples", ctypes.c_int32), ("sec_point", ctypes.c_int32),
                 ("pix_begin", ctypes.c_int32), ("pix_end", ctypes.c_int32), ("edge_begin", ctypes.c_int64),
-                ("edge_end", ctypes.c_int64)]
+                ("edge_end", ctypes.c_int64), ("aov", ctypes.c_int32)]
 
 
 class MlpWeights(ctypes.Structure):
@@ -65,9 +66,28 @@ class MlpGrads(ctypes.Structure):
                 ("w3", ctypes.c_void_p), ("b3", ctypes.c_void_p)]
 
 
+class MlpLog(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("seg_log", ctypes.c_void_p), ("seg_len", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("n_samples", ctypes.c_double)]
+
+
+class MlpState(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_void_p * 6), ("m1", ctypes.c_void_p * 6), ("m2", ctypes.c_void_p * 6),
+                ("g", ctypes.c_void_p * 6), ("w1_bf16", ctypes.c_void_p), ("w2_bf16", ctypes.c_void_p),
+                ("step", ctypes.c_int64)]
+
+
+class MlpTrainOpts(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("delta", ctypes.c_float), ("seed", ctypes.c_uint64), ("loss", ctypes.c_void_p),
+                ("rows_target", ctypes.c_void_p), ("rows_mask", ctypes.c_void_p), ("rows_index", ctypes.c_void_p)]
+
+
 class Grads(ctypes.Structure):
     _fields_ = [("d_verts", ctypes.c_void_p), ("d_albedo", ctypes.c_void_p), ("d_radiance", ctypes.c_void_p),
-                ("d_cam_to_world", ctypes.c_void_p), ("d_cam_scale", ctypes.c_void_p)]
+                ("d_cam_to_world", ctypes.c_void_p), ("d_cam_scale", ctypes.c_void_p),
+                ("dimage_dparam", ctypes.c_void_p), ("n_jac", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("jac_param", ctypes.c_int64 * 8)]
 
 
 class BatchItem(ctypes.Structure):
@@ -131,9 +151,11 @@ def load(build_if_missing: bool = True):
         "drt_batch_get_info": ([vp, vp, ctypes.POINTER(BatchInfo)], i32),
         "drt_batch_free": ([vp, vp], i32),
         "drt_render_batch": ([vp, pp, i32, ctypes.POINTER(RenderOpts), pp, pp, ctypes.POINTER(Grads), vp], i32),
+        "drt_mlp_train": ([vp, ctypes.POINTER(MlpLog), i32, ctypes.POINTER(MlpTrainOpts), ctypes.POINTER(MlpState),
+                           vp], i32),
         "drt_probe_fma": ([vp, ctypes.POINTER(ctypes.c_double), vp], i32),
         "drt_probe_l2": ([vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), vp], i32),
-        "drt_last_error": ([], ctypes.c_char_p),
+        "drt_last_error": ([vp], ctypes.c_char_p),
         "drt_version": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -146,7 +168,7 @@ def load(build_if_missing: bool = True):
 
 def _check(status):
     if status != DRT_OK:
-        raise DrtError(status, load().drt_last_error().decode(errors="replace"))
+        raise DrtError(status, load().drt_last_error(None).decode(errors="replace"))
 
 
 def _ptr(a):
@@ -178,7 +200,7 @@ def _stream(stream):
 
 def make_opts(spp, edge_spp=None, max_depth=1, primary_only=False, seed=0, eps_rel=0.0, terms=0,
               seg_weights=None, seg_log=None, seg_scores=None, scene_id=0, sec_tree_samples=0,
-              sec_point=0, pixels=None, edges=None) -> RenderOpts:
+              sec_point=0, pixels=None, edges=None, aov=0) -> RenderOpts:
     """seg_weights: a CUDA float32 tensor of per-segment weights selects the
     mixture proposal 1; seg_scores: per-segment network scores select the
     mixture proposal 2.  The tensor must stay alive until the backward call
@@ -188,18 +210,20 @@ def make_opts(spp, edge_spp=None, max_depth=1, primary_only=False, seed=0, eps_r
     the edge's arc mixed with uniform (0: uniform).  pixels=(begin, end) and
     edges=(begin, end) restrict the backward pass to the interior and
     secondary samples of those pixels and to those primary edge samples
-    (default: all)."""
+    (default: all).  aov: geometry buffer of the first hit (AOV_ALBEDO,
+    AOV_POSITION, AOV_NORMAL, AOV_DEPTH; 0: the image)."""
     if seg_weights is not None and seg_scores is not None:
         raise ValueError("give seg_weights or seg_scores, not both")
     mode, w = (1, seg_weights) if seg_weights is not None else ((2, seg_scores) if seg_scores is not None else (0, None))
     n = int(w.numel()) if w is not None else 0
-    return RenderOpts(int(spp), int(spp if edge_spp is None else edge_spp), int(max_depth), int(bool(primary_only)),
+    return RenderOpts(int(spp), int(spp if edge_spp is None else edge_spp), int(max_depth),
+                      int(bool(primary_only) or aov > 0),
                       int(seed) & (2 ** 64 - 1), float(eps_rel), int(terms), mode,
                       _ptr(w) if w is not None else None, n,
                       _ptr(seg_log) if seg_log is not None else None, int(scene_id),
                       1 if sec_tree_samples > 0 else 0, int(sec_tree_samples), int(sec_point),
                       int(pixels[0]) if pixels else 0, int(pixels[1]) if pixels else 0,
-                      int(edges[0]) if edges else 0, int(edges[1]) if edges else 0)
+                      int(edges[0]) if edges else 0, int(edges[1]) if edges else 0, int(aov))
 
 
 class Context:
@@ -284,6 +308,16 @@ class Context:
         _check(self.lib.drt_mlp_backward(self.handle, _ptr(x), _ptr(target), _ptr(mask), int(x.shape[0]),
                                          float(inv_n), ctypes.byref(w), ctypes.byref(g), _ptr(loss),
                                          _stream(stream)))
+
+    def mlp_train(self, logs, state: "MlpState", steps, batch=0, lr=0.0, delta=0.0, seed=0, loss=None,
+                  rows_target=None, rows_mask=None, rows_index=None, stream=None):
+        """drt_mlp_train over a sequence of MlpLog records (their arrays must
+        stay alive during the call); state is updated in place."""
+        arr = (MlpLog * len(logs))(*logs)
+        o = MlpTrainOpts(int(steps), int(batch), float(lr), float(delta), int(seed) & (2 ** 64 - 1), _ptr(loss),
+                         _ptr(rows_target), _ptr(rows_mask), _ptr(rows_index))
+        _check(self.lib.drt_mlp_train(self.handle, arr, len(logs), ctypes.byref(o), ctypes.byref(state),
+                                      _stream(stream)))
 
     def adam_step(self, params, grads, m1, m2, params_bf16, lr, step, beta1=0.9, beta2=0.999, eps=1e-8,
                   stream=None):
@@ -407,9 +441,17 @@ class Scene:
                                                         _stream(stream)))
 
     def backward(self, d_image, opts: RenderOpts, tape=None, d_verts=None, d_albedo=None, d_radiance=None,
-                 d_cam_to_world=None, d_cam_scale=None, stream=None):
-        """Add d loss / d parameters into the given gradient arrays."""
+                 d_cam_to_world=None, d_cam_scale=None, dimage_dparam=None, jac_params=None, stream=None):
+        """Add d loss / d parameters into the given gradient arrays;
+        dimage_dparam [n, H, W] with jac_params (n <= 8 flat parameter
+        indices) also receives the per-pixel gradient image."""
         g = Grads(_ptr(d_verts), _ptr(d_albedo), _ptr(d_radiance), _ptr(d_cam_to_world), _ptr(d_cam_scale))
+        if dimage_dparam is not None:
+            idx = [int(i) for i in (jac_params or [])]
+            g.dimage_dparam = _ptr(dimage_dparam)
+            g.n_jac = len(idx)
+            for k, i in enumerate(idx[:8]):
+                g.jac_param[k] = i
         _check(self.ctx.lib.drt_render_backward(self.ctx.handle, self.handle, tape.handle if tape else None,
                                                 ctypes.byref(opts), _ptr(d_image), ctypes.byref(g),
                                                 _stream(stream)))

@@ -135,40 +135,50 @@ class EdgeProposal:
             self.ctx.adam_step(self.p[k], self.g[k], self.m1[k], self.m2[k], self.pb.get(k), lr, self.steps,
                                stream=stream)
 
-    def fit(self, data: "Dataset", steps: int, batch: int = 16384, lr: float = 3e-3, log_every: int = 200):
-        """Mini-batch Adam over the (pre-shuffled) dataset; returns the mean
-        loss of each block of log_every steps."""
-        n = data.x.shape[0]
-        batch = min(batch, n)
-        nb = max(1, n // batch)
-        hist = []
-        acc = torch.zeros(1, device=data.x.device)
-        for i in range(steps):
-            b = i % nb
-            sl = slice(b * batch, (b + 1) * batch)
-            # cosine decay to lr/10
-            lr_i = lr * (0.55 + 0.45 * math.cos(math.pi * i / max(1, steps)))
-            self.train_step(data.x[sl], data.target[sl], data.mask[sl], lr_i, acc)
-            if (i + 1) % log_every == 0 or i + 1 == steps:
-                k = (i % log_every) + 1
-                hist.append(acc.item() / k)
-                acc.zero_()
-        return hist
+    def state(self) -> drt.MlpState:
+        """The library's view of the parameters, Adam moments and gradients."""
+        st = drt.MlpState()
+        for i, k in enumerate(NAMES):
+            st.p[i] = self.p[k].data_ptr()
+            st.m1[i] = self.m1[k].data_ptr()
+            st.m2[i] = self.m2[k].data_ptr()
+            st.g[i] = self.g[k].data_ptr()
+        st.w1_bf16 = self.pb["w1"].data_ptr()
+        st.w2_bf16 = self.pb["w2"].data_ptr()
+        st.step = self.steps
+        return st
+
+    def fit(self, data: "Dataset", steps: int, batch: int = 16384, lr: float = 3e-3, seed: int = 0) -> float:
+        """Mini-batch Adam over the logged rows, all in the library
+        (drt_mlp_train: targets, shuffle, learning-rate schedule and steps);
+        returns the mean loss per step."""
+        st = self.state()
+        loss = torch.zeros(1, device=data.parts[0].x.device)
+        self.ctx.mlp_train([p.record() for p in data.parts], st, steps, batch=batch, lr=lr, seed=seed, loss=loss)
+        self.steps = int(st.step)
+        return float(loss.item()) / max(1, steps)
+
+
+@dataclasses.dataclass
+class SceneLog:
+    """One scene's logged training data (see drt_mlp_log)."""
+    x: torch.Tensor        # [n, 32] bf16 bits of the segment features
+    seg_log: torch.Tensor  # [n] logged sums of |w (f_u - f_l)| per segment
+    seg_len: torch.Tensor  # [n] FP64 screen lengths of the segments
+    n_samples: float       # primary edge samples behind seg_log
+
+    def record(self) -> drt.MlpLog:
+        return drt.MlpLog(self.x.data_ptr(), self.seg_log.data_ptr(), self.seg_len.data_ptr(), int(self.x.shape[0]),
+                          float(self.n_samples))
 
 
 @dataclasses.dataclass
 class Dataset:
-    x: torch.Tensor       # [n, 32] bf16 bits
-    target: torch.Tensor  # [n] log relative contribution density
-    mask: torch.Tensor    # [n] regression weight (segment length / mean length)
+    parts: list  # SceneLog per logged scene
 
-    @staticmethod
-    def concat(parts, seed: int = 0) -> "Dataset":
-        x = torch.cat([p.x for p in parts])
-        t = torch.cat([p.target for p in parts])
-        m = torch.cat([p.mask for p in parts])
-        perm = torch.from_numpy(np.random.default_rng(seed).permutation(x.shape[0])).to(x.device)
-        return Dataset(x[perm].contiguous(), t[perm].contiguous(), m[perm].contiguous())
+    @property
+    def rows(self) -> int:
+        return sum(int(p.x.shape[0]) for p in self.parts)
 
 
 def _zero(n, dev):
@@ -176,10 +186,11 @@ def _zero(n, dev):
 
 
 def collect(ctx: drt.Context, scene: drt.Scene, d_image: torch.Tensor, *, edge_spp: int, passes: int, seed: int,
-            max_depth: int = 1, delta: float = 1e-3) -> Dataset:
-    """Training rows of one scene from the plain (length) distribution over
-    its tile segments: `passes` backward passes of the primary edge term, each
-    with edge_spp samples per pixel, log |w (f_u - f_l)| per segment."""
+            max_depth: int = 1) -> SceneLog:
+    """Training data of one scene from the plain (length) distribution over
+    its tile segments: `passes` backward passes of the primary edge term,
+    each with edge_spp samples per pixel, logging |w (f_u - f_l)| per segment,
+    and the segments' features."""
     dev = d_image.device
     _, _, _, seg_len = scene.segments()
     n = len(seg_len)
@@ -191,17 +202,9 @@ def collect(ctx: drt.Context, scene: drt.Scene, d_image: torch.Tensor, *, edge_s
                           seg_log=log)
         scene.backward(d_image, o, d_verts=dv)
     n_samples = float(passes) * edge_spp * scene.width * scene.height
-    L = float(seg_len.sum())
-    lens = torch.from_numpy(seg_len).to(dev)
-    # integral of |w (f_u - f_l)| over the segment, per unit length
-    dens = log.double() * (L / n_samples) / lens.clamp_min(1e-12)
-    mean = float(log.double().sum()) / n_samples  # = integral over all edges / L
-    rel = dens / max(mean, 1e-30)
-    target = torch.log(rel + delta).float()
-    mask = (lens / lens.mean()).float()
     x = torch.empty((n, N_IN), dtype=torch.int16, device=dev)
     scene.segment_features(d_image, x, step_image(scene, seed, max_depth))
-    return Dataset(x, target, mask)
+    return SceneLog(x, log, torch.from_numpy(np.ascontiguousarray(seg_len, np.float64)).to(dev), n_samples)
 
 
 IMAGE_SPP = 16
@@ -321,11 +324,11 @@ def protocol(ctx: drt.Context, *, steps: int = 6000, k_direct: int = 32, k_proce
         _, s, w = _make_scene(ctx, "procedural", seed)
         parts.append(collect(ctx, s, w, edge_spp=4, passes=2, seed=seed * 1000, max_depth=3))
         s.free()
-    data = Dataset.concat(parts)
+    data = Dataset(parts)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     net = EdgeProposal(ctx, 0)
-    hist = net.fit(data, steps=steps)
+    loss_mean = net.fit(data, steps=steps)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     scenes = []
@@ -347,8 +350,8 @@ def protocol(ctx: drt.Context, *, steps: int = 6000, k_direct: int = 32, k_proce
         raise RuntimeError("device error flag %d (%d) in the proposal protocol" % (code, info))
     gm = float(np.exp(np.mean([np.log(max(r["ratio"], 1e-30)) for r in scenes])))
     return {"ratio_geomean": gm, "ratio_unit": "learned/plain gradient variance x time (<1: learned wins)",
-            "scenes": scenes, "train_rows": int(data.x.shape[0]), "train_steps": steps,
-            "collect_s": t1 - t0, "train_s": t2 - t1, "loss_first": hist[0], "loss_last": hist[-1],
+            "scenes": scenes, "train_rows": data.rows, "train_steps": steps,
+            "collect_s": t1 - t0, "train_s": t2 - t1, "loss_mean": loss_mean,
             "variance": "mean over vertex entries of the run variance of the primary edge gradient, "
                         "over the mean squared gradient",
             "time": "median device ms of one gradient estimate; learned includes segment features, network "

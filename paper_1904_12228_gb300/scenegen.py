@@ -17,6 +17,7 @@ import numpy as np
 
 CAM_ORTHO = 0
 CAM_PINHOLE = 1
+CAM_FISHEYE = 2
 
 
 @dataclasses.dataclass
@@ -288,6 +289,18 @@ def indirect_panel(view: str = "interior", width: int = 12, height: int = 12) ->
     cam = look_at((centre[0], 0.05, centre[1]), (centre[0], 1.0, centre[1]), up=(0, 0, -1))
     return Scene(verts=verts, tris=tris, albedo=alb, light_tris=[4, 5], radiance=[40, 40, 40], cam_to_world=cam,
                  cam_scale=half, cam_type=CAM_ORTHO, width=width, height=height)
+
+
+def fisheye_view(seed: int, width: int = 64, height: int = 48, subdiv: int = 2, theta_half_height: float = 1.1
+                 ) -> Scene:
+    """The direct-lighting scene (jittered icosphere on a ground quad under an
+    area light) seen through an equidistant fisheye from close by: the screen
+    point at distance r from the centre, in units of half the image height,
+    looks along the direction theta = r * theta_half_height from the optical
+    axis (every pixel, corners included, sees a direction below pi)."""
+    sc = direct_lighting(seed, width=width, height=height, subdiv=subdiv)
+    return dataclasses.replace(sc, cam_to_world=look_at((0.4, 1.2, 2.6), (0.0, -0.2, 0.0)),
+                               cam_scale=float(theta_half_height), cam_type=CAM_FISHEYE)
 
 
 def gi_panel(width: int = 16, height: int = 16) -> Scene:

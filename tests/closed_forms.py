@@ -134,6 +134,34 @@ def coverage_gradient(tri2d, weight, width, height):
     return g
 
 
+def coverage_gradient_pixels(tri2d, weight, width, height):
+    """The terms of coverage_gradient pixel by pixel: [H, W, 3, 2], the
+    boundary integral over the part of each edge inside pixel (j, i)."""
+    tri = [np.asarray(p, float) for p in tri2d]
+    g = np.zeros((height, width, 3, 2))
+    for e in range(3):
+        ia, ib, ic = e, (e + 1) % 3, (e + 2) % 3
+        a, b, c = tri[ia], tri[ib], tri[ic]
+        d = b - a
+        L = np.hypot(d[0], d[1])
+        n = np.array([d[1], -d[0]]) / L
+        if np.dot(n, c - a) > 0:
+            n = -n
+        x0, x1 = min(a[0], b[0]), max(a[0], b[0])
+        y0, y1 = min(a[1], b[1]), max(a[1], b[1])
+        for j in range(max(0, int(np.floor(y0))), min(height, int(np.floor(y1)) + 1)):
+            for i in range(max(0, int(np.floor(x0))), min(width, int(np.floor(x1)) + 1)):
+                iv = segment_in_box(a, b, i, j, i + 1, j + 1)
+                if iv is None:
+                    continue
+                s0, s1 = iv
+                wa = (s1 - s0) - 0.5 * (s1 * s1 - s0 * s0)
+                wb = 0.5 * (s1 * s1 - s0 * s0)
+                g[j, i, ia] += weight[j, i] * wa * L * n
+                g[j, i, ib] += weight[j, i] * wb * L * n
+    return g
+
+
 def polygon_irradiance(p, normal, poly3d):
     """Lambert's formula: integral over the polygon's solid angle of
     cos(theta) d omega = 1/2 sum_i Theta_i (n . Gamma_i)."""

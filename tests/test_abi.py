@@ -45,7 +45,8 @@ def test_binding_structs_match_the_header_layout(tmp_path):
     from paper_1904_12228_gb300 import drt
     pairs = [("drt_scene_desc", drt.SceneDesc), ("drt_render_opts", drt.RenderOpts), ("drt_grads", drt.Grads),
              ("drt_batch_item", drt.BatchItem), ("drt_batch_info", drt.BatchInfo),
-             ("drt_mlp_weights", drt.MlpWeights), ("drt_mlp_grads", drt.MlpGrads)]
+             ("drt_mlp_weights", drt.MlpWeights), ("drt_mlp_grads", drt.MlpGrads), ("drt_mlp_log", drt.MlpLog),
+             ("drt_mlp_state", drt.MlpState), ("drt_mlp_train_opts", drt.MlpTrainOpts)]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "drt.h"', "int main(void) {"]
     for cname, py in pairs:
         lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))

@@ -130,3 +130,122 @@ def test_training_fits_a_smooth_function(env):
             ctx.adam_step(t[k], g[k], st[k][0], st[k][1], t.get(k + "b"), lr=3e-3, step=step)
         losses.append(loss.item())
     assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
+
+
+def _train_problem(rng, rows_per_log=(700, 1300)):
+    logs = []
+    for n in rows_per_log:
+        x = rng.normal(size=(n, 32)).astype(np.float32)
+        seg_log = (rng.exponential(size=n) * (rng.uniform(size=n) > 0.2)).astype(np.float32)
+        seg_len = rng.uniform(0.1, 30.0, size=n)
+        logs.append((x, seg_log, seg_len, float(16 * 96 * 96)))
+    return logs
+
+
+def _reference_rows(logs, seed, delta=1e-3):
+    """Targets, weights and shuffle of drt_mlp_train, written out in numpy."""
+    import oracle
+    tgt, msk, xs = [], [], []
+    for x, seg_log, seg_len, N in logs:
+        S, L = float(np.sum(seg_log.astype(np.float64))), float(np.sum(seg_len))
+        dens = seg_log.astype(np.float64) * (L / N) / np.maximum(seg_len, 1e-12)
+        tgt.append(np.log(dens / max(S / N, 1e-30) + delta))
+        msk.append(seg_len / (L / len(seg_len)))
+        xs.append(x)
+    tgt, msk, xs = np.concatenate(tgt), np.concatenate(msk), np.concatenate(xs)
+    key = np.array([seed & 0xFFFFFFFF, seed >> 32], np.uint32)
+    keys = np.array([oracle.philox(np.array([r, 0, 0x4D4C5054, 0], np.uint32), key)[0] for r in range(len(tgt))],
+                    np.uint64)
+    perm = np.argsort(keys, kind="stable")
+    return tgt[perm], msk[perm], xs[perm], perm
+
+
+def _device_logs(drt, logs):
+    held, recs = [], []
+    for x, seg_log, seg_len, N in logs:
+        t = (torch.from_numpy(mlp.bf16_bits(x).view(np.int16)).cuda(), torch.from_numpy(seg_log).cuda(),
+             torch.from_numpy(seg_len).cuda())
+        held.append(t)
+        recs.append(drt.MlpLog(t[0].data_ptr(), t[1].data_ptr(), t[2].data_ptr(), len(seg_log), N))
+    return held, recs
+
+
+def _state(drt, p):
+    names = ("w1", "b1", "w2", "b2", "w3", "b3")
+    t, _ = _device_params(drt, p)
+    m1 = {k: torch.zeros_like(t[k]) for k in names}
+    m2 = {k: torch.zeros_like(t[k]) for k in names}
+    g = {k: torch.zeros_like(t[k]) for k in names}
+    st = drt.MlpState()
+    for i, k in enumerate(names):
+        st.p[i], st.m1[i], st.m2[i], st.g[i] = t[k].data_ptr(), m1[k].data_ptr(), m2[k].data_ptr(), g[k].data_ptr()
+    st.w1_bf16, st.w2_bf16, st.step = t["w1b"].data_ptr(), t["w2b"].data_ptr(), 0
+    return st, t, m1, m2, g
+
+
+def test_mlp_train_prepares_the_rows_as_specified(env):
+    """drt_mlp_train's targets, regression weights and shuffle against their
+    definition, written out in numpy (targets in FP32 of an FP64 value)."""
+    drt, ctx = env
+    rng = np.random.default_rng(11)
+    logs = _train_problem(rng)
+    held, recs = _device_logs(drt, logs)
+    st, *_ = _state(drt, mlp.init_params(3))
+    rows = sum(len(l[1]) for l in logs)
+    tg = torch.zeros(rows, device="cuda")
+    mk = torch.zeros(rows, device="cuda")
+    ix = torch.zeros(rows, dtype=torch.int64, device="cuda")
+    seed = (7 << 32) + 12345
+    ctx.mlp_train(recs, st, 0, seed=seed, rows_target=tg, rows_mask=mk, rows_index=ix)
+    want_t, want_m, _, perm = _reference_rows(logs, seed)
+    assert np.array_equal(ix.cpu().numpy(), perm)
+    assert np.allclose(tg.cpu().numpy(), want_t, rtol=1e-6, atol=1e-6)
+    assert np.allclose(mk.cpu().numpy(), want_m, rtol=1e-6, atol=0)
+    assert st.step == 0
+
+
+def test_mlp_train_step_matches_the_reference(env):
+    """One training step: the gradient on the first shuffled batch against
+    the FP64 reference, and the weights after it against bias-corrected Adam
+    applied to that gradient at the step's learning rate."""
+    drt, ctx = env
+    rng = np.random.default_rng(12)
+    logs = _train_problem(rng)
+    held, recs = _device_logs(drt, logs)
+    p = mlp.init_params(4)
+    st, t, m1, m2, g = _state(drt, p)
+    seed, batch, lr = 99, 512, 2e-3
+    loss = torch.zeros(1, device="cuda")
+    ctx.mlp_train(recs, st, 1, batch=batch, lr=lr, seed=seed, loss=loss)
+    torch.cuda.synchronize()
+    assert ctx.check_device() == (0, 0)
+    assert st.step == 1
+    want_t, want_m, xs, _ = _reference_rows(logs, seed)
+    want_g, want_loss = mlp.backward(xs[:batch], want_t[:batch], want_m[:batch], 1.0 / batch, p)
+    for k in ("w1", "b1", "w2", "b2", "w3", "b3"):
+        got = g[k].cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(got - want_g[k]) <= 4e-3 * np.abs(want_g[k]).max() + 1e-6), k
+        # Adam's first step from zero moments, on the gradient the library used
+        gk = got.astype(np.float32).astype(np.float64)
+        m = 0.1 * gk
+        v = 0.001 * gk * gk
+        upd = lr * (m / 0.1) / (np.sqrt(v / 0.001) + 1e-8)  # schedule factor at step 0 is 1
+        want_p = np.asarray(p[k], np.float64) - upd
+        assert np.allclose(t[k].cpu().numpy(), want_p, rtol=1e-5, atol=1e-6), k
+    assert abs(loss.item() - want_loss) <= 4e-3 * want_loss + 1e-6
+    assert np.array_equal(t["w1b"].cpu().numpy().view(np.uint16), mlp.bf16_bits(t["w1"].cpu().numpy()))
+
+
+def test_mlp_train_options_are_checked(env):
+    drt, ctx = env
+    rng = np.random.default_rng(13)
+    logs = _train_problem(rng, (50,))
+    x, seg_log, seg_len, N = logs[0]
+    st, *_ = _state(drt, mlp.init_params(5))
+    bad = [drt.MlpLog(torch.zeros(1).data_ptr(), 0, 0, 50, N)]  # host / NULL arrays
+    with pytest.raises(drt.DrtError):
+        ctx.mlp_train(bad, st, 1)
+    held, recs = _device_logs(drt, logs)
+    recs[0].n_samples = 0.0
+    with pytest.raises(drt.DrtError):
+        ctx.mlp_train(recs, st, 1)

@@ -355,3 +355,93 @@ def test_mixture_proposal_gradient(drt, ctx, spp, mode):
     assert_grads(got, g[:3 * V], a[:3 * V], "mixture proposal")
     plain, _ = oracle.backward(scene, w, spp=spp, edge_spp=spp, seed=3, terms=oracle.TERM_PRIMARY, n_threads=NT)
     assert not np.allclose(plain[:3 * V], g[:3 * V])
+
+
+# ---------------------------------------------------------------------------
+# Per-pixel gradient image (drt_grads.dimage_dparam)
+# ---------------------------------------------------------------------------
+def _gpu_jacobian(drt, ctx, scene, w, spp, seed, params, depth=1, primary_only=False):
+    s = drt.Scene.from_arrays(ctx, scene)
+    img = torch.zeros((scene.height, scene.width, 3), device="cuda")
+    opts = drt.make_opts(spp, spp, max_depth=depth, primary_only=primary_only, seed=seed)
+    tape = s.render(img, opts, want_tape=True)
+    dv = torch.zeros((len(scene.verts), 3), device="cuda")
+    jac = torch.zeros((len(params), scene.height, scene.width), device="cuda")
+    z = lambda *sh: torch.zeros(sh, device="cuda")  # noqa: E731
+    da, dr, dc, ds = z(len(scene.tris), 3), z(3), z(3, 4), z(1)
+    s.backward(torch.from_numpy(w).cuda(), opts, tape=tape, d_verts=dv, d_albedo=da, d_radiance=dr,
+               d_cam_to_world=dc, d_cam_scale=ds, dimage_dparam=jac, jac_params=params)
+    torch.cuda.synchronize()
+    assert ctx.check_device() == (0, 0)
+    flat = np.concatenate([x.cpu().numpy().ravel().astype(np.float64) for x in (dv, da, dr, dc, ds)])
+    return jac.double().cpu().numpy(), flat
+
+
+def _assert_jacobian(got, want, absum, label):
+    """Per pixel within 1e-4 |J| + 1e-6 A_k, with A_k the oracle's magnitude
+    of the terms summed into the whole gradient entry k (it bounds the terms
+    of any one pixel)."""
+    err = np.abs(got - want)
+    bound = 1e-4 * np.abs(want) + 1e-6 * np.asarray(absum, np.float64)[:, None, None] + 1e-12
+    bad = err > bound
+    assert not bad.any(), "%s: %d of %d pixel entries off, worst %g (bound %g)" % (
+        label, bad.sum(), bad.size, err.max(), bound.flat[np.argmax(err / bound)])
+
+
+@pytest.mark.parametrize("seed", [1235, 7])
+def test_single_triangle_pixel_gradient_image(drt, ctx, seed):
+    """The six screen-plane vertex coordinates of the single-triangle case:
+    the per-pixel gradient image against the oracle's (which is pinned to the
+    per-pixel Reynolds boundary integral), and its sum over the pixels
+    against the gradient."""
+    scene = sg.single_triangle(seed)
+    w = sg.loss_adjoint(seed, scene.width, scene.height)
+    params = [3 * v + c for v in range(3) for c in range(2)]
+    got, grad = _gpu_jacobian(drt, ctx, scene, w, 16, seed, params, primary_only=True)
+    g, a, want = oracle.backward(scene, w, spp=16, edge_spp=16, seed=seed, primary_only=True, n_threads=NT,
+                                 jacobian=params)
+    _assert_jacobian(got, want, a[params], "single triangle")
+    assert np.allclose(got.sum(axis=(1, 2)), grad[params], rtol=1e-4, atol=1e-6 * np.abs(grad).max())
+    assert np.count_nonzero(want) > 10
+
+
+@pytest.mark.parametrize("depth", [1, 2])
+def test_lit_scene_pixel_gradient_image(drt, ctx, depth):
+    """Vertex, albedo, radiance, camera and camera-scale entries of a lit
+    scene with all gradient terms."""
+    scene = _small_lit(W=24, H=18, subdiv=1)
+    V, T = len(scene.verts), len(scene.tris)
+    w = sg.loss_adjoint(6, scene.width, scene.height)
+    params = [3 * 2 + 1, 3 * (V - 3) + 0, 3 * (V - 1) + 2, 3 * V + 3 * 4 + 1, 3 * V + 3 * T + 0,
+              3 * V + 3 * T + 3 + 3, 3 * V + 3 * T + 3 + 5, 3 * V + 3 * T + 15]
+    got, grad = _gpu_jacobian(drt, ctx, scene, w, 6, 4, params, depth=depth)
+    g, a, want = oracle.backward(scene, w, spp=6, edge_spp=6, seed=4, max_depth=depth, n_threads=NT,
+                                 jacobian=params)
+    _assert_jacobian(got, want, a[params], "lit depth %d" % depth)
+    assert np.allclose(got.sum(axis=(1, 2)), grad[params], rtol=1e-4, atol=1e-5 * np.abs(grad[params]).max())
+
+
+# ---------------------------------------------------------------------------
+# Geometry buffers (the AOV extension of Sec. 5.4)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("aov", [1, 2, 3, 4])
+def test_geometry_buffer_image_and_gradient(drt, ctx, aov):
+    scene = _small_lit(W=40, H=28, subdiv=2)
+    s = drt.Scene.from_arrays(ctx, scene)
+    img = torch.zeros((28, 40, 3), device="cuda")
+    opts = drt.make_opts(8, 8, seed=13, aov=aov)
+    tape = s.render(img, opts, want_tape=True)
+    want_img = oracle.render(scene, spp=8, seed=13, aov=aov, n_threads=NT)
+    assert_pixels(img.double().cpu().numpy(), want_img, "aov %d image" % aov)
+    w = sg.loss_adjoint(14, 40, 28)
+    z = lambda *sh: torch.zeros(sh, dtype=torch.float32, device="cuda")  # noqa: E731
+    dv, da, dr, dc, ds = z(len(scene.verts), 3), z(len(scene.tris), 3), z(3), z(3, 4), z(1)
+    s.backward(torch.from_numpy(w).cuda(), opts, tape=tape, d_verts=dv, d_albedo=da, d_radiance=dr,
+               d_cam_to_world=dc, d_cam_scale=ds)
+    torch.cuda.synchronize()
+    assert ctx.check_device() == (0, 0)
+    got = np.concatenate([x.cpu().numpy().ravel().astype(np.float64) for x in (dv, da, dr, dc, ds)])
+    want, absum, c = oracle.backward(scene, w, spp=8, edge_spp=8, seed=13, aov=aov, n_threads=NT,
+                                     contributions=True)
+    assert_grads(got, want, absum, "aov %d gradient" % aov, c)
+    assert np.abs(want).max() > 0

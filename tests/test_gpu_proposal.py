@@ -27,16 +27,18 @@ def trained():
         s = drt.Scene.from_arrays(ctx, sc)
         w = torch.from_numpy(sg.loss_adjoint(seed, sc.width, sc.height)).cuda()
         parts.append(P.collect(ctx, s, w, edge_spp=8, passes=4, seed=seed * 1000, max_depth=3))
-    data = P.Dataset.concat(parts)
+    data = P.Dataset(parts)
     net = P.EdgeProposal(ctx, 0)
-    hist = net.fit(data, steps=1500, batch=8192)
+    # the library trains: targets, shuffle, schedule and steps (drt_mlp_train)
+    hist = [net.fit(data, steps=100, batch=8192, seed=1), net.fit(data, steps=1400, batch=8192, seed=2)]
     return ctx, P, net, hist
 
 
 def test_training_lowers_the_loss(trained):
-    _, _, _, hist = trained
+    _, _, net, hist = trained
     assert np.all(np.isfinite(hist))
     assert hist[-1] < 0.8 * hist[0], hist
+    assert net.steps == 1500
 
 
 @pytest.mark.parametrize("kind,seed", [("direct", 200), ("procedural", 202)])

@@ -191,6 +191,45 @@ def test_single_triangle_edge_gradient_reynolds(seed):
         oracle.split_params(scene, g)["verts"][:, 2] == 0)
 
 
+def test_single_triangle_pixel_gradient_image_reynolds():
+    """The per-pixel gradient image of the six screen-plane vertex coordinates
+    (each primary edge sample counted in the pixel that contains its point)
+    is, in expectation, the Reynolds boundary integral over the part of the
+    triangle's edges inside that pixel; pixels the edges do not cross get
+    exactly zero; the image sums to the gradient."""
+    scene = sg.single_triangle(1235)
+    W, H = scene.width, scene.height
+    w = sg.loss_adjoint(1235, W, H)
+    wsum = w.astype(np.float64).sum(axis=2)
+    gp = cf.coverage_gradient_pixels(_tri_pixels(scene), 0.7 * wsum, W, H)
+    want = np.stack([gp[..., 0] * W / 2.0, -gp[..., 1] * H / 2.0], axis=-1)  # [H, W, 3, 2]
+    params = [3 * v + c for v in range(3) for c in range(2)]
+    runs = []
+    for k in range(8):
+        g, _, jac = oracle.backward(scene, w, spp=1, edge_spp=16, seed=2000 + k, primary_only=True,
+                                    terms=oracle.TERM_PRIMARY, n_threads=NT, jacobian=params)
+        assert np.allclose(jac.sum(axis=(1, 2)), g[params], rtol=1e-10, atol=1e-12)
+        runs.append(jac)
+    runs = np.array(runs)  # [K, 6, H, W]
+    want6 = want.reshape(H, W, 6).transpose(2, 0, 1)
+    crossed = np.abs(want6) > 0
+    assert np.all(runs[:, ~crossed] == 0.0)
+    mean, se = runs.mean(0), runs.std(0, ddof=1) / np.sqrt(len(runs))
+    z = np.abs(mean - want6)[crossed] / (se[crossed] + 1e-3 * np.abs(want6).max())
+    assert np.mean(z < 3.0) > 0.97 and z.max() < 6.0, (np.mean(z < 3.0), z.max())
+
+
+def test_pixel_gradient_image_sums_to_the_gradient_at_depth_two():
+    scene = sg.direct_lighting(1236, width=12, height=10, subdiv=1)
+    V, T = len(scene.verts), len(scene.tris)
+    w = sg.loss_adjoint(7, scene.width, scene.height)
+    params = [0, 3 * 5 + 1, 3 * (V - 3) + 2, 3 * V + 4, 3 * V + 3 * T + 1, 3 * V + 3 * T + 3 + 3,
+              3 * V + 3 * T + 15]
+    g, _, jac = oracle.backward(scene, w, spp=4, edge_spp=4, seed=8, max_depth=2, n_threads=NT, jacobian=params)
+    assert np.allclose(jac.sum(axis=(1, 2)), g[params], rtol=1e-10, atol=1e-12 * np.abs(g).max())
+    assert np.count_nonzero(jac) > 0
+
+
 def test_single_triangle_albedo_homogeneity():
     """Per seed, exactly: sum_c rho_c dL/drho_c = sum_p w_p . I_p."""
     scene = sg.single_triangle(5)
