@@ -64,7 +64,17 @@ typedef struct drt_scene drt_scene;
 typedef struct drt_tape drt_tape;
 typedef struct drt_batch drt_batch;
 
-enum { DRT_CAMERA_ORTHO = 0, DRT_CAMERA_PINHOLE = 1 };
+/* Cameras: orthographic and pinhole map 3D lines to screen lines, so their
+ * primary edges are sampled on the projected segments (Sec. 5.2.1).  The
+ * equidistant fisheye (Sec. 5.2, "Cameras with Non-linear Projections")
+ * sends the screen point at distance r from the image centre, in units of
+ * half the image height, along the direction at angle r * cam_scale from
+ * the optical axis; its primary edges are sampled in 3D (by their chord on
+ * the unit sphere of directions from the camera), and each sample's edge
+ * term follows the curved image of the edge.  A fisheye scene needs
+ * cam_scale * sqrt((W/H)^2 + 1) < 0.99 pi (every pixel sees a direction);
+ * it takes the length proposal only and no batch. */
+enum { DRT_CAMERA_ORTHO = 0, DRT_CAMERA_PINHOLE = 1, DRT_CAMERA_FISHEYE = 2 };
 
 /* A scene given as flat arrays, the way Sec. 5.4 builds scenes from tensors
  * (float vertices, integer indices, material, light and camera).  All triangles are both occluders and reflectors
@@ -80,8 +90,9 @@ typedef struct {
   int32_t n_light_tris;
   const float* radiance;       /* [3] emitted radiance of every light triangle */
   const float* cam_to_world;   /* [4,4] row-major affine camera matrix; camera looks down -z, y up */
-  float cam_scale;             /* pinhole: tan(fov_y/2); ortho: half height of the view */
-  int32_t cam_type;            /* DRT_CAMERA_ORTHO or DRT_CAMERA_PINHOLE */
+  float cam_scale;             /* pinhole: tan(fov_y/2); ortho: half height of the view; fisheye: the
+                                  angle from the optical axis at half the image height (radians) */
+  int32_t cam_type;            /* DRT_CAMERA_ORTHO, DRT_CAMERA_PINHOLE or DRT_CAMERA_FISHEYE */
   int32_t width, height;       /* image size in pixels */
   int32_t bvh_leaf_size;       /* most triangles per BVH leaf, 1..8 (0 selects 1).  Two suit work
                                   dominated by coherent first-vertex rays (direct lighting: 4 %

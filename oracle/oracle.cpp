@@ -1078,9 +1078,11 @@ void secondary_edge(Ctx& C, int b, uint32_t c0, uint32_t c1, uint32_t pass, cons
   D3 A0 = V0d - Ps, A1 = V1d - Ps;
   D3 Nd = cross(A0, A1);
   const float* Le = P.sc->radiance;
+  /* both side rays first: which sides count */
+  bool ok[2] = {false, false};
+  Hit hs_[2];
   for (int side = 0; side < 2; ++side) {
     const float* ds = side == 0 ? du : dl;
-    double sgn = side == 0 ? 1.0 : -1.0;
     /* a side leaving below the shading horizon by more than 1e-5 |omega| is
      * not traced (FP32 decision, fixed order) */
     if (dot32(ns32, ds) < -1e-5f * wl) continue;
@@ -1090,11 +1092,27 @@ void secondary_edge(Ctx& C, int b, uint32_t c0, uint32_t c1, uint32_t pass, cons
     float m32[3];
     bary_point32(M.v0, M.v1, M.v2, h.b1, h.b2, m32);
     float dm32[3] = {m32[0] - p32[0], m32[1] - p32[1], m32[2] - p32[2]};
+    /* the hit must lie above the shading horizon (FP32 decision from the hit) */
+    if (!(dot32(ns32, dm32) > 0.0f)) continue;
+    ok[side] = true;
+    hs_[side] = h;
+  }
+  /* Both sides on one triangle: the edge separates no surfaces at this point,
+   * so the jump h_u - h_l of Eq. dirac_3d_edge is zero there; the difference
+   * of the two evaluations a finite offset apart would be an O(eps) residue */
+  if (ok[0] && ok[1] && hs_[0].tri == hs_[1].tri) return;
+  for (int side = 0; side < 2; ++side) {
+    if (!ok[side]) continue;
+    const float* ds = side == 0 ? du : dl;
+    double sgn = side == 0 ? 1.0 : -1.0;
+    Hit h = hs_[side];
+    TriV M = tri_of(P, h.tri);
+    float m32[3];
+    bary_point32(M.v0, M.v1, M.v2, h.b1, h.b2, m32);
+    float dm32[3] = {m32[0] - p32[0], m32[1] - p32[1], m32[2] - p32[2]};
     float nf32[3];
     face_normal32(M.v0, M.v1, M.v2, nf32);
-    /* the hit must lie above the shading horizon; the direct part also needs
-     * the light's front face toward p: both decided in FP32 from the hit */
-    if (!(dot32(ns32, dm32) > 0.0f)) continue;
+    /* the direct part needs the light's front face toward p (FP32 decision) */
     bool front = dot32(nf32, dm32) < 0.0f;
     V3 m{m32[0], m32[1], m32[2]};
     V3 dm = m - p;

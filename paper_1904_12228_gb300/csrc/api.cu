@@ -5,6 +5,7 @@
 // a status (nothing throws across the ABI); device work is enqueued on the
 // caller's stream; caller arrays may be host or device memory.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -330,8 +331,14 @@ drt_status drt_scene_upload(drt_context* ctx, const drt_scene_desc* d, void* str
   *out = nullptr;
   if (d->n_verts < 3 || d->n_tris < 1) return fail(DRT_ERR_INVALID_ARG, "need >= 3 vertices and >= 1 triangle");
   if (d->width < 1 || d->height < 1) return fail(DRT_ERR_INVALID_ARG, "bad image size %dx%d", d->width, d->height);
-  if (d->cam_type != DRT_CAMERA_ORTHO && d->cam_type != DRT_CAMERA_PINHOLE)
+  if (d->cam_type != DRT_CAMERA_ORTHO && d->cam_type != DRT_CAMERA_PINHOLE && d->cam_type != DRT_CAMERA_FISHEYE)
     return fail(DRT_ERR_INVALID_ARG, "bad cam_type %d", d->cam_type);
+  if (d->cam_type == DRT_CAMERA_FISHEYE) {
+    double aspect = (double)d->width / (double)d->height;
+    if (!((double)d->cam_scale * std::sqrt(aspect * aspect + 1.0) < 0.99 * 3.141592653589793))
+      return fail(DRT_ERR_INVALID_ARG, "fisheye cam_scale %g reaches past the direction behind the camera",
+                  (double)d->cam_scale);
+  }
   if (!d->verts || !d->tris || !d->albedo || !d->radiance || !d->cam_to_world)
     return fail(DRT_ERR_INVALID_ARG, "NULL scene array");
   if (d->n_light_tris < 0 || (d->n_light_tris > 0 && !d->light_tris))
@@ -550,6 +557,8 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
       return fail(DRT_ERR_STATE, "tape was recorded with different sampling options");
   }
   cudaStream_t st = (cudaStream_t)stream;
+  if (op.proposal >= 1 && s->cam_type == DRT_CAMERA_FISHEYE)
+    return fail(DRT_ERR_INVALID_ARG, "the fisheye camera takes the length proposal (proposal 0)");
   if (op.proposal >= 1) {
     DRT_TRY(build_segments(s, st));
     if (!opts->seg_weights || opts->n_seg_weights != s->seg_n)
@@ -737,6 +746,7 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
 drt_status drt_scene_segments(drt_context* ctx, drt_scene* s, int64_t* n, int32_t* edge_tile, float* s01,
                               double* lens, int64_t cap, void* stream) {
   if (!ctx || !s || !n || cap < 0) return fail(DRT_ERR_INVALID_ARG, "bad argument");
+  if (s->cam_type == DRT_CAMERA_FISHEYE) return fail(DRT_ERR_INVALID_ARG, "no screen segments for the fisheye camera");
   cudaStream_t st = (cudaStream_t)stream;
   DRT_TRY(build_segments(s, st));
   *n = s->seg_n;
@@ -763,6 +773,7 @@ drt_status drt_segment_features(drt_context* ctx, drt_scene* s, const float* d_i
   if (!ctx || !s || !d_image || !x) return fail(DRT_ERR_INVALID_ARG, "NULL argument");
   if (!is_device_ptr(d_image) || !is_device_ptr(x) || (image && !is_device_ptr(image)))
     return fail(DRT_ERR_INVALID_ARG, "device arrays only");
+  if (s->cam_type == DRT_CAMERA_FISHEYE) return fail(DRT_ERR_INVALID_ARG, "no screen segments for the fisheye camera");
   cudaStream_t st = (cudaStream_t)stream;
   DRT_TRY(build_segments(s, st));
   CUDA_TRY(drt::launch_segment_features(s, d_image, image, x, st));

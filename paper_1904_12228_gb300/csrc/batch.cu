@@ -424,6 +424,8 @@ drt_status drt_batch_create(drt_context* ctx, const drt_batch_item* items, int32
     if (!it.scene || !it.image) return bfail(DRT_ERR_INVALID_ARG, "every batch item needs a scene and an image");
     if (it.grads.dimage_dparam || it.grads.n_jac != 0)
       return bfail(DRT_ERR_INVALID_ARG, "a batch writes no per-pixel gradient image");
+    if (it.scene->cam_type == DRT_CAMERA_FISHEYE)
+      return bfail(DRT_ERR_INVALID_ARG, "a batch takes pinhole and orthographic cameras");
     const void* arrays[] = {it.image, it.d_image, it.grads.d_verts, it.grads.d_albedo, it.grads.d_radiance,
                             it.grads.d_cam_to_world, it.grads.d_cam_scale, it.verts};
     for (const void* a : arrays)

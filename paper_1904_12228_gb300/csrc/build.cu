@@ -104,7 +104,25 @@ __global__ void k_edge_tables(SceneView s, float* pedge, double* plen, double* s
   float ax, ay, bx, by, t0, t1;
   double len = 0.0;
   float row[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  if (project(s, a, &ax, &ay) && project(s, b, &bx, &by) &&
+  if (s.cam_type == 2) {
+    // fisheye: edges sampled in 3D, by the chord between the unit directions
+    // from the camera to their end points (FP64, fixed order)
+    double va[3], vb[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      double ti = (double)s.cam[4 * i + 3];
+      va[i] = ds((double)a[i], ti);
+      vb[i] = ds((double)b[i], ti);
+    }
+    double la = __dsqrt_rn(da(da(dm(va[0], va[0]), dm(va[1], va[1])), dm(va[2], va[2])));
+    double lb = __dsqrt_rn(da(da(dm(vb[0], vb[0]), dm(vb[1], vb[1])), dm(vb[2], vb[2])));
+    if (la > 0.0 && lb > 0.0) {
+      double u[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) u[i] = ds(ddv(va[i], la), ddv(vb[i], lb));
+      len = __dsqrt_rn(da(da(dm(u[0], u[0]), dm(u[1], u[1])), dm(u[2], u[2])));
+    }
+  } else if (project(s, a, &ax, &ay) && project(s, b, &bx, &by) &&
       clip_screen(ax, ay, bx, by, (float)s.W, (float)s.H, &t0, &t1)) {
     row[0] = ax; row[1] = ay; row[2] = bx; row[3] = by; row[4] = t0; row[5] = t1;
     double dx = fs(bx, ax), dy = fs(by, ay);

@@ -216,7 +216,40 @@ __device__ __forceinline__ const float* vtx(const SceneView& s, int i) { return 
 // ---------------------------------------------------------------------------
 // FP32 decision path
 // ---------------------------------------------------------------------------
-// Camera ray through screen point (sx, sy), pixel units, y down.
+__device__ __forceinline__ void sincos_2pi(float r, float* c_out, float* s_out);
+
+// atan2(y, x) for y >= 0, in [0, pi], FP32 with one rounding per operation
+// in a fixed order (no library call: the fisheye's screen points are
+// decisions): the ratio of the smaller to the larger magnitude in [0, 1];
+// above tan(pi/12) reduced by atan(a) = pi/6 + atan((sqrt(3) a - 1) / (a +
+// sqrt(3))); the Taylor series of atan about 0 to z^13 (coefficients
+// (-1)^k / (2k + 1)) by Horner's rule; then the octant restored.
+__device__ __forceinline__ float atan2_pos(float y, float x) {
+  float ax = fabsf(x);
+  bool swap = y > ax;
+  float num = swap ? ax : y, den = swap ? y : ax;
+  float a = den > 0.0f ? fdv(num, den) : 0.0f;
+  bool red = a > 0.267949194f;
+  float z = red ? fdv(fs(fm(a, 1.73205078f), 1.0f), fa(a, 1.73205078f)) : a;
+  float z2 = fm(z, z);
+  float p = 0.0769230798f;
+  p = fa(fm(z2, p), -0.0909090936f);
+  p = fa(fm(z2, p), 0.111111112f);
+  p = fa(fm(z2, p), -0.142857149f);
+  p = fa(fm(z2, p), 0.200000003f);
+  p = fa(fm(z2, p), -0.333333343f);
+  float r = fa(z, fm(fm(z, z2), p));
+  if (red) r = fa(0.523598790f, r);
+  if (swap) r = fs(1.57079637f, r);
+  if (x < 0.0f) r = fs(3.14159274f, r);
+  return r;
+}
+
+// Camera ray through screen point (sx, sy), pixel units, y down.  Pinhole
+// and orthographic cameras map lines to lines (Sec. 5.2.1); the equidistant
+// fisheye (Sec. 5.2, non-linear projections) sends the screen point at
+// distance r from the centre, in units of half the image height, along the
+// direction at angle r * cam_scale from the optical axis (-z).
 __device__ __forceinline__ void camera_ray(const SceneView& s, float sx, float sy, float o[3], float d[3]) {
   const float* M = s.cam;
   float S = s.cam_scale[0];
@@ -224,6 +257,21 @@ __device__ __forceinline__ void camera_ray(const SceneView& s, float sx, float s
   float xn = fdv(fs(fm(2.0f, sx), fw), fw);
   float yn = fdv(fs(fh, fm(2.0f, sy)), fh);
   float aspect = fdv(fw, fh);
+  if (s.cam_type == 2) {
+    float a = fm(xn, aspect), b = yn;
+    float r = fsq(fa(fm(a, a), fm(b, b)));
+    float th = fm(r, S);
+    float c, sn;
+    sincos_2pi(fm(th, 0.159154937f), &c, &sn);
+    float k = r > 0.0f ? fdv(sn, r) : 0.0f;
+    float dc0 = fm(a, k), dc1 = fm(b, k), dc2 = -c;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      o[i] = M[4 * i + 3];
+      d[i] = fa(fa(fm(M[4 * i], dc0), fm(M[4 * i + 1], dc1)), fm(M[4 * i + 2], dc2));
+    }
+    return;
+  }
   float sxs = fm(aspect, S);
   float lx = fm(xn, sxs), ly = fm(yn, S);
 #pragma unroll
@@ -237,6 +285,28 @@ __device__ __forceinline__ void camera_ray(const SceneView& s, float sx, float s
       d[i] = -m2;
     }
   }
+}
+
+// Equidistant fisheye projection of a world point (the inverse of
+// camera_ray for cam_type 2); false near the direction opposite the optical
+// axis (theta >= 3.1), which no pixel sees.
+__device__ __forceinline__ bool fisheye_project(const SceneView& s, const float v[3], float* sx, float* sy) {
+  const float* Wm = s.w2c;
+  float vc[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    vc[i] = fa(fa(fa(fm(Wm[4 * i], v[0]), fm(Wm[4 * i + 1], v[1])), fm(Wm[4 * i + 2], v[2])), Wm[4 * i + 3]);
+  float rho = fsq(fa(fm(vc[0], vc[0]), fm(vc[1], vc[1])));
+  float th = atan2_pos(rho, -vc[2]);
+  if (!(th < 3.1f)) return false;
+  float S = s.cam_scale[0];
+  float k = rho > 0.0f ? fdv(th, fm(S, rho)) : 0.0f;
+  float a = fm(k, vc[0]), b = fm(k, vc[1]);
+  float fw = (float)s.W, fh = (float)s.H;
+  float xn = fdv(a, fdv(fw, fh));
+  *sx = fm(fa(xn, 1.0f), fm(0.5f, fw));
+  *sy = fm(fs(1.0f, b), fm(0.5f, fh));
+  return true;
 }
 
 // Screen projection with the FP32 world-to-camera rows; false if behind.

@@ -613,6 +613,26 @@ __device__ __forceinline__ void camera_ray_adjoint(const SceneView& s, float sx,
   float fw = (float)s.W, fh = (float)s.H;
   float xn = (2.0f * sx - fw) / fw, yn = (fh - 2.0f * sy) / fh;
   float aspect = fw / fh;
+  if (s.cam_type == 2) {
+    // fisheye: d = M3 (a/r sin th, b/r sin th, -cos th), th = r S, o = t
+    float a = xn * aspect, b = yn, r = sqrtf(a * a + b * b);
+    float sn, cs;
+    sincosf(r * S, &sn, &cs);
+    float ar = r > 0.f ? a / r : 0.f, br = r > 0.f ? b / r : 0.f;
+    float dc[3] = {ar * sn, br * sn, -cs}, dth[3] = {ar * cs, br * cs, sn};
+    float dov[3] = {do_.x, do_.y, do_.z}, ddv[3] = {dd_.x, dd_.y, dd_.z};
+    float gth = 0.f;
+    for (int i = 0; i < 3; ++i) {
+      float* gm = g + 3 + 4 * i;
+      gm[3] += dov[i];
+      for (int j = 0; j < 3; ++j) {
+        gm[j] += ddv[i] * dc[j];
+        gth += ddv[i] * M[4 * i + j] * dth[j];
+      }
+    }
+    g[15] += gth * r;
+    return;
+  }
   float lx = xn * aspect * S, ly = yn * S;
   float dov[3] = {do_.x, do_.y, do_.z}, ddv[3] = {dd_.x, dd_.y, dd_.z};
   float dlx = 0.f, dly = 0.f;
@@ -676,6 +696,63 @@ __device__ __forceinline__ float3 project_adjoint(const SceneView& s, float3 v, 
     for (int j = 0; j < 3; ++j) gm[j] -= dva[i] * vc[j];
   }
   return dv;
+}
+
+// Fisheye projection of world point v (smooth FP32): given d loss/d(sx, sy),
+// return d loss/dv and accumulate the camera and scale adjoints.  With the
+// camera-space point (x, y, vz), rho = |(x, y)|, theta = atan2(rho, -vz) and
+// k = theta / (S rho): a = k x, b = k y, sx = (a / aspect + 1) W / 2,
+// sy = (1 - b) H / 2.
+__device__ __forceinline__ float3 fisheye_project_adjoint(const SceneView& s, float3 v, float gx, float gy,
+                                                          float g[kGlobals]) {
+  const float* Wm = s.w2c;
+  float vc[3];
+  for (int i = 0; i < 3; ++i) vc[i] = Wm[4 * i] * v.x + Wm[4 * i + 1] * v.y + Wm[4 * i + 2] * v.z + Wm[4 * i + 3];
+  float S = s.cam_scale[0];
+  float x = vc[0], y = vc[1], zz = -vc[2];
+  float rho2 = x * x + y * y, rho = sqrtf(rho2), R2 = rho2 + zz * zz;
+  float th = atan2f(rho, zz);
+  float k = th / (S * rho);
+  float a = k * x, b = k * y;
+  float hh = 0.5f * (float)s.H;
+  float ga = gx * hh, gb = -gy * hh;
+  float gk = ga * x + gb * y;
+  float dthx = zz * x / (rho * R2), dthy = zz * y / (rho * R2), dthz = rho / R2;
+  float dkx = dthx / (S * rho) - th * x / (S * rho * rho2), dky = dthy / (S * rho) - th * y / (S * rho * rho2);
+  float dkz = dthz / (S * rho);
+  float dvc[3] = {ga * k + gk * dkx, gb * k + gk * dky, gk * dkz};
+  g[15] += -(ga * a + gb * b) / S;
+  float3 dv;
+  dv.x = Wm[0] * dvc[0] + Wm[4] * dvc[1] + Wm[8] * dvc[2];
+  dv.y = Wm[1] * dvc[0] + Wm[5] * dvc[1] + Wm[9] * dvc[2];
+  dv.z = Wm[2] * dvc[0] + Wm[6] * dvc[1] + Wm[10] * dvc[2];
+  float dva[3] = {dv.x, dv.y, dv.z};
+  for (int i = 0; i < 3; ++i) {
+    float* gm = g + 3 + 4 * i;
+    gm[3] -= dva[i];
+    for (int j = 0; j < 3; ++j) gm[j] -= dva[i] * vc[j];
+  }
+  return dv;
+}
+// Tangent of the fisheye image of v + t dw with respect to t (smooth FP32).
+__device__ __forceinline__ float2 fisheye_tangent(const SceneView& s, float3 v, float3 dw) {
+  const float* Wm = s.w2c;
+  float vc[3], dc[3];
+  for (int i = 0; i < 3; ++i) {
+    vc[i] = Wm[4 * i] * v.x + Wm[4 * i + 1] * v.y + Wm[4 * i + 2] * v.z + Wm[4 * i + 3];
+    dc[i] = Wm[4 * i] * dw.x + Wm[4 * i + 1] * dw.y + Wm[4 * i + 2] * dw.z;
+  }
+  float S = s.cam_scale[0];
+  float x = vc[0], y = vc[1], zz = -vc[2];
+  float rho2 = x * x + y * y, rho = sqrtf(rho2), R2 = rho2 + zz * zz;
+  float th = atan2f(rho, zz);
+  float k = th / (S * rho);
+  float drho = (x * dc[0] + y * dc[1]) / rho, dzz = -dc[2];
+  float dth = (zz * drho - rho * dzz) / R2;
+  float dk = dth / (S * rho) - th * drho / (S * rho2);
+  float da_ = k * dc[0] + x * dk, db_ = k * dc[1] + y * dk;
+  float hh = 0.5f * (float)s.H;
+  return make_float2(hh * da_, -hh * db_);
 }
 
 // ---------------------------------------------------------------------------
@@ -1234,6 +1311,10 @@ __device__ __forceinline__ bool secondary_side_hits(const SceneView& s, const Op
     if (!(dot3x(gm.n32, dm32) > 0.f)) act[side] = false;
     front[side] = dot3x(mv.nu, dm32) < 0.f;
   }
+  // both sides on one triangle: the edge separates no surfaces at this point,
+  // so the jump of Eq. dirac_3d_edge is zero (the difference of the two
+  // evaluations a finite offset apart would be an O(eps) residue)
+  if (act[0] && act[1] && hms[0].tri == hms[1].tri) act[0] = act[1] = false;
   return act[0] || act[1];
 }
 
@@ -2143,8 +2224,15 @@ struct EdgeSample {
   int e, seg;
   bool valid;
   float ax, ay, bx, by, dx, dy, x, y;
-  double inv_pdf_len;  // 1 / (point density per unit screen length)
+  float t;             // fisheye: parameter of the point along the 3D edge
+  double inv_pdf_len;  // 1 / (point density per unit screen length); fisheye: 1 / P(edge)
 };
+// A point of a 3D edge, v0 + t (v1 - v0), FP32 in a fixed order.
+__device__ __forceinline__ void edge_point3(float3 v0, float3 v1, float t, float p[3]) {
+  p[0] = fa(v0.x, fm(t, fs(v1.x, v0.x)));
+  p[1] = fa(v0.y, fm(t, fs(v1.y, v0.y)));
+  p[2] = fa(v0.z, fm(t, fs(v1.z, v0.z)));
+}
 // Plain sampler: edge by clipped length, uniform point.  Learned proposal:
 // tile segment by the mixture CDF, uniform point on the segment.
 __device__ __forceinline__ EdgeSample primary_sample(const SceneView& s, const Opts& op, int64_t j, double ptotal) {
@@ -2153,6 +2241,34 @@ __device__ __forceinline__ EdgeSample primary_sample(const SceneView& s, const O
   float t0, t1;
   es.valid = true;
   es.seg = -1;
+  es.t = 0.f;
+  if (s.cam_type == 2) {
+    // fisheye (Sec. 5.2, non-linear projections): the edge by its chord on the
+    // unit sphere of directions, t uniform in [0, 1), the point's image x(t)
+    // on the curved edge image; the side offset runs perpendicular to the
+    // FP32 chord of x(t - 1/1024) and x(t + 1/1024) (clamped to the edge)
+    es.e = cdf_pick_guided(s.pcdf, s.E, dm(u01d(r.x, r.y), ptotal), s.pguide, ptotal);
+    double pe = s.pcdf[es.e] - (es.e > 0 ? s.pcdf[es.e - 1] : 0.0);
+    es.inv_pdf_len = pe > 0.0 ? ddv(ptotal, pe) : 0.0;
+    es.ax = es.ay = es.bx = es.by = 0.f;
+    es.t = u01f(r.z);
+    int2 ev = s.edges[es.e];
+    float3 v0 = ld3(s.verts + 3 * ev.x), v1 = ld3(s.verts + 3 * ev.y);
+    float p[3], q0[3], q1[3];
+    edge_point3(v0, v1, es.t, p);
+    float ta = fmaxf(fs(es.t, 0.0009765625f), 0.0f), tb = fminf(fa(es.t, 0.0009765625f), 1.0f);
+    edge_point3(v0, v1, ta, q0);
+    edge_point3(v0, v1, tb, q1);
+    float x0 = 0.f, y0 = 0.f, x1 = 0.f, y1 = 0.f;
+    es.x = es.y = 0.f;
+    bool ok = pe > 0.0 && fisheye_project(s, p, &es.x, &es.y) && fisheye_project(s, q0, &x0, &y0) &&
+              fisheye_project(s, q1, &x1, &y1);
+    ok = ok && es.x >= 0.0f && es.x < (float)s.W && es.y >= 0.0f && es.y < (float)s.H;
+    es.dx = fs(x1, x0);
+    es.dy = fs(y1, y0);
+    es.valid = ok && fsq(fa(fm(es.dx, es.dx), fm(es.dy, es.dy))) > 0.0f;
+    return es;
+  }
   if (s.seg_cdf) {
     double qt = s.seg_cdf[s.n_seg - 1];
     int k = cdf_pick(s.seg_cdf, s.n_seg, dm(u01d(r.x, r.y), qt));
@@ -2315,7 +2431,21 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
       float ax = es.ax, ay = es.ay, bx = es.bx, by = es.by;
       float diff = dot(w, Lme - Lot);
       if (op.seg_log && es.seg >= 0) atomicAdd(op.seg_log + es.seg, fabsf(diff));
-      if (diff != 0.f) {
+      if (diff != 0.f && s.cam_type == 2) {
+        // the curved edge image: alpha = x'_y X - x'_x Y at the sample's
+        // point (-perp(x') . x, perp pointing to the side at +eps)
+        int2 ev = s.edges[e];
+        ia = ev.x; ib = ev.y;
+        float3 v0 = ld3(s.verts + 3 * ia), v1 = ld3(s.verts + 3 * ib);
+        float pt[3];
+        edge_point3(v0, v1, es.t, pt);
+        float2 xt = fisheye_tangent(s, f3(pt), v1 - v0);
+        float c = diff * (float)(es.inv_pdf_len * inv_n);
+        float3 dvp = fisheye_project_adjoint(s, f3(pt), c * xt.y, -c * xt.x, gs);
+        da3 = (1.f - es.t) * dvp;
+        db3 = es.t * dvp;
+        for (int q = 0; q < kGlobals; ++q) g[q] += gs[q];
+      } else if (diff != 0.f) {
         float gl = sqrtf((ax - bx) * (ax - bx) + (ay - by) * (ay - by));
         float c = diff * (float)(es.inv_pdf_len * inv_n) / gl;
         float dax = c * (by - y), day = c * (x - bx), dbx = c * (y - ay), dby = c * (ax - x);
