@@ -1308,6 +1308,16 @@ void jitter(const or_opts_t& op, int pix, int s, int W, float* sx, float* sy) {
   *sy = (float)(pix / W) + u01f(r[1]);
 }
 
+/* Both side points of a primary edge sample see the same triangle first: the
+ * edge bounds nothing visible there, so f is continuous across it and the
+ * sample's term of Eq. mc is zero (the difference of the two evaluations a
+ * finite offset apart would be an O(eps) residue). */
+bool same_first_hit(const Prep& P, float xu, float yu, float xl, float yl) {
+  R32 ru = camera_ray32(*P.sc, xu, yu), rl = camera_ray32(*P.sc, xl, yl);
+  Hit hu = closest(P, ru.o, ru.d, -1), hl = closest(P, rl.o, rl.d, -1);
+  return hu.tri >= 0 && hu.tri == hl.tri;
+}
+
 /* ---- primary edge sample of the fisheye (Sec. 5.2, non-linear projections) --
  * The image of an edge is a curve x(t) = pi(v0 + t (v1 - v0)).  The edge is
  * picked by its chord on the unit sphere of directions (prepare), t
@@ -1352,6 +1362,7 @@ void primary_edge_sample_fisheye(Ctx& C, int64_t jj, const uint32_t r[4]) {
   float xu = x + eps * nx, yu = y + eps * ny, xl = x - eps * nx, yl = y - eps * ny;
   int px = (int)std::floor(x), py = (int)std::floor(y);
   C.pix = (int64_t)py * sc.width + px;
+  if (same_first_hit(P, xu, yu, xl, yl)) return;
   const float* w = C.w + 3 * ((size_t)py * sc.width + px);
   double zero[3] = {0, 0, 0};
   bool saved = C.track;
@@ -1427,6 +1438,7 @@ void primary_edge_sample(Ctx& C, int64_t jj) {
   px = std::min(std::max(px, 0), sc.width - 1);
   py = std::min(std::max(py, 0), sc.height - 1);
   C.pix = (int64_t)py * sc.width + px;  /* the sample belongs to the pixel containing its point */
+  if (same_first_hit(P, xu, yu, xl, yl)) return;
   const float* w = C.w + 3 * ((size_t)py * sc.width + px);
   double zero[3] = {0, 0, 0};
   bool saved = C.track;

@@ -335,13 +335,22 @@ __device__ __forceinline__ float3 aov_value(const Opts& op, const Vertex& x, flo
   return alb;
 }
 
+// L += c * t with one rounding per component, written as an explicit FMA so
+// that every evaluation of a path (in one kernel or in stages) rounds alike
+// whatever the compiler would contract.
+__device__ __forceinline__ void nee_add(float3& L, float c, float3 t) {
+  L.x = __fmaf_rn(c, t.x, L.x);
+  L.y = __fmaf_rn(c, t.y, L.y);
+  L.z = __fmaf_rn(c, t.z, L.z);
+}
+
 // path_value of a camera path (from depth 0, first emission counted) for the
 // 32 lanes of a warp together, traced by the warp-cooperative traversals.
 // All lanes call; a lane with act = false traces nothing, writes no tape and
 // returns 0.  Same values and tape entries as path_value.
 __device__ float3 path_value_warp(const SceneView& s, const Opts& op, const float o_in[3], const float d_in[3],
                                   bool act, uint32_t c0, uint32_t c1, uint32_t pass, int32_t* tape_tri,
-                                  float2* tape_bary, int64_t n_idx, int64_t n_stride) {
+                                  float2* tape_bary, int64_t n_idx, int64_t n_stride, int* first_tri = nullptr) {
   const unsigned full = 0xffffffffu;
   float o[3] = {o_in[0], o_in[1], o_in[2]}, d[3] = {d_in[0], d_in[1], d_in[2]};
   float3 L = zero3(), beta = make_float3(1.f, 1.f, 1.f);
@@ -365,6 +374,7 @@ __device__ float3 path_value_warp(const SceneView& s, const Opts& op, const floa
       h.t = h.b1 = h.b2 = 0.f;
     }
     if (alive && h.tri < 0) alive = false;
+    if (b == 0 && first_tri) *first_tri = alive ? h.tri : -1;
     Vertex x;
     x.k = -1;
     x.p[0] = x.p[1] = x.p[2] = 0.f;
@@ -403,7 +413,7 @@ __device__ float3 path_value_warp(const SceneView& s, const Opts& op, const floa
       if (alive && !occ) {
         vis = 1;
         float g = nee_geometry(s, f3(x.p), f3(n32), ls);
-        L += (kInvPi * g) * (beta * alb * Le);
+        nee_add(L, kInvPi * g, beta * alb * Le);
       }
     }
     if (alive) {
@@ -473,7 +483,7 @@ __device__ float3 path_first_vertex_warp(const SceneView& s, const Opts& op, con
     trace_any2_warp(s, x.p, sd, x.k, ls.lt, x.p, sd, -1, -1, alive, false, kShadowTmax, occ, occ_unused);
     if (alive && !occ) {
       float g = nee_geometry(s, f3(x.p), f3(n32), ls);
-      L += (kInvPi * g) * (alb * Le);
+      nee_add(L, kInvPi * g, alb * Le);
     }
   }
   if (alive && md > 1) {
@@ -531,7 +541,7 @@ __device__ void path_value2_from(const SceneView& s, const Opts& op, const float
       for (int q = 0; q < 2; ++q)
         if (alive[q] && !occ[q]) {
           float g = nee_geometry(s, f3(x[q].p), f3(n32[q]), ls);
-          L[q] += (kInvPi * g) * (beta[q] * alb[q] * Le);
+          nee_add(L[q], kInvPi * g, beta[q] * alb[q] * Le);
         }
     }
     if (b + 1 >= md) break;
@@ -2102,10 +2112,11 @@ __global__ void __launch_bounds__(kBlock, DRT_BOUNCE_MIN_BLOCKS) k_path_bounce(B
           for (int k = 0; k < 2; ++k)
             if (alive[k] && !occ[k]) {
               float g = nee_geometry(s, f3(x[k].p), f3(n32[k]), ls);
-              float3 add = (kInvPi * g) * (beta[k] * alb[k] * Le);
-              lr[3 * k] += add.x;
-              lr[3 * k + 1] += add.y;
-              lr[3 * k + 2] += add.z;
+              float3 acc = make_float3(lr[3 * k], lr[3 * k + 1], lr[3 * k + 2]);
+              nee_add(acc, kInvPi * g, beta[k] * alb[k] * Le);
+              lr[3 * k] = acc.x;
+              lr[3 * k + 1] = acc.y;
+              lr[3 * k + 2] = acc.z;
             }
         }
         if (bb + 1 < md) {
@@ -2380,15 +2391,26 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
     }
     float3 Lme, Lot;
     if (kStage == kPrimFused) {
-      Lme = path_value_warp(s, op, o, d, active, (uint32_t)j, 0u, kPassPrimaryEdge, nullptr, nullptr, 0, 0);
+      int ftri = -1;
+      Lme = path_value_warp(s, op, o, d, active, (uint32_t)j, 0u, kPassPrimaryEdge, nullptr, nullptr, 0, 0, &ftri);
       Lot = make_float3(__shfl_xor_sync(kFull, Lme.x, 1), __shfl_xor_sync(kFull, Lme.y, 1),
                         __shfl_xor_sync(kFull, Lme.z, 1));
+      // both sides see the same triangle first: the edge bounds nothing
+      // visible there and the sample's term is zero
+      int ftri_other = __shfl_xor_sync(kFull, ftri, 1);
+      if (ftri >= 0 && ftri == ftri_other) Lme = Lot = zero3();
     } else if (kStage == kPrimFirst) {
       bool cont;
       Hit h0;
       float nd[3];
       float3 alb;
       float3 L0 = path_first_vertex_warp(s, op, o, d, active, (uint32_t)j, 0u, kPassPrimaryEdge, cont, h0, nd, alb);
+      // both sides see the same triangle first: the sample's term is zero
+      // and its paths need not go on
+      int ftri = active ? h0.tri : -1;
+      int ftri_other = __shfl_xor_sync(kFull, ftri, 1);
+      bool same = ftri >= 0 && ftri == ftri_other;
+      if (same) L0 = zero3();
       if (active) {
         float* lr = ps.lr + 6 * i + 3 * side;
         lr[0] = L0.x;
@@ -2397,7 +2419,7 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
       }
       // the pair's two continuation rays become one pending entry of the
       // path stages, pushed by the even lane
-      cont = cont && active;
+      cont = cont && active && !same;
       bool cont1 = __shfl_xor_sync(kFull, cont, 1);
       int tri1 = __shfl_xor_sync(kFull, h0.tri, 1);
       float b11 = __shfl_xor_sync(kFull, h0.b1, 1), b21 = __shfl_xor_sync(kFull, h0.b2, 1);
@@ -2429,7 +2451,10 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
     if (active) {
       int e = es.e;
       float ax = es.ax, ay = es.ay, bx = es.bx, by = es.by;
-      float diff = dot(w, Lme - Lot);
+      // w . (Lme - Lot) with every rounding written out: the fused and the
+      // staged kernels must form the same value from the same radiance
+      float diff = __fmaf_rn(w.z, __fsub_rn(Lme.z, Lot.z),
+                             __fmaf_rn(w.y, __fsub_rn(Lme.y, Lot.y), __fmul_rn(w.x, __fsub_rn(Lme.x, Lot.x))));
       if (op.seg_log && es.seg >= 0) atomicAdd(op.seg_log + es.seg, fabsf(diff));
       if (diff != 0.f && s.cam_type == 2) {
         // the curved edge image: alpha = x'_y X - x'_x Y at the sample's
