@@ -77,3 +77,19 @@ def test_translation_is_recovered(cuda):
         loss.backward()
         opt.step()
     assert theta.detach().abs().max().item() < 0.03, theta
+
+
+def test_object_translations_are_recovered(cuda):
+    """The same reduced protocol with one translation per object instead of
+    free vertices (start = N(0, 0.05) per axis), the residual from an
+    independent render and a cosine learning-rate decay: the vertex error
+    falls (0.091 -> 0.051 when measured).  The image loss is no measure here:
+    at 8 spp it is mostly Monte Carlo noise (the loss at the true positions
+    is as large as at the start)."""
+    from paper_1904_12228_gb300 import inverse
+    scene = sg.procedural(1237, n_target=20_000, width=128, height=128)
+    hist = inverse.run(scene, steps=80, spp=8, max_depth=2, target_spp=64, lr=5e-3, lr_final=5e-4, objects=True,
+                       decorrelate=True)
+    assert all(np.isfinite(h["loss"]) for h in hist)
+    assert hist[-1]["vertex_rms_error"] < 0.7 * hist[0]["vertex_rms_error"], \
+        (hist[0]["vertex_rms_error"], hist[-1]["vertex_rms_error"])
