@@ -50,7 +50,7 @@ class _Opts(ctypes.Structure):
                 ("scene_id", ctypes.c_int32), ("proposal", ctypes.c_int32), ("seg_weights", ctypes.c_void_p),
                 ("n_seg_weights", ctypes.c_int64), ("sec_sampler", ctypes.c_int32), ("sec_tree_samples", ctypes.c_int32),
                 ("sec_point", ctypes.c_int32), ("n_jac", ctypes.c_int32), ("jac_param", ctypes.c_int64 * 8),
-                ("aov", ctypes.c_int32)]
+                ("aov", ctypes.c_int32), ("sec_nee", ctypes.c_int32), ("nee_width", ctypes.c_float)]
 
 
 def lib():
@@ -127,7 +127,7 @@ def backward(scene, d_image: np.ndarray, *, spp: int, edge_spp: int, seed: int, 
              primary_only: bool = False, terms: int = TERMS_ALL, eps_rel: float = EPS_REL, pixels=None,
              edges=None, n_threads=None, scene_id: int = 0, proposal_weights=None, proposal_scores=None,
              sec_tree_samples: int = 0, sec_point: int = 0, contributions: bool = False, jacobian=None,
-             aov: int = 0):
+             aov: int = 0, sec_nee: int = 0, nee_width: float = 0.0):
     """Gradient of sum(d_image * image) as a flat FP64 vector, and per entry
     the magnitude of the terms summed into it (absolute-value chain rule),
     which scales the rounding error an FP32 implementation may make.
@@ -142,7 +142,13 @@ def backward(scene, d_image: np.ndarray, *, spp: int, edge_spp: int, seed: int, 
     magnitude of each sample's whole contribution, sum_k |c_k| (a third
     array).  jacobian: up to 8 flat parameter indices; then the per-pixel
     shares of those gradient entries, [n, H, W], are returned last.  aov > 0:
-    the gradient of a geometry buffer of the first hit (see render)."""
+    the gradient of a geometry buffer of the first hit (see render).
+    sec_nee = 1 adds next-event estimation for edges (Sec. 5.3.3): at every
+    shading vertex one more secondary edge sample from the billboards its
+    shadow ray crosses, both samples weighed by the balance heuristic (with
+    the length sampler and the uniform point only); nee_width is the
+    billboards' width (<= 0: 2 % of the vertices' mean absolute deviation
+    per coordinate, combined in L2)."""
     if proposal_weights is not None and proposal_scores is not None:
         raise ValueError("give proposal_weights or proposal_scores, not both")
     P = _Pinned(scene)
@@ -153,6 +159,8 @@ def backward(scene, d_image: np.ndarray, *, spp: int, edge_spp: int, seed: int, 
     pw = None if pw is None else np.ascontiguousarray(pw, np.float32)
     o = _opts(spp, edge_spp, max_depth, primary_only, seed, eps_rel, terms, pixels, edges, n_threads, scene_id,
               pw, mode, sec_tree_samples, sec_point, aov)
+    o.sec_nee = int(sec_nee)
+    o.nee_width = float(nee_width)
     n = num_params(scene)
     g = np.zeros(n, np.float64)
     a = np.zeros(n, np.float64)
@@ -186,6 +194,97 @@ def edge_point(p, n, v0, v1, u: float, usel: float):
     lib().or_edge_point(*[a.ctypes.data_as(ctypes.c_void_p) for a in arrs], ctypes.c_float(u), ctypes.c_float(usel),
                         ctypes.byref(t), ctypes.byref(q))
     return float(t.value), float(q.value)
+
+
+def ln32(x: float) -> float:
+    """The FP32 natural logarithm of next-event estimation for edges' race."""
+    f = lib().or_ln32
+    f.restype = ctypes.c_float
+    return float(f(ctypes.c_float(x)))
+
+
+def nee_half_width(scene) -> float:
+    """Half the billboard width derived from the scene's vertices."""
+    P = _Pinned(scene)
+    f = lib().or_nee_half_width
+    f.restype = ctypes.c_float
+    return float(f(ctypes.byref(P.s)))
+
+
+class NeeQuery:
+    """Next-event estimation for edges (Sec. 5.3.3) on one scene: billboard
+    crossings of a ray, the race's pick, the ray of an edge's family through
+    (t, u), its Jacobian and the sampler's density."""
+
+    def __init__(self, scene):
+        self._pin = _Pinned(scene)
+        L = lib()
+        L.or_nee_open.restype = ctypes.c_void_p
+        L.or_nee_jacobian.restype = ctypes.c_double
+        self._h = ctypes.c_void_p(L.or_nee_open(ctypes.byref(self._pin.s)))
+
+    def close(self):
+        if self._h:
+            lib().or_nee_close(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _f3(a):
+        return np.ascontiguousarray(a, np.float32).reshape(3)
+
+    def crossings(self, p, n, d, smax, hw, cap=4096):
+        """(edge ids, [n, 4] of s, t, u, importance) of the billboards the ray
+        p + s d crosses for s in (0, smax); n: the shading normal at p."""
+        p, n, d = self._f3(p), self._f3(n), self._f3(d)
+        eid = np.zeros(cap, np.int32)
+        stui = np.zeros((cap, 4), np.float32)
+        n = lib().or_nee_crossings(self._h, p.ctypes.data_as(ctypes.c_void_p), n.ctypes.data_as(ctypes.c_void_p),
+                                   d.ctypes.data_as(ctypes.c_void_p),
+                                   ctypes.c_float(smax), ctypes.c_float(hw), eid.ctypes.data_as(ctypes.c_void_p),
+                                   stui.ctypes.data_as(ctypes.c_void_p), cap)
+        n = min(n, cap)
+        return eid[:n].copy(), stui[:n].copy()
+
+    def pick(self, p, n, d, smax, hw, key0, key1) -> int:
+        p, n, d = self._f3(p), self._f3(n), self._f3(d)
+        return int(lib().or_nee_pick(self._h, p.ctypes.data_as(ctypes.c_void_p), n.ctypes.data_as(ctypes.c_void_p),
+                                     d.ctypes.data_as(ctypes.c_void_p),
+                                     ctypes.c_float(smax), ctypes.c_float(hw), ctypes.c_uint32(key0),
+                                     ctypes.c_uint32(key1)))
+
+    def ray(self, eid, p, t, u):
+        p = self._f3(p)
+        d = np.zeros(3, np.float32)
+        ok = lib().or_nee_ray(self._h, int(eid), p.ctypes.data_as(ctypes.c_void_p), ctypes.c_float(t),
+                              ctypes.c_float(u), d.ctypes.data_as(ctypes.c_void_p))
+        return d if ok else None
+
+    def jacobian(self, eid, p, t, u) -> float:
+        p = self._f3(p)
+        return float(lib().or_nee_jacobian(self._h, int(eid), p.ctypes.data_as(ctypes.c_void_p), ctypes.c_float(t),
+                                           ctypes.c_float(u)))
+
+    def density(self, p, n, d, eid, t, u, hw) -> np.ndarray:
+        """p_B at samples: p [n,3], normals n [n,3], d [n,3], eid [n], t [n], u [n]."""
+        p = np.ascontiguousarray(p, np.float32).reshape(-1, 3)
+        nrm = np.ascontiguousarray(n, np.float32).reshape(-1, 3)
+        d = np.ascontiguousarray(d, np.float32).reshape(-1, 3)
+        eid = np.ascontiguousarray(eid, np.int32).reshape(-1)
+        t = np.ascontiguousarray(t, np.float32).reshape(-1)
+        u = np.ascontiguousarray(u, np.float32).reshape(-1)
+        out = np.zeros(len(eid), np.float64)
+        lib().or_nee_density(self._h, len(eid), p.ctypes.data_as(ctypes.c_void_p),
+                             nrm.ctypes.data_as(ctypes.c_void_p), d.ctypes.data_as(ctypes.c_void_p),
+                             eid.ctypes.data_as(ctypes.c_void_p), t.ctypes.data_as(ctypes.c_void_p),
+                             u.ctypes.data_as(ctypes.c_void_p), ctypes.c_float(hw),
+                             out.ctypes.data_as(ctypes.c_void_p))
+        return out
 
 
 def philox(ctr, key) -> np.ndarray:

@@ -1,6 +1,6 @@
 """Build step for the CPU oracle (test infrastructure only).
 
-Compiles ``oracle.cpp`` (which includes ``edge_tree.h``) into ``oracle/_build/liboracle.so`` with
+Compiles ``oracle.cpp`` (which includes ``edge_tree.h`` and ``nee_edge.h``) into ``oracle/_build/liboracle.so`` with
 ``-ffp-contract=off`` so every FP32 operation on the decision path is one
 IEEE rounding, as the oracle's header requires.
 """
@@ -9,7 +9,7 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "oracle.cpp")
-DEPS = [SRC, os.path.join(HERE, "edge_tree.h")]
+DEPS = [SRC, os.path.join(HERE, "edge_tree.h"), os.path.join(HERE, "nee_edge.h")]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
 

@@ -65,7 +65,7 @@ void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]
 
 /* Stream kinds and passes of the counter layout. */
 enum { K_CAMERA = 0, K_LIGHT = 1, K_BSDF = 2, K_EDGE_PRIMARY = 3, K_EDGE_SECONDARY = 4 };
-enum { PASS_INTERIOR = 0, PASS_PRIMARY_EDGE = 1, PASS_SECONDARY_BASE = 2 };
+enum { PASS_INTERIOR = 0, PASS_PRIMARY_EDGE = 1, PASS_SECONDARY_BASE = 2, PASS_NEE_BASE = 18 };
 
 void rng(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t kind, uint32_t bounce, uint32_t pass,
          uint32_t scene, uint32_t out[4]) {
@@ -243,6 +243,8 @@ typedef struct {
   int32_t aov;               /* with primary_only: 0, 1 albedo; 2 world position; 3 unit shading normal
                                 (facing the ray); 4 distance from the ray origin (Sec. 5.4, geometry
                                 buffers) */
+  int32_t sec_nee;           /* 1: next-event estimation for edges (Sec. 5.3.3) beside the length sampler */
+  float nee_width;           /* billboard width; <= 0: from the vertices' mean absolute deviation */
 } or_opts_t;
 }
 
@@ -854,6 +856,7 @@ D3 hit_point_dual(const D3& O, const D3& D, const D3& V0, const D3& V1, const D3
 }
 
 #include "edge_tree.h"
+#include "nee_edge.h"
 
 struct Ctx {
   const Prep* P;
@@ -866,6 +869,8 @@ struct Ctx {
   double* gc = nullptr;  /* sum over accumulate calls of |coef x'| per parameter [P] (or null) */
   double* jac = nullptr; /* [n_jac, H, W] per-pixel share of the gradient (or null) */
   int64_t pix = 0;       /* pixel the current sample's contributions belong to */
+  float nee_hw = 0.0f;   /* billboard half width of next-event estimation for edges (0: off) */
+  const std::vector<int>* leaf_of_edge = nullptr;  /* edge id -> position in tree->leaf */
 };
 
 /* grad += coef * x';  tolerance scale += coef_abs * |x|' (see Dual).  Each
@@ -1016,6 +1021,10 @@ void path_radiance(Ctx& C, int depth0, int max_depth, const float o32_in[3], con
                    const D3& O_in, const D3& D_in, int exclude_in, bool emission_first, uint32_t c0, uint32_t c1,
                    uint32_t pass, const double wscale[3], const double beta_in[3], bool backward, RGB* out);
 
+void secondary_edge_eval(Ctx& C, int b, uint32_t c0, uint32_t c1, const float p32[3], const D3& Pd, V3 ns,
+                         const float ns32[3], int k, const double albedo_k[3], const double beta[3],
+                         const double wscale[3], int max_depth, int e, float t, double inv_pe,
+                         uint32_t cont_pass);
 void secondary_edge(Ctx& C, int b, uint32_t c0, uint32_t c1, uint32_t pass, const float p32[3], const D3& Pd,
                     V3 ns, const float ns32[3], int k, const double albedo_k[3], const double beta[3],
                     const double wscale[3], int max_depth) {
@@ -1045,6 +1054,64 @@ void secondary_edge(Ctx& C, int b, uint32_t c0, uint32_t c1, uint32_t pass, cons
     t = ep.t;
     inv_pe = inv_pe / ep.q;
   }
+  if (!(C.nee_hw > 0.0f)) {
+    secondary_edge_eval(C, b, c0, c1, p32, Pd, ns, ns32, k, albedo_k, beta, wscale, max_depth, e, t, inv_pe,
+                        PASS_SECONDARY_BASE + (uint32_t)b);
+    return;
+  }
+  /* next-event estimation for edges (Sec. 5.3.3): the sample above and one
+   * billboard sample, each weighed by the balance heuristic */
+  const EdgeTree& T = *C.tree;
+  const float hw = C.nee_hw;
+  uint32_t rn[4];
+  rng(C.opt->seed, c0, c1, K_EDGE_NEE, (uint32_t)b, pass, (uint32_t)C.opt->scene_id, rn);
+  {
+    float uA = hw * (2.0f * u01f(rn[0]) - 1.0f);
+    int leaf = (*C.leaf_of_edge)[e];
+    float d[3];
+    double pB = 0.0;
+    if (nee_ray(T.leaf[leaf], p32, t, uA, d)) pB = nee_density(P, T, p32, ns32, d, leaf, t, uA, hw);
+    double pA = 1.0 / inv_pe;
+    secondary_edge_eval(C, b, c0, c1, p32, Pd, ns, ns32, k, albedo_k, beta, wscale, max_depth, e, t,
+                        1.0 / (pA + (2.0 * (double)hw) * pB), PASS_SECONDARY_BASE + (uint32_t)b);
+  }
+  if (!(P.light_total > 0.0)) return;
+  /* the shadow ray of this vertex's next-event estimation, drawn again */
+  uint32_t rl[4];
+  rng(C.opt->seed, c0, c1, K_LIGHT, (uint32_t)b, pass, (uint32_t)C.opt->scene_id, rl);
+  int j = cdf_pick(P.light_cdf, u01d(rl[0], rl[1]) * P.light_total);
+  float y32[3], by[3];
+  D3 Yunused;
+  light_point(P, j, u01f(rl[2]), u01f(rl[3]), false, y32, &Yunused, by);
+  float d[3] = {y32[0] - p32[0], y32[1] - p32[1], y32[2] - p32[2]};
+  int lt = P.sc->light_tris[j];
+  float Tj, tb1, tb2;
+  if (!watertight(make_shear(d), p32, vtx(P, P.sc->tris[3 * lt]), vtx(P, P.sc->tris[3 * lt + 1]),
+                  vtx(P, P.sc->tris[3 * lt + 2]), INFINITY, &Tj, &tb1, &tb2))
+    return;
+  std::vector<NeeCross> xs;
+  nee_crossings(T, p32, ns32, d, Tj, hw, xs);
+  int w = nee_race(T, xs, rn[2], rn[3]);
+  if (w < 0) return;
+  const NeeCross& x = xs[w];
+  int eB = T.leaf[x.leaf].eid;
+  double pB = nee_density(P, T, p32, ns32, d, x.leaf, x.t, x.u, hw);
+  double le = P.scdf[eB] - (eB > 0 ? P.scdf[eB - 1] : 0.0);
+  double pA = le / P.stotal;
+  double den = pA + (2.0 * (double)hw) * pB;
+  if (!(den > 0.0)) return;
+  secondary_edge_eval(C, b, c0, c1, p32, Pd, ns, ns32, k, albedo_k, beta, wscale, max_depth, eB, x.t, 1.0 / den,
+                      PASS_NEE_BASE + (uint32_t)b);
+}
+
+/* One secondary edge sample at edge e, parameter t, weighed by inv_pe (one
+ * over its density); cont_pass: the pass of the side paths' continuation. */
+void secondary_edge_eval(Ctx& C, int b, uint32_t c0, uint32_t c1, const float p32[3], const D3& Pd, V3 ns,
+                         const float ns32[3], int k, const double albedo_k[3], const double beta[3],
+                         const double wscale[3], int max_depth, int e, float t, double inv_pe,
+                         uint32_t cont_pass) {
+  const Prep& P = *C.P;
+  const float *v0 = vtx(P, P.e0[e]), *v1 = vtx(P, P.e1[e]);
   float om[3], a0[3], a1[3];
   for (int i = 0; i < 3; ++i) {
     float ei = v1[i] - v0[i];
@@ -1156,8 +1223,7 @@ void secondary_edge(Ctx& C, int b, uint32_t c0, uint32_t c1, uint32_t pass, cons
       RGB Lr;
       bool saved = C.track;
       C.track = false;
-      path_radiance(C, b + 1, max_depth, p32, ds, Oc, Dc, k, false, c0, c1, PASS_SECONDARY_BASE + (uint32_t)b,
-                    zero, one, false, &Lr);
+      path_radiance(C, b + 1, max_depth, p32, ds, Oc, Dc, k, false, c0, c1, cont_pass, zero, one, false, &Lr);
       C.track = saved;
       double hs = 0.0, hs_abs = 0.0;
       for (int c = 0; c < 3; ++c) {
@@ -1689,12 +1755,18 @@ int or_backward4(const or_scene_t* sc, const or_opts_t* op, const float* d_image
   g_dual_overflow = false;
   int npix = sc->width * sc->height;
   EdgeTree tree;
-  if (op->sec_sampler == 1) build_edge_tree(P, tree);
+  if (op->sec_nee && (op->sec_sampler != 0 || op->sec_point != 0)) return 3;  /* length sampler, uniform point */
+  if (op->sec_sampler == 1 || op->sec_nee) build_edge_tree(P, tree);
+  std::vector<int> leaf_of_edge(tree.leaf.size(), -1);
+  for (int q = 0; q < (int)tree.leaf.size(); ++q) leaf_of_edge[tree.leaf[q].eid] = q;
+  float nee_hw = !op->sec_nee ? 0.0f : (op->nee_width > 0.0f ? 0.5f * op->nee_width : nee_half_width(*sc));
   if (op->terms & 5) {
     int pb = op->pix_begin, pe = op->pix_end > 0 ? op->pix_end : npix;
     parallel_for(pb, pe, nt, [&](int tid, int64_t b, int64_t e) {
       Ctx C{&P, op, true, d_image, g[tid].data(), ga[tid].data(), &tree, contrib_abs ? gc[tid].data() : nullptr,
             n_jac > 0 ? gj[tid].data() : nullptr};
+      C.nee_hw = nee_hw;
+      C.leaf_of_edge = &leaf_of_edge;
       for (int64_t pix = b; pix < e; ++pix) {
         C.pix = pix;
         const float* w = d_image + 3 * pix;
@@ -1746,6 +1818,64 @@ int or_backward3(const or_scene_t* sc, const or_opts_t* op, const float* d_image
 }
 int or_backward(const or_scene_t* sc, const or_opts_t* op, const float* d_image, double* grad, double* abs_grad) {
   return or_backward4(sc, op, d_image, grad, abs_grad, nullptr, nullptr);
+}
+
+/* ---- next-event estimation for edges: pieces for the CPU pins ---------- */
+float or_ln32(float x) { return ln32(x); }
+float or_nee_half_width(const or_scene_t* sc) { return nee_half_width(*sc); }
+
+/* Builds the scene's edge tree once and answers batches of queries. */
+struct OrNee {
+  Prep P;
+  EdgeTree T;
+  std::vector<int> leaf_of_edge;
+};
+void* or_nee_open(const or_scene_t* sc) {
+  OrNee* q = new OrNee;
+  prepare(sc, q->P);
+  build_edge_tree(q->P, q->T);
+  q->leaf_of_edge.assign(q->T.leaf.size(), -1);
+  for (int k = 0; k < (int)q->T.leaf.size(); ++k) q->leaf_of_edge[q->T.leaf[k].eid] = k;
+  return q;
+}
+void or_nee_close(void* h) { delete (OrNee*)h; }
+/* Crossings of the ray p + s d, s in (0, smax): up to cap of (eid, s, t, u, imp);
+ * returns their number. */
+int or_nee_crossings(void* h, const float* p, const float* n, const float* d, float smax, float hw, int32_t* eid,
+                     float* stui, int cap) {
+  OrNee* q = (OrNee*)h;
+  std::vector<NeeCross> xs;
+  nee_crossings(q->T, p, n, d, smax, hw, xs);
+  for (int i = 0; i < (int)xs.size() && i < cap; ++i) {
+    eid[i] = q->T.leaf[xs[i].leaf].eid;
+    stui[4 * i] = xs[i].s; stui[4 * i + 1] = xs[i].t; stui[4 * i + 2] = xs[i].u; stui[4 * i + 3] = xs[i].imp;
+  }
+  return (int)xs.size();
+}
+/* The race's pick among the crossings before smax: edge id or -1. */
+int or_nee_pick(void* h, const float* p, const float* n, const float* d, float smax, float hw, uint32_t key0,
+                uint32_t key1) {
+  OrNee* q = (OrNee*)h;
+  std::vector<NeeCross> xs;
+  nee_crossings(q->T, p, n, d, smax, hw, xs);
+  int w = nee_race(q->T, xs, key0, key1);
+  return w < 0 ? -1 : q->T.leaf[xs[w].leaf].eid;
+}
+/* The ray of edge eid's family through (t, u): 1 and d, or 0. */
+int or_nee_ray(void* h, int eid, const float* p, float t, float u, float* d) {
+  OrNee* q = (OrNee*)h;
+  return nee_ray(q->T.leaf[q->leaf_of_edge[eid]], p, t, u, d) ? 1 : 0;
+}
+double or_nee_jacobian(void* h, int eid, const float* p, float t, float u) {
+  OrNee* q = (OrNee*)h;
+  return nee_jacobian(q->T.leaf[q->leaf_of_edge[eid]], p, t, u);
+}
+/* p_B at n samples (eid, t, u) with their rays d. */
+void or_nee_density(void* h, int n, const float* p, const float* nrm, const float* d, const int32_t* eid,
+                    const float* t, const float* u, float hw, double* out) {
+  OrNee* q = (OrNee*)h;
+  for (int i = 0; i < n; ++i)
+    out[i] = nee_density(q->P, q->T, p + 3 * i, nrm + 3 * i, d + 3 * i, q->leaf_of_edge[eid[i]], t[i], u[i], hw);
 }
 
 /* Self-check of the two secondary-edge measures at one edge point: for a
