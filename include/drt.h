@@ -165,6 +165,24 @@ typedef struct {
                                    interior derivative of the buffer and the primary edge term of
                                    its discontinuities, so a deferred shading of the buffers written
                                    by the caller differentiates end to end */
+  int32_t sec_nee;              /* 1: next-event estimation for edges (Sec. 5.3.3) beside the length
+                                   sampler.  At every shading vertex the shadow ray of next-event
+                                   estimation is drawn again; the edges whose billboards (width
+                                   nee_width, facing the ray: the two lines pass within half the
+                                   width, at an edge parameter in [0, 1], before the light point)
+                                   it crosses race for one more secondary sample (key -ln U /
+                                   importance; importance length / distance, zero off the silhouette
+                                   seen from the vertex, at or below its tangent plane, or within
+                                   the width of the vertex).  Both
+                                   samples are weighed by the balance heuristic 1 / (p_length +
+                                   width p_billboard) over an auxiliary offset, which keeps the term
+                                   unbiased.  Needs sec_sampler 0 and sec_point 0
+                                   (DRT_ERR_INVALID_ARG otherwise); builds the edge hierarchy for
+                                   its crossing queries; doubles the secondary scratch.  The batch
+                                   and the allocation-free backward take 0 only. */
+  float nee_width;              /* sec_nee: billboard width; <= 0 selects the L2 norm over the
+                                   three coordinates of 2 % of the vertices' mean absolute
+                                   deviation, computed on the backward call's stream */
 } drt_render_opts;
 
 /* Gradient outputs: device or host arrays, each may be NULL (not wanted).
@@ -252,6 +270,8 @@ drt_status drt_tape_free(drt_context* ctx, drt_tape* tape);
  *   - Only the length proposal for primary edges: opts->proposal != 0 is
  *     DRT_ERR_INVALID_ARG (the mixture proposals build their CDF in
  *     scene-owned buffers that grow on demand).
+ *   - No next-event estimation for edges: opts->sec_nee != 0 is
+ *     DRT_ERR_INVALID_ARG (its samples are queued in scene-owned scratch).
  *   - With the edge hierarchy (sec_sampler 1) the hierarchy's buffers must
  *     exist from an earlier drt_render_backward with it on this scene, else
  *     DRT_ERR_STATE; a scene changed since is rebuilt in place.

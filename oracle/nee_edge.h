@@ -23,8 +23,9 @@
  *    crossing test uses w/2).
  *  - Importance of a crossed edge: length / distance from p to the crossing's
  *    point on the edge, zero unless the edge is a silhouette seen from p and
- *    that point lies above p's tangent plane (the factors of Sec. 5.3.1 that
- *    differ between billboards along one ray).  The pick is an exponential race: each crossed edge draws a key
+ *    that point lies above p's tangent plane and farther from p than the
+ *    width w (the factors of Sec. 5.3.1 that differ between billboards along
+ *    one ray).  The pick is an exponential race: each crossed edge draws a key
  *    -ln(U_e) / importance_e and the smallest key wins (ties to the lower
  *    edge id), which picks e with probability importance_e / sum over the
  *    crossed edges, whatever order the edges are visited in.  U_e comes from
@@ -114,9 +115,11 @@ struct NeeCross {
 /* Crossing of the billboard of leaf L by the ray p + s d, s in (0, smax), with
  * half width hw (FP32, fixed order); n: the shading normal at p.  The
  * importance is zero unless the edge is a silhouette seen from p and the
- * crossing's point on the edge lies strictly above p's tangent plane (edges
- * in or below that plane, such as those of p's own triangle, are left to the
- * plain sampler).  The closest points of the two lines:
+ * crossing's point on the edge lies strictly above p's tangent plane and
+ * farther from p than the billboard's width (edges in or below that plane,
+ * such as those of p's own triangle, and edges of p's immediate surroundings
+ * are left to the plain sampler: a shadow ray crosses their billboards at its
+ * very start, where they bound no light).  The closest points of the two lines:
  * with r = v0 - p, E = v1 - v0 and c = d x E,
  *   s = ((r x E) . c) / |c|^2,  t = ((r x d) . c) / |c|^2,  u = (c . r) / |c|. */
 bool nee_cross(const ETLeaf& L, const float p[3], const float n[3], const float d[3], float smax, float hw,
@@ -142,7 +145,7 @@ bool nee_cross(const ETLeaf& L, const float p[3], const float n[3], const float 
     float dm[3];
     for (int i = 0; i < 3; ++i) dm[i] = r[i] + t * E[i];
     float dist = std::sqrt(dot32(dm, dm));
-    if (dist > 0.0f && dot32(n, dm) > 0.0f) out->imp = L.len / dist;
+    if (dist > 2.0f * hw && dot32(n, dm) > 0.0f) out->imp = L.len / dist;
   }
   return true;
 }

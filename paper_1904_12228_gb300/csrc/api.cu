@@ -130,7 +130,8 @@ void free_scene_buffers(drt_scene* s) {
                   s->flags, s->child_orig, s->hist, s->hist_tmp, s->bounds, s->partials, s->esort.keys, s->esort.keys2,
                   s->esort.hist, s->esort.hist_tmp, s->esort.vals, s->esort.vals2, s->seg_edge, s->seg_tile,
                   s->seg_count, s->seg_scan_tmp, s->seg_s, s->seg_len, s->seg_a, s->seg_b, s->seg_cdf, s->seg_tmp,
-                  s->sec.dp, s->sec.queue, s->sec.count, s->sec.pick, s->sec.hits, s->sec.lr, s->sec.path[0],
+                  s->sec.dp, s->sec.queue, s->sec.count, s->sec.pick, s->sec.nee, s->nee_hw, s->sec.hits, s->sec.lr,
+                  s->sec.path[0],
                   s->sec.path[1], s->sec.path_count, s->prim.lr, s->prim.path[0], s->prim.path[1], s->prim.count,
                   s->pguide, s->sguide, s->edge_opp,
                   s->et_nodes, s->et_leaf, s->et_keys, s->et_keys2, s->et_hist, s->et_hist_tmp, s->et_vals,
@@ -165,6 +166,15 @@ drt_status make_opts(const drt_render_opts* o, drt::Opts* op) {
   op->sec_sampler = o->sec_sampler;
   op->sec_point = o->sec_point;
   op->sec_samples = o->sec_tree_samples > 0 ? o->sec_tree_samples : drt::kEtDefaultSamples;
+  // next-event estimation for edges: beside the length sampler and the uniform point only
+  if (o->sec_nee < 0 || o->sec_nee > 1) return fail(DRT_ERR_INVALID_ARG, "sec_nee must be 0 or 1");
+  if (o->sec_nee && (o->sec_sampler != 0 || o->sec_point != 0))
+    return fail(DRT_ERR_INVALID_ARG, "sec_nee needs sec_sampler 0 and sec_point 0");
+  if (!(o->nee_width == o->nee_width) || o->nee_width == INFINITY)
+    return fail(DRT_ERR_INVALID_ARG, "nee_width must be finite");
+  op->nee = o->sec_nee;
+  op->nee_hw = o->nee_width > 0.0f ? 0.5f * o->nee_width : 0.0f;
+  op->nee_hw_dev = nullptr;
   // which samples the backward pass evaluates (all by default)
   if (o->pix_begin < 0 || o->edge_begin < 0)
     return fail(DRT_ERR_INVALID_ARG, "pix_begin and edge_begin must be >= 0");
@@ -182,7 +192,7 @@ drt_status make_opts(const drt_render_opts* o, drt::Opts* op) {
 
 // Secondary edge hierarchy for the scene's current state: allocated on first
 // use (unless alloc is false), rebuilt on the stream when the scene changed.
-drt_status ensure_edge_tree(drt_scene* s, bool alloc, cudaStream_t st) {
+drt_status ensure_edge_tree(drt_scene* s, bool alloc, cudaStream_t st, bool spatial) {
   int E = s->E;
   if (E <= 0) return DRT_OK;
   if (!s->et_leaf) {
@@ -212,9 +222,10 @@ drt_status ensure_edge_tree(drt_scene* s, bool alloc, cudaStream_t st) {
       return a;
     }
   }
-  if (s->et_generation == s->generation) return DRT_OK;
-  CUDA_TRY(drt::build_edge_tree(s, st));
+  if (s->et_generation == s->generation && s->et_spatial == spatial) return DRT_OK;
+  CUDA_TRY(drt::build_edge_tree(s, st, spatial));
   s->et_generation = s->generation;
+  s->et_spatial = spatial;
   return DRT_OK;
 }
 
@@ -634,12 +645,29 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
     }
     sort = &s->esort;
   }
-  if (op.sec_sampler == 1 && !op.primary_only && (op.terms & 4) && s->E > 0 && s->L > 0) {
-    drt_status a = ensure_edge_tree(s, true, st);
+  if ((op.sec_sampler == 1 || op.nee) && !op.primary_only && (op.terms & 4) && s->E > 0 && s->L > 0) {
+    drt_status a = ensure_edge_tree(s, true, st, op.nee != 0);
     if (a != DRT_OK) {
       unstage(sg, 7, st);
       return a;
     }
+  }
+  // billboard half width of next-event estimation for edges from the
+  // vertices (one block, fixed-order FP64 sums), when the caller gives none
+  if (op.nee && !(op.nee_hw > 0.0f) && !op.primary_only && (op.terms & 4) && s->E > 0 && s->L > 0) {
+    if (!s->nee_hw) {
+      drt_status a = dalloc_n(&s->nee_hw, 1);
+      if (a != DRT_OK) {
+        unstage(sg, 7, st);
+        return a;
+      }
+    }
+    cudaError_t e = drt::launch_nee_half_width(s->verts, s->V, s->nee_hw, st);
+    if (e != cudaSuccess) {
+      unstage(sg, 7, st);
+      return fail(DRT_ERR_CUDA, "billboard width: %s", cudaGetErrorString(e));
+    }
+    op.nee_hw_dev = s->nee_hw;
   }
   // secondary edge samples that need rays are queued and traced apart
   const drt::SecScratch* secs = nullptr;
@@ -652,6 +680,7 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
       dfree(b.queue);
       dfree(b.count);
       dfree(b.pick);
+      dfree(b.nee);
       dfree(b.hits);
       dfree(b.lr);
       dfree(b.path[0]);
@@ -695,6 +724,18 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
       }
       b.wave_cap = cap;
       b.path_cap = pcap;
+    }
+    if (op.nee && cap > s->sec.nee_cap) {
+      cudaStreamSynchronize(st);
+      dfree(s->sec.nee);
+      s->sec.nee = nullptr;
+      s->sec.nee_cap = 0;
+      drt_status a = dalloc_n(&s->sec.nee, (size_t)cap);
+      if (a != DRT_OK) {
+        unstage(sg, 7, st);
+        return a;
+      }
+      s->sec.nee_cap = cap;
     }
     if (op.sec_sampler == 1 && cap > s->sec.pick_cap) {
       cudaStreamSynchronize(st);

@@ -793,13 +793,14 @@ __global__ void k_etree_light(const float* verts, const int32_t* tris, const int
   *out = make_float4(c[0], c[1], c[2], r);
 }
 
-__global__ void k_etree_keys(SceneView s, const int2* opp, const int* b, uint32_t* keys, int32_t* vals) {
+__global__ void k_etree_keys(SceneView s, const int2* opp, const int* b, uint32_t* keys, int32_t* vals, int spatial) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= s.E) return;
   float O[3], blo[3], bhi[3], R;
   et_frame_of_scene(s, b, O, blo, bhi, &R);
   EtLeafData L;
   et_leaf_data(s.verts, s.edges[e], opp[e], O, L);
+  if (spatial) L.classB = false;  // one 3D hierarchy: compact boxes for segment queries
   keys[e] = et_key(L, blo, bhi, R);
   vals[e] = e;
 }
@@ -1013,7 +1014,7 @@ cudaError_t build_edge_cdfs(drt_scene* s, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t build_edge_tree(drt_scene* s, cudaStream_t st) {
+cudaError_t build_edge_tree(drt_scene* s, cudaStream_t st, bool spatial) {
   int E = s->E;
   if (E <= 0) return cudaSuccess;
   SceneView v = s->view();
@@ -1022,7 +1023,7 @@ cudaError_t build_edge_tree(drt_scene* s, cudaStream_t st) {
                                                                         s->et_leaf + (size_t)kEtLeafF4 * E));
   // the scene box (s->bounds) is the one the triangle LBVH build computed
   DRT_PROF_LAUNCH("etree_keys", st, k_etree_keys<<<(E + kBlock - 1) / kBlock, kBlock, 0, st>>>(
-                                        v, s->edge_opp, s->bounds, s->et_keys, s->et_vals));
+                                        v, s->edge_opp, s->bounds, s->et_keys, s->et_vals, spatial ? 1 : 0));
   bool alt = radix_sort_pairs(s->et_keys, s->et_vals, s->et_keys2, s->et_vals2, s->et_hist, s->et_hist_tmp, E, 31, st);
   uint32_t* ka = alt ? s->et_keys2 : s->et_keys;
   int32_t* va = alt ? s->et_vals2 : s->et_vals;

@@ -56,7 +56,10 @@ __host__ __device__ __forceinline__ int leaf_enc(int first, int count) { return 
 
 
 enum { kCamera = 0, kLight = 1, kBsdf = 2, kEdgePrimary = 3, kEdgeSecondary = 4 };
-enum { kPassInterior = 0, kPassPrimaryEdge = 1, kPassSecondaryBase = 2 };
+// passes of the counter layout: the continuation paths of a secondary sample at
+// vertex b use kPassSecondaryBase + b, those of a billboard sample of next-event
+// estimation for edges kPassNeeBase + b
+enum { kPassInterior = 0, kPassPrimaryEdge = 1, kPassSecondaryBase = 2, kPassNeeBase = 18 };
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11)
@@ -153,6 +156,11 @@ struct Opts {
   int pix_begin, pix_end;
   int64_t edge_begin, edge_end;
   int aov;  // with primary_only: 0, 1 albedo; 2 world position; 3 unit shading normal; 4 distance from the ray origin
+  // next-event estimation for edges (Sec. 5.3.3): billboard half width, given
+  // (nee_hw > 0) or computed on the device into *nee_hw_dev
+  int nee;
+  float nee_hw;
+  const float* nee_hw_dev;
   // per-pixel gradient image of up to 8 parameters (n = 0: none)
   struct {
     float* out;         // [n, H, W]
@@ -195,8 +203,11 @@ struct BatchScene {
   // secondary edge samples that need rays, queued and traced apart
   float* dp_sec;                  // [W*H*spp, depth] adjoint of each path vertex from its secondary sample
   unsigned long long* sec_queue;  // (sample << 3 | vertex) of the queued samples
-  unsigned long long* sec_count;  // number queued per path vertex [8]; vertex b's samples in slots [b n, b n + count)
+  unsigned long long* sec_count;  // number queued per region [16]: region b < depth holds vertex b's samples in slots
+                                  // [b n, b n + count); with next-event estimation for edges region depth + b
+                                  // holds vertex b's billboard samples
   int2* sec_pick;                 // hierarchy sampler: (edge, weight bits) of each queued sample, or null
+  int4* sec_nee;                  // next-event estimation for edges: (edge, weight bits, t bits, 0) per slot, or null
   int64_t sec_cap;                // queue capacity = W*H*spp*depth
   // beyond depth 1, the queued samples in stages (null: one fused kernel)
   int4* sec_hits;                 // [sec_cap, 2] side hits (tri, b1, b2, flags) per queue slot

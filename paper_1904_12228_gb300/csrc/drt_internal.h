@@ -31,9 +31,10 @@ struct NvtxRange {
 };
 
 namespace drt {
-// Counters of the queue of secondary edge samples: one per path vertex (the
-// queue holds one region per vertex; max_depth <= 8).
-constexpr int kSecCounters = 8;
+// Counters of the queue of secondary edge samples: one per region (one region
+// per path vertex, max_depth <= 8, and as many again for the billboard
+// samples of next-event estimation for edges).
+constexpr int kSecCounters = 16;
 // Scratch for the secondary edge samples traced apart: per (sample, vertex)
 // the vertex adjoint, the queue of samples to trace and its length.
 struct SecScratch {
@@ -43,6 +44,8 @@ struct SecScratch {
   int64_t cap = 0;  // (sample, vertex) pairs the buffers hold
   int2* pick = nullptr;  // edge hierarchy: (edge, weight bits) per queued pair
   int64_t pick_cap = 0;
+  int4* nee = nullptr;   // next-event estimation for edges: (edge, weight, t, 0) per queued pair
+  int64_t nee_cap = 0;
   // beyond depth 1: side hits and continuation radiance per queue slot, and
   // two buffers of continuation-path states (5 float4 each)
   int4* hits = nullptr;
@@ -90,6 +93,7 @@ struct drt_scene {
   int32_t *et_vals = nullptr, *et_vals2 = nullptr, *et_parent = nullptr, *et_leaf_parent = nullptr, *et_flags = nullptr;
   int2* et_child = nullptr;
   uint64_t et_generation = ~0ull;
+  bool et_spatial = false;     // built with 3D keys for every edge (next-event estimation for edges)
   float* tile_w = nullptr;     // mean |d_image| per screen tile (features)
   float* pedge = nullptr;
   double *plen = nullptr, *pcdf = nullptr, *slen = nullptr, *scdf = nullptr, *scan_tmp = nullptr;
@@ -114,6 +118,7 @@ struct drt_scene {
   int64_t seg_cap = 0, seg_n = -1;
   uint64_t seg_generation = ~0ull;
   int sort_blocks = 0;
+  float* nee_hw = nullptr;   // billboard half width derived from the vertices (next-event estimation for edges)
   drt::SceneView view() const;
 };
 
@@ -158,8 +163,10 @@ bool radix_sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys2, int32_t* v
                       uint32_t* hist_tmp, int n, int bits, cudaStream_t st);
 size_t radix_hist_entries(int n);
 // Secondary edge hierarchy (Sec. 5.3.1) for the scene's current vertices and
-// camera; the buffers must be allocated.
-cudaError_t build_edge_tree(drt_scene* s, cudaStream_t st);
+// camera; the buffers must be allocated.  spatial: every edge keyed by the 3D
+// Morton code of its centroid (no 6D class), the tree the billboard queries
+// of next-event estimation for edges walk.
+cudaError_t build_edge_tree(drt_scene* s, cudaStream_t st, bool spatial = false);
 cudaError_t scan_exclusive_u32(uint32_t* data, uint32_t* tmp, int n, cudaStream_t st);
 size_t scan_tmp_entries(int n);
 cudaError_t scan_inclusive_f64(const double* in, double* out, double* tmp, int n, cudaStream_t st);
@@ -187,6 +194,8 @@ int64_t secondary_path_capacity(int W, int H, const Opts& op);
 // and *b.sec_count zeroed by the caller)
 cudaError_t launch_secondary_apart(const BatchScene& b, cudaStream_t st);
 int64_t backward_partial_rows(const drt_scene* s, const Opts& op);
+// billboard half width of next-event estimation for edges from the vertices
+cudaError_t launch_nee_half_width(const float* verts, int V, float* out, cudaStream_t st);
 cudaError_t launch_debug_closest(const drt_scene* s, int64_t n, const float* o, const float* d, int32_t* tri,
                                  float* tb, cudaStream_t st);
 // the single-scene launch shapes the batch reproduces

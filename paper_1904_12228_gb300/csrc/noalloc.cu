@@ -70,6 +70,8 @@ drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* s, const drt
   drt_status so = drt::convert_opts(opts, &op);
   if (so != DRT_OK) return so;
   if (opts->proposal != 0) return fail_noalloc(DRT_ERR_INVALID_ARG, "drt_render_backward_noalloc supports proposal 0");
+  if (opts->sec_nee != 0)
+    return fail_noalloc(DRT_ERR_INVALID_ARG, "drt_render_backward_noalloc supports sec_nee 0 (it has no queue)");
   op.proposal = 0;
   op.seg_log = nullptr;
   if (!op.primary_only && op.max_depth > 1 && (op.terms & 5) && !tape) {
@@ -125,10 +127,11 @@ drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* s, const drt
     if (!s->et_leaf) {
       return fail_noalloc(DRT_ERR_STATE, "the edge hierarchy is not allocated: run one drt_render_backward with it first");
     }
-    if (s->et_generation != s->generation) {
-      cudaError_t eb = drt::build_edge_tree(s, (cudaStream_t)stream);
+    if (s->et_generation != s->generation || s->et_spatial) {
+      cudaError_t eb = drt::build_edge_tree(s, (cudaStream_t)stream, false);
       if (eb != cudaSuccess) return fail_noalloc(DRT_ERR_CUDA, cudaGetErrorString(eb));
       s->et_generation = s->generation;
+      s->et_spatial = false;
     }
   }
   cudaError_t e = drt::launch_backward(s, op, tape, d_image, grads->d_verts, grads->d_albedo, grads->d_radiance,

@@ -13,6 +13,7 @@
 
 #include "drt_internal.h"
 #include "edge_tree.cuh"
+#include "nee_edge.cuh"
 
 namespace drt {
 namespace {
@@ -1138,9 +1139,10 @@ struct SecOut {
 };
 // How a secondary edge is selected: by the 3D length CDF, through the edge
 // hierarchy (Sec. 5.3.1), or taken from a hierarchy pick made earlier for the
-// same sample (`pre`).  A template parameter, so kernels of the length sampler
-// carry no call into the hierarchy.
-enum { kSelLength = 0, kSelTree = 1, kSelTreePre = 2 };
+// same sample (`pre`), or a pick of next-event estimation for edges made by
+// the queue (`pre4`: edge, weight, point; Sec. 5.3.3).  A template parameter,
+// so kernels of the length sampler carry no call into the hierarchy.
+enum { kSelLength = 0, kSelTree = 1, kSelTreePre = 2, kSelNeePre = 3 };
 
 // Secondary edge sample at path vertex b (Sec. 5.2.2): the edge (see above),
 // the point on it, the side
@@ -1240,11 +1242,16 @@ static __device__ __noinline__ double edge_point_pdf(const float p[3], const flo
 template <int kSel>
 __device__ __forceinline__ bool secondary_sides(const SceneView& s, const Opts& op, uint32_t c0, uint32_t c1, int b,
                                                 int md, const Vertex& x, float3 n, SecGeom& gm,
-                                                const int2* pre = nullptr) {
+                                                const int2* pre = nullptr, const int4* pre4 = nullptr) {
   uint4 r = rng4(op.key, c0, c1, kEdgeSecondary, (uint32_t)b, kPassInterior, op.scene_id);
   int e;
   float inv_pe;
-  if (kSel == kSelTreePre) {
+  if (kSel == kSelNeePre) {
+    int4 pk = *pre4;
+    e = pk.x;
+    inv_pe = __int_as_float(pk.y);
+    if (e < 0) return false;
+  } else if (kSel == kSelTreePre) {
     int2 pk = *pre;
     e = pk.x;
     inv_pe = __int_as_float(pk.y);
@@ -1262,7 +1269,7 @@ __device__ __forceinline__ bool secondary_sides(const SceneView& s, const Opts& 
     if (!(le > 0.0)) return false;
     inv_pe = (float)(stotal / le);
   }
-  float t = u01f(r.z);
+  float t = kSel == kSelNeePre ? __int_as_float(pre4->z) : u01f(r.z);
   int2 ev = s.edges[e];
   float3 ve0 = ld3(s.verts + 3 * ev.x), ve1 = ld3(s.verts + 3 * ev.y);
   // which sides are traced is a discrete decision: FP32 in a fixed order
@@ -1307,9 +1314,10 @@ __device__ __forceinline__ bool secondary_sides(const SceneView& s, const Opts& 
 template <int kSel>
 __device__ __forceinline__ bool secondary_side_hits(const SceneView& s, const Opts& op, uint32_t c0, uint32_t c1,
                                                     int b, int md, const Vertex& x, float3 n, SecGeom& gm,
-                                                    Hit hms[2], bool front[2], const int2* pre = nullptr) {
+                                                    Hit hms[2], bool front[2], const int2* pre = nullptr,
+                                                    const int4* pre4 = nullptr) {
   front[0] = front[1] = false;
-  if (!secondary_sides<kSel>(s, op, c0, c1, b, md, x, n, gm, pre)) return false;
+  if (!secondary_sides<kSel>(s, op, c0, c1, b, md, x, n, gm, pre, pre4)) return false;
   float (*dsd)[3] = gm.dsd;
   bool* act = gm.act;
   trace_closest2(s, x.p, dsd[0], x.p, dsd[1], act[0], act[1], x.k, x.k, hms[0], hms[1]);
@@ -1422,7 +1430,9 @@ __device__ __forceinline__ void secondary_contrib(const SceneView& s, const Vert
 template <int kSel>
 __device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Opts& op, uint32_t c0, uint32_t c1,
                                                     int b, int md, const Vertex& x, float3 n, float3 alb, float3 ab,
-                                                    float3 Le, float3& dp, SecOut& so, const int2* pre = nullptr) {
+                                                    float3 Le, float3& dp, SecOut& so, const int2* pre = nullptr,
+                                                    const int4* pre4 = nullptr,
+                                                    uint32_t cont_pass = kPassSecondaryBase) {
   so.de0 = so.de1 = zero3();
   so.eid0 = so.eid1 = 0;
   so.have_edge = false;
@@ -1433,10 +1443,11 @@ __device__ __forceinline__ void secondary_at_vertex(const SceneView& s, const Op
   SecGeom gm;
   Hit hms[2];
   bool front[2];
-  if (!secondary_side_hits<kSel>(s, op, c0, c1, b, md, x, n, gm, hms, front, pre)) return;
+  if (!secondary_side_hits<kSel>(s, op, c0, c1, b, md, x, n, gm, hms, front, pre, pre4)) return;
   // radiance along both continuation paths, from the hits found above
+  // (cont_pass: kPassSecondaryBase, or kPassNeeBase for a billboard sample)
   float3 Lr[2] = {zero3(), zero3()};
-  if (!gm.last) path_value2_from(s, op, gm.dsd, hms, gm.act, b + 1, c0, c1, kPassSecondaryBase + (uint32_t)b, Lr);
+  if (!gm.last) path_value2_from(s, op, gm.dsd, hms, gm.act, b + 1, c0, c1, cont_pass + (uint32_t)b, Lr);
   secondary_contrib(s, x, n, alb, ab, Le, gm, hms, front, Lr, dp, so);
 }
 
@@ -1821,6 +1832,158 @@ __global__ void __launch_bounds__(kBlock, kSel == kSelLength ? DRT_QUEUE_MIN_BLO
   }
 }
 
+// Queue of next-event estimation for edges (Sec. 5.3.3), beside the length
+// sampler: per (sample, vertex) the length sample and the billboard sample
+// of the vertex's shadow ray, each with its balance-heuristic weight
+// 1 / (p_length + w p_billboard) and its point, into the regions of their
+// kind (length: vertex b; billboard: depth + b).  The length sample's u is
+// uniform in [-w/2, w/2]; its p_billboard comes from a query along the ray
+// of its family through (t, u).  Same random numbers and arithmetic as the
+// oracle's secondary edge sample with next-event estimation for edges.
+__device__ __forceinline__ void sec_push(const BatchScene& bs, int region, unsigned long long n, bool need,
+                                         unsigned long long item, int4 rec) {
+  int lane = threadIdx.x & 31;
+  unsigned m = __ballot_sync(kFull, need);
+  if (!m) return;
+  int leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(bs.sec_count + region, (unsigned long long)__popc(m));
+  base = __shfl_sync(kFull, base, leader);
+  if (need) {
+    unsigned long long slot = (unsigned long long)region * n + base + __popc(m & ((1u << lane) - 1u));
+    bs.sec_queue[slot] = item;
+    bs.sec_nee[slot] = rec;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock, DRT_TREE_QUEUE_MIN_BLOCKS) k_sec_queue_nee(BatchScene bs) {
+  const SceneView& s = bs.v;
+  const Opts& op = bs.op;
+  int64_t n = (int64_t)s.W * s.H * op.spp;
+  int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  int md = op.primary_only ? 1 : min(op.max_depth, kMaxDepth);
+  bool alive = i < n;
+  int64_t pix = alive ? i / op.spp : 0;
+  int sidx = alive ? (int)(i % op.spp) : 0;
+  alive = alive && pix >= op.pix_begin && pix < op.pix_end;
+  if (alive) {
+    float3 w = ld3(bs.d_image + 3 * pix);
+    alive = w.x != 0.f || w.y != 0.f || w.z != 0.f;
+  }
+  CamHit c;
+  c.k = -1;
+  if (alive) {
+    camera_hit(s, op, bs.tape_tri, bs.tape_bary, pix, sidx, c);
+    alive = c.k >= 0;
+  }
+  const float hw = op.nee_hw > 0.0f ? op.nee_hw : (op.nee_hw_dev ? *op.nee_hw_dev : 0.0f);
+  const double width = 2.0 * (double)hw;
+  const double stotal = s.scdf[s.E - 1];
+  float d[3] = {c.d[0], c.d[1], c.d[2]};
+  int k = c.k;
+  float b1 = c.b1, b2 = c.b2;
+  for (int b = 0; b < md; ++b) {
+    Vertex x;
+    bool needA = false, needB = false;
+    int4 recA = make_int4(-1, 0, 0, 0), recB = make_int4(-1, 0, 0, 0);
+    if (alive) {
+      load_vertex(s, k, b1, b2, d, x);
+      float3 nrm = shading_normal(x);
+      float n32[3];
+      shading_normal32(x, n32);
+      uint4 rn = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kEdgeNee, (uint32_t)b, kPassInterior, op.scene_id);
+      SecGeom gm;
+      needA = secondary_sides<kSelLength>(s, op, (uint32_t)pix, (uint32_t)sidx, b, md, x, nrm, gm);
+      if (needA) {
+        float uA = fm(hw, fs(fm(2.0f, u01f(rn.x)), 1.0f));
+        double pB = 0.0;
+        float dA[3];
+        if (nee_ray(gm.ve0, gm.ve1, x.p, gm.t, uA, dA)) {
+          NeeHits h;
+          nee_light_hits(s, x.p, dA, h);
+          if (h.n > 0) {
+            NeeQuery o;
+            nee_query(s, x.p, n32, dA, hw, 0.0f, make_uint2(0u, 0u), gm.e, h, o);
+            pB = nee_density(o, h, nee_jacobian(gm.ve0, gm.ve1, x.p, gm.t, uA));
+          }
+        }
+        double le = s.scdf[gm.e] - (gm.e > 0 ? s.scdf[gm.e - 1] : 0.0);
+        recA = make_int4(gm.e, __float_as_int((float)(1.0 / (le / stotal + width * pB))), __float_as_int(gm.t), 0);
+      }
+      if (s.L > 0) {
+        // the shadow ray of this vertex's next-event estimation, drawn again
+        uint4 rl = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kLight, (uint32_t)b, kPassInterior, op.scene_id);
+        LightSample ls;
+        sample_light(s, rl, ls);
+        float dB[3] = {fs(ls.y[0], x.p[0]), fs(ls.y[1], x.p[1]), fs(ls.y[2], x.p[2])};
+        float Tj, tb1, tb2;
+        if (watertight(make_shear(dB), x.p, ls.l0, ls.l1, ls.l2, INFINITY, &Tj, &tb1, &tb2)) {
+          NeeHits h;
+          nee_light_hits(s, x.p, dB, h);
+          NeeQuery o;
+          nee_query(s, x.p, n32, dB, hw, Tj, make_uint2(rn.z, rn.w), -1, h, o);
+          if (o.has_win) {
+            o.timp = o.win.imp;
+            o.ts = o.win.s;
+            int2 ev = s.edges[o.win.eid];
+            float3 v0 = ld3(s.verts + 3 * ev.x), v1 = ld3(s.verts + 3 * ev.y);
+            double pB = nee_density(o, h, nee_jacobian(v0, v1, x.p, o.win.t, o.win.u));
+            double le = s.scdf[o.win.eid] - (o.win.eid > 0 ? s.scdf[o.win.eid - 1] : 0.0);
+            double den = le / stotal + width * pB;
+            if (den > 0.0) {
+              recB = make_int4(o.win.eid, __float_as_int((float)(1.0 / den)), __float_as_int(o.win.t), 0);
+              SecGeom gb;
+              needB = secondary_sides<kSelNeePre>(s, op, (uint32_t)pix, (uint32_t)sidx, b, md, x, nrm, gb, nullptr,
+                                                  &recB);
+            }
+          }
+        }
+      }
+    }
+    unsigned long long item = ((unsigned long long)i << 3) | (unsigned)b;
+    sec_push(bs, b, (unsigned long long)n, needA, item, recA);
+    sec_push(bs, md + b, (unsigned long long)n, needB, item, recB);
+    if (alive) {  // on to vertex b + 1
+      if (b + 1 >= md) {
+        alive = false;
+      } else {
+        float n32[3];
+        shading_normal32(x, n32);
+        uint4 r = rng4(op.key, (uint32_t)pix, (uint32_t)sidx, kBsdf, (uint32_t)b, kPassInterior, op.scene_id);
+        float nd[3];
+        cosine_dir(n32, u01f(r.x), u01f(r.y), nd);
+        if (!(dot(f3(n32), f3(nd)) > 0.f)) {
+          alive = false;
+        } else {
+          for (int q = 0; q < 3; ++q) d[q] = nd[q];
+          int32_t tt = bs.tape_tri[(int64_t)(b + 1) * n + i];
+          if (tt == -1) {
+            alive = false;
+          } else {
+            k = tt & 0x7fffffff;
+            float2 bb = bs.tape_bary[(int64_t)(b + 1) * n + i];
+            b1 = bb.x;
+            b2 = bb.y;
+          }
+        }
+      }
+    }
+  }
+}
+
+// regions of the secondary queue: one per path vertex, and as many again for
+// the billboard samples of next-event estimation for edges
+__device__ __forceinline__ int sec_regions(const Opts& op, int md) { return op.nee ? 2 * md : md; }
+// queue slot of the qq-th queued sample (R regions of n slots, in order)
+__device__ __forceinline__ unsigned long long sec_slot(const unsigned long long* cnt, int R, unsigned long long n,
+                                                       unsigned long long qq) {
+  for (int b = 0; b < R; ++b) {
+    if (qq < cnt[b]) return (unsigned long long)b * n + qq;
+    qq -= cnt[b];
+  }
+  return qq;
+}
+
 // Pass 2: the queued (sample, vertex) pairs, a block-stride loop over the
 // vertex regions of the queue in order (first vertex first: its samples
 // carry the longest continuation paths); vertex gradients through the block
@@ -1833,25 +1996,19 @@ __global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_trace(BatchS
   int md = op.primary_only ? 1 : min(op.max_depth, kMaxDepth);
   const float3 Le = ld3(s.radiance);
   const unsigned long long n_region = (unsigned long long)s.W * s.H * op.spp;
-  __shared__ unsigned long long cnt[kMaxDepth];
-  if (threadIdx.x < kMaxDepth) cnt[threadIdx.x] = (int)threadIdx.x < md ? bs.sec_count[threadIdx.x] : 0ull;
+  const int R = sec_regions(op, md);
+  __shared__ unsigned long long cnt[2 * kMaxDepth];
+  if (threadIdx.x < 2 * kMaxDepth) cnt[threadIdx.x] = (int)threadIdx.x < R ? bs.sec_count[threadIdx.x] : 0ull;
   __syncthreads();
   unsigned long long count = 0;
-  for (int b = 0; b < md; ++b) count += cnt[b];
+  for (int b = 0; b < R; ++b) count += cnt[b];
   for (unsigned long long base = (unsigned long long)blockIdx.x * kBlock; base < count;
        base += (unsigned long long)gridDim.x * kBlock) {
     cache_init(cv);
     __syncthreads();
-    unsigned long long qq = base + threadIdx.x, q = qq;
     int64_t jpix = 0;  // pixel of the queued sample (per-pixel gradient image)
-    // queue slot of the qq-th queued sample: region b, offset within it
-    for (int b = 0; b < md; ++b) {
-      if (qq < cnt[b]) {
-        q = (unsigned long long)b * n_region + qq;
-        break;
-      }
-      qq -= cnt[b];
-    }
+    // queue slot of the queued sample: region, offset within it
+    unsigned long long q = sec_slot(cnt, R, n_region, base + threadIdx.x);
     SecOut so;
     so.have_edge = false;
     so.have_m[0] = so.have_m[1] = false;
@@ -1872,11 +2029,14 @@ __global__ void __launch_bounds__(kBlock, DRT_SEC_MIN_BLOCKS) k_sec_trace(BatchS
         float3 ab = ((1.0f / (float)op.spp) * ld3(bs.d_image + 3 * pix)) * beta;
         float3 dp = zero3();
         secondary_at_vertex<kSel>(s, op, (uint32_t)pix, (uint32_t)sidx, b, md, x, shading_normal(x),
-                                  ld3(s.albedo + 3 * x.k), ab, Le, dp, so, bs.sec_pick + q);
+                                  ld3(s.albedo + 3 * x.k), ab, Le, dp, so, bs.sec_pick + q, bs.sec_nee + q,
+                                  q >= (unsigned long long)md * n_region ? kPassNeeBase : kPassSecondaryBase);
+        // a vertex's length and billboard samples add to one slot (two
+        // additions onto zero: the same sum in either order)
         float* o = bs.dp_sec + 3 * (i * md + b);
-        o[0] = dp.x;
-        o[1] = dp.y;
-        o[2] = dp.z;
+        atomicAdd(o, dp.x);
+        atomicAdd(o + 1, dp.y);
+        atomicAdd(o + 2, dp.z);
       }
     }
     scatter3(bs.d_verts, so.eid0, so.de0, so.have_edge, &cv);
@@ -1932,16 +2092,6 @@ __device__ __forceinline__ void sec_push_path(const BatchScene& bs, int buf, boo
   }
 }
 
-// queue slot of the qq-th queued sample (regions per vertex, in order)
-__device__ __forceinline__ unsigned long long sec_slot(const unsigned long long* cnt, int md, unsigned long long n,
-                                                       unsigned long long qq) {
-  for (int b = 0; b < md; ++b) {
-    if (qq < cnt[b]) return (unsigned long long)b * n + qq;
-    qq -= cnt[b];
-  }
-  return qq;
-}
-
 // Stage 1: side rays of every queued sample; samples above the last vertex
 // start their continuation paths in state buffer 0.
 template <int kSel>
@@ -1950,15 +2100,16 @@ __global__ void __launch_bounds__(kBlock, DRT_SIDES_MIN_BLOCKS) k_sec_sides(Batc
   const Opts& op = bs.op;
   int md = op.primary_only ? 1 : min(op.max_depth, kMaxDepth);
   const unsigned long long n_region = (unsigned long long)s.W * s.H * op.spp;
-  __shared__ unsigned long long cnt[kMaxDepth];
-  if (threadIdx.x < kMaxDepth) cnt[threadIdx.x] = (int)threadIdx.x < md ? bs.sec_count[threadIdx.x] : 0ull;
+  const int R = sec_regions(op, md);
+  __shared__ unsigned long long cnt[2 * kMaxDepth];
+  if (threadIdx.x < 2 * kMaxDepth) cnt[threadIdx.x] = (int)threadIdx.x < R ? bs.sec_count[threadIdx.x] : 0ull;
   __syncthreads();
   unsigned long long count = 0;
-  for (int b = 0; b < md; ++b) count += cnt[b];
+  for (int b = 0; b < R; ++b) count += cnt[b];
   for (unsigned long long base = (unsigned long long)blockIdx.x * kBlock; base < count;
        base += (unsigned long long)gridDim.x * kBlock) {
     bool in = base + threadIdx.x < count;
-    unsigned long long q = in ? sec_slot(cnt, md, n_region, base + threadIdx.x) : 0ull;
+    unsigned long long q = in ? sec_slot(cnt, R, n_region, base + threadIdx.x) : 0ull;
     bool push = false;
     SecPathState st;
     if (in) {
@@ -1978,7 +2129,7 @@ __global__ void __launch_bounds__(kBlock, DRT_SIDES_MIN_BLOCKS) k_sec_sides(Batc
         SecGeom gm;
         bool front[2];
         if (secondary_side_hits<kSel>(s, op, (uint32_t)pix, (uint32_t)sidx, b, md, x, shading_normal(x), gm, hms,
-                                      front, bs.sec_pick + q)) {
+                                      front, bs.sec_pick + q, bs.sec_nee + q)) {
           flags = (gm.act[0] ? 1 : 0) | (gm.act[1] ? 2 : 0) | (front[0] ? 4 : 0) | (front[1] ? 8 : 0);
           if (!last) {
             push = true;
@@ -2059,7 +2210,9 @@ __global__ void __launch_bounds__(kBlock, DRT_BOUNCE_MIN_BLOCKS) k_path_bounce(B
         int64_t i = (int64_t)(item >> 3);
         c0 = (uint32_t)(i / op.spp);
         c1 = (uint32_t)(i % op.spp);
-        pass = kPassSecondaryBase + (uint32_t)(item & 7u);
+        // billboard samples (regions from md on) continue with their own pass
+        bool nee_slot = q >= (unsigned long long)md * ((unsigned long long)s.W * s.H * op.spp);
+        pass = (nee_slot ? kPassNeeBase : kPassSecondaryBase) + (uint32_t)(item & 7u);
       } else {
         c0 = bs.order ? (uint32_t)bs.order[q] : (uint32_t)q;
         c1 = 0u;
@@ -2155,11 +2308,12 @@ __global__ void __launch_bounds__(kBlock, DRT_FINISH_MIN_BLOCKS) k_sec_finish(Ba
   int md = op.primary_only ? 1 : min(op.max_depth, kMaxDepth);
   const float3 Le = ld3(s.radiance);
   const unsigned long long n_region = (unsigned long long)s.W * s.H * op.spp;
-  __shared__ unsigned long long cnt[kMaxDepth];
-  if (threadIdx.x < kMaxDepth) cnt[threadIdx.x] = (int)threadIdx.x < md ? bs.sec_count[threadIdx.x] : 0ull;
+  const int R = sec_regions(op, md);
+  __shared__ unsigned long long cnt[2 * kMaxDepth];
+  if (threadIdx.x < 2 * kMaxDepth) cnt[threadIdx.x] = (int)threadIdx.x < R ? bs.sec_count[threadIdx.x] : 0ull;
   __syncthreads();
   unsigned long long count = 0;
-  for (int b = 0; b < md; ++b) count += cnt[b];
+  for (int b = 0; b < R; ++b) count += cnt[b];
   for (unsigned long long base = (unsigned long long)blockIdx.x * kBlock; base < count;
        base += (unsigned long long)gridDim.x * kBlock) {
     cache_init(cv);
@@ -2173,7 +2327,7 @@ __global__ void __launch_bounds__(kBlock, DRT_FINISH_MIN_BLOCKS) k_sec_finish(Ba
       for (int j = 0; j < 3; ++j) { so.dm[h][j] = zero3(); so.mid[h][j] = 0; }
     int64_t jpix = 0;  // pixel of the queued sample (per-pixel gradient image)
     if (base + threadIdx.x < count) {
-      unsigned long long q = sec_slot(cnt, md, n_region, base + threadIdx.x);
+      unsigned long long q = sec_slot(cnt, R, n_region, base + threadIdx.x);
       int4 h0 = bs.sec_hits[2 * q], h1 = bs.sec_hits[2 * q + 1];
       int flags = h0.w;
       unsigned long long item = bs.sec_queue[q];
@@ -2187,7 +2341,8 @@ __global__ void __launch_bounds__(kBlock, DRT_FINISH_MIN_BLOCKS) k_sec_finish(Ba
       SecGeom gm;
       if ((flags & 3) && tape_vertex(s, op, bs.tape_tri, bs.tape_bary, pix, sidx, b, md, x, beta)) {
         float3 n = shading_normal(x);
-        if (secondary_sides<kSel>(s, op, (uint32_t)pix, (uint32_t)sidx, b, md, x, n, gm, bs.sec_pick + q)) {
+        if (secondary_sides<kSel>(s, op, (uint32_t)pix, (uint32_t)sidx, b, md, x, n, gm, bs.sec_pick + q,
+                                  bs.sec_nee + q)) {
           gm.act[0] = (flags & 1) != 0;
           gm.act[1] = (flags & 2) != 0;
           bool front[2] = {(flags & 4) != 0, (flags & 8) != 0};
@@ -2203,10 +2358,12 @@ __global__ void __launch_bounds__(kBlock, DRT_FINISH_MIN_BLOCKS) k_sec_finish(Ba
           float3 ab = ((1.0f / (float)op.spp) * ld3(bs.d_image + 3 * pix)) * beta;
           float3 dp = zero3();
           secondary_contrib(s, x, n, ld3(s.albedo + 3 * x.k), ab, Le, gm, hms, front, Lr, dp, so);
+          // length and billboard samples of a vertex share the slot (two
+          // additions onto zero: the same sum in either order)
           float* o = bs.dp_sec + 3 * (i * md + b);
-          o[0] = dp.x;
-          o[1] = dp.y;
-          o[2] = dp.z;
+          atomicAdd(o, dp.x);
+          atomicAdd(o + 1, dp.y);
+          atomicAdd(o + 2, dp.z);
         }
       }
     }
@@ -2735,9 +2892,14 @@ cudaError_t launch_render(const drt_scene* sc, const Opts& op, float* image, drt
   return cudaGetLastError();
 }
 
+cudaError_t launch_nee_half_width(const float* verts, int V, float* out, cudaStream_t st) {
+  DRT_PROF_LAUNCH("nee_half_width", st, k_nee_half_width<<<1, 1024, 0, st>>>(verts, V, out));
+  return cudaGetLastError();
+}
+
 int64_t secondary_capacity(int W, int H, const Opts& op) {
   int md = op.primary_only ? 1 : std::min(op.max_depth, kMaxDepth);
-  return (int64_t)W * H * op.spp * md;
+  return (int64_t)W * H * op.spp * md * (op.nee ? 2 : 1);
 }
 
 cudaError_t launch_secondary_apart(const BatchScene& b, cudaStream_t st) {
@@ -2746,8 +2908,12 @@ cudaError_t launch_secondary_apart(const BatchScene& b, cudaStream_t st) {
   BatchScene q = b;
   q.v.counters = nullptr;
   bool tree = b.op.sec_sampler == 1 && b.sec_pick;
+  bool nee = b.op.nee != 0;
+  if (nee && !b.sec_nee) return cudaErrorInvalidValue;
   unsigned gq = (unsigned)((n + kBlock - 1) / kBlock);
-  if (tree)
+  if (nee)
+    DRT_PROF_LAUNCH("backward_secondary_queue", st, k_sec_queue_nee<<<gq, kBlock, 0, st>>>(q));
+  else if (tree)
     DRT_PROF_LAUNCH("backward_secondary_queue", st, k_sec_queue<kSelTree><<<gq, kBlock, 0, st>>>(q));
   else
     DRT_PROF_LAUNCH("backward_secondary_queue", st, k_sec_queue<kSelLength><<<gq, kBlock, 0, st>>>(q));
@@ -2758,7 +2924,9 @@ cudaError_t launch_secondary_apart(const BatchScene& b, cudaStream_t st) {
   bool staged = md > 1 && b.sec_hits && b.sec_lr && b.sec_path[0] && b.sec_path[1] && b.sec_path_count &&
                 b.sec_cap < (int64_t(1) << 31);
   if (!staged) {
-    if (tree)
+    if (nee)
+      DRT_PROF_LAUNCH("backward_secondary_edges", st, k_sec_trace<kSelNeePre><<<(unsigned)grid, kBlock, 0, st>>>(t));
+    else if (tree)
       DRT_PROF_LAUNCH("backward_secondary_edges", st,
                       k_sec_trace<kSelTreePre><<<(unsigned)grid, kBlock, 0, st>>>(t));
     else
@@ -2768,7 +2936,9 @@ cudaError_t launch_secondary_apart(const BatchScene& b, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(b.sec_path_count, 0, 2 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   t.v.counters = counter_slot(kSlotBwdSecSides);
-  if (tree)
+  if (nee)
+    DRT_PROF_LAUNCH("backward_secondary_sides", st, k_sec_sides<kSelNeePre><<<(unsigned)grid, kBlock, 0, st>>>(t));
+  else if (tree)
     DRT_PROF_LAUNCH("backward_secondary_sides", st, k_sec_sides<kSelTreePre><<<(unsigned)grid, kBlock, 0, st>>>(t));
   else
     DRT_PROF_LAUNCH("backward_secondary_sides", st, k_sec_sides<kSelLength><<<(unsigned)grid, kBlock, 0, st>>>(t));
@@ -2785,7 +2955,9 @@ cudaError_t launch_secondary_apart(const BatchScene& b, cudaStream_t st) {
   }
   BatchScene f = b;
   f.v.counters = nullptr;
-  if (tree)
+  if (nee)
+    DRT_PROF_LAUNCH("backward_secondary_finish", st, k_sec_finish<kSelNeePre><<<(unsigned)grid, kBlock, 0, st>>>(f));
+  else if (tree)
     DRT_PROF_LAUNCH("backward_secondary_finish", st,
                     k_sec_finish<kSelTreePre><<<(unsigned)grid, kBlock, 0, st>>>(f));
   else
@@ -2795,7 +2967,7 @@ cudaError_t launch_secondary_apart(const BatchScene& b, cudaStream_t st) {
 
 int64_t secondary_path_capacity(int W, int H, const Opts& op) {
   int md = op.primary_only ? 1 : std::min(op.max_depth, kMaxDepth);
-  return md > 1 ? (int64_t)W * H * op.spp * (md - 1) : 0;
+  return md > 1 ? (int64_t)W * H * op.spp * (md - 1) * (op.nee ? 2 : 1) : 0;
 }
 
 cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape* tape, const float* d_image,
@@ -2860,6 +3032,7 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
     bsd.sec_queue = secs->queue;
     bsd.sec_count = secs->count;
     bsd.sec_pick = op.sec_sampler == 1 ? secs->pick : nullptr;
+    bsd.sec_nee = op.nee ? secs->nee : nullptr;
     bsd.sec_cap = secondary_capacity(sc->W, sc->H, op);
     if (secs->wave_cap >= bsd.sec_cap && secs->path_cap >= secondary_path_capacity(sc->W, sc->H, op)) {
       bsd.sec_hits = secs->hits;

@@ -103,8 +103,12 @@ def test_crossing_is_the_closest_approach_of_the_two_lines():
                     checked += 1
                     if a >= 3 * 40:
                         continue  # the light quad: its diagonal has two faces (the next test covers those)
-                    # a soup edge has one face, so it is a silhouette; the point must lie above p's tangent plane
-                    want_imp = np.linalg.norm(V[b] - V[a]) / np.linalg.norm(m - p) if n @ (m - p) > 0 else 0.0
+                    # a soup edge has one face, so it is a silhouette; the point must lie above p's tangent
+                    # plane and farther from p than the width
+                    dist = np.linalg.norm(m - p)
+                    want_imp = np.linalg.norm(V[b] - V[a]) / dist if n @ (m - p) > 0 and dist > 2 * hw else 0.0
+                    if abs(dist - 2 * hw) < 1e-4 * hw:
+                        continue
                     assert abs(gimp - want_imp) <= 1e-4 * want_imp
         q.close()
     assert checked > 50, checked
@@ -322,8 +326,8 @@ def test_density_integrates_to_the_covered_measure():
         for t in (np.arange(nt) + 0.5) / nt:
             for u in (np.arange(nu) + 0.5) / nu * 2 * hw - hw:
                 m = A + t * (B - A)
-                if (m - p) @ nrm <= 0:
-                    continue  # at or below p's tangent plane: no importance
+                if (m - p) @ nrm <= 0 or np.linalg.norm(m - p) <= 2 * hw:
+                    continue  # at or below p's tangent plane, or within the width of p: no importance
                 if a < 4 and b < 4:
                     continue  # the receiver's own edges lie in that plane
                 w = _family_direction(p.astype(np.float64), A, B, t, abs(u), 1 if u > 0 else -1)
