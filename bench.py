@@ -18,10 +18,11 @@ proposal against the plain edge sampler (train on logs of 20 scenes, score 4
 held-out scenes) under "variance_x_time" (--no-proposal skips it); the
 64-scene batched workload (persistent launches in a CUDA graph) under
 "batched", and the same with 64 small scenes under "batched_small"
-(--no-batched skips both); the secondary-edge hierarchy (Sec. 5.3.1) and the
-importance-sampled point on an edge (Sec. 5.3.2) against 3D length sampling
-with a uniform point, as gradient variance x time, under
-"secondary_samplers" (--no-hierarchy skips it); the tensor-core network's
+(--no-batched skips both); the secondary-edge hierarchy (Sec. 5.3.1), the
+importance-sampled point on an edge (Sec. 5.3.2) and next-event estimation
+for edges (Sec. 5.3.3) against 3D length sampling with a uniform point, as
+gradient variance x time, under "secondary_samplers" (--no-hierarchy skips
+it); the tensor-core network's
 BF16 rate under "mlp".
 
 Roofline: the ray kernels are bound by issue slots and L1/L2 bandwidth (no
@@ -97,7 +98,8 @@ OPS_PER_TRI = 26          # watertight test: shear and edge functions
 BYTES_PER_NODE = 64
 BYTES_PER_TRI = 48
 # profiled kernel name -> work-counter slot
-COUNTER_OF = {"render": "render", "backward_interior": "backward_interior", "backward_path": "backward_interior",
+COUNTER_OF = {"render": "render", "render_first": "render", "render_bounce": "render_bounce",
+              "backward_interior": "backward_interior", "backward_path": "backward_interior",
               "backward_primary_edges": "backward_primary_edges",
               "backward_secondary_edges": "backward_secondary_edges",
               "backward_secondary_sides": "backward_secondary_sides",
@@ -256,11 +258,12 @@ def run_batched(ctx, dev, replays=20, t_min=1000, t_max=100_000, resolutions=(12
 
 
 def run_secondary_samplers(ctx, dev, K=24, samples=16):
-    """Secondary edge term (Sec. 5.2.2) under three samplers, as gradient
+    """Secondary edge term (Sec. 5.2.2) under four samplers, as gradient
     variance x time against the plain one (3D length CDF, uniform point): the
-    edge hierarchy of Sec. 5.3.1 (`samples` root samples), and the
+    edge hierarchy of Sec. 5.3.1 (`samples` root samples), the
     importance-sampled point on the edge of Sec. 5.3.2 (clamped cosine over
-    the edge's arc, mixed with uniform); the hierarchy also with 4 root
+    the edge's arc, mixed with uniform), and next-event estimation for edges
+    of Sec. 5.3.3 beside the plain sampler; the hierarchy also with 4 root
     samples.  Per scene, K runs with independent
     seeds; each run re-uploads the vertices (so the hierarchy is rebuilt
     inside the timed backward, as in an optimisation step), renders its tape
@@ -275,21 +278,24 @@ def run_secondary_samplers(ctx, dev, K=24, samples=16):
     from paper_1904_12228_gb300 import scenegen as sg
     out = []
     cases = (("direct lighting 256x256, 5124 tris, 64 spp", sg.direct_lighting(DIRECT.seed), 1, 64, 2),
+             ("direct lighting 256x256, 5124 tris, 64 spp, small light (0.1 x 0.1, same power)",
+              sg.direct_lighting(DIRECT.seed, light_half=0.05), 1, 64, 2),
              ("procedural 512x512, 200k tris, depth 3, 32 spp", sg.procedural(1237), 3, 32, 1))
-    samplers = (("length", 0, 0), ("hierarchy", samples, 0), ("hierarchy_4", 4, 0), ("point", 0, 1))
+    samplers = (("length", 0, 0, 0), ("hierarchy", samples, 0, 0), ("hierarchy_4", 4, 0, 0), ("point", 0, 1, 0),
+                ("nee", 0, 0, 1))
     for name, sc, depth, spp, leaf in cases:
         S = drt.Scene.from_arrays(ctx, sc, bvh_leaf_size=leaf)
         verts = torch.from_numpy(sc.verts).to(dev)
         w = torch.from_numpy(sg.loss_adjoint(DIRECT.seed, sc.width, sc.height)).to(dev)
         img = torch.zeros((sc.height, sc.width, 3), device=dev)
         res = {}
-        for label, tree, point in samplers:
+        for label, tree, point, nee in samplers:
             runs = torch.zeros((K, 3 * len(sc.verts)), device=dev)
             times = []
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             for k in range(-2, K):  # two warm-up runs
                 o = drt.make_opts(spp, 0, max_depth=depth, seed=7000 + k, terms=4, sec_tree_samples=tree,
-                                  sec_point=point)
+                                  sec_point=point, sec_nee=nee)
                 S.update_vertices(verts)  # new scene version: the backward rebuilds the hierarchy
                 tape = S.render(img, o, want_tape=True)
                 dv = runs[max(k, 0)].view(-1, 3)
@@ -320,11 +326,12 @@ def run_secondary_samplers(ctx, dev, K=24, samples=16):
         out.append(entry)
         S.free()
     geo = {lab: float(np.exp(np.mean([np.log(max(o["ratio"][lab], 1e-30)) for o in out])))
-           for lab in ("hierarchy", "hierarchy_4", "point")}
+           for lab in ("hierarchy", "hierarchy_4", "point", "nee")}
     return {"ratio_geomean": geo, "root_samples": samples,
             "ratio_unit": "sampler/plain secondary-edge gradient variance x time (<1: the sampler wins); plain = "
                           "3D length CDF and uniform point; hierarchy = Sec. 5.3.1 with `root_samples` (hierarchy_4: "
-                          "4) root samples; point = Sec. 5.3.2 (Lambertian)",
+                          "4) root samples; point = Sec. 5.3.2 (Lambertian); nee = Sec. 5.3.3, billboard samples of "
+                          "the shadow rays beside the length sampler (balance heuristic)",
             "scenes": out}
 
 

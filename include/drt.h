@@ -489,14 +489,15 @@ drt_status drt_debug_closest(drt_context* ctx, drt_scene* scene, int64_t n, cons
 drt_status drt_profile_enable(drt_context* ctx, int enable);
 drt_status drt_profile_read(drt_context* ctx, int max, char* names, double* ms, int64_t* launches, int* n);
 
-/* Work counters (off by default): per kernel slot (0 render, 1 backward
- * interior, 2 backward primary edges (the first vertex of their side paths
- * beyond depth 1), 3 debug, 4 backward secondary edges in one kernel (depth
- * 1), 5 and 6 the side-ray and continuation stages of the secondary edges
- * beyond depth 1, 7 the continuation stages of the primary edges) four int64
- * counts -- rays traced to the closest hit, shadow rays, BVH nodes visited,
- * triangle tests.  drt_counters_read synchronises the device, copies [8][4]
- * counts to out and resets them. */
+/* Work counters (off by default): per kernel slot (0 render (the first vertex
+ * of its paths beyond depth 1), 1 backward interior, 2 backward primary edges
+ * (the first vertex of their side paths beyond depth 1), 3 debug, 4 backward
+ * secondary edges in one kernel (depth 1), 5 and 6 the side-ray and
+ * continuation stages of the secondary edges beyond depth 1, 7 the
+ * continuation stages of the primary edges, 8 the continuation stages of the
+ * render) four int64 counts -- rays traced to the closest hit, shadow rays,
+ * BVH nodes visited, triangle tests.  drt_counters_read synchronises the
+ * device, copies [9][4] counts to out and resets them. */
 drt_status drt_counters_enable(drt_context* ctx, int enable);
 drt_status drt_counters_read(drt_context* ctx, int64_t* out);
 

@@ -133,6 +133,7 @@ void free_scene_buffers(drt_scene* s) {
                   s->sec.dp, s->sec.queue, s->sec.count, s->sec.pick, s->sec.nee, s->nee_hw, s->sec.hits, s->sec.lr,
                   s->sec.path[0],
                   s->sec.path[1], s->sec.path_count, s->prim.lr, s->prim.path[0], s->prim.path[1], s->prim.count,
+                  s->rnd.L, s->rnd.path[0], s->rnd.path[1], s->rnd.count,
                   s->pguide, s->sguide, s->edge_opp,
                   s->et_nodes, s->et_leaf, s->et_keys, s->et_keys2, s->et_hist, s->et_hist_tmp, s->et_vals,
                   s->et_vals2, s->et_parent, s->et_leaf_parent, s->et_flags, s->et_child};
@@ -536,7 +537,33 @@ drt_status drt_render(drt_context* ctx, drt_scene* s, const drt_render_opts* opt
     drt_tape_free(ctx, tp);
     return r;
   }
-  cudaError_t e = drt::launch_render(s, op, (float*)img.dev, tp, st);
+  // beyond depth 1 the camera paths are rendered in stages: radiance per
+  // sample and continuation states
+  const drt::RenderScratch* rs = nullptr;
+  int64_t n_s = (int64_t)s->W * s->H * op.spp;
+  if (!op.primary_only && op.max_depth > 1 && n_s < (int64_t(1) << 31)) {
+    if (n_s > s->rnd.cap) {
+      cudaStreamSynchronize(st);
+      drt::RenderScratch& b = s->rnd;
+      dfree(b.L);
+      dfree(b.path[0]);
+      dfree(b.path[1]);
+      dfree(b.count);
+      b = drt::RenderScratch();
+      drt_status a = dalloc_n(&b.L, 3 * (size_t)n_s);
+      if (a == DRT_OK) a = dalloc_n(&b.path[0], 5 * (size_t)n_s);
+      if (a == DRT_OK) a = dalloc_n(&b.path[1], 5 * (size_t)n_s);
+      if (a == DRT_OK) a = dalloc_n(&b.count, 2);
+      if (a != DRT_OK) {
+        unstage(&img, 1, st);
+        drt_tape_free(ctx, tp);
+        return a;
+      }
+      b.cap = n_s;
+    }
+    rs = &s->rnd;
+  }
+  cudaError_t e = drt::launch_render(s, op, (float*)img.dev, tp, rs, st);
   if (e != cudaSuccess) {
     unstage(&img, 1, st);
     drt_tape_free(ctx, tp);

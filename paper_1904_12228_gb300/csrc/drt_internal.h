@@ -63,6 +63,14 @@ struct PrimScratch {
   unsigned long long* count = nullptr;
   int64_t cap = 0;  // edge samples the buffers hold
 };
+// Scratch of the render beyond depth 1, in stages: radiance per sample and
+// two buffers of continuation-path states (5 float4 each).
+struct RenderScratch {
+  float* L = nullptr;
+  float4* path[2] = {nullptr, nullptr};
+  unsigned long long* count = nullptr;
+  int64_t cap = 0;  // samples the buffers hold
+};
 // Scratch for sorting primary edge samples by screen position (key, index).
 struct SortBuffers {
   uint32_t *keys = nullptr, *keys2 = nullptr, *hist = nullptr, *hist_tmp = nullptr;
@@ -110,6 +118,7 @@ struct drt_scene {
   drt::SortBuffers esort;    // backward: primary edge samples sorted by screen position
   drt::SecScratch sec;       // backward: secondary edge samples queued and traced apart
   drt::PrimScratch prim;     // backward: primary edge samples beyond depth 1 in stages
+  drt::RenderScratch rnd;    // render: camera paths beyond depth 1 in stages
   // tile segments of the primary edges (built on demand)
   int32_t *seg_edge = nullptr, *seg_tile = nullptr;
   uint32_t *seg_count = nullptr, *seg_scan_tmp = nullptr;
@@ -147,7 +156,7 @@ struct ProfToken {
 ProfToken prof_begin(const char* name, cudaStream_t st);
 void prof_end(const ProfToken& t, cudaStream_t st);
 enum { kSlotRender = 0, kSlotBwdInterior = 1, kSlotBwdPrimary = 2, kSlotDebug = 3, kSlotBwdSecondary = 4,
-       kSlotBwdSecSides = 5, kSlotBwdSecBounce = 6, kSlotBwdPrimBounce = 7, kKernelSlots = 8 };
+       kSlotBwdSecSides = 5, kSlotBwdSecBounce = 6, kSlotBwdPrimBounce = 7, kSlotRenderBounce = 8, kKernelSlots = 9 };
 unsigned long long* counter_slot(int kernel);  // null unless counters are enabled
 #define DRT_PROF_LAUNCH(name, st, ...)                      \
   do {                                                      \
@@ -181,7 +190,8 @@ cudaError_t build_bvh(drt_scene* s, cudaStream_t st);
 cudaError_t build_edge_cdfs(drt_scene* s, cudaStream_t st);
 cudaError_t check_finite(drt_scene* s, cudaStream_t st);
 // render.cu
-cudaError_t launch_render(const drt_scene* s, const Opts& op, float* image, drt_tape* tape, cudaStream_t st);
+cudaError_t launch_render(const drt_scene* s, const Opts& op, float* image, drt_tape* tape, const RenderScratch* rs,
+                          cudaStream_t st);
 cudaError_t launch_backward(const drt_scene* s, const Opts& op, const drt_tape* tape, const float* d_image,
                             float* d_verts, float* d_albedo, float* d_radiance, float* d_cam, float* d_cam_scale,
                             float* scratch_global, const SortBuffers* sort, const SecScratch* secs,

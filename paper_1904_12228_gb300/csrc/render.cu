@@ -450,12 +450,13 @@ __device__ float3 path_value_warp(const SceneView& s, const Opts& op, const floa
 // albedo (the throughput of what follows).
 __device__ float3 path_first_vertex_warp(const SceneView& s, const Opts& op, const float o[3], const float d[3],
                                          bool act, uint32_t c0, uint32_t c1, uint32_t pass, bool& cont, Hit& h0,
-                                         float nd[3], float3& alb) {
+                                         float nd[3], float3& alb, int* vis_out = nullptr) {
   int md = op.primary_only ? 1 : op.max_depth;
   const float3 Le = ld3(s.radiance);
   float3 L = zero3();
   bool alive = act;
   cont = false;
+  if (vis_out) *vis_out = 0;
   alb = zero3();
   nd[0] = nd[1] = 0.f;
   nd[2] = 1.f;
@@ -485,6 +486,7 @@ __device__ float3 path_first_vertex_warp(const SceneView& s, const Opts& op, con
     if (alive && !occ) {
       float g = nee_geometry(s, f3(x.p), f3(n32), ls);
       nee_add(L, kInvPi * g, alb * Le);
+      if (vis_out) *vis_out = 1;
     }
   }
   if (alive && md > 1) {
@@ -2165,7 +2167,11 @@ struct PathStage {
   unsigned long long* count;   // [2] entries in each buffer
   float* lr;                   // [slots, 6] radiance gathered by each side
 };
-enum { kSrcSecondary = 0, kSrcPrimary = 1 };
+// sources of continuation paths: secondary edge samples (pairs of side
+// paths), primary edge samples (pairs), camera paths of the render (one path
+// per entry, side 1 unused; radiance per sample in lr[3 i], tape entries
+// written at every vertex)
+enum { kSrcSecondary = 0, kSrcPrimary = 1, kSrcRender = 2 };
 constexpr int kPathPending = 1024;
 
 __device__ __forceinline__ void path_push(const PathStage& ps, int buf, bool push, const SecPathState& st) {
@@ -2213,10 +2219,14 @@ __global__ void __launch_bounds__(kBlock, DRT_BOUNCE_MIN_BLOCKS) k_path_bounce(B
         // billboard samples (regions from md on) continue with their own pass
         bool nee_slot = q >= (unsigned long long)md * ((unsigned long long)s.W * s.H * op.spp);
         pass = (nee_slot ? kPassNeeBase : kPassSecondaryBase) + (uint32_t)(item & 7u);
-      } else {
+      } else if (kSrc == kSrcPrimary) {
         c0 = bs.order ? (uint32_t)bs.order[q] : (uint32_t)q;
         c1 = 0u;
         pass = kPassPrimaryEdge;
+      } else {
+        c0 = (uint32_t)(q / (unsigned long long)op.spp);
+        c1 = (uint32_t)(q % (unsigned long long)op.spp);
+        pass = kPassInterior;
       }
       int bb = st.e.w & 255;
       bool alive[2] = {(st.e.w & 256) != 0, (st.e.w & 512) != 0};
@@ -2247,6 +2257,7 @@ __global__ void __launch_bounds__(kBlock, DRT_BOUNCE_MIN_BLOCKS) k_path_bounce(B
         alb[k] = ld3(s.albedo + 3 * x[k].k);
       }
       if (alive[0] || alive[1]) {
+        int vis = 0;  // render: the vertex's next-event ray reached the light (tape bit)
         float n32[2][3];
         for (int k = 0; k < 2; ++k)
           if (alive[k]) shading_normal32(x[k], n32[k]);
@@ -2261,7 +2272,7 @@ __global__ void __launch_bounds__(kBlock, DRT_BOUNCE_MIN_BLOCKS) k_path_bounce(B
           bool occ[2];
           trace_any2(s, x[0].p, sd[0], x[0].k, ls.lt, x[1].p, sd[1], x[1].k, ls.lt, alive[0], alive[1],
                      kShadowTmax, occ[0], occ[1]);
-          float* lr = ps.lr + 6 * q;
+          float* lr = ps.lr + (kSrc == kSrcRender ? 3 : 6) * q;
           for (int k = 0; k < 2; ++k)
             if (alive[k] && !occ[k]) {
               float g = nee_geometry(s, f3(x[k].p), f3(n32[k]), ls);
@@ -2270,7 +2281,13 @@ __global__ void __launch_bounds__(kBlock, DRT_BOUNCE_MIN_BLOCKS) k_path_bounce(B
               lr[3 * k] = acc.x;
               lr[3 * k + 1] = acc.y;
               lr[3 * k + 2] = acc.z;
+              if (kSrc == kSrcRender) vis = 1;
             }
+        }
+        if (kSrc == kSrcRender && alive[0] && bs.tape_tri) {
+          const int64_t n = (int64_t)s.W * s.H * op.spp;
+          bs.tape_tri[(int64_t)bb * n + (int64_t)q] = x[0].k | (vis << 31);
+          bs.tape_bary[(int64_t)bb * n + (int64_t)q] = make_float2(h[0].b1, h[0].b2);
         }
         if (bb + 1 < md) {
           uint4 r = rng4(op.key, c0, c1, kBsdf, (uint32_t)bb, pass, op.scene_id);
@@ -2295,6 +2312,93 @@ __global__ void __launch_bounds__(kBlock, DRT_BOUNCE_MIN_BLOCKS) k_path_bounce(B
       }
     }
     path_push(ps, in ^ 1, push, st);
+  }
+}
+
+// The render beyond one vertex in stages.  k_render_first: the first vertex
+// of every camera path with the warp-cooperative traversal (the lanes of a
+// warp hold one pixel's samples, so their rays are coherent), its tape entry
+// and radiance (emission and next-event estimation), and the continuation
+// pushed as a pending ray.  k_path_bounce<kSrcRender>: one launch per later
+// vertex over the live paths only, so a warp holds live paths whatever their
+// pixels.  k_render_finish: the pixel means in the fused kernel's order.
+// Same random numbers, tape entries and image as k_render.
+__global__ void __launch_bounds__(kBlock, DRT_RENDER_MIN_BLOCKS)
+    k_render_first(SceneView s, Opts op, int32_t* tape_tri, float2* tape_bary, int G, PathStage ps) {
+  int lane = threadIdx.x & 31;
+  int64_t gw = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
+  int ppw = 32 / G;
+  int64_t pix = gw * ppw + lane / G;
+  int npix = s.W * s.H;
+  bool active = pix < npix;
+  int iters = (op.spp + G - 1) / G;
+  for (int it = 0; it < iters; ++it) {
+    int sidx = lane % G + it * G;
+    bool act = active && sidx < op.spp;
+    float o[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 1.f};
+    if (act) {
+      float sx, sy;
+      jitter(op, (int)pix, sidx, s.W, &sx, &sy);
+      camera_ray(s, sx, sy, o, d);
+    }
+    int64_t i = pix * op.spp + sidx;
+    bool cont;
+    Hit h0;
+    float nd[3];
+    float3 alb;
+    int vis = 0;
+    float3 L0 = path_first_vertex_warp(s, op, o, d, act, (uint32_t)pix, (uint32_t)sidx, kPassInterior, cont, h0, nd,
+                                       alb, &vis);
+    bool hit = act && h0.tri >= 0;
+    if (act) {
+      float* lr = ps.lr + 3 * i;
+      lr[0] = L0.x;
+      lr[1] = L0.y;
+      lr[2] = L0.z;
+      if (tape_tri) {
+        tape_tri[i] = hit ? (h0.tri | (vis << 31)) : -1;
+        tape_bary[i] = make_float2(hit ? h0.b1 : 0.f, hit ? h0.b2 : 0.f);
+      }
+    }
+    bool push = act && cont;
+    SecPathState st;
+    if (push) {
+      st.a = make_float4(nd[0], nd[1], nd[2], alb.x);
+      st.b = make_float4(0.f, 0.f, 1.f, alb.y);
+      st.c = make_float4(alb.z, 0.f, 0.f, 0.f);
+      st.d = make_float4(h0.b1, h0.b2, 0.f, 0.f);
+      st.e = make_int4((int)(uint32_t)i, h0.tri, -1, 1 | 256 | kPathPending);
+    }
+    path_push(ps, 0, push, st);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_render_finish(SceneView s, Opts op, float* image, int G, const float* L) {
+  int lane = threadIdx.x & 31;
+  int64_t gw = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
+  int ppw = 32 / G;
+  int64_t pix = gw * ppw + lane / G;
+  int npix = s.W * s.H;
+  bool active = pix < npix;
+  float3 acc = zero3();
+  int iters = (op.spp + G - 1) / G;
+  for (int it = 0; it < iters; ++it) {
+    int sidx = lane % G + it * G;
+    if (active && sidx < op.spp) {
+      const float* l = L + 3 * (pix * op.spp + sidx);
+      acc += make_float3(l[0], l[1], l[2]);
+    }
+  }
+  for (int o = G >> 1; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(kFull, acc.x, o);
+    acc.y += __shfl_xor_sync(kFull, acc.y, o);
+    acc.z += __shfl_xor_sync(kFull, acc.z, o);
+  }
+  if (active && lane % G == 0) {
+    float inv = 1.0f / (float)op.spp;
+    image[3 * pix] = acc.x * inv;
+    image[3 * pix + 1] = acc.y * inv;
+    image[3 * pix + 2] = acc.z * inv;
   }
 }
 
@@ -2878,13 +2982,47 @@ cudaError_t launch_reduce_globals(float* partials, int64_t rows, float* d_radian
   return cudaGetLastError();
 }
 
-cudaError_t launch_render(const drt_scene* sc, const Opts& op, float* image, drt_tape* tape, cudaStream_t st) {
+cudaError_t launch_render(const drt_scene* sc, const Opts& op, float* image, drt_tape* tape, const RenderScratch* rs,
+                          cudaStream_t st) {
   SceneView s = sc->view();
   s.counters = counter_slot(kSlotRender);
   int npix = s.W * s.H;
   int G = group_size(op.spp);
   int64_t warps = ((int64_t)npix + (32 / G) - 1) / (32 / G);
   int64_t blocks = (warps * 32 + kBlock - 1) / kBlock;
+  int md = op.primary_only ? 1 : std::min(op.max_depth, kMaxDepth);
+  int64_t n = (int64_t)npix * op.spp;
+  if (md > 1 && rs && rs->cap >= n && n < (int64_t(1) << 31)) {
+    // paths beyond one vertex in stages (k_render_first, k_path_bounce, k_render_finish)
+    int32_t* tt = tape ? tape->tri : nullptr;
+    float2* tb = tape ? tape->bary : nullptr;
+    cudaError_t e = cudaSuccess;
+    if (tt) e = cudaMemsetAsync(tt + n, 0xff, sizeof(int32_t) * (size_t)n * (md - 1), st);  // -1: no vertex
+    if (e == cudaSuccess) e = cudaMemsetAsync(rs->count, 0, 2 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    PathStage ps{{rs->path[0], rs->path[1]}, rs->count, rs->L};
+    DRT_PROF_LAUNCH("render_first", st,
+                    k_render_first<<<(unsigned)blocks, kBlock, 0, st>>>(s, op, tt, tb, G, ps));
+    BatchScene bs;
+    std::memset(&bs, 0, sizeof(bs));
+    bs.v = s;
+    bs.v.counters = counter_slot(kSlotRenderBounce);
+    bs.op = op;
+    bs.tape_tri = tt;
+    bs.tape_bary = tb;
+    int64_t grid_p = std::min<int64_t>((n + kBlock - 1) / kBlock, 152 * 8);
+    for (int level = 0; level + 1 < md; ++level) {
+      int in = level & 1;
+      e = cudaMemsetAsync(rs->count + (in ^ 1), 0, sizeof(unsigned long long), st);
+      if (e != cudaSuccess) return e;
+      DRT_PROF_LAUNCH("render_bounce", st,
+                      k_path_bounce<kSrcRender><<<(unsigned)std::max<int64_t>(grid_p, 1), kBlock, 0, st>>>(
+                          bs, ps, in));
+    }
+    DRT_PROF_LAUNCH("render_finish", st,
+                    k_render_finish<<<(unsigned)blocks, kBlock, 0, st>>>(s, op, image, G, rs->L));
+    return cudaGetLastError();
+  }
   ProfToken pt = prof_begin("render", st);
   k_render<<<(unsigned)blocks, kBlock, 0, st>>>(s, op, image, tape ? tape->tri : nullptr, tape ? tape->bary : nullptr,
                                                 G);

@@ -281,7 +281,8 @@ class Context:
         _check(self.lib.drt_counters_enable(self.handle, int(bool(enable))))
 
     COUNTER_SLOTS = ("render", "backward_interior", "backward_primary_edges", "debug", "backward_secondary_edges",
-                     "backward_secondary_sides", "backward_secondary_bounce", "backward_primary_bounce")
+                     "backward_secondary_sides", "backward_secondary_bounce", "backward_primary_bounce",
+                     "render_bounce")
 
     def counters_read(self):
         """{slot: dict(closest_rays, shadow_rays, nodes, tris)} (synchronises, resets)."""

@@ -132,21 +132,24 @@ def single_triangle(seed: int, width: int = 64, height: int = 64, color: float =
 
 
 def direct_lighting(seed: int, width: int = 256, height: int = 256, subdiv: int = 4,
-                    jitter: float = 0.01) -> Scene:
+                    jitter: float = 0.01, light_half: float = 0.5) -> Scene:
     """Jittered icosphere (radius 1) on a 2-triangle ground at y=-1 spanning
-    [-4,4]^2, lit by a 1x1 two-triangle area light at y=3 facing down with
-    radiance 10; per-triangle albedo uniform in [0.2,0.8]^3; pinhole camera
-    at (0,1,5) looking at the origin, 45 degree vertical field of view."""
+    [-4,4]^2, lit by a two-triangle square area light of half size
+    light_half (default 0.5: 1x1) at y=3 facing down with radiance
+    10 (0.5 / light_half)^2 (the same power for any size); per-triangle albedo
+    uniform in [0.2,0.8]^3; pinhole camera at (0,1,5) looking at the origin,
+    45 degree vertical field of view."""
     rng = np.random.default_rng(seed)
     sv, sf = icosphere(subdiv)
     sv = sv + rng.normal(0.0, jitter, size=sv.shape)
     gv, gf = quad((0, -1, 0), (0, 0, 4), (4, 0, 0))
-    lv, lf = quad((0, 3, 0), (0.5, 0, 0), (0, 0, 0.5))
+    lv, lf = quad((0, 3, 0), (light_half, 0, 0), (0, 0, light_half))
     verts, tris = _merge([(sv, sf), (gv, gf), (lv, lf)])
     n = len(tris)
     albedo = rng.uniform(0.2, 0.8, size=(n, 3))
     light_tris = np.array([n - 2, n - 1], np.int32)
-    return Scene(verts=verts, tris=tris, albedo=albedo, light_tris=light_tris, radiance=[10.0, 10.0, 10.0],
+    le = 10.0 * (0.5 / light_half) ** 2
+    return Scene(verts=verts, tris=tris, albedo=albedo, light_tris=light_tris, radiance=[le, le, le],
                  cam_to_world=look_at((0, 1, 5), (0, 0, 0)), cam_scale=math.tan(math.radians(22.5)),
                  cam_type=CAM_PINHOLE, width=width, height=height)
 
