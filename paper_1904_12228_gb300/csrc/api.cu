@@ -133,7 +133,8 @@ void free_scene_buffers(drt_scene* s) {
                   s->sec.dp, s->sec.queue, s->sec.count, s->sec.pick, s->sec.nee, s->nee_hw, s->sec.hits, s->sec.lr,
                   s->sec.path[0],
                   s->sec.path[1], s->sec.path_count, s->prim.lr, s->prim.path[0], s->prim.path[1], s->prim.count,
-                  s->rnd.L, s->rnd.path[0], s->rnd.path[1], s->rnd.count,
+                  s->rnd.L, s->rnd.path[0], s->rnd.path[1], s->rnd.count, s->pool.crec, s->pool.hits, s->pool.arec,
+                  s->pool.occ, s->pool.next,
                   s->pguide, s->sguide, s->edge_opp,
                   s->et_nodes, s->et_leaf, s->et_keys, s->et_keys2, s->et_hist, s->et_hist_tmp, s->et_vals,
                   s->et_vals2, s->et_parent, s->et_leaf_parent, s->et_flags, s->et_child};
@@ -500,6 +501,35 @@ drt_status drt_tape_free(drt_context* ctx, drt_tape* t) {
   return DRT_OK;
 }
 
+// Records and results of the traversal pools for `cap` continuation entries.
+drt_status ensure_pool(drt_scene* s, int64_t cap, cudaStream_t st) {
+  if (cap <= s->pool.cap) return DRT_OK;
+  cudaStreamSynchronize(st);
+  drt::PoolScratch& b = s->pool;
+  dfree(b.crec);
+  dfree(b.hits);
+  dfree(b.arec);
+  dfree(b.occ);
+  dfree(b.next);
+  b = drt::PoolScratch();
+  drt_status a = dalloc_n(&b.crec, (size_t)drt::kClosestRecF4 * cap);
+  if (a == DRT_OK) a = dalloc_n(&b.hits, 2 * (size_t)cap);
+  if (a == DRT_OK) a = dalloc_n(&b.arec, (size_t)drt::kAnyRecF4 * cap);
+  if (a == DRT_OK) a = dalloc_n(&b.occ, (size_t)cap);
+  if (a == DRT_OK) a = dalloc_n(&b.next, 2);
+  if (a != DRT_OK) {
+    dfree(b.crec);
+    dfree(b.hits);
+    dfree(b.arec);
+    dfree(b.occ);
+    dfree(b.next);
+    b = drt::PoolScratch();
+    return a;
+  }
+  b.cap = cap;
+  return DRT_OK;
+}
+
 drt_status drt_render(drt_context* ctx, drt_scene* s, const drt_render_opts* opts, float* image, drt_tape** tape,
                       void* stream) {
   NvtxRange nvtx_range("drt_render");
@@ -560,6 +590,12 @@ drt_status drt_render(drt_context* ctx, drt_scene* s, const drt_render_opts* opt
         return a;
       }
       b.cap = n_s;
+    }
+    drt_status a = ensure_pool(s, n_s, st);
+    if (a != DRT_OK) {
+      unstage(&img, 1, st);
+      drt_tape_free(ctx, tp);
+      return a;
     }
     rs = &s->rnd;
   }
@@ -802,6 +838,17 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
       b.cap = n_edge;
     }
     prims = &s->prim;
+  }
+  // the continuation stages trace through the pools
+  int64_t pool_need = 0;
+  if (prims) pool_need = std::max(pool_need, n_edge);
+  if (secs) pool_need = std::max(pool_need, drt::secondary_path_capacity(s->W, s->H, op));
+  if (pool_need > 0) {
+    drt_status a = ensure_pool(s, pool_need, st);
+    if (a != DRT_OK) {
+      unstage(sg, 7, st);
+      return a;
+    }
   }
   cudaError_t e = drt::launch_backward(s, op, tape, (const float*)sg[0].dev, (float*)sg[1].dev, (float*)sg[2].dev,
                                        (float*)sg[3].dev, (float*)sg[4].dev, (float*)sg[5].dev, s->partials, sort,

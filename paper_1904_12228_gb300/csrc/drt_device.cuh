@@ -52,6 +52,9 @@ constexpr float kTile = 16.0f;  // screen tile of the segment split, pixels
 // node visits of coherent first-vertex rays by more than the extra tests cost.
 constexpr int kLeafLimit = 8;
 __host__ __device__ __forceinline__ int leaf_enc(int first, int count) { return ~(first | ((count - 1) << 28)); }
+// float4 per closest-hit and any-hit pair record of the traversal pools
+constexpr int kClosestRecF4 = 4;
+constexpr int kAnyRecF4 = 5;
 // device error-flag codes (mirrors the public enum in drt.h)
 
 
@@ -215,6 +218,13 @@ struct BatchScene {
   float4* sec_path[2];            // [sec_path_cap, 5] continuation states, ping-pong between bounces
   unsigned long long* sec_path_count;  // [2] entries in sec_path[0], sec_path[1]
   int64_t sec_path_cap;           // entries each state buffer holds = W*H*spp*(depth-1)
+  // traversal pools of the continuation stages (null: the one-kernel continuation)
+  float4* pool_crec;
+  int4* pool_hits;
+  float4* pool_arec;
+  int* pool_occ;
+  unsigned long long* pool_next;
+  int64_t pool_cap;
 };
 
 

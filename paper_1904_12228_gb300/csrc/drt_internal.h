@@ -71,6 +71,16 @@ struct RenderScratch {
   unsigned long long* count = nullptr;
   int64_t cap = 0;  // samples the buffers hold
 };
+// Records and results of the persistent traversal pools the continuation
+// stages trace through (closest-hit and any-hit pair records per entry).
+struct PoolScratch {
+  float4* crec = nullptr;
+  int4* hits = nullptr;
+  float4* arec = nullptr;
+  int* occ = nullptr;
+  unsigned long long* next = nullptr;
+  int64_t cap = 0;  // entries the buffers hold
+};
 // Scratch for sorting primary edge samples by screen position (key, index).
 struct SortBuffers {
   uint32_t *keys = nullptr, *keys2 = nullptr, *hist = nullptr, *hist_tmp = nullptr;
@@ -119,6 +129,7 @@ struct drt_scene {
   drt::SecScratch sec;       // backward: secondary edge samples queued and traced apart
   drt::PrimScratch prim;     // backward: primary edge samples beyond depth 1 in stages
   drt::RenderScratch rnd;    // render: camera paths beyond depth 1 in stages
+  drt::PoolScratch pool;     // render and backward: traversal pools of the continuation stages
   // tile segments of the primary edges (built on demand)
   int32_t *seg_edge = nullptr, *seg_tile = nullptr;
   uint32_t *seg_count = nullptr, *seg_scan_tmp = nullptr;

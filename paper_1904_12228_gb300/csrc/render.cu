@@ -14,6 +14,7 @@
 #include "drt_internal.h"
 #include "edge_tree.cuh"
 #include "nee_edge.cuh"
+#include "trace_pool.cuh"
 
 namespace drt {
 namespace {
@@ -2315,6 +2316,203 @@ __global__ void __launch_bounds__(kBlock, DRT_BOUNCE_MIN_BLOCKS) k_path_bounce(B
   }
 }
 
+// The continuation step of k_path_bounce split around two persistent
+// traversal pools (trace_pool.cuh), so that the traversals of incoherent rays
+// keep their lanes busy: phase 0 writes the pending rays of every entry (a
+// closest-hit pair record), the pool traces them; phase 1 resolves the hits
+// and writes the next-event rays (an any-hit pair record), the pool traces
+// those; phase 2 adds the next-event radiance, writes the render's tape
+// entries and pushes the continuation.  Same random numbers and arithmetic
+// as k_path_bounce.
+struct PoolBufs {
+  float4* crec;   // [entries, kClosestRecF4]
+  int4* hits;     // [entries, 2]
+  float4* arec;   // [entries, kAnyRecF4]
+  int* occ;       // [entries]
+  unsigned long long* next;  // [2] fetch counters of the two pools
+};
+
+template <int kSrc, int kPhase>
+__global__ void __launch_bounds__(kBlock) k_bounce_phase(BatchScene bs, PathStage ps, int in, PoolBufs pb) {
+  const SceneView& s = bs.v;
+  const Opts& op = bs.op;
+  int md = op.primary_only ? 1 : min(op.max_depth, kMaxDepth);
+  const float3 Le = ld3(s.radiance);
+  unsigned long long count = ps.count[in];
+  const SecPathState* src = reinterpret_cast<const SecPathState*>(ps.path[in]);
+  for (unsigned long long base = (unsigned long long)blockIdx.x * kBlock; base < count;
+       base += (unsigned long long)gridDim.x * kBlock) {
+    unsigned long long e = base + threadIdx.x;
+    bool push = false;
+    SecPathState st;
+    if (e < count) {
+      st = src[e];
+      unsigned long long q = (uint32_t)st.e.x;
+      uint32_t c0, c1, pass;
+      if (kSrc == kSrcSecondary) {
+        unsigned long long item = bs.sec_queue[q];
+        int64_t i = (int64_t)(item >> 3);
+        c0 = (uint32_t)(i / op.spp);
+        c1 = (uint32_t)(i % op.spp);
+        bool nee_slot = q >= (unsigned long long)md * ((unsigned long long)s.W * s.H * op.spp);
+        pass = (nee_slot ? kPassNeeBase : kPassSecondaryBase) + (uint32_t)(item & 7u);
+      } else if (kSrc == kSrcPrimary) {
+        c0 = bs.order ? (uint32_t)bs.order[q] : (uint32_t)q;
+        c1 = 0u;
+        pass = kPassPrimaryEdge;
+      } else {
+        c0 = (uint32_t)(q / (unsigned long long)op.spp);
+        c1 = (uint32_t)(q % (unsigned long long)op.spp);
+        pass = kPassInterior;
+      }
+      int bb = st.e.w & 255;
+      bool pending = (st.e.w & kPathPending) != 0;
+      bool alive[2] = {(st.e.w & 256) != 0, (st.e.w & 512) != 0};
+      float d[2][3] = {{st.a.x, st.a.y, st.a.z}, {st.b.x, st.b.y, st.b.z}};
+      float3 beta[2] = {make_float3(st.a.w, st.b.w, st.c.x), make_float3(st.c.y, st.c.z, st.c.w)};
+      Hit h[2];
+      h[0].tri = st.e.y; h[0].b1 = st.d.x; h[0].b2 = st.d.y; h[0].t = 0.f;
+      h[1].tri = st.e.z; h[1].b1 = st.d.z; h[1].b2 = st.d.w; h[1].t = 0.f;
+      if (kPhase == 0) {
+        // the pending rays leave the previous vertex (its FP32 hit point)
+        float4* r = pb.crec + (size_t)kClosestRecF4 * e;
+        for (int k = 0; k < 2; ++k) {
+          float o[3] = {0.f, 0.f, 0.f};
+          bool act = pending && alive[k];
+          if (act) {
+            Vertex xo;
+            load_vertex(s, h[k].tri, h[k].b1, h[k].b2, d[k], xo);
+            for (int j = 0; j < 3; ++j) o[j] = xo.p[j];
+          }
+          r[2 * k] = make_float4(o[0], o[1], o[2], __int_as_float(act ? h[k].tri : -1));
+          r[2 * k + 1] = make_float4(d[k][0], d[k][1], d[k][2], act ? 1.0f : 0.0f);
+        }
+      } else {
+        if (pending)
+          for (int k = 0; k < 2; ++k) {
+            if (!alive[k]) continue;
+            int4 hv = pb.hits[2 * e + k];
+            h[k].tri = hv.x;
+            h[k].t = __int_as_float(hv.y);
+            h[k].b1 = __int_as_float(hv.z);
+            h[k].b2 = __int_as_float(hv.w);
+          }
+        Vertex x[2];
+        float3 alb[2];
+        for (int k = 0; k < 2; ++k) {
+          alb[k] = zero3();
+          if (!alive[k]) continue;
+          if (h[k].tri < 0) { alive[k] = false; continue; }
+          load_vertex(s, h[k].tri, h[k].b1, h[k].b2, d[k], x[k]);
+          alb[k] = ld3(s.albedo + 3 * x[k].k);
+        }
+        float n32[2][3];
+        for (int k = 0; k < 2; ++k)
+          if (alive[k]) shading_normal32(x[k], n32[k]);
+        LightSample ls;
+        float sd[2][3] = {{0.f, 0.f, 1.f}, {0.f, 0.f, 1.f}};
+        if (s.L > 0 && (alive[0] || alive[1])) {
+          uint4 r = rng4(op.key, c0, c1, kLight, (uint32_t)bb, pass, op.scene_id);
+          sample_light(s, r, ls);
+          for (int k = 0; k < 2; ++k)
+            if (alive[k])
+              for (int j = 0; j < 3; ++j) sd[k][j] = fs(ls.y[j], x[k].p[j]);
+        }
+        if (kPhase == 1) {
+          float4* r = pb.arec + (size_t)kAnyRecF4 * e;
+          bool act[2] = {s.L > 0 && alive[0], s.L > 0 && alive[1]};
+          for (int k = 0; k < 2; ++k) {
+            r[2 * k] = make_float4(act[k] ? x[k].p[0] : 0.f, act[k] ? x[k].p[1] : 0.f, act[k] ? x[k].p[2] : 0.f,
+                                   __int_as_float(act[k] ? x[k].k : -1));
+            r[2 * k + 1] = make_float4(sd[k][0], sd[k][1], sd[k][2], __int_as_float(act[k] ? ls.lt : -1));
+          }
+          r[4] = make_float4(act[0] ? 1.f : 0.f, act[1] ? 1.f : 0.f, 0.f, 0.f);
+        } else {
+          int vis = 0;
+          if (s.L > 0 && (alive[0] || alive[1])) {
+            int oc = pb.occ[e];
+            bool occ[2] = {(oc & 1) != 0, (oc & 2) != 0};
+            float* lr = ps.lr + (kSrc == kSrcRender ? 3 : 6) * q;
+            for (int k = 0; k < 2; ++k)
+              if (alive[k] && !occ[k]) {
+                float g = nee_geometry(s, f3(x[k].p), f3(n32[k]), ls);
+                float3 acc = make_float3(lr[3 * k], lr[3 * k + 1], lr[3 * k + 2]);
+                nee_add(acc, kInvPi * g, beta[k] * alb[k] * Le);
+                lr[3 * k] = acc.x;
+                lr[3 * k + 1] = acc.y;
+                lr[3 * k + 2] = acc.z;
+                if (kSrc == kSrcRender) vis = 1;
+              }
+          }
+          if (kSrc == kSrcRender && alive[0] && bs.tape_tri) {
+            const int64_t n = (int64_t)s.W * s.H * op.spp;
+            bs.tape_tri[(int64_t)bb * n + (int64_t)q] = x[0].k | (vis << 31);
+            bs.tape_bary[(int64_t)bb * n + (int64_t)q] = make_float2(h[0].b1, h[0].b2);
+          }
+          if ((alive[0] || alive[1]) && bb + 1 < md) {
+            uint4 r = rng4(op.key, c0, c1, kBsdf, (uint32_t)bb, pass, op.scene_id);
+            for (int k = 0; k < 2; ++k) {
+              if (!alive[k]) continue;
+              float nd[3];
+              cosine_dir(n32[k], u01f(r.x), u01f(r.y), nd);
+              if (!(dot(f3(n32[k]), f3(nd)) > 0.f)) { alive[k] = false; continue; }
+              beta[k] = beta[k] * alb[k];
+              for (int j = 0; j < 3; ++j) d[k][j] = nd[j];
+            }
+            if (alive[0] || alive[1]) {
+              push = true;
+              st.a = make_float4(d[0][0], d[0][1], d[0][2], beta[0].x);
+              st.b = make_float4(d[1][0], d[1][1], d[1][2], beta[0].y);
+              st.c = make_float4(beta[0].z, beta[1].x, beta[1].y, beta[1].z);
+              st.d = make_float4(h[0].b1, h[0].b2, h[1].b1, h[1].b2);
+              st.e = make_int4(st.e.x, alive[0] ? h[0].tri : -1, alive[1] ? h[1].tri : -1,
+                               (bb + 1) | (alive[0] ? 256 : 0) | (alive[1] ? 512 : 0) | kPathPending);
+            }
+          }
+        }
+      }
+    }
+    if (kPhase == 2) path_push(ps, in ^ 1, push, st);
+  }
+}
+
+// One continuation level through the pools: phase 0, closest-hit pool,
+// phase 1, any-hit pool, phase 2 (entries read from buffer `in`).
+template <int kSrc>
+cudaError_t launch_bounce_level(const BatchScene& bs, const PathStage& ps, int in, const PoolBufs& pb,
+                                int64_t grid, int pool_grid, const char* name, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(ps.count + (in ^ 1), 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pb.next, 0, 2 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  unsigned g = (unsigned)std::max<int64_t>(grid, 1);
+  ProfToken pt = prof_begin(name, st);
+  k_bounce_phase<kSrc, 0><<<g, kBlock, 0, st>>>(bs, ps, in, pb);
+  k_pool_closest<<<pool_grid, 256, 0, st>>>(bs.v, pb.crec, ps.count + in, pb.hits, pb.next);
+  k_bounce_phase<kSrc, 1><<<g, kBlock, 0, st>>>(bs, ps, in, pb);
+  k_pool_any<<<pool_grid, 256, 0, st>>>(bs.v, pb.arec, ps.count + in, pb.occ, pb.next + 1);
+  k_bounce_phase<kSrc, 2><<<g, kBlock, 0, st>>>(bs, ps, in, pb);
+  prof_end(pt, st);
+  return cudaGetLastError();
+}
+
+// Resident CTAs of the pool kernels on the device (a persistent launch).
+static int pool_grid_size() {
+  static int g = 0;
+  if (g == 0) {
+    int dev = 0, sms = 0, b1 = 0, b2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_pool_closest, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_pool_any, 256, 0);
+    g = std::max(1, sms) * std::max(1, std::min(b1, b2));
+  }
+  return g;
+}
+
+__host__ __forceinline__ PoolBufs pool_of(const BatchScene& b) {
+  return PoolBufs{b.pool_crec, b.pool_hits, b.pool_arec, b.pool_occ, b.pool_next};
+}
+
 // The render beyond one vertex in stages.  k_render_first: the first vertex
 // of every camera path with the warp-cooperative traversal (the lanes of a
 // warp hold one pixel's samples, so their rays are coherent), its tape entry
@@ -3011,8 +3209,19 @@ cudaError_t launch_render(const drt_scene* sc, const Opts& op, float* image, drt
     bs.tape_tri = tt;
     bs.tape_bary = tb;
     int64_t grid_p = std::min<int64_t>((n + kBlock - 1) / kBlock, 152 * 8);
+    const PoolScratch& pl = sc->pool;
+    bool pooled = pl.cap >= n;
+    if (pooled) {
+      bs.pool_crec = pl.crec; bs.pool_hits = pl.hits; bs.pool_arec = pl.arec; bs.pool_occ = pl.occ;
+      bs.pool_next = pl.next; bs.pool_cap = pl.cap;
+    }
     for (int level = 0; level + 1 < md; ++level) {
       int in = level & 1;
+      if (pooled) {
+        e = launch_bounce_level<kSrcRender>(bs, ps, in, pool_of(bs), grid_p, pool_grid_size(), "render_bounce", st);
+        if (e != cudaSuccess) return e;
+        continue;
+      }
       e = cudaMemsetAsync(rs->count + (in ^ 1), 0, sizeof(unsigned long long), st);
       if (e != cudaSuccess) return e;
       DRT_PROF_LAUNCH("render_bounce", st,
@@ -3083,8 +3292,15 @@ cudaError_t launch_secondary_apart(const BatchScene& b, cudaStream_t st) {
   int64_t grid_p = std::min<int64_t>((b.sec_path_cap + kBlock - 1) / kBlock, 152 * 8);
   t.v.counters = counter_slot(kSlotBwdSecBounce);
   PathStage ps{{b.sec_path[0], b.sec_path[1]}, b.sec_path_count, b.sec_lr};
+  bool pooled = b.pool_crec && b.pool_cap >= b.sec_path_cap;
   for (int level = 0; level + 1 < md; ++level) {
     int in = level & 1;
+    if (pooled) {
+      e = launch_bounce_level<kSrcSecondary>(t, ps, in, pool_of(b), grid_p, pool_grid_size(),
+                                             "backward_secondary_bounce", st);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     e = cudaMemsetAsync(b.sec_path_count + (in ^ 1), 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     DRT_PROF_LAUNCH("backward_secondary_bounce", st,
@@ -3179,6 +3395,11 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
       bsd.sec_path[1] = secs->path[1];
       bsd.sec_path_count = secs->path_count;
       bsd.sec_path_cap = secondary_path_capacity(sc->W, sc->H, op);
+      const PoolScratch& pl = sc->pool;
+      if (pl.cap >= bsd.sec_path_cap) {
+        bsd.pool_crec = pl.crec; bsd.pool_hits = pl.hits; bsd.pool_arec = pl.arec; bsd.pool_occ = pl.occ;
+        bsd.pool_next = pl.next; bsd.pool_cap = pl.cap;
+      }
     }
     cudaError_t e = cudaMemsetAsync(secs->dp, 0, sizeof(float) * 3 * bsd.sec_cap, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(secs->count, 0, sizeof(unsigned long long) * kSecCounters, st);
@@ -3248,8 +3469,20 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
     t.op = op;
     t.order = order;
     int64_t grid_p = std::min<int64_t>((n_edge + kBlock - 1) / kBlock, 152 * 8);
+    const PoolScratch& pl = sc->pool;
+    bool pooled = pl.cap >= n_edge;
+    if (pooled) {
+      t.pool_crec = pl.crec; t.pool_hits = pl.hits; t.pool_arec = pl.arec; t.pool_occ = pl.occ;
+      t.pool_next = pl.next; t.pool_cap = pl.cap;
+    }
     for (int level = 0; level + 1 < md; ++level) {
       int in = level & 1;
+      if (pooled) {
+        e = launch_bounce_level<kSrcPrimary>(t, ps, in, pool_of(t), grid_p, pool_grid_size(),
+                                             "backward_primary_bounce", st);
+        if (e != cudaSuccess) return e;
+        continue;
+      }
       e = cudaMemsetAsync(prims->count + (in ^ 1), 0, sizeof(unsigned long long), st);
       if (e != cudaSuccess) return e;
       DRT_PROF_LAUNCH("backward_primary_bounce", st,
