@@ -516,7 +516,7 @@ drt_status ensure_pool(drt_scene* s, int64_t cap, cudaStream_t st) {
   if (a == DRT_OK) a = dalloc_n(&b.hits, 2 * (size_t)cap);
   if (a == DRT_OK) a = dalloc_n(&b.arec, (size_t)drt::kAnyRecF4 * cap);
   if (a == DRT_OK) a = dalloc_n(&b.occ, (size_t)cap);
-  if (a == DRT_OK) a = dalloc_n(&b.next, 2);
+  if (a == DRT_OK) a = dalloc_n(&b.next, 2);  // the fetch counters of the two pools
   if (a != DRT_OK) {
     dfree(b.crec);
     dfree(b.hits);

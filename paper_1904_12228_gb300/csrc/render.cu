@@ -1308,22 +1308,12 @@ __device__ __forceinline__ bool secondary_sides(const SceneView& s, const Opts& 
   return gm.act[0] || gm.act[1];
 }
 
-// The side rays of the secondary edge sample at vertex b: the sample's edge,
-// point and side directions (secondary_sides), both side rays traced in one
-// traversal, and which sides count: a side counts when its hit lies above
-// the shading horizon and, for the direct part, on the front face of a
-// light, both decided in FP32 in a fixed order from the hit point, so the
-// oracle takes the same decisions.  False: no side counts.
-template <int kSel>
-__device__ __forceinline__ bool secondary_side_hits(const SceneView& s, const Opts& op, uint32_t c0, uint32_t c1,
-                                                    int b, int md, const Vertex& x, float3 n, SecGeom& gm,
-                                                    Hit hms[2], bool front[2], const int2* pre = nullptr,
-                                                    const int4* pre4 = nullptr) {
-  front[0] = front[1] = false;
-  if (!secondary_sides<kSel>(s, op, c0, c1, b, md, x, n, gm, pre, pre4)) return false;
+// Which sides of a secondary edge sample count, given the side hits hms.
+__device__ __forceinline__ bool secondary_side_decide(const SceneView& s, const Vertex& x, SecGeom& gm, Hit hms[2],
+                                                      bool front[2]) {
   float (*dsd)[3] = gm.dsd;
   bool* act = gm.act;
-  trace_closest2(s, x.p, dsd[0], x.p, dsd[1], act[0], act[1], x.k, x.k, hms[0], hms[1]);
+  front[0] = front[1] = false;
   for (int side = 0; side < 2; ++side) {
     if (!act[side] || hms[side].tri < 0) { act[side] = false; continue; }
     Vertex mv;
@@ -1337,6 +1327,23 @@ __device__ __forceinline__ bool secondary_side_hits(const SceneView& s, const Op
   // evaluations a finite offset apart would be an O(eps) residue)
   if (act[0] && act[1] && hms[0].tri == hms[1].tri) act[0] = act[1] = false;
   return act[0] || act[1];
+}
+
+// The side rays of the secondary edge sample at vertex b: the sample's edge,
+// point and side directions (secondary_sides), both side rays traced in one
+// traversal, and which sides count: a side counts when its hit lies above
+// the shading horizon and, for the direct part, on the front face of a
+// light, both decided in FP32 in a fixed order from the hit point, so the
+// oracle takes the same decisions.  False: no side counts.
+template <int kSel>
+__device__ __forceinline__ bool secondary_side_hits(const SceneView& s, const Opts& op, uint32_t c0, uint32_t c1,
+                                                    int b, int md, const Vertex& x, float3 n, SecGeom& gm,
+                                                    Hit hms[2], bool front[2], const int2* pre = nullptr,
+                                                    const int4* pre4 = nullptr) {
+  front[0] = front[1] = false;
+  if (!secondary_sides<kSel>(s, op, c0, c1, b, md, x, n, gm, pre, pre4)) return false;
+  trace_closest2(s, x.p, gm.dsd[0], x.p, gm.dsd[1], gm.act[0], gm.act[1], x.k, x.k, hms[0], hms[1]);
+  return secondary_side_decide(s, x, gm, hms, front);
 }
 
 // The edge term's contributions of a secondary edge sample whose side hits

@@ -44,7 +44,7 @@ __device__ __forceinline__ void pool_fetch(unsigned long long* next, unsigned lo
   }
 }
 
-__global__ void __launch_bounds__(256) k_pool_closest(SceneView s, const float4* rec, const unsigned long long* count_ptr,
+__global__ void __launch_bounds__(256, 4) k_pool_closest(SceneView s, const float4* rec, const unsigned long long* count_ptr,
                                                       int4* hits, unsigned long long* next) {
   const unsigned long long count = *count_ptr;
   bool have = false, done = false;
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(256) k_pool_closest(SceneView s, const float4*
   }
 }
 
-__global__ void __launch_bounds__(256) k_pool_any(SceneView s, const float4* rec, const unsigned long long* count_ptr,
+__global__ void __launch_bounds__(256, 4) k_pool_any(SceneView s, const float4* rec, const unsigned long long* count_ptr,
                                                   int* occ, unsigned long long* next) {
   const unsigned long long count = *count_ptr;
   const float tmax = kShadowTmax;
