@@ -183,6 +183,17 @@ typedef struct {
   float nee_width;              /* sec_nee: billboard width; <= 0 selects the L2 norm over the
                                    three coordinates of 2 % of the vertices' mean absolute
                                    deviation, computed on the backward call's stream */
+  int32_t spp_per_pass;         /* > 0 and < spp: the interior samples in P = spp / spp_per_pass passes
+                                   (spp must be a multiple), which bounds the tape to one pass (the
+                                   checkpoint of Sec. 5.4 then holds spp_per_pass paths per pixel).
+                                   Pass p draws spp_per_pass samples per pixel with the Philox key
+                                   seed + p * 0x9E3779B97F4A7C15 (mod 2^64); the image is the mean of
+                                   the passes' images and the gradient the sum of their gradients
+                                   with d_image / P.  drt_render returns the last pass's tape;
+                                   drt_render_backward renders every pass again into scene-owned
+                                   scratch (the tape argument may be NULL) and runs the primary edge
+                                   term once with the full edge_spp and the key seed.  0: one pass.
+                                   The batch and the allocation-free backward take 0 only. */
 } drt_render_opts;
 
 /* Gradient outputs: device or host arrays, each may be NULL (not wanted).
@@ -270,8 +281,9 @@ drt_status drt_tape_free(drt_context* ctx, drt_tape* tape);
  *   - Only the length proposal for primary edges: opts->proposal != 0 is
  *     DRT_ERR_INVALID_ARG (the mixture proposals build their CDF in
  *     scene-owned buffers that grow on demand).
- *   - No next-event estimation for edges: opts->sec_nee != 0 is
- *     DRT_ERR_INVALID_ARG (its samples are queued in scene-owned scratch).
+ *   - No next-event estimation for edges and one sample pass: opts->sec_nee
+ *     != 0 or 0 < spp_per_pass < spp is DRT_ERR_INVALID_ARG (scene-owned
+ *     scratch).
  *   - With the edge hierarchy (sec_sampler 1) the hierarchy's buffers must
  *     exist from an earlier drt_render_backward with it on this scene, else
  *     DRT_ERR_STATE; a scene changed since is rebuilt in place.

@@ -139,6 +139,9 @@ void free_scene_buffers(drt_scene* s) {
                   s->et_nodes, s->et_leaf, s->et_keys, s->et_keys2, s->et_hist, s->et_hist_tmp, s->et_vals,
                   s->et_vals2, s->et_parent, s->et_leaf_parent, s->et_flags, s->et_child};
   for (void* b : bufs) dfree(b);
+  dfree(s->pass_img);
+  dfree(s->pass_dimg);
+  drt_tape_free(nullptr, s->pass_tape);
 }
 
 drt_status make_opts(const drt_render_opts* o, drt::Opts* op) {
@@ -174,6 +177,9 @@ drt_status make_opts(const drt_render_opts* o, drt::Opts* op) {
     return fail(DRT_ERR_INVALID_ARG, "sec_nee needs sec_sampler 0 and sec_point 0");
   if (!(o->nee_width == o->nee_width) || o->nee_width == INFINITY)
     return fail(DRT_ERR_INVALID_ARG, "nee_width must be finite");
+  if (o->spp_per_pass < 0) return fail(DRT_ERR_INVALID_ARG, "spp_per_pass must be >= 0");
+  if (o->spp_per_pass > 0 && o->spp_per_pass < o->spp && o->spp % o->spp_per_pass != 0)
+    return fail(DRT_ERR_INVALID_ARG, "spp (%d) must be a multiple of spp_per_pass (%d)", o->spp, o->spp_per_pass);
   op->nee = o->sec_nee;
   op->nee_hw = o->nee_width > 0.0f ? 0.5f * o->nee_width : 0.0f;
   op->nee_hw_dev = nullptr;
@@ -530,6 +536,17 @@ drt_status ensure_pool(drt_scene* s, int64_t cap, cudaStream_t st) {
   return DRT_OK;
 }
 
+// Philox key of sample pass p (spp_per_pass): the golden-ratio increment.
+uint64_t pass_seed(uint64_t seed, int p) { return seed + (uint64_t)p * 0x9E3779B97F4A7C15ull; }
+
+// One pass's image and the scaled loss adjoint, scene-owned.
+drt_status ensure_pass_buffers(drt_scene* s, bool dimg) {
+  size_t n = 3 * (size_t)s->W * s->H;
+  if (!s->pass_img) DRT_TRY(dalloc_n(&s->pass_img, n));
+  if (dimg && !s->pass_dimg) DRT_TRY(dalloc_n(&s->pass_dimg, n));
+  return DRT_OK;
+}
+
 drt_status drt_render(drt_context* ctx, drt_scene* s, const drt_render_opts* opts, float* image, drt_tape** tape,
                       void* stream) {
   NvtxRange nvtx_range("drt_render");
@@ -537,6 +554,27 @@ drt_status drt_render(drt_context* ctx, drt_scene* s, const drt_render_opts* opt
   drt::Opts op;
   DRT_TRY(make_opts(opts, &op));
   cudaStream_t st = (cudaStream_t)stream;
+  if (opts->spp_per_pass > 0 && opts->spp_per_pass < opts->spp) {
+    // sample passes: the image is the mean of the passes' images
+    int P = opts->spp / opts->spp_per_pass;
+    Staged img;
+    DRT_TRY(stage(img, image, 12 * (size_t)s->W * s->H, false, true, st));
+    drt_status r = ensure_pass_buffers(s, false);
+    for (int p = 0; p < P && r == DRT_OK; ++p) {
+      drt_render_opts o = *opts;
+      o.spp = opts->spp_per_pass;
+      o.spp_per_pass = 0;
+      o.seed = pass_seed(opts->seed, p);
+      r = drt_render(ctx, s, &o, s->pass_img, p + 1 == P ? tape : nullptr, stream);
+      if (r == DRT_OK) {
+        cudaError_t e = drt::launch_axpy((float*)img.dev, s->pass_img, (float)(1.0 / P),
+                                         3 * (int64_t)s->W * s->H, p == 0, st);
+        if (e != cudaSuccess) r = fail(DRT_ERR_CUDA, "pass accumulation: %s", cudaGetErrorString(e));
+      }
+    }
+    drt_status u = unstage(&img, 1, st);
+    return r != DRT_OK ? r : u;
+  }
   drt_tape* tp = nullptr;
   if (tape) {
     int64_t n = (int64_t)s->W * s->H * op.spp;
@@ -620,6 +658,38 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
   if (!ctx || !s || !d_image || !grads) return fail(DRT_ERR_INVALID_ARG, "NULL argument");
   drt::Opts op;
   DRT_TRY(make_opts(opts, &op));
+  if (opts->spp_per_pass > 0 && opts->spp_per_pass < opts->spp) {
+    // sample passes: the primary edge term once (full edge budget, key seed);
+    // the interior and secondary terms per pass, each pass rendered again
+    // into scene-owned scratch, with d_image / P
+    cudaStream_t st = (cudaStream_t)stream;
+    int P = opts->spp / opts->spp_per_pass;
+    int terms = opts->terms == 0 ? 7 : opts->terms;
+    if (terms & 2) {
+      drt_render_opts o = *opts;
+      o.spp_per_pass = 0;
+      o.terms = 2;
+      DRT_TRY(drt_render_backward(ctx, s, nullptr, &o, d_image, grads, stream));
+    }
+    if (!(terms & 5)) return DRT_OK;
+    DRT_TRY(ensure_pass_buffers(s, true));
+    Staged w;
+    DRT_TRY(stage(w, d_image, 12 * (size_t)s->W * s->H, true, false, st));
+    cudaError_t e = drt::launch_axpy(s->pass_dimg, (const float*)w.dev, (float)(1.0 / P), 3 * (int64_t)s->W * s->H,
+                                     true, st);
+    drt_status r = unstage(&w, 1, st);
+    if (e != cudaSuccess) return fail(DRT_ERR_CUDA, "pass adjoint: %s", cudaGetErrorString(e));
+    for (int p = 0; p < P && r == DRT_OK; ++p) {
+      drt_render_opts o = *opts;
+      o.spp = opts->spp_per_pass;
+      o.spp_per_pass = 0;
+      o.seed = pass_seed(opts->seed, p);
+      o.terms = terms & 5;
+      r = drt_render(ctx, s, &o, s->pass_img, &s->pass_tape, stream);
+      if (r == DRT_OK) r = drt_render_backward(ctx, s, s->pass_tape, &o, s->pass_dimg, grads, stream);
+    }
+    return r;
+  }
   if (!op.primary_only && op.max_depth > 1 && (op.terms & 5) && !tape)
     return fail(DRT_ERR_INVALID_ARG, "interior or secondary terms with max_depth > 1 need the tape of the forward pass");
   if (tape) {

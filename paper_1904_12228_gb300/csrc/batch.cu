@@ -416,6 +416,8 @@ drt_status drt_batch_create(drt_context* ctx, const drt_batch_item* items, int32
   if (op.sec_sampler != 0) return bfail(DRT_ERR_INVALID_ARG, "a batch samples secondary edges by length (sec_sampler 0)");
   if (op.sec_point != 0) return bfail(DRT_ERR_INVALID_ARG, "a batch samples the point on a secondary edge uniformly (sec_point 0)");
   if (op.nee != 0) return bfail(DRT_ERR_INVALID_ARG, "a batch takes no next-event estimation for edges (sec_nee 0)");
+  if (opts->spp_per_pass > 0 && opts->spp_per_pass < opts->spp)
+    return bfail(DRT_ERR_INVALID_ARG, "a batch takes one sample pass (spp_per_pass 0)");
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != ctx->device)
     return bfail(DRT_ERR_STATE, "the context's device must be the current device");

@@ -139,6 +139,10 @@ struct drt_scene {
   uint64_t seg_generation = ~0ull;
   int sort_blocks = 0;
   float* nee_hw = nullptr;   // billboard half width derived from the vertices (next-event estimation for edges)
+  // sample passes (spp_per_pass): one pass's image, the scaled loss adjoint and the pass tape
+  float* pass_img = nullptr;
+  float* pass_dimg = nullptr;
+  drt_tape* pass_tape = nullptr;
   drt::SceneView view() const;
 };
 
@@ -215,6 +219,8 @@ int64_t secondary_path_capacity(int W, int H, const Opts& op);
 // and *b.sec_count zeroed by the caller)
 cudaError_t launch_secondary_apart(const BatchScene& b, cudaStream_t st);
 int64_t backward_partial_rows(const drt_scene* s, const Opts& op);
+// out = in * scale (first) or out + in * scale, n floats
+cudaError_t launch_axpy(float* out, const float* in, float scale, int64_t n, bool first, cudaStream_t st);
 // billboard half width of next-event estimation for edges from the vertices
 cudaError_t launch_nee_half_width(const float* verts, int V, float* out, cudaStream_t st);
 cudaError_t launch_debug_closest(const drt_scene* s, int64_t n, const float* o, const float* d, int32_t* tri,

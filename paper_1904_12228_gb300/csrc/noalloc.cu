@@ -72,6 +72,8 @@ drt_status drt_render_backward_noalloc(drt_context* ctx, drt_scene* s, const drt
   if (opts->proposal != 0) return fail_noalloc(DRT_ERR_INVALID_ARG, "drt_render_backward_noalloc supports proposal 0");
   if (opts->sec_nee != 0)
     return fail_noalloc(DRT_ERR_INVALID_ARG, "drt_render_backward_noalloc supports sec_nee 0 (it has no queue)");
+  if (opts->spp_per_pass > 0 && opts->spp_per_pass < opts->spp)
+    return fail_noalloc(DRT_ERR_INVALID_ARG, "drt_render_backward_noalloc takes one sample pass (spp_per_pass 0)");
   op.proposal = 0;
   op.seg_log = nullptr;
   if (!op.primary_only && op.max_depth > 1 && (op.terms & 5) && !tape) {

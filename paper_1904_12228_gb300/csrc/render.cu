@@ -3246,6 +3246,19 @@ cudaError_t launch_render(const drt_scene* sc, const Opts& op, float* image, drt
   return cudaGetLastError();
 }
 
+__global__ void k_axpy(float* out, const float* in, float scale, int64_t n, int first) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float v = in[i] * scale;
+  out[i] = first ? v : out[i] + v;
+}
+
+cudaError_t launch_axpy(float* out, const float* in, float scale, int64_t n, bool first, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_axpy<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, st>>>(out, in, scale, n, first ? 1 : 0);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_nee_half_width(const float* verts, int V, float* out, cudaStream_t st) {
   DRT_PROF_LAUNCH("nee_half_width", st, k_nee_half_width<<<1, 1024, 0, st>>>(verts, V, out));
   return cudaGetLastError();

@@ -54,7 +54,7 @@ class RenderOpts(ctypes.Structure):
                 ("sec_sampler", ctypes.c_int32), ("sec_tree_samples", ctypes.c_int32), ("sec_point", ctypes.c_int32),
                 ("pix_begin", ctypes.c_int32), ("pix_end", ctypes.c_int32), ("edge_begin", ctypes.c_int64),
                 ("edge_end", ctypes.c_int64), ("aov", ctypes.c_int32), ("sec_nee", ctypes.c_int32),
-                ("nee_width", ctypes.c_float)]
+                ("nee_width", ctypes.c_float), ("spp_per_pass", ctypes.c_int32)]
 
 
 class MlpWeights(ctypes.Structure):
@@ -201,7 +201,7 @@ def _stream(stream):
 
 def make_opts(spp, edge_spp=None, max_depth=1, primary_only=False, seed=0, eps_rel=0.0, terms=0,
               seg_weights=None, seg_log=None, seg_scores=None, scene_id=0, sec_tree_samples=0,
-              sec_point=0, pixels=None, edges=None, aov=0, sec_nee=0, nee_width=0.0) -> RenderOpts:
+              sec_point=0, pixels=None, edges=None, aov=0, sec_nee=0, nee_width=0.0, spp_per_pass=0) -> RenderOpts:
     """seg_weights: a CUDA float32 tensor of per-segment weights selects the
     mixture proposal 1; seg_scores: per-segment network scores select the
     mixture proposal 2.  The tensor must stay alive until the backward call
@@ -214,7 +214,11 @@ def make_opts(spp, edge_spp=None, max_depth=1, primary_only=False, seed=0, eps_r
     (default: all).  aov: geometry buffer of the first hit (AOV_ALBEDO,
     AOV_POSITION, AOV_NORMAL, AOV_DEPTH; 0: the image).  sec_nee=1 adds
     next-event estimation for edges (Sec. 5.3.3) beside the length sampler,
-    with billboards of width nee_width (<= 0: derived from the vertices)."""
+    with billboards of width nee_width (<= 0: derived from the vertices).
+    spp_per_pass = k (0 < k < spp, spp a multiple of k) renders and
+    differentiates the interior samples in spp / k passes of k samples per
+    pixel with the Philox keys seed + p 0x9E3779B97F4A7C15, so the tape
+    holds one pass."""
     if seg_weights is not None and seg_scores is not None:
         raise ValueError("give seg_weights or seg_scores, not both")
     mode, w = (1, seg_weights) if seg_weights is not None else ((2, seg_scores) if seg_scores is not None else (0, None))
@@ -227,7 +231,7 @@ def make_opts(spp, edge_spp=None, max_depth=1, primary_only=False, seed=0, eps_r
                       1 if sec_tree_samples > 0 else 0, int(sec_tree_samples), int(sec_point),
                       int(pixels[0]) if pixels else 0, int(pixels[1]) if pixels else 0,
                       int(edges[0]) if edges else 0, int(edges[1]) if edges else 0, int(aov), int(sec_nee),
-                      float(nee_width))
+                      float(nee_width), int(spp_per_pass))
 
 
 class Context:
