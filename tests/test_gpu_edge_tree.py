@@ -139,3 +139,30 @@ def test_hierarchy_options_are_checked(env):
         S.backward(w, drt.make_opts(2, 2, sec_tree_samples=65), d_verts=torch.zeros((3, 3), device="cuda"))
     with pytest.raises(drt.DrtError):  # a batch samples secondary edges by length
         drt.Batch(ctx, [S], [img], drt.make_opts(2, 2, sec_tree_samples=4))
+
+
+def test_noalloc_backward_rebuilds_the_hierarchy_after_an_update(env):
+    """After the vertices and the camera change, the allocation-free backward
+    rebuilds the hierarchy in place (kernel launches into the buffers an
+    earlier backward allocated) and matches the oracle on the new scene."""
+    drt, ctx = env
+    scene = _scene("direct")
+    w = sg.loss_adjoint(5, scene.width, scene.height)
+    S = drt.Scene.from_arrays(ctx, scene)
+    _gpu(drt, ctx, scene, w, 4, 4, 2, 1, 4, 16, S=S)  # allocates the hierarchy's buffers
+    moved = sg.perturb_vertices(scene, 7, sigma=0.02)
+    S.update_vertices(torch.from_numpy(moved).cuda())
+    cam = np.array(scene.cam_to_world, np.float32)
+    cam[:3, 3] += np.array([-0.04, 0.03, 0.01], np.float32)
+    S.update_params(cam_to_world=torch.from_numpy(cam).cuda())
+    opts = drt.make_opts(4, 4, seed=9, terms=4, sec_tree_samples=16)
+    img = torch.zeros((scene.height, scene.width, 3), device="cuda")
+    tape = S.render(img, opts, want_tape=True)
+    got = _zeros(scene)
+    S.backward_noalloc(torch.from_numpy(w).cuda(), opts, tape=tape, **got)
+    torch.cuda.synchronize()
+    assert ctx.check_device() == (0, 0)
+    scene2 = dataclasses.replace(scene, verts=moved, cam_to_world=cam)
+    want, absum, c = oracle.backward(scene2, w, spp=4, edge_spp=4, seed=9, terms=4, sec_tree_samples=16, n_threads=NT,
+                                     contributions=True)
+    _assert_grads(_flat(got), want, absum, "hierarchy noalloc after update", c)

@@ -56,6 +56,49 @@ def test_noalloc_backward_matches_backward_on_consecutive_calls():
     assert ctx.check_device() == (0, 0)
 
 
+def test_noalloc_backward_allocates_nothing_and_records_into_a_graph():
+    """After one warm call the entry point allocates no device memory (free
+    memory unchanged around a call) and records into a CUDA graph captured in
+    global mode, where an allocation or a synchronising call ends the capture
+    with an error; the replayed graph gives the oracle's gradients."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1904_12228_gb300 import drt
+    ctx = drt.Context(0)
+    scene = sg.direct_lighting(1236, width=40, height=28, subdiv=2)
+    S = drt.Scene.from_arrays(ctx, scene)
+    opts = drt.make_opts(8, 8, seed=13)
+    img = torch.zeros((28, 40, 3), device="cuda")
+    tape = S.render(img, opts, want_tape=True)
+    w = torch.from_numpy(sg.loss_adjoint(4, 40, 28)).cuda()
+    got = _zeros(scene)
+    S.backward_noalloc(w, opts, tape=tape, **got)  # warm call
+    torch.cuda.synchronize()
+    for t in got.values():
+        t.zero_()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    S.backward_noalloc(w, opts, tape=tape, **got)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    for t in got.values():
+        t.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="global"):
+        S.backward_noalloc(w, opts, tape=tape, **got)
+    for t in got.values():
+        t.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert ctx.check_device() == (0, 0)
+    want, absum = oracle.backward(scene, w.cpu().numpy(), spp=8, edge_spp=8, seed=13)
+    gr = _flat(*got.values())
+    err = np.abs(gr - want)
+    bound = 1e-4 * np.abs(want) + 1e-6 * absum + 1e-12
+    assert np.all(err <= bound), "%d entries off" % int((err > bound).sum())
+    assert np.abs(gr).max() > 0
+
+
 def test_noalloc_backward_matches_backward_at_depth_two():
     """The allocation-free backward evaluates the secondary edge samples inside
     the path pass; the regular backward queues and traces them apart."""
