@@ -2494,9 +2494,11 @@ cudaError_t launch_bounce_level(const BatchScene& bs, const PathStage& ps, int i
   unsigned g = (unsigned)std::max<int64_t>(grid, 1);
   ProfToken pt = prof_begin(name, st);
   k_bounce_phase<kSrc, 0><<<g, kBlock, 0, st>>>(bs, ps, in, pb);
-  k_pool_closest<<<pool_grid, 256, 0, st>>>(bs.v, pb.crec, ps.count + in, pb.hits, pb.next);
+  // a camera path is one ray per record; an edge sample's two side paths, two
+  constexpr bool kPair = kSrc != kSrcRender;
+  k_pool_closest<kPair><<<pool_grid, 256, 0, st>>>(bs.v, pb.crec, ps.count + in, pb.hits, pb.next);
   k_bounce_phase<kSrc, 1><<<g, kBlock, 0, st>>>(bs, ps, in, pb);
-  k_pool_any<<<pool_grid, 256, 0, st>>>(bs.v, pb.arec, ps.count + in, pb.occ, pb.next + 1);
+  k_pool_any<kPair><<<pool_grid, 256, 0, st>>>(bs.v, pb.arec, ps.count + in, pb.occ, pb.next + 1);
   k_bounce_phase<kSrc, 2><<<g, kBlock, 0, st>>>(bs, ps, in, pb);
   prof_end(pt, st);
   return cudaGetLastError();
@@ -2509,8 +2511,8 @@ static int pool_grid_size() {
     int dev = 0, sms = 0, b1 = 0, b2 = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_pool_closest, 256, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_pool_any, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_pool_closest<true>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_pool_any<true>, 256, 0);
     g = std::max(1, sms) * std::max(1, std::min(b1, b2));
   }
   return g;

@@ -44,6 +44,9 @@ __device__ __forceinline__ void pool_fetch(unsigned long long* next, unsigned lo
   }
 }
 
+// kPair false: every record's second ray is inactive (the camera paths'
+// continuation), and the kernel is compiled for one ray per record.
+template <bool kPair>
 __global__ void __launch_bounds__(256, 4) k_pool_closest(SceneView s, const float4* rec, const unsigned long long* count_ptr,
                                                       int4* hits, unsigned long long* next) {
   const unsigned long long count = *count_ptr;
@@ -63,11 +66,11 @@ __global__ void __launch_bounds__(256, 4) k_pool_closest(SceneView s, const floa
       float4 a = r[0], b = r[1], c = r[2], d = r[3];
       float o0[3] = {a.x, a.y, a.z}, d0[3] = {b.x, b.y, b.z}, o1[3] = {c.x, c.y, c.z}, d1[3] = {d.x, d.y, d.z};
       ray_pre(r0, o0, d0);
-      ray_pre(r1, o1, d1);
+      if (kPair) ray_pre(r1, o1, d1);
       ex0 = __float_as_int(a.w);
       ex1 = __float_as_int(c.w);
       act0 = b.w != 0.0f;
-      act1 = d.w != 0.0f;
+      act1 = kPair && d.w != 0.0f;
       h0.tri = -1; h0.t = INFINITY; h0.b1 = h0.b2 = 0.f;
       h1.tri = -1; h1.t = INFINITY; h1.b1 = h1.b2 = 0.f;
       sp = 0;
@@ -92,7 +95,12 @@ __global__ void __launch_bounds__(256, 4) k_pool_closest(SceneView s, const floa
         float tl0, tr0, tl1, tr1;
         bool hl0, hr0, hl1, hr1;
         slab2(r0, a, b, c, h0.t, &tl0, &hl0, &tr0, &hr0);
-        slab2(r1, a, b, c, h1.t, &tl1, &hl1, &tr1, &hr1);
+        if (kPair) {
+          slab2(r1, a, b, c, h1.t, &tl1, &hl1, &tr1, &hr1);
+        } else {
+          tl1 = tr1 = INFINITY;
+          hl1 = hr1 = false;
+        }
         bool hl = (act0 && hl0) || (act1 && hl1), hr = (act0 && hr0) || (act1 && hr1);
         float tl = fminf(act0 && hl0 ? tl0 : INFINITY, act1 && hl1 ? tl1 : INFINITY);
         float tr = fminf(act0 && hr0 ? tr0 : INFINITY, act1 && hr1 ? tr1 : INFINITY);
@@ -143,6 +151,7 @@ __global__ void __launch_bounds__(256, 4) k_pool_closest(SceneView s, const floa
   }
 }
 
+template <bool kPair>
 __global__ void __launch_bounds__(256, 4) k_pool_any(SceneView s, const float4* rec, const unsigned long long* count_ptr,
                                                   int* occ, unsigned long long* next) {
   const unsigned long long count = *count_ptr;
@@ -162,13 +171,13 @@ __global__ void __launch_bounds__(256, 4) k_pool_any(SceneView s, const float4* 
       float4 a = r[0], b = r[1], c = r[2], d = r[3], f = r[4];
       float o0[3] = {a.x, a.y, a.z}, d0[3] = {b.x, b.y, b.z}, o1[3] = {c.x, c.y, c.z}, d1[3] = {d.x, d.y, d.z};
       ray_pre(r0, o0, d0);
-      ray_pre(r1, o1, d1);
+      if (kPair) ray_pre(r1, o1, d1);
       a0x = __float_as_int(a.w);
       a0y = __float_as_int(b.w);
       a1x = __float_as_int(c.w);
       a1y = __float_as_int(d.w);
       act0 = f.x != 0.0f;
-      act1 = f.y != 0.0f;
+      act1 = kPair && f.y != 0.0f;
       live0 = act0;
       live1 = act1;
       occ0 = occ1 = false;
