@@ -2483,11 +2483,26 @@ __global__ void __launch_bounds__(kBlock) k_bounce_phase(BatchScene bs, PathStag
   }
 }
 
+// Resident CTAs of the pool kernels on the device (a persistent launch).
+template <bool kPair>
+static int pool_grid_size() {
+  static int g = 0;
+  if (g == 0) {
+    int dev = 0, sms = 0, b1 = 0, b2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_pool_closest<kPair>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_pool_any<kPair>, 256, 0);
+    g = std::max(1, sms) * std::max(1, std::min(b1, b2));
+  }
+  return g;
+}
+
 // One continuation level through the pools: phase 0, closest-hit pool,
 // phase 1, any-hit pool, phase 2 (entries read from buffer `in`).
 template <int kSrc>
 cudaError_t launch_bounce_level(const BatchScene& bs, const PathStage& ps, int in, const PoolBufs& pb,
-                                int64_t grid, int pool_grid, const char* name, cudaStream_t st) {
+                                int64_t grid, const char* name, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(ps.count + (in ^ 1), 0, sizeof(unsigned long long), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(pb.next, 0, 2 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
@@ -2496,6 +2511,7 @@ cudaError_t launch_bounce_level(const BatchScene& bs, const PathStage& ps, int i
   k_bounce_phase<kSrc, 0><<<g, kBlock, 0, st>>>(bs, ps, in, pb);
   // a camera path is one ray per record; an edge sample's two side paths, two
   constexpr bool kPair = kSrc != kSrcRender;
+  const int pool_grid = pool_grid_size<kPair>();
   k_pool_closest<kPair><<<pool_grid, 256, 0, st>>>(bs.v, pb.crec, ps.count + in, pb.hits, pb.next);
   k_bounce_phase<kSrc, 1><<<g, kBlock, 0, st>>>(bs, ps, in, pb);
   k_pool_any<kPair><<<pool_grid, 256, 0, st>>>(bs.v, pb.arec, ps.count + in, pb.occ, pb.next + 1);
@@ -2504,19 +2520,6 @@ cudaError_t launch_bounce_level(const BatchScene& bs, const PathStage& ps, int i
   return cudaGetLastError();
 }
 
-// Resident CTAs of the pool kernels on the device (a persistent launch).
-static int pool_grid_size() {
-  static int g = 0;
-  if (g == 0) {
-    int dev = 0, sms = 0, b1 = 0, b2 = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_pool_closest<true>, 256, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_pool_any<true>, 256, 0);
-    g = std::max(1, sms) * std::max(1, std::min(b1, b2));
-  }
-  return g;
-}
 
 __host__ __forceinline__ PoolBufs pool_of(const BatchScene& b) {
   return PoolBufs{b.pool_crec, b.pool_hits, b.pool_arec, b.pool_occ, b.pool_next};
@@ -3227,7 +3230,7 @@ cudaError_t launch_render(const drt_scene* sc, const Opts& op, float* image, drt
     for (int level = 0; level + 1 < md; ++level) {
       int in = level & 1;
       if (pooled) {
-        e = launch_bounce_level<kSrcRender>(bs, ps, in, pool_of(bs), grid_p, pool_grid_size(), "render_bounce", st);
+        e = launch_bounce_level<kSrcRender>(bs, ps, in, pool_of(bs), grid_p, "render_bounce", st);
         if (e != cudaSuccess) return e;
         continue;
       }
@@ -3318,7 +3321,7 @@ cudaError_t launch_secondary_apart(const BatchScene& b, cudaStream_t st) {
   for (int level = 0; level + 1 < md; ++level) {
     int in = level & 1;
     if (pooled) {
-      e = launch_bounce_level<kSrcSecondary>(t, ps, in, pool_of(b), grid_p, pool_grid_size(),
+      e = launch_bounce_level<kSrcSecondary>(t, ps, in, pool_of(b), grid_p,
                                              "backward_secondary_bounce", st);
       if (e != cudaSuccess) return e;
       continue;
@@ -3500,7 +3503,7 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
     for (int level = 0; level + 1 < md; ++level) {
       int in = level & 1;
       if (pooled) {
-        e = launch_bounce_level<kSrcPrimary>(t, ps, in, pool_of(t), grid_p, pool_grid_size(),
+        e = launch_bounce_level<kSrcPrimary>(t, ps, in, pool_of(t), grid_p,
                                              "backward_primary_bounce", st);
         if (e != cudaSuccess) return e;
         continue;

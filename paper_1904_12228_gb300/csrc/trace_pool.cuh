@@ -17,6 +17,13 @@
 
 namespace drt {
 
+// Resident CTAs per SM of the one-ray pools (5: at most 51 registers; of 4,
+// 5 and 6 the fastest on the 200k-triangle depth-3 step).  The two-ray pools
+// run 4 (64 registers).
+#ifndef DRT_POOL1_BLOCKS
+#define DRT_POOL1_BLOCKS 5
+#endif
+
 // Closest-hit record: (o0.xyz, exclude0 bits), (d0.xyz, active0), (o1.xyz,
 // exclude1 bits), (d1.xyz, active1); result: (tri, t bits, b1 bits, b2 bits)
 // per ray, tri -1 for a miss or an inactive ray.
@@ -47,7 +54,7 @@ __device__ __forceinline__ void pool_fetch(unsigned long long* next, unsigned lo
 // kPair false: every record's second ray is inactive (the camera paths'
 // continuation), and the kernel is compiled for one ray per record.
 template <bool kPair>
-__global__ void __launch_bounds__(256, 4) k_pool_closest(SceneView s, const float4* rec, const unsigned long long* count_ptr,
+__global__ void __launch_bounds__(256, kPair ? 4 : DRT_POOL1_BLOCKS) k_pool_closest(SceneView s, const float4* rec, const unsigned long long* count_ptr,
                                                       int4* hits, unsigned long long* next) {
   const unsigned long long count = *count_ptr;
   bool have = false, done = false;
@@ -152,7 +159,7 @@ __global__ void __launch_bounds__(256, 4) k_pool_closest(SceneView s, const floa
 }
 
 template <bool kPair>
-__global__ void __launch_bounds__(256, 4) k_pool_any(SceneView s, const float4* rec, const unsigned long long* count_ptr,
+__global__ void __launch_bounds__(256, kPair ? 4 : DRT_POOL1_BLOCKS) k_pool_any(SceneView s, const float4* rec, const unsigned long long* count_ptr,
                                                   int* occ, unsigned long long* next) {
   const unsigned long long count = *count_ptr;
   const float tmax = kShadowTmax;
