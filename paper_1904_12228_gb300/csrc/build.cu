@@ -514,6 +514,173 @@ __global__ void k_refit(SceneView s, const int32_t* vals, float4* nodes, float4*
   }
 }
 
+// Treelet restructuring of the refitted hierarchy (Karras and Aila, "Fast
+// parallel construction of high-quality bounding volume hierarchies", HPG
+// 2013).  A Morton-order hierarchy splits space, not cost: its nodes often
+// have boxes much larger than a surface-area-guided split would give, and
+// every ray that enters them pays for it.  Bottom-up, each node whose subtree
+// holds at least `gamma` triangles takes a treelet: its two children, then
+// repeatedly the treelet leaf with the largest box replaced by its two
+// children, up to kTreeletLeaves leaves.  Over every subset of those leaves
+// a dynamic program finds the binary topology with the least total surface
+// area of internal nodes (the surface-area cost of the treelet, whose leaves
+// keep their subtrees), and the treelet's internal nodes are rewritten with
+// it.  Leaves, leaf ranges and every box of a leaf are unchanged, so the
+// hierarchy holds the same triangles in the same boxes and every traversal
+// finds the same hits; only the internal topology and its unions change.
+// One warp per triangle climbs the Morton hierarchy's parent links as in
+// k_refit; the second to reach a node processes it.  A treelet rewrites only
+// its root and nodes below it, so a node keeps its children until it is
+// processed, the set of nodes below it never changes, and the links stay
+// valid for the climb (one pass).  `flags` holds, per node, the triangle
+// count of the first child to arrive (zero before).
+constexpr int kTreeletLeaves = 7;
+
+__device__ __forceinline__ float box_area(const float b[6]) {
+  float dx = fmaxf(b[3] - b[0], 0.0f), dy = fmaxf(b[4] - b[1], 0.0f), dz = fmaxf(b[5] - b[2], 0.0f);
+  return dx * dy + dy * dz + dz * dx;
+}
+
+// child slot k (0 left, 1 right) of node n: box and encoding (L2 reads: other
+// threads wrote the nodes below)
+__device__ __forceinline__ void node_child(const float4* nodes, int n, int k, float b[6], int* enc) {
+  const float* f = reinterpret_cast<const float*>(nodes + 4 * (size_t)n);
+  for (int i = 0; i < 6; ++i) b[i] = __ldcg(f + 6 * k + i);
+  int2 ch = __ldcg(reinterpret_cast<const int2*>(f + 12));
+  *enc = k == 0 ? ch.x : ch.y;
+}
+
+// One treelet, by the 32 lanes of a warp together: every lane forms the
+// same treelet (reads only); the subsets' areas, then their best splits, one
+// size at a time, are spread over the lanes (cost, area and split in the
+// warp's shared arrays); lane 0 rewrites the nodes.
+__device__ void restructure_treelet(float4* nodes, int root, float* cost, float* area, unsigned char* split,
+                                    int lane) {
+  float lb[kTreeletLeaves][6];
+  int le[kTreeletLeaves];
+  int inner[kTreeletLeaves - 1];
+  int nl = 2, ni = 1;
+  inner[0] = root;
+  node_child(nodes, root, 0, lb[0], &le[0]);
+  node_child(nodes, root, 1, lb[1], &le[1]);
+  while (nl < kTreeletLeaves) {
+    int best = -1;
+    float best_a = -1.0f;
+    for (int i = 0; i < nl; ++i) {
+      if (le[i] < 0) continue;  // a leaf range stays a leaf
+      float a = box_area(lb[i]);
+      if (a > best_a) { best_a = a; best = i; }
+    }
+    if (best < 0) break;
+    int e = le[best];
+    inner[ni++] = e;
+    node_child(nodes, e, 0, lb[best], &le[best]);
+    node_child(nodes, e, 1, lb[nl], &le[nl]);
+    ++nl;
+  }
+  if (nl < 3) return;  // two leaves: one topology
+  const int full = (1 << nl) - 1;
+  for (int m = lane + 1; m <= full; m += 32) {
+    cost[m] = 0.0f;  // one leaf: its subtree is fixed
+    float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    for (int i = 0; i < nl; ++i)
+      if ((m >> i) & 1)
+        for (int k = 0; k < 3; ++k) {
+          b[k] = fminf(b[k], lb[i][k]);
+          b[3 + k] = fmaxf(b[3 + k], lb[i][3 + k]);
+        }
+    area[m] = box_area(b);
+  }
+  __syncwarp();
+  for (int size = 2; size <= nl; ++size) {
+    for (int m = lane + 1; m <= full; m += 32) {
+      if (__popc(m) != size) continue;
+      // the two parts: p holds m's lowest leaf, q the rest (both non-empty)
+      int low = m & -m, rest = m ^ low;
+      float bc = INFINITY;
+      int bp = low;
+      for (int q = (rest - 1) & rest;; q = (q - 1) & rest) {
+        int p = low | q;
+        float c = cost[p] + cost[m ^ p];
+        if (c < bc) { bc = c; bp = p; }
+        if (q == 0) break;
+      }
+      cost[m] = area[m] + bc;
+      split[m] = (unsigned char)bp;
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    // the full set at the treelet root, each further set of two or more
+    // leaves at the next internal node of the treelet
+    int st_m[kTreeletLeaves], st_n[kTreeletLeaves];
+    int sp = 0, next = 1;
+    st_m[sp] = full;
+    st_n[sp++] = root;
+    while (sp > 0) {
+      --sp;
+      int m = st_m[sp], n = st_n[sp];
+      int part[2] = {split[m], m ^ split[m]};
+      float* f = reinterpret_cast<float*>(nodes + 4 * (size_t)n);
+      int enc[2];
+      for (int k = 0; k < 2; ++k) {
+        int pm = part[k];
+        float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        for (int i = 0; i < nl; ++i)
+          if ((pm >> i) & 1)
+            for (int j = 0; j < 3; ++j) {
+              b[j] = fminf(b[j], lb[i][j]);
+              b[3 + j] = fmaxf(b[3 + j], lb[i][3 + j]);
+            }
+        if ((pm & (pm - 1)) == 0) {
+          enc[k] = le[__ffs(pm) - 1];
+        } else {
+          enc[k] = inner[next++];
+          st_m[sp] = pm;
+          st_n[sp++] = enc[k];
+        }
+        for (int i = 0; i < 6; ++i) f[6 * k + i] = b[i];
+      }
+      reinterpret_cast<int4*>(f)[3] = make_int4(enc[0], enc[1], 0, 0);
+    }
+  }
+  __syncwarp();
+}
+
+// One warp per triangle climbs (lane 0 takes the arrival counters).
+constexpr int kTreeletWarps = 4;
+__global__ void __launch_bounds__(32 * kTreeletWarps) k_treelets(int T, int leaf_max, int gamma, float4* nodes,
+                                                                 const int32_t* parent, const int32_t* leaf_parent,
+                                                                 int32_t* flags, int32_t* err) {
+  __shared__ float s_cost[kTreeletWarps][1 << kTreeletLeaves];
+  __shared__ float s_area[kTreeletWarps][1 << kTreeletLeaves];
+  __shared__ unsigned char s_split[kTreeletWarps][1 << kTreeletLeaves];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pos = blockIdx.x * kTreeletWarps + w;
+  if (pos >= T || T < 2) return;  // uniform across the warp
+  int node = leaf_parent[pos];
+  int size = 1;
+  int climb = 0;
+  while (node >= 0) {
+    if (++climb > T) {
+      if (lane == 0 && err) raise_flag(err, DRT_DEV_REFIT_CAP, pos);
+      return;
+    }
+    int other = 0;
+    if (lane == 0) {
+      __threadfence();
+      other = atomicAdd(flags + node, size);
+    }
+    other = __shfl_sync(0xffffffffu, other, 0);
+    if (other == 0) return;  // the sibling's warp goes on
+    __threadfence();
+    size += other;
+    // nodes inside a leaf range are never traversed
+    if (size > leaf_max && size >= gamma) restructure_treelet(nodes, node, s_cost[w], s_area[w], s_split[w], lane);
+    node = parent[node];
+  }
+}
+
 // Tile segments of primary edge e (same crossing arithmetic as the oracle):
 // calls emit(s0, s1) for each piece in increasing t.
 template <class F>
@@ -980,6 +1147,10 @@ cudaError_t build_bvh(drt_scene* s, cudaStream_t st) {
     DRT_PROF_LAUNCH("karras", st, k_karras<<<(T - 1 + kBlock - 1) / kBlock, kBlock, 0, st>>>(ka, T, s->leaf_max, s->nodes, s->child_orig, s->parent, s->leaf_parent));
   }
   DRT_PROF_LAUNCH("refit", st, k_refit<<<(T + kBlock - 1) / kBlock, kBlock, 0, st>>>(v, va, s->nodes, s->soup, s->child_orig, s->parent, s->leaf_parent, s->flags));
+  if (T > s->leaf_max && T >= kTreeletLeaves) {
+    cudaMemsetAsync(s->flags, 0, sizeof(int32_t) * (T - 1), st);
+    DRT_PROF_LAUNCH("treelets", st, k_treelets<<<(T + kTreeletWarps - 1) / kTreeletWarps, 32 * kTreeletWarps, 0, st>>>(T, s->leaf_max, kTreeletLeaves, s->nodes, s->parent, s->leaf_parent, s->flags, s->ctx->err));
+  }
   return cudaGetLastError();
 }
 
