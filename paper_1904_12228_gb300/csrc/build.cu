@@ -532,9 +532,14 @@ __global__ void k_refit(SceneView s, const int32_t* vals, float4* nodes, float4*
 // k_refit; the second to reach a node processes it.  A treelet rewrites only
 // its root and nodes below it, so a node keeps its children until it is
 // processed, the set of nodes below it never changes, and the links stay
-// valid for the climb (one pass).  `flags` holds, per node, the triangle
+// valid for the climb.  `flags` holds, per node, the triangle
 // count of the first child to arrive (zero before).
 constexpr int kTreeletLeaves = 7;
+// Passes over the hierarchy, the k-th on subtrees of 7 * 2^k triangles or
+// more (of 1, 2 and 3 passes, 2 gave the fastest 200k-triangle depth-3 step).
+#ifndef DRT_TREELET_ROUNDS
+#define DRT_TREELET_ROUNDS 2
+#endif
 
 __device__ __forceinline__ float box_area(const float b[6]) {
   float dx = fmaxf(b[3] - b[0], 0.0f), dy = fmaxf(b[4] - b[1], 0.0f), dz = fmaxf(b[5] - b[2], 0.0f);
@@ -554,8 +559,8 @@ __device__ __forceinline__ void node_child(const float4* nodes, int n, int k, fl
 // same treelet (reads only); the subsets' areas, then their best splits, one
 // size at a time, are spread over the lanes (cost, area and split in the
 // warp's shared arrays); lane 0 rewrites the nodes.
-__device__ void restructure_treelet(float4* nodes, int root, float* cost, float* area, unsigned char* split,
-                                    int lane) {
+__device__ void restructure_treelet(float4* nodes, int32_t* parent, int32_t* leaf_parent, int root, float* cost,
+                                    float* area, unsigned char* split, int lane) {
   float lb[kTreeletLeaves][6];
   int le[kTreeletLeaves];
   int inner[kTreeletLeaves - 1];
@@ -640,6 +645,10 @@ __device__ void restructure_treelet(float4* nodes, int root, float* cost, float*
           st_n[sp++] = enc[k];
         }
         for (int i = 0; i < 6; ++i) f[6 * k + i] = b[i];
+        // links of the new topology for a further pass (single-triangle
+        // leaves only: a range keeps its own chain of Morton nodes)
+        if (enc[k] >= 0) parent[enc[k]] = n;
+        else if (((~enc[k]) >> 28) == 0) leaf_parent[(~enc[k]) & 0x0fffffff] = n;
       }
       reinterpret_cast<int4*>(f)[3] = make_int4(enc[0], enc[1], 0, 0);
     }
@@ -650,7 +659,7 @@ __device__ void restructure_treelet(float4* nodes, int root, float* cost, float*
 // One warp per triangle climbs (lane 0 takes the arrival counters).
 constexpr int kTreeletWarps = 4;
 __global__ void __launch_bounds__(32 * kTreeletWarps) k_treelets(int T, int leaf_max, int gamma, float4* nodes,
-                                                                 const int32_t* parent, const int32_t* leaf_parent,
+                                                                 int32_t* parent, int32_t* leaf_parent,
                                                                  int32_t* flags, int32_t* err) {
   __shared__ float s_cost[kTreeletWarps][1 << kTreeletLeaves];
   __shared__ float s_area[kTreeletWarps][1 << kTreeletLeaves];
@@ -676,7 +685,8 @@ __global__ void __launch_bounds__(32 * kTreeletWarps) k_treelets(int T, int leaf
     __threadfence();
     size += other;
     // nodes inside a leaf range are never traversed
-    if (size > leaf_max && size >= gamma) restructure_treelet(nodes, node, s_cost[w], s_area[w], s_split[w], lane);
+    if (size > leaf_max && size >= gamma)
+      restructure_treelet(nodes, parent, leaf_parent, node, s_cost[w], s_area[w], s_split[w], lane);
     node = parent[node];
   }
 }
@@ -1148,8 +1158,13 @@ cudaError_t build_bvh(drt_scene* s, cudaStream_t st) {
   }
   DRT_PROF_LAUNCH("refit", st, k_refit<<<(T + kBlock - 1) / kBlock, kBlock, 0, st>>>(v, va, s->nodes, s->soup, s->child_orig, s->parent, s->leaf_parent, s->flags));
   if (T > s->leaf_max && T >= kTreeletLeaves) {
-    cudaMemsetAsync(s->flags, 0, sizeof(int32_t) * (T - 1), st);
-    DRT_PROF_LAUNCH("treelets", st, k_treelets<<<(T + kTreeletWarps - 1) / kTreeletWarps, 32 * kTreeletWarps, 0, st>>>(T, s->leaf_max, kTreeletLeaves, s->nodes, s->parent, s->leaf_parent, s->flags, s->ctx->err));
+    // further passes, on larger subtrees, need the links of the new topology,
+    // which the restructuring keeps for single-triangle leaves
+    int rounds = s->leaf_max == 1 ? DRT_TREELET_ROUNDS : 1;
+    for (int r = 0; r < rounds; ++r) {
+      cudaMemsetAsync(s->flags, 0, sizeof(int32_t) * (T - 1), st);
+      DRT_PROF_LAUNCH("treelets", st, k_treelets<<<(T + kTreeletWarps - 1) / kTreeletWarps, 32 * kTreeletWarps, 0, st>>>(T, s->leaf_max, kTreeletLeaves << r, s->nodes, s->parent, s->leaf_parent, s->flags, s->ctx->err));
+    }
   }
   return cudaGetLastError();
 }
