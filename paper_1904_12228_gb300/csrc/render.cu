@@ -357,10 +357,14 @@ __device__ __forceinline__ void nee_add(float3& L, float c, float3 t) {
 // path_value of a camera path (from depth 0, first emission counted) for the
 // 32 lanes of a warp together, traced by the warp-cooperative traversals.
 // All lanes call; a lane with act = false traces nothing, writes no tape and
-// returns 0.  Same values and tape entries as path_value.
+// returns 0.  Same values and tape entries as path_value.  pair_lanes: lanes
+// 2k and 2k+1 hold the two sides of one edge sample, whose term is zero when
+// both first hits are one triangle; such a pair stops after its first hit
+// (first_tri is still reported, and the caller discards the value).
 __device__ float3 path_value_warp(const SceneView& s, const Opts& op, const float o_in[3], const float d_in[3],
                                   bool act, uint32_t c0, uint32_t c1, uint32_t pass, int32_t* tape_tri,
-                                  float2* tape_bary, int64_t n_idx, int64_t n_stride, int* first_tri = nullptr) {
+                                  float2* tape_bary, int64_t n_idx, int64_t n_stride, int* first_tri = nullptr,
+                                  bool pair_lanes = false) {
   const unsigned full = 0xffffffffu;
   float o[3] = {o_in[0], o_in[1], o_in[2]}, d[3] = {d_in[0], d_in[1], d_in[2]};
   float3 L = zero3(), beta = make_float3(1.f, 1.f, 1.f);
@@ -385,6 +389,11 @@ __device__ float3 path_value_warp(const SceneView& s, const Opts& op, const floa
     }
     if (alive && h.tri < 0) alive = false;
     if (b == 0 && first_tri) *first_tri = alive ? h.tri : -1;
+    if (b == 0 && pair_lanes) {
+      int mine = alive ? h.tri : -1;
+      int other = __shfl_xor_sync(full, mine, 1);  // every lane, before any branch on alive
+      if (alive && mine == other) alive = false;
+    }
     Vertex x;
     x.k = -1;
     x.p[0] = x.p[1] = x.p[2] = 0.f;
@@ -459,7 +468,7 @@ __device__ float3 path_value_warp(const SceneView& s, const Opts& op, const floa
 // albedo (the throughput of what follows).
 __device__ float3 path_first_vertex_warp(const SceneView& s, const Opts& op, const float o[3], const float d[3],
                                          bool act, uint32_t c0, uint32_t c1, uint32_t pass, bool& cont, Hit& h0,
-                                         float nd[3], float3& alb, int* vis_out = nullptr) {
+                                         float nd[3], float3& alb, int* vis_out = nullptr, bool pair_lanes = false) {
   int md = op.primary_only ? 1 : op.max_depth;
   const float3 Le = ld3(s.radiance);
   float3 L = zero3();
@@ -473,6 +482,13 @@ __device__ float3 path_first_vertex_warp(const SceneView& s, const Opts& op, con
   trace_closest2_warp(s, o, d, o, d, alive, false, -1, -1, h, h_unused);
   if (alive && h.tri < 0) alive = false;
   h0 = h;
+  // the two sides of an edge sample (lanes 2k, 2k+1) on one triangle: a zero
+  // term, the caller discards this vertex; no shadow ray and no continuation
+  if (pair_lanes) {
+    int mine = alive ? h.tri : -1;
+    int other = __shfl_xor_sync(0xffffffffu, mine, 1);  // every lane, before any branch on alive
+    if (alive && mine == other) alive = false;
+  }
   Vertex x;
   x.k = -1;
   x.p[0] = x.p[1] = x.p[2] = 0.f;
@@ -2871,7 +2887,8 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
     float3 Lme, Lot;
     if (kStage == kPrimFused) {
       int ftri = -1;
-      Lme = path_value_warp(s, op, o, d, active, (uint32_t)j, 0u, kPassPrimaryEdge, nullptr, nullptr, 0, 0, &ftri);
+      Lme = path_value_warp(s, op, o, d, active, (uint32_t)j, 0u, kPassPrimaryEdge, nullptr, nullptr, 0, 0, &ftri,
+                            true);
       Lot = make_float3(__shfl_xor_sync(kFull, Lme.x, 1), __shfl_xor_sync(kFull, Lme.y, 1),
                         __shfl_xor_sync(kFull, Lme.z, 1));
       // both sides see the same triangle first: the edge bounds nothing
@@ -2883,7 +2900,8 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
       Hit h0;
       float nd[3];
       float3 alb;
-      float3 L0 = path_first_vertex_warp(s, op, o, d, active, (uint32_t)j, 0u, kPassPrimaryEdge, cont, h0, nd, alb);
+      float3 L0 = path_first_vertex_warp(s, op, o, d, active, (uint32_t)j, 0u, kPassPrimaryEdge, cont, h0, nd, alb,
+                                         nullptr, true);
       // both sides see the same triangle first: the sample's term is zero
       // and its paths need not go on
       int ftri = active ? h0.tri : -1;
