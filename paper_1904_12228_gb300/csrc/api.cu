@@ -127,7 +127,7 @@ void free_scene_buffers(drt_scene* s) {
                   s->w2c, s->light_cdf, s->light_area, s->light_box, s->nodes, s->soup, s->edges, s->edge_faces,
                   s->tile_w, s->pedge, s->plen, s->pcdf,
                   s->slen, s->scdf, s->scan_tmp, s->keys, s->keys2, s->vals, s->vals2, s->parent, s->leaf_parent,
-                  s->flags, s->child_orig, s->hist, s->hist_tmp, s->bounds, s->partials, s->esort.keys, s->esort.keys2,
+                  s->flags, s->tsize, s->child_orig, s->hist, s->hist_tmp, s->bounds, s->partials, s->esort.keys, s->esort.keys2,
                   s->esort.hist, s->esort.hist_tmp, s->esort.vals, s->esort.vals2, s->seg_edge, s->seg_tile,
                   s->seg_count, s->seg_scan_tmp, s->seg_s, s->seg_len, s->seg_a, s->seg_b, s->seg_cdf, s->seg_tmp,
                   s->sec.dp, s->sec.queue, s->sec.count, s->sec.pick, s->sec.nee, s->nee_hw, s->sec.hits, s->sec.lr,
@@ -428,7 +428,7 @@ drt_status drt_scene_upload(drt_context* ctx, const drt_scene_desc* d, void* str
   ALLOC(slen, std::max(1, E)) ALLOC(scdf, std::max(1, E)) ALLOC(scan_tmp, std::max(1, E / 1024 + 2))
   ALLOC(pguide, drt::kGuide + 1) ALLOC(sguide, drt::kGuide + 1)
   ALLOC(keys, T) ALLOC(keys2, T) ALLOC(vals, T) ALLOC(vals2, T) ALLOC(parent, std::max(1, T))
-  ALLOC(leaf_parent, T) ALLOC(flags, std::max(1, T)) ALLOC(child_orig, std::max(1, T)) ALLOC(hist, drt::radix_hist_entries(T))
+  ALLOC(leaf_parent, T) ALLOC(flags, std::max(1, T)) ALLOC(tsize, std::max(1, T)) ALLOC(child_orig, std::max(1, T)) ALLOC(hist, drt::radix_hist_entries(T))
   ALLOC(hist_tmp, drt::radix_hist_tmp_entries(T)) ALLOC(bounds, 8)
 #undef ALLOC
   if (stt != DRT_OK) {

@@ -462,7 +462,7 @@ __global__ void k_karras(const uint32_t* keys, int n, int leaf_max, float4* node
 
 // Triangle soup in leaf order and bottom-up refit with arrival counters.
 __global__ void k_refit(SceneView s, const int32_t* vals, float4* nodes, float4* soup, const int2* child_orig,
-                        const int32_t* parent, const int32_t* leaf_parent, int32_t* flags) {
+                        const int32_t* parent, const int32_t* leaf_parent, int32_t* flags, int32_t* tsize) {
   int pos = blockIdx.x * blockDim.x + threadIdx.x;
   if (pos >= s.T) return;
   int t = vals[pos];
@@ -487,6 +487,7 @@ __global__ void k_refit(SceneView s, const int32_t* vals, float4* nodes, float4*
   int child = ~pos;
   int node = leaf_parent[pos];
   int climb = 0;
+  int size = 1;  // triangles below `child`
   while (node >= 0) {
     if (++climb > s.T) {  // deeper than the tree can be: parent links are broken
       raise_flag(s.err, DRT_DEV_REFIT_CAP, pos);
@@ -502,8 +503,13 @@ __global__ void k_refit(SceneView s, const int32_t* vals, float4* nodes, float4*
       f[6] = lo[0]; f[7] = lo[1]; f[8] = lo[2]; f[9] = hi[0]; f[10] = hi[1]; f[11] = hi[2];
     }
     __threadfence();
-    if (atomicAdd(flags + node, 1) == 0) return;  // the sibling finishes this node
+    // the first to arrive leaves its triangle count; the sibling finishes
+    // this node with the sum
+    int other = atomicAdd(flags + node, size);
+    if (other == 0) return;
     __threadfence();
+    size += other;
+    tsize[node] = size;
     const float* o = reinterpret_cast<const float*>(n4) + (is_left ? 6 : 0);
     for (int k = 0; k < 3; ++k) {
       lo[k] = fminf(lo[k], __ldcg(o + k));
@@ -528,15 +534,18 @@ __global__ void k_refit(SceneView s, const int32_t* vals, float4* nodes, float4*
 // it.  Leaves, leaf ranges and every box of a leaf are unchanged, so the
 // hierarchy holds the same triangles in the same boxes and every traversal
 // finds the same hits; only the internal topology and its unions change.
-// One warp per triangle climbs the Morton hierarchy's parent links as in
-// k_refit; the second to reach a node processes it.  A treelet rewrites only
-// its root and nodes below it, so a node keeps its children until it is
-// processed, the set of nodes below it never changes, and the links stay
-// valid for the climb.  `flags` holds, per node, the triangle
-// count of the first child to arrive (zero before).
+// A pass starts one warp at every node it processes whose children it does
+// not (subtree triangle counts from the refit, kept up to date by the
+// rewrites); a warp climbs the parent links and processes each node once
+// every child of it that the pass processes is done (the second of two to
+// arrive goes on).  A treelet rewrites only its root and nodes below it, so
+// a node keeps its children until it is processed, the set of nodes below
+// it never changes, and the rewrites keep the links of the new topology for
+// the next pass.
 constexpr int kTreeletLeaves = 7;
 // Passes over the hierarchy, the k-th on subtrees of 7 * 2^k triangles or
-// more (of 1, 2 and 3 passes, 2 gave the fastest 200k-triangle depth-3 step).
+// more (of 1, 2 and 3 passes, 2 gave the fastest 200k-triangle depth-3 step;
+// hierarchies with leaf ranges take one).
 #ifndef DRT_TREELET_ROUNDS
 #define DRT_TREELET_ROUNDS 2
 #endif
@@ -559,7 +568,12 @@ __device__ __forceinline__ void node_child(const float4* nodes, int n, int k, fl
 // same treelet (reads only); the subsets' areas, then their best splits, one
 // size at a time, are spread over the lanes (cost, area and split in the
 // warp's shared arrays); lane 0 rewrites the nodes.
-__device__ void restructure_treelet(float4* nodes, int32_t* parent, int32_t* leaf_parent, int root, float* cost,
+// Triangles below a child reference: a leaf range's count, or the node's.
+__device__ __forceinline__ int child_size(const int32_t* tsize, int enc) {
+  return enc < 0 ? (((~enc) >> 28) + 1) : __ldcg(tsize + enc);
+}
+
+__device__ void restructure_treelet(float4* nodes, int32_t* parent, int32_t* tsize, int root, float* cost,
                                     float* area, unsigned char* split, int lane) {
   float lb[kTreeletLeaves][6];
   int le[kTreeletLeaves];
@@ -584,6 +598,8 @@ __device__ void restructure_treelet(float4* nodes, int32_t* parent, int32_t* lea
     ++nl;
   }
   if (nl < 3) return;  // two leaves: one topology
+  int lsz[kTreeletLeaves];
+  for (int i = 0; i < nl; ++i) lsz[i] = child_size(tsize, le[i]);
   const int full = (1 << nl) - 1;
   for (int m = lane + 1; m <= full; m += 32) {
     cost[m] = 0.0f;  // one leaf: its subtree is fixed
@@ -645,10 +661,15 @@ __device__ void restructure_treelet(float4* nodes, int32_t* parent, int32_t* lea
           st_n[sp++] = enc[k];
         }
         for (int i = 0; i < 6; ++i) f[6 * k + i] = b[i];
-        // links of the new topology for a further pass (single-triangle
-        // leaves only: a range keeps its own chain of Morton nodes)
-        if (enc[k] >= 0) parent[enc[k]] = n;
-        else if (((~enc[k]) >> 28) == 0) leaf_parent[(~enc[k]) & 0x0fffffff] = n;
+        // links and triangle counts of the new topology (for the climb and
+        // a further pass)
+        if (enc[k] >= 0) {
+          parent[enc[k]] = n;
+          int sz = 0;
+          for (int i = 0; i < nl; ++i)
+            if ((pm >> i) & 1) sz += lsz[i];
+          tsize[enc[k]] = sz;
+        }
       }
       reinterpret_cast<int4*>(f)[3] = make_int4(enc[0], enc[1], 0, 0);
     }
@@ -656,38 +677,44 @@ __device__ void restructure_treelet(float4* nodes, int32_t* parent, int32_t* lea
   __syncwarp();
 }
 
-// One warp per triangle climbs (lane 0 takes the arrival counters).
+// One warp per binary internal node; lane 0 takes the arrival counters.
 constexpr int kTreeletWarps = 4;
 __global__ void __launch_bounds__(32 * kTreeletWarps) k_treelets(int T, int leaf_max, int gamma, float4* nodes,
-                                                                 int32_t* parent, int32_t* leaf_parent,
-                                                                 int32_t* flags, int32_t* err) {
+                                                                 int32_t* parent, int32_t* tsize, int32_t* flags,
+                                                                 int32_t* err) {
   __shared__ float s_cost[kTreeletWarps][1 << kTreeletLeaves];
   __shared__ float s_area[kTreeletWarps][1 << kTreeletLeaves];
   __shared__ unsigned char s_split[kTreeletWarps][1 << kTreeletLeaves];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int pos = blockIdx.x * kTreeletWarps + w;
-  if (pos >= T || T < 2) return;  // uniform across the warp
-  int node = leaf_parent[pos];
-  int size = 1;
+  int node = blockIdx.x * kTreeletWarps + w;
+  if (node >= T - 1) return;  // uniform across the warp
+  // a node the pass processes: a subtree of at least gamma triangles that is
+  // not inside a leaf range (those are never traversed)
+  auto takes = [&](int enc) { return enc >= 0 && child_size(tsize, enc) > leaf_max && child_size(tsize, enc) >= gamma; };
+  if (!takes(node)) return;
+  int2 ch = __ldcg(reinterpret_cast<const int2*>(nodes + 4 * (size_t)node + 3));
+  if (takes(ch.x) || takes(ch.y)) return;  // a warp from below gets here
   int climb = 0;
-  while (node >= 0) {
+  while (true) {
     if (++climb > T) {
-      if (lane == 0 && err) raise_flag(err, DRT_DEV_REFIT_CAP, pos);
+      if (lane == 0 && err) raise_flag(err, DRT_DEV_REFIT_CAP, node);
       return;
     }
-    int other = 0;
-    if (lane == 0) {
+    restructure_treelet(nodes, parent, tsize, node, s_cost[w], s_area[w], s_split[w], lane);
+    int p = __ldcg(parent + node);
+    if (p < 0) return;
+    int2 pc = __ldcg(reinterpret_cast<const int2*>(nodes + 4 * (size_t)p + 3));
+    if (takes(pc.x) && takes(pc.y)) {  // two warps arrive: the second goes on
+      int other = 0;
+      if (lane == 0) {
+        __threadfence();
+        other = atomicAdd(flags + p, 1);
+      }
+      other = __shfl_sync(0xffffffffu, other, 0);
+      if (other == 0) return;
       __threadfence();
-      other = atomicAdd(flags + node, size);
     }
-    other = __shfl_sync(0xffffffffu, other, 0);
-    if (other == 0) return;  // the sibling's warp goes on
-    __threadfence();
-    size += other;
-    // nodes inside a leaf range are never traversed
-    if (size > leaf_max && size >= gamma)
-      restructure_treelet(nodes, parent, leaf_parent, node, s_cost[w], s_area[w], s_split[w], lane);
-    node = parent[node];
+    node = p;
   }
 }
 
@@ -1156,14 +1183,15 @@ cudaError_t build_bvh(drt_scene* s, cudaStream_t st) {
     cudaMemsetAsync(s->flags, 0, sizeof(int32_t) * (T - 1), st);
     DRT_PROF_LAUNCH("karras", st, k_karras<<<(T - 1 + kBlock - 1) / kBlock, kBlock, 0, st>>>(ka, T, s->leaf_max, s->nodes, s->child_orig, s->parent, s->leaf_parent));
   }
-  DRT_PROF_LAUNCH("refit", st, k_refit<<<(T + kBlock - 1) / kBlock, kBlock, 0, st>>>(v, va, s->nodes, s->soup, s->child_orig, s->parent, s->leaf_parent, s->flags));
+  DRT_PROF_LAUNCH("refit", st, k_refit<<<(T + kBlock - 1) / kBlock, kBlock, 0, st>>>(v, va, s->nodes, s->soup, s->child_orig, s->parent, s->leaf_parent, s->flags, s->tsize));
   if (T > s->leaf_max && T >= kTreeletLeaves) {
-    // further passes, on larger subtrees, need the links of the new topology,
-    // which the restructuring keeps for single-triangle leaves
+    // a second pass pays with single-triangle leaves (the 200k-triangle
+    // depth-3 step), not with two per leaf (the 5k-triangle direct-lighting
+    // step: 6.62 -> 6.98 ms)
     int rounds = s->leaf_max == 1 ? DRT_TREELET_ROUNDS : 1;
     for (int r = 0; r < rounds; ++r) {
       cudaMemsetAsync(s->flags, 0, sizeof(int32_t) * (T - 1), st);
-      DRT_PROF_LAUNCH("treelets", st, k_treelets<<<(T + kTreeletWarps - 1) / kTreeletWarps, 32 * kTreeletWarps, 0, st>>>(T, s->leaf_max, kTreeletLeaves << r, s->nodes, s->parent, s->leaf_parent, s->flags, s->ctx->err));
+      DRT_PROF_LAUNCH("treelets", st, k_treelets<<<(T - 1 + kTreeletWarps - 1) / kTreeletWarps, 32 * kTreeletWarps, 0, st>>>(T, s->leaf_max, kTreeletLeaves << r, s->nodes, s->parent, s->tsize, s->flags, s->ctx->err));
     }
   }
   return cudaGetLastError();

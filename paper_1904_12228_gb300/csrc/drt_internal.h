@@ -118,7 +118,8 @@ struct drt_scene {
   int *pguide = nullptr, *sguide = nullptr;  // guide tables of pcdf and scdf
   // LBVH build scratch
   uint32_t *keys = nullptr, *keys2 = nullptr;
-  int32_t *vals = nullptr, *vals2 = nullptr, *parent = nullptr, *leaf_parent = nullptr, *flags = nullptr;
+  int32_t *vals = nullptr, *vals2 = nullptr, *parent = nullptr, *leaf_parent = nullptr, *flags = nullptr,
+          *tsize = nullptr;  // triangles below each internal node (refit, treelet passes)
   int2* child_orig = nullptr;  // Karras children before leaf collapsing (refit)
   uint32_t* hist = nullptr;
   uint32_t* hist_tmp = nullptr;
