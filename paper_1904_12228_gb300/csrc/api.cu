@@ -127,7 +127,7 @@ void free_scene_buffers(drt_scene* s) {
                   s->w2c, s->light_cdf, s->light_area, s->light_box, s->nodes, s->soup, s->edges, s->edge_faces,
                   s->tile_w, s->pedge, s->plen, s->pcdf,
                   s->slen, s->scdf, s->scan_tmp, s->keys, s->keys2, s->vals, s->vals2, s->parent, s->leaf_parent,
-                  s->flags, s->tsize, s->child_orig, s->hist, s->hist_tmp, s->bounds, s->partials, s->esort.keys, s->esort.keys2,
+                  s->flags, s->tsize, s->child_orig, s->hist, s->hist_tmp, s->bounds, s->partials, s->esort.keys, s->esort.keys2, s->esort.rec,
                   s->esort.hist, s->esort.hist_tmp, s->esort.vals, s->esort.vals2, s->seg_edge, s->seg_tile,
                   s->seg_count, s->seg_scan_tmp, s->seg_s, s->seg_len, s->seg_a, s->seg_b, s->seg_cdf, s->seg_tmp,
                   s->sec.dp, s->sec.queue, s->sec.count, s->sec.pick, s->sec.nee, s->nee_hw, s->sec.hits, s->sec.lr,
@@ -760,7 +760,7 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
     if (n_edge > s->esort.cap) {
       cudaStreamSynchronize(st);
       drt::SortBuffers& b = s->esort;
-      void* old[] = {b.keys, b.keys2, b.hist, b.hist_tmp, b.vals, b.vals2};
+      void* old[] = {b.keys, b.keys2, b.hist, b.hist_tmp, b.vals, b.vals2, b.rec};
       for (void* p : old) dfree(p);
       b = drt::SortBuffers();
       int n = (int)n_edge;
@@ -770,6 +770,7 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
       if (a == DRT_OK) a = dalloc_n(&b.vals2, n);
       if (a == DRT_OK) a = dalloc_n(&b.hist, drt::radix_hist_entries(n));
       if (a == DRT_OK) a = dalloc_n(&b.hist_tmp, drt::radix_hist_tmp_entries(n));
+      if (a == DRT_OK) a = dalloc_n(&b.rec, 4 * (size_t)n);
       if (a != DRT_OK) {
         unstage(sg, 7, st);
         return a;

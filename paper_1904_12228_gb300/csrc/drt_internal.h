@@ -85,6 +85,7 @@ struct PoolScratch {
 struct SortBuffers {
   uint32_t *keys = nullptr, *keys2 = nullptr, *hist = nullptr, *hist_tmp = nullptr;
   int32_t *vals = nullptr, *vals2 = nullptr;
+  float4* rec = nullptr;  // [4 * cap] the samples themselves, by sample index (the key pass keeps them)
   int64_t cap = 0;  // samples the buffers hold
 };
 }  // namespace drt

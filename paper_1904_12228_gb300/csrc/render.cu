@@ -2733,6 +2733,29 @@ struct EdgeSample {
   float t;             // fisheye: parameter of the point along the 3D edge
   double inv_pdf_len;  // 1 / (point density per unit screen length); fisheye: 1 / P(edge)
 };
+// An edge sample as four float4 (bit for bit), written by the key pass and
+// read back in screen order by the kernels that evaluate it.
+__device__ __forceinline__ void store_sample(float4* rec, int64_t j, const EdgeSample& es) {
+  float4* r = rec + 4 * j;
+  r[0] = make_float4(es.x, es.y, es.dx, es.dy);
+  r[1] = make_float4(es.ax, es.ay, es.bx, es.by);
+  r[2] = make_float4(es.t, __int_as_float(es.e), __int_as_float(es.seg), es.valid ? 1.0f : 0.0f);
+  r[3] = make_float4(__int_as_float(__double2loint(es.inv_pdf_len)), __int_as_float(__double2hiint(es.inv_pdf_len)),
+                     0.0f, 0.0f);
+}
+__device__ __forceinline__ EdgeSample load_sample(const float4* rec, int64_t j) {
+  const float4* r = rec + 4 * j;
+  float4 a = r[0], b = r[1], c = r[2], d = r[3];
+  EdgeSample es;
+  es.x = a.x; es.y = a.y; es.dx = a.z; es.dy = a.w;
+  es.ax = b.x; es.ay = b.y; es.bx = b.z; es.by = b.w;
+  es.t = c.x;
+  es.e = __float_as_int(c.y);
+  es.seg = __float_as_int(c.z);
+  es.valid = c.w != 0.0f;
+  es.inv_pdf_len = __hiloint2double(__float_as_int(d.y), __float_as_int(d.x));
+  return es;
+}
 // A point of a 3D edge, v0 + t (v1 - v0), FP32 in a fixed order.
 __device__ __forceinline__ void edge_point3(float3 v0, float3 v1, float t, float p[3]) {
   p[0] = fa(v0.x, fm(t, fs(v1.x, v0.x)));
@@ -2817,13 +2840,14 @@ __device__ __forceinline__ uint32_t spread_bits16(uint32_t x) {
 // Screen-space Morton key of every primary edge sample, so the samples can be
 // evaluated in screen order (coherent rays, aggregated scatter).  Only the
 // evaluation order changes; each sample's arithmetic is the same.
-__global__ void k_primary_keys(SceneView s, Opts op, int64_t n_edge, uint32_t* keys, int32_t* vals) {
+__global__ void k_primary_keys(SceneView s, Opts op, int64_t n_edge, uint32_t* keys, int32_t* vals, float4* rec) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n_edge) return;
   double ptotal = s.pcdf[s.E - 1];
   uint32_t key = 0;
   if (ptotal > 0.0) {
     EdgeSample es = primary_sample(s, op, j, ptotal);
+    if (rec) store_sample(rec, j, es);  // the evaluation reads it back
     // position at 1/kKeySub of a pixel
     int px = min(max((int)floorf(es.x * kKeySub), 0), s.W * kKeySub - 1);
     int py = min(max((int)floorf(es.y * kKeySub), 0), s.H * kKeySub - 1);
@@ -2845,7 +2869,8 @@ enum { kPrimFused = 0, kPrimFirst = 1, kPrimFinish = 2 };
 template <int kStage = kPrimFused>
 __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op, const float* d_image, Grads gr,
                                               int64_t n_edge, int64_t per_thread, const int32_t* order,
-                                              int64_t blk, PathStage ps = PathStage{}) {
+                                              int64_t blk, PathStage ps = PathStage{},
+                                              const float4* rec = nullptr) {
   float g[kGlobals];
   for (int i = 0; i < kGlobals; ++i) g[i] = 0.f;
   double ptotal = s.pcdf[s.E - 1];
@@ -2865,7 +2890,7 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
     for (int q = 0; q < kGlobals; ++q) gs[q] = 0.f;
     EdgeSample es = {};
     if (active && side == 0) {
-      es = primary_sample(s, op, j, ptotal);
+      es = rec ? load_sample(rec, j) : primary_sample(s, op, j, ptotal);
       active = es.valid;
     }
     // the odd lane takes the sample's point and direction from its pair
@@ -2992,18 +3017,18 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
 }
 __global__ void __launch_bounds__(kBlock, DRT_PRIMARY_MIN_BLOCKS) k_backward_primary(SceneView s, Opts op, const float* d_image, Grads gr,
                                                              int64_t n_edge, int64_t per_thread,
-                                                             const int32_t* order) {
-  primary_block(s, op, d_image, gr, n_edge, per_thread, order, blockIdx.x);
+                                                             const int32_t* order, const float4* rec) {
+  primary_block(s, op, d_image, gr, n_edge, per_thread, order, blockIdx.x, PathStage{}, rec);
 }
 __global__ void __launch_bounds__(kBlock, DRT_PRIMARY_MIN_BLOCKS)
     k_primary_first(SceneView s, Opts op, const float* d_image, Grads gr, int64_t n_edge, int64_t per_thread,
-                    const int32_t* order, PathStage ps) {
-  primary_block<kPrimFirst>(s, op, d_image, gr, n_edge, per_thread, order, blockIdx.x, ps);
+                    const int32_t* order, PathStage ps, const float4* rec) {
+  primary_block<kPrimFirst>(s, op, d_image, gr, n_edge, per_thread, order, blockIdx.x, ps, rec);
 }
 __global__ void __launch_bounds__(kBlock, DRT_PRIMARY_MIN_BLOCKS)
     k_primary_finish(SceneView s, Opts op, const float* d_image, Grads gr, int64_t n_edge, int64_t per_thread,
-                     const int32_t* order, PathStage ps) {
-  primary_block<kPrimFinish>(s, op, d_image, gr, n_edge, per_thread, order, blockIdx.x, ps);
+                     const int32_t* order, PathStage ps, const float4* rec) {
+  primary_block<kPrimFinish>(s, op, d_image, gr, n_edge, per_thread, order, blockIdx.x, ps, rec);
 }
 
 __global__ void k_debug_closest(SceneView s, int64_t n, const float* o, const float* d, int32_t* tri, float* tb) {
@@ -3395,6 +3420,7 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
   // beside the secondary and interior passes, and are joined back before the
   // primary edge kernel.
   const int32_t* order = nullptr;
+  const float4* rec = nullptr;  // the samples, kept by the key pass
   bool forked = false;
   if (blocks_e > 0 && sort && sort->cap >= n_edge) {
     cudaStream_t ss = st;
@@ -3410,7 +3436,8 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
     int bits = screen_key_bits(s.W, s.H);
     DRT_PROF_LAUNCH("primary_keys", ss,
                     k_primary_keys<<<(unsigned)((n_edge + kBlock - 1) / kBlock), kBlock, 0, ss>>>(
-                        s, op, n_edge, sort->keys, sort->vals));
+                        s, op, n_edge, sort->keys, sort->vals, sort->rec));
+    rec = sort->rec;
     bool alt = radix_sort_pairs(sort->keys, sort->vals, sort->keys2, sort->vals2, sort->hist, sort->hist_tmp,
                                 (int)n_edge, bits, ss);
     order = alt ? sort->vals2 : sort->vals;
@@ -3499,7 +3526,7 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
     if (forked) cudaStreamWaitEvent(st, sc->ctx->join, 0);
     s.counters = counter_slot(kSlotBwdPrimary);
     ProfToken pt = prof_begin("backward_primary_edges", st);
-    k_backward_primary<<<(unsigned)blocks_e, kBlock, 0, st>>>(s, op, d_image, ge, n_edge, per_thread, order);
+    k_backward_primary<<<(unsigned)blocks_e, kBlock, 0, st>>>(s, op, d_image, ge, n_edge, per_thread, order, rec);
     prof_end(pt, st);
   } else if (prim_staged) {
     // beyond one vertex: the first vertex of both side paths (coherent rays in
@@ -3512,7 +3539,7 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
     s.counters = counter_slot(kSlotBwdPrimary);
     DRT_PROF_LAUNCH("backward_primary_first", st,
                     k_primary_first<<<(unsigned)blocks_e, kBlock, 0, st>>>(s, op, d_image, ge, n_edge, per_thread,
-                                                                            order, ps));
+                                                                            order, ps, rec));
     BatchScene t;
     std::memset(&t, 0, sizeof(t));
     t.v = s;
@@ -3543,7 +3570,7 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
     s.counters = nullptr;
     DRT_PROF_LAUNCH("backward_primary_finish", st,
                     k_primary_finish<<<(unsigned)blocks_e, kBlock, 0, st>>>(s, op, d_image, ge, n_edge, per_thread,
-                                                                             order, ps));
+                                                                             order, ps, rec));
   }
   cudaError_t e = launch_reduce_globals(partials, (need_i ? blocks_i : 0) + blocks_e, d_radiance, d_cam, d_cam_scale,
                                         st);
