@@ -2734,10 +2734,13 @@ struct EdgeSample {
   double inv_pdf_len;  // 1 / (point density per unit screen length); fisheye: 1 / P(edge)
 };
 // An edge sample as four float4 (bit for bit), written by the key pass and
-// read back in screen order by the kernels that evaluate it.
+// read back in screen order by the kernels that evaluate it.  The first
+// float4 alone (point, direction; NaN point: no valid sample) is what the
+// first vertex of the side paths needs, one sector per sample of the
+// scattered reads.
 __device__ __forceinline__ void store_sample(float4* rec, int64_t j, const EdgeSample& es) {
   float4* r = rec + 4 * j;
-  r[0] = make_float4(es.x, es.y, es.dx, es.dy);
+  r[0] = es.valid ? make_float4(es.x, es.y, es.dx, es.dy) : make_float4(NAN, NAN, NAN, NAN);
   r[1] = make_float4(es.ax, es.ay, es.bx, es.by);
   r[2] = make_float4(es.t, __int_as_float(es.e), __int_as_float(es.seg), es.valid ? 1.0f : 0.0f);
   r[3] = make_float4(__int_as_float(__double2loint(es.inv_pdf_len)), __int_as_float(__double2hiint(es.inv_pdf_len)),
@@ -2754,6 +2757,13 @@ __device__ __forceinline__ EdgeSample load_sample(const float4* rec, int64_t j) 
   es.seg = __float_as_int(c.z);
   es.valid = c.w != 0.0f;
   es.inv_pdf_len = __hiloint2double(__float_as_int(d.y), __float_as_int(d.x));
+  return es;
+}
+__device__ __forceinline__ EdgeSample load_sample_point(const float4* rec, int64_t j) {
+  float4 a = rec[4 * j];
+  EdgeSample es = {};
+  es.x = a.x; es.y = a.y; es.dx = a.z; es.dy = a.w;
+  es.valid = !isnan(a.x);
   return es;
 }
 // A point of a 3D edge, v0 + t (v1 - v0), FP32 in a fixed order.
@@ -2890,7 +2900,8 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
     for (int q = 0; q < kGlobals; ++q) gs[q] = 0.f;
     EdgeSample es = {};
     if (active && side == 0) {
-      es = rec ? load_sample(rec, j) : primary_sample(s, op, j, ptotal);
+      es = !rec ? primary_sample(s, op, j, ptotal)
+                : (kStage == kPrimFirst ? load_sample_point(rec, j) : load_sample(rec, j));
       active = es.valid;
     }
     // the odd lane takes the sample's point and direction from its pair
