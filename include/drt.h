@@ -17,7 +17,9 @@
  *   - Pointers to arrays may be device memory or host memory; the library
  *     checks each with cudaPointerGetAttributes.  Host inputs are copied to the
  *     device on `stream`; when an OUTPUT pointer is host memory the call
- *     synchronises `stream` before returning so the data is there.
+ *     synchronises `stream` before returning so the data is there.  The device
+ *     staging buffers of host arrays are kept per device for later calls
+ *     (at most 16) and released by drt_destroy.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All device
  *     work of a call is enqueued on it, in order.
  *   - Arrays are C-order float32 / int32 unless stated.  Images are [H,W,3],

@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 #include <climits>
 
@@ -79,8 +80,69 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device staging buffers for host arrays, kept per device for the next call
+// (a cudaMalloc and cudaFree per array and call cost more than the copies
+// and synchronised the device).  A buffer returns to its pool only after the
+// call that used it has synchronised its stream; drt_destroy releases the
+// device's pool.
+constexpr int kStageDevices = 64;
+constexpr size_t kStageKeep = 16;  // buffers kept per device
+std::mutex g_stage_mu;
+std::vector<std::pair<void*, size_t>> g_stage_pool[kStageDevices];
+
+int current_device() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return dev >= 0 && dev < kStageDevices ? dev : -1;
+}
+// The smallest pooled buffer of at least `bytes`, else a new one.
+drt_status stage_get(void** p, size_t bytes) {
+  int dev = current_device();
+  if (dev >= 0) {
+    std::lock_guard<std::mutex> lk(g_stage_mu);
+    auto& pool = g_stage_pool[dev];
+    int best = -1;
+    for (int i = 0; i < (int)pool.size(); ++i)
+      if (pool[i].second >= bytes && (best < 0 || pool[i].second < pool[best].second)) best = i;
+    if (best >= 0) {
+      *p = pool[best].first;
+      pool.erase(pool.begin() + best);
+      return DRT_OK;
+    }
+  }
+  return dalloc(p, bytes);
+}
+void stage_put(void* p, size_t bytes) {
+  if (!p) return;
+  int dev = current_device();
+  if (dev < 0) {
+    dfree(p);
+    return;
+  }
+  std::lock_guard<std::mutex> lk(g_stage_mu);
+  auto& pool = g_stage_pool[dev];
+  pool.emplace_back(p, bytes == 0 ? 16 : bytes);
+  if (pool.size() > kStageKeep) {  // drop the smallest
+    auto it = std::min_element(pool.begin(), pool.end(),
+                               [](const std::pair<void*, size_t>& a, const std::pair<void*, size_t>& b) {
+                                 return a.second < b.second;
+                               });
+    dfree(it->first);
+    pool.erase(it);
+  }
+}
+void stage_release_device(int dev) {
+  if (dev < 0 || dev >= kStageDevices) return;
+  std::lock_guard<std::mutex> lk(g_stage_mu);
+  for (auto& b : g_stage_pool[dev]) dfree(b.first);
+  g_stage_pool[dev].clear();
+}
+
 // A device view of a caller array: the array itself if it is device memory,
-// else a temporary device copy (inputs) or staging buffer (outputs).
+// else a device copy (inputs) or staging buffer (outputs) from the pool.
 struct Staged {
   void* dev = nullptr;
   void* user = nullptr;
@@ -97,7 +159,7 @@ drt_status stage(Staged& s, const void* user, size_t bytes, bool input, bool out
     s.dev = s.user;
     return DRT_OK;
   }
-  DRT_TRY(dalloc(&s.dev, bytes));
+  DRT_TRY(stage_get(&s.dev, bytes));
   s.temp = true;
   if (input) CUDA_TRY(cudaMemcpyAsync(s.dev, user, bytes, cudaMemcpyHostToDevice, st));
   return DRT_OK;
@@ -115,7 +177,7 @@ drt_status unstage(Staged* arr, int n, cudaStream_t st) {
   if (any || anytemp) CUDA_TRY(cudaStreamSynchronize(st));
   for (int i = 0; i < n; ++i)
     if (arr[i].temp) {
-      dfree(arr[i].dev);
+      stage_put(arr[i].dev, arr[i].bytes);
       arr[i].dev = nullptr;
       arr[i].temp = false;
     }
@@ -127,7 +189,7 @@ void free_scene_buffers(drt_scene* s) {
                   s->w2c, s->light_cdf, s->light_area, s->light_box, s->nodes, s->soup, s->edges, s->edge_faces,
                   s->tile_w, s->pedge, s->plen, s->pcdf,
                   s->slen, s->scdf, s->scan_tmp, s->keys, s->keys2, s->vals, s->vals2, s->parent, s->leaf_parent,
-                  s->flags, s->tsize, s->child_orig, s->hist, s->hist_tmp, s->bounds, s->partials, s->esort.keys, s->esort.keys2, s->esort.rec,
+                  s->flags, s->tsize, s->child_orig, s->hist, s->hist_tmp, s->bounds, s->partials, s->esort.keys, s->esort.keys2, s->esort.rec, s->esort.rec_sorted,
                   s->esort.hist, s->esort.hist_tmp, s->esort.vals, s->esort.vals2, s->seg_edge, s->seg_tile,
                   s->seg_count, s->seg_scan_tmp, s->seg_s, s->seg_len, s->seg_a, s->seg_b, s->seg_cdf, s->seg_tmp,
                   s->sec.dp, s->sec.queue, s->sec.count, s->sec.pick, s->sec.nee, s->nee_hw, s->sec.hits, s->sec.lr,
@@ -340,6 +402,7 @@ drt_status drt_destroy(drt_context* ctx) {
   if (ctx->join) cudaEventDestroy(ctx->join);
   if (ctx->side) cudaStreamDestroy(ctx->side);
   dfree(ctx->err);
+  stage_release_device(ctx->device);
   delete ctx;
   return DRT_OK;
 }
@@ -760,7 +823,7 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
     if (n_edge > s->esort.cap) {
       cudaStreamSynchronize(st);
       drt::SortBuffers& b = s->esort;
-      void* old[] = {b.keys, b.keys2, b.hist, b.hist_tmp, b.vals, b.vals2, b.rec};
+      void* old[] = {b.keys, b.keys2, b.hist, b.hist_tmp, b.vals, b.vals2, b.rec, b.rec_sorted};
       for (void* p : old) dfree(p);
       b = drt::SortBuffers();
       int n = (int)n_edge;
@@ -771,6 +834,7 @@ drt_status drt_render_backward(drt_context* ctx, drt_scene* s, const drt_tape* t
       if (a == DRT_OK) a = dalloc_n(&b.hist, drt::radix_hist_entries(n));
       if (a == DRT_OK) a = dalloc_n(&b.hist_tmp, drt::radix_hist_tmp_entries(n));
       if (a == DRT_OK) a = dalloc_n(&b.rec, 4 * (size_t)n);
+      if (a == DRT_OK) a = dalloc_n(&b.rec_sorted, 4 * (size_t)n);
       if (a != DRT_OK) {
         unstage(sg, 7, st);
         return a;

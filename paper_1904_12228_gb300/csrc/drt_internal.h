@@ -85,7 +85,8 @@ struct PoolScratch {
 struct SortBuffers {
   uint32_t *keys = nullptr, *keys2 = nullptr, *hist = nullptr, *hist_tmp = nullptr;
   int32_t *vals = nullptr, *vals2 = nullptr;
-  float4* rec = nullptr;  // [4 * cap] the samples themselves, by sample index (the key pass keeps them)
+  float4* rec = nullptr;         // [4 * cap] the samples themselves, by sample index (the key pass keeps them)
+  float4* rec_sorted = nullptr;  // [4 * cap] the same in screen order
   int64_t cap = 0;  // samples the buffers hold
 };
 }  // namespace drt

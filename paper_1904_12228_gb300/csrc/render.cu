@@ -2733,11 +2733,11 @@ struct EdgeSample {
   float t;             // fisheye: parameter of the point along the 3D edge
   double inv_pdf_len;  // 1 / (point density per unit screen length); fisheye: 1 / P(edge)
 };
-// An edge sample as four float4 (bit for bit), written by the key pass and
-// read back in screen order by the kernels that evaluate it.  The first
-// float4 alone (point, direction; NaN point: no valid sample) is what the
-// first vertex of the side paths needs, one sector per sample of the
-// scattered reads.
+// An edge sample as four float4 (bit for bit), written by the key pass by
+// sample index, gathered into screen order after the sort, and read there by
+// the kernels that evaluate it.  The first float4 alone (point, direction;
+// NaN point: no valid sample) is what the first vertex of the side paths
+// needs.
 __device__ __forceinline__ void store_sample(float4* rec, int64_t j, const EdgeSample& es) {
   float4* r = rec + 4 * j;
   r[0] = es.valid ? make_float4(es.x, es.y, es.dx, es.dy) : make_float4(NAN, NAN, NAN, NAN);
@@ -2850,6 +2850,14 @@ __device__ __forceinline__ uint32_t spread_bits16(uint32_t x) {
 // Screen-space Morton key of every primary edge sample, so the samples can be
 // evaluated in screen order (coherent rays, aggregated scatter).  Only the
 // evaluation order changes; each sample's arithmetic is the same.
+// rec_sorted[i] = rec[order[i]]: the samples in screen order (scattered
+// reads once here, sequential reads in the kernels that evaluate them).
+__global__ void k_gather_samples(const float4* rec, const int32_t* order, int64_t n, float4* rec_sorted) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // one float4 each
+  if (k >= 4 * n) return;
+  int64_t i = k >> 2;
+  rec_sorted[k] = rec[4 * (int64_t)order[i] + (k & 3)];
+}
 __global__ void k_primary_keys(SceneView s, Opts op, int64_t n_edge, uint32_t* keys, int32_t* vals, float4* rec) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n_edge) return;
@@ -2900,8 +2908,9 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
     for (int q = 0; q < kGlobals; ++q) gs[q] = 0.f;
     EdgeSample es = {};
     if (active && side == 0) {
+      // rec: the samples in screen order (position i)
       es = !rec ? primary_sample(s, op, j, ptotal)
-                : (kStage == kPrimFirst ? load_sample_point(rec, j) : load_sample(rec, j));
+                : (kStage == kPrimFirst ? load_sample_point(rec, i) : load_sample(rec, i));
       active = es.valid;
     }
     // the odd lane takes the sample's point and direction from its pair
@@ -3448,10 +3457,15 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
     DRT_PROF_LAUNCH("primary_keys", ss,
                     k_primary_keys<<<(unsigned)((n_edge + kBlock - 1) / kBlock), kBlock, 0, ss>>>(
                         s, op, n_edge, sort->keys, sort->vals, sort->rec));
-    rec = sort->rec;
     bool alt = radix_sort_pairs(sort->keys, sort->vals, sort->keys2, sort->vals2, sort->hist, sort->hist_tmp,
                                 (int)n_edge, bits, ss);
     order = alt ? sort->vals2 : sort->vals;
+    if (sort->rec && sort->rec_sorted) {
+      DRT_PROF_LAUNCH("primary_gather", ss,
+                      k_gather_samples<<<(unsigned)((4 * n_edge + kBlock - 1) / kBlock), kBlock, 0, ss>>>(
+                          sort->rec, order, n_edge, sort->rec_sorted));
+      rec = sort->rec_sorted;
+    }
     if (forked) cudaEventRecord(cx->join, ss);
   }
   const int32_t* tt = tape ? tape->tri : nullptr;
