@@ -86,7 +86,7 @@ struct SortBuffers {
   uint32_t *keys = nullptr, *keys2 = nullptr, *hist = nullptr, *hist_tmp = nullptr;
   int32_t *vals = nullptr, *vals2 = nullptr;
   float4* rec = nullptr;         // [4 * cap] the samples themselves, by sample index (the key pass keeps them)
-  float4* rec_sorted = nullptr;  // [4 * cap] the same in screen order
+  float4* rec_sorted = nullptr;  // [4 * cap] the same in screen order: n points, then 3 n float4 of the rest
   int64_t cap = 0;  // samples the buffers hold
 };
 }  // namespace drt

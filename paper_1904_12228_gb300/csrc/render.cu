@@ -2746,21 +2746,8 @@ __device__ __forceinline__ void store_sample(float4* rec, int64_t j, const EdgeS
   r[3] = make_float4(__int_as_float(__double2loint(es.inv_pdf_len)), __int_as_float(__double2hiint(es.inv_pdf_len)),
                      0.0f, 0.0f);
 }
-__device__ __forceinline__ EdgeSample load_sample(const float4* rec, int64_t j) {
-  const float4* r = rec + 4 * j;
-  float4 a = r[0], b = r[1], c = r[2], d = r[3];
-  EdgeSample es;
-  es.x = a.x; es.y = a.y; es.dx = a.z; es.dy = a.w;
-  es.ax = b.x; es.ay = b.y; es.bx = b.z; es.by = b.w;
-  es.t = c.x;
-  es.e = __float_as_int(c.y);
-  es.seg = __float_as_int(c.z);
-  es.valid = c.w != 0.0f;
-  es.inv_pdf_len = __hiloint2double(__float_as_int(d.y), __float_as_int(d.x));
-  return es;
-}
-__device__ __forceinline__ EdgeSample load_sample_point(const float4* rec, int64_t j) {
-  float4 a = rec[4 * j];
+__device__ __forceinline__ EdgeSample load_sample_point(const float4* pts, int64_t i) {
+  float4 a = pts[i];
   EdgeSample es = {};
   es.x = a.x; es.y = a.y; es.dx = a.z; es.dy = a.w;
   es.valid = !isnan(a.x);
@@ -2850,13 +2837,30 @@ __device__ __forceinline__ uint32_t spread_bits16(uint32_t x) {
 // Screen-space Morton key of every primary edge sample, so the samples can be
 // evaluated in screen order (coherent rays, aggregated scatter).  Only the
 // evaluation order changes; each sample's arithmetic is the same.
-// rec_sorted[i] = rec[order[i]]: the samples in screen order (scattered
-// reads once here, sequential reads in the kernels that evaluate them).
-__global__ void k_gather_samples(const float4* rec, const int32_t* order, int64_t n, float4* rec_sorted) {
+// The samples in screen order (scattered reads once here, sequential reads
+// in the kernels that evaluate them): sample order[i]'s first float4 (point
+// and direction) to pts[i], its other three to rest[3 i .. 3 i + 2].
+__global__ void k_gather_samples(const float4* rec, const int32_t* order, int64_t n, float4* pts, float4* rest) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // one float4 each
   if (k >= 4 * n) return;
   int64_t i = k >> 2;
-  rec_sorted[k] = rec[4 * (int64_t)order[i] + (k & 3)];
+  int c = (int)(k & 3);
+  float4 v = rec[4 * (int64_t)order[i] + c];
+  if (c == 0) pts[i] = v;
+  else rest[3 * i + c - 1] = v;
+}
+// A sample in screen order from the gathered arrays.
+__device__ __forceinline__ EdgeSample load_sorted_sample(const float4* pts, const float4* rest, int64_t i) {
+  float4 a = pts[i], b = rest[3 * i], c = rest[3 * i + 1], d = rest[3 * i + 2];
+  EdgeSample es;
+  es.x = a.x; es.y = a.y; es.dx = a.z; es.dy = a.w;
+  es.ax = b.x; es.ay = b.y; es.bx = b.z; es.by = b.w;
+  es.t = c.x;
+  es.e = __float_as_int(c.y);
+  es.seg = __float_as_int(c.z);
+  es.valid = c.w != 0.0f;
+  es.inv_pdf_len = __hiloint2double(__float_as_int(d.y), __float_as_int(d.x));
+  return es;
 }
 __global__ void k_primary_keys(SceneView s, Opts op, int64_t n_edge, uint32_t* keys, int32_t* vals, float4* rec) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -2888,7 +2892,7 @@ template <int kStage = kPrimFused>
 __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op, const float* d_image, Grads gr,
                                               int64_t n_edge, int64_t per_thread, const int32_t* order,
                                               int64_t blk, PathStage ps = PathStage{},
-                                              const float4* rec = nullptr) {
+                                              const float4* pts = nullptr, const float4* rest = nullptr) {
   float g[kGlobals];
   for (int i = 0; i < kGlobals; ++i) g[i] = 0.f;
   double ptotal = s.pcdf[s.E - 1];
@@ -2908,9 +2912,9 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
     for (int q = 0; q < kGlobals; ++q) gs[q] = 0.f;
     EdgeSample es = {};
     if (active && side == 0) {
-      // rec: the samples in screen order (position i)
-      es = !rec ? primary_sample(s, op, j, ptotal)
-                : (kStage == kPrimFirst ? load_sample_point(rec, i) : load_sample(rec, i));
+      // pts, rest: the samples in screen order (position i)
+      es = !pts ? primary_sample(s, op, j, ptotal)
+                : (kStage == kPrimFirst ? load_sample_point(pts, i) : load_sorted_sample(pts, rest, i));
       active = es.valid;
     }
     // the odd lane takes the sample's point and direction from its pair
@@ -3037,18 +3041,19 @@ __device__ __forceinline__ void primary_block(const SceneView& s, const Opts& op
 }
 __global__ void __launch_bounds__(kBlock, DRT_PRIMARY_MIN_BLOCKS) k_backward_primary(SceneView s, Opts op, const float* d_image, Grads gr,
                                                              int64_t n_edge, int64_t per_thread,
-                                                             const int32_t* order, const float4* rec) {
-  primary_block(s, op, d_image, gr, n_edge, per_thread, order, blockIdx.x, PathStage{}, rec);
+                                                             const int32_t* order, const float4* pts,
+                                                             const float4* rest) {
+  primary_block(s, op, d_image, gr, n_edge, per_thread, order, blockIdx.x, PathStage{}, pts, rest);
 }
 __global__ void __launch_bounds__(kBlock, DRT_PRIMARY_MIN_BLOCKS)
     k_primary_first(SceneView s, Opts op, const float* d_image, Grads gr, int64_t n_edge, int64_t per_thread,
-                    const int32_t* order, PathStage ps, const float4* rec) {
-  primary_block<kPrimFirst>(s, op, d_image, gr, n_edge, per_thread, order, blockIdx.x, ps, rec);
+                    const int32_t* order, PathStage ps, const float4* pts, const float4* rest) {
+  primary_block<kPrimFirst>(s, op, d_image, gr, n_edge, per_thread, order, blockIdx.x, ps, pts, rest);
 }
 __global__ void __launch_bounds__(kBlock, DRT_PRIMARY_MIN_BLOCKS)
     k_primary_finish(SceneView s, Opts op, const float* d_image, Grads gr, int64_t n_edge, int64_t per_thread,
-                     const int32_t* order, PathStage ps, const float4* rec) {
-  primary_block<kPrimFinish>(s, op, d_image, gr, n_edge, per_thread, order, blockIdx.x, ps, rec);
+                     const int32_t* order, PathStage ps, const float4* pts, const float4* rest) {
+  primary_block<kPrimFinish>(s, op, d_image, gr, n_edge, per_thread, order, blockIdx.x, ps, pts, rest);
 }
 
 __global__ void k_debug_closest(SceneView s, int64_t n, const float* o, const float* d, int32_t* tri, float* tb) {
@@ -3440,7 +3445,8 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
   // beside the secondary and interior passes, and are joined back before the
   // primary edge kernel.
   const int32_t* order = nullptr;
-  const float4* rec = nullptr;  // the samples, kept by the key pass
+  const float4* pts = nullptr;   // the samples, kept by the key pass, in screen order
+  const float4* rest = nullptr;
   bool forked = false;
   if (blocks_e > 0 && sort && sort->cap >= n_edge) {
     cudaStream_t ss = st;
@@ -3463,8 +3469,9 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
     if (sort->rec && sort->rec_sorted) {
       DRT_PROF_LAUNCH("primary_gather", ss,
                       k_gather_samples<<<(unsigned)((4 * n_edge + kBlock - 1) / kBlock), kBlock, 0, ss>>>(
-                          sort->rec, order, n_edge, sort->rec_sorted));
-      rec = sort->rec_sorted;
+                          sort->rec, order, n_edge, sort->rec_sorted, sort->rec_sorted + n_edge));
+      pts = sort->rec_sorted;
+      rest = sort->rec_sorted + n_edge;
     }
     if (forked) cudaEventRecord(cx->join, ss);
   }
@@ -3551,7 +3558,7 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
     if (forked) cudaStreamWaitEvent(st, sc->ctx->join, 0);
     s.counters = counter_slot(kSlotBwdPrimary);
     ProfToken pt = prof_begin("backward_primary_edges", st);
-    k_backward_primary<<<(unsigned)blocks_e, kBlock, 0, st>>>(s, op, d_image, ge, n_edge, per_thread, order, rec);
+    k_backward_primary<<<(unsigned)blocks_e, kBlock, 0, st>>>(s, op, d_image, ge, n_edge, per_thread, order, pts, rest);
     prof_end(pt, st);
   } else if (prim_staged) {
     // beyond one vertex: the first vertex of both side paths (coherent rays in
@@ -3564,7 +3571,7 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
     s.counters = counter_slot(kSlotBwdPrimary);
     DRT_PROF_LAUNCH("backward_primary_first", st,
                     k_primary_first<<<(unsigned)blocks_e, kBlock, 0, st>>>(s, op, d_image, ge, n_edge, per_thread,
-                                                                            order, ps, rec));
+                                                                            order, ps, pts, rest));
     BatchScene t;
     std::memset(&t, 0, sizeof(t));
     t.v = s;
@@ -3595,7 +3602,7 @@ cudaError_t launch_backward(const drt_scene* sc, const Opts& op, const drt_tape*
     s.counters = nullptr;
     DRT_PROF_LAUNCH("backward_primary_finish", st,
                     k_primary_finish<<<(unsigned)blocks_e, kBlock, 0, st>>>(s, op, d_image, ge, n_edge, per_thread,
-                                                                             order, ps, rec));
+                                                                             order, ps, pts, rest));
   }
   cudaError_t e = launch_reduce_globals(partials, (need_i ? blocks_i : 0) + blocks_e, d_radiance, d_cam, d_cam_scale,
                                         st);
