@@ -539,10 +539,15 @@ def run_workload(ctx, dev, wl, steps, warmup, rank, world, dist, flush, timed_ex
 
 
 def roofline_of(res, steps, peaks, wl):
+    """Roofline of the dominant kernel: the ray kernel (one with counted work)
+    with the most event time.  Kernels on the second stream (the sample keys
+    and their sort) are left out: their event times include waiting for the
+    kernels beside them."""
     kr = kernel_rooflines(res["prof"], res["counters"], steps, peaks["alu_ops"], peaks["l2_bytes"])
-    dom_name, (dom_ms, dom_launches) = max(res["prof"].items(), key=lambda kv: kv[1][0])
-    if dom_name not in kr:
+    if not kr:
         return None, kr
+    dom_name, (dom_ms, dom_launches) = max(((n, v) for n, v in res["prof"].items() if n in kr),
+                                           key=lambda kv: kv[1][0])
     k = kr[dom_name]
     binding = "alu" if k["alu"]["frac"] >= k["l2"]["frac"] else "l2"
     b = k[binding]
